@@ -1,0 +1,222 @@
+"""FETI-DP (Section 2.2, Eqs. 8-12) with corner primal DOFs (oracle).
+
+Test infrastructure only (see the package docstring).
+
+Each subdomain's DOFs split into primal corner DOFs c and the remaining DOFs
+r (Eq. 8); u_c^s = B_c^s u_c selects them from the global primal vector
+(Eq. 9); continuity of the r-DOFs is B_r u_r = 0 (Eq. 10).  Eliminating u_r
+from Eq. (11) gives Eq. (12):
+
+    F_rr   = B_r K_rr^{-1} B_r^T          F_rc = B_r K_rr^{-1} K_rc
+    Kbar_cc = K_cc - K_cr K_rr^{-1} K_rc  d_r  = B_r K_rr^{-1} f_r
+    fbar_c  = f_c - K_cr K_rr^{-1} f_r
+
+and condensing u_c (Section 2.2, last paragraph; u_c from the second row of
+Eq. 12) the dual problem on lambda alone:
+
+    (F_rr + F_rc Kbar_cc^{-1} F_rc^T) lambda = d_r - F_rc Kbar_cc^{-1} fbar_c.
+
+Readings:
+* Primal set: every non-fixed DOF at a vertex of the tile grid ("corner nodes
+  in a regular subdomain partitioning", Section 2.2), including vertices on
+  the outer boundary.
+* The printed fbar_c carries the index "kk" on K^{-1}; it is read as K_rr.
+* Fixed (Dirichlet) DOFs are eliminated from K^s; FETI-DP has no c-vector.
+* K_rr^{-1} is only ever needed on the DOFs that B_r touches (the "b" DOFs)
+  and on K_rc; the oracle forms those restrictions once per distinct
+  subdomain matrix (identical modules share them, Section 1).
+"""
+import hashlib
+
+import numpy as np
+import scipy.linalg as sla
+import scipy.sparse as sp
+
+from .assemble import local_dirichlet, local_load, local_stiffness, mesh_of, gather_global, element_moduli
+from .fem import element_stiffness
+from .scaling import Constraints, pairwise_rows, row_weights
+from .tfeti import schur_complement
+
+
+class _Module:
+    """Per-distinct-subdomain factorisation data (shared by identical modules)."""
+
+    def __init__(self, Ks, r_loc, c_loc, b_in_r):
+        self.Krr = Ks[np.ix_(r_loc, r_loc)]
+        self.Krc = Ks[np.ix_(r_loc, c_loc)]
+        self.Kcc = Ks[np.ix_(c_loc, c_loc)]
+        self.cho = sla.cho_factor(self.Krr, lower=True)
+        nr = self.Krr.shape[0]
+        Eb = np.zeros((nr, b_in_r.size))
+        Eb[b_in_r, np.arange(b_in_r.size)] = 1.0
+        KinvEb = sla.cho_solve(self.cho, Eb)
+        self.KinvKrc = sla.cho_solve(self.cho, self.Krc)             # K_rr^{-1} K_rc   [nr, nc]
+        self.Fb = KinvEb[b_in_r]                                       # [K_rr^{-1}]_bb  [nb, nb]
+        self.Fb = 0.5 * (self.Fb + self.Fb.T)
+        self.Frc_b = self.KinvKrc[b_in_r]                              # [K_rr^{-1} K_rc]_b
+        self.Kbar = self.Kcc - self.Krc.T @ self.KinvKrc               # local Kbar_cc^s
+        self.S = schur_complement(self.Krr, b_in_r)                    # Eq. (13) on r-DOFs
+
+
+class FETIDP:
+    def __init__(self, problem, scaling="k", dedup=True):
+        self.problem = problem
+        mesh = self.mesh = mesh_of(problem)
+        dim = self.dim = problem.dim
+        k0 = element_stiffness(dim, problem.nu)
+        E = element_moduli(problem)
+        ns = self.n_sub = mesh.n_sub
+        # --- global primal numbering (Eq. 9) ---
+        corner_nodes = [gn for gn in range(mesh.n_nodes) if mesh.is_tile_vertex(gn)]
+        self.primal = {}
+        for gn in corner_nodes:
+            for d in range(dim):
+                if not problem.dirichlet[gn * dim + d]:
+                    self.primal[gn * dim + d] = len(self.primal)
+        self.n_c = len(self.primal)
+        # --- per-subdomain split (Eq. 8) ---
+        self.r_loc, self.c_loc, self.c_glob = [], [], []
+        self.f_r, self.f_c = [], []
+        self.diagK = []
+        self.mod_key = []
+        self.modules = {}
+        Ks_cache = {}
+        for s in range(ns):
+            Ks = local_stiffness(problem, mesh, s, k0, E)
+            fs = local_load(problem, mesh, s)
+            fixed = local_dirichlet(problem, mesh, s)
+            g2 = mesh.local_to_global_nodes(s)
+            is_corner = np.repeat(np.array([mesh.is_tile_vertex(g) for g in g2]), dim)
+            gdofs = (g2[:, None] * dim + np.arange(dim)[None, :]).ravel()
+            r_loc = np.flatnonzero(~fixed & ~is_corner)
+            c_loc = np.flatnonzero(~fixed & is_corner)
+            self.r_loc.append(r_loc)
+            self.c_loc.append(c_loc)
+            self.c_glob.append(np.array([self.primal[g] for g in gdofs[c_loc]], dtype=np.int64))
+            self.f_r.append(fs[r_loc])
+            self.f_c.append(fs[c_loc])
+            self.diagK.append(np.diag(Ks).copy())
+            Ks_cache[s] = Ks
+        # --- B_r rows (Eq. 10): pair-wise rows at shared non-corner, non-fixed DOFs ---
+        pos_in_r = []
+        for s in range(ns):
+            p = -np.ones(mesh.n_loc_dofs, np.int64)
+            p[self.r_loc[s]] = np.arange(self.r_loc[s].size)
+            pos_in_r.append(p)
+        entries, sharing = [], []
+        for gn in range(mesh.n_nodes):
+            own = mesh.owners[gn]
+            if len(own) < 2 or mesh.is_tile_vertex(gn):
+                continue
+            for d in range(dim):
+                if problem.dirichlet[gn * dim + d]:
+                    continue
+                copies = [(s, ln * dim + d) for (s, ln) in own]
+                for row in pairwise_rows(copies):
+                    entries.append(row)
+                    sharing.append(copies)
+        cons_loc = Constraints(entries, sharing, np.zeros(len(entries)))
+        w = row_weights(cons_loc, self.diagK, scaling)
+        # re-express the rows on r-local indices
+        entries_r = [[(s, int(pos_in_r[s][k]), sg) for (s, k, sg) in ent] for ent in entries]
+        self.cons = Constraints(entries_r, sharing, np.zeros(len(entries)))
+        self.weights = w
+        self.n_lam = self.cons.n_lam
+        self.Br = [self.cons.B_sub(s, self.r_loc[s].size) for s in range(ns)]
+        self.Brt = [self.cons.B_sub(s, self.r_loc[s].size, w) for s in range(ns)]
+        self.bset = [np.unique(self.Br[s].indices) for s in range(ns)]
+        self.Bc = [sp.csr_matrix((np.ones(cg.size), (np.arange(cg.size), cg)), shape=(cg.size, self.n_c))
+                   for cg in self.c_glob]
+        # --- per-module factorisations ---
+        for s in range(ns):
+            Ks = Ks_cache.pop(s)
+            h = hashlib.sha1()
+            for a in (Ks, self.r_loc[s], self.c_loc[s], self.bset[s]):
+                h.update(np.ascontiguousarray(a).tobytes())
+            key = h.hexdigest() if dedup else s
+            if key not in self.modules:
+                self.modules[key] = _Module(Ks, self.r_loc[s], self.c_loc[s], self.bset[s])
+            self.mod_key.append(key)
+        # --- coarse problem and right-hand sides (Eq. 12) ---
+        Kbar = np.zeros((self.n_c, self.n_c))
+        fbar = np.zeros(self.n_c)
+        d_r = np.zeros(self.n_lam)
+        for s in range(ns):
+            M = self.mod(s)
+            cg = self.c_glob[s]
+            Kbar[np.ix_(cg, cg)] += M.Kbar
+            y = sla.cho_solve(M.cho, self.f_r[s])                      # K_rr^{-1} f_r^s
+            np.add.at(fbar, cg, self.f_c[s] - M.Krc.T @ y)
+            d_r += self.Br[s] @ y
+        self.Kbar = 0.5 * (Kbar + Kbar.T)
+        self.Kbar_cho = sla.cho_factor(self.Kbar, lower=True)
+        self.fbar = fbar
+        self.d_r = d_r
+        self.d = d_r - self.apply_Frc(sla.cho_solve(self.Kbar_cho, fbar)[:, None])[:, 0]
+        self.lam0 = np.zeros(self.n_lam)
+
+    def mod(self, s):
+        return self.modules[self.mod_key[s]]
+
+    # -- blocks of Eq. (12) ---------------------------------------------------
+    def apply_Frr(self, X):
+        Y = np.zeros((self.n_lam, X.shape[1]))
+        for s in range(self.n_sub):
+            b = self.bset[s]
+            Bb = self.Br[s][:, b]
+            Y += Bb @ (self.mod(s).Fb @ (Bb.T @ X))
+        return Y
+
+    def apply_FrcT(self, X):
+        V = np.zeros((self.n_c, X.shape[1]))
+        for s in range(self.n_sub):
+            b = self.bset[s]
+            Bb = self.Br[s][:, b]
+            np.add.at(V, self.c_glob[s], self.mod(s).Frc_b.T @ (Bb.T @ X))
+        return V
+
+    def apply_Frc(self, V):
+        Y = np.zeros((self.n_lam, V.shape[1]))
+        for s in range(self.n_sub):
+            b = self.bset[s]
+            Bb = self.Br[s][:, b]
+            Y += Bb @ (self.mod(s).Frc_b @ V[self.c_glob[s]])
+        return Y
+
+    # -- condensed operator used by the Krylov solvers --------------------------
+    def apply_F(self, X):
+        """(F_rr + F_rc Kbar_cc^{-1} F_rc^T) X for X [n_lam, m]."""
+        X = np.atleast_2d(X.T).T
+        V = sla.cho_solve(self.Kbar_cho, self.apply_FrcT(X))
+        return self.apply_Frr(X) + self.apply_Frc(V)
+
+    def project(self, X):
+        return X            # FETI-DP needs no projector
+
+    project_T = project
+
+    def precond_columns(self, r):
+        """Z = [..., B~_r^s S^s B~_r^sT r, ...]: one column per subdomain (Eq. 13 on r-DOFs)."""
+        Z = np.zeros((self.n_lam, self.n_sub))
+        for s in range(self.n_sub):
+            Bb = self.Brt[s][:, self.bset[s]]
+            Z[:, s] = Bb @ (self.mod(s).S @ (Bb.T @ r))
+        return Z
+
+    # -- recovery (second row of Eq. 12, then the second row of Eq. 11) ----------
+    def recover_local(self, lam):
+        uc = sla.cho_solve(self.Kbar_cho, self.fbar + self.apply_FrcT(lam[:, None])[:, 0])
+        us = []
+        for s in range(self.n_sub):
+            M = self.mod(s)
+            ucs = uc[self.c_glob[s]]
+            ur = sla.cho_solve(M.cho, self.f_r[s] - M.Krc @ ucs - self.Br[s].T @ lam)
+            u = np.zeros(self.mesh.n_loc_dofs)
+            u[self.r_loc[s]] = ur
+            u[self.c_loc[s]] = ucs
+            us.append(u)
+        return us, uc
+
+    def recover(self, lam):
+        us, _ = self.recover_local(lam)
+        return gather_global(self.mesh, self.dim, us, self.problem.dirichlet)

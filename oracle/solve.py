@@ -1,0 +1,21 @@
+"""One-call driver of the oracle: build the dual problem, run the Krylov
+solver, recover the global displacement (test infrastructure only)."""
+from .fetidp import FETIDP
+from .krylov import solve_dual
+from .tfeti import TFETI
+
+
+def build(problem, method="fetidp", scaling="k"):
+    if method == "tfeti":
+        return TFETI(problem, scaling)
+    if method == "fetidp":
+        return FETIDP(problem, scaling)
+    raise ValueError(method)
+
+
+def solve(problem, method="fetidp", scaling="k", krylov="rrs", tol=1e-6, max_iter=500,
+          rr_tol=1e-10, op=None):
+    """Returns (u_global, lambda, info, op)."""
+    op = op or build(problem, method, scaling)
+    lam, info = solve_dual(op, tol=tol, max_iter=max_iter, rr_tol=rr_tol, variant=krylov)
+    return op.recover(lam), lam, info, op

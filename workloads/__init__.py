@@ -1,0 +1,220 @@
+"""Seeded synthetic inputs for the FETI solvers: tile meshes, SIMP densities,
+Dirichlet masks and nodal loads.
+
+This module only *describes* state problems (array shapes, random fields,
+boundary masks).  It holds none of the solver's arithmetic: no stiffness,
+no tearing, no dual operator.  Both the CPU oracle and the CUDA path consume
+these descriptions, so a parity test feeds both sides bit-identical inputs.
+
+Conventions shared by every consumer (they are the library's public input
+format, not a method choice):
+
+* A problem is a regular grid of ``tiles`` subdomains (modules), each a
+  regular grid of ``elems`` unit square (2D) or unit cube (3D) elements.
+* Global elements are numbered lexicographically with x fastest, then y,
+  then z; global nodes likewise on the (n_el + 1)-per-axis node grid.
+* ``rho``: float64 [n_elements], the SIMP relative density of each element.
+* ``dirichlet``: uint8 [n_nodes * dim], 1 where that DOF is fixed to zero;
+  DOF ``dim * node + d``.
+* ``f``: float64 [n_nodes * dim], the global nodal load vector.
+
+The paper's own benchmark geometries (the laminated academic problems and
+the modular MBB-beam snapshots, Section 4) are not available; the seeded
+random fields below stand in for them with the same structure: fixed regular
+modular partitioning and stiffness contrast that reaches the interfaces.
+"""
+from __future__ import annotations
+
+import dataclasses
+import math
+from typing import List, Tuple
+
+import numpy as np
+
+__all__ = [
+    "Problem", "tile_problem", "gaussian_field", "binary_patterns",
+    "config1", "config2", "config3", "config4", "config5",
+]
+
+
+@dataclasses.dataclass
+class Problem:
+    """One linear-elastic state problem on a tile grid (see module doc)."""
+
+    name: str
+    dim: int
+    tiles: Tuple[int, ...]
+    elems: Tuple[int, ...]
+    E0: float
+    Emin: float
+    nu: float
+    p: float
+    rho: np.ndarray
+    dirichlet: np.ndarray
+    f: np.ndarray
+
+    @property
+    def n_el_axis(self) -> Tuple[int, ...]:
+        return tuple(t * e for t, e in zip(self.tiles, self.elems))
+
+    @property
+    def n_node_axis(self) -> Tuple[int, ...]:
+        return tuple(n + 1 for n in self.n_el_axis)
+
+    @property
+    def n_elements(self) -> int:
+        return int(np.prod(self.n_el_axis))
+
+    @property
+    def n_nodes(self) -> int:
+        return int(np.prod(self.n_node_axis))
+
+    @property
+    def n_dofs(self) -> int:
+        return self.n_nodes * self.dim
+
+    @property
+    def n_subdomains(self) -> int:
+        return int(np.prod(self.tiles))
+
+    def node_id(self, *ijk: int) -> int:
+        nn = self.n_node_axis
+        if self.dim == 2:
+            return ijk[0] + nn[0] * ijk[1]
+        return ijk[0] + nn[0] * (ijk[1] + nn[1] * ijk[2])
+
+
+def _empty_bc(dim, tiles, elems):
+    nn = [t * e + 1 for t, e in zip(tiles, elems)]
+    n_nodes = int(np.prod(nn))
+    return nn, np.zeros(n_nodes * dim, np.uint8), np.zeros(n_nodes * dim, np.float64)
+
+
+def tile_problem(name, dim, tiles, elems, rho, *, bc="clamped_left", E0=1.0,
+                 Emin=1e-6, nu=0.3, p=3.0) -> Problem:
+    """Wrap a density field with one of the boundary-condition recipes.
+
+    ``clamped_left``: every node on x = 0 is fixed in all directions; a unit
+    point load acts in -y (2D) or -z (3D) at the middle node of the x = max
+    edge (2D) or face (3D).
+    ``mbb``: the two bottom corner nodes (x = 0 and x = max at y = 0) are
+    fixed in x and y; a unit -y load acts at the midspan node of the top edge.
+    """
+    tiles = tuple(int(t) for t in tiles)
+    elems = tuple(int(e) for e in elems)
+    nn, dmask, f = _empty_bc(dim, tiles, elems)
+    def nid(*ijk):
+        if dim == 2:
+            return ijk[0] + nn[0] * ijk[1]
+        return ijk[0] + nn[0] * (ijk[1] + nn[1] * ijk[2])
+    if bc == "clamped_left":
+        if dim == 2:
+            for j in range(nn[1]):
+                n = nid(0, j)
+                dmask[2 * n:2 * n + 2] = 1
+            f[2 * nid(nn[0] - 1, (nn[1] - 1) // 2) + 1] = -1.0
+        else:
+            for k in range(nn[2]):
+                for j in range(nn[1]):
+                    n = nid(0, j, k)
+                    dmask[3 * n:3 * n + 3] = 1
+            f[3 * nid(nn[0] - 1, (nn[1] - 1) // 2, (nn[2] - 1) // 2) + 2] = -1.0
+    elif bc == "mbb":
+        assert dim == 2
+        for n in (nid(0, 0), nid(nn[0] - 1, 0)):
+            dmask[2 * n:2 * n + 2] = 1
+        f[2 * nid((nn[0] - 1) // 2, nn[1] - 1) + 1] = -1.0
+    else:
+        raise ValueError(bc)
+    rho = np.ascontiguousarray(rho, dtype=np.float64).reshape(-1)
+    assert rho.size == int(np.prod([t * e for t, e in zip(tiles, elems)]))
+    return Problem(name, dim, tiles, elems, float(E0), float(Emin), float(nu), float(p),
+                   rho, dmask, f)
+
+
+def gaussian_field(shape, sigma, rng) -> np.ndarray:
+    """Smoothed Gaussian random field mapped to (0, 1).
+
+    White noise -> periodic Gaussian filter of standard deviation ``sigma``
+    (in elements, applied in Fourier space) -> standardise -> standard normal
+    CDF.  Returned with axis 0 = x (so ``.ravel(order='F')`` is the global
+    lexicographic element order).
+    """
+    noise = rng.standard_normal(shape)
+    freqs = [np.fft.fftfreq(n) for n in shape]
+    grids = np.meshgrid(*freqs, indexing="ij")
+    k2 = sum(g * g for g in grids)
+    kernel = np.exp(-2.0 * (math.pi ** 2) * (sigma ** 2) * k2)
+    field = np.real(np.fft.ifftn(np.fft.fftn(noise) * kernel))
+    field = (field - field.mean()) / max(field.std(), 1e-300)
+    from scipy.special import ndtr
+    return ndtr(field)
+
+
+def _assemble_tiles(tile_fields: List[np.ndarray], tiles, elems) -> np.ndarray:
+    """Place per-tile element fields (axis 0 = x) into the global lexicographic array."""
+    dim = len(tiles)
+    full = np.empty(tuple(t * e for t, e in zip(tiles, elems)), np.float64)
+    for s, fld in enumerate(tile_fields):
+        idx = np.unravel_index(s, tiles, order="F")
+        sl = tuple(slice(i * e, (i + 1) * e) for i, e in zip(idx, elems))
+        full[sl] = fld
+    return full.ravel(order="F") if dim else full
+
+
+def binary_patterns(n_patterns, elems, sigma, rng, lo=1e-3, hi=1.0):
+    """Binary module patterns: smoothed field thresholded at 0.5 -> {lo, hi}."""
+    return [np.where(gaussian_field(tuple(elems), sigma, rng) >= 0.5, hi, lo)
+            for _ in range(n_patterns)]
+
+
+def config1(seed: int = 0) -> Problem:
+    """2x2 subdomains of 8x8 Q4, rho ~ U[0,1] i.i.d., Emin = 1e-6."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    tiles, elems = (2, 2), (8, 8)
+    rho = rng.uniform(0.0, 1.0, size=16 * 16)
+    return tile_problem("2x2 tiles of 8x8 Q4, iid U[0,1]", 2, tiles, elems, rho, Emin=1e-6)
+
+
+def config2(tiles: int = 16, elems: int = 32, n_patterns: int = 4, seed: int = 1,
+            sigma: float = 4.0) -> Problem:
+    """Modular tiles: each subdomain carries one of ``n_patterns`` seeded binary
+    patterns (rho in {1e-3, 1}), Emin = 0 so the contrast after p = 3 is 1e9."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    pats = binary_patterns(n_patterns, (elems, elems), sigma, rng)
+    choice = rng.integers(0, n_patterns, size=tiles * tiles)
+    rho = _assemble_tiles([pats[c] for c in choice], (tiles, tiles), (elems, elems))
+    return tile_problem(f"{tiles}x{tiles} tiles of {elems}x{elems} Q4, {n_patterns} binary modules",
+                        2, (tiles, tiles), (elems, elems), rho, Emin=0.0)
+
+
+def config3(n_problems: int = 64, seed: int = 3, tile_range=(4, 24), elem_range=(16, 48),
+            sigma: float = 8.0) -> List[Problem]:
+    """Many independent 2D state problems of uneven size (batching workload)."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    out = []
+    for q in range(n_problems):
+        t = int(rng.integers(tile_range[0], tile_range[1] + 1))
+        e = int(rng.integers(elem_range[0], elem_range[1] + 1))
+        fld = gaussian_field((t * e, t * e), sigma, rng)
+        rho = np.where(fld >= 0.5, 1.0, 0.0).ravel(order="F")
+        out.append(tile_problem(f"batch[{q}] {t}x{t} tiles of {e}x{e}", 2, (t, t), (e, e), rho,
+                                Emin=1e-6))
+    return out
+
+
+def config4(tiles: int = 8, elems: int = 8, seed: int = 4, sigma: float = 8.0) -> Problem:
+    """3D H8: tiles^3 subdomains of elems^3 elements, smoothed field clipped to [1e-3, 1]."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    n = tiles * elems
+    fld = np.clip(gaussian_field((n, n, n), sigma, rng), 1e-3, 1.0)
+    return tile_problem(f"{tiles}^3 tiles of {elems}^3 H8, smoothed field", 3,
+                        (tiles,) * 3, (elems,) * 3, fld.ravel(order="F"), Emin=0.0)
+
+
+def config5(tiles: int = 32, elems: int = 64, volfrac: float = 0.4) -> Problem:
+    """MBB-type beam for the compliance / sensitivity loop: uniform start density."""
+    n = tiles * elems
+    rho = np.full(n * n, volfrac)
+    return tile_problem(f"MBB beam {tiles}x{tiles} tiles of {elems}x{elems}", 2, (tiles, tiles),
+                        (elems, elems), rho, bc="mbb", Emin=1e-6)
