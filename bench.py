@@ -1,0 +1,326 @@
+#!/usr/bin/env python
+"""Benchmark of the FETI dual-operator hot path on one GB300 (or N replicas).
+
+Workload: the modular 2D problem -- 16x16 subdomains of 32x32 bilinear
+elements (526,338 DOF), each tile one of 4 seeded binary modules with
+densities {1e-3, 1} and Emin = 0 (stiffness contrast 1e9 after p = 3),
+clamped left edge, unit load at the mid-right node.  Solver: FETI-DP with
+corner primals, k-scaling and rank-revealing Simultaneous FETI, FP64,
+relative residual 1e-6.
+
+One step = factorize (SIMP assembly, banded + dense Cholesky, local dual
+blocks, coarse problem) + solve_dual (Algorithm 1) + recover_displacements,
+on inputs resident in HBM.  The metric is dual-operator columns applied per
+second over the whole step ("F-applies/s"); time-to-solve is reported beside
+it.  ``e2e`` repeats the step through the public API from host buffers
+(set-up with host->device copies, result copied back).
+
+``--impl reference`` times the FP64 CPU oracle on a bounded sample of the
+same workload instead (rank 0 only).
+"""
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+import workloads  # noqa: E402
+
+METRIC = "F-applies/s & time-to-solve @rel.res 1e-6 vs plain FP64; % of HBM roofline"
+FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.070e9 / 1e12   # 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--tiles", type=int, default=16)
+    ap.add_argument("--elems", type=int, default=32)
+    ap.add_argument("--tol", type=float, default=1e-6)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    return ap.parse_args()
+
+
+def workload_config(a, extra=None):
+    cfg = {"workload": f"modular 2D Q4: {a.tiles}x{a.tiles} subdomains of {a.elems}x{a.elems} elements, "
+                       f"4 binary modules, contrast 1e9",
+           "tiles": a.tiles, "elems": a.elems, "method": "FETI-DP (corner primals)", "scaling": "k",
+           "krylov": "rank-revealing S-FETI", "rel_tol": a.tol, "precision": "fp64",
+           "parallelism": "replicas", "l2": "flushed (256 MB write) between timed steps"}
+    if extra:
+        cfg.update(extra)
+    return cfg
+
+
+# ------------------------------------------------------------------ clocks
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.rows = []
+        self.proc = None
+        self.thread = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+            return
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.rows.append([x.strip() for x in line.split(",")])
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.thread.join(timeout=5)
+        sm = [float(r[1]) for r in self.rows if len(r) >= 9 and r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in self.rows if len(r) >= 9 and r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = set()
+        for r in self.rows:
+            if len(r) >= 9:
+                for k, nm in enumerate(names):
+                    if r[5 + k].lower() == "active":
+                        reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ------------------------------------------------------------------ oracle baseline
+def oracle_sample(a, tiles=8):
+    """The oracle (as it stands) on a bounded sample of the workload: the same
+    32x32 modules and boundary recipe on a tiles x tiles grid, full FETI-DP +
+    k + RRS solve.  Returns (F-applies/s, seconds, description)."""
+    import oracle
+    p = workloads.config2(tiles=tiles, elems=a.elems)
+    t0 = time.perf_counter()
+    u, lam, info, op = oracle.solve(p, "fetidp", "k", "rrs", tol=a.tol)
+    dt = time.perf_counter() - t0
+    return info.f_applies / dt, dt, (f"oracle FETI-DP+k+RRS full step (build+solve+recover) on a {tiles}x{tiles}-tile "
+                                     f"sample of the same {a.elems}x{a.elems} modules: {info.f_applies} F-applies, "
+                                     f"{info.iterations} iterations, {dt:.1f} s")
+
+
+def cpu_threads():
+    try:
+        return len(os.sched_getaffinity(0))
+    except AttributeError:
+        return os.cpu_count()
+
+
+# ------------------------------------------------------------------ our arm
+def run_ours(a, rank, world):
+    import torch
+
+    import paper_2111_11728_gb300 as fg
+    dev = torch.device("cuda", int(os.environ.get("LOCAL_RANK", 0)))
+    torch.cuda.set_device(dev)
+    stream = torch.cuda.current_stream()
+    p = workloads.config2(tiles=a.tiles, elems=a.elems)
+    rho_d = torch.from_numpy(p.rho).to(dev)
+    f_d = torch.from_numpy(p.f).to(dev)
+    u_d = torch.empty(p.n_dofs, dtype=torch.float64, device=dev)
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)
+
+    s = fg.Solver(fg.FETI_FETIDP, fg.FETI_SCALING_K, fg.FETI_RRS, tol=a.tol, max_iter=500,
+                  stream=stream.cuda_stream)
+    s.setup(p, rho=rho_d, f=f_d, on_device=True)
+
+    def step():
+        fg.feti_factorize(s.ctx)
+        _, st = fg.feti_solve_dual(s.ctx, allow_notconv=True)
+        fg.feti_recover_displacements(s.ctx, u_d, True)
+        return st
+
+    for _ in range(a.warmup):
+        step()
+        flush.zero_()
+    torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    clocks = ClockSampler(dev.index)
+    clocks.start()
+    l0 = fg.feti_query(s.ctx, fg.FETI_Q_LAUNCHES)
+    fg.feti_profile_begin(s.ctx)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(a.steps)]
+    applies, iters, conv = 0, [], []
+    t_wall0 = time.perf_counter()
+    for k in range(a.steps):
+        ev[k][0].record(stream)
+        st = step()
+        ev[k][1].record(stream)
+        applies += st.f_applies
+        iters.append(st.iterations)
+        conv.append(bool(st.converged))
+        flush.zero_()
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - t_wall0
+    gf, gms, gn = fg.feti_profile_end(s.ctx)
+    launches = fg.feti_query(s.ctx, fg.FETI_Q_LAUNCHES) - l0
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    step_ms = [e0.elapsed_time(e1) for e0, e1 in ev]
+    t_steps = sum(step_ms) / 1e3
+    # max over ranks
+    if world > 1:
+        t = torch.tensor([t_steps], dtype=torch.float64, device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        t_steps = float(t.item())
+        ap = torch.tensor([applies], dtype=torch.float64, device=dev)
+        torch.distributed.all_reduce(ap)
+        applies_total = float(ap.item())
+    else:
+        applies_total = float(applies)
+    value = applies_total / t_steps
+
+    # solve-only time (factorization excluded), one extra measured step
+    torch.cuda.synchronize()
+    fg.feti_factorize(s.ctx)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    _, st_solve = fg.feti_solve_dual(s.ctx, allow_notconv=True)
+    fg.feti_recover_displacements(s.ctx, u_d, True)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    solve_ms = e0.elapsed_time(e1)
+
+    # primal residual ||f - K u|| / ||f|| with the oracle's global assembly (CPU, outside timing)
+    rel_res = None
+    if rank == 0:
+        try:
+            from oracle.assemble import global_stiffness
+            K = global_stiffness(p)
+            u = u_d.cpu().numpy()
+            free = p.dirichlet == 0
+            rel_res = float(np.linalg.norm((p.f - K @ u)[free]) / np.linalg.norm(p.f))
+        except Exception as exc:  # pragma: no cover - diagnostics only
+            rel_res = f"unavailable: {exc}"
+
+    # end to end through the public API from pinned host buffers
+    e2e = None
+    if not a.no_e2e:
+        rho_h = torch.from_numpy(p.rho).pin_memory()
+        f_h = torch.from_numpy(p.f).pin_memory()
+        u_h = torch.empty(p.n_dofs, dtype=torch.float64).pin_memory()
+        s2 = fg.Solver(fg.FETI_FETIDP, fg.FETI_SCALING_K, fg.FETI_RRS, tol=a.tol, max_iter=500,
+                       stream=stream.cuda_stream)
+        e2e_applies, e2e_t = 0, 0.0
+        for k in range(max(1, a.steps)):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            s2.setup(p, rho=rho_h.numpy(), f=f_h.numpy(), on_device=False)
+            fg.feti_factorize(s2.ctx)
+            _, st2 = fg.feti_solve_dual(s2.ctx, allow_notconv=True)
+            fg.feti_recover_displacements(s2.ctx, u_h.numpy(), False)
+            torch.cuda.synchronize()
+            e2e_t += time.perf_counter() - t0
+            e2e_applies += st2.f_applies
+            flush.zero_()
+        s2.close()
+        if world > 1:
+            t = torch.tensor([e2e_t], dtype=torch.float64, device=dev)
+            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+            e2e_t = float(t.item())
+            ap = torch.tensor([e2e_applies], dtype=torch.float64, device=dev)
+            torch.distributed.all_reduce(ap)
+            e2e_applies = float(ap.item())
+        e2e = {"value": e2e_applies / e2e_t, "unit": "F-applies/s",
+               "h2d_bytes_per_step": int(p.rho.nbytes + p.f.nbytes + p.dirichlet.nbytes),
+               "d2h_bytes_per_step": int(p.f.nbytes + 8),
+               "ms_per_step": 1e3 * e2e_t / max(1, a.steps)}
+
+    gemm_tflops = gf / (gms / 1e3) / 1e12 if gms > 0 else None
+    out = {
+        "metric": METRIC, "value": value, "unit": "F-applies/s", "n_gpus": world, "steps": a.steps,
+        "warmup": a.warmup, "ms_per_step": 1e3 * t_steps / a.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": workload_config(a),
+        "time_to_solve_ms": 1e3 * t_steps / a.steps,
+        "solve_and_recover_ms": solve_ms,
+        "iterations": iters, "converged": conv, "f_applies_per_step": applies // max(1, a.steps),
+        "primal_rel_residual": rel_res,
+        "roofline": {"bound": "alu", "kernel": "dgemm_kernel (FP64 GEMM: dual-operator blocks, Gram, "
+                                               "orthogonalization, Schur)",
+                     "achieved": gemm_tflops, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                     "frac": (gemm_tflops / FP64_PEAK_TFLOPS) if gemm_tflops else None,
+                     "traffic": None, "peak_source": "derived: 152 SMs x 2 FP64 FMA/clk x 2.07 GHz",
+                     "kernel_share_of_step": (gms / 1e3) / t_steps if t_steps > 0 else None,
+                     "launches": gn},
+        "e2e": e2e, "gpu_launches": int(launches), "clocks": clk, "wall_s": wall,
+    }
+    s.close()
+    return out
+
+
+def main():
+    a = parse()
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    if a.impl == "reference":
+        if rank != 0:
+            return
+        vals, secs, desc = [], [], ""
+        for _ in range(a.warmup if a.warmup < 1 else 1):
+            oracle_sample(a, tiles=4)
+        for _ in range(a.steps):
+            v, dt, desc = oracle_sample(a, tiles=4)
+            vals.append(v)
+            secs.append(dt)
+        value = float(np.mean(vals))
+        out = {"impl": "reference", "metric": METRIC, "value": value, "unit": "F-applies/s", "n_gpus": a.gpus,
+               "steps": a.steps, "warmup": a.warmup, "ms_per_step": 1e3 * float(np.mean(secs)),
+               "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+               "data": "synthetic", "config": workload_config(a, {"sample": "4x4-tile sample per step"}),
+               "cpu_baseline": {"value": value, "unit": "F-applies/s", "cores": cpu_threads(), "kind": "oracle",
+                                "sample": desc},
+               "e2e": {"value": value, "unit": "F-applies/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+        print(json.dumps(out))
+        return
+    if world > 1:
+        import torch
+        torch.distributed.init_process_group("nccl")
+        torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", 0)))
+    out = run_ours(a, rank, world)
+    if rank == 0:
+        if world == 1 and not a.no_cpu_baseline:
+            v, dt, desc = oracle_sample(a, tiles=6)
+            out["cpu_baseline"] = {"value": v, "unit": "F-applies/s", "cores": cpu_threads(), "kind": "oracle",
+                                   "sample": desc}
+        print(json.dumps(out))
+    if world > 1:
+        import torch
+        torch.distributed.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,202 @@
+/*
+ * feti.h - C ABI of the GB300 FETI dual-operator library.
+ *
+ * The library solves the linear-elastic state problem K u = f (Eq. 2 of
+ * "Comparison of FETI-based domain decomposition methods for topology
+ * optimization problems", Medricky, Doskar, Pultarova, Zeman) on a regular
+ * grid of subdomains (modules) with Total FETI (Section 2.1) or FETI-DP
+ * (Section 2.2), k-scaling or multiplicity scaling (Section 3.1), and plain
+ * PCG, full orthogonalization (Section 3.2) or rank-revealing Simultaneous
+ * FETI (Section 3.3, Algorithm 1).  Every step of the computation runs in
+ * CUDA kernels on the device of the stream given to feti_create.
+ *
+ * Conventions used by every entry point
+ * -------------------------------------
+ * - Mesh: tiles[d] subdomains per axis, each of elems[d] unit elements
+ *   (Q4 bilinear quads in 2D, plane stress, unit thickness; H8 trilinear
+ *   hexahedra in 3D).  Global elements and nodes are numbered
+ *   lexicographically, x fastest; DOF = dim * node + direction.
+ * - Subdomain s is the tile with lexicographic index s; its local nodes
+ *   are numbered lexicographically inside the tile; local DOF
+ *   = dim * local_node + direction.
+ * - All floating-point data are IEEE double (FP64) unless stated.
+ * - "Device pointer" means memory of the context's CUDA device; "host
+ *   pointer" means ordinary CPU memory.  Where a call accepts both, the
+ *   on_device flag of the problem (or the argument) says which.
+ * - Ownership: the caller owns every buffer it passes; the library copies
+ *   what it needs during the call (or, for device outputs, writes into the
+ *   caller's memory on the context stream).  The library owns the context
+ *   and all internal device memory, released by feti_destroy.
+ * - Errors: no entry point aborts or exits.  A non-OK status leaves a
+ *   human-readable message in feti_last_error(ctx).  FETI_ESTATE means the
+ *   call order setup -> factorize -> solve -> recover was not respected.
+ * - Asynchrony: device outputs are complete when the call returns (every
+ *   call synchronises the context stream before returning).
+ */
+#ifndef FETI_GB300_H
+#define FETI_GB300_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct feti_ctx feti_ctx;
+
+typedef enum {
+  FETI_OK = 0,
+  FETI_EINVAL = 1,      /* bad argument (null pointer, size, option value) */
+  FETI_ENOMEM = 2,      /* device allocation failed */
+  FETI_ESTATE = 3,      /* call order violated */
+  FETI_ENOTCONV = 4,    /* max_iter reached: outputs valid but unconverged */
+  FETI_EBREAKDOWN = 5,  /* NaN/Inf or no independent search direction left */
+  FETI_ECUDA = 6,       /* a CUDA runtime call or kernel launch failed */
+  FETI_ENOTSUP = 7      /* option combination not implemented */
+} feti_status;
+
+enum { FETI_TFETI = 0, FETI_FETIDP = 1 };                 /* Sections 2.1 / 2.2 */
+enum { FETI_SCALING_K = 0, FETI_SCALING_MULT = 1 };       /* Eq. 15 / multiplicity */
+enum { FETI_PCG = 0, FETI_FO = 1, FETI_RRS = 2 };         /* Sections 3.2, 3.3 */
+enum { FETI_FP64 = 0, FETI_FP32 = 1 };                    /* dense block-product precision */
+
+typedef struct {
+  int method;          /* FETI_TFETI or FETI_FETIDP */
+  int scaling;         /* FETI_SCALING_K or FETI_SCALING_MULT */
+  int krylov;          /* FETI_PCG, FETI_FO or FETI_RRS */
+  int precision;       /* FETI_FP64 (default) */
+  int max_iter;        /* Krylov iteration cap (default 500) */
+  int dedup_modules;   /* 1: factorize identical modules once (Section 1) */
+  double tol;          /* relative tolerance on sqrt(r^T z) (default 1e-6) */
+  double rr_tol;       /* rank-revealing cutoff on the remaining/initial pivot ratio (1e-10) */
+} feti_options;
+
+typedef struct {
+  int dim;                       /* 2 or 3 */
+  int tiles[3];                  /* subdomains per axis (unused axes: 1) */
+  int elems[3];                  /* elements per subdomain per axis */
+  double E0, Emin, nu, p;        /* SIMP parameters of Eq. 1 and Poisson ratio */
+  const double* rho;             /* [n_elements] element densities */
+  const unsigned char* dirichlet;/* [n_nodes*dim] 1 = DOF fixed to zero */
+  const double* f;               /* [n_nodes*dim] global nodal load */
+  int on_device;                 /* rho and f are device pointers (dirichlet is always host) */
+} feti_problem;
+
+typedef struct {
+  int iterations;       /* Krylov iterations performed */
+  int converged;        /* 1 if sqrt(r^T z) <= tol * initial value */
+  int f_applies;        /* dual-operator columns applied (sum of retained ranks) */
+  int last_rank;        /* retained directions in the last iteration */
+  double eps0, eps;     /* initial and final sqrt(r^T z) */
+} feti_stats;
+
+/* Fill *opt with the defaults listed above.  Never fails for non-null opt. */
+feti_status feti_options_default(feti_options* opt);
+
+/* Create a context bound to the current CUDA device and to `stream`
+ * (a cudaStream_t; NULL = the legacy default stream).  *out receives the
+ * context (owned by the library until feti_destroy). */
+feti_status feti_create(feti_ctx** out, const feti_options* opt, void* stream);
+
+/* Tear the mesh into subdomains and build every index map on the host
+ * (Eqs. 4-5 for TFETI; Eqs. 8-10 and the corner primal set for FETI-DP;
+ * pair-wise redundant multipliers at DOFs shared by more than two subdomains,
+ * Section 3.1), then copy the maps and the problem data to the device.
+ * May be called again to replace the problem (resets the call order).
+ * Errors: FETI_EINVAL for inconsistent sizes or null pointers. */
+feti_status feti_setup_subdomains(feti_ctx* ctx, const feti_problem* prob);
+
+/* Replace the element densities (same mesh, same boundary conditions):
+ * `rho` has n_elements entries, host or device per on_device.  Requires a
+ * new feti_factorize before the next solve.  (Used by the SIMP loop,
+ * Section 1.) */
+feti_status feti_set_density(feti_ctx* ctx, const double* rho, int on_device);
+
+/* Assemble the SIMP-weighted subdomain stiffness (Eqs. 1, 3), factorise its
+ * interior block (banded Cholesky), form the Schur complement onto the
+ * interface and corner DOFs, and from it the dense local dual blocks:
+ * FETI-DP: F_s = [K_rr^{-1}]_bb, F_rc,s, local Kbar_cc (Eq. 12) and the
+ * Dirichlet-preconditioner Schur complement S_s (Eq. 13); TFETI: a
+ * generalised inverse of K_s on the interface (Section 2.1) and S_s.
+ * Then the coarse problem (Kbar_cc for FETI-DP, G G^T for TFETI), the
+ * scaling weights (Eq. 15) and the right-hand sides of Eq. 7 / Eq. 12.
+ * All in FP64 on the device. */
+feti_status feti_factorize(feti_ctx* ctx);
+
+/* Run the Krylov solver (Algorithm 1 or its PCG/FO special cases) on the
+ * dual problem.  lambda_inout: NULL, or a DEVICE array [n_lambda] used as the
+ * initial multiplier (warm start) and overwritten with the result.  stats may
+ * be NULL.  Returns FETI_ENOTCONV if max_iter was reached (results still
+ * valid) and FETI_EBREAKDOWN if no direction survived the rank test. */
+feti_status feti_solve_dual(feti_ctx* ctx, double* lambda_inout, feti_stats* stats);
+
+/* Recover the global displacement from the last solve: FETI-DP from the
+ * second rows of Eq. 12 and Eq. 11; TFETI from u = K^+(f - B^T lambda) + R alpha
+ * (Section 2.1).  u_out: [n_nodes*dim], device pointer if on_device != 0 else
+ * host; a node shared by several subdomains gets the mean of its copies and
+ * fixed DOFs are exactly zero.  compliance_out (host, may be NULL): f^T u. */
+feti_status feti_recover_displacements(feti_ctx* ctx, double* u_out, int on_device,
+                                       double* compliance_out);
+
+/* SIMP compliance sensitivity from the recovered displacement (self-adjoint,
+ * Section 1): dc/drho_e = -p rho_e^(p-1) (E0 - Emin) u_e^T k0 u_e.
+ * dc_drho: [n_elements], device if on_device else host. */
+feti_status feti_compliance_grad(feti_ctx* ctx, double* dc_drho, int on_device);
+
+/* The dual operator on a block of directions (the hot path of Algorithm 1):
+ * Y = F X with F the TFETI F of Eq. 7 or the condensed FETI-DP operator
+ * F_rr + F_rc Kbar_cc^{-1} F_rc^T of Eq. 12.  X, Y: DEVICE column-major
+ * [n_lambda x m] with leading dimensions ldx, ldy >= n_lambda.  Requires
+ * feti_factorize. */
+feti_status feti_apply_dual(feti_ctx* ctx, const double* X, int ldx, int m, double* Y, int ldy);
+
+/* The block Dirichlet preconditioner of Algorithm 1: column s of Z is
+ * B~^s S^s B~^sT r (Eq. 13 with the scaled B~ of Section 3.1), z = Z 1.
+ * r: DEVICE [n_lambda]; Z: DEVICE column-major [n_lambda x n_subdomains] with
+ * ldz >= n_lambda (may be NULL); z: DEVICE [n_lambda] (may be NULL). */
+feti_status feti_apply_precond(feti_ctx* ctx, const double* r, double* Z, int ldz, double* z);
+
+/* Integer facts about the set-up problem; key is one of FETI_Q_*. */
+enum {
+  FETI_Q_N_LAMBDA = 0, FETI_Q_N_SUBDOMAINS = 1, FETI_Q_N_PRIMAL = 2, FETI_Q_N_MODULES = 3,
+  FETI_Q_N_B_TOTAL = 4, FETI_Q_N_DOFS = 5, FETI_Q_N_ELEMENTS = 6, FETI_Q_MAX_NB = 7,
+  FETI_Q_DEVICE_BYTES = 8, FETI_Q_N_RBM = 9,
+  FETI_Q_LAUNCHES = 10   /* process-wide count of kernels this library has launched (any ctx state) */
+};
+feti_status feti_query(const feti_ctx* ctx, int key, int64_t* value);
+
+/* Instrumentation (not part of the method): between feti_profile_begin and
+ * feti_profile_end every FP64 GEMM launch of this process is bracketed by
+ * CUDA events on its stream.  feti_profile_end synchronises the context
+ * stream and returns (each pointer may be NULL) the summed algorithmic flops
+ * of those products (2 M N K, or the structural count where a factor is
+ * triangular), their summed device time in milliseconds, and the number of
+ * profiled launches.  One profile may be active per process. */
+feti_status feti_profile_begin(feti_ctx* ctx);
+feti_status feti_profile_end(feti_ctx* ctx, double* gemm_flops, double* gemm_ms, int64_t* gemm_launches);
+
+/* Layout of the multipliers, for comparing lambda-space vectors with an
+ * independent implementation: for each multiplier l, out[6*l .. 6*l+5] =
+ * (s1, local_dof1, sign1, s2, local_dof2, sign2); a single-subdomain
+ * (Dirichlet) row has s2 = -1.  out: host [6 * n_lambda]. */
+feti_status feti_lambda_layout(const feti_ctx* ctx, int32_t* out);
+
+/* Dense local blocks of subdomain s after feti_factorize, for parity checks:
+ * bdofs/cdofs (host int32 [n_b] / [n_c], may be NULL) receive the local DOF
+ * ids of the interface / corner DOFs in the library's order; F [n_b*n_b],
+ * S [n_b*n_b], Frc [n_b*n_c] (FETI-DP) receive F_s, S_s, F_rc,s row-major
+ * (host, each may be NULL); nb, nc (host) receive the sizes. */
+feti_status feti_local_blocks(feti_ctx* ctx, int s, int* nb, int* nc, int32_t* bdofs, int32_t* cdofs,
+                              double* F, double* S, double* Frc);
+
+/* The last error message of ctx (never NULL; "" if none). */
+const char* feti_last_error(const feti_ctx* ctx);
+
+/* Release the context and all of its device memory.  Accepts NULL. */
+void feti_destroy(feti_ctx* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* FETI_GB300_H */

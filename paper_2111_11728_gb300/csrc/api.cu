@@ -1,0 +1,940 @@
+// C ABI entry points and the host driver of Algorithm 1.
+//
+// The host only sequences kernels and reads two scalars per Krylov iteration
+// (the retained rank k_i and sqrt(r^T z)); every arithmetic step runs on the
+// device in FP64.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "kernels.h"
+
+using namespace feti;
+
+struct feti_ctx {
+  Ctx c;
+};
+
+namespace {
+
+#define TRY(expr)                              \
+  do {                                         \
+    feti_status _s = (expr);                   \
+    if (_s != FETI_OK) return _s;              \
+  } while (0)
+#define CU(expr) FETI_CUDA_TRY(&c, expr)
+
+template <class T>
+feti_status dalloc(Ctx& c, T*& p, size_t n) {
+  p = nullptr;
+  if (n == 0) n = 1;
+  void* q = nullptr;
+  cudaError_t e = cudaMalloc(&q, n * sizeof(T));
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    c.err = "device allocation of " + std::to_string(n * sizeof(T)) + " bytes failed: " + cudaGetErrorString(e);
+    return FETI_ENOMEM;
+  }
+  c.allocs.push_back(q);
+  c.device_bytes += n * sizeof(T);
+  p = static_cast<T*>(q);
+  return FETI_OK;
+}
+
+template <class T>
+feti_status upload(Ctx& c, T*& p, const std::vector<T>& v) {
+  TRY(dalloc(c, p, v.size()));
+  if (!v.empty()) CU(cudaMemcpy(p, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice));
+  return FETI_OK;
+}
+
+void free_all(Ctx& c) {
+  for (void* p : c.allocs) cudaFree(p);
+  c.allocs.clear();
+  c.device_bytes = 0;
+  c.hist_W.clear();
+  c.hist_Q.clear();
+  c.hist_k.clear();
+  c.blk_cap = 0;
+  c.kr_cap = 0;
+  c.split_cap = 0;
+}
+
+inline int64_t align32(int64_t x) { return (x + 31) / 32 * 32; }
+
+feti_status sync_check(Ctx& c) {
+  CU(cudaStreamSynchronize(c.stream));
+  CU(cudaGetLastError());
+  return FETI_OK;
+}
+
+// ---- GEMM descriptor builders -------------------------------------------------------
+feti_status build_block_descs(Ctx& c) {
+  const HostProblem& hp = c.hp;
+  const int64_t nbt = hp.n_b_total, nct = std::max<int64_t>(c.n_c_total, 1);
+  std::vector<GemmDesc> dF(hp.n_sub), dFrcT(hp.n_sub), dFrc(hp.n_sub);
+  for (int s = 0; s < hp.n_sub; ++s) {
+    const DevSub& S = c.h_subs[s];
+    const DevModule& M = c.h_mods[S.module];
+    const DevType& T = c.h_types[S.type];
+    GemmDesc g{};
+    g.A = c.d_modmem + M.F; g.B = c.d_Xb + S.b_off; g.C = c.d_Yb + S.b_off;
+    g.M = T.n_b; g.N = 1; g.K = T.n_b;
+    g.ars = T.n_b; g.acs = 1; g.brs = 1; g.bcs = nbt; g.crs = 1; g.ccs = nbt;
+    dF[s] = g;
+    GemmDesc h{};
+    h.A = c.d_modmem + M.Frc; h.B = c.d_Xb + S.b_off; h.C = c.d_Cb + S.c_off;
+    h.M = T.n_c; h.N = 1; h.K = T.n_b;
+    h.ars = 1; h.acs = std::max(T.n_c, 1); h.brs = 1; h.bcs = nbt; h.crs = 1; h.ccs = nct;
+    dFrcT[s] = h;
+    GemmDesc q{};
+    q.A = c.d_modmem + M.Frc; q.B = c.d_Vc + S.c_off; q.C = c.d_Yb + S.b_off;
+    q.M = T.n_b; q.N = 1; q.K = T.n_c;
+    q.ars = std::max(T.n_c, 1); q.acs = 1; q.brs = 1; q.bcs = nct; q.crs = 1; q.ccs = nbt;
+    dFrc[s] = q;
+  }
+  if (!c.d_gemm_F) {
+    TRY(dalloc(c, c.d_gemm_F, hp.n_sub));
+    TRY(dalloc(c, c.d_gemm_FrcT, hp.n_sub));
+    TRY(dalloc(c, c.d_gemm_Frc, hp.n_sub));
+  }
+  CU(cudaMemcpy(c.d_gemm_F, dF.data(), dF.size() * sizeof(GemmDesc), cudaMemcpyHostToDevice));
+  CU(cudaMemcpy(c.d_gemm_FrcT, dFrcT.data(), dFrcT.size() * sizeof(GemmDesc), cudaMemcpyHostToDevice));
+  CU(cudaMemcpy(c.d_gemm_Frc, dFrc.data(), dFrc.size() * sizeof(GemmDesc), cudaMemcpyHostToDevice));
+  return FETI_OK;
+}
+
+// Block buffers of the dual operator for up to `m` columns.
+feti_status ensure_blocks(Ctx& c, int m) {
+  if (m <= c.blk_cap) return FETI_OK;
+  const HostProblem& hp = c.hp;
+  const int cap = std::max(m, 64);
+  const int64_t nbt = hp.n_b_total, nct = std::max<int64_t>(c.n_c_total, 1);
+  const int64_t np = std::max(hp.n_primal, 1);
+  TRY(dalloc(c, c.d_Xb, (size_t)nbt * cap));
+  TRY(dalloc(c, c.d_Yb, (size_t)nbt * cap));
+  TRY(dalloc(c, c.d_Cb, (size_t)nct * cap));
+  TRY(dalloc(c, c.d_Vc, (size_t)nct * cap));
+  TRY(dalloc(c, c.d_Vraw, (size_t)np * cap));
+  TRY(dalloc(c, c.d_V, (size_t)np * cap));
+  if (c.n_coarse > 0 && hp.method == FETI_TFETI) {
+    TRY(dalloc(c, c.d_ct1, (size_t)c.n_coarse * cap));
+    TRY(dalloc(c, c.d_ct2, (size_t)c.n_coarse * cap));
+  }
+  c.blk_cap = cap;
+  return build_block_descs(c);
+}
+
+feti_status ensure_split(Ctx& c, int64_t need) {
+  if (need <= c.split_cap) return FETI_OK;
+  TRY(dalloc(c, c.d_split, (size_t)need));
+  c.split_cap = need;
+  return FETI_OK;
+}
+
+// C (col-major M x N, ld ldc) = alpha * A^T B + beta * C with A (K x M) and
+// B (K x N) column-major (ld lda, ldb): the Gram products of Algorithm 1.
+feti_status gemm_tn(Ctx& c, const double* A, int64_t lda, const double* B, int64_t ldb, double* C, int64_t ldc,
+                    int M, int N, int K, double alpha, double beta) {
+  GemmDesc d{};
+  d.A = A; d.B = B; d.C = C; d.M = M; d.N = N; d.K = K;
+  d.ars = lda; d.acs = 1; d.brs = 1; d.bcs = ldb; d.crs = 1; d.ccs = ldc;
+  const int splits = split_for(M, N, K);
+  if (splits > 1) TRY(ensure_split(c, (int64_t)splits * M * N));
+  CU(dgemm_split(d, splits, c.d_split, alpha, beta, c.stream));
+  return FETI_OK;
+}
+
+// C (col-major M x N) = alpha * A B + beta * C, A (M x K), B (K x N) column-major.
+feti_status gemm_nn(Ctx& c, const double* A, int64_t lda, const double* B, int64_t ldb, double* C, int64_t ldc,
+                    int M, int N, int K, double alpha, double beta, double alg_flops = -1.0) {
+  GemmDesc d{};
+  d.A = A; d.B = B; d.C = C; d.M = M; d.N = N; d.K = K;
+  d.ars = 1; d.acs = lda; d.brs = 1; d.bcs = ldb; d.crs = 1; d.ccs = ldc;
+  CU(dgemm_split(d, 1, nullptr, alpha, beta, c.stream, alg_flops));
+  return FETI_OK;
+}
+
+// TFETI projector P X = X - G^T (G G^T)^{-1} G X, X column-major [n_lam x m].
+feti_status project(Ctx& c, double* X, int64_t ldx, int m) {
+  if (c.hp.method != FETI_TFETI) return FETI_OK;
+  TRY(ensure_blocks(c, m));
+  const int nco = c.n_coarse;
+  const int64_t nl = c.hp.n_lam;
+  // t1 = G X  (G row-major nco x nl)
+  {
+    GemmDesc d{};
+    d.A = c.d_G; d.B = X; d.C = c.d_ct1; d.M = nco; d.N = m; d.K = (int)nl;
+    d.ars = nl; d.acs = 1; d.brs = 1; d.bcs = ldx; d.crs = 1; d.ccs = nco;
+    const int splits = split_for(nco, m, (int)nl);
+    if (splits > 1) TRY(ensure_split(c, (int64_t)splits * nco * m));
+    CU(dgemm_split(d, splits, c.d_split, 1.0, 0.0, c.stream));
+  }
+  // t2 = (G G^T)^{-1} t1
+  {
+    GemmDesc d{};
+    d.A = c.d_Kbar_inv; d.B = c.d_ct1; d.C = c.d_ct2; d.M = nco; d.N = m; d.K = nco;
+    d.ars = nco; d.acs = 1; d.brs = 1; d.bcs = nco; d.crs = 1; d.ccs = nco;
+    CU(dgemm_split(d, 1, nullptr, 1.0, 0.0, c.stream));
+  }
+  // X -= G^T t2
+  {
+    GemmDesc d{};
+    d.A = c.d_G; d.B = c.d_ct2; d.C = X; d.M = (int)nl; d.N = m; d.K = nco;
+    d.ars = 1; d.acs = nl; d.brs = 1; d.bcs = nco; d.crs = 1; d.ccs = ldx;
+    CU(dgemm_split(d, 1, nullptr, -1.0, 1.0, c.stream));
+  }
+  return FETI_OK;
+}
+
+// Y = F X for m columns (device, column-major).
+feti_status apply_dual(Ctx& c, const double* X, int64_t ldx, int m, double* Y, int64_t ldy) {
+  TRY(ensure_blocks(c, m));
+  CU(gather_lam_to_b(c, X, ldx, m, c.d_Xb, c.stream));
+  if (c.hp.method == FETI_FETIDP && c.hp.n_primal > 0) {
+    const int np = c.hp.n_primal;
+    CU(corner_reduce(c, c.d_Xb, m, c.d_Cb, c.d_Vraw, c.stream));
+    GemmDesc d{};
+    d.A = c.d_Kbar_inv; d.B = c.d_Vraw; d.C = c.d_V; d.M = np; d.N = m; d.K = np;
+    d.ars = np; d.acs = 1; d.brs = 1; d.bcs = np; d.crs = 1; d.ccs = np;
+    CU(dgemm_split(d, 1, nullptr, 1.0, 0.0, c.stream));
+    CU(apply_local_F(c, c.d_Xb, c.d_Yb, m, 0.0, c.stream));
+    CU(corner_expand(c, c.d_V, m, c.d_Vc, c.d_Yb, c.stream));
+  } else {
+    CU(apply_local_F(c, c.d_Xb, c.d_Yb, m, 0.0, c.stream));
+  }
+  CU(scatter_b_to_lam(c, c.d_Yb, m, Y, ldy, c.stream));
+  return FETI_OK;
+}
+
+feti_status check_status(Ctx& c, const char* where) {
+  int st = 0;
+  CU(cudaMemcpy(&st, c.d_status, sizeof(int), cudaMemcpyDeviceToHost));
+  if (st != 0) {
+    c.err = std::string(where) + ": non-positive pivot (";
+    if (st >= 2000000) c.err += "dense factor, tag " + std::to_string(st - 2000000);
+    else c.err += "banded factor of module " + std::to_string(st - 1000000);
+    c.err += "); the stiffness is not positive definite (zero density with Emin = 0?)";
+    CU(cudaMemset(c.d_status, 0, sizeof(int)));
+    return FETI_EBREAKDOWN;
+  }
+  return FETI_OK;
+}
+
+// Host-side rigid modes at the b DOFs of a type: raw (same formula as the
+// device's rbm()) and orthonormalised by modified Gram-Schmidt.
+void type_rigid_modes(const HostProblem& hp, const StructType& T, std::vector<double>& raw,
+                      std::vector<double>& hat) {
+  const int nr = hp.n_rbm, dim = hp.dim;
+  raw.assign((size_t)T.n_b * nr, 0.0);
+  for (int k = 0; k < T.n_b; ++k) {
+    const int ld = T.blist[k];
+    int c[3];
+    local_node_coords(hp, ld / dim, c);
+    const int d = ld % dim;
+    const double x = c[0], y = c[1], z = c[2];
+    for (int q = 0; q < nr; ++q) {
+      double v;
+      if (dim == 2) v = q < 2 ? (d == q ? 1.0 : 0.0) : (d == 0 ? -y : x);
+      else if (q < 3) v = d == q ? 1.0 : 0.0;
+      else if (q == 3) v = d == 1 ? -z : (d == 2 ? y : 0.0);
+      else if (q == 4) v = d == 0 ? z : (d == 2 ? -x : 0.0);
+      else v = d == 0 ? -y : (d == 1 ? x : 0.0);
+      raw[(size_t)k * nr + q] = v;
+    }
+  }
+  hat = raw;
+  for (int q = 0; q < nr; ++q) {
+    for (int p = 0; p < q; ++p) {
+      double dp = 0.0;
+      for (int k = 0; k < T.n_b; ++k) dp += hat[(size_t)k * nr + p] * hat[(size_t)k * nr + q];
+      for (int k = 0; k < T.n_b; ++k) hat[(size_t)k * nr + q] -= dp * hat[(size_t)k * nr + p];
+    }
+    double nn = 0.0;
+    for (int k = 0; k < T.n_b; ++k) nn += hat[(size_t)k * nr + q] * hat[(size_t)k * nr + q];
+    nn = std::sqrt(nn);
+    for (int k = 0; k < T.n_b; ++k) hat[(size_t)k * nr + q] /= nn;
+  }
+}
+
+}  // namespace
+
+// ================================================================================
+extern "C" {
+
+feti_status feti_options_default(feti_options* opt) {
+  if (!opt) return FETI_EINVAL;
+  opt->method = FETI_FETIDP;
+  opt->scaling = FETI_SCALING_K;
+  opt->krylov = FETI_RRS;
+  opt->precision = FETI_FP64;
+  opt->max_iter = 500;
+  opt->dedup_modules = 1;
+  opt->tol = 1e-6;
+  opt->rr_tol = 1e-10;
+  return FETI_OK;
+}
+
+feti_status feti_create(feti_ctx** out, const feti_options* opt, void* stream) {
+  if (!out) return FETI_EINVAL;
+  *out = nullptr;
+  feti_options o;
+  feti_options_default(&o);
+  if (opt) o = *opt;
+  if ((o.method != FETI_TFETI && o.method != FETI_FETIDP) ||
+      (o.scaling != FETI_SCALING_K && o.scaling != FETI_SCALING_MULT) ||
+      (o.krylov < FETI_PCG || o.krylov > FETI_RRS) || o.max_iter < 0 || !(o.tol >= 0.0) || !(o.rr_tol >= 0.0))
+    return FETI_EINVAL;
+  if (o.precision != FETI_FP64) return FETI_ENOTSUP;
+  feti_ctx* ctx = new (std::nothrow) feti_ctx;
+  if (!ctx) return FETI_ENOMEM;
+  Ctx& c = ctx->c;
+  c.opt = o;
+  c.stream = static_cast<cudaStream_t>(stream);
+  if (cudaGetDevice(&c.device) != cudaSuccess || cudaMallocHost(&c.h_pin, 64 * sizeof(double)) != cudaSuccess) {
+    cudaGetLastError();
+    delete ctx;
+    return FETI_ECUDA;
+  }
+  *out = ctx;
+  return FETI_OK;
+}
+
+void feti_destroy(feti_ctx* ctx) {
+  if (!ctx) return;
+  free_all(ctx->c);
+  if (ctx->c.h_pin) cudaFreeHost(ctx->c.h_pin);
+  delete ctx;
+}
+
+const char* feti_last_error(const feti_ctx* ctx) { return ctx ? ctx->c.err.c_str() : "null context"; }
+
+feti_status feti_setup_subdomains(feti_ctx* ctx, const feti_problem* prob) {
+  if (!ctx || !prob) return FETI_EINVAL;
+  Ctx& c = ctx->c;
+  c.err.clear();
+  if (!prob->rho || !prob->dirichlet || !prob->f) { c.err = "null problem array"; return FETI_EINVAL; }
+  free_all(c);
+  c = Ctx{c.opt, c.stream, std::string(), 0, c.device, HostProblem(), {}, 0, c.h_pin};
+  // densities on the host for module de-duplication
+  int64_t nel = 1, nn = 1;
+  for (int a = 0; a < prob->dim && a < 3; ++a) {
+    nel *= (int64_t)prob->tiles[a] * prob->elems[a];
+    nn *= (int64_t)prob->tiles[a] * prob->elems[a] + 1;
+  }
+  if (prob->dim != 2 && prob->dim != 3) { c.err = "dim must be 2 or 3"; return FETI_EINVAL; }
+  std::vector<double> rho_h(nel);
+  if (prob->on_device) CU(cudaMemcpy(rho_h.data(), prob->rho, nel * sizeof(double), cudaMemcpyDeviceToHost));
+  else std::memcpy(rho_h.data(), prob->rho, nel * sizeof(double));
+  for (double r : rho_h)
+    if (!(r >= 0.0 && r <= 1.0)) { c.err = "densities must lie in [0, 1]"; return FETI_EINVAL; }
+  std::string msg = build_host_problem(*prob, c.opt.method, c.opt.dedup_modules, rho_h.data(), c.hp);
+  if (!msg.empty()) { c.err = msg; return FETI_EINVAL; }
+  HostProblem& hp = c.hp;
+  // ---- problem arrays ----
+  TRY(upload(c, c.d_rho, rho_h));
+  TRY(dalloc(c, c.d_E, hp.n_elements));
+  TRY(dalloc(c, c.d_fglob, hp.n_dofs));
+  CU(cudaMemcpy(c.d_fglob, prob->f, hp.n_dofs * sizeof(double),
+                prob->on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice));
+  c.h_k0.assign((size_t)(hp.dim == 2 ? 64 : 576), 0.0);
+  element_stiffness_host(hp.dim, hp.nu, c.h_k0.data());
+  TRY(upload(c, c.d_k0, c.h_k0));
+  TRY(upload(c, c.d_dirichlet, hp.dirichlet));
+  // ---- types ----
+  c.h_types.resize(hp.types.size());
+  c.max_nb = 1; c.max_nc = 1;
+  for (size_t t = 0; t < hp.types.size(); ++t) {
+    const StructType& T = hp.types[t];
+    std::vector<int> ci(T.n_loc);
+    for (int a = 0; a < T.n_loc; ++a) ci[a] = (T.cls[a] << 24) | std::max(T.idx[a], 0);
+    DevType d{};
+    d.n_loc = T.n_loc; d.n_i = T.n_i; d.n_b = T.n_b; d.n_c = T.n_c; d.bw = T.bw;
+    int *p1, *p2, *p3, *p4;
+    TRY(upload(c, p1, ci));
+    TRY(upload(c, p2, T.ilist));
+    TRY(upload(c, p3, T.blist));
+    TRY(upload(c, p4, T.clist));
+    d.cls_idx = p1; d.ilist = p2; d.blist = p3; d.clist = p4;
+    if (hp.n_rbm > 0) {
+      std::vector<double> raw, hat;
+      type_rigid_modes(hp, T, raw, hat);
+      double *r1, *r2;
+      TRY(upload(c, r1, raw));
+      TRY(upload(c, r2, hat));
+      d.Rraw = r1; d.Rhat = r2;
+    }
+    c.h_types[t] = d;
+    c.max_nb = std::max(c.max_nb, T.n_b);
+    c.max_nc = std::max(c.max_nc, T.n_c);
+  }
+  TRY(upload(c, c.d_types, c.h_types));
+  // ---- modules: memory layout ----
+  c.n_mod = (int)hp.module_rep.size();
+  c.h_mods.resize(c.n_mod);
+  int64_t off = 0;
+  for (int m = 0; m < c.n_mod; ++m) {
+    const StructType& T = hp.types[hp.module_type[m]];
+    const int64_t W = T.bw + 1, nbc = T.n_bc();
+    DevModule M{};
+    M.type = hp.module_type[m];
+    M.rep = hp.module_rep[m];
+    M.lcol = off; off = align32(off + (int64_t)T.n_i * W);
+    M.lrow = off; off = align32(off + (int64_t)T.n_i * W);
+    M.rdiag = off; off = align32(off + T.n_i);
+    M.Y = off; off = align32(off + (int64_t)T.n_i * nbc);
+    M.S = off; off = align32(off + nbc * nbc);
+    M.W = off; off = align32(off + nbc * nbc);
+    M.Li = off; off = align32(off + (int64_t)T.n_b * T.n_b);
+    M.F = off; off = align32(off + (int64_t)T.n_b * T.n_b);
+    M.Frc = off; off = align32(off + (int64_t)T.n_b * T.n_c);
+    M.Kb = off; off = align32(off + (int64_t)T.n_c * T.n_c);
+    M.Rb = off; off = align32(off + (int64_t)T.n_b * hp.n_rbm);
+    c.h_mods[m] = M;
+  }
+  c.modmem_len = off;
+  TRY(dalloc(c, c.d_modmem, (size_t)off));
+  TRY(upload(c, c.d_mods, c.h_mods));
+  // ---- subdomains ----
+  c.h_subs.resize(hp.n_sub);
+  c.h_ioff.assign(hp.n_sub + 1, 0);
+  std::vector<int64_t> coff(hp.n_sub);
+  for (int s = 0; s < hp.n_sub; ++s) {
+    const StructType& Ts = hp.types[hp.sub_type[s]];
+    c.fl_F += 2.0 * Ts.n_b * (double)Ts.n_b;
+    c.fl_FrcT += 2.0 * Ts.n_c * (double)Ts.n_b;
+    c.fl_Frc += 2.0 * Ts.n_b * (double)Ts.n_c;
+    DevSub S{};
+    S.module = hp.sub_module[s];
+    S.type = hp.sub_type[s];
+    S.b_off = hp.b_off[s];
+    S.c_off = hp.c_off.empty() ? 0 : hp.c_off[s];
+    S.tile[0] = s % hp.tiles[0];
+    S.tile[1] = (s / hp.tiles[0]) % hp.tiles[1];
+    S.tile[2] = s / (hp.tiles[0] * hp.tiles[1]);
+    c.h_subs[s] = S;
+    coff[s] = S.c_off;
+    c.h_ioff[s + 1] = c.h_ioff[s] + align32(hp.types[S.type].n_i);
+  }
+  TRY(upload(c, c.d_subs, c.h_subs));
+  TRY(upload(c, c.d_ioff, c.h_ioff));
+  TRY(upload(c, c.d_c_off, coff));
+  c.n_c_total = hp.c_off.empty() ? 0 : hp.c_off[hp.n_sub];
+  // ---- maps ----
+  TRY(upload(c, c.d_lam_b0, hp.lam_b0));
+  TRY(upload(c, c.d_lam_b1, hp.lam_b1));
+  TRY(upload(c, c.d_lam_s0, hp.lam_s0));
+  TRY(upload(c, c.d_lam_s1, hp.lam_s1));
+  TRY(upload(c, c.d_lam_group, hp.lam_group));
+  TRY(upload(c, c.d_group_off, hp.group_off));
+  TRY(upload(c, c.d_group_b, hp.group_b));
+  TRY(upload(c, c.d_b2l_off, hp.b2l_off));
+  TRY(upload(c, c.d_b2l_lam, hp.b2l_lam));
+  TRY(upload(c, c.d_b2l_sign, hp.b2l_sign));
+  TRY(upload(c, c.d_b_sub, hp.b_sub));
+  TRY(upload(c, c.d_c_glob, hp.c_glob));
+  std::vector<int> csub(c.n_c_total);
+  for (int s = 0; s < hp.n_sub; ++s)
+    for (int64_t k = hp.c_off.empty() ? 0 : hp.c_off[s]; !hp.c_off.empty() && k < hp.c_off[s + 1]; ++k) csub[k] = s;
+  TRY(upload(c, c.d_c_sub, csub));
+  TRY(upload(c, c.d_prim_off, hp.prim_off.empty() ? std::vector<int>{0} : hp.prim_off));
+  TRY(upload(c, c.d_prim_src, hp.prim_src));
+  TRY(upload(c, c.d_load_src, hp.load_src));
+  TRY(upload(c, c.d_dof_copy_off, hp.dof_copy_off));
+  TRY(upload(c, c.d_dof_copy, hp.dof_copy));
+  // ---- vectors ----
+  const int64_t nbt = hp.n_b_total, nl = hp.n_lam;
+  TRY(dalloc(c, c.d_diagKb, nbt));
+  TRY(dalloc(c, c.d_w0, nl));
+  TRY(dalloc(c, c.d_w1, nl));
+  TRY(dalloc(c, c.d_floc, (size_t)hp.n_sub * hp.n_loc_dofs));
+  TRY(dalloc(c, c.d_h, c.h_ioff[hp.n_sub]));
+  TRY(dalloc(c, c.d_t, c.h_ioff[hp.n_sub]));
+  TRY(dalloc(c, c.d_ft, nbt + c.n_c_total));
+  TRY(dalloc(c, c.d_pb0, nbt));
+  TRY(dalloc(c, c.d_pb1, nbt));
+  c.n_coarse = hp.method == FETI_FETIDP ? hp.n_primal : hp.n_rbm * hp.n_sub;
+  const int64_t nco = std::max(c.n_coarse, 1);
+  TRY(dalloc(c, c.d_Kbar, nco * nco));
+  TRY(dalloc(c, c.d_Kbar_L, nco * nco));
+  TRY(dalloc(c, c.d_Kbar_inv, nco * nco));
+  TRY(dalloc(c, c.d_fbar, std::max(hp.n_primal, 1)));
+  if (hp.method == FETI_TFETI) {
+    TRY(dalloc(c, c.d_G, (size_t)nco * nl));
+    TRY(dalloc(c, c.d_e, nco));
+    TRY(dalloc(c, c.d_alpha, nco));
+  }
+  TRY(dalloc(c, c.d_d, nl));
+  TRY(dalloc(c, c.d_lam0, nl));
+  TRY(dalloc(c, c.d_lam, nl));
+  TRY(dalloc(c, c.d_uloc, (size_t)hp.n_sub * hp.n_loc_dofs));
+  TRY(dalloc(c, c.d_uglob, hp.n_dofs));
+  TRY(dalloc(c, c.d_scalar, 64));
+  TRY(dalloc(c, c.d_status, 4));
+  TRY(dalloc(c, c.d_kdev, 4));
+  TRY(dalloc(c, c.d_red, 1024));
+  CU(cudaMemset(c.d_status, 0, 4 * sizeof(int)));
+  // ---- per-module descriptors for the factorization ----
+  {
+    std::vector<GemmDesc> schur(c.n_mod), frc(c.n_mod), kb(c.n_mod);
+    std::vector<DenseDesc> dd(c.n_mod);
+    for (int m = 0; m < c.n_mod; ++m) {
+      const DevModule& M = c.h_mods[m];
+      const StructType& T = hp.types[M.type];
+      const int nbc = T.n_bc();
+      GemmDesc g{};   // S -= Y^T Y
+      g.A = c.d_modmem + M.Y; g.B = c.d_modmem + M.Y; g.C = c.d_modmem + M.S;
+      g.M = nbc; g.N = nbc; g.K = T.n_i;
+      g.ars = 1; g.acs = nbc; g.brs = nbc; g.bcs = 1; g.crs = nbc; g.ccs = 1;
+      schur[m] = g;
+      GemmDesc f{};   // F_rc = L_bb^{-T} L_cb^T  (= S_bb^{-1} S_bc)
+      f.A = c.d_modmem + M.Li; f.B = c.d_modmem + M.W + (int64_t)T.n_b * nbc; f.C = c.d_modmem + M.Frc;
+      f.M = T.n_b; f.N = T.n_c; f.K = T.n_b;
+      f.ars = 1; f.acs = T.n_b; f.brs = 1; f.bcs = nbc; f.crs = std::max(T.n_c, 1); f.ccs = 1;
+      frc[m] = f;
+      GemmDesc k{};   // Kb -= S_cb Frc
+      k.A = c.d_modmem + M.S + (int64_t)T.n_b * nbc; k.B = c.d_modmem + M.Frc; k.C = c.d_modmem + M.Kb;
+      k.M = T.n_c; k.N = T.n_c; k.K = T.n_b;
+      k.ars = nbc; k.acs = 1; k.brs = std::max(T.n_c, 1); k.bcs = 1; k.crs = std::max(T.n_c, 1); k.ccs = 1;
+      kb[m] = k;
+      c.fl_schur += 2.0 * nbc * (double)nbc * T.n_i;
+      c.fl_frcmake += 2.0 * T.n_b * (double)T.n_c * T.n_b;
+      c.fl_kbmake += 2.0 * T.n_c * (double)T.n_c * T.n_b;
+      DenseDesc q{};
+      q.A = c.d_modmem + M.W; q.Linv = c.d_modmem + M.Li; q.out = c.d_modmem + M.F;
+      q.n = T.n_b; q.ld = nbc; q.tag = m; q.n_full = nbc;
+      dd[m] = q;
+    }
+    TRY(upload(c, c.d_gemm_schur, schur));
+    TRY(upload(c, c.d_gemm_frcmake, frc));
+    TRY(upload(c, c.d_gemm_kbmake, kb));
+    TRY(upload(c, c.d_dense_mod, dd));
+    std::vector<DenseDesc> dc(1);
+    dc[0].A = c.d_Kbar; dc[0].Linv = c.d_Kbar_L; dc[0].out = c.d_Kbar_inv;
+    dc[0].n = c.n_coarse; dc[0].ld = c.n_coarse; dc[0].tag = 999999; dc[0].n_full = c.n_coarse;
+    TRY(upload(c, c.d_dense_coarse, dc));
+  }
+  TRY(ensure_blocks(c, std::max(64, hp.n_sub)));
+  TRY(sync_check(c));
+  c.state = 1;
+  return FETI_OK;
+}
+
+feti_status feti_set_density(feti_ctx* ctx, const double* rho, int on_device) {
+  if (!ctx || !rho) return FETI_EINVAL;
+  Ctx& c = ctx->c;
+  if (c.state < 1) { c.err = "feti_set_density before feti_setup_subdomains"; return FETI_ESTATE; }
+  if (c.opt.dedup_modules && c.n_mod < c.hp.n_sub) {
+    c.err = "feti_set_density needs a context created with dedup_modules = 0 (module sharing depends on rho)";
+    return FETI_ENOTSUP;
+  }
+  CU(cudaMemcpyAsync(c.d_rho, rho, c.hp.n_elements * sizeof(double),
+                     on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, c.stream));
+  TRY(sync_check(c));
+  c.state = 1;
+  return FETI_OK;
+}
+
+feti_status feti_factorize(feti_ctx* ctx) {
+  if (!ctx) return FETI_EINVAL;
+  Ctx& c = ctx->c;
+  c.err.clear();
+  if (c.state < 1) { c.err = "feti_factorize before feti_setup_subdomains"; return FETI_ESTATE; }
+  const HostProblem& hp = c.hp;
+  cudaStream_t st = c.stream;
+  const bool dp = hp.method == FETI_FETIDP;
+  // local stiffness (Eqs. 1, 3)
+  CU(launch_moduli(c, c.d_E, st));
+  CU(cudaMemsetAsync(c.d_modmem, 0, c.modmem_len * sizeof(double), st));
+  CU(launch_assemble_with(c, c.d_E, st));
+  CU(launch_gather_diag_b(c, st));
+  CU(launch_scaling_weights(c, c.opt.scaling, st));
+  // interior factor and Schur complement onto b + c
+  CU(launch_band_chol(c, st));
+  CU(launch_band_fwd_multi(c, st));
+  int max_bc = 1;
+  for (auto& t : hp.types) max_bc = std::max(max_bc, t.n_bc());
+  CU(dgemm_batched(c.d_gemm_schur, c.n_mod, max_bc, max_bc, 0, -1.0, 1.0, st, c.fl_schur));
+  // local dual block F_s = S_bb^{-1} (FETI-DP) or (S_b + Rhat Rhat^T)^{-1} (TFETI):
+  // Cholesky of the whole b+c Schur complement with only the b columns
+  // eliminated, so the corner block is Schur-complemented in the same
+  // (stable) sweep instead of through the explicit inverse.
+  CU(launch_copy_block(c, 0, st));
+  if (!dp) CU(tfeti_add_rrt(c, st));
+  {
+    std::vector<DenseDesc> hd(c.n_mod);
+    for (int m = 0; m < c.n_mod; ++m) {
+      hd[m].n = hp.types[c.h_mods[m].type].n_b;
+      hd[m].n_full = hp.types[c.h_mods[m].type].n_bc();
+    }
+    CU(dense_spd_inverse(c.d_dense_mod, hd.data(), c.n_mod, c.d_status, st));
+  }
+  TRY(sync_check(c));
+  TRY(check_status(c, "subdomain factorization"));
+  if (dp) {
+    // the partial factorisation left Kbar_s = S_cc - S_cb S_bb^{-1} S_bc in the trailing block
+    CU(dgemm_batched(c.d_gemm_frcmake, c.n_mod, c.max_nb, c.max_nc, 0, 1.0, 0.0, st, c.fl_frcmake));
+    CU(launch_copy_block(c, 1, st));
+  }
+  // loads: f^s, h = L^{-1} f_i, f~ = f_bc - Y^T h
+  CU(launch_load_gather(c, st));
+  CU(launch_band_fwd_single(c, st));
+  CU(launch_condense_load(c, st));
+  const int64_t nl = hp.n_lam, nbt = hp.n_b_total;
+  // d_r (FETI-DP) or d = B K^# f (TFETI, c = 0): x_b = F f~_b, scattered
+  CU(batched_gemv(c, 0, c.d_ft, c.d_pb0, 0.0, st));
+  CU(scatter_b_to_lam(c, c.d_pb0, 1, c.d_d, nl, st));
+  CU(cudaMemsetAsync(c.d_lam0, 0, nl * sizeof(double), st));
+  if (dp) {
+    const int np = hp.n_primal;
+    // coarse matrix Kbar_cc (Eq. 12) and its inverse
+    CU(launch_coarse_assemble_impl(c, c.d_c_sub, c.d_c_off, c.d_Kbar, st));
+    {
+      DenseDesc hd{};
+      hd.n = np;
+      CU(dense_spd_inverse(c.d_dense_coarse, &hd, 1, c.d_status, st));
+    }
+    // fbar_c = sum_s B_c^sT (f~_c - F_rc,s^T f~_b)
+    CU(cudaMemcpyAsync(c.d_Xb, c.d_ft, nbt * sizeof(double), cudaMemcpyDeviceToDevice, st));
+    CU(corner_reduce(c, c.d_Xb, 1, c.d_Cb, c.d_Vraw, st));
+    CU(corner_gather_vec(c, c.d_ft + nbt, c.d_fbar, st));
+    CU(axpby(np, -1.0, c.d_Vraw, 1.0, c.d_fbar, st));
+    // d = d_r - F_rc Kbar^{-1} fbar
+    CU(gemv_dense(c.d_Kbar_inv, np, np, c.d_fbar, c.d_V, 0.0, st));
+    CU(cudaMemsetAsync(c.d_Yb, 0, nbt * sizeof(double), st));
+    CU(corner_expand(c, c.d_V, 1, c.d_Vc, c.d_Yb, st));
+    CU(scatter_b_to_lam(c, c.d_Yb, 1, c.d_lam, nl, st));
+    CU(axpby(nl, -1.0, c.d_lam, 1.0, c.d_d, st));
+  } else {
+    // TFETI coarse space: G = -R^T B^T, G G^T, e = -R^T f, lambda_0 = G^T (G G^T)^{-1} e
+    const int nco = c.n_coarse;
+    CU(tfeti_build_G(c, c.d_G, st));
+    TRY(gemm_tn(c, c.d_G, nl, c.d_G, nl, c.d_Kbar, nco, nco, nco, (int)nl, 1.0, 0.0));
+    {
+      DenseDesc hd{};
+      hd.n = nco;
+      CU(dense_spd_inverse(c.d_dense_coarse, &hd, 1, c.d_status, st));
+    }
+    CU(tfeti_build_e(c, c.d_e, st));
+    CU(gemv_dense(c.d_Kbar_inv, nco, nco, c.d_e, c.d_alpha, 0.0, st));
+    TRY(gemm_nn(c, c.d_G, nl, c.d_alpha, nco, c.d_lam0, nl, (int)nl, 1, nco, 1.0, 0.0));
+  }
+  TRY(sync_check(c));
+  TRY(check_status(c, "coarse factorization"));
+  c.state = 2;
+  c.have_solution = 0;
+  return FETI_OK;
+}
+
+}  // extern "C"
+
+// ---------------------------------------------------------------- Algorithm 1
+static feti_status ensure_krylov(Ctx& c, int mmax) {
+  if (mmax <= c.kr_cap) return FETI_OK;
+  const int64_t nl = c.hp.n_lam;
+  TRY(dalloc(c, c.d_r, nl));
+  TRY(dalloc(c, c.d_z, nl));
+  TRY(dalloc(c, c.d_lamt, nl));
+  TRY(dalloc(c, c.d_Wb, (size_t)nl * mmax));
+  TRY(dalloc(c, c.d_Qb, (size_t)nl * mmax));
+  TRY(dalloc(c, c.d_Delta, (size_t)mmax * mmax));
+  TRY(dalloc(c, c.d_T, (size_t)mmax * mmax));
+  TRY(dalloc(c, c.d_gamma, mmax));
+  TRY(dalloc(c, c.d_rrwork, (size_t)2 * mmax * mmax + mmax));
+  c.kr_cap = mmax;
+  return FETI_OK;
+}
+
+static feti_status read_scalar(Ctx& c, const double* d, double* out) {
+  CU(cudaMemcpyAsync(c.h_pin, d, sizeof(double), cudaMemcpyDeviceToHost, c.stream));
+  CU(cudaStreamSynchronize(c.stream));
+  *out = c.h_pin[0];
+  return FETI_OK;
+}
+
+static feti_status solve_impl(Ctx& c, double* lambda_inout, feti_stats* stats) {
+  const HostProblem& hp = c.hp;
+  const int64_t nl = hp.n_lam;
+  const bool multi = c.opt.krylov == FETI_RRS;
+  const bool full = c.opt.krylov != FETI_PCG;
+  const int mmax = multi ? hp.n_sub : 1;
+  if (mmax > 1024) { c.err = "more than 1024 subdomains per direction block"; return FETI_ENOTSUP; }
+  TRY(ensure_krylov(c, mmax));
+  TRY(ensure_blocks(c, mmax));
+  cudaStream_t st = c.stream;
+  feti_stats S{};
+  // lambda_0 (warm start or the method's own), r_0 = P^T (d - F lambda_0)
+  CU(cudaMemcpyAsync(c.d_lam, lambda_inout ? lambda_inout : c.d_lam0, nl * sizeof(double),
+                     cudaMemcpyDeviceToDevice, st));
+  if (lambda_inout && hp.method == FETI_TFETI) {
+    // keep G lambda = e: lambda = lambda_0 + P (lambda_in - lambda_0)
+    CU(axpby(nl, -1.0, c.d_lam0, 1.0, c.d_lam, st));
+    TRY(project(c, c.d_lam, nl, 1));
+    CU(axpby(nl, 1.0, c.d_lam0, 1.0, c.d_lam, st));
+  }
+  TRY(apply_dual(c, c.d_lam, nl, 1, c.d_r, nl));
+  CU(axpby(nl, 1.0, c.d_d, -1.0, c.d_r, st));
+  TRY(project(c, c.d_r, nl, 1));
+  // Z_0, W_0 = P Z_0
+  CU(precond_apply(c, c.d_r, multi ? c.d_Wb : nullptr, nl, c.d_z, st));
+  if (!multi) CU(cudaMemcpyAsync(c.d_Wb, c.d_z, nl * sizeof(double), cudaMemcpyDeviceToDevice, st));
+  const int m = mmax;
+  TRY(project(c, c.d_Wb, nl, m));
+  CU(cudaMemsetAsync(c.d_lamt, 0, nl * sizeof(double), st));
+  CU(dot(c.d_r, c.d_z, nl, c.d_red, c.d_scalar, st));
+  double rz = 0.0;
+  TRY(read_scalar(c, c.d_scalar, &rz));
+  const double eps0 = std::sqrt(std::max(rz, 0.0));
+  double eps = eps0;
+  S.eps0 = eps0;
+  int it = 0;
+  feti_status result = FETI_OK;
+  c.hist_k.clear();
+  while (eps > c.opt.tol * eps0 && it < c.opt.max_iter) {
+    // Q = F W, Delta = Q^T W
+    TRY(apply_dual(c, c.d_Wb, nl, m, c.d_Qb, nl));
+    TRY(gemm_tn(c, c.d_Qb, nl, c.d_Wb, nl, c.d_Delta, m, m, m, (int)nl, 1.0, 0.0));
+    // rank-revealing factorization and F-orthonormal transform T = N^T [L~^{-T}; 0]
+    CU(rr_cholesky(c.d_Delta, m, m, c.opt.rr_tol, c.d_rrwork, c.d_T, c.d_kdev, st));
+    int k = 0;
+    CU(cudaMemcpyAsync(c.h_pin, c.d_kdev, sizeof(int), cudaMemcpyDeviceToHost, st));
+    CU(cudaStreamSynchronize(st));
+    std::memcpy(&k, c.h_pin, sizeof(int));
+    S.last_rank = k;
+    if (k <= 0) { result = FETI_EBREAKDOWN; c.err = "no independent search direction left"; break; }
+    if ((int)c.hist_W.size() <= it) {
+      double *w, *q;
+      TRY(dalloc(c, w, (size_t)nl * mmax));
+      TRY(dalloc(c, q, (size_t)nl * mmax));
+      c.hist_W.push_back(w);
+      c.hist_Q.push_back(q);
+    }
+    double* Wi = c.hist_W[it];
+    double* Qi = c.hist_Q[it];
+    c.hist_k.push_back(k);
+    const double fl_T = (double)nl * k * (k + 1.0);   // 2 n nnz(T), T = N^T [L~^{-T}; 0]
+    TRY(gemm_nn(c, c.d_Wb, nl, c.d_T, m, Wi, nl, (int)nl, k, m, 1.0, 0.0, fl_T));
+    TRY(gemm_nn(c, c.d_Qb, nl, c.d_T, m, Qi, nl, (int)nl, k, m, 1.0, 0.0, fl_T));
+    S.f_applies += m;
+    // gamma = W^T r; lambda~ += W gamma; r -= P^T Q gamma
+    CU(gemv_t(Wi, nl, nl, k, c.d_r, c.d_gamma, st));
+    if (hp.method == FETI_TFETI) {
+      CU(step_update(Wi, Qi, nl, nl, k, c.d_gamma, c.d_lamt, c.d_r, c.d_z, st));
+      TRY(project(c, c.d_z, nl, 1));
+      CU(axpby(nl, -1.0, c.d_z, 1.0, c.d_r, st));
+    } else {
+      CU(step_update(Wi, Qi, nl, nl, k, c.d_gamma, c.d_lamt, c.d_r, nullptr, st));
+    }
+    // Z_{i+1}, W_{i+1} = P Z_{i+1}
+    CU(precond_apply(c, c.d_r, multi ? c.d_Wb : nullptr, nl, c.d_z, st));
+    if (!multi) CU(cudaMemcpyAsync(c.d_Wb, c.d_z, nl * sizeof(double), cudaMemcpyDeviceToDevice, st));
+    TRY(project(c, c.d_Wb, nl, m));
+    // F-orthogonalise against the stored blocks, oldest first (modified Gram-Schmidt)
+    for (int j = full ? 0 : it; j <= it; ++j) {
+      const int kj = c.hist_k[j];
+      TRY(gemm_tn(c, c.hist_Q[j], nl, c.d_Wb, nl, c.d_Delta, kj, kj, m, (int)nl, 1.0, 0.0));
+      TRY(gemm_nn(c, c.hist_W[j], nl, c.d_Delta, kj, c.d_Wb, nl, (int)nl, m, kj, -1.0, 1.0));
+    }
+    CU(dot(c.d_r, c.d_z, nl, c.d_red, c.d_scalar, st));
+    TRY(read_scalar(c, c.d_scalar, &rz));
+    ++it;
+    eps = std::sqrt(std::max(rz, 0.0));
+    if (!std::isfinite(rz)) { result = FETI_EBREAKDOWN; c.err = "NaN or Inf in the residual"; break; }
+  }
+  CU(axpby(nl, 1.0, c.d_lamt, 1.0, c.d_lam, st));
+  if (lambda_inout) CU(cudaMemcpyAsync(lambda_inout, c.d_lam, nl * sizeof(double), cudaMemcpyDeviceToDevice, st));
+  TRY(sync_check(c));
+  S.iterations = it;
+  S.eps = eps;
+  S.converged = eps <= c.opt.tol * eps0;
+  if (result == FETI_OK && !S.converged) {
+    result = FETI_ENOTCONV;
+    c.err = "max_iter reached";
+  }
+  c.last = S;
+  if (stats) *stats = S;
+  return result;
+}
+
+extern "C" {
+
+feti_status feti_solve_dual(feti_ctx* ctx, double* lambda_inout, feti_stats* stats) {
+  if (!ctx) return FETI_EINVAL;
+  Ctx& c = ctx->c;
+  c.err.clear();
+  if (c.state < 2) { c.err = "feti_solve_dual before feti_factorize"; return FETI_ESTATE; }
+  feti_status s = solve_impl(c, lambda_inout, stats);
+  if (s == FETI_OK || s == FETI_ENOTCONV) {
+    c.state = 3;
+    c.have_solution = 1;
+  }
+  return s;
+}
+
+feti_status feti_recover_displacements(feti_ctx* ctx, double* u_out, int on_device, double* compliance_out) {
+  if (!ctx) return FETI_EINVAL;
+  Ctx& c = ctx->c;
+  c.err.clear();
+  if (c.state < 3 || !c.have_solution) { c.err = "feti_recover_displacements before feti_solve_dual"; return FETI_ESTATE; }
+  const HostProblem& hp = c.hp;
+  cudaStream_t st = c.stream;
+  if (hp.method == FETI_FETIDP) {
+    CU(recover_fetidp(c, c.d_lam, st));
+  } else {
+    // alpha = (G G^T)^{-1} G (d - F lambda)
+    const int64_t nl = hp.n_lam;
+    const int nco = c.n_coarse;
+    TRY(ensure_krylov(c, 1));
+    TRY(apply_dual(c, c.d_lam, nl, 1, c.d_r, nl));
+    CU(axpby(nl, 1.0, c.d_d, -1.0, c.d_r, st));
+    TRY(gemm_tn(c, c.d_G, nl, c.d_r, nl, c.d_ct1, nco, nco, 1, (int)nl, 1.0, 0.0));
+    CU(gemv_dense(c.d_Kbar_inv, nco, nco, c.d_ct1, c.d_alpha, 0.0, st));
+    CU(recover_tfeti(c, c.d_lam, c.d_alpha, st));
+  }
+  CU(launch_gather_u(c, st));
+  if (u_out)
+    CU(cudaMemcpyAsync(u_out, c.d_uglob, hp.n_dofs * sizeof(double),
+                       on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, st));
+  if (compliance_out) {
+    CU(dot(c.d_fglob, c.d_uglob, hp.n_dofs, c.d_red, c.d_scalar, st));
+    TRY(read_scalar(c, c.d_scalar, compliance_out));
+  }
+  TRY(sync_check(c));
+  c.state = 4;
+  return FETI_OK;
+}
+
+feti_status feti_compliance_grad(feti_ctx* ctx, double* dc_drho, int on_device) {
+  if (!ctx || !dc_drho) return FETI_EINVAL;
+  Ctx& c = ctx->c;
+  c.err.clear();
+  if (c.state < 4) { c.err = "feti_compliance_grad before feti_recover_displacements"; return FETI_ESTATE; }
+  if (on_device) {
+    CU(launch_grad(c, dc_drho, c.stream));
+  } else {
+    double* tmp;
+    TRY(dalloc(c, tmp, c.hp.n_elements));
+    CU(launch_grad(c, tmp, c.stream));
+    CU(cudaMemcpyAsync(dc_drho, tmp, c.hp.n_elements * sizeof(double), cudaMemcpyDeviceToHost, c.stream));
+  }
+  TRY(sync_check(c));
+  return FETI_OK;
+}
+
+feti_status feti_apply_dual(feti_ctx* ctx, const double* X, int ldx, int m, double* Y, int ldy) {
+  if (!ctx || !X || !Y || m < 0) return FETI_EINVAL;
+  Ctx& c = ctx->c;
+  c.err.clear();
+  if (c.state < 2) { c.err = "feti_apply_dual before feti_factorize"; return FETI_ESTATE; }
+  if (ldx < c.hp.n_lam || ldy < c.hp.n_lam) { c.err = "leading dimension smaller than n_lambda"; return FETI_EINVAL; }
+  if (m == 0) return FETI_OK;
+  TRY(apply_dual(c, X, ldx, m, Y, ldy));
+  TRY(sync_check(c));
+  return FETI_OK;
+}
+
+feti_status feti_apply_precond(feti_ctx* ctx, const double* r, double* Z, int ldz, double* z) {
+  if (!ctx || !r) return FETI_EINVAL;
+  Ctx& c = ctx->c;
+  c.err.clear();
+  if (c.state < 2) { c.err = "feti_apply_precond before feti_factorize"; return FETI_ESTATE; }
+  if (Z && ldz < c.hp.n_lam) { c.err = "ldz smaller than n_lambda"; return FETI_EINVAL; }
+  CU(precond_apply(c, r, Z, ldz, z, c.stream));
+  TRY(sync_check(c));
+  return FETI_OK;
+}
+
+feti_status feti_query(const feti_ctx* ctx, int key, int64_t* value) {
+  if (!ctx || !value) return FETI_EINVAL;
+  const Ctx& c = ctx->c;
+  if (key == FETI_Q_LAUNCHES) { *value = launches(); return FETI_OK; }
+  if (c.state < 1) return FETI_ESTATE;
+  const HostProblem& hp = c.hp;
+  switch (key) {
+    case FETI_Q_N_LAMBDA: *value = hp.n_lam; break;
+    case FETI_Q_N_SUBDOMAINS: *value = hp.n_sub; break;
+    case FETI_Q_N_PRIMAL: *value = hp.n_primal; break;
+    case FETI_Q_N_MODULES: *value = c.n_mod; break;
+    case FETI_Q_N_B_TOTAL: *value = hp.n_b_total; break;
+    case FETI_Q_N_DOFS: *value = hp.n_dofs; break;
+    case FETI_Q_N_ELEMENTS: *value = hp.n_elements; break;
+    case FETI_Q_MAX_NB: *value = c.max_nb; break;
+    case FETI_Q_DEVICE_BYTES: *value = (int64_t)c.device_bytes; break;
+    case FETI_Q_N_RBM: *value = hp.n_rbm; break;
+    case FETI_Q_LAUNCHES: *value = launches(); break;
+    default: return FETI_EINVAL;
+  }
+  return FETI_OK;
+}
+
+feti_status feti_profile_begin(feti_ctx* ctx) {
+  if (!ctx) return FETI_EINVAL;
+  Ctx& c = ctx->c;
+  if (c.prof) { c.err = "a profile is already active"; return FETI_ESTATE; }
+  c.prof = new_gemm_profile();
+  set_gemm_profile(static_cast<GemmProfile*>(c.prof));
+  return FETI_OK;
+}
+
+feti_status feti_profile_end(feti_ctx* ctx, double* gemm_flops, double* gemm_ms, int64_t* gemm_launches) {
+  if (!ctx) return FETI_EINVAL;
+  Ctx& c = ctx->c;
+  if (!c.prof) { c.err = "no active profile"; return FETI_ESTATE; }
+  CU(cudaStreamSynchronize(c.stream));
+  set_gemm_profile(nullptr);
+  double f = 0, t = 0;
+  int64_t n = 0;
+  finish_gemm_profile(static_cast<GemmProfile*>(c.prof), &f, &t, &n);
+  c.prof = nullptr;
+  if (gemm_flops) *gemm_flops = f;
+  if (gemm_ms) *gemm_ms = t;
+  if (gemm_launches) *gemm_launches = n;
+  return FETI_OK;
+}
+
+feti_status feti_lambda_layout(const feti_ctx* ctx, int32_t* out) {
+  if (!ctx || !out) return FETI_EINVAL;
+  const Ctx& c = ctx->c;
+  if (c.state < 1) return FETI_ESTATE;
+  const HostProblem& hp = c.hp;
+  for (int64_t l = 0; l < hp.n_lam; ++l) {
+    for (int t = 0; t < 2; ++t) {
+      const int b = t == 0 ? hp.lam_b0[l] : hp.lam_b1[l];
+      int32_t* o = out + 6 * l + 3 * t;
+      if (b < 0) { o[0] = -1; o[1] = -1; o[2] = 0; continue; }
+      const int s = hp.b_sub[b];
+      const StructType& T = hp.types[hp.sub_type[s]];
+      o[0] = s;
+      o[1] = T.blist[b - hp.b_off[s]];
+      o[2] = t == 0 ? hp.lam_s0[l] : hp.lam_s1[l];
+    }
+  }
+  return FETI_OK;
+}
+
+feti_status feti_local_blocks(feti_ctx* ctx, int s, int* nb, int* nc, int32_t* bdofs, int32_t* cdofs, double* F,
+                              double* Sout, double* Frc) {
+  if (!ctx) return FETI_EINVAL;
+  Ctx& c = ctx->c;
+  if (c.state < 2) { c.err = "feti_local_blocks before feti_factorize"; return FETI_ESTATE; }
+  if (s < 0 || s >= c.hp.n_sub) return FETI_EINVAL;
+  const DevSub& S = c.h_subs[s];
+  const DevModule& M = c.h_mods[S.module];
+  const StructType& T = c.hp.types[S.type];
+  if (nb) *nb = T.n_b;
+  if (nc) *nc = T.n_c;
+  if (bdofs) for (int k = 0; k < T.n_b; ++k) bdofs[k] = T.blist[k];
+  if (cdofs) for (int k = 0; k < T.n_c; ++k) cdofs[k] = T.clist[k];
+  const int nbc = T.n_bc();
+  if (F) CU(cudaMemcpy(F, c.d_modmem + M.F, (size_t)T.n_b * T.n_b * sizeof(double), cudaMemcpyDeviceToHost));
+  if (Sout)
+    CU(cudaMemcpy2D(Sout, T.n_b * sizeof(double), c.d_modmem + M.S, nbc * sizeof(double), T.n_b * sizeof(double),
+                    T.n_b, cudaMemcpyDeviceToHost));
+  if (Frc && T.n_c > 0)
+    CU(cudaMemcpy(Frc, c.d_modmem + M.Frc, (size_t)T.n_b * T.n_c * sizeof(double), cudaMemcpyDeviceToHost));
+  return FETI_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,218 @@
+// Dual-operator kernels: the hot path of Algorithm 1.
+//
+//   Y = F X:  gather X into the interface ("b") space of every subdomain
+//             (B^sT X, signed), multiply by the dense local blocks, scatter
+//             back with B^s.  FETI-DP (Eq. 12, u_c condensed) adds the corner
+//             correction F_rc Kbar_cc^{-1} F_rc^T X between the two halves.
+//   Z = [B~^s S^s B~^sT r]_s: the same gather with the scaling weights of
+//             Eq. (15), one dense S^s product per subdomain, and a scatter that
+//             keeps each subdomain's contribution in its own column (Section 3.3).
+//
+// Every multiplier row has at most two entries, so the scatter is a gather
+// from the multiplier side: deterministic, no atomics.
+#include <algorithm>
+
+#include "kernels.h"
+
+namespace feti {
+
+namespace {
+
+__global__ void k_gather(int64_t nbt, int m, const int* __restrict__ off, const int* __restrict__ lam,
+                         const signed char* __restrict__ sg, const double* __restrict__ X, int64_t ldx,
+                         double* __restrict__ Xb) {
+  const int64_t b = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  const int j = blockIdx.y;
+  if (b >= nbt || j >= m) return;
+  const double* x = X + (int64_t)j * ldx;
+  double v = 0.0;
+  for (int e = off[b]; e < off[b + 1]; ++e) v += sg[e] > 0 ? x[lam[e]] : -x[lam[e]];
+  Xb[b + (int64_t)j * nbt] = v;
+}
+
+__global__ void k_scatter(int64_t nl, int m, const int* __restrict__ b0, const signed char* __restrict__ s0,
+                          const int* __restrict__ b1, const signed char* __restrict__ s1,
+                          const double* __restrict__ Yb, int64_t nbt, double* __restrict__ Y, int64_t ldy) {
+  const int64_t l = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  const int j = blockIdx.y;
+  if (l >= nl || j >= m) return;
+  const double* yb = Yb + (int64_t)j * nbt;
+  const double a = yb[b0[l]];
+  double v = s0[l] > 0 ? a : -a;
+  const int q = b1[l];
+  if (q >= 0) {
+    const double c = yb[q];
+    v += s1[l] > 0 ? c : -c;
+  }
+  Y[l + (int64_t)j * ldy] = v;
+}
+
+// rb[b] = sum over rows of b of w * sign * r  (B~^sT r)
+__global__ void k_gather_weighted(int64_t nbt, const int* __restrict__ off, const int* __restrict__ lam,
+                                  const signed char* __restrict__ sg, const int* __restrict__ lb0,
+                                  const double* __restrict__ w0, const double* __restrict__ w1,
+                                  const double* __restrict__ r, double* __restrict__ rb) {
+  const int64_t b = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (b >= nbt) return;
+  double v = 0.0;
+  for (int e = off[b]; e < off[b + 1]; ++e) {
+    const int l = lam[e];
+    const double w = lb0[l] == (int)b ? w0[l] : w1[l];
+    const double t = w * r[l];
+    v += sg[e] > 0 ? t : -t;
+  }
+  rb[b] = v;
+}
+
+// Z[l, sub] = w * sign * zb[b] for each entry of row l; z[l] = row sum.
+__global__ void k_prec_scatter(int64_t nl, const int* __restrict__ b0, const signed char* __restrict__ s0,
+                               const int* __restrict__ b1, const signed char* __restrict__ s1,
+                               const double* __restrict__ w0, const double* __restrict__ w1,
+                               const int* __restrict__ bsub, const double* __restrict__ zb,
+                               double* __restrict__ Z, int64_t ldz, double* __restrict__ z) {
+  const int64_t l = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (l >= nl) return;
+  const int q0 = b0[l];
+  double v0 = w0[l] * zb[q0];
+  if (s0[l] < 0) v0 = -v0;
+  double v = v0;
+  if (Z) Z[l + (int64_t)bsub[q0] * ldz] = v0;
+  const int q1 = b1[l];
+  if (q1 >= 0) {
+    double v1 = w1[l] * zb[q1];
+    if (s1[l] < 0) v1 = -v1;
+    v += v1;
+    if (Z) Z[l + (int64_t)bsub[q1] * ldz] = v1;
+  }
+  if (z) z[l] = v;
+}
+
+// y_b(s) = A_s x_b(s) (+ beta y) with A_s = F_s (which 0), S_bb (which 1);
+// one warp per row.
+__global__ void k_sub_gemv(const DevType* __restrict__ types, const DevModule* __restrict__ mods,
+                           const DevSub* __restrict__ subs, const double* __restrict__ mem, int which,
+                           const double* __restrict__ x, double* __restrict__ y, double beta) {
+  const DevSub S = subs[blockIdx.y];
+  const DevType T = types[S.type];
+  const DevModule M = mods[S.module];
+  const int row = blockIdx.x * (blockDim.x / 32) + threadIdx.x / 32;
+  const int lane = threadIdx.x & 31;
+  const int n = T.n_b;
+  if (row >= n) return;
+  const double* A = mem + (which == 0 ? M.F : M.S);
+  const int64_t ld = which == 0 ? n : (int64_t)(T.n_b + T.n_c);
+  const double* a = A + (int64_t)row * ld;
+  const double* xs = x + S.b_off;
+  double acc = 0.0;
+  for (int k = lane; k < n; k += 32) acc = fma(a[k], xs[k], acc);
+  for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+  if (lane == 0) {
+    double* yp = y + S.b_off + row;
+    *yp = beta != 0.0 ? fma(beta, *yp, acc) : acc;
+  }
+}
+
+// Vraw[g + j*np] = sum over the corner copies of g of Cb[src + j*nct]
+__global__ void k_corner_gather(int np, int m, const int* __restrict__ poff, const int* __restrict__ psrc,
+                                const double* __restrict__ Cb, int64_t nct, double* __restrict__ V) {
+  const int g = blockIdx.x * blockDim.x + threadIdx.x;
+  const int j = blockIdx.y;
+  if (g >= np || j >= m) return;
+  double v = 0.0;
+  for (int a = poff[g]; a < poff[g + 1]; ++a) v += Cb[psrc[a] + (int64_t)j * nct];
+  V[g + (int64_t)j * np] = v;
+}
+
+// Vc[k + j*nct] = V[c_glob[k] + j*np]
+__global__ void k_corner_spread(int64_t nct, int m, const int* __restrict__ cg, const double* __restrict__ V,
+                                int np, double* __restrict__ Vc) {
+  const int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  const int j = blockIdx.y;
+  if (k >= nct || j >= m) return;
+  Vc[k + (int64_t)j * nct] = V[cg[k] + (int64_t)j * np];
+}
+
+}  // namespace
+
+cudaError_t gather_lam_to_b(const Ctx& c, const double* X, int64_t ldx, int m, double* Xb, cudaStream_t st) {
+  const int64_t nbt = c.hp.n_b_total;
+  dim3 g((unsigned)((nbt + 255) / 256), m);
+  k_gather<<<g, 256, 0, st>>>(nbt, m, c.d_b2l_off, c.d_b2l_lam, c.d_b2l_sign, X, ldx, Xb);
+  note_launches(1);
+  return cudaGetLastError();
+}
+
+cudaError_t scatter_b_to_lam(const Ctx& c, const double* Yb, int m, double* Y, int64_t ldy, cudaStream_t st) {
+  const int64_t nl = c.hp.n_lam;
+  dim3 g((unsigned)((nl + 255) / 256), m);
+  k_scatter<<<g, 256, 0, st>>>(nl, m, c.d_lam_b0, c.d_lam_s0, c.d_lam_b1, c.d_lam_s1, Yb, c.hp.n_b_total, Y, ldy);
+  note_launches(1);
+  return cudaGetLastError();
+}
+
+cudaError_t apply_local_F(Ctx& c, const double* /*Xb*/, double* /*Yb*/, int m, double beta, cudaStream_t st) {
+  // descriptors point at c.d_Xb / c.d_Yb (fixed buffers)
+  return dgemm_batched(c.d_gemm_F, c.hp.n_sub, c.max_nb, c.max_nb, m, 1.0, beta, st, c.fl_F * m);
+}
+
+cudaError_t corner_reduce(Ctx& c, const double* /*Xb*/, int m, double* /*Cb*/, double* Vraw, cudaStream_t st) {
+  cudaError_t e = dgemm_batched(c.d_gemm_FrcT, c.hp.n_sub, c.max_nc, c.max_nb, m, 1.0, 0.0, st, c.fl_FrcT * m);
+  if (e != cudaSuccess) return e;
+  const int np = c.hp.n_primal;
+  dim3 g((np + 127) / 128, m);
+  k_corner_gather<<<g, 128, 0, st>>>(np, m, c.d_prim_off, c.d_prim_src, c.d_Cb, c.n_c_total, Vraw);
+  note_launches(1);
+  return cudaGetLastError();
+}
+
+cudaError_t corner_gather_vec(const Ctx& c, const double* src, double* out, cudaStream_t st) {
+  const int np = c.hp.n_primal;
+  k_corner_gather<<<(np + 127) / 128, 128, 0, st>>>(np, 1, c.d_prim_off, c.d_prim_src, src,
+                                                    std::max<int64_t>(c.n_c_total, 1), out);
+  note_launches(1);
+  return cudaGetLastError();
+}
+
+cudaError_t corner_expand(Ctx& c, const double* V, int m, double* Vc, double* /*Yb*/, cudaStream_t st) {
+  const int64_t nct = c.n_c_total;
+  dim3 g((unsigned)((nct + 255) / 256), m);
+  k_corner_spread<<<g, 256, 0, st>>>(nct, m, c.d_c_glob, V, c.hp.n_primal, Vc);
+  note_launches(1);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  return dgemm_batched(c.d_gemm_Frc, c.hp.n_sub, c.max_nb, c.max_nb, m, 1.0, 1.0, st, c.fl_Frc * m);
+}
+
+cudaError_t batched_gemv(const Ctx& c, int which, const double* xb, double* yb, double beta, cudaStream_t st) {
+  dim3 g((c.max_nb + 7) / 8, c.hp.n_sub);
+  k_sub_gemv<<<g, 256, 0, st>>>(c.d_types, c.d_mods, c.d_subs, c.d_modmem, which, xb, yb, beta);
+  note_launches(1);
+  return cudaGetLastError();
+}
+
+cudaError_t batched_gemv_F(Ctx& c, const double* xb, double* yb, cudaStream_t st) {
+  return batched_gemv(c, 0, xb, yb, 0.0, st);
+}
+
+cudaError_t precond_apply(Ctx& c, const double* r, double* Z, int64_t ldz, double* z, cudaStream_t st) {
+  const int64_t nbt = c.hp.n_b_total, nl = c.hp.n_lam;
+  double* rb = c.d_pb0;
+  double* zb = c.d_pb1;
+  k_gather_weighted<<<(unsigned)((nbt + 255) / 256), 256, 0, st>>>(nbt, c.d_b2l_off, c.d_b2l_lam, c.d_b2l_sign,
+                                                                   c.d_lam_b0, c.d_w0, c.d_w1, r, rb);
+  note_launches(1);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  e = batched_gemv(c, 1, rb, zb, 0.0, st);
+  if (e != cudaSuccess) return e;
+  if (Z) {
+    e = cudaMemsetAsync(Z, 0, sizeof(double) * (size_t)ldz * c.hp.n_sub, st);
+    if (e != cudaSuccess) return e;
+  }
+  k_prec_scatter<<<(unsigned)((nl + 255) / 256), 256, 0, st>>>(nl, c.d_lam_b0, c.d_lam_s0, c.d_lam_b1, c.d_lam_s1,
+                                                               c.d_w0, c.d_w1, c.d_b_sub, zb, Z, ldz, z);
+  note_launches(1);
+  return cudaGetLastError();
+}
+
+}  // namespace feti

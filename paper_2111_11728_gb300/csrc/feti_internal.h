@@ -1,0 +1,242 @@
+// Internal declarations shared by the library's translation units.
+#pragma once
+
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include <cuda_runtime.h>
+
+#include "../../include/feti.h"
+
+namespace feti {
+
+// ---------------------------------------------------------------------------
+// Host-side description of the torn problem (built by setup.cpp).
+// ---------------------------------------------------------------------------
+
+// Local DOF classes.  FETI-DP: interior (i), interface (b), corner primal (c),
+// fixed and eliminated (x).  TFETI: i and b only (b = every DOF a row of B touches).
+enum DofClass : int { CLS_I = 0, CLS_B = 1, CLS_C = 2, CLS_X = 3 };
+
+// Subdomains with the same boundary situation share one DOF classification.
+struct StructType {
+  int n_loc = 0;                 // local DOFs
+  std::vector<int> cls;          // [n_loc] DofClass
+  std::vector<int> idx;          // [n_loc] position inside its class list
+  std::vector<int> ilist, blist, clist;   // local DOF ids per class (i, b, c order)
+  int n_i = 0, n_b = 0, n_c = 0;
+  int bw = 0;                    // half-bandwidth of K_ii in i-order
+  int n_bc() const { return n_b + n_c; }
+};
+
+struct HostProblem {
+  // mesh
+  int dim = 2;
+  int tiles[3] = {1, 1, 1}, elems[3] = {1, 1, 1};
+  int nel[3] = {1, 1, 1}, nnod[3] = {1, 1, 1}, lnod[3] = {1, 1, 1};
+  int64_t n_nodes = 0, n_elements = 0, n_dofs = 0;
+  int n_sub = 0, n_loc_nodes = 0, n_loc_dofs = 0, n_loc_elems = 0;
+  double E0 = 1, Emin = 0, nu = 0.3, p = 3;
+  int method = FETI_FETIDP;
+
+  // structure types and modules
+  std::vector<StructType> types;
+  std::vector<int> sub_type;     // [n_sub]
+  std::vector<int> sub_module;   // [n_sub]
+  std::vector<int> module_rep;   // [n_mod] representative subdomain
+  std::vector<int> module_type;  // [n_mod]
+
+  // interface (b) space: global b index = b_off[s] + position in the type's blist
+  std::vector<int64_t> b_off;    // [n_sub + 1]
+  int64_t n_b_total = 0;
+  std::vector<int> b_sub;        // [n_b_total] owning subdomain
+
+  // multipliers: each row has one or two (global b, sign) entries
+  int64_t n_lam = 0;
+  std::vector<int> lam_b0, lam_b1;        // [n_lam] global b indices (lam_b1 = -1 for one-entry rows)
+  std::vector<signed char> lam_s0, lam_s1;
+  std::vector<int> lam_group;             // [n_lam] sharing group (all copies of the DOF)
+  std::vector<int> group_off, group_b;    // CSR over groups -> global b of every copy
+  std::vector<int> b2l_off, b2l_lam;      // CSR global b -> multiplier rows
+  std::vector<signed char> b2l_sign;
+
+  // primal (FETI-DP corners)
+  int n_primal = 0;
+  std::vector<int64_t> c_off;             // [n_sub + 1] offset into c_glob
+  std::vector<int> c_glob;                // primal index of each local corner DOF
+  std::vector<int> prim_off, prim_src;    // CSR primal -> (c_off[s] + k) contributors
+
+  // loads and output gather
+  std::vector<int64_t> load_src;          // [n_sub * n_loc_dofs] global DOF feeding the local load, or -1
+  std::vector<int64_t> dof_copy_off;      // [n_dofs + 1] CSR global DOF -> local copies
+  std::vector<int64_t> dof_copy;          // s * n_loc_dofs + local dof
+  std::vector<unsigned char> dirichlet;   // [n_dofs]
+
+  // rigid-body modes (TFETI): n_rbm per subdomain
+  int n_rbm = 0;
+};
+
+// Builds the host description; returns an error message or "".
+std::string build_host_problem(const feti_problem& prob, int method, int dedup,
+                               const double* rho_host, HostProblem& hp);
+
+// Local node (lexicographic in the tile) -> tile-local integer coordinates.
+inline void local_node_coords(const HostProblem& hp, int ln, int c[3]) {
+  c[0] = ln % hp.lnod[0];
+  int r = ln / hp.lnod[0];
+  c[1] = r % hp.lnod[1];
+  c[2] = r / hp.lnod[1];
+}
+
+// ---------------------------------------------------------------------------
+// Device-side data.
+// ---------------------------------------------------------------------------
+
+// Per-structure-type device info.
+struct DevType {
+  int n_loc, n_i, n_b, n_c, bw;
+  int pad;
+  const int* cls_idx;            // [n_loc] (cls << 24) | idx
+  const int* ilist;              // [n_i]
+  const int* blist;              // [n_b]
+  const int* clist;              // [n_c]
+  const double* Rraw;            // [n_b x n_rbm] rigid modes at the b DOFs (TFETI)
+  const double* Rhat;            // [n_b x n_rbm] orthonormal basis of their span (TFETI)
+};
+
+// Per-module offsets into the module arrays (in doubles).
+struct DevModule {
+  int type;
+  int rep;                       // representative subdomain
+  int64_t lcol, lrow, rdiag;     // band factor (column and row form), reciprocal diagonal
+  int64_t Y;                     // [n_i x n_bc] row-major: L^{-1} K_{i,bc}
+  int64_t S;                     // [n_bc x n_bc] row-major Schur complement onto b+c
+  int64_t W;                     // [n_b x n_b] Cholesky factor of S_bb (work)
+  int64_t Li;                    // [n_b x n_b] its inverse (work)
+  int64_t F;                     // [n_b x n_b] row-major local dual block
+  int64_t Frc;                   // [n_b x n_c] row-major (FETI-DP)
+  int64_t Kb;                    // [n_c x n_c] local Kbar_cc (FETI-DP)
+  int64_t Rb;                    // [n_b x n_rbm] orthonormal rigid modes on b (TFETI)
+};
+
+// Per-subdomain device info.
+struct DevSub {
+  int module;
+  int type;
+  int64_t b_off;                 // into the global b space
+  int64_t c_off;                 // into c_glob
+  int tile[3];
+  int pad;
+};
+
+struct GemmDesc;
+struct DenseDesc;
+
+struct Ctx {
+  feti_options opt{};
+  cudaStream_t stream = nullptr;
+  std::string err;
+  int state = 0;                 // 0 created, 1 set up, 2 factorized, 3 solved, 4 recovered
+  int device = 0;
+  HostProblem hp;
+  std::vector<void*> allocs;     // every device allocation (freed at destroy)
+  size_t device_bytes = 0;
+  double* h_pin = nullptr;       // pinned host scalars
+
+  // problem data
+  double* d_rho = nullptr;       // [n_elements]
+  double* d_E = nullptr;         // [n_elements] SIMP moduli
+  double* d_fglob = nullptr;     // [n_dofs]
+  double* d_k0 = nullptr;        // element stiffness for E = 1
+  std::vector<double> h_k0;
+  // types / modules / subdomains
+  DevType* d_types = nullptr;
+  DevModule* d_mods = nullptr;
+  DevSub* d_subs = nullptr;
+  std::vector<DevType> h_types;
+  std::vector<DevModule> h_mods;
+  std::vector<DevSub> h_subs;
+  int n_mod = 0, max_nb = 1, max_nc = 1;
+  // algorithmic flops of the batched products (per column where they scale with m)
+  double fl_F = 0, fl_FrcT = 0, fl_Frc = 0, fl_schur = 0, fl_frcmake = 0, fl_kbmake = 0;
+  void* prof = nullptr;          // active GEMM profile (GemmProfile*)
+  double* d_modmem = nullptr;    // module arrays
+  int64_t modmem_len = 0;
+  // maps
+  int *d_lam_b0 = nullptr, *d_lam_b1 = nullptr, *d_lam_group = nullptr;
+  signed char *d_lam_s0 = nullptr, *d_lam_s1 = nullptr;
+  int *d_group_off = nullptr, *d_group_b = nullptr;
+  int *d_b2l_off = nullptr, *d_b2l_lam = nullptr;
+  signed char* d_b2l_sign = nullptr;
+  int* d_b_sub = nullptr;
+  int* d_c_glob = nullptr;
+  int* d_c_sub = nullptr;
+  int64_t* d_c_off = nullptr;    // [n_sub] c offsets
+  int *d_prim_off = nullptr, *d_prim_src = nullptr;
+  int64_t* d_load_src = nullptr;
+  int64_t *d_dof_copy_off = nullptr, *d_dof_copy = nullptr;
+  unsigned char* d_dirichlet = nullptr;
+  // per-b data
+  double* d_diagKb = nullptr;    // [n_b_total] diagonal stiffness of each b copy
+  double* d_w0 = nullptr;        // [n_lam] scaling weight of entry 0
+  double* d_w1 = nullptr;        // [n_lam] scaling weight of entry 1
+  // per-subdomain vectors
+  double* d_floc = nullptr;      // [n_sub * n_loc_dofs] local loads
+  double* d_h = nullptr;         // [sum n_i] L^{-1} f_i per subdomain
+  double* d_t = nullptr;         // [sum n_i] recovery work
+  int64_t* d_ioff = nullptr;     // [n_sub + 1] offsets of per-subdomain i-vectors
+  std::vector<int64_t> h_ioff;
+  double* d_ft = nullptr;        // [n_b_total + n_c_total] condensed loads f~ (b part, then c part)
+  int64_t n_c_total = 0;
+  // coarse
+  double* d_Kbar = nullptr;      // [n_coarse^2]
+  double* d_Kbar_L = nullptr;    // [n_coarse^2] inverse Cholesky factor (work)
+  double* d_Kbar_inv = nullptr;  // [n_coarse^2] explicit inverse
+  double* d_fbar = nullptr;      // [n_primal]
+  int n_coarse = 0;
+  double* d_G = nullptr;         // TFETI: dense G [n_coarse x n_lam]
+  double* d_e = nullptr;         // TFETI: e = -R^T f
+  double* d_alpha = nullptr;     // TFETI: rigid-body amplitudes
+  double *d_ct1 = nullptr, *d_ct2 = nullptr;   // [n_coarse x blk] projector work
+  // dual right-hand side and solution
+  double* d_d = nullptr;         // [n_lam]
+  double* d_lam0 = nullptr;      // [n_lam]
+  double* d_lam = nullptr;       // [n_lam]
+  double* d_uloc = nullptr;      // [n_sub * n_loc_dofs]
+  double* d_uglob = nullptr;     // [n_dofs]
+  int have_solution = 0;
+  // scratch
+  double* d_scalar = nullptr;    // small device scalars
+  int* d_status = nullptr;       // device status word
+  int* d_kdev = nullptr;         // rank from the rank-revealing factorization
+  double* d_red = nullptr;       // reduction partials (>= 1024)
+  // block buffers for the dual operator
+  int blk_cap = 0;
+  double *d_Xb = nullptr, *d_Yb = nullptr, *d_Cb = nullptr, *d_Vraw = nullptr, *d_V = nullptr, *d_Vc = nullptr;
+  double *d_pb0 = nullptr, *d_pb1 = nullptr;   // [n_b_total] vectors
+  // GEMM descriptors (device)
+  GemmDesc *d_gemm_F = nullptr, *d_gemm_FrcT = nullptr, *d_gemm_Frc = nullptr;
+  GemmDesc *d_gemm_schur = nullptr, *d_gemm_frcmake = nullptr, *d_gemm_kbmake = nullptr;
+  DenseDesc *d_dense_mod = nullptr, *d_dense_coarse = nullptr;
+  // Krylov buffers
+  int kr_cap = 0;
+  double *d_r = nullptr, *d_z = nullptr, *d_lamt = nullptr, *d_Wb = nullptr, *d_Qb = nullptr, *d_Wn = nullptr;
+  double *d_Delta = nullptr, *d_T = nullptr, *d_gamma = nullptr, *d_rrwork = nullptr, *d_split = nullptr;
+  int64_t split_cap = 0;
+  std::vector<double*> hist_W, hist_Q;
+  std::vector<int> hist_k;
+  feti_stats last{};
+};
+
+// error helpers
+#define FETI_CUDA_TRY(ctx, expr)                                                     \
+  do {                                                                               \
+    cudaError_t _e = (expr);                                                         \
+    if (_e != cudaSuccess) {                                                         \
+      (ctx)->err = std::string(#expr) + ": " + cudaGetErrorString(_e);              \
+      return FETI_ECUDA;                                                             \
+    }                                                                                \
+  } while (0)
+
+}  // namespace feti

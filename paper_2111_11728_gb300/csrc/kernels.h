@@ -1,0 +1,130 @@
+// Launchers of the device kernels (one namespace, several translation units).
+#pragma once
+
+#include <cstdint>
+
+#include <cuda_runtime.h>
+
+#include "feti_internal.h"
+
+namespace feti {
+
+// Instrumentation: a process-wide count of kernel launches, and an optional
+// CUDA-event profile of the FP64 GEMM launches (algorithmic flops, time).
+void note_launches(int n);
+int64_t launches();
+struct GemmProfile;
+void set_gemm_profile(GemmProfile* p);
+GemmProfile* new_gemm_profile();
+void finish_gemm_profile(GemmProfile* p, double* flops, double* ms, int64_t* count);
+
+// C = alpha * A B + beta * C with element (i,k) of A at A[i*ars + k*acs],
+// (k,j) of B at B[k*brs + j*bcs] and (i,j) of C at C[i*crs + j*ccs].
+struct GemmDesc {
+  const double* A;
+  const double* B;
+  double* C;
+  int M, N, K;
+  int pad;
+  int64_t ars, acs, brs, bcs, crs, ccs;
+};
+
+// Batched FP64 GEMM over n_batch descriptors living in device memory.
+// n_override > 0 replaces every descriptor's N.  beta == 0 never reads C.
+// alg_flops: the product's algorithmic flop count (for the profile only).
+cudaError_t dgemm_batched(const GemmDesc* d_desc, int n_batch, int max_m, int max_n,
+                          int n_override, double alpha, double beta, cudaStream_t st, double alg_flops = 0.0);
+
+// One FP64 GEMM with a deterministic split over K: partial tiles go to
+// `work` ([splits][M][N]) and are summed in a fixed order.
+// alg_flops < 0 means 2 M N K.
+cudaError_t dgemm_split(const GemmDesc& d, int splits, double* work, double alpha, double beta,
+                        cudaStream_t st, double alg_flops = -1.0);
+
+// Chooses a split count that fills the GPU for an M x N x K product.
+int split_for(int M, int N, int K);
+
+// ---- assembly (fem.cu) --------------------------------------------------------
+void element_stiffness_host(int dim, double nu, double* k0);
+cudaError_t launch_moduli(const Ctx& c, double* E, cudaStream_t st);
+cudaError_t launch_assemble_with(const Ctx& c, const double* E, cudaStream_t st);
+cudaError_t launch_gather_diag_b(const Ctx& c, cudaStream_t st);
+cudaError_t launch_scaling_weights(const Ctx& c, int kind, cudaStream_t st);
+cudaError_t launch_load_gather(const Ctx& c, cudaStream_t st);
+cudaError_t launch_gather_u(const Ctx& c, cudaStream_t st);
+cudaError_t launch_grad(const Ctx& c, double* out, cudaStream_t st);
+
+// ---- factorization (factor.cu) ------------------------------------------------
+cudaError_t launch_band_chol(const Ctx& c, cudaStream_t st);
+cudaError_t launch_band_fwd_multi(const Ctx& c, cudaStream_t st);
+// Dense SPD matrices listed as (pointer, n, ld) triples in device memory:
+// Cholesky in place (lower), then explicit inverse into `out` via L^{-T} L^{-1}.
+// With n_full > n the Cholesky eliminates only the leading n columns of the
+// n_full x n_full matrix: the trailing block is left holding the Schur
+// complement of the leading block (lower triangle), rows n.. of the first n
+// columns hold L_21.
+struct DenseDesc {
+  double* A;      // n_full x n_full row-major with leading dimension ld (overwritten by L)
+  double* Linv;   // n x n row-major scratch for L^{-1} of the leading block
+  double* out;    // n x n row-major result (leading block)^{-1}
+  int n, ld;
+  int tag;        // reported in the status word on failure
+  int n_full;     // 0 or n: plain Cholesky of the n x n matrix
+};
+cudaError_t dense_spd_inverse(const DenseDesc* d_desc, const DenseDesc* h_desc, int count, int* d_status,
+                              cudaStream_t st);
+// 0: W = S (the whole b+c Schur complement); 1: Kb = symmetrised trailing block of W
+cudaError_t launch_copy_block(const Ctx& c, int which, cudaStream_t st);
+cudaError_t launch_coarse_assemble_impl(const Ctx& c, const int* d_c_sub, const int64_t* d_c_off, double* K,
+                                        cudaStream_t st);
+cudaError_t launch_band_fwd_single(const Ctx& c, cudaStream_t st);   // h = L^{-1} f_i
+cudaError_t launch_condense_load(const Ctx& c, cudaStream_t st);     // f~ = f_bc - Y^T h
+
+// ---- dual operator pieces (dual.cu) -------------------------------------------
+// Xb[b + j*nbt] = sum over the rows l of b of sign * X[l + j*ldx]  (B^T X in b space)
+cudaError_t gather_lam_to_b(const Ctx& c, const double* X, int64_t ldx, int m, double* Xb, cudaStream_t st);
+// Y[l + j*ldy] = sum over the entries (b, sign) of row l of sign * Yb[b + j*nbt]  (B Yb)
+cudaError_t scatter_b_to_lam(const Ctx& c, const double* Yb, int m, double* Y, int64_t ldy, cudaStream_t st);
+// Y_b(s) = F_s X_b(s) for every subdomain (batched over subdomains)
+cudaError_t apply_local_F(Ctx& c, const double* Xb, double* Yb, int m, double beta, cudaStream_t st);
+// Vraw[g + j*np] = sum over corner copies of (F_rc,s^T X_b(s))[k, j]
+cudaError_t corner_reduce(Ctx& c, const double* Xb, int m, double* Cb, double* Vraw, cudaStream_t st);
+// out[g] = sum over the corner copies of g of src[c_off(s) + k]  (B_c^T applied to a c-space vector)
+cudaError_t corner_gather_vec(const Ctx& c, const double* src, double* out, cudaStream_t st);
+// Yb(s) += F_rc,s V[c_glob(s), :]
+cudaError_t corner_expand(Ctx& c, const double* V, int m, double* Vc, double* Yb, cudaStream_t st);
+// weighted gather / preconditioner scatter
+cudaError_t precond_apply(Ctx& c, const double* r, double* Z, int64_t ldz, double* z, cudaStream_t st);
+cudaError_t batched_gemv_F(Ctx& c, const double* xb, double* yb, cudaStream_t st);   // y_b = F_s x_b
+// y_b = A_s x_b (+ beta y_b), A_s = F_s (which 0) or S_bb (which 1)
+cudaError_t batched_gemv(const Ctx& c, int which, const double* xb, double* yb, double beta, cudaStream_t st);
+
+// ---- Krylov helpers (krylov.cu) ------------------------------------------------
+// Rank-revealing pivoted Cholesky of Delta (m x m, column-major ld): writes
+// T (m x k, column-major ld m) = N^T [L~^{-T}; 0] and k into *d_k.
+cudaError_t rr_cholesky(const double* Delta, int m, int ld, double rr_tol, double* work, double* T,
+                        int* d_k, cudaStream_t st);
+// lam_t += W g ; then r -= Q g, or qout = Q g when qout is not null
+// (W, Q column-major n x k with leading dimension ld)
+cudaError_t step_update(const double* W, const double* Q, int64_t ld, int64_t n, int k, const double* g,
+                        double* lam_t, double* r, double* qout, cudaStream_t st);
+// out[0] = x . y (deterministic two-pass reduction; work has >= 1024 doubles)
+cudaError_t dot(const double* x, const double* y, int64_t n, double* work, double* out, cudaStream_t st);
+// y = a*x + b*y
+cudaError_t axpby(int64_t n, double a, const double* x, double b, double* y, cudaStream_t st);
+// out[j] = W[:, j] . r for j < k
+cudaError_t gemv_t(const double* W, int64_t ld, int64_t n, int k, const double* r, double* out, cudaStream_t st);
+// y = A x (+ beta y), A row-major n x n with leading dimension ld
+cudaError_t gemv_dense(const double* A, int n, int ld, const double* x, double* y, double beta, cudaStream_t st);
+
+// ---- recovery (recover.cu) ------------------------------------------------------
+cudaError_t recover_fetidp(Ctx& c, const double* lam, cudaStream_t st);
+// TFETI: u^s = K^#(f^s - B^sT lambda) + R^s alpha_s
+cudaError_t recover_tfeti(Ctx& c, const double* lam, const double* alpha, cudaStream_t st);
+
+// ---- TFETI (tfeti.cu) -------------------------------------------------------------
+cudaError_t tfeti_add_rrt(const Ctx& c, cudaStream_t st);                 // W += Rhat Rhat^T per module
+cudaError_t tfeti_build_G(const Ctx& c, double* G, cudaStream_t st);      // dense G [n_coarse x n_lam]
+cudaError_t tfeti_build_e(const Ctx& c, double* e, cudaStream_t st);      // e = -R^T f
+
+}  // namespace feti

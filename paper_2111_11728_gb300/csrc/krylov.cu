@@ -1,0 +1,268 @@
+// Krylov helpers for Algorithm 1 (Section 3.3): the rank-revealing pivoted
+// Cholesky of the Gram matrix Delta = Q^T W with the F-orthonormalising
+// transform it implies, and the vector kernels of the step (all FP64, all
+// reductions in a fixed order so that runs are bit-reproducible).
+#include <algorithm>
+
+#include "kernels.h"
+
+namespace feti {
+
+namespace {
+
+constexpr double EPS2 = 4.930380657631324e-32;   // (2^-52)^2
+
+// Single CTA.  work holds 2*m*m + m doubles.  Pivot rule: the largest ratio of
+// the remaining Schur-complement diagonal to the column's initial diagonal,
+// exact ties to the lowest original column; stop when it is <= rr_tol.
+// Output T (column-major, ld m, k columns) = N^T [L~^{-T}; 0] and *d_k = k.
+__global__ void __launch_bounds__(1024) k_rr_chol(const double* __restrict__ Delta, int m, int ld, double rr_tol,
+                                                  double* __restrict__ work, double* __restrict__ T,
+                                                  int* __restrict__ d_k) {
+  double* A = work;              // m x m row-major
+  double* L = work + (int64_t)m * m;
+  double* d0 = L + (int64_t)m * m;
+  __shared__ int perm[1024];
+  __shared__ unsigned char alive[1024];
+  __shared__ double rv[32];
+  __shared__ int rp[32], rpos[32];
+  __shared__ int s_bt, s_k;
+  __shared__ double s_best;
+  const int tid = threadIdx.x, nt = blockDim.x;
+  const int lane = tid & 31, wid = tid >> 5, nw = nt >> 5;
+
+  for (int64_t e = tid; e < (int64_t)m * m; e += nt) {
+    const int i = (int)(e / m), j = (int)(e % m);
+    A[e] = 0.5 * (Delta[i + (int64_t)j * ld] + Delta[j + (int64_t)i * ld]);
+    L[e] = 0.0;
+  }
+  __syncthreads();
+  double mx = 0.0;
+  for (int t = tid; t < m; t += nt) {
+    perm[t] = t;
+    d0[t] = A[(int64_t)t * m + t];
+    mx = fmax(mx, d0[t]);
+  }
+  for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+  if (lane == 0) rv[wid] = mx;
+  __syncthreads();
+  if (tid == 0) {
+    double v = 0.0;
+    for (int w = 0; w < nw; ++w) v = fmax(v, rv[w]);
+    s_best = v;
+    s_k = 0;
+  }
+  __syncthreads();
+  const double dmax = s_best;
+  for (int t = tid; t < m; t += nt) alive[t] = (dmax > 0.0 && d0[t] > EPS2 * dmax) ? 1 : 0;
+  __syncthreads();
+
+  for (int j = 0; j < m; ++j) {
+    // --- pivot search -------------------------------------------------------
+    double bv = -1.0;
+    int bp = 0x7fffffff, bpos = -1;
+    for (int t = j + tid; t < m; t += nt) {
+      const int pt = perm[t];
+      if (!alive[pt]) continue;
+      const double ratio = A[(int64_t)t * m + t] / d0[pt];
+      if (ratio > bv || (ratio == bv && pt < bp)) { bv = ratio; bp = pt; bpos = t; }
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+      const double ov = __shfl_xor_sync(0xffffffffu, bv, o);
+      const int op = __shfl_xor_sync(0xffffffffu, bp, o);
+      const int opos = __shfl_xor_sync(0xffffffffu, bpos, o);
+      if (ov > bv || (ov == bv && op < bp)) { bv = ov; bp = op; bpos = opos; }
+    }
+    if (lane == 0) { rv[wid] = bv; rp[wid] = bp; rpos[wid] = bpos; }
+    __syncthreads();
+    if (tid == 0) {
+      double v = -1.0;
+      int p = 0x7fffffff, pos = -1;
+      for (int w = 0; w < nw; ++w)
+        if (rv[w] > v || (rv[w] == v && rp[w] < p)) { v = rv[w]; p = rp[w]; pos = rpos[w]; }
+      s_best = v;
+      s_bt = pos;
+    }
+    __syncthreads();
+    if (s_bt < 0 || !(s_best > rr_tol)) break;
+    const int bt = s_bt;
+    // --- symmetric swap of positions j and bt ---------------------------------
+    if (bt != j) {
+      for (int t = tid; t < m; t += nt) {
+        const double a = A[(int64_t)j * m + t];
+        A[(int64_t)j * m + t] = A[(int64_t)bt * m + t];
+        A[(int64_t)bt * m + t] = a;
+      }
+      __syncthreads();
+      for (int t = tid; t < m; t += nt) {
+        const double a = A[(int64_t)t * m + j];
+        A[(int64_t)t * m + j] = A[(int64_t)t * m + bt];
+        A[(int64_t)t * m + bt] = a;
+      }
+      for (int t = tid; t < j; t += nt) {
+        const double a = L[(int64_t)j * m + t];
+        L[(int64_t)j * m + t] = L[(int64_t)bt * m + t];
+        L[(int64_t)bt * m + t] = a;
+      }
+      if (tid == 0) { const int p = perm[j]; perm[j] = perm[bt]; perm[bt] = p; }
+      __syncthreads();
+    }
+    // --- column j of L and the trailing update --------------------------------
+    const double piv = sqrt(A[(int64_t)j * m + j]);
+    const double rpiv = 1.0 / piv;
+    for (int t = j + tid; t < m; t += nt) L[(int64_t)t * m + j] = t == j ? piv : A[(int64_t)t * m + j] * rpiv;
+    __syncthreads();
+    const int len = m - 1 - j;
+    for (int64_t e = tid; e < (int64_t)len * len; e += nt) {
+      const int a = j + 1 + (int)(e / len), b = j + 1 + (int)(e % len);
+      A[(int64_t)a * m + b] = fma(-L[(int64_t)a * m + j], L[(int64_t)b * m + j], A[(int64_t)a * m + b]);
+    }
+    if (tid == 0) s_k = j + 1;
+    __syncthreads();
+  }
+  const int k = s_k;
+  // --- Linv = L~^{-1} (k x k, row-major, ld m) into A; one thread per column ----
+  for (int c = tid; c < k; c += nt) {
+    for (int i = 0; i < c; ++i) A[(int64_t)i * m + c] = 0.0;
+    A[(int64_t)c * m + c] = 1.0 / L[(int64_t)c * m + c];
+    for (int i = c + 1; i < k; ++i) {
+      double acc = 0.0;
+      for (int q = c; q < i; ++q) acc = fma(L[(int64_t)i * m + q], A[(int64_t)q * m + c], acc);
+      A[(int64_t)i * m + c] = -acc / L[(int64_t)i * m + i];
+    }
+  }
+  __syncthreads();
+  // --- T[perm[j] + i*m] = Linv[i][j] for j < k; other rows zero ---------------
+  for (int64_t e = tid; e < (int64_t)m * k; e += nt) T[e] = 0.0;
+  __syncthreads();
+  for (int64_t e = tid; e < (int64_t)k * k; e += nt) {
+    const int i = (int)(e / k), jj = (int)(e % k);
+    T[perm[jj] + (int64_t)i * m] = A[(int64_t)i * m + jj];
+  }
+  if (tid == 0) *d_k = k;
+}
+
+// out[j] = W[:, j] . r  (one block per column, fixed-order reduction)
+__global__ void k_gemv_t(const double* __restrict__ W, int64_t ld, int64_t n, const double* __restrict__ r,
+                         double* __restrict__ out) {
+  const int j = blockIdx.x;
+  const double* w = W + (int64_t)j * ld;
+  double acc = 0.0;
+  for (int64_t l = threadIdx.x; l < n; l += blockDim.x) acc = fma(w[l], r[l], acc);
+  __shared__ double red[32];
+  for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double s = 0.0;
+    for (int w2 = 0; w2 < (int)(blockDim.x >> 5); ++w2) s += red[w2];
+    out[j] = s;
+  }
+}
+
+__global__ void k_step(const double* __restrict__ W, const double* __restrict__ Q, int64_t ld, int64_t n, int k,
+                       const double* __restrict__ g, double* __restrict__ lam_t, double* __restrict__ r,
+                       double* __restrict__ qout) {
+  __shared__ double gs[1024];
+  for (int t = threadIdx.x; t < k; t += blockDim.x) gs[t] = g[t];
+  __syncthreads();
+  const int64_t l = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (l >= n) return;
+  double aw = 0.0, aq = 0.0;
+  for (int j = 0; j < k; ++j) {
+    aw = fma(W[l + (int64_t)j * ld], gs[j], aw);
+    aq = fma(Q[l + (int64_t)j * ld], gs[j], aq);
+  }
+  lam_t[l] += aw;
+  if (qout) qout[l] = aq;
+  else r[l] -= aq;
+}
+
+__global__ void k_dot_partial(const double* __restrict__ x, const double* __restrict__ y, int64_t n,
+                              double* __restrict__ part) {
+  double acc = 0.0;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    acc = fma(x[i], y[i], acc);
+  __shared__ double red[32];
+  for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double s = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) s += red[w];
+    part[blockIdx.x] = s;
+  }
+}
+
+__global__ void k_sum(const double* __restrict__ part, int n, double* __restrict__ out) {
+  if (threadIdx.x == 0 && blockIdx.x == 0) {
+    double s = 0.0;
+    for (int i = 0; i < n; ++i) s += part[i];
+    *out = s;
+  }
+}
+
+__global__ void k_axpby(int64_t n, double a, const double* __restrict__ x, double b, double* __restrict__ y) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i < n) y[i] = fma(a, x[i], b * y[i]);
+}
+
+__global__ void k_gemv_dense(const double* __restrict__ A, int n, int ld, const double* __restrict__ x,
+                             double* __restrict__ y, double beta) {
+  const int row = blockIdx.x * (blockDim.x / 32) + threadIdx.x / 32;
+  const int lane = threadIdx.x & 31;
+  if (row >= n) return;
+  const double* a = A + (int64_t)row * ld;
+  double acc = 0.0;
+  for (int k = lane; k < n; k += 32) acc = fma(a[k], x[k], acc);
+  for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+  if (lane == 0) y[row] = beta != 0.0 ? fma(beta, y[row], acc) : acc;
+}
+
+}  // namespace
+
+cudaError_t rr_cholesky(const double* Delta, int m, int ld, double rr_tol, double* work, double* T, int* d_k,
+                        cudaStream_t st) {
+  if (m > 1024) return cudaErrorInvalidValue;
+  k_rr_chol<<<1, 1024, 0, st>>>(Delta, m, ld, rr_tol, work, T, d_k);
+  note_launches(1);
+  return cudaGetLastError();
+}
+
+cudaError_t gemv_t(const double* W, int64_t ld, int64_t n, int k, const double* r, double* out, cudaStream_t st) {
+  if (k <= 0) return cudaSuccess;
+  k_gemv_t<<<k, 256, 0, st>>>(W, ld, n, r, out);
+  note_launches(1);
+  return cudaGetLastError();
+}
+
+cudaError_t step_update(const double* W, const double* Q, int64_t ld, int64_t n, int k, const double* g,
+                        double* lam_t, double* r, double* qout, cudaStream_t st) {
+  if (k > 1024) return cudaErrorInvalidValue;
+  k_step<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(W, Q, ld, n, k, g, lam_t, r, qout);
+  note_launches(1);
+  return cudaGetLastError();
+}
+
+cudaError_t dot(const double* x, const double* y, int64_t n, double* work, double* out, cudaStream_t st) {
+  const int blocks = 256;
+  k_dot_partial<<<blocks, 256, 0, st>>>(x, y, n, work);
+  note_launches(1);
+  k_sum<<<1, 32, 0, st>>>(work, blocks, out);
+  note_launches(1);
+  return cudaGetLastError();
+}
+
+cudaError_t axpby(int64_t n, double a, const double* x, double b, double* y, cudaStream_t st) {
+  k_axpby<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(n, a, x, b, y);
+  note_launches(1);
+  return cudaGetLastError();
+}
+
+cudaError_t gemv_dense(const double* A, int n, int ld, const double* x, double* y, double beta, cudaStream_t st) {
+  k_gemv_dense<<<(n + 7) / 8, 256, 0, st>>>(A, n, ld, x, y, beta);
+  note_launches(1);
+  return cudaGetLastError();
+}
+
+}  // namespace feti

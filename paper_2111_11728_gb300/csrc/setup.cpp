@@ -1,0 +1,419 @@
+// Host-side tearing of a regular tile mesh into subdomains and construction of
+// every index map the device kernels use.
+//
+// * TFETI (Section 2.1, Eqs. 4-5): every subdomain keeps all of its DOFs; a
+//   fixed DOF gets one single-entry row per subdomain copy (the Dirichlet part
+//   of B u = c); a free DOF shared by several subdomains gets one row
+//   u^a - u^b = 0 per pair of copies (pair-wise, redundant at cross points,
+//   Section 3.1).
+// * FETI-DP (Section 2.2, Eqs. 8-10): fixed DOFs are eliminated, the DOFs at
+//   the vertices of the tile grid are primal (corner nodes of a regular
+//   partition), and the remaining shared DOFs get pair-wise rows of B_r.
+//
+// Subdomains whose local DOF classification is identical share a "type";
+// subdomains of one type whose element densities are also identical share a
+// "module" (one factorization, Section 1: repeated modules are reused).
+#include <algorithm>
+#include <cstring>
+#include <map>
+#include <string>
+#include <unordered_map>
+
+#include "feti_internal.h"
+
+namespace feti {
+
+namespace {
+
+struct NodeOwners {
+  int n = 0;
+  int sub[8];
+  int lnode[8];
+  int mask[8];   // per owner: bitmask of the relative offsets of the *other* owners
+};
+
+inline int sub_index(const HostProblem& hp, const int t[3]) {
+  return t[0] + hp.tiles[0] * (t[1] + hp.tiles[1] * t[2]);
+}
+
+inline int64_t gnode_index(const HostProblem& hp, const int g[3]) {
+  return g[0] + (int64_t)hp.nnod[0] * (g[1] + (int64_t)hp.nnod[1] * g[2]);
+}
+
+inline int lnode_index(const HostProblem& hp, const int c[3]) {
+  return c[0] + hp.lnod[0] * (c[1] + hp.lnod[1] * c[2]);
+}
+
+// All subdomains whose closed tile contains global node g, sorted by index.
+void owners_of(const HostProblem& hp, const int g[3], NodeOwners& o) {
+  int cand[3][2], nc[3];
+  for (int a = 0; a < 3; ++a) {
+    nc[a] = 0;
+    if (a >= hp.dim) { cand[a][0] = 0; nc[a] = 1; continue; }
+    int e = hp.elems[a];
+    int t = g[a] / e;
+    int r = g[a] % e;
+    if (r == 0) {
+      if (t > 0) cand[a][nc[a]++] = t - 1;
+      if (t < hp.tiles[a]) cand[a][nc[a]++] = t;
+    } else {
+      cand[a][nc[a]++] = t;
+    }
+  }
+  o.n = 0;
+  int tt[3];
+  for (int i = 0; i < nc[0]; ++i)
+    for (int j = 0; j < nc[1]; ++j)
+      for (int k = 0; k < nc[2]; ++k) {
+        tt[0] = cand[0][i]; tt[1] = cand[1][j]; tt[2] = cand[2][k];
+        int c[3] = {0, 0, 0};
+        for (int a = 0; a < hp.dim; ++a) c[a] = g[a] - tt[a] * hp.elems[a];
+        o.sub[o.n] = sub_index(hp, tt);
+        o.lnode[o.n] = lnode_index(hp, c);
+        o.n++;
+      }
+  // sort by subdomain (insertion sort, n <= 8)
+  for (int a = 1; a < o.n; ++a)
+    for (int b = a; b > 0 && o.sub[b] < o.sub[b - 1]; --b) {
+      std::swap(o.sub[b], o.sub[b - 1]);
+      std::swap(o.lnode[b], o.lnode[b - 1]);
+    }
+  // relative-offset masks
+  for (int a = 0; a < o.n; ++a) {
+    int ta[3] = {o.sub[a] % hp.tiles[0], (o.sub[a] / hp.tiles[0]) % hp.tiles[1],
+                 o.sub[a] / (hp.tiles[0] * hp.tiles[1])};
+    int m = 0;
+    for (int b = 0; b < o.n; ++b) {
+      if (b == a) continue;
+      int tb[3] = {o.sub[b] % hp.tiles[0], (o.sub[b] / hp.tiles[0]) % hp.tiles[1],
+                   o.sub[b] / (hp.tiles[0] * hp.tiles[1])};
+      int code = (tb[0] - ta[0] + 1) + 3 * (tb[1] - ta[1] + 1) + 9 * (tb[2] - ta[2] + 1);
+      m |= 1 << code;
+    }
+    o.mask[a] = m;
+  }
+}
+
+}  // namespace
+
+std::string build_host_problem(const feti_problem& prob, int method, int dedup,
+                               const double* rho_host, HostProblem& hp) {
+  hp = HostProblem();
+  if (prob.dim != 2 && prob.dim != 3) return "dim must be 2 or 3";
+  hp.dim = prob.dim;
+  hp.method = method;
+  for (int a = 0; a < 3; ++a) {
+    int t = a < hp.dim ? prob.tiles[a] : 1;
+    int e = a < hp.dim ? prob.elems[a] : 1;
+    if (t < 1 || e < 1) return "tiles and elems must be >= 1";
+    hp.tiles[a] = t;
+    hp.elems[a] = a < hp.dim ? e : 0;
+    hp.nel[a] = a < hp.dim ? t * e : 1;
+    hp.nnod[a] = a < hp.dim ? t * e + 1 : 1;
+    hp.lnod[a] = a < hp.dim ? e + 1 : 1;
+  }
+  if (hp.dim == 2) { hp.elems[2] = 0; }
+  hp.n_nodes = (int64_t)hp.nnod[0] * hp.nnod[1] * hp.nnod[2];
+  hp.n_elements = (int64_t)hp.nel[0] * hp.nel[1] * hp.nel[2];
+  hp.n_dofs = hp.n_nodes * hp.dim;
+  hp.n_sub = hp.tiles[0] * hp.tiles[1] * hp.tiles[2];
+  hp.n_loc_nodes = hp.lnod[0] * hp.lnod[1] * hp.lnod[2];
+  hp.n_loc_dofs = hp.n_loc_nodes * hp.dim;
+  hp.n_loc_elems = 1;
+  for (int a = 0; a < hp.dim; ++a) hp.n_loc_elems *= hp.elems[a];
+  hp.E0 = prob.E0; hp.Emin = prob.Emin; hp.nu = prob.nu; hp.p = prob.p;
+  if (!(hp.nu > -1.0 && hp.nu < 0.5)) return "nu must lie in (-1, 0.5)";
+  if (hp.n_sub < 2) return "at least two subdomains are required";
+  hp.dirichlet.assign(prob.dirichlet, prob.dirichlet + hp.n_dofs);
+  hp.n_rbm = method == FETI_TFETI ? (hp.dim == 2 ? 3 : 6) : 0;
+
+  const int dim = hp.dim;
+  const int nld = hp.n_loc_dofs;
+
+  // ---- classify local DOFs of every subdomain, group into types ----------------
+  std::map<std::vector<int>, int> type_of_key;
+  hp.sub_type.assign(hp.n_sub, -1);
+  std::vector<std::vector<int>> type_masks;   // per type: neighbour mask per local DOF
+  NodeOwners own;
+  for (int s = 0; s < hp.n_sub; ++s) {
+    int t[3] = {s % hp.tiles[0], (s / hp.tiles[0]) % hp.tiles[1], s / (hp.tiles[0] * hp.tiles[1])};
+    std::vector<int> key(2 * nld);
+    for (int ln = 0; ln < hp.n_loc_nodes; ++ln) {
+      int c[3];
+      local_node_coords(hp, ln, c);
+      int g[3] = {0, 0, 0};
+      bool vertex = true;
+      for (int a = 0; a < dim; ++a) {
+        g[a] = t[a] * hp.elems[a] + c[a];
+        if (c[a] != 0 && c[a] != hp.elems[a]) vertex = false;
+      }
+      owners_of(hp, g, own);
+      int me = 0;
+      for (int q = 0; q < own.n; ++q) if (own.sub[q] == s) me = q;
+      int64_t gn = gnode_index(hp, g);
+      for (int d = 0; d < dim; ++d) {
+        int ld = ln * dim + d;
+        bool fixed = hp.dirichlet[gn * dim + d] != 0;
+        int cls;
+        if (method == FETI_FETIDP) {
+          if (fixed) cls = CLS_X;
+          else if (vertex) cls = CLS_C;
+          else if (own.n > 1) cls = CLS_B;
+          else cls = CLS_I;
+        } else {
+          cls = (fixed || own.n > 1) ? CLS_B : CLS_I;
+        }
+        key[2 * ld] = cls;
+        key[2 * ld + 1] = own.mask[me];
+      }
+    }
+    auto it = type_of_key.find(key);
+    if (it == type_of_key.end()) {
+      int id = (int)hp.types.size();
+      type_of_key.emplace(key, id);
+      StructType T;
+      T.n_loc = nld;
+      T.cls.resize(nld);
+      T.idx.assign(nld, -1);
+      std::vector<int> masks(nld);
+      for (int ld = 0; ld < nld; ++ld) { T.cls[ld] = key[2 * ld]; masks[ld] = key[2 * ld + 1]; }
+      // i and c lists: lexicographic; b list: grouped by neighbour set, then lexicographic
+      std::vector<std::pair<int64_t, int>> bkeys;
+      for (int ld = 0; ld < nld; ++ld) {
+        if (T.cls[ld] == CLS_I) T.ilist.push_back(ld);
+        else if (T.cls[ld] == CLS_C) T.clist.push_back(ld);
+        else if (T.cls[ld] == CLS_B) bkeys.push_back({((int64_t)masks[ld] << 32) | ld, ld});
+      }
+      std::sort(bkeys.begin(), bkeys.end());
+      for (auto& kv : bkeys) T.blist.push_back(kv.second);
+      T.n_i = (int)T.ilist.size();
+      T.n_b = (int)T.blist.size();
+      T.n_c = (int)T.clist.size();
+      for (int k = 0; k < T.n_i; ++k) T.idx[T.ilist[k]] = k;
+      for (int k = 0; k < T.n_b; ++k) T.idx[T.blist[k]] = k;
+      for (int k = 0; k < T.n_c; ++k) T.idx[T.clist[k]] = k;
+      // half-bandwidth of K_ii in i-order (element-neighbour coupling)
+      int bw = 0;
+      for (int k = 0; k < T.n_i; ++k) {
+        int ld = T.ilist[k];
+        int ln = ld / dim;
+        int c[3];
+        local_node_coords(hp, ln, c);
+        for (int dz = (dim == 3 ? -1 : 0); dz <= (dim == 3 ? 1 : 0); ++dz)
+          for (int dy = -1; dy <= 1; ++dy)
+            for (int dx = -1; dx <= 1; ++dx) {
+              int cc[3] = {c[0] + dx, c[1] + dy, c[2] + dz};
+              bool ok = true;
+              for (int a = 0; a < dim; ++a) if (cc[a] < 0 || cc[a] > hp.elems[a]) ok = false;
+              if (!ok) continue;
+              int m = lnode_index(hp, cc);
+              for (int d2 = 0; d2 < dim; ++d2) {
+                int l2 = m * dim + d2;
+                if (T.cls[l2] != CLS_I) continue;
+                bw = std::max(bw, std::abs(T.idx[l2] - k));
+              }
+            }
+      }
+      T.bw = bw;
+      hp.types.push_back(std::move(T));
+      type_masks.push_back(std::move(masks));
+      hp.sub_type[s] = id;
+    } else {
+      hp.sub_type[s] = it->second;
+    }
+  }
+
+  // ---- modules (identical type + identical densities share one factorization) --
+  hp.sub_module.assign(hp.n_sub, -1);
+  std::unordered_map<std::string, int> mod_of_key;
+  std::vector<double> tile_rho(hp.n_loc_elems);
+  for (int s = 0; s < hp.n_sub; ++s) {
+    int id;
+    if (dedup && rho_host) {
+      int t[3] = {s % hp.tiles[0], (s / hp.tiles[0]) % hp.tiles[1], s / (hp.tiles[0] * hp.tiles[1])};
+      int k = 0;
+      int ez = dim == 3 ? hp.elems[2] : 1;
+      for (int z = 0; z < ez; ++z)
+        for (int y = 0; y < hp.elems[1]; ++y)
+          for (int x = 0; x < hp.elems[0]; ++x) {
+            int64_t gx = t[0] * hp.elems[0] + x, gy = t[1] * hp.elems[1] + y,
+                    gz = dim == 3 ? t[2] * hp.elems[2] + z : 0;
+            tile_rho[k++] = rho_host[gx + hp.nel[0] * (gy + (int64_t)hp.nel[1] * gz)];
+          }
+      std::string key((const char*)tile_rho.data(), tile_rho.size() * sizeof(double));
+      key.append((const char*)&hp.sub_type[s], sizeof(int));
+      auto it = mod_of_key.find(key);
+      if (it == mod_of_key.end()) {
+        id = (int)hp.module_rep.size();
+        mod_of_key.emplace(std::move(key), id);
+        hp.module_rep.push_back(s);
+        hp.module_type.push_back(hp.sub_type[s]);
+      } else {
+        id = it->second;
+      }
+    } else {
+      id = (int)hp.module_rep.size();
+      hp.module_rep.push_back(s);
+      hp.module_type.push_back(hp.sub_type[s]);
+    }
+    hp.sub_module[s] = id;
+  }
+
+  // ---- b space --------------------------------------------------------------
+  hp.b_off.assign(hp.n_sub + 1, 0);
+  for (int s = 0; s < hp.n_sub; ++s) hp.b_off[s + 1] = hp.b_off[s] + hp.types[hp.sub_type[s]].n_b;
+  hp.n_b_total = hp.b_off[hp.n_sub];
+  hp.b_sub.resize(hp.n_b_total);
+  for (int s = 0; s < hp.n_sub; ++s)
+    for (int64_t b = hp.b_off[s]; b < hp.b_off[s + 1]; ++b) hp.b_sub[b] = s;
+
+  auto global_b = [&](int q, int lnode, int d) -> int64_t {
+    const StructType& T = hp.types[hp.sub_type[q]];
+    int ld = lnode * dim + d;
+    if (T.cls[ld] != CLS_B) return -1;
+    return hp.b_off[q] + T.idx[ld];
+  };
+
+  // ---- multipliers ------------------------------------------------------------
+  hp.group_off.push_back(0);
+  for (int s = 0; s < hp.n_sub; ++s) {
+    const StructType& T = hp.types[hp.sub_type[s]];
+    int t[3] = {s % hp.tiles[0], (s / hp.tiles[0]) % hp.tiles[1], s / (hp.tiles[0] * hp.tiles[1])};
+    for (int k = 0; k < T.n_b; ++k) {
+      int ld = T.blist[k];
+      int ln = ld / dim, d = ld % dim;
+      int c[3];
+      local_node_coords(hp, ln, c);
+      int g[3] = {0, 0, 0};
+      for (int a = 0; a < dim; ++a) g[a] = t[a] * hp.elems[a] + c[a];
+      owners_of(hp, g, own);
+      int64_t gn = gnode_index(hp, g);
+      bool fixed = hp.dirichlet[gn * dim + d] != 0;
+      int64_t my_b = hp.b_off[s] + k;
+      if (method == FETI_TFETI && fixed) {
+        int grp = (int)hp.group_off.size() - 1;
+        hp.group_b.push_back((int)my_b);
+        hp.group_off.push_back((int)hp.group_b.size());
+        hp.lam_b0.push_back((int)my_b); hp.lam_s0.push_back(1);
+        hp.lam_b1.push_back(-1); hp.lam_s1.push_back(0);
+        hp.lam_group.push_back(grp);
+        continue;
+      }
+      if (own.sub[0] != s || own.n < 2) continue;   // rows are emitted by the lowest owner
+      int grp = (int)hp.group_off.size() - 1;
+      int64_t gb[8];
+      for (int q = 0; q < own.n; ++q) {
+        gb[q] = global_b(own.sub[q], own.lnode[q], d);
+        if (gb[q] < 0) return "internal error: shared DOF is not an interface DOF in every copy";
+        hp.group_b.push_back((int)gb[q]);
+      }
+      hp.group_off.push_back((int)hp.group_b.size());
+      for (int a = 0; a < own.n; ++a)
+        for (int b = a + 1; b < own.n; ++b) {
+          hp.lam_b0.push_back((int)gb[a]); hp.lam_s0.push_back(1);
+          hp.lam_b1.push_back((int)gb[b]); hp.lam_s1.push_back(-1);
+          hp.lam_group.push_back(grp);
+        }
+    }
+  }
+  hp.n_lam = (int64_t)hp.lam_b0.size();
+  if (hp.n_lam == 0) return "the problem has no interface multipliers";
+  // b -> lambda CSR
+  std::vector<int> cnt(hp.n_b_total + 1, 0);
+  for (int64_t l = 0; l < hp.n_lam; ++l) {
+    cnt[hp.lam_b0[l] + 1]++;
+    if (hp.lam_b1[l] >= 0) cnt[hp.lam_b1[l] + 1]++;
+  }
+  hp.b2l_off.assign(hp.n_b_total + 1, 0);
+  for (int64_t b = 0; b < hp.n_b_total; ++b) hp.b2l_off[b + 1] = hp.b2l_off[b] + cnt[b + 1];
+  hp.b2l_lam.resize(hp.b2l_off[hp.n_b_total]);
+  hp.b2l_sign.resize(hp.b2l_off[hp.n_b_total]);
+  std::vector<int> fill(hp.b2l_off.begin(), hp.b2l_off.end() - 1);
+  for (int64_t l = 0; l < hp.n_lam; ++l) {
+    int b0 = hp.lam_b0[l];
+    hp.b2l_lam[fill[b0]] = (int)l; hp.b2l_sign[fill[b0]] = hp.lam_s0[l]; fill[b0]++;
+    int b1 = hp.lam_b1[l];
+    if (b1 >= 0) { hp.b2l_lam[fill[b1]] = (int)l; hp.b2l_sign[fill[b1]] = hp.lam_s1[l]; fill[b1]++; }
+  }
+
+  // ---- primal corners (FETI-DP) ------------------------------------------------
+  hp.c_off.assign(hp.n_sub + 1, 0);
+  if (method == FETI_FETIDP) {
+    std::unordered_map<int64_t, int> prim;
+    // enumerate tile-grid vertices lexicographically
+    int nv[3] = {hp.tiles[0] + 1, hp.tiles[1] + 1, dim == 3 ? hp.tiles[2] + 1 : 1};
+    for (int vz = 0; vz < nv[2]; ++vz)
+      for (int vy = 0; vy < nv[1]; ++vy)
+        for (int vx = 0; vx < nv[0]; ++vx) {
+          int g[3] = {vx * hp.elems[0], vy * hp.elems[1], dim == 3 ? vz * hp.elems[2] : 0};
+          int64_t gn = gnode_index(hp, g);
+          for (int d = 0; d < dim; ++d)
+            if (!hp.dirichlet[gn * dim + d]) prim.emplace(gn * dim + d, hp.n_primal++);
+        }
+    for (int s = 0; s < hp.n_sub; ++s) hp.c_off[s + 1] = hp.c_off[s] + hp.types[hp.sub_type[s]].n_c;
+    hp.c_glob.resize(hp.c_off[hp.n_sub]);
+    std::vector<std::vector<int>> src(hp.n_primal);
+    for (int s = 0; s < hp.n_sub; ++s) {
+      const StructType& T = hp.types[hp.sub_type[s]];
+      int t[3] = {s % hp.tiles[0], (s / hp.tiles[0]) % hp.tiles[1], s / (hp.tiles[0] * hp.tiles[1])};
+      for (int k = 0; k < T.n_c; ++k) {
+        int ld = T.clist[k];
+        int c[3];
+        local_node_coords(hp, ld / dim, c);
+        int g[3] = {0, 0, 0};
+        for (int a = 0; a < dim; ++a) g[a] = t[a] * hp.elems[a] + c[a];
+        int64_t gd = gnode_index(hp, g) * dim + ld % dim;
+        int pidx = prim.at(gd);
+        hp.c_glob[hp.c_off[s] + k] = pidx;
+        src[pidx].push_back((int)(hp.c_off[s] + k));
+      }
+    }
+    hp.prim_off.assign(hp.n_primal + 1, 0);
+    for (int q = 0; q < hp.n_primal; ++q) {
+      hp.prim_off[q + 1] = hp.prim_off[q] + (int)src[q].size();
+      for (int v : src[q]) hp.prim_src.push_back(v);
+    }
+  }
+
+  // ---- loads (lowest owner takes a shared node's load) and output gather ---------
+  hp.load_src.assign((int64_t)hp.n_sub * nld, -1);
+  std::vector<int64_t> copies_cnt(hp.n_dofs + 1, 0);
+  for (int s = 0; s < hp.n_sub; ++s) {
+    const StructType& T = hp.types[hp.sub_type[s]];
+    int t[3] = {s % hp.tiles[0], (s / hp.tiles[0]) % hp.tiles[1], s / (hp.tiles[0] * hp.tiles[1])};
+    for (int ln = 0; ln < hp.n_loc_nodes; ++ln) {
+      int c[3];
+      local_node_coords(hp, ln, c);
+      int g[3] = {0, 0, 0};
+      bool lowest = true;
+      for (int a = 0; a < dim; ++a) {
+        g[a] = t[a] * hp.elems[a] + c[a];
+        if (c[a] == 0 && t[a] > 0) lowest = false;     // a lower-index tile also owns it
+      }
+      int64_t gn = gnode_index(hp, g);
+      for (int d = 0; d < dim; ++d) {
+        int ld = ln * dim + d;
+        copies_cnt[gn * dim + d + 1]++;
+        if (lowest && T.cls[ld] != CLS_X) hp.load_src[(int64_t)s * nld + ld] = gn * dim + d;
+      }
+    }
+  }
+  hp.dof_copy_off.assign(hp.n_dofs + 1, 0);
+  for (int64_t q = 0; q < hp.n_dofs; ++q) hp.dof_copy_off[q + 1] = hp.dof_copy_off[q] + copies_cnt[q + 1];
+  hp.dof_copy.resize(hp.dof_copy_off[hp.n_dofs]);
+  std::vector<int64_t> pos(hp.dof_copy_off.begin(), hp.dof_copy_off.end() - 1);
+  for (int s = 0; s < hp.n_sub; ++s) {
+    int t[3] = {s % hp.tiles[0], (s / hp.tiles[0]) % hp.tiles[1], s / (hp.tiles[0] * hp.tiles[1])};
+    for (int ln = 0; ln < hp.n_loc_nodes; ++ln) {
+      int c[3];
+      local_node_coords(hp, ln, c);
+      int g[3] = {0, 0, 0};
+      for (int a = 0; a < dim; ++a) g[a] = t[a] * hp.elems[a] + c[a];
+      int64_t gn = gnode_index(hp, g);
+      for (int d = 0; d < dim; ++d) hp.dof_copy[pos[gn * dim + d]++] = (int64_t)s * nld + ln * dim + d;
+    }
+  }
+  return "";
+}
+
+}  // namespace feti
