@@ -157,6 +157,20 @@ feti_status feti_apply_dual(feti_ctx* ctx, const double* X, int ldx, int m, doub
  * ldz >= n_lambda (may be NULL); z: DEVICE [n_lambda] (may be NULL). */
 feti_status feti_apply_precond(feti_ctx* ctx, const double* r, double* Z, int ldz, double* z);
 
+/* Allocation-free variant of feti_apply_precond (the paper has no
+ * counterpart: this is a deployment aid).  Same arguments, same result.
+ * It is meant for callers that cannot let the library call cudaMalloc while
+ * they run -- e.g. code under a fixed device-memory budget or one that must
+ * not bypass its own device allocator.  The two interface-space work vectors
+ * live in a static device array of 4 MiB that every GPU loading the library
+ * holds until the process exits; problems whose interface space has more
+ * than 262144 entries (FETI_Q_N_B_TOTAL) are rejected with FETI_EINVAL.
+ * All calls share that array: calls whose kernels overlap on the GPU race,
+ * so serialise them.  The first call on a device looks up the array's device
+ * address; make that first call before any stream capture.  No CUDA or other
+ * allocation is made by this call. */
+feti_status feti_apply_precond_noalloc(feti_ctx* ctx, const double* r, double* Z, int ldz, double* z);
+
 /* Integer facts about the set-up problem; key is one of FETI_Q_*. */
 enum {
   FETI_Q_N_LAMBDA = 0, FETI_Q_N_SUBDOMAINS = 1, FETI_Q_N_PRIMAL = 2, FETI_Q_N_MODULES = 3,

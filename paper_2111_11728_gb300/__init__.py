@@ -30,7 +30,7 @@ STATUS_NAMES = {0: "FETI_OK", 1: "FETI_EINVAL", 2: "FETI_ENOMEM", 3: "FETI_ESTAT
 EXPORTS = [
     "feti_options_default", "feti_create", "feti_setup_subdomains", "feti_set_density", "feti_factorize",
     "feti_solve_dual", "feti_recover_displacements", "feti_compliance_grad", "feti_apply_dual",
-    "feti_apply_precond", "feti_query", "feti_profile_begin", "feti_profile_end", "feti_lambda_layout", "feti_local_blocks", "feti_last_error",
+    "feti_apply_precond", "feti_apply_precond_noalloc", "feti_query", "feti_profile_begin", "feti_profile_end", "feti_lambda_layout", "feti_local_blocks", "feti_last_error",
     "feti_destroy",
 ]
 
@@ -75,6 +75,7 @@ def lib():
             "feti_compliance_grad": ([vp, vp, i], i),
             "feti_apply_dual": ([vp, vp, i, i, vp, i], i),
             "feti_apply_precond": ([vp, vp, vp, i, vp], i),
+            "feti_apply_precond_noalloc": ([vp, vp, vp, i, vp], i),
             "feti_query": ([vp, i, ctypes.POINTER(i64)], i),
             "feti_profile_begin": ([vp], i),
             "feti_profile_end": ([vp, ctypes.POINTER(d), ctypes.POINTER(d), ctypes.POINTER(i64)], i),
@@ -188,6 +189,10 @@ def feti_apply_dual(ctx, X, ldx, m, Y, ldy):
 
 def feti_apply_precond(ctx, r, Z, ldz, z):
     return _check(ctx, lib().feti_apply_precond(ctx, _ptr(r), _ptr(Z), int(ldz), _ptr(z)))
+
+
+def feti_apply_precond_noalloc(ctx, r, Z, ldz, z):
+    return _check(ctx, lib().feti_apply_precond_noalloc(ctx, _ptr(r), _ptr(Z), int(ldz), _ptr(z)))
 
 
 def feti_query(ctx, key):

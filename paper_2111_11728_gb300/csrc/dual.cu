@@ -215,4 +215,26 @@ cudaError_t precond_apply(Ctx& c, const double* r, double* Z, int64_t ldz, doubl
   return cudaGetLastError();
 }
 
+// The block preconditioner with caller-provided work vectors rb, zb
+// ([n_b_total] each, fully overwritten); used by the allocation-free entry point.
+cudaError_t precond_apply_scratch(const Ctx& c, const double* r, double* Z, int64_t ldz, double* z, double* rb,
+                                  double* zb, cudaStream_t st) {
+  const int64_t nbt = c.hp.n_b_total, nl = c.hp.n_lam;
+  k_gather_weighted<<<(unsigned)((nbt + 255) / 256), 256, 0, st>>>(nbt, c.d_b2l_off, c.d_b2l_lam, c.d_b2l_sign,
+                                                                   c.d_lam_b0, c.d_w0, c.d_w1, r, rb);
+  note_launches(1);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  e = batched_gemv(c, 1, rb, zb, 0.0, st);
+  if (e != cudaSuccess) return e;
+  if (Z) {
+    e = cudaMemsetAsync(Z, 0, sizeof(double) * (size_t)ldz * c.hp.n_sub, st);
+    if (e != cudaSuccess) return e;
+  }
+  k_prec_scatter<<<(unsigned)((nl + 255) / 256), 256, 0, st>>>(nl, c.d_lam_b0, c.d_lam_s0, c.d_lam_b1, c.d_lam_s1,
+                                                               c.d_w0, c.d_w1, c.d_b_sub, zb, Z, ldz, z);
+  note_launches(1);
+  return cudaGetLastError();
+}
+
 }  // namespace feti

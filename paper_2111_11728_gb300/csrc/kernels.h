@@ -95,6 +95,8 @@ cudaError_t corner_gather_vec(const Ctx& c, const double* src, double* out, cuda
 cudaError_t corner_expand(Ctx& c, const double* V, int m, double* Vc, double* Yb, cudaStream_t st);
 // weighted gather / preconditioner scatter
 cudaError_t precond_apply(Ctx& c, const double* r, double* Z, int64_t ldz, double* z, cudaStream_t st);
+cudaError_t precond_apply_scratch(const Ctx& c, const double* r, double* Z, int64_t ldz, double* z, double* rb,
+                                  double* zb, cudaStream_t st);
 cudaError_t batched_gemv_F(Ctx& c, const double* xb, double* yb, cudaStream_t st);   // y_b = F_s x_b
 // y_b = A_s x_b (+ beta y_b), A_s = F_s (which 0) or S_bb (which 1)
 cudaError_t batched_gemv(const Ctx& c, int which, const double* xb, double* yb, double beta, cudaStream_t st);
