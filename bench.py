@@ -49,6 +49,7 @@ def parse():
     ap.add_argument("--tol", type=float, default=1e-6)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-accuracy", action="store_true")
     return ap.parse_args()
 
 
@@ -214,17 +215,17 @@ def run_ours(a, rank, world):
     torch.cuda.synchronize()
     solve_ms = e0.elapsed_time(e1)
 
-    # primal residual ||f - K u|| / ||f|| with the oracle's global assembly (CPU, outside timing)
-    rel_res = None
-    if rank == 0:
+    # accuracy: relative displacement error against a direct sparse solve of
+    # Eq. (2) assembled by the oracle (CPU, outside the timed region)
+    rel_err = None
+    if rank == 0 and not a.no_accuracy:
         try:
-            from oracle.assemble import global_stiffness
-            K = global_stiffness(p)
+            from oracle.assemble import direct_solve
+            ud = direct_solve(p)
             u = u_d.cpu().numpy()
-            free = p.dirichlet == 0
-            rel_res = float(np.linalg.norm((p.f - K @ u)[free]) / np.linalg.norm(p.f))
+            rel_err = float(np.linalg.norm(u - ud) / np.linalg.norm(ud))
         except Exception as exc:  # pragma: no cover - diagnostics only
-            rel_res = f"unavailable: {exc}"
+            rel_err = f"unavailable: {exc}"
 
     # end to end through the public API from pinned host buffers
     e2e = None
@@ -268,7 +269,7 @@ def run_ours(a, rank, world):
         "time_to_solve_ms": 1e3 * t_steps / a.steps,
         "solve_and_recover_ms": solve_ms,
         "iterations": iters, "converged": conv, "f_applies_per_step": applies // max(1, a.steps),
-        "primal_rel_residual": rel_res,
+        "rel_error_vs_direct_solve": rel_err,
         "roofline": {"bound": "alu", "kernel": "dgemm_kernel (FP64 GEMM: dual-operator blocks, Gram, "
                                                "orthogonalization, Schur)",
                      "achieved": gemm_tflops, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
