@@ -50,6 +50,8 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-accuracy", action="store_true")
+    ap.add_argument("--no-forms", action="store_true")
+    ap.add_argument("--forms-rho-lo", type=float, default=0.1)
     return ap.parse_args()
 
 
@@ -133,6 +135,70 @@ def cpu_threads():
         return len(os.sched_getaffinity(0))
     except AttributeError:
         return os.cpu_count()
+
+
+# ------------------------------------------------------------------ forms
+def apply_timing(fg, torch, stream, flush, s, n, m, reps=5):
+    """Device time of one dual-operator block apply Y = F X (m columns)."""
+    X = torch.randn(m, n, dtype=torch.float64, device=flush.device)
+    Y = torch.empty_like(X)
+    for _ in range(3):
+        fg.feti_apply_dual(s.ctx, X, n, m, Y, n)
+    ts = []
+    for _ in range(reps):
+        flush.zero_()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        fg.feti_apply_dual(s.ctx, X, n, m, Y, n)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ts.append(e0.elapsed_time(e1))
+    return float(np.median(ts))
+
+
+def compare_forms(a, fg, torch, dev, stream, flush):
+    """The precision form (TF32 tensor-core block products inside FP64 refinement
+    on the dual residual) against the plain FP64 form at equal accuracy (same
+    FP64 relative dual residual), on the same modular layout with densities
+    {rho_lo, 1} (contrast (1/rho_lo)^3), where the reduced-precision blocks
+    still carry the information the solve needs."""
+    p = workloads.config2(tiles=a.tiles, elems=a.elems)
+    p.rho = np.where(p.rho < 0.5, a.forms_rho_lo, 1.0)
+    p.Emin = 1e-9
+    rho_d = torch.from_numpy(p.rho).to(dev)
+    f_d = torch.from_numpy(p.f).to(dev)
+    out = {"workload": f"same layout, densities {{{a.forms_rho_lo}, 1}}, contrast {1 / a.forms_rho_lo ** 3:.0e}",
+           "rel_tol": a.tol}
+    sols = {}
+    for name, prec in (("fp64", fg.FETI_FP64), ("tf32", fg.FETI_TF32)):
+        s = fg.Solver(fg.FETI_FETIDP, fg.FETI_SCALING_K, fg.FETI_RRS, tol=a.tol, max_iter=500,
+                      stream=stream.cuda_stream, precision=prec)
+        s.setup(p, rho=rho_d, f=f_d, on_device=True)
+        u = torch.empty(p.n_dofs, dtype=torch.float64, device=dev)
+        times, st = [], None
+        for k in range(4):
+            flush.zero_()
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            fg.feti_factorize(s.ctx)
+            _, st = fg.feti_solve_dual(s.ctx, allow_notconv=True)
+            fg.feti_recover_displacements(s.ctx, u, True)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            if k >= 1:
+                times.append(e0.elapsed_time(e1))
+        n = fg.feti_query(s.ctx, fg.FETI_Q_N_LAMBDA)
+        ms_apply = apply_timing(fg, torch, stream, flush, s, n, 256)
+        sols[name] = u.cpu().numpy()
+        out[name] = {"time_to_solve_ms": float(np.median(times)), "iterations": st.iterations,
+                     "refinements": st.refinements, "f_applies": st.f_applies, "converged": bool(st.converged),
+                     "apply_256_cols_ms": ms_apply, "apply_f_applies_per_s": 256 / (ms_apply / 1e3)}
+        s.close()
+    out["tf32_vs_fp64_rel_diff"] = float(np.linalg.norm(sols["tf32"] - sols["fp64"]) / np.linalg.norm(sols["fp64"]))
+    out["speedup_time_to_solve"] = out["fp64"]["time_to_solve_ms"] / out["tf32"]["time_to_solve_ms"]
+    out["speedup_apply"] = out["fp64"]["apply_256_cols_ms"] / out["tf32"]["apply_256_cols_ms"]
+    return out
 
 
 # ------------------------------------------------------------------ our arm
@@ -260,6 +326,10 @@ def run_ours(a, rank, world):
                "d2h_bytes_per_step": int(p.f.nbytes + 8),
                "ms_per_step": 1e3 * e2e_t / max(1, a.steps)}
 
+    forms = None
+    if not a.no_forms:
+        forms = compare_forms(a, fg, torch, dev, stream, flush)
+
     gemm_tflops = gf / (gms / 1e3) / 1e12 if gms > 0 else None
     out = {
         "metric": METRIC, "value": value, "unit": "F-applies/s", "n_gpus": world, "steps": a.steps,
@@ -278,6 +348,7 @@ def run_ours(a, rank, world):
                      "kernel_share_of_step": (gms / 1e3) / t_steps if t_steps > 0 else None,
                      "launches": gn},
         "e2e": e2e, "gpu_launches": int(launches), "clocks": clk, "wall_s": wall,
+        "forms": forms,
     }
     s.close()
     return out

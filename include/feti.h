@@ -59,17 +59,21 @@ typedef enum {
 enum { FETI_TFETI = 0, FETI_FETIDP = 1 };                 /* Sections 2.1 / 2.2 */
 enum { FETI_SCALING_K = 0, FETI_SCALING_MULT = 1 };       /* Eq. 15 / multiplicity */
 enum { FETI_PCG = 0, FETI_FO = 1, FETI_RRS = 2 };         /* Sections 3.2, 3.3 */
-enum { FETI_FP64 = 0, FETI_FP32 = 1 };                    /* dense block-product precision */
+enum { FETI_FP64 = 0, FETI_TF32 = 1 };                    /* dense block-product precision */
 
 typedef struct {
   int method;          /* FETI_TFETI or FETI_FETIDP */
   int scaling;         /* FETI_SCALING_K or FETI_SCALING_MULT */
   int krylov;          /* FETI_PCG, FETI_FO or FETI_RRS */
-  int precision;       /* FETI_FP64 (default) */
+  int precision;       /* FETI_FP64 (default) or FETI_TF32: the dense F_s / S_s block products in
+                          TF32 on the tensor cores (FP32 accumulation) inside FP64 iterative
+                          refinement on the dual residual; Gram and orthogonalization stay FP64 */
   int max_iter;        /* Krylov iteration cap (default 500) */
   int dedup_modules;   /* 1: factorize identical modules once (Section 1) */
   double tol;          /* relative tolerance on sqrt(r^T z) (default 1e-6) */
   double rr_tol;       /* rank-revealing cutoff on the remaining/initial pivot ratio (1e-10) */
+  double inner_tol;    /* FETI_TF32: relative tolerance of each low-precision inner solve (1e-2) */
+  int max_refine;      /* FETI_TF32: cap on the FP64 refinement steps (30) */
 } feti_options;
 
 typedef struct {
@@ -88,7 +92,8 @@ typedef struct {
   int converged;        /* 1 if sqrt(r^T z) <= tol * initial value */
   int f_applies;        /* dual-operator columns applied (sum of retained ranks) */
   int last_rank;        /* retained directions in the last iteration */
-  double eps0, eps;     /* initial and final sqrt(r^T z) */
+  double eps0, eps;     /* initial and final sqrt(r^T z) (FP64 operator) */
+  int refinements;      /* FETI_TF32: FP64 refinement steps taken (0 for FETI_FP64) */
 } feti_stats;
 
 /* Fill *opt with the defaults listed above.  Never fails for non-null opt. */
@@ -146,7 +151,9 @@ feti_status feti_compliance_grad(feti_ctx* ctx, double* dc_drho, int on_device);
 
 /* The dual operator on a block of directions (the hot path of Algorithm 1):
  * Y = F X with F the TFETI F of Eq. 7 or the condensed FETI-DP operator
- * F_rr + F_rc Kbar_cc^{-1} F_rc^T of Eq. 12.  X, Y: DEVICE column-major
+ * F_rr + F_rc Kbar_cc^{-1} F_rc^T of Eq. 12, with the local blocks in the
+ * context's precision (FETI_TF32: tensor-core products of the diagonally
+ * scaled blocks).  X, Y: DEVICE column-major
  * [n_lambda x m] with leading dimensions ldx, ldy >= n_lambda.  Requires
  * feti_factorize. */
 feti_status feti_apply_dual(feti_ctx* ctx, const double* X, int ldx, int m, double* Y, int ldy);

@@ -20,7 +20,7 @@ FETI_OK, FETI_EINVAL, FETI_ENOMEM, FETI_ESTATE, FETI_ENOTCONV, FETI_EBREAKDOWN, 
 FETI_TFETI, FETI_FETIDP = 0, 1
 FETI_SCALING_K, FETI_SCALING_MULT = 0, 1
 FETI_PCG, FETI_FO, FETI_RRS = 0, 1, 2
-FETI_FP64, FETI_FP32 = 0, 1
+FETI_FP64, FETI_TF32 = 0, 1
 (FETI_Q_N_LAMBDA, FETI_Q_N_SUBDOMAINS, FETI_Q_N_PRIMAL, FETI_Q_N_MODULES, FETI_Q_N_B_TOTAL, FETI_Q_N_DOFS,
  FETI_Q_N_ELEMENTS, FETI_Q_MAX_NB, FETI_Q_DEVICE_BYTES, FETI_Q_N_RBM, FETI_Q_LAUNCHES) = range(11)
 
@@ -38,7 +38,8 @@ EXPORTS = [
 class feti_options(ctypes.Structure):
     _fields_ = [("method", ctypes.c_int), ("scaling", ctypes.c_int), ("krylov", ctypes.c_int),
                 ("precision", ctypes.c_int), ("max_iter", ctypes.c_int), ("dedup_modules", ctypes.c_int),
-                ("tol", ctypes.c_double), ("rr_tol", ctypes.c_double)]
+                ("tol", ctypes.c_double), ("rr_tol", ctypes.c_double), ("inner_tol", ctypes.c_double),
+                ("max_refine", ctypes.c_int)]
 
 
 class feti_problem(ctypes.Structure):
@@ -50,7 +51,8 @@ class feti_problem(ctypes.Structure):
 
 class feti_stats(ctypes.Structure):
     _fields_ = [("iterations", ctypes.c_int), ("converged", ctypes.c_int), ("f_applies", ctypes.c_int),
-                ("last_rank", ctypes.c_int), ("eps0", ctypes.c_double), ("eps", ctypes.c_double)]
+                ("last_rank", ctypes.c_int), ("eps0", ctypes.c_double), ("eps", ctypes.c_double),
+                ("refinements", ctypes.c_int)]
 
 
 _LIB = None
@@ -242,9 +244,11 @@ class Solver:
     """
 
     def __init__(self, method=FETI_FETIDP, scaling=FETI_SCALING_K, krylov=FETI_RRS, tol=1e-6, max_iter=500,
-                 rr_tol=1e-10, dedup=True, stream=None):
+                 rr_tol=1e-10, dedup=True, stream=None, precision=FETI_FP64, inner_tol=None):
         o = feti_options_default()
-        o.method, o.scaling, o.krylov = method, scaling, krylov
+        o.method, o.scaling, o.krylov, o.precision = method, scaling, krylov, precision
+        if inner_tol is not None:
+            o.inner_tol = inner_tol
         o.tol, o.max_iter, o.rr_tol, o.dedup_modules = tol, max_iter, rr_tol, int(dedup)
         self.ctx = feti_create(o, stream)
 

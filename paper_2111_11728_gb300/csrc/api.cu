@@ -137,13 +137,29 @@ feti_status ensure_split(Ctx& c, int64_t need) {
 // C (col-major M x N, ld ldc) = alpha * A^T B + beta * C with A (K x M) and
 // B (K x N) column-major (ld lda, ldb): the Gram products of Algorithm 1.
 feti_status gemm_tn(Ctx& c, const double* A, int64_t lda, const double* B, int64_t ldb, double* C, int64_t ldc,
-                    int M, int N, int K, double alpha, double beta) {
+                    int M, int N, int K, double alpha, double beta, int lower = 0) {
   GemmDesc d{};
   d.A = A; d.B = B; d.C = C; d.M = M; d.N = N; d.K = K;
   d.ars = lda; d.acs = 1; d.brs = 1; d.bcs = ldb; d.crs = 1; d.ccs = ldc;
+  d.tri = lower ? 1 : 0;
   const int splits = split_for(M, N, K);
   if (splits > 1) TRY(ensure_split(c, (int64_t)splits * M * N));
-  CU(dgemm_split(d, splits, c.d_split, alpha, beta, c.stream));
+  // symmetric products: the algorithmic count is the lower triangle
+  const double fl = lower ? (double)M * (M + 1.0) * K : -1.0;
+  CU(dgemm_split(d, splits, c.d_split, alpha, beta, c.stream, fl));
+  return FETI_OK;
+}
+
+// C (col-major M x N) = A[:, perm[0..K)] U with U upper triangular (K x N,
+// column-major ld ldu), A column-major n x m.
+feti_status gemm_perm_upper(Ctx& c, const double* A, int64_t lda, const int* perm, const double* U, int64_t ldu,
+                            double* C, int64_t ldc, int M, int N, double alg_flops) {
+  GemmDesc d{};
+  d.A = A; d.B = U; d.C = C; d.M = M; d.N = N; d.K = N;
+  d.ars = 1; d.acs = lda; d.brs = 1; d.bcs = ldu; d.crs = 1; d.ccs = ldc;
+  d.tri = 2;
+  d.acol = perm;
+  CU(dgemm_split(d, 1, nullptr, 1.0, 0.0, c.stream, alg_flops));
   return FETI_OK;
 }
 
@@ -189,6 +205,19 @@ feti_status project(Ctx& c, double* X, int64_t ldx, int m) {
   return FETI_OK;
 }
 
+// Inverse of the coarse matrix in c.d_Kbar: one CTA for small ones, the
+// blocked multi-CTA factorisation otherwise.
+cudaError_t coarse_inverse(Ctx& c) {
+  const int n = c.n_coarse;
+  if (n <= 128) {
+    DenseDesc hd{};
+    hd.n = n;
+    return dense_spd_inverse(c.d_dense_coarse, &hd, 1, c.d_status, c.stream);
+  }
+  return dense_spd_inverse_blocked(c.d_Kbar, c.d_Kbar_L, c.d_Kbar_inv, n, c.d_coarse_work, c.d_status,
+                                   c.d_dense_coarse, c.stream);
+}
+
 // Y = F X for m columns (device, column-major).
 feti_status apply_dual(Ctx& c, const double* X, int64_t ldx, int m, double* Y, int64_t ldy) {
   TRY(ensure_blocks(c, m));
@@ -209,11 +238,38 @@ feti_status apply_dual(Ctx& c, const double* X, int64_t ldx, int m, double* Y, i
   return FETI_OK;
 }
 
+// Y = F X with the local blocks on the tensor cores (TF32 inputs, FP32
+// accumulation); the thin corner coupling and the coarse solve stay FP64.
+feti_status apply_dual_lowp(Ctx& c, const double* X, int64_t ldx, int m, double* Y, int64_t ldy) {
+  TRY(ensure_blocks(c, m));
+  if (c.hp.method == FETI_FETIDP && c.hp.n_primal > 0) {
+    const int np = c.hp.n_primal;
+    CU(gather_lam_to_b(c, X, ldx, m, c.d_Xb, c.stream));
+    CU(corner_reduce(c, c.d_Xb, m, c.d_Cb, c.d_Vraw, c.stream));
+    GemmDesc d{};
+    d.A = c.d_Kbar_inv; d.B = c.d_Vraw; d.C = c.d_V; d.M = np; d.N = m; d.K = np;
+    d.ars = np; d.acs = 1; d.brs = 1; d.bcs = np; d.crs = 1; d.ccs = np;
+    CU(dgemm_split(d, 1, nullptr, 1.0, 0.0, c.stream));
+    CU(tc_apply_local(c, X, ldx, m, c.d_Yb, c.stream));
+    CU(corner_expand_thin(c, c.d_V, m, c.d_Yb, c.stream));
+  } else {
+    CU(tc_apply_local(c, X, ldx, m, c.d_Yb, c.stream));
+  }
+  CU(scatter_b_to_lam(c, c.d_Yb, m, Y, ldy, c.stream));
+  return FETI_OK;
+}
+
 feti_status check_status(Ctx& c, const char* where) {
   int st = 0;
   CU(cudaMemcpy(&st, c.d_status, sizeof(int), cudaMemcpyDeviceToHost));
   if (st != 0) {
     c.err = std::string(where) + ": non-positive pivot (";
+    if (st >= 3000000) {
+      c.err = std::string(where) + ": a tensor-core product timed out waiting for its MMAs (subdomain " +
+              std::to_string(st - 3000000) + ")";
+      CU(cudaMemset(c.d_status, 0, sizeof(int)));
+      return FETI_ECUDA;
+    }
     if (st >= 2000000) c.err += "dense factor, tag " + std::to_string(st - 2000000);
     else c.err += "banded factor of module " + std::to_string(st - 1000000);
     c.err += "); the stiffness is not positive definite (zero density with Emin = 0?)";
@@ -274,6 +330,8 @@ feti_status feti_options_default(feti_options* opt) {
   opt->dedup_modules = 1;
   opt->tol = 1e-6;
   opt->rr_tol = 1e-10;
+  opt->inner_tol = 1e-2;
+  opt->max_refine = 30;
   return FETI_OK;
 }
 
@@ -287,7 +345,8 @@ feti_status feti_create(feti_ctx** out, const feti_options* opt, void* stream) {
       (o.scaling != FETI_SCALING_K && o.scaling != FETI_SCALING_MULT) ||
       (o.krylov < FETI_PCG || o.krylov > FETI_RRS) || o.max_iter < 0 || !(o.tol >= 0.0) || !(o.rr_tol >= 0.0))
     return FETI_EINVAL;
-  if (o.precision != FETI_FP64) return FETI_ENOTSUP;
+  if (o.precision != FETI_FP64 && o.precision != FETI_TF32) return FETI_EINVAL;
+  if (o.precision == FETI_TF32 && !(o.inner_tol > 0.0 && o.inner_tol < 1.0 && o.max_refine > 0)) return FETI_EINVAL;
   feti_ctx* ctx = new (std::nothrow) feti_ctx;
   if (!ctx) return FETI_ENOMEM;
   Ctx& c = ctx->c;
@@ -461,10 +520,19 @@ feti_status feti_setup_subdomains(feti_ctx* ctx, const feti_problem* prob) {
   TRY(dalloc(c, c.d_Kbar_L, nco * nco));
   TRY(dalloc(c, c.d_Kbar_inv, nco * nco));
   TRY(dalloc(c, c.d_fbar, std::max(hp.n_primal, 1)));
+  TRY(dalloc(c, c.d_coarse_work, (size_t)128 * nco + (size_t)((nco + 63) / 64) * 4096));
   if (hp.method == FETI_TFETI) {
     TRY(dalloc(c, c.d_G, (size_t)nco * nl));
     TRY(dalloc(c, c.d_e, nco));
     TRY(dalloc(c, c.d_alpha, nco));
+  }
+  if (c.opt.precision == FETI_TF32) {
+    TRY(dalloc(c, c.d_fmem, (size_t)c.modmem_len));
+    TRY(dalloc(c, c.d_sqrtDF, nbt));
+    TRY(dalloc(c, c.d_sqrtDS, nbt));
+    TRY(dalloc(c, c.d_rout, nl));
+    TRY(dalloc(c, c.d_zout, nl));
+    TRY(dalloc(c, c.d_dl, nl));
   }
   TRY(dalloc(c, c.d_d, nl));
   TRY(dalloc(c, c.d_lam0, nl));
@@ -474,6 +542,7 @@ feti_status feti_setup_subdomains(feti_ctx* ctx, const feti_problem* prob) {
   TRY(dalloc(c, c.d_scalar, 64));
   TRY(dalloc(c, c.d_status, 4));
   TRY(dalloc(c, c.d_kdev, 4));
+  TRY(dalloc(c, c.d_perm, 1024));
   TRY(dalloc(c, c.d_red, 1024));
   CU(cudaMemset(c.d_status, 0, 4 * sizeof(int)));
   // ---- per-module descriptors for the factorization ----
@@ -578,6 +647,7 @@ feti_status feti_factorize(feti_ctx* ctx) {
     CU(dgemm_batched(c.d_gemm_frcmake, c.n_mod, c.max_nb, c.max_nc, 0, 1.0, 0.0, st, c.fl_frcmake));
     CU(launch_copy_block(c, 1, st));
   }
+  if (c.opt.precision == FETI_TF32) CU(tc_prepare(c, st));
   // loads: f^s, h = L^{-1} f_i, f~ = f_bc - Y^T h
   CU(launch_load_gather(c, st));
   CU(launch_band_fwd_single(c, st));
@@ -591,11 +661,7 @@ feti_status feti_factorize(feti_ctx* ctx) {
     const int np = hp.n_primal;
     // coarse matrix Kbar_cc (Eq. 12) and its inverse
     CU(launch_coarse_assemble_impl(c, c.d_c_sub, c.d_c_off, c.d_Kbar, st));
-    {
-      DenseDesc hd{};
-      hd.n = np;
-      CU(dense_spd_inverse(c.d_dense_coarse, &hd, 1, c.d_status, st));
-    }
+    CU(coarse_inverse(c));
     // fbar_c = sum_s B_c^sT (f~_c - F_rc,s^T f~_b)
     CU(cudaMemcpyAsync(c.d_Xb, c.d_ft, nbt * sizeof(double), cudaMemcpyDeviceToDevice, st));
     CU(corner_reduce(c, c.d_Xb, 1, c.d_Cb, c.d_Vraw, st));
@@ -612,11 +678,7 @@ feti_status feti_factorize(feti_ctx* ctx) {
     const int nco = c.n_coarse;
     CU(tfeti_build_G(c, c.d_G, st));
     TRY(gemm_tn(c, c.d_G, nl, c.d_G, nl, c.d_Kbar, nco, nco, nco, (int)nl, 1.0, 0.0));
-    {
-      DenseDesc hd{};
-      hd.n = nco;
-      CU(dense_spd_inverse(c.d_dense_coarse, &hd, 1, c.d_status, st));
-    }
+    CU(coarse_inverse(c));
     CU(tfeti_build_e(c, c.d_e, st));
     CU(gemv_dense(c.d_Kbar_inv, nco, nco, c.d_e, c.d_alpha, 0.0, st));
     TRY(gemm_nn(c, c.d_G, nl, c.d_alpha, nco, c.d_lam0, nl, (int)nl, 1, nco, 1.0, 0.0));
@@ -654,33 +716,25 @@ static feti_status read_scalar(Ctx& c, const double* d, double* out) {
   return FETI_OK;
 }
 
-static feti_status solve_impl(Ctx& c, double* lambda_inout, feti_stats* stats) {
+// Algorithm 1 on F lambda~ = r_0 with r_0 already in c.d_r (projected);
+// leaves lambda~ in c.d_lamt and the final residual in c.d_r.  lowp selects
+// the tensor-core local products and the FP32 preconditioner blocks.
+static feti_status krylov_core(Ctx& c, double tol, int max_iter, bool lowp, feti_stats& S) {
   const HostProblem& hp = c.hp;
   const int64_t nl = hp.n_lam;
   const bool multi = c.opt.krylov == FETI_RRS;
   const bool full = c.opt.krylov != FETI_PCG;
-  const int mmax = multi ? hp.n_sub : 1;
-  if (mmax > 1024) { c.err = "more than 1024 subdomains per direction block"; return FETI_ENOTSUP; }
-  TRY(ensure_krylov(c, mmax));
-  TRY(ensure_blocks(c, mmax));
+  const int m = multi ? hp.n_sub : 1;
   cudaStream_t st = c.stream;
-  feti_stats S{};
-  // lambda_0 (warm start or the method's own), r_0 = P^T (d - F lambda_0)
-  CU(cudaMemcpyAsync(c.d_lam, lambda_inout ? lambda_inout : c.d_lam0, nl * sizeof(double),
-                     cudaMemcpyDeviceToDevice, st));
-  if (lambda_inout && hp.method == FETI_TFETI) {
-    // keep G lambda = e: lambda = lambda_0 + P (lambda_in - lambda_0)
-    CU(axpby(nl, -1.0, c.d_lam0, 1.0, c.d_lam, st));
-    TRY(project(c, c.d_lam, nl, 1));
-    CU(axpby(nl, 1.0, c.d_lam0, 1.0, c.d_lam, st));
-  }
-  TRY(apply_dual(c, c.d_lam, nl, 1, c.d_r, nl));
-  CU(axpby(nl, 1.0, c.d_d, -1.0, c.d_r, st));
-  TRY(project(c, c.d_r, nl, 1));
+  auto applyF = [&](const double* X, int mm, double* Y) {
+    return lowp ? apply_dual_lowp(c, X, nl, mm, Y, nl) : apply_dual(c, X, nl, mm, Y, nl);
+  };
+  auto precond = [&](double* Z, double* z) -> cudaError_t {
+    return lowp ? precond_apply_lowp(c, c.d_r, Z, nl, z, st) : precond_apply(c, c.d_r, Z, nl, z, st);
+  };
   // Z_0, W_0 = P Z_0
-  CU(precond_apply(c, c.d_r, multi ? c.d_Wb : nullptr, nl, c.d_z, st));
+  CU(precond(multi ? c.d_Wb : nullptr, c.d_z));
   if (!multi) CU(cudaMemcpyAsync(c.d_Wb, c.d_z, nl * sizeof(double), cudaMemcpyDeviceToDevice, st));
-  const int m = mmax;
   TRY(project(c, c.d_Wb, nl, m));
   CU(cudaMemsetAsync(c.d_lamt, 0, nl * sizeof(double), st));
   CU(dot(c.d_r, c.d_z, nl, c.d_red, c.d_scalar, st));
@@ -688,16 +742,16 @@ static feti_status solve_impl(Ctx& c, double* lambda_inout, feti_stats* stats) {
   TRY(read_scalar(c, c.d_scalar, &rz));
   const double eps0 = std::sqrt(std::max(rz, 0.0));
   double eps = eps0;
-  S.eps0 = eps0;
   int it = 0;
   feti_status result = FETI_OK;
   c.hist_k.clear();
-  while (eps > c.opt.tol * eps0 && it < c.opt.max_iter) {
-    // Q = F W, Delta = Q^T W
-    TRY(apply_dual(c, c.d_Wb, nl, m, c.d_Qb, nl));
-    TRY(gemm_tn(c, c.d_Qb, nl, c.d_Wb, nl, c.d_Delta, m, m, m, (int)nl, 1.0, 0.0));
-    // rank-revealing factorization and F-orthonormal transform T = N^T [L~^{-T}; 0]
-    CU(rr_cholesky(c.d_Delta, m, m, c.opt.rr_tol, c.d_rrwork, c.d_T, c.d_kdev, st));
+  while (eps > tol * eps0 && it < max_iter) {
+    // Q = F W, Delta = Q^T W (symmetric: lower-triangular tiles suffice)
+    TRY(applyF(c.d_Wb, m, c.d_Qb));
+    TRY(gemm_tn(c, c.d_Qb, nl, c.d_Wb, nl, c.d_Delta, m, m, m, (int)nl, 1.0, 0.0, 1));
+    // rank-revealing factorization and F-orthonormal transform: N^T [L~^{-T}; 0]
+    // applied as (W with columns in pivot order) times the upper-triangular L~^{-T}
+    CU(rr_cholesky(c.d_Delta, m, m, c.opt.rr_tol, c.d_rrwork, c.d_T, c.d_kdev, c.d_perm, st));
     int k = 0;
     CU(cudaMemcpyAsync(c.h_pin, c.d_kdev, sizeof(int), cudaMemcpyDeviceToHost, st));
     CU(cudaStreamSynchronize(st));
@@ -706,17 +760,17 @@ static feti_status solve_impl(Ctx& c, double* lambda_inout, feti_stats* stats) {
     if (k <= 0) { result = FETI_EBREAKDOWN; c.err = "no independent search direction left"; break; }
     if ((int)c.hist_W.size() <= it) {
       double *w, *q;
-      TRY(dalloc(c, w, (size_t)nl * mmax));
-      TRY(dalloc(c, q, (size_t)nl * mmax));
+      TRY(dalloc(c, w, (size_t)nl * m));
+      TRY(dalloc(c, q, (size_t)nl * m));
       c.hist_W.push_back(w);
       c.hist_Q.push_back(q);
     }
     double* Wi = c.hist_W[it];
     double* Qi = c.hist_Q[it];
     c.hist_k.push_back(k);
-    const double fl_T = (double)nl * k * (k + 1.0);   // 2 n nnz(T), T = N^T [L~^{-T}; 0]
-    TRY(gemm_nn(c, c.d_Wb, nl, c.d_T, m, Wi, nl, (int)nl, k, m, 1.0, 0.0, fl_T));
-    TRY(gemm_nn(c, c.d_Qb, nl, c.d_T, m, Qi, nl, (int)nl, k, m, 1.0, 0.0, fl_T));
+    const double fl_T = (double)nl * k * (k + 1.0);   // 2 n nnz(U)
+    TRY(gemm_perm_upper(c, c.d_Wb, nl, c.d_perm, c.d_T, m, Wi, nl, (int)nl, k, fl_T));
+    TRY(gemm_perm_upper(c, c.d_Qb, nl, c.d_perm, c.d_T, m, Qi, nl, (int)nl, k, fl_T));
     S.f_applies += m;
     // gamma = W^T r; lambda~ += W gamma; r -= P^T Q gamma
     CU(gemv_t(Wi, nl, nl, k, c.d_r, c.d_gamma, st));
@@ -728,7 +782,7 @@ static feti_status solve_impl(Ctx& c, double* lambda_inout, feti_stats* stats) {
       CU(step_update(Wi, Qi, nl, nl, k, c.d_gamma, c.d_lamt, c.d_r, nullptr, st));
     }
     // Z_{i+1}, W_{i+1} = P Z_{i+1}
-    CU(precond_apply(c, c.d_r, multi ? c.d_Wb : nullptr, nl, c.d_z, st));
+    CU(precond(multi ? c.d_Wb : nullptr, c.d_z));
     if (!multi) CU(cudaMemcpyAsync(c.d_Wb, c.d_z, nl * sizeof(double), cudaMemcpyDeviceToDevice, st));
     TRY(project(c, c.d_Wb, nl, m));
     // F-orthogonalise against the stored blocks, oldest first (modified Gram-Schmidt)
@@ -743,12 +797,77 @@ static feti_status solve_impl(Ctx& c, double* lambda_inout, feti_stats* stats) {
     eps = std::sqrt(std::max(rz, 0.0));
     if (!std::isfinite(rz)) { result = FETI_EBREAKDOWN; c.err = "NaN or Inf in the residual"; break; }
   }
-  CU(axpby(nl, 1.0, c.d_lamt, 1.0, c.d_lam, st));
+  S.iterations += it;
+  S.eps0 = eps0;
+  S.eps = eps;
+  S.converged = eps <= tol * eps0;
+  return result;
+}
+
+static feti_status solve_impl(Ctx& c, double* lambda_inout, feti_stats* stats) {
+  const HostProblem& hp = c.hp;
+  const int64_t nl = hp.n_lam;
+  const bool multi = c.opt.krylov == FETI_RRS;
+  const int mmax = multi ? hp.n_sub : 1;
+  if (mmax > 1024) { c.err = "more than 1024 subdomains per direction block"; return FETI_ENOTSUP; }
+  TRY(ensure_krylov(c, mmax));
+  TRY(ensure_blocks(c, mmax));
+  cudaStream_t st = c.stream;
+  feti_stats S{};
+  // lambda_0 (warm start or the method's own)
+  CU(cudaMemcpyAsync(c.d_lam, lambda_inout ? lambda_inout : c.d_lam0, nl * sizeof(double),
+                     cudaMemcpyDeviceToDevice, st));
+  if (lambda_inout && hp.method == FETI_TFETI) {
+    // keep G lambda = e: lambda = lambda_0 + P (lambda_in - lambda_0)
+    CU(axpby(nl, -1.0, c.d_lam0, 1.0, c.d_lam, st));
+    TRY(project(c, c.d_lam, nl, 1));
+    CU(axpby(nl, 1.0, c.d_lam0, 1.0, c.d_lam, st));
+  }
+  feti_status result = FETI_OK;
+  if (c.opt.precision == FETI_FP64) {
+    // r_0 = P^T (d - F lambda_0), then Algorithm 1; lambda = lambda_0 + lambda~
+    TRY(apply_dual(c, c.d_lam, nl, 1, c.d_r, nl));
+    CU(axpby(nl, 1.0, c.d_d, -1.0, c.d_r, st));
+    TRY(project(c, c.d_r, nl, 1));
+    result = krylov_core(c, c.opt.tol, c.opt.max_iter, false, S);
+    CU(axpby(nl, 1.0, c.d_lamt, 1.0, c.d_lam, st));
+  } else {
+    // FP64 iterative refinement on the dual residual: r = P^T (d - F lambda)
+    // with the FP64 operator; each correction solves F dl = r with the
+    // low-precision local products to inner_tol.
+    double eps0 = -1.0, eps = 0.0;
+    int outer = 0;
+    for (;;) {
+      TRY(apply_dual(c, c.d_lam, nl, 1, c.d_rout, nl));
+      CU(axpby(nl, 1.0, c.d_d, -1.0, c.d_rout, st));
+      TRY(project(c, c.d_rout, nl, 1));
+      CU(precond_apply(c, c.d_rout, nullptr, nl, c.d_zout, st));
+      CU(dot(c.d_rout, c.d_zout, nl, c.d_red, c.d_scalar, st));
+      double rz = 0.0;
+      TRY(read_scalar(c, c.d_scalar, &rz));
+      eps = std::sqrt(std::max(rz, 0.0));
+      if (eps0 < 0.0) eps0 = eps;
+      S.f_applies += 1;
+      if (!std::isfinite(rz)) { result = FETI_EBREAKDOWN; c.err = "NaN or Inf in the refined residual"; break; }
+      if (eps <= c.opt.tol * eps0 || outer >= c.opt.max_refine || S.iterations >= c.opt.max_iter) break;
+      CU(cudaMemcpyAsync(c.d_r, c.d_rout, nl * sizeof(double), cudaMemcpyDeviceToDevice, st));
+      feti_stats inner{};
+      feti_status s2 = krylov_core(c, c.opt.inner_tol, c.opt.max_iter - S.iterations, true, inner);
+      S.iterations += inner.iterations;
+      S.f_applies += inner.f_applies;
+      S.last_rank = inner.last_rank;
+      ++outer;
+      if (s2 != FETI_OK && s2 != FETI_ENOTCONV) { result = s2; break; }
+      CU(axpby(nl, 1.0, c.d_lamt, 1.0, c.d_lam, st));
+    }
+    S.eps0 = eps0;
+    S.eps = eps;
+    S.converged = eps <= c.opt.tol * eps0;
+    S.refinements = outer;
+  }
   if (lambda_inout) CU(cudaMemcpyAsync(lambda_inout, c.d_lam, nl * sizeof(double), cudaMemcpyDeviceToDevice, st));
   TRY(sync_check(c));
-  S.iterations = it;
-  S.eps = eps;
-  S.converged = eps <= c.opt.tol * eps0;
+  TRY(check_status(c, "solve"));
   if (result == FETI_OK && !S.converged) {
     result = FETI_ENOTCONV;
     c.err = "max_iter reached";
@@ -830,6 +949,11 @@ feti_status feti_apply_dual(feti_ctx* ctx, const double* X, int ldx, int m, doub
   if (c.state < 2) { c.err = "feti_apply_dual before feti_factorize"; return FETI_ESTATE; }
   if (ldx < c.hp.n_lam || ldy < c.hp.n_lam) { c.err = "leading dimension smaller than n_lambda"; return FETI_EINVAL; }
   if (m == 0) return FETI_OK;
+  if (c.opt.precision == FETI_TF32) TRY(apply_dual_lowp(c, X, ldx, m, Y, ldy));
+  else TRY(apply_dual(c, X, ldx, m, Y, ldy));
+  TRY(sync_check(c));
+  TRY(check_status(c, "feti_apply_dual"));
+  return FETI_OK;
   TRY(apply_dual(c, X, ldx, m, Y, ldy));
   TRY(sync_check(c));
   return FETI_OK;

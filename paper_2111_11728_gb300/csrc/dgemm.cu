@@ -71,7 +71,14 @@ __device__ __forceinline__ void load_tile_A(const GemmDesc& d, int row0, int k0,
                                             double (*As)[BM + 1], int tid) {
   // As[k][i] = A(row0 + i, k0 + k); choose the thread order that walks the
   // contiguous dimension of A.
-  if (d.ars == 1) {
+  if (d.acol) {
+#pragma unroll
+    for (int e = tid; e < BM * BK; e += NT) {
+      int i = e % BM, k = e / BM;
+      int gi = row0 + i, gk = k0 + k;
+      As[k][i] = (gi < d.M && gk < k1) ? d.A[(int64_t)gi * d.ars + (int64_t)d.acol[gk] * d.acs] : 0.0;
+    }
+  } else if (d.ars == 1) {
 #pragma unroll
     for (int e = tid; e < BM * BK; e += NT) {
       int i = e % BM, k = e / BM;
@@ -117,10 +124,12 @@ __global__ void __launch_bounds__(NT) dgemm_kernel(const GemmDesc* __restrict__ 
   const int tm = blockIdx.x % tiles_m, tn = blockIdx.x / tiles_m;
   const int row0 = tm * BM, col0 = tn * BN;
   if (row0 >= d.M || col0 >= N) return;
+  if (d.tri == 1 && col0 > row0 + BM - 1) return;          // strictly above the diagonal
   int kchunk = (d.K + splits - 1) / splits;
   kchunk = (kchunk + BK - 1) / BK * BK;
   const int kb = blockIdx.z * kchunk;
-  const int ke = min(d.K, kb + kchunk);
+  int ke = min(d.K, kb + kchunk);
+  if (d.tri == 2) ke = min(ke, col0 + BN);                  // B upper triangular
 
   __shared__ double As[BK][BM + 1];
   __shared__ double Bs[BK][BN + 1];
@@ -188,6 +197,7 @@ __global__ void split_reduce_kernel(GemmDesc d, const double* __restrict__ parti
   for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
        e += (int64_t)gridDim.x * blockDim.x) {
     int gi = (int)(e / d.N), gj = (int)(e % d.N);
+    if (d.tri == 1 && (gj / BN) * BN > (gi / BM) * BM + BM - 1) continue;   // tile never computed
     double s = 0.0;
     for (int z = 0; z < splits; ++z) s += partial[(int64_t)z * total + e];
     double* cp = d.C + (int64_t)gi * d.crs + (int64_t)gj * d.ccs;

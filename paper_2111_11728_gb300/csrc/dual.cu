@@ -112,6 +112,36 @@ __global__ void k_sub_gemv(const DevType* __restrict__ types, const DevModule* _
   }
 }
 
+// Cb[c_off(s) + c + j*nct] = sum_k F_rc,s(k, c) X_b(s)[k, j]: the thin corner
+// product (n_c <= 24 rows), one thread per (column j, subdomain) with all
+// n_c sums in registers, so no FP64 work is spent on tile padding.
+template <int NC>
+__global__ void k_frct(const DevType* __restrict__ types, const DevModule* __restrict__ mods,
+                       const DevSub* __restrict__ subs, const double* __restrict__ mem,
+                       const double* __restrict__ Xb, int64_t nbt, int m, double* __restrict__ Cb, int64_t nct) {
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  const DevSub S = subs[blockIdx.y];
+  if (j >= m) return;
+  const DevType T = types[S.type];
+  const int nc = T.n_c, nb = T.n_b;
+  const double* F = mem + mods[S.module].Frc;    // [nb x nc] row-major
+  const double* x = Xb + S.b_off + (int64_t)j * nbt;
+  double acc[NC];
+#pragma unroll
+  for (int c = 0; c < NC; ++c) acc[c] = 0.0;
+  for (int k = 0; k < nb; ++k) {
+    const double xv = x[k];
+    const double* fr = F + (int64_t)k * nc;
+#pragma unroll
+    for (int c = 0; c < NC; ++c)
+      if (c < nc) acc[c] = fma(fr[c], xv, acc[c]);
+  }
+  double* out = Cb + S.c_off + (int64_t)j * nct;
+#pragma unroll
+  for (int c = 0; c < NC; ++c)
+    if (c < nc) out[c] = acc[c];
+}
+
 // Vraw[g + j*np] = sum over the corner copies of g of Cb[src + j*nct]
 __global__ void k_corner_gather(int np, int m, const int* __restrict__ poff, const int* __restrict__ psrc,
                                 const double* __restrict__ Cb, int64_t nct, double* __restrict__ V) {
@@ -156,7 +186,20 @@ cudaError_t apply_local_F(Ctx& c, const double* /*Xb*/, double* /*Yb*/, int m, d
 }
 
 cudaError_t corner_reduce(Ctx& c, const double* /*Xb*/, int m, double* /*Cb*/, double* Vraw, cudaStream_t st) {
-  cudaError_t e = dgemm_batched(c.d_gemm_FrcT, c.hp.n_sub, c.max_nc, c.max_nb, m, 1.0, 0.0, st, c.fl_FrcT * m);
+  cudaError_t e;
+  if (c.max_nc <= 8) {
+    k_frct<8><<<dim3((m + 63) / 64, c.hp.n_sub), 64, 0, st>>>(c.d_types, c.d_mods, c.d_subs, c.d_modmem, c.d_Xb,
+                                                             c.hp.n_b_total, m, c.d_Cb, c.n_c_total);
+    note_launches(1);
+    e = cudaGetLastError();
+  } else if (c.max_nc <= 24) {
+    k_frct<24><<<dim3((m + 63) / 64, c.hp.n_sub), 64, 0, st>>>(c.d_types, c.d_mods, c.d_subs, c.d_modmem, c.d_Xb,
+                                                              c.hp.n_b_total, m, c.d_Cb, c.n_c_total);
+    note_launches(1);
+    e = cudaGetLastError();
+  } else {
+    e = dgemm_batched(c.d_gemm_FrcT, c.hp.n_sub, c.max_nc, c.max_nb, m, 1.0, 0.0, st, c.fl_FrcT * m);
+  }
   if (e != cudaSuccess) return e;
   const int np = c.hp.n_primal;
   dim3 g((np + 127) / 128, m);
@@ -226,6 +269,64 @@ cudaError_t precond_apply_scratch(const Ctx& c, const double* r, double* Z, int6
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   e = batched_gemv(c, 1, rb, zb, 0.0, st);
+  if (e != cudaSuccess) return e;
+  if (Z) {
+    e = cudaMemsetAsync(Z, 0, sizeof(double) * (size_t)ldz * c.hp.n_sub, st);
+    if (e != cudaSuccess) return e;
+  }
+  k_prec_scatter<<<(unsigned)((nl + 255) / 256), 256, 0, st>>>(nl, c.d_lam_b0, c.d_lam_s0, c.d_lam_b1, c.d_lam_s1,
+                                                               c.d_w0, c.d_w1, c.d_b_sub, zb, Z, ldz, z);
+  note_launches(1);
+  return cudaGetLastError();
+}
+
+namespace {
+
+// Yb[b_off(s) + k + j*nbt] += sum_c F_rc,s(k, c) V[c_glob(s, c) + j*np]; one
+// thread per interface row, 32 columns per thread.
+__global__ void k_frc_expand(const DevType* __restrict__ types, const DevModule* __restrict__ mods,
+                             const DevSub* __restrict__ subs, const double* __restrict__ mem,
+                             const int* __restrict__ cg, const double* __restrict__ V, int np, int m,
+                             double* __restrict__ Yb, int64_t nbt) {
+  const DevSub S = subs[blockIdx.y];
+  const DevType T = types[S.type];
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= T.n_b) return;
+  const int nc = T.n_c;
+  if (nc == 0) return;
+  const double* fr = mem + mods[S.module].Frc + (int64_t)k * nc;
+  double f[24];
+  int g[24];
+  for (int c = 0; c < nc && c < 24; ++c) { f[c] = fr[c]; g[c] = cg[S.c_off + c]; }
+  const int j0 = blockIdx.z * 32, j1 = min(m, j0 + 32);
+  for (int j = j0; j < j1; ++j) {
+    double acc = 0.0;
+    for (int c = 0; c < nc && c < 24; ++c) acc = fma(f[c], V[g[c] + (int64_t)j * np], acc);
+    Yb[S.b_off + k + (int64_t)j * nbt] += acc;
+  }
+}
+
+}  // namespace
+
+cudaError_t corner_expand_thin(Ctx& c, const double* V, int m, double* Yb, cudaStream_t st) {
+  if (c.max_nc > 24) return corner_expand(c, V, m, c.d_Vc, Yb, st);
+  dim3 g((c.max_nb + 127) / 128, c.hp.n_sub, (m + 31) / 32);
+  k_frc_expand<<<g, 128, 0, st>>>(c.d_types, c.d_mods, c.d_subs, c.d_modmem, c.d_c_glob, V, c.hp.n_primal, m, Yb,
+                                  c.hp.n_b_total);
+  note_launches(1);
+  return cudaGetLastError();
+}
+
+cudaError_t precond_apply_lowp(Ctx& c, const double* r, double* Z, int64_t ldz, double* z, cudaStream_t st) {
+  const int64_t nbt = c.hp.n_b_total, nl = c.hp.n_lam;
+  double* rb = c.d_pb0;
+  double* zb = c.d_pb1;
+  k_gather_weighted<<<(unsigned)((nbt + 255) / 256), 256, 0, st>>>(nbt, c.d_b2l_off, c.d_b2l_lam, c.d_b2l_sign,
+                                                                   c.d_lam_b0, c.d_w0, c.d_w1, r, rb);
+  note_launches(1);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  e = lowp_gemv_S(c, rb, zb, st);
   if (e != cudaSuccess) return e;
   if (Z) {
     e = cudaMemsetAsync(Z, 0, sizeof(double) * (size_t)ldz * c.hp.n_sub, st);

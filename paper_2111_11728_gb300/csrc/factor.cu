@@ -140,25 +140,34 @@ __global__ void __launch_bounds__(NT) k_dense_chol(const DenseDesc* __restrict__
 }
 
 // Linv = L^{-1} (row-major, zero above the diagonal); one thread per column.
+// A warp walks the rows of its 32 columns together, starting at its first
+// column, so every load of Linv is one contiguous row segment (the entries
+// above a column's diagonal are zero and add nothing).
 __global__ void k_tri_inv(const DenseDesc* __restrict__ descs) {
   const DenseDesc D = descs[blockIdx.y];
   const int n = D.n, ld = D.ld;
   const int j = blockIdx.x * blockDim.x + threadIdx.x;
-  if (j >= n) return;
+  const int j0 = blockIdx.x * blockDim.x + (threadIdx.x & ~31);
+  if (j0 >= n) return;
+  const bool act = j < n;
   const double* L = D.A;
   double* X = D.Linv;
-  for (int i = 0; i < j; ++i) X[(int64_t)i * n + j] = 0.0;
-  X[(int64_t)j * n + j] = 1.0 / L[(int64_t)j * ld + j];
-  for (int i = j + 1; i < n; ++i) {
+  if (act) {
+    for (int i = 0; i < j; ++i) X[(int64_t)i * n + j] = 0.0;
+    X[(int64_t)j * n + j] = 1.0 / L[(int64_t)j * ld + j];
+  }
+  __syncwarp();
+  for (int i = j0 + 1; i < n; ++i) {
     const double* Li = L + (int64_t)i * ld;
     double a0 = 0.0, a1 = 0.0;
-    int k = j;
+    int k = j0;
     for (; k + 1 < i; k += 2) {
-      a0 = fma(Li[k], X[(int64_t)k * n + j], a0);
-      a1 = fma(Li[k + 1], X[(int64_t)(k + 1) * n + j], a1);
+      a0 = fma(Li[k], act ? X[(int64_t)k * n + j] : 0.0, a0);
+      a1 = fma(Li[k + 1], act ? X[(int64_t)(k + 1) * n + j] : 0.0, a1);
     }
-    if (k < i) a0 = fma(Li[k], X[(int64_t)k * n + j], a0);
-    X[(int64_t)i * n + j] = -(a0 + a1) / Li[i];
+    if (k < i) a0 = fma(Li[k], act ? X[(int64_t)k * n + j] : 0.0, a0);
+    if (act && i > j) X[(int64_t)i * n + j] = -(a0 + a1) / Li[i];
+    __syncwarp();
   }
 }
 
@@ -280,7 +289,122 @@ __global__ void k_copy_block(const DevType* __restrict__ types, const DevModule*
   }
 }
 
+// Diagonal block [c0, c0+nb) of a row-major n x n matrix: Cholesky in shared
+// memory, written back (lower triangle), and its inverse into Dinv (nb x nb
+// row-major, ld 64).  One CTA of 256 threads.
+__global__ void __launch_bounds__(256) k_diag_block(double* __restrict__ A, int n, int c0, int nb,
+                                                   double* __restrict__ Dinv, int* __restrict__ status, int tag) {
+  __shared__ double S[64][65];
+  __shared__ double X[64][65];
+  const int tid = threadIdx.x;
+  for (int e = tid; e < nb * nb; e += 256) {
+    const int r = e / nb, q = e % nb;
+    S[r][q] = A[(int64_t)(c0 + r) * n + c0 + q];
+  }
+  __syncthreads();
+  for (int j = 0; j < nb; ++j) {
+    const double piv = S[j][j];
+    __syncthreads();
+    if (!(piv > 0.0)) {
+      if (tid == 0) atomicCAS(status, 0, 2000000 + tag);
+      return;
+    }
+    const double dj = sqrt(piv), rd = 1.0 / dj;
+    for (int t = j + tid; t < nb; t += 256) S[t][j] = t == j ? dj : S[t][j] * rd;
+    __syncthreads();
+    for (int e = tid; e < (nb - 1 - j) * (nb - 1 - j); e += 256) {
+      const int a = j + 1 + e / (nb - 1 - j), b = j + 1 + e % (nb - 1 - j);
+      if (b <= a) S[a][b] = fma(-S[a][j], S[b][j], S[a][b]);
+    }
+    __syncthreads();
+  }
+  // inverse of the lower-triangular block, one thread per column
+  if (tid < nb) {
+    const int c = tid;
+    for (int i = 0; i < c; ++i) X[i][c] = 0.0;
+    X[c][c] = 1.0 / S[c][c];
+    for (int i = c + 1; i < nb; ++i) {
+      double acc = 0.0;
+      for (int k = c; k < i; ++k) acc = fma(S[i][k], X[k][c], acc);
+      X[i][c] = -acc / S[i][i];
+    }
+  }
+  __syncthreads();
+  for (int e = tid; e < nb * nb; e += 256) {
+    const int r = e / nb, q = e % nb;
+    if (q <= r) A[(int64_t)(c0 + r) * n + c0 + q] = S[r][q];
+    Dinv[r * 64 + q] = X[r][q];
+  }
+}
+
+__global__ void k_copy_rows(const double* __restrict__ src, int64_t lds, double* __restrict__ dst, int64_t ldd,
+                            int rows, int cols, double scale) {
+  const int64_t total = (int64_t)rows * cols;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+    const int r = (int)(e / cols), q = (int)(e % cols);
+    dst[r * ldd + q] = scale * src[r * lds + q];
+  }
+}
+
 }  // namespace
+
+// Blocked right-looking Cholesky of one SPD n x n row-major matrix A (full
+// symmetric storage; on return its lower triangle holds L), then
+// X = L^{-1} block row by block row, then out = X^T X = A^{-1}.  All large
+// products go through the FP64 GEMM, so the whole GPU works on it.
+// work: 64 * n * 2 + ceil(n/64) * 4096 doubles.
+cudaError_t dense_spd_inverse_blocked(double* A, double* X, double* out, int n, double* work, int* status,
+                                      const DenseDesc* d_desc_for_ltl, cudaStream_t st) {
+  const int NB = 64;
+  const int nbk = (n + NB - 1) / NB;
+  double* Dinv = work;                       // nbk x 64 x 64
+  double* R = work + (int64_t)nbk * 4096;    // 64 x n
+  cudaError_t e;
+  for (int kb = 0; kb < nbk; ++kb) {
+    const int c0 = kb * NB, nb = std::min(NB, n - c0);
+    k_diag_block<<<1, 256, 0, st>>>(A, n, c0, nb, Dinv + (int64_t)kb * 4096, status, 999999);
+    note_launches(1);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    const int r0 = c0 + nb, rest = n - r0;
+    if (rest <= 0) break;
+    // panel: L21 = A21 L11^{-T}   (in place: each CTA owns its 64 rows and all nb columns)
+    GemmDesc p{};
+    p.A = A + (int64_t)r0 * n + c0; p.B = Dinv + (int64_t)kb * 4096; p.C = A + (int64_t)r0 * n + c0;
+    p.M = rest; p.N = nb; p.K = nb;
+    p.ars = n; p.acs = 1; p.brs = 1; p.bcs = 64; p.crs = n; p.ccs = 1;
+    if ((e = dgemm_split(p, 1, nullptr, 1.0, 0.0, st)) != cudaSuccess) return e;
+    // trailing update: A22 -= L21 L21^T
+    GemmDesc t{};
+    t.A = A + (int64_t)r0 * n + c0; t.B = A + (int64_t)r0 * n + c0; t.C = A + (int64_t)r0 * n + r0;
+    t.M = rest; t.N = rest; t.K = nb;
+    t.ars = n; t.acs = 1; t.brs = 1; t.bcs = n; t.crs = n; t.ccs = 1;
+    if ((e = dgemm_split(t, 1, nullptr, -1.0, 1.0, st)) != cudaSuccess) return e;
+  }
+  // X = L^{-1}: X_ii = Dinv_i; X[i, 0:i] = -Dinv_i (L[i, 0:i] X[0:i, 0:i])
+  if ((e = cudaMemsetAsync(X, 0, sizeof(double) * (size_t)n * n, st)) != cudaSuccess) return e;
+  for (int ib = 0; ib < nbk; ++ib) {
+    const int r0 = ib * NB, nb = std::min(NB, n - r0);
+    k_copy_rows<<<16, 256, 0, st>>>(Dinv + (int64_t)ib * 4096, 64, X + (int64_t)r0 * n + r0, n, nb, nb, 1.0);
+    note_launches(1);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    if (r0 == 0) continue;
+    GemmDesc a{};   // R = L[i, 0:r0] X[0:r0, 0:r0]
+    a.A = A + (int64_t)r0 * n; a.B = X; a.C = R;
+    a.M = nb; a.N = r0; a.K = r0;
+    a.ars = n; a.acs = 1; a.brs = n; a.bcs = 1; a.crs = n; a.ccs = 1;
+    if ((e = dgemm_split(a, 1, nullptr, 1.0, 0.0, st)) != cudaSuccess) return e;
+    GemmDesc b{};   // X[i, 0:r0] = -Dinv_i R
+    b.A = Dinv + (int64_t)ib * 4096; b.B = R; b.C = X + (int64_t)r0 * n;
+    b.M = nb; b.N = r0; b.K = nb;
+    b.ars = 64; b.acs = 1; b.brs = n; b.bcs = 1; b.crs = n; b.ccs = 1;
+    if ((e = dgemm_split(b, 1, nullptr, -1.0, 0.0, st)) != cudaSuccess) return e;
+  }
+  dim3 g((n + 15) / 16, (n + 15) / 16, 1);
+  k_lt_l<<<g, 256, 0, st>>>(d_desc_for_ltl);
+  note_launches(1);
+  (void)out;
+  return cudaGetLastError();
+}
 
 cudaError_t launch_band_chol(const Ctx& c, cudaStream_t st) {
   int maxbw = 1;

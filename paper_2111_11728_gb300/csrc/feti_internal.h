@@ -193,6 +193,12 @@ struct Ctx {
   double* d_Kbar = nullptr;      // [n_coarse^2]
   double* d_Kbar_L = nullptr;    // [n_coarse^2] inverse Cholesky factor (work)
   double* d_Kbar_inv = nullptr;  // [n_coarse^2] explicit inverse
+  double* d_coarse_work = nullptr;   // blocked coarse factorisation work
+  // precision form (FETI_TF32)
+  float* d_fmem = nullptr;       // FP32 copies at the module offsets: Fhat at M.F, Shat at M.W
+  double* d_sqrtDF = nullptr;    // [n_b_total] sqrt(diag F_s)
+  double* d_sqrtDS = nullptr;    // [n_b_total] sqrt(diag S_s)
+  double *d_rout = nullptr, *d_zout = nullptr, *d_dl = nullptr;   // refinement vectors
   double* d_fbar = nullptr;      // [n_primal]
   int n_coarse = 0;
   double* d_G = nullptr;         // TFETI: dense G [n_coarse x n_lam]
@@ -210,6 +216,7 @@ struct Ctx {
   double* d_scalar = nullptr;    // small device scalars
   int* d_status = nullptr;       // device status word
   int* d_kdev = nullptr;         // rank from the rank-revealing factorization
+  int* d_perm = nullptr;         // its pivot order
   double* d_red = nullptr;       // reduction partials (>= 1024)
   // block buffers for the dual operator
   int blk_cap = 0;

@@ -20,13 +20,20 @@ void finish_gemm_profile(GemmProfile* p, double* flops, double* ms, int64_t* cou
 
 // C = alpha * A B + beta * C with element (i,k) of A at A[i*ars + k*acs],
 // (k,j) of B at B[k*brs + j*bcs] and (i,j) of C at C[i*crs + j*ccs].
+//
+// tri = 1: only tiles on or below the diagonal of C are computed (symmetric
+//          products; the strictly upper part of C is left untouched).
+// tri = 2: B is upper triangular (B(k, j) = 0 for k > j): each column tile
+//          stops its K loop after its last column.
+// acol (optional): column k of A is stored at A + acol[k] * acs.
 struct GemmDesc {
   const double* A;
   const double* B;
   double* C;
   int M, N, K;
-  int pad;
+  int tri;
   int64_t ars, acs, brs, bcs, crs, ccs;
+  const int* acol;
 };
 
 // Batched FP64 GEMM over n_batch descriptors living in device memory.
@@ -74,6 +81,11 @@ struct DenseDesc {
 cudaError_t dense_spd_inverse(const DenseDesc* d_desc, const DenseDesc* h_desc, int count, int* d_status,
                               cudaStream_t st);
 // 0: W = S (the whole b+c Schur complement); 1: Kb = symmetrised trailing block of W
+// One large SPD matrix (the coarse problem): blocked multi-CTA Cholesky, L^{-1}
+// and out = L^{-T} L^{-1} through the FP64 GEMM.  X receives L^{-1}; the
+// device descriptor must describe (Linv = X, out, n).
+cudaError_t dense_spd_inverse_blocked(double* A, double* X, double* out, int n, double* work, int* status,
+                                      const DenseDesc* d_desc_for_ltl, cudaStream_t st);
 cudaError_t launch_copy_block(const Ctx& c, int which, cudaStream_t st);
 cudaError_t launch_coarse_assemble_impl(const Ctx& c, const int* d_c_sub, const int64_t* d_c_off, double* K,
                                         cudaStream_t st);
@@ -102,10 +114,12 @@ cudaError_t batched_gemv_F(Ctx& c, const double* xb, double* yb, cudaStream_t st
 cudaError_t batched_gemv(const Ctx& c, int which, const double* xb, double* yb, double beta, cudaStream_t st);
 
 // ---- Krylov helpers (krylov.cu) ------------------------------------------------
-// Rank-revealing pivoted Cholesky of Delta (m x m, column-major ld): writes
-// T (m x k, column-major ld m) = N^T [L~^{-T}; 0] and k into *d_k.
+// Rank-revealing pivoted Cholesky of Delta (m x m, column-major ld; only its
+// lower triangle is read): writes U = L~^{-T} (k x k upper triangular,
+// column-major ld m) into T, the pivot order into d_perm[0..m) and k into
+// *d_k, so that W N^T [L~^{-T}; 0] = W[:, perm[0..k)] U.
 cudaError_t rr_cholesky(const double* Delta, int m, int ld, double rr_tol, double* work, double* T,
-                        int* d_k, cudaStream_t st);
+                        int* d_k, int* d_perm, cudaStream_t st);
 // lam_t += W g ; then r -= Q g, or qout = Q g when qout is not null
 // (W, Q column-major n x k with leading dimension ld)
 cudaError_t step_update(const double* W, const double* Q, int64_t ld, int64_t n, int k, const double* g,
@@ -118,6 +132,16 @@ cudaError_t axpby(int64_t n, double a, const double* x, double b, double* y, cud
 cudaError_t gemv_t(const double* W, int64_t ld, int64_t n, int k, const double* r, double* out, cudaStream_t st);
 // y = A x (+ beta y), A row-major n x n with leading dimension ld
 cudaError_t gemv_dense(const double* A, int n, int ld, const double* x, double* y, double beta, cudaStream_t st);
+
+// ---- precision form (tc_apply.cu) -------------------------------------------------
+size_t tc_apply_smem_bytes();
+cudaError_t tc_prepare(const Ctx& c, cudaStream_t st);   // Fhat, Shat (FP32) and sqrt-diagonals
+// Yb = D^{1/2} Fhat D^{1/2} B^T X (tcgen05 kind::tf32); rows >= n_b untouched
+cudaError_t tc_apply_local(const Ctx& c, const double* X, int64_t ldx, int m, double* Yb, cudaStream_t st);
+cudaError_t lowp_gemv_S(const Ctx& c, const double* xb, double* yb, cudaStream_t st);
+// Yb(s) += F_rc,s V[c_glob(s), :] with a thin kernel (no tile padding)
+cudaError_t corner_expand_thin(Ctx& c, const double* V, int m, double* Yb, cudaStream_t st);
+cudaError_t precond_apply_lowp(Ctx& c, const double* r, double* Z, int64_t ldz, double* z, cudaStream_t st);
 
 // ---- recovery (recover.cu) ------------------------------------------------------
 cudaError_t recover_fetidp(Ctx& c, const double* lam, cudaStream_t st);

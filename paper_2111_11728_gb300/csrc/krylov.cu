@@ -15,15 +15,18 @@ constexpr double EPS2 = 4.930380657631324e-32;   // (2^-52)^2
 // Single CTA.  work holds 2*m*m + m doubles.  Pivot rule: the largest ratio of
 // the remaining Schur-complement diagonal to the column's initial diagonal,
 // exact ties to the lowest original column; stop when it is <= rr_tol.
+// Only the lower triangle of the remaining block is updated; the current
+// column of L is staged in shared memory.
 // Output T (column-major, ld m, k columns) = N^T [L~^{-T}; 0] and *d_k = k.
 __global__ void __launch_bounds__(1024) k_rr_chol(const double* __restrict__ Delta, int m, int ld, double rr_tol,
                                                   double* __restrict__ work, double* __restrict__ T,
-                                                  int* __restrict__ d_k) {
-  double* A = work;              // m x m row-major
+                                                  int* __restrict__ d_k, int* __restrict__ perm_out) {
+  double* A = work;              // m x m row-major, lower triangle live
   double* L = work + (int64_t)m * m;
   double* d0 = L + (int64_t)m * m;
   __shared__ int perm[1024];
   __shared__ unsigned char alive[1024];
+  __shared__ double lcol[1024];
   __shared__ double rv[32];
   __shared__ int rp[32], rpos[32];
   __shared__ int s_bt, s_k;
@@ -33,7 +36,7 @@ __global__ void __launch_bounds__(1024) k_rr_chol(const double* __restrict__ Del
 
   for (int64_t e = tid; e < (int64_t)m * m; e += nt) {
     const int i = (int)(e / m), j = (int)(e % m);
-    A[e] = 0.5 * (Delta[i + (int64_t)j * ld] + Delta[j + (int64_t)i * ld]);
+    A[e] = j <= i ? Delta[i + (int64_t)j * ld] : 0.0;      // lower triangle of Delta
     L[e] = 0.0;
   }
   __syncthreads();
@@ -86,18 +89,22 @@ __global__ void __launch_bounds__(1024) k_rr_chol(const double* __restrict__ Del
     __syncthreads();
     if (s_bt < 0 || !(s_best > rr_tol)) break;
     const int bt = s_bt;
-    // --- symmetric swap of positions j and bt ---------------------------------
+    // --- symmetric swap of positions j < bt in the live lower triangle --------
     if (bt != j) {
-      for (int t = tid; t < m; t += nt) {
-        const double a = A[(int64_t)j * m + t];
-        A[(int64_t)j * m + t] = A[(int64_t)bt * m + t];
-        A[(int64_t)bt * m + t] = a;
-      }
-      __syncthreads();
-      for (int t = tid; t < m; t += nt) {
-        const double a = A[(int64_t)t * m + j];
-        A[(int64_t)t * m + j] = A[(int64_t)t * m + bt];
-        A[(int64_t)t * m + bt] = a;
+      for (int t = j + tid; t < m; t += nt) {
+        if (t == j) {
+          const double a = A[(int64_t)j * m + j];
+          A[(int64_t)j * m + j] = A[(int64_t)bt * m + bt];
+          A[(int64_t)bt * m + bt] = a;
+        } else if (t < bt) {          // (t, j) <-> (bt, t)
+          const double a = A[(int64_t)t * m + j];
+          A[(int64_t)t * m + j] = A[(int64_t)bt * m + t];
+          A[(int64_t)bt * m + t] = a;
+        } else if (t > bt) {          // (t, j) <-> (t, bt)
+          const double a = A[(int64_t)t * m + j];
+          A[(int64_t)t * m + j] = A[(int64_t)t * m + bt];
+          A[(int64_t)t * m + bt] = a;
+        }
       }
       for (int t = tid; t < j; t += nt) {
         const double a = L[(int64_t)j * m + t];
@@ -107,38 +114,54 @@ __global__ void __launch_bounds__(1024) k_rr_chol(const double* __restrict__ Del
       if (tid == 0) { const int p = perm[j]; perm[j] = perm[bt]; perm[bt] = p; }
       __syncthreads();
     }
-    // --- column j of L and the trailing update --------------------------------
+    // --- column j of L and the trailing (lower) update -------------------------
     const double piv = sqrt(A[(int64_t)j * m + j]);
     const double rpiv = 1.0 / piv;
-    for (int t = j + tid; t < m; t += nt) L[(int64_t)t * m + j] = t == j ? piv : A[(int64_t)t * m + j] * rpiv;
+    for (int t = j + tid; t < m; t += nt) {
+      const double v = t == j ? piv : A[(int64_t)t * m + j] * rpiv;
+      L[(int64_t)t * m + j] = v;
+      lcol[t] = v;
+    }
     __syncthreads();
-    const int len = m - 1 - j;
-    for (int64_t e = tid; e < (int64_t)len * len; e += nt) {
-      const int a = j + 1 + (int)(e / len), b = j + 1 + (int)(e % len);
-      A[(int64_t)a * m + b] = fma(-L[(int64_t)a * m + j], L[(int64_t)b * m + j], A[(int64_t)a * m + b]);
+    for (int a = j + 1 + wid; a < m; a += nw) {
+      const double la = lcol[a];
+      double* row = A + (int64_t)a * m;
+      for (int b = j + 1 + lane; b <= a; b += 32) row[b] = fma(-la, lcol[b], row[b]);
     }
     if (tid == 0) s_k = j + 1;
     __syncthreads();
   }
   const int k = s_k;
-  // --- Linv = L~^{-1} (k x k, row-major, ld m) into A; one thread per column ----
-  for (int c = tid; c < k; c += nt) {
-    for (int i = 0; i < c; ++i) A[(int64_t)i * m + c] = 0.0;
-    A[(int64_t)c * m + c] = 1.0 / L[(int64_t)c * m + c];
-    for (int i = c + 1; i < k; ++i) {
-      double acc = 0.0;
-      for (int q = c; q < i; ++q) acc = fma(L[(int64_t)i * m + q], A[(int64_t)q * m + c], acc);
-      A[(int64_t)i * m + c] = -acc / L[(int64_t)i * m + i];
-    }
+  // --- X = L~^{-1} (k x k, row-major, ld m) into A, right-looking: row q of X
+  // is final once divided by L(q,q); it then updates every later row
+  // (warp per row, lanes over columns, row q staged in shared memory) ------
+  for (int64_t e = tid; e < (int64_t)k * k; e += nt) {
+    const int i = (int)(e / k), c = (int)(e % k);
+    A[(int64_t)i * m + c] = i == c ? 1.0 : 0.0;
   }
   __syncthreads();
-  // --- T[perm[j] + i*m] = Linv[i][j] for j < k; other rows zero ---------------
-  for (int64_t e = tid; e < (int64_t)m * k; e += nt) T[e] = 0.0;
-  __syncthreads();
+  for (int q = 0; q < k; ++q) {
+    const double rq = 1.0 / L[(int64_t)q * m + q];
+    for (int c = tid; c <= q; c += nt) {
+      const double v = A[(int64_t)q * m + c] * rq;
+      A[(int64_t)q * m + c] = v;
+      lcol[c] = v;
+    }
+    __syncthreads();
+    for (int i = q + 1 + wid; i < k; i += nw) {
+      const double li = L[(int64_t)i * m + q];
+      double* row = A + (int64_t)i * m;
+      for (int c = lane; c <= q; c += 32) row[c] = fma(-li, lcol[c], row[c]);
+    }
+    __syncthreads();
+  }
+  // --- U = L~^{-T}: U[jj + i*m] = Linv[i][jj] (upper triangular, column-major)
+  // and the pivot order; W N^T [L~^{-T}; 0] = W[:, perm[0..k)] U ------------
   for (int64_t e = tid; e < (int64_t)k * k; e += nt) {
     const int i = (int)(e / k), jj = (int)(e % k);
-    T[perm[jj] + (int64_t)i * m] = A[(int64_t)i * m + jj];
+    T[jj + (int64_t)i * m] = jj <= i ? A[(int64_t)i * m + jj] : 0.0;
   }
+  for (int t = tid; t < m; t += nt) perm_out[t] = perm[t];
   if (tid == 0) *d_k = k;
 }
 
@@ -222,9 +245,9 @@ __global__ void k_gemv_dense(const double* __restrict__ A, int n, int ld, const 
 }  // namespace
 
 cudaError_t rr_cholesky(const double* Delta, int m, int ld, double rr_tol, double* work, double* T, int* d_k,
-                        cudaStream_t st) {
+                        int* d_perm, cudaStream_t st) {
   if (m > 1024) return cudaErrorInvalidValue;
-  k_rr_chol<<<1, 1024, 0, st>>>(Delta, m, ld, rr_tol, work, T, d_k);
+  k_rr_chol<<<1, 1024, 0, st>>>(Delta, m, ld, rr_tol, work, T, d_k, d_perm);
   note_launches(1);
   return cudaGetLastError();
 }

@@ -29,7 +29,7 @@ def test_autograd_gradient_matches_oracle_and_fd():
     c = simp.compliance(rho, cp)
     c.backward()
     ud = direct_solve(p)
-    assert float(c) == pytest.approx(oracle_compliance(p, ud), rel=1e-9)
+    assert float(c.detach()) == pytest.approx(oracle_compliance(p, ud), rel=1e-9)
     g_ref = compliance_gradient(p, ud)
     g = rho.grad.cpu().numpy()
     assert np.linalg.norm(g - g_ref) <= 1e-8 * np.linalg.norm(g_ref)
