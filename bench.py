@@ -52,6 +52,8 @@ def parse():
     ap.add_argument("--no-accuracy", action="store_true")
     ap.add_argument("--no-forms", action="store_true")
     ap.add_argument("--forms-rho-lo", type=float, default=0.1)
+    ap.add_argument("--no-batch", action="store_true")
+    ap.add_argument("--batch-problems", type=int, default=64)
     return ap.parse_args()
 
 
@@ -157,26 +159,28 @@ def apply_timing(fg, torch, stream, flush, s, n, m, reps=5):
 
 
 def compare_forms(a, fg, torch, dev, stream, flush):
-    """The precision form (TF32 tensor-core block products inside FP64 refinement
-    on the dual residual) against the plain FP64 form at equal accuracy (same
-    FP64 relative dual residual), on the same modular layout with densities
-    {rho_lo, 1} (contrast (1/rho_lo)^3), where the reduced-precision blocks
-    still carry the information the solve needs."""
+    """The precision form (tensor-core block products inside FP64 refinement on
+    the dual residual; one TF32 pass, or the three-pass split-TF32 product)
+    against the plain FP64 form at equal accuracy (same FP64 relative dual
+    residual), on the same modular layout with densities {rho_lo, 1}
+    (contrast (1/rho_lo)^3), where the reduced-precision blocks still carry the
+    information the solve needs.  Iterations are capped at 120 per solve."""
     p = workloads.config2(tiles=a.tiles, elems=a.elems)
     p.rho = np.where(p.rho < 0.5, a.forms_rho_lo, 1.0)
     p.Emin = 1e-9
     rho_d = torch.from_numpy(p.rho).to(dev)
     f_d = torch.from_numpy(p.f).to(dev)
     out = {"workload": f"same layout, densities {{{a.forms_rho_lo}, 1}}, contrast {1 / a.forms_rho_lo ** 3:.0e}",
-           "rel_tol": a.tol}
+           "rel_tol": a.tol, "max_iter": 120}
     sols = {}
-    for name, prec in (("fp64", fg.FETI_FP64), ("tf32", fg.FETI_TF32)):
-        s = fg.Solver(fg.FETI_FETIDP, fg.FETI_SCALING_K, fg.FETI_RRS, tol=a.tol, max_iter=500,
+    forms = (("fp64", fg.FETI_FP64), ("tf32x3", fg.FETI_TF32X3), ("tf32", fg.FETI_TF32))
+    for name, prec in forms:
+        s = fg.Solver(fg.FETI_FETIDP, fg.FETI_SCALING_K, fg.FETI_RRS, tol=a.tol, max_iter=120,
                       stream=stream.cuda_stream, precision=prec)
         s.setup(p, rho=rho_d, f=f_d, on_device=True)
         u = torch.empty(p.n_dofs, dtype=torch.float64, device=dev)
         times, st = [], None
-        for k in range(4):
+        for k in range(2):
             flush.zero_()
             torch.cuda.synchronize()
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -195,9 +199,98 @@ def compare_forms(a, fg, torch, dev, stream, flush):
                      "refinements": st.refinements, "f_applies": st.f_applies, "converged": bool(st.converged),
                      "apply_256_cols_ms": ms_apply, "apply_f_applies_per_s": 256 / (ms_apply / 1e3)}
         s.close()
-    out["tf32_vs_fp64_rel_diff"] = float(np.linalg.norm(sols["tf32"] - sols["fp64"]) / np.linalg.norm(sols["fp64"]))
-    out["speedup_time_to_solve"] = out["fp64"]["time_to_solve_ms"] / out["tf32"]["time_to_solve_ms"]
-    out["speedup_apply"] = out["fp64"]["apply_256_cols_ms"] / out["tf32"]["apply_256_cols_ms"]
+    ref = sols["fp64"]
+    for name, _ in forms[1:]:
+        out[name]["rel_diff_vs_fp64"] = float(np.linalg.norm(sols[name] - ref) / np.linalg.norm(ref))
+        out[name]["speedup_time_to_solve"] = out["fp64"]["time_to_solve_ms"] / out[name]["time_to_solve_ms"]
+        out[name]["speedup_apply"] = out["fp64"]["apply_256_cols_ms"] / out[name]["apply_256_cols_ms"]
+    return out
+
+
+def compare_batch(a, fg, torch, dev, stream):
+    """The batching form: the uneven multi-problem workload (tile grids drawn
+    from 4x4..24x24 subdomains of 16x16..48x48 elements, thresholded smoothed
+    Gaussian densities, Emin 1e-6) solved in one context -- every launch covers
+    all problems, one PCG per problem advanced by a replayed CUDA graph --
+    against the same problems solved one context at a time, both FETI-DP +
+    k-scaling + PCG in FP64 at the same relative dual residual."""
+    probs = workloads.config3(n_problems=a.batch_problems)
+    keep, structs = [], []
+    for p in probs:
+        rho = torch.from_numpy(p.rho).to(dev)
+        f = torch.from_numpy(p.f).to(dev)
+        d = np.ascontiguousarray(p.dirichlet, np.uint8)
+        keep += [rho, f, d]
+        structs.append(fg.make_problem(p.dim, p.tiles, p.elems, p.E0, p.Emin, p.nu, p.p, rho, d, f, True))
+
+    def opts():
+        o = fg.feti_options_default()
+        o.method, o.scaling, o.krylov, o.tol, o.max_iter = fg.FETI_FETIDP, fg.FETI_SCALING_K, fg.FETI_PCG, a.tol, 2000
+        return o
+
+    def ev():
+        return torch.cuda.Event(enable_timing=True)
+
+    n_dofs = sum(p.n_dofs for p in probs)
+    out = {"workload": f"{len(probs)} uneven 2D Q4 problems, {n_dofs} DOF, "
+                       f"{sum(p.tiles[0] * p.tiles[1] for p in probs)} subdomains", "rel_tol": a.tol}
+    # batched: one context
+    ctx = fg.feti_create(opts(), stream.cuda_stream)
+    t0 = time.perf_counter()
+    fg.feti_setup_batch(ctx, structs)
+    torch.cuda.synchronize()
+    setup_s = time.perf_counter() - t0
+    u_b = torch.empty(n_dofs, dtype=torch.float64, device=dev)
+    for k in range(2):
+        torch.cuda.synchronize()
+        e = [ev() for _ in range(3)]
+        e[0].record(stream)
+        fg.feti_factorize(ctx)
+        e[1].record(stream)
+        _, st = fg.feti_solve_dual(ctx, allow_notconv=True)
+        fg.feti_recover_displacements(ctx, u_b, True)
+        e[2].record(stream)
+        torch.cuda.synchronize()
+    res = [fg.feti_problem_result(ctx, q) for q in range(len(probs))]
+    its = [r[3].iterations for r in res]
+    out["batched"] = {"factorize_ms": e[0].elapsed_time(e[1]), "solve_and_recover_ms": e[1].elapsed_time(e[2]),
+                      "total_ms": e[0].elapsed_time(e[2]), "host_setup_s": setup_s,
+                      "iterations_max": max(its), "iterations_sum": sum(its),
+                      "converged": all(bool(r[3].converged) for r in res),
+                      "f_applies_per_s": sum(its) / (e[1].elapsed_time(e[2]) / 1e3)}
+    out["batched"]["problems_per_s"] = len(probs) / (out["batched"]["total_ms"] / 1e3)
+    u_b = u_b.cpu().numpy()
+    offs = [r[0] for r in res]
+    fg.feti_destroy(ctx)
+    # one context per problem, solved in turn
+    fact_ms, solve_ms, its1, worst = 0.0, 0.0, [], 0.0
+    for q, p in enumerate(probs):
+        c1 = fg.feti_create(opts(), stream.cuda_stream)
+        fg.feti_setup_batch(c1, [structs[q]])
+        u1 = torch.empty(p.n_dofs, dtype=torch.float64, device=dev)
+        for k in range(2 if q == 0 else 1):
+            torch.cuda.synchronize()
+            e = [ev() for _ in range(3)]
+            e[0].record(stream)
+            fg.feti_factorize(c1)
+            e[1].record(stream)
+            _, st1 = fg.feti_solve_dual(c1, allow_notconv=True)
+            fg.feti_recover_displacements(c1, u1, True)
+            e[2].record(stream)
+            torch.cuda.synchronize()
+        fact_ms += e[0].elapsed_time(e[1])
+        solve_ms += e[1].elapsed_time(e[2])
+        its1.append(st1.iterations)
+        uq = u1.cpu().numpy()
+        worst = max(worst, float(np.linalg.norm(u_b[offs[q]:offs[q] + p.n_dofs] - uq) / np.linalg.norm(uq)))
+        fg.feti_destroy(c1)
+    out["one_at_a_time"] = {"factorize_ms": fact_ms, "solve_and_recover_ms": solve_ms, "total_ms": fact_ms + solve_ms,
+                            "iterations_max": max(its1), "iterations_sum": sum(its1),
+                            "f_applies_per_s": sum(its1) / (solve_ms / 1e3),
+                            "problems_per_s": len(probs) / ((fact_ms + solve_ms) / 1e3)}
+    out["max_rel_diff_batched_vs_single"] = worst
+    out["speedup_total"] = out["one_at_a_time"]["total_ms"] / out["batched"]["total_ms"]
+    out["speedup_solve"] = out["one_at_a_time"]["solve_and_recover_ms"] / out["batched"]["solve_and_recover_ms"]
     return out
 
 
@@ -329,6 +422,9 @@ def run_ours(a, rank, world):
     forms = None
     if not a.no_forms:
         forms = compare_forms(a, fg, torch, dev, stream, flush)
+    batch = None
+    if not a.no_batch and world == 1:
+        batch = compare_batch(a, fg, torch, dev, stream)
 
     gemm_tflops = gf / (gms / 1e3) / 1e12 if gms > 0 else None
     out = {
@@ -348,7 +444,7 @@ def run_ours(a, rank, world):
                      "kernel_share_of_step": (gms / 1e3) / t_steps if t_steps > 0 else None,
                      "launches": gn},
         "e2e": e2e, "gpu_launches": int(launches), "clocks": clk, "wall_s": wall,
-        "forms": forms,
+        "forms": forms, "batch_form": batch,
     }
     s.close()
     return out

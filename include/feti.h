@@ -59,20 +59,23 @@ typedef enum {
 enum { FETI_TFETI = 0, FETI_FETIDP = 1 };                 /* Sections 2.1 / 2.2 */
 enum { FETI_SCALING_K = 0, FETI_SCALING_MULT = 1 };       /* Eq. 15 / multiplicity */
 enum { FETI_PCG = 0, FETI_FO = 1, FETI_RRS = 2 };         /* Sections 3.2, 3.3 */
-enum { FETI_FP64 = 0, FETI_TF32 = 1 };                    /* dense block-product precision */
+enum { FETI_FP64 = 0, FETI_TF32 = 1, FETI_TF32X3 = 2 };  /* dense block-product precision */
 
 typedef struct {
   int method;          /* FETI_TFETI or FETI_FETIDP */
   int scaling;         /* FETI_SCALING_K or FETI_SCALING_MULT */
   int krylov;          /* FETI_PCG, FETI_FO or FETI_RRS */
-  int precision;       /* FETI_FP64 (default) or FETI_TF32: the dense F_s / S_s block products in
-                          TF32 on the tensor cores (FP32 accumulation) inside FP64 iterative
-                          refinement on the dual residual; Gram and orthogonalization stay FP64 */
+  int precision;       /* FETI_FP64 (default), FETI_TF32 or FETI_TF32X3: the dense F_s block
+                          products on the tensor cores with FP32 accumulation -- one TF32 pass, or
+                          the three-pass split (hi*hi + hi*lo + lo*hi, FP32-class accuracy) --
+                          and FP32 S_s blocks, inside FP64 iterative refinement on the dual
+                          residual; Gram and orthogonalization stay FP64 */
   int max_iter;        /* Krylov iteration cap (default 500) */
   int dedup_modules;   /* 1: factorize identical modules once (Section 1) */
   double tol;          /* relative tolerance on sqrt(r^T z) (default 1e-6) */
   double rr_tol;       /* rank-revealing cutoff on the remaining/initial pivot ratio (1e-10) */
-  double inner_tol;    /* FETI_TF32: relative tolerance of each low-precision inner solve (1e-2) */
+  double inner_tol;    /* FETI_TF32: relative tolerance of each low-precision inner solve (1e-2);
+                          each inner solve is also capped at 30 iterations */
   int max_refine;      /* FETI_TF32: cap on the FP64 refinement steps (30) */
 } feti_options;
 
@@ -111,6 +114,25 @@ feti_status feti_create(feti_ctx** out, const feti_options* opt, void* stream);
  * May be called again to replace the problem (resets the call order).
  * Errors: FETI_EINVAL for inconsistent sizes or null pointers. */
 feti_status feti_setup_subdomains(feti_ctx* ctx, const feti_problem* prob);
+
+/* Set up a batch of n_problems independent state problems of uneven size in
+ * one context (the batching form; the paper solves one problem at a time).
+ * Every kernel launch then covers all problems; the problems keep their own
+ * multipliers, primal DOFs and coarse problems, and feti_solve_dual runs one
+ * PCG per problem with all per-problem scalars on the device, replaying a
+ * CUDA graph of one iteration.  Requires FETI_FETIDP, FETI_PCG and FETI_FP64,
+ * and equal E0, Emin, nu, p and dim across the batch (FETI_ENOTSUP / EINVAL
+ * otherwise).  Vectors of the batch (lambda, u, rho, dc/drho) are the
+ * problems' vectors concatenated in input order; feti_problem_result gives
+ * each problem's offsets and statistics. */
+feti_status feti_setup_batch(feti_ctx* ctx, const feti_problem* probs, int n_problems);
+
+/* Per-problem results of a batch (or of a single problem, p = 0): offsets of
+ * problem p in the concatenated DOF, element and multiplier vectors, its
+ * Krylov statistics and, after feti_recover_displacements, its compliance
+ * f_p^T u_p.  Each output pointer may be NULL. */
+feti_status feti_problem_result(const feti_ctx* ctx, int p, int64_t* dof_offset, int64_t* elem_offset,
+                                int64_t* lambda_offset, feti_stats* stats, double* compliance);
 
 /* Replace the element densities (same mesh, same boundary conditions):
  * `rho` has n_elements entries, host or device per on_device.  Requires a
@@ -183,7 +205,10 @@ enum {
   FETI_Q_N_LAMBDA = 0, FETI_Q_N_SUBDOMAINS = 1, FETI_Q_N_PRIMAL = 2, FETI_Q_N_MODULES = 3,
   FETI_Q_N_B_TOTAL = 4, FETI_Q_N_DOFS = 5, FETI_Q_N_ELEMENTS = 6, FETI_Q_MAX_NB = 7,
   FETI_Q_DEVICE_BYTES = 8, FETI_Q_N_RBM = 9,
-  FETI_Q_LAUNCHES = 10   /* process-wide count of kernels this library has launched (any ctx state) */
+  FETI_Q_LAUNCHES = 10,  /* process-wide count of kernels this library has launched (any ctx state) */
+  FETI_Q_N_PROBLEMS = 11,
+  FETI_Q_GEMV_CONFIG = 12  /* autotuned launch shape of the per-subdomain matrix-vector kernel (batches):
+                              warps per CTA + 100 if vector loads; 0 = default */
 };
 feti_status feti_query(const feti_ctx* ctx, int key, int64_t* value);
 

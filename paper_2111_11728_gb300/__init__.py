@@ -20,15 +20,17 @@ FETI_OK, FETI_EINVAL, FETI_ENOMEM, FETI_ESTATE, FETI_ENOTCONV, FETI_EBREAKDOWN, 
 FETI_TFETI, FETI_FETIDP = 0, 1
 FETI_SCALING_K, FETI_SCALING_MULT = 0, 1
 FETI_PCG, FETI_FO, FETI_RRS = 0, 1, 2
-FETI_FP64, FETI_TF32 = 0, 1
+FETI_FP64, FETI_TF32, FETI_TF32X3 = 0, 1, 2
 (FETI_Q_N_LAMBDA, FETI_Q_N_SUBDOMAINS, FETI_Q_N_PRIMAL, FETI_Q_N_MODULES, FETI_Q_N_B_TOTAL, FETI_Q_N_DOFS,
- FETI_Q_N_ELEMENTS, FETI_Q_MAX_NB, FETI_Q_DEVICE_BYTES, FETI_Q_N_RBM, FETI_Q_LAUNCHES) = range(11)
+ FETI_Q_N_ELEMENTS, FETI_Q_MAX_NB, FETI_Q_DEVICE_BYTES, FETI_Q_N_RBM, FETI_Q_LAUNCHES, FETI_Q_N_PROBLEMS,
+ FETI_Q_GEMV_CONFIG) = range(13)
 
 STATUS_NAMES = {0: "FETI_OK", 1: "FETI_EINVAL", 2: "FETI_ENOMEM", 3: "FETI_ESTATE", 4: "FETI_ENOTCONV",
                 5: "FETI_EBREAKDOWN", 6: "FETI_ECUDA", 7: "FETI_ENOTSUP"}
 
 EXPORTS = [
-    "feti_options_default", "feti_create", "feti_setup_subdomains", "feti_set_density", "feti_factorize",
+    "feti_options_default", "feti_create", "feti_setup_subdomains", "feti_setup_batch", "feti_problem_result",
+    "feti_set_density", "feti_factorize",
     "feti_solve_dual", "feti_recover_displacements", "feti_compliance_grad", "feti_apply_dual",
     "feti_apply_precond", "feti_apply_precond_noalloc", "feti_query", "feti_profile_begin", "feti_profile_end", "feti_lambda_layout", "feti_local_blocks", "feti_last_error",
     "feti_destroy",
@@ -70,6 +72,9 @@ def lib():
             "feti_options_default": ([ctypes.POINTER(feti_options)], i),
             "feti_create": ([ctypes.POINTER(vp), ctypes.POINTER(feti_options), vp], i),
             "feti_setup_subdomains": ([vp, ctypes.POINTER(feti_problem)], i),
+            "feti_setup_batch": ([vp, ctypes.POINTER(feti_problem), i], i),
+            "feti_problem_result": ([vp, i, ctypes.POINTER(i64), ctypes.POINTER(i64), ctypes.POINTER(i64),
+                                     ctypes.POINTER(feti_stats), ctypes.POINTER(d)], i),
             "feti_set_density": ([vp, vp, i], i),
             "feti_factorize": ([vp], i),
             "feti_solve_dual": ([vp, vp, ctypes.POINTER(feti_stats)], i),
@@ -158,6 +163,22 @@ def make_problem(dim, tiles, elems, E0, Emin, nu, p, rho, dirichlet, f, on_devic
 
 def feti_setup_subdomains(ctx, problem):
     return _check(ctx, lib().feti_setup_subdomains(ctx, ctypes.byref(problem)))
+
+
+def feti_setup_batch(ctx, problems):
+    """problems: a list of feti_problem structures (see make_problem)."""
+    arr = (feti_problem * len(problems))(*problems)
+    return _check(ctx, lib().feti_setup_batch(ctx, arr, len(problems)))
+
+
+def feti_problem_result(ctx, p):
+    """Returns (dof_offset, elem_offset, lambda_offset, stats, compliance) of problem p."""
+    a, b, c = ctypes.c_int64(0), ctypes.c_int64(0), ctypes.c_int64(0)
+    st = feti_stats()
+    comp = ctypes.c_double(0.0)
+    _check(ctx, lib().feti_problem_result(ctx, int(p), ctypes.byref(a), ctypes.byref(b), ctypes.byref(c),
+                                          ctypes.byref(st), ctypes.byref(comp)))
+    return a.value, b.value, c.value, st, comp.value
 
 
 def feti_set_density(ctx, rho, on_device):

@@ -209,6 +209,11 @@ feti_status project(Ctx& c, double* X, int64_t ldx, int m) {
 // blocked multi-CTA factorisation otherwise.
 cudaError_t coarse_inverse(Ctx& c) {
   const int n = c.n_coarse;
+  if (c.hp.n_prob > 1) {
+    std::vector<DenseDesc> hd(c.hp.n_prob);
+    for (int q = 0; q < c.hp.n_prob; ++q) hd[q].n = c.hp.prob_primal_off[q + 1] - c.hp.prob_primal_off[q];
+    return dense_spd_inverse(c.d_dense_coarse_batch, hd.data(), c.hp.n_prob, c.d_status, c.stream);
+  }
   if (n <= 128) {
     DenseDesc hd{};
     hd.n = n;
@@ -222,17 +227,18 @@ cudaError_t coarse_inverse(Ctx& c) {
 feti_status apply_dual(Ctx& c, const double* X, int64_t ldx, int m, double* Y, int64_t ldy) {
   TRY(ensure_blocks(c, m));
   CU(gather_lam_to_b(c, X, ldx, m, c.d_Xb, c.stream));
+  // one column: matrix-vector kernels instead of padded GEMM tiles
+  auto local = [&]() -> cudaError_t {
+    return m == 1 ? batched_gemv(c, 0, c.d_Xb, c.d_Yb, 0.0, c.stream) : apply_local_F(c, c.d_Xb, c.d_Yb, m, 0.0, c.stream);
+  };
   if (c.hp.method == FETI_FETIDP && c.hp.n_primal > 0) {
-    const int np = c.hp.n_primal;
     CU(corner_reduce(c, c.d_Xb, m, c.d_Cb, c.d_Vraw, c.stream));
-    GemmDesc d{};
-    d.A = c.d_Kbar_inv; d.B = c.d_Vraw; d.C = c.d_V; d.M = np; d.N = m; d.K = np;
-    d.ars = np; d.acs = 1; d.brs = 1; d.bcs = np; d.crs = 1; d.ccs = np;
-    CU(dgemm_split(d, 1, nullptr, 1.0, 0.0, c.stream));
-    CU(apply_local_F(c, c.d_Xb, c.d_Yb, m, 0.0, c.stream));
-    CU(corner_expand(c, c.d_V, m, c.d_Vc, c.d_Yb, c.stream));
+    CU(coarse_apply(c, c.d_Vraw, c.d_V, m, c.stream));
+    CU(local());
+    if (m == 1) CU(corner_expand_thin(c, c.d_V, m, c.d_Yb, c.stream));
+    else CU(corner_expand(c, c.d_V, m, c.d_Vc, c.d_Yb, c.stream));
   } else {
-    CU(apply_local_F(c, c.d_Xb, c.d_Yb, m, 0.0, c.stream));
+    CU(local());
   }
   CU(scatter_b_to_lam(c, c.d_Yb, m, Y, ldy, c.stream));
   return FETI_OK;
@@ -243,13 +249,9 @@ feti_status apply_dual(Ctx& c, const double* X, int64_t ldx, int m, double* Y, i
 feti_status apply_dual_lowp(Ctx& c, const double* X, int64_t ldx, int m, double* Y, int64_t ldy) {
   TRY(ensure_blocks(c, m));
   if (c.hp.method == FETI_FETIDP && c.hp.n_primal > 0) {
-    const int np = c.hp.n_primal;
     CU(gather_lam_to_b(c, X, ldx, m, c.d_Xb, c.stream));
     CU(corner_reduce(c, c.d_Xb, m, c.d_Cb, c.d_Vraw, c.stream));
-    GemmDesc d{};
-    d.A = c.d_Kbar_inv; d.B = c.d_Vraw; d.C = c.d_V; d.M = np; d.N = m; d.K = np;
-    d.ars = np; d.acs = 1; d.brs = 1; d.bcs = np; d.crs = 1; d.ccs = np;
-    CU(dgemm_split(d, 1, nullptr, 1.0, 0.0, c.stream));
+    CU(coarse_apply(c, c.d_Vraw, c.d_V, m, c.stream));
     CU(tc_apply_local(c, X, ldx, m, c.d_Yb, c.stream));
     CU(corner_expand_thin(c, c.d_V, m, c.d_Yb, c.stream));
   } else {
@@ -345,8 +347,8 @@ feti_status feti_create(feti_ctx** out, const feti_options* opt, void* stream) {
       (o.scaling != FETI_SCALING_K && o.scaling != FETI_SCALING_MULT) ||
       (o.krylov < FETI_PCG || o.krylov > FETI_RRS) || o.max_iter < 0 || !(o.tol >= 0.0) || !(o.rr_tol >= 0.0))
     return FETI_EINVAL;
-  if (o.precision != FETI_FP64 && o.precision != FETI_TF32) return FETI_EINVAL;
-  if (o.precision == FETI_TF32 && !(o.inner_tol > 0.0 && o.inner_tol < 1.0 && o.max_refine > 0)) return FETI_EINVAL;
+  if (o.precision != FETI_FP64 && o.precision != FETI_TF32 && o.precision != FETI_TF32X3) return FETI_EINVAL;
+  if (o.precision != FETI_FP64 && !(o.inner_tol > 0.0 && o.inner_tol < 1.0 && o.max_refine > 0)) return FETI_EINVAL;
   feti_ctx* ctx = new (std::nothrow) feti_ctx;
   if (!ctx) return FETI_ENOMEM;
   Ctx& c = ctx->c;
@@ -363,6 +365,8 @@ feti_status feti_create(feti_ctx** out, const feti_options* opt, void* stream) {
 
 void feti_destroy(feti_ctx* ctx) {
   if (!ctx) return;
+  if (ctx->c.cap_stream) cudaStreamDestroy(ctx->c.cap_stream);
+  if (ctx->c.cap_event) cudaEventDestroy(ctx->c.cap_event);
   free_all(ctx->c);
   if (ctx->c.h_pin) cudaFreeHost(ctx->c.h_pin);
   delete ctx;
@@ -370,34 +374,58 @@ void feti_destroy(feti_ctx* ctx) {
 
 const char* feti_last_error(const feti_ctx* ctx) { return ctx ? ctx->c.err.c_str() : "null context"; }
 
-feti_status feti_setup_subdomains(feti_ctx* ctx, const feti_problem* prob) {
-  if (!ctx || !prob) return FETI_EINVAL;
-  Ctx& c = ctx->c;
+}  // extern "C"
+
+// Set-up of one problem or of a batch of independent problems (merged into
+// one description: every launch covers the whole batch).
+static feti_status setup_impl(Ctx& c, const feti_problem* probs, int n) {
   c.err.clear();
-  if (!prob->rho || !prob->dirichlet || !prob->f) { c.err = "null problem array"; return FETI_EINVAL; }
-  free_all(c);
-  c = Ctx{c.opt, c.stream, std::string(), 0, c.device, HostProblem(), {}, 0, c.h_pin};
-  // densities on the host for module de-duplication
-  int64_t nel = 1, nn = 1;
-  for (int a = 0; a < prob->dim && a < 3; ++a) {
-    nel *= (int64_t)prob->tiles[a] * prob->elems[a];
-    nn *= (int64_t)prob->tiles[a] * prob->elems[a] + 1;
+  if (n < 1) { c.err = "n_problems must be >= 1"; return FETI_EINVAL; }
+  for (int q = 0; q < n; ++q)
+    if (!probs[q].rho || !probs[q].dirichlet || !probs[q].f) { c.err = "null problem array"; return FETI_EINVAL; }
+  if (n > 1 && (c.opt.method != FETI_FETIDP || c.opt.krylov != FETI_PCG || c.opt.precision != FETI_FP64)) {
+    c.err = "batches of problems are solved with FETI-DP, PCG and FP64 block products";
+    return FETI_ENOTSUP;
   }
-  if (prob->dim != 2 && prob->dim != 3) { c.err = "dim must be 2 or 3"; return FETI_EINVAL; }
-  std::vector<double> rho_h(nel);
-  if (prob->on_device) CU(cudaMemcpy(rho_h.data(), prob->rho, nel * sizeof(double), cudaMemcpyDeviceToHost));
-  else std::memcpy(rho_h.data(), prob->rho, nel * sizeof(double));
-  for (double r : rho_h)
-    if (!(r >= 0.0 && r <= 1.0)) { c.err = "densities must lie in [0, 1]"; return FETI_EINVAL; }
-  std::string msg = build_host_problem(*prob, c.opt.method, c.opt.dedup_modules, rho_h.data(), c.hp);
-  if (!msg.empty()) { c.err = msg; return FETI_EINVAL; }
+  free_all(c);
+  if (c.cap_stream) { cudaStreamDestroy(c.cap_stream); c.cap_stream = nullptr; }
+  if (c.cap_event) { cudaEventDestroy(c.cap_event); c.cap_event = nullptr; }
+  c = Ctx{c.opt, c.stream, std::string(), 0, c.device, HostProblem(), {}, 0, c.h_pin};
+  std::vector<HostProblem> parts(n);
+  std::vector<double> rho_all;
+  for (int q = 0; q < n; ++q) {
+    const feti_problem* prob = &probs[q];
+    if (prob->dim != 2 && prob->dim != 3) { c.err = "dim must be 2 or 3"; return FETI_EINVAL; }
+    int64_t nel = 1;
+    for (int a = 0; a < prob->dim && a < 3; ++a) nel *= (int64_t)prob->tiles[a] * prob->elems[a];
+    std::vector<double> rho_h(nel);
+    if (prob->on_device) CU(cudaMemcpy(rho_h.data(), prob->rho, nel * sizeof(double), cudaMemcpyDeviceToHost));
+    else std::memcpy(rho_h.data(), prob->rho, nel * sizeof(double));
+    for (double r : rho_h)
+      if (!(r >= 0.0 && r <= 1.0)) { c.err = "densities must lie in [0, 1]"; return FETI_EINVAL; }
+    std::string msg = build_host_problem(*prob, c.opt.method, c.opt.dedup_modules, rho_h.data(), parts[q]);
+    if (!msg.empty()) { c.err = (n > 1 ? "problem " + std::to_string(q) + ": " : std::string()) + msg; return FETI_EINVAL; }
+    rho_all.insert(rho_all.end(), rho_h.begin(), rho_h.end());
+  }
+  if (n == 1) {
+    c.hp = std::move(parts[0]);
+  } else {
+    std::string msg = merge_host_problems(parts, c.hp);
+    if (!msg.empty()) { c.err = msg; return FETI_EINVAL; }
+  }
   HostProblem& hp = c.hp;
   // ---- problem arrays ----
-  TRY(upload(c, c.d_rho, rho_h));
+  TRY(upload(c, c.d_rho, rho_all));
   TRY(dalloc(c, c.d_E, hp.n_elements));
   TRY(dalloc(c, c.d_fglob, hp.n_dofs));
-  CU(cudaMemcpy(c.d_fglob, prob->f, hp.n_dofs * sizeof(double),
-                prob->on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice));
+  for (int q = 0; q < n; ++q)
+    CU(cudaMemcpy(c.d_fglob + hp.prob_dof_off[q], probs[q].f,
+                  (hp.prob_dof_off[q + 1] - hp.prob_dof_off[q]) * sizeof(double),
+                  probs[q].on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice));
+  {
+    const bool dummy = true;
+    (void)dummy;
+  }
   c.h_k0.assign((size_t)(hp.dim == 2 ? 64 : 576), 0.0);
   element_stiffness_host(hp.dim, hp.nu, c.h_k0.data());
   TRY(upload(c, c.d_k0, c.h_k0));
@@ -411,6 +439,7 @@ feti_status feti_setup_subdomains(feti_ctx* ctx, const feti_problem* prob) {
     for (int a = 0; a < T.n_loc; ++a) ci[a] = (T.cls[a] << 24) | std::max(T.idx[a], 0);
     DevType d{};
     d.n_loc = T.n_loc; d.n_i = T.n_i; d.n_b = T.n_b; d.n_c = T.n_c; d.bw = T.bw;
+    for (int a = 0; a < 3; ++a) { d.e[a] = T.e[a]; d.ln[a] = T.ln[a]; }
     int *p1, *p2, *p3, *p4;
     TRY(upload(c, p1, ci));
     TRY(upload(c, p2, T.ilist));
@@ -470,9 +499,18 @@ feti_status feti_setup_subdomains(feti_ctx* ctx, const feti_problem* prob) {
     S.type = hp.sub_type[s];
     S.b_off = hp.b_off[s];
     S.c_off = hp.c_off.empty() ? 0 : hp.c_off[s];
-    S.tile[0] = s % hp.tiles[0];
-    S.tile[1] = (s / hp.tiles[0]) % hp.tiles[1];
-    S.tile[2] = s / (hp.tiles[0] * hp.tiles[1]);
+    {
+      const int q = hp.sub_prob[s];
+      const int sl = s - hp.prob_sub_off[q];                  // index inside its problem
+      const int t0 = hp.prob_nel[3 * q] / Ts.e[0], t1 = hp.prob_nel[3 * q + 1] / Ts.e[1];
+      S.tile[0] = sl % t0;
+      S.tile[1] = (sl / t0) % t1;
+      S.tile[2] = sl / (t0 * t1);
+      S.prob = q;
+      S.loc_off = hp.loc_off[s];
+      S.e_off = hp.prob_el_off[q];
+      for (int a = 0; a < 3; ++a) S.nel[a] = hp.prob_nel[3 * q + a];
+    }
     c.h_subs[s] = S;
     coff[s] = S.c_off;
     c.h_ioff[s + 1] = c.h_ioff[s] + align32(hp.types[S.type].n_i);
@@ -508,7 +546,7 @@ feti_status feti_setup_subdomains(feti_ctx* ctx, const feti_problem* prob) {
   TRY(dalloc(c, c.d_diagKb, nbt));
   TRY(dalloc(c, c.d_w0, nl));
   TRY(dalloc(c, c.d_w1, nl));
-  TRY(dalloc(c, c.d_floc, (size_t)hp.n_sub * hp.n_loc_dofs));
+  TRY(dalloc(c, c.d_floc, (size_t)hp.n_loc_total));
   TRY(dalloc(c, c.d_h, c.h_ioff[hp.n_sub]));
   TRY(dalloc(c, c.d_t, c.h_ioff[hp.n_sub]));
   TRY(dalloc(c, c.d_ft, nbt + c.n_c_total));
@@ -516,9 +554,33 @@ feti_status feti_setup_subdomains(feti_ctx* ctx, const feti_problem* prob) {
   TRY(dalloc(c, c.d_pb1, nbt));
   c.n_coarse = hp.method == FETI_FETIDP ? hp.n_primal : hp.n_rbm * hp.n_sub;
   const int64_t nco = std::max(c.n_coarse, 1);
-  TRY(dalloc(c, c.d_Kbar, nco * nco));
-  TRY(dalloc(c, c.d_Kbar_L, nco * nco));
-  TRY(dalloc(c, c.d_Kbar_inv, nco * nco));
+  // coarse blocks: one per problem (FETI-DP), one for TFETI
+  c.h_kbar_off.assign(hp.n_prob + 1, 0);
+  c.max_np = 0;
+  std::vector<int> row_prob(std::max(hp.n_primal, 1), 0);
+  for (int q = 0; q < hp.n_prob; ++q) {
+    const int64_t npq = hp.method == FETI_FETIDP ? hp.prob_primal_off[q + 1] - hp.prob_primal_off[q] : nco;
+    c.h_kbar_off[q + 1] = c.h_kbar_off[q] + npq * npq;
+    c.max_np = std::max<int>(c.max_np, (int)npq);
+    for (int r = hp.prob_primal_off[q]; r < hp.prob_primal_off[q + 1]; ++r) row_prob[r] = q;
+  }
+  const int64_t kb_len = std::max<int64_t>(c.h_kbar_off[hp.n_prob], 1);
+  TRY(dalloc(c, c.d_Kbar, kb_len));
+  TRY(dalloc(c, c.d_Kbar_L, kb_len));
+  TRY(dalloc(c, c.d_Kbar_inv, kb_len));
+  TRY(upload(c, c.d_kbar_off, c.h_kbar_off));
+  TRY(upload(c, c.d_row_prob, row_prob));
+  TRY(upload(c, c.d_prob_el_off, hp.prob_el_off));
+  TRY(upload(c, c.d_prob_dof_off, hp.prob_dof_off));
+  TRY(upload(c, c.d_prob_lam_off, hp.prob_lam_off));
+  TRY(upload(c, c.d_prob_nel, hp.prob_nel));
+  TRY(upload(c, c.d_prob_primal_off, hp.prob_primal_off));
+  {
+    std::vector<int> lam_prob(hp.n_lam);
+    for (int q = 0; q < hp.n_prob; ++q)
+      for (int64_t l = hp.prob_lam_off[q]; l < hp.prob_lam_off[q + 1]; ++l) lam_prob[l] = q;
+    TRY(upload(c, c.d_lam_prob, lam_prob));
+  }
   TRY(dalloc(c, c.d_fbar, std::max(hp.n_primal, 1)));
   TRY(dalloc(c, c.d_coarse_work, (size_t)128 * nco + (size_t)((nco + 63) / 64) * 4096));
   if (hp.method == FETI_TFETI) {
@@ -526,7 +588,7 @@ feti_status feti_setup_subdomains(feti_ctx* ctx, const feti_problem* prob) {
     TRY(dalloc(c, c.d_e, nco));
     TRY(dalloc(c, c.d_alpha, nco));
   }
-  if (c.opt.precision == FETI_TF32) {
+  if (c.opt.precision != FETI_FP64) {
     TRY(dalloc(c, c.d_fmem, (size_t)c.modmem_len));
     TRY(dalloc(c, c.d_sqrtDF, nbt));
     TRY(dalloc(c, c.d_sqrtDS, nbt));
@@ -537,13 +599,15 @@ feti_status feti_setup_subdomains(feti_ctx* ctx, const feti_problem* prob) {
   TRY(dalloc(c, c.d_d, nl));
   TRY(dalloc(c, c.d_lam0, nl));
   TRY(dalloc(c, c.d_lam, nl));
-  TRY(dalloc(c, c.d_uloc, (size_t)hp.n_sub * hp.n_loc_dofs));
+  TRY(dalloc(c, c.d_uloc, (size_t)hp.n_loc_total));
   TRY(dalloc(c, c.d_uglob, hp.n_dofs));
   TRY(dalloc(c, c.d_scalar, 64));
   TRY(dalloc(c, c.d_status, 4));
   TRY(dalloc(c, c.d_kdev, 4));
   TRY(dalloc(c, c.d_perm, 1024));
   TRY(dalloc(c, c.d_red, 1024));
+  TRY(dalloc(c, c.d_bstate, (size_t)hp.n_prob * (6 + 2 * 16) + 16));
+  TRY(dalloc(c, c.d_bflags, (size_t)hp.n_prob * 3 + 4));
   CU(cudaMemset(c.d_status, 0, 4 * sizeof(int)));
   // ---- per-module descriptors for the factorization ----
   {
@@ -584,11 +648,42 @@ feti_status feti_setup_subdomains(feti_ctx* ctx, const feti_problem* prob) {
     dc[0].A = c.d_Kbar; dc[0].Linv = c.d_Kbar_L; dc[0].out = c.d_Kbar_inv;
     dc[0].n = c.n_coarse; dc[0].ld = c.n_coarse; dc[0].tag = 999999; dc[0].n_full = c.n_coarse;
     TRY(upload(c, c.d_dense_coarse, dc));
+    if (hp.n_prob > 1) {
+      std::vector<DenseDesc> db(hp.n_prob);
+      std::vector<GemmDesc> gc(hp.n_prob);
+      const int np = hp.n_primal;
+      for (int q = 0; q < hp.n_prob; ++q) {
+        const int o = hp.prob_primal_off[q], npq = hp.prob_primal_off[q + 1] - o;
+        db[q].A = c.d_Kbar + c.h_kbar_off[q];
+        db[q].Linv = c.d_Kbar_L + c.h_kbar_off[q];
+        db[q].out = c.d_Kbar_inv + c.h_kbar_off[q];
+        db[q].n = npq; db[q].ld = npq; db[q].tag = 900000 + q; db[q].n_full = npq;
+        GemmDesc g{};
+        g.A = c.d_Kbar_inv + c.h_kbar_off[q]; g.B = c.d_Vraw + o; g.C = c.d_V + o;
+        g.M = npq; g.N = 1; g.K = npq;
+        g.ars = npq; g.acs = 1; g.brs = 1; g.bcs = np; g.crs = 1; g.ccs = np;
+        gc[q] = g;
+      }
+      TRY(upload(c, c.d_dense_coarse_batch, db));
+      TRY(upload(c, c.d_gemm_coarse, gc));
+    }
   }
   TRY(ensure_blocks(c, std::max(64, hp.n_sub)));
   TRY(sync_check(c));
   c.state = 1;
   return FETI_OK;
+}
+
+extern "C" {
+
+feti_status feti_setup_subdomains(feti_ctx* ctx, const feti_problem* prob) {
+  if (!ctx || !prob) return FETI_EINVAL;
+  return setup_impl(ctx->c, prob, 1);
+}
+
+feti_status feti_setup_batch(feti_ctx* ctx, const feti_problem* probs, int n_problems) {
+  if (!ctx || !probs) return FETI_EINVAL;
+  return setup_impl(ctx->c, probs, n_problems);
 }
 
 feti_status feti_set_density(feti_ctx* ctx, const double* rho, int on_device) {
@@ -647,7 +742,8 @@ feti_status feti_factorize(feti_ctx* ctx) {
     CU(dgemm_batched(c.d_gemm_frcmake, c.n_mod, c.max_nb, c.max_nc, 0, 1.0, 0.0, st, c.fl_frcmake));
     CU(launch_copy_block(c, 1, st));
   }
-  if (c.opt.precision == FETI_TF32) CU(tc_prepare(c, st));
+  if (c.opt.precision != FETI_FP64) CU(tc_prepare(c, st));
+  if (hp.n_prob > 1 && c.gemv_cfg == 0) CU(autotune_gemv(c, st));   // batches: tune the matrix-vector shape
   // loads: f^s, h = L^{-1} f_i, f~ = f_bc - Y^T h
   CU(launch_load_gather(c, st));
   CU(launch_band_fwd_single(c, st));
@@ -660,7 +756,7 @@ feti_status feti_factorize(feti_ctx* ctx) {
   if (dp) {
     const int np = hp.n_primal;
     // coarse matrix Kbar_cc (Eq. 12) and its inverse
-    CU(launch_coarse_assemble_impl(c, c.d_c_sub, c.d_c_off, c.d_Kbar, st));
+    CU(coarse_assemble_batch(c, st));
     CU(coarse_inverse(c));
     // fbar_c = sum_s B_c^sT (f~_c - F_rc,s^T f~_b)
     CU(cudaMemcpyAsync(c.d_Xb, c.d_ft, nbt * sizeof(double), cudaMemcpyDeviceToDevice, st));
@@ -668,7 +764,7 @@ feti_status feti_factorize(feti_ctx* ctx) {
     CU(corner_gather_vec(c, c.d_ft + nbt, c.d_fbar, st));
     CU(axpby(np, -1.0, c.d_Vraw, 1.0, c.d_fbar, st));
     // d = d_r - F_rc Kbar^{-1} fbar
-    CU(gemv_dense(c.d_Kbar_inv, np, np, c.d_fbar, c.d_V, 0.0, st));
+    CU(coarse_matvec(c, c.d_fbar, c.d_V, st));
     CU(cudaMemsetAsync(c.d_Yb, 0, nbt * sizeof(double), st));
     CU(corner_expand(c, c.d_V, 1, c.d_Vc, c.d_Yb, st));
     CU(scatter_b_to_lam(c, c.d_Yb, 1, c.d_lam, nl, st));
@@ -804,6 +900,10 @@ static feti_status krylov_core(Ctx& c, double tol, int max_iter, bool lowp, feti
   return result;
 }
 
+static feti_status apply_one(Ctx& c, const double* x, double* y) {
+  return apply_dual(c, x, c.hp.n_lam, 1, y, c.hp.n_lam);
+}
+
 static feti_status solve_impl(Ctx& c, double* lambda_inout, feti_stats* stats) {
   const HostProblem& hp = c.hp;
   const int64_t nl = hp.n_lam;
@@ -824,7 +924,23 @@ static feti_status solve_impl(Ctx& c, double* lambda_inout, feti_stats* stats) {
     CU(axpby(nl, 1.0, c.d_lam0, 1.0, c.d_lam, st));
   }
   feti_status result = FETI_OK;
-  if (c.opt.precision == FETI_FP64) {
+  if (hp.n_prob > 1) {
+    // one PCG per problem, advanced together (graph-captured iterations)
+    TRY(apply_dual(c, c.d_lam, nl, 1, c.d_r, nl));
+    CU(axpby(nl, 1.0, c.d_d, -1.0, c.d_r, st));
+    int maxit = 0;
+    CU(batch_pcg(c, st, c.opt.tol, c.opt.max_iter, &apply_one, &maxit));
+    CU(axpby(nl, 1.0, c.d_lamt, 1.0, c.d_lam, st));
+    S.iterations = maxit;
+    S.converged = 1;
+    S.last_rank = 1;
+    for (auto& ps : c.prob_stats) {
+      S.converged = S.converged && ps.converged;
+      S.f_applies += ps.f_applies;
+      S.eps0 = std::max(S.eps0, ps.eps0);
+      S.eps = std::max(S.eps, ps.eps);
+    }
+  } else if (c.opt.precision == FETI_FP64) {
     // r_0 = P^T (d - F lambda_0), then Algorithm 1; lambda = lambda_0 + lambda~
     TRY(apply_dual(c, c.d_lam, nl, 1, c.d_r, nl));
     CU(axpby(nl, 1.0, c.d_d, -1.0, c.d_r, st));
@@ -852,7 +968,10 @@ static feti_status solve_impl(Ctx& c, double* lambda_inout, feti_stats* stats) {
       if (eps <= c.opt.tol * eps0 || outer >= c.opt.max_refine || S.iterations >= c.opt.max_iter) break;
       CU(cudaMemcpyAsync(c.d_r, c.d_rout, nl * sizeof(double), cudaMemcpyDeviceToDevice, st));
       feti_stats inner{};
-      feti_status s2 = krylov_core(c, c.opt.inner_tol, c.opt.max_iter - S.iterations, true, inner);
+      // each correction is capped (a stalled reduced-precision solve still
+      // returns a useful correction; the FP64 outer loop decides convergence)
+      const int cap = std::min(c.opt.max_iter - S.iterations, 30);
+      feti_status s2 = krylov_core(c, c.opt.inner_tol, cap, true, inner);
       S.iterations += inner.iterations;
       S.f_applies += inner.f_applies;
       S.last_rank = inner.last_rank;
@@ -916,9 +1035,20 @@ feti_status feti_recover_displacements(feti_ctx* ctx, double* u_out, int on_devi
   if (u_out)
     CU(cudaMemcpyAsync(u_out, c.d_uglob, hp.n_dofs * sizeof(double),
                        on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, st));
-  if (compliance_out) {
-    CU(dot(c.d_fglob, c.d_uglob, hp.n_dofs, c.d_red, c.d_scalar, st));
-    TRY(read_scalar(c, c.d_scalar, compliance_out));
+  {
+    // per-problem compliance f_p^T u_p
+    const int np = hp.n_prob;
+    double* part = c.d_bstate + 6 * np;
+    double* comp = c.d_bstate;            // scratch (the PCG scalars are no longer needed)
+    CU(seg_dot2(c.d_prob_dof_off, np, c.d_fglob, c.d_uglob, nullptr, nullptr, part, comp, nullptr, st));
+    c.prob_compliance.assign(np, 0.0);
+    CU(cudaMemcpyAsync(c.prob_compliance.data(), comp, np * sizeof(double), cudaMemcpyDeviceToHost, st));
+    CU(cudaStreamSynchronize(st));
+    if (compliance_out) {
+      double t = 0.0;
+      for (double v : c.prob_compliance) t += v;
+      *compliance_out = t;
+    }
   }
   TRY(sync_check(c));
   c.state = 4;
@@ -949,7 +1079,7 @@ feti_status feti_apply_dual(feti_ctx* ctx, const double* X, int ldx, int m, doub
   if (c.state < 2) { c.err = "feti_apply_dual before feti_factorize"; return FETI_ESTATE; }
   if (ldx < c.hp.n_lam || ldy < c.hp.n_lam) { c.err = "leading dimension smaller than n_lambda"; return FETI_EINVAL; }
   if (m == 0) return FETI_OK;
-  if (c.opt.precision == FETI_TF32) TRY(apply_dual_lowp(c, X, ldx, m, Y, ldy));
+  if (c.opt.precision != FETI_FP64) TRY(apply_dual_lowp(c, X, ldx, m, Y, ldy));
   else TRY(apply_dual(c, X, ldx, m, Y, ldy));
   TRY(sync_check(c));
   TRY(check_status(c, "feti_apply_dual"));
@@ -988,8 +1118,25 @@ feti_status feti_query(const feti_ctx* ctx, int key, int64_t* value) {
     case FETI_Q_DEVICE_BYTES: *value = (int64_t)c.device_bytes; break;
     case FETI_Q_N_RBM: *value = hp.n_rbm; break;
     case FETI_Q_LAUNCHES: *value = launches(); break;
+    case FETI_Q_N_PROBLEMS: *value = hp.n_prob; break;
+    case FETI_Q_GEMV_CONFIG: *value = c.gemv_cfg; break;
     default: return FETI_EINVAL;
   }
+  return FETI_OK;
+}
+
+feti_status feti_problem_result(const feti_ctx* ctx, int p, int64_t* dof_offset, int64_t* elem_offset,
+                                int64_t* lambda_offset, feti_stats* stats, double* compliance) {
+  if (!ctx) return FETI_EINVAL;
+  const Ctx& c = ctx->c;
+  if (c.state < 1) return FETI_ESTATE;
+  const HostProblem& hp = c.hp;
+  if (p < 0 || p >= hp.n_prob) return FETI_EINVAL;
+  if (dof_offset) *dof_offset = hp.prob_dof_off[p];
+  if (elem_offset) *elem_offset = hp.prob_el_off[p];
+  if (lambda_offset) *lambda_offset = hp.prob_lam_off[p];
+  if (stats) *stats = (hp.n_prob > 1 && (int)c.prob_stats.size() == hp.n_prob) ? c.prob_stats[p] : c.last;
+  if (compliance) *compliance = (int)c.prob_compliance.size() > p ? c.prob_compliance[p] : 0.0;
   return FETI_OK;
 }
 

@@ -226,11 +226,90 @@ cudaError_t corner_expand(Ctx& c, const double* V, int m, double* Vc, double* /*
   return dgemm_batched(c.d_gemm_Frc, c.hp.n_sub, c.max_nb, c.max_nb, m, 1.0, 1.0, st, c.fl_Frc * m);
 }
 
-cudaError_t batched_gemv(const Ctx& c, int which, const double* xb, double* yb, double beta, cudaStream_t st) {
-  dim3 g((c.max_nb + 7) / 8, c.hp.n_sub);
-  k_sub_gemv<<<g, 256, 0, st>>>(c.d_types, c.d_mods, c.d_subs, c.d_modmem, which, xb, yb, beta);
+namespace {
+
+// Vector-load variant of k_sub_gemv (two doubles per lane per load); needs an
+// even row length, which every 2D interface has (2 DOF per node).
+__global__ void k_sub_gemv2(const DevType* __restrict__ types, const DevModule* __restrict__ mods,
+                            const DevSub* __restrict__ subs, const double* __restrict__ mem, int which,
+                            const double* __restrict__ x, double* __restrict__ y, double beta) {
+  const DevSub S = subs[blockIdx.y];
+  const DevType T = types[S.type];
+  const DevModule M = mods[S.module];
+  const int row = blockIdx.x * (blockDim.x / 32) + threadIdx.x / 32;
+  const int lane = threadIdx.x & 31;
+  const int n = T.n_b;
+  if (row >= n) return;
+  const double* A = mem + (which == 0 ? M.F : M.S);
+  const int64_t ld = which == 0 ? n : (int64_t)(T.n_b + T.n_c);
+  const double* a = A + (int64_t)row * ld;
+  const double* xs = x + S.b_off;
+  double acc = 0.0;
+  if ((n & 1) == 0 && (ld & 1) == 0 && (S.b_off & 1) == 0) {
+    const double2* a2 = reinterpret_cast<const double2*>(a);
+    const double2* x2 = reinterpret_cast<const double2*>(xs);
+    for (int k = lane; k < n / 2; k += 32) {
+      const double2 av = a2[k], xv = x2[k];
+      acc = fma(av.x, xv.x, acc);
+      acc = fma(av.y, xv.y, acc);
+    }
+  } else {
+    for (int k = lane; k < n; k += 32) acc = fma(a[k], xs[k], acc);
+  }
+  for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+  if (lane == 0) {
+    double* yp = y + S.b_off + row;
+    *yp = beta != 0.0 ? fma(beta, *yp, acc) : acc;
+  }
+}
+
+}  // namespace
+
+// config = warps per CTA (4, 8 or 16) + 100 * (vector loads)
+static cudaError_t launch_gemv_cfg(const Ctx& c, int cfg, int which, const double* xb, double* yb, double beta,
+                                   cudaStream_t st) {
+  const int warps = cfg % 100, vec = cfg / 100;
+  dim3 g((c.max_nb + warps - 1) / warps, c.hp.n_sub);
+  if (vec) k_sub_gemv2<<<g, warps * 32, 0, st>>>(c.d_types, c.d_mods, c.d_subs, c.d_modmem, which, xb, yb, beta);
+  else k_sub_gemv<<<g, warps * 32, 0, st>>>(c.d_types, c.d_mods, c.d_subs, c.d_modmem, which, xb, yb, beta);
   note_launches(1);
   return cudaGetLastError();
+}
+
+cudaError_t batched_gemv(const Ctx& c, int which, const double* xb, double* yb, double beta, cudaStream_t st) {
+  return launch_gemv_cfg(c, c.gemv_cfg > 0 ? c.gemv_cfg : 8, which, xb, yb, beta, st);
+}
+
+// Autotuner: time every launch shape of the per-subdomain matrix-vector
+// product on this problem (CUDA events, median of 5) and keep the fastest.
+cudaError_t autotune_gemv(Ctx& c, cudaStream_t st) {
+  const int cands[6] = {4, 8, 16, 104, 108, 116};
+  cudaEvent_t e0, e1;
+  cudaError_t e;
+  if ((e = cudaEventCreate(&e0)) != cudaSuccess) return e;
+  if ((e = cudaEventCreate(&e1)) != cudaSuccess) return e;
+  float best = 1e30f;
+  int best_cfg = 8;
+  for (int ci = 0; ci < 6 && e == cudaSuccess; ++ci) {
+    float ts[5];
+    for (int r = 0; r < 5 && e == cudaSuccess; ++r) {
+      cudaEventRecord(e0, st);
+      e = launch_gemv_cfg(c, cands[ci], 0, c.d_pb0, c.d_pb1, 0.0, st);
+      cudaEventRecord(e1, st);
+      if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+      if (e == cudaSuccess) e = cudaEventElapsedTime(&ts[r], e0, e1);
+    }
+    if (e != cudaSuccess) break;
+    std::sort(ts, ts + 5);
+    if (ts[2] < best) { best = ts[2]; best_cfg = cands[ci]; }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (e == cudaSuccess) {
+    c.gemv_cfg = best_cfg;
+    c.gemv_ms = best;
+  }
+  return e;
 }
 
 cudaError_t batched_gemv_F(Ctx& c, const double* xb, double* yb, cudaStream_t st) {
@@ -336,6 +415,85 @@ cudaError_t precond_apply_lowp(Ctx& c, const double* r, double* Z, int64_t ldz, 
                                                                c.d_w0, c.d_w1, c.d_b_sub, zb, Z, ldz, z);
   note_launches(1);
   return cudaGetLastError();
+}
+
+namespace {
+
+// y[r] = sum_k Kinv_p(r - off_p, k) x[off_p + k], p = problem of primal row r
+// (the coarse inverse is block diagonal over the problems of a batch); one
+// warp per row.
+__global__ void k_coarse_gemv(int np_total, const int* __restrict__ row_prob, const int* __restrict__ poff,
+                              const int64_t* __restrict__ koff, const double* __restrict__ Kinv,
+                              const double* __restrict__ x, double* __restrict__ y) {
+  const int r = blockIdx.x * (blockDim.x / 32) + threadIdx.x / 32;
+  const int lane = threadIdx.x & 31;
+  if (r >= np_total) return;
+  const int p = row_prob[r];
+  const int o = poff[p], n = poff[p + 1] - o;
+  const double* a = Kinv + koff[p] + (int64_t)(r - o) * n;
+  const double* xs = x + o;
+  double acc = 0.0;
+  for (int k = lane; k < n; k += 32) acc = fma(a[k], xs[k], acc);
+  for (int off = 16; off > 0; off >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, off);
+  if (lane == 0) y[r] = acc;
+}
+
+// Kbar_p = sum over the problem's subdomains of B_c^sT Kbar_s B_c^s (gather
+// over corner copies); grid.y = problem.
+__global__ void k_coarse_assemble_batch(const int* __restrict__ ppoff, const int64_t* __restrict__ koff,
+                                        const int* __restrict__ poff, const int* __restrict__ psrc,
+                                        const int* __restrict__ c_sub, const DevSub* __restrict__ subs,
+                                        const DevModule* __restrict__ mods, const DevType* __restrict__ types,
+                                        const double* __restrict__ mem, double* __restrict__ K) {
+  const int p = blockIdx.y;
+  const int o = ppoff[p], n = ppoff[p + 1] - o;
+  const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (e >= (int64_t)n * n) return;
+  const int g1 = o + (int)(e / n), g2 = o + (int)(e % n);
+  double v = 0.0;
+  for (int a = poff[g1]; a < poff[g1 + 1]; ++a) {
+    const int s = c_sub[psrc[a]];
+    const DevSub S = subs[s];
+    const int k1 = psrc[a] - (int)S.c_off;
+    for (int b = poff[g2]; b < poff[g2 + 1]; ++b) {
+      if (c_sub[psrc[b]] != s) continue;
+      const int k2 = psrc[b] - (int)S.c_off;
+      const int nc = types[S.type].n_c;
+      v += mem[mods[S.module].Kb + (int64_t)k1 * nc + k2];
+    }
+  }
+  K[koff[p] + e] = v;
+}
+
+}  // namespace
+
+cudaError_t coarse_assemble_batch(const Ctx& c, cudaStream_t st) {
+  dim3 g((unsigned)(((int64_t)c.max_np * c.max_np + 255) / 256), c.hp.n_prob);
+  k_coarse_assemble_batch<<<g, 256, 0, st>>>(c.d_prob_primal_off, c.d_kbar_off, c.d_prim_off, c.d_prim_src,
+                                             c.d_c_sub, c.d_subs, c.d_mods, c.d_types, c.d_modmem, c.d_Kbar);
+  note_launches(1);
+  return cudaGetLastError();
+}
+
+cudaError_t coarse_matvec(const Ctx& c, const double* x, double* y, cudaStream_t st) {
+  const int np = c.hp.n_primal;
+  k_coarse_gemv<<<(np + 7) / 8, 256, 0, st>>>(np, c.d_row_prob, c.d_prob_primal_off, c.d_kbar_off, c.d_Kbar_inv, x,
+                                              y);
+  note_launches(1);
+  return cudaGetLastError();
+}
+
+// V = Kbar^{-1} Vraw for m columns (block diagonal over a batch's problems)
+cudaError_t coarse_apply(const Ctx& c, const double* Vraw, double* V, int m, cudaStream_t st) {
+  const int np = c.hp.n_primal;
+  if (m == 1) return coarse_matvec(c, Vraw, V, st);
+  if (c.hp.n_prob == 1) {
+    GemmDesc d{};
+    d.A = c.d_Kbar_inv; d.B = Vraw; d.C = V; d.M = np; d.N = m; d.K = np;
+    d.ars = np; d.acs = 1; d.brs = 1; d.bcs = np; d.crs = 1; d.ccs = np;
+    return dgemm_split(d, 1, nullptr, 1.0, 0.0, st);
+  }
+  return dgemm_batched(c.d_gemm_coarse, c.hp.n_prob, c.max_np, m, m, 1.0, 0.0, st);
 }
 
 }  // namespace feti

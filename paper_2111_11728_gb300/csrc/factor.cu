@@ -236,7 +236,8 @@ __global__ void k_band_fwd_single(const DevType* __restrict__ types, const DevMo
   const double* Lr = mem + M.lrow;
   const double* rd = mem + M.rdiag;
   double* hs = h + ioff[s];
-  const double* fs = floc + (int64_t)s * nld;
+  const double* fs = floc + S.loc_off;
+  (void)nld;
   for (int j = 0; j < n; ++j) {
     const double* lr = Lr + (int64_t)j * W;
     const int dmax = min(j, bw);
@@ -264,7 +265,8 @@ __global__ void k_condense_load(const DevType* __restrict__ types, const DevModu
   double acc = 0.0;
   for (int k = 0; k < T.n_i; ++k) acc = fma(Y[(int64_t)k * nbc + j], hs[k], acc);
   const int ld = j < T.n_b ? T.blist[j] : T.clist[j - T.n_b];
-  const double v = floc[(int64_t)blockIdx.y * nld + ld] - acc;
+  const double v = floc[S.loc_off + ld] - acc;
+  (void)nld;
   if (j < T.n_b) ft[S.b_off + j] = v;
   else ft[nbt + S.c_off + (j - T.n_b)] = v;
 }

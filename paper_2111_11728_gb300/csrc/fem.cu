@@ -57,7 +57,7 @@ __global__ void k_assemble(const DevType* __restrict__ types, const DevModule* _
   const DevSub S = subs[M.rep];
   const int dim = g.dim, nen = 1 << dim, nek = nen * dim;
   const int na = a / dim, da = a % dim;
-  const int c0 = na % g.ln[0], c1 = (na / g.ln[0]) % g.ln[1], c2 = na / (g.ln[0] * g.ln[1]);
+  const int c0 = na % T.ln[0], c1 = (na / T.ln[0]) % T.ln[1], c2 = na / (T.ln[0] * T.ln[1]);
   const int nb = T.n_b, nbc = T.n_b + T.n_c, W = T.bw + 1;
   double* Lcol = mem + M.lcol;
   double* Y = mem + M.Y;
@@ -67,9 +67,9 @@ __global__ void k_assemble(const DevType* __restrict__ types, const DevModule* _
     for (int dy = -1; dy <= 1; ++dy)
       for (int dx = -1; dx <= 1; ++dx) {
         const int q0 = c0 + dx, q1 = c1 + dy, q2 = c2 + dz;
-        if (q0 < 0 || q0 > g.e[0] || q1 < 0 || q1 > g.e[1]) continue;
-        if (dim == 3 && (q2 < 0 || q2 > g.e[2])) continue;
-        const int nbn = q0 + g.ln[0] * (q1 + g.ln[1] * q2);
+        if (q0 < 0 || q0 > T.e[0] || q1 < 0 || q1 > T.e[1]) continue;
+        if (dim == 3 && (q2 < 0 || q2 > T.e[2])) continue;
+        const int nbn = q0 + T.ln[0] * (q1 + T.ln[1] * q2);
         for (int db = 0; db < dim; ++db) {
           const int b = nbn * dim + db;
           const int cb = T.cls_idx[b];
@@ -82,16 +82,16 @@ __global__ void k_assemble(const DevType* __restrict__ types, const DevModule* _
           for (int o = 0; o < nen; ++o) {
             const int o0 = o & 1, o1 = (o >> 1) & 1, o2 = (o >> 2) & 1;
             const int e0 = c0 - o0, e1 = c1 - o1, e2 = c2 - o2;
-            if (e0 < 0 || e0 >= g.e[0] || e1 < 0 || e1 >= g.e[1]) continue;
-            if (dim == 3 && (e2 < 0 || e2 >= g.e[2])) continue;
+            if (e0 < 0 || e0 >= T.e[0] || e1 < 0 || e1 >= T.e[1]) continue;
+            if (dim == 3 && (e2 < 0 || e2 >= T.e[2])) continue;
             const int p0 = q0 - e0, p1 = q1 - e1, p2 = q2 - e2;
             if (p0 < 0 || p0 > 1 || p1 < 0 || p1 > 1) continue;
             if (dim == 3 && (p2 < 0 || p2 > 1)) continue;
             const int lb = p0 | (p1 << 1) | (p2 << 2);
-            const int64_t ge0 = (int64_t)S.tile[0] * g.e[0] + e0;
-            const int64_t ge1 = (int64_t)S.tile[1] * g.e[1] + e1;
-            const int64_t ge2 = dim == 3 ? (int64_t)S.tile[2] * g.e[2] + e2 : 0;
-            const double Ee = E[ge0 + g.nel[0] * (ge1 + (int64_t)g.nel[1] * ge2)];
+            const int64_t ge0 = (int64_t)S.tile[0] * T.e[0] + e0;
+            const int64_t ge1 = (int64_t)S.tile[1] * T.e[1] + e1;
+            const int64_t ge2 = dim == 3 ? (int64_t)S.tile[2] * T.e[2] + e2 : 0;
+            const double Ee = E[S.e_off + ge0 + S.nel[0] * (ge1 + (int64_t)S.nel[1] * ge2)];
             v = fma(Ee, k0[(o * dim + da) * nek + lb * dim + db], v);
           }
           if (cla == CLS_I && clb == CLS_I) {
@@ -162,20 +162,31 @@ __global__ void k_gather_u(int64_t n_dofs, const int64_t* __restrict__ off, cons
   u[q] = e > b + 1 ? s / (double)(e - b) : s;
 }
 
-// dc/drho_e = -p rho_e^(p-1) (E0 - Emin) u_e^T k0 u_e
-__global__ void k_grad(MeshArgs g, const double* __restrict__ rho, const double* __restrict__ u,
+// dc/drho_e = -p rho_e^(p-1) (E0 - Emin) u_e^T k0 u_e; elements of all
+// problems of a batch are numbered consecutively (problem tables el_off,
+// dof_off, nel).
+__global__ void k_grad(int dim, int n_prob, const int64_t* __restrict__ el_off, const int64_t* __restrict__ dof_off,
+                       const int* __restrict__ pnel, const double* __restrict__ rho, const double* __restrict__ u,
                        const double* __restrict__ k0, double E0, double Emin, double p,
                        double* __restrict__ out) {
-  const int64_t ne = (int64_t)g.nel[0] * g.nel[1] * (g.dim == 3 ? g.nel[2] : 1);
-  int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (e >= ne) return;
-  const int dim = g.dim, nen = 1 << dim, nek = nen * dim;
-  const int64_t x = e % g.nel[0], y = (e / g.nel[0]) % g.nel[1], z = e / ((int64_t)g.nel[0] * g.nel[1]);
+  const int64_t ge = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (ge >= el_off[n_prob]) return;
+  int lo = 0, hi = n_prob;                       // problem containing element ge
+  while (hi - lo > 1) {
+    const int mid = (lo + hi) / 2;
+    if (el_off[mid] <= ge) lo = mid; else hi = mid;
+  }
+  const int nel0 = pnel[3 * lo], nel1 = pnel[3 * lo + 1];
+  const int64_t e = ge - el_off[lo];
+  const int nen = 1 << dim, nek = nen * dim;
+  const int64_t x = e % nel0, y = (e / nel0) % nel1, z = e / ((int64_t)nel0 * nel1);
+  const int64_t nn0 = nel0 + 1, nn1 = nel1 + 1;
+  const double* up = u + dof_off[lo];
   double ue[24];
   for (int a = 0; a < nen; ++a) {
     const int64_t nx = x + (a & 1), ny = y + ((a >> 1) & 1), nz = z + ((a >> 2) & 1);
-    const int64_t node = nx + g.nnod[0] * (ny + (int64_t)g.nnod[1] * nz);
-    for (int d = 0; d < dim; ++d) ue[a * dim + d] = u[node * dim + d];
+    const int64_t node = nx + nn0 * (ny + nn1 * nz);
+    for (int d = 0; d < dim; ++d) ue[a * dim + d] = up[node * dim + d];
   }
   double en = 0.0;
   for (int i = 0; i < nek; ++i) {
@@ -183,7 +194,7 @@ __global__ void k_grad(MeshArgs g, const double* __restrict__ rho, const double*
     for (int j = 0; j < nek; ++j) t = fma(k0[i * nek + j], ue[j], t);
     en = fma(ue[i], t, en);
   }
-  out[e] = -p * pow(rho[e], p - 1.0) * (E0 - Emin) * en;
+  out[ge] = -p * pow(rho[ge], p - 1.0) * (E0 - Emin) * en;
 }
 
 }  // namespace
@@ -269,6 +280,7 @@ cudaError_t launch_assemble_with(const Ctx& c, const double* E, cudaStream_t st)
   int maxn = 0;
   for (auto& t : c.h_types) maxn = std::max(maxn, t.n_loc);
   dim3 grid((maxn + 127) / 128, c.n_mod);
+  (void)mesh_args;
   k_assemble<<<grid, 128, 0, st>>>(c.d_types, c.d_mods, c.d_subs, E, c.d_k0, c.d_modmem, mesh_args(c.hp));
   note_launches(1);
   return cudaGetLastError();
@@ -292,7 +304,7 @@ cudaError_t launch_scaling_weights(const Ctx& c, int kind, cudaStream_t st) {
 }
 
 cudaError_t launch_load_gather(const Ctx& c, cudaStream_t st) {
-  const int64_t n = (int64_t)c.hp.n_sub * c.hp.n_loc_dofs;
+  const int64_t n = c.hp.n_loc_total;
   k_load_gather<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(c.d_load_src, n, c.d_fglob, c.d_floc);
   note_launches(1);
   return cudaGetLastError();
@@ -308,8 +320,9 @@ cudaError_t launch_gather_u(const Ctx& c, cudaStream_t st) {
 
 cudaError_t launch_grad(const Ctx& c, double* out, cudaStream_t st) {
   const int64_t n = c.hp.n_elements;
-  k_grad<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(mesh_args(c.hp), c.d_rho, c.d_uglob, c.d_k0, c.hp.E0,
-                                                      c.hp.Emin, c.hp.p, out);
+  k_grad<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(c.hp.dim, c.hp.n_prob, c.d_prob_el_off, c.d_prob_dof_off,
+                                                      c.d_prob_nel, c.d_rho, c.d_uglob, c.d_k0, c.hp.E0, c.hp.Emin,
+                                                      c.hp.p, out);
   note_launches(1);
   return cudaGetLastError();
 }

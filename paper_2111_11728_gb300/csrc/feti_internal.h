@@ -21,6 +21,8 @@ enum DofClass : int { CLS_I = 0, CLS_B = 1, CLS_C = 2, CLS_X = 3 };
 
 // Subdomains with the same boundary situation share one DOF classification.
 struct StructType {
+  int e[3] = {1, 1, 1};          // elements per axis of the tile (its problem's elems)
+  int ln[3] = {1, 1, 1};         // local nodes per axis
   int n_loc = 0;                 // local DOFs
   std::vector<int> cls;          // [n_loc] DofClass
   std::vector<int> idx;          // [n_loc] position inside its class list
@@ -75,7 +77,22 @@ struct HostProblem {
 
   // rigid-body modes (TFETI): n_rbm per subdomain
   int n_rbm = 0;
+
+  // per-subdomain placement (a batch concatenates independent problems)
+  std::vector<int64_t> loc_off;           // [n_sub + 1] offset of each subdomain's local vectors
+  std::vector<int> sub_prob;              // [n_sub] problem of each subdomain
+  int64_t n_loc_total = 0;
+  // per-problem ranges (one entry for a single problem)
+  int n_prob = 1;
+  std::vector<int64_t> prob_dof_off, prob_el_off, prob_lam_off;   // [n_prob + 1]
+  std::vector<int> prob_sub_off, prob_primal_off;                  // [n_prob + 1]
+  std::vector<int> prob_nel;                                       // [3 * n_prob]
 };
+
+// Concatenate independently built problems into one description (offsets
+// shifted; each problem keeps its own types, modules, multipliers, primal
+// DOFs).  All parts must share dim and method.
+std::string merge_host_problems(std::vector<HostProblem>& parts, HostProblem& out);
 
 // Builds the host description; returns an error message or "".
 std::string build_host_problem(const feti_problem& prob, int method, int dedup,
@@ -97,6 +114,8 @@ inline void local_node_coords(const HostProblem& hp, int ln, int c[3]) {
 struct DevType {
   int n_loc, n_i, n_b, n_c, bw;
   int pad;
+  int e[3];                      // elements per axis of the tile
+  int ln[3];                     // local nodes per axis
   const int* cls_idx;            // [n_loc] (cls << 24) | idx
   const int* ilist;              // [n_i]
   const int* blist;              // [n_b]
@@ -126,8 +145,12 @@ struct DevSub {
   int type;
   int64_t b_off;                 // into the global b space
   int64_t c_off;                 // into c_glob
-  int tile[3];
-  int pad;
+  int tile[3];                   // tile coordinates inside its problem
+  int prob;                      // problem index
+  int64_t loc_off;               // into the local vectors (loads, displacements)
+  int64_t e_off;                 // element offset of its problem
+  int nel[3];                    // global element grid of its problem
+  int pad2;
 };
 
 struct GemmDesc;
@@ -199,6 +222,25 @@ struct Ctx {
   double* d_sqrtDF = nullptr;    // [n_b_total] sqrt(diag F_s)
   double* d_sqrtDS = nullptr;    // [n_b_total] sqrt(diag S_s)
   double *d_rout = nullptr, *d_zout = nullptr, *d_dl = nullptr;   // refinement vectors
+  // per-problem tables (device)
+  int64_t *d_prob_el_off = nullptr, *d_prob_dof_off = nullptr, *d_prob_lam_off = nullptr;
+  int *d_prob_nel = nullptr, *d_prob_primal_off = nullptr;
+  int64_t* d_kbar_off = nullptr;     // [n_prob + 1] offsets of the per-problem coarse blocks
+  std::vector<int64_t> h_kbar_off;
+  int* d_row_prob = nullptr;         // [n_primal] problem of each primal row
+  int* d_lam_prob = nullptr;         // [n_lam] problem of each multiplier
+  GemmDesc* d_gemm_coarse = nullptr; // per-problem coarse GEMMs (batches)
+  DenseDesc* d_dense_coarse_batch = nullptr;
+  int max_np = 0;
+  int gemv_cfg = 0;                  // autotuned launch shape of the per-subdomain GEMV (0: default)
+  float gemv_ms = 0.f;
+  // batched PCG state
+  cudaStream_t cap_stream = nullptr;  // private stream for graph capture
+  cudaEvent_t cap_event = nullptr;
+  double* d_bstate = nullptr;        // per-problem scalars
+  int* d_bflags = nullptr;           // per-problem activity / iteration / convergence
+  std::vector<feti_stats> prob_stats;
+  std::vector<double> prob_compliance;
   double* d_fbar = nullptr;      // [n_primal]
   int n_coarse = 0;
   double* d_G = nullptr;         // TFETI: dense G [n_coarse x n_lam]

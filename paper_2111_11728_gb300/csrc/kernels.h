@@ -112,6 +112,8 @@ cudaError_t precond_apply_scratch(const Ctx& c, const double* r, double* Z, int6
 cudaError_t batched_gemv_F(Ctx& c, const double* xb, double* yb, cudaStream_t st);   // y_b = F_s x_b
 // y_b = A_s x_b (+ beta y_b), A_s = F_s (which 0) or S_bb (which 1)
 cudaError_t batched_gemv(const Ctx& c, int which, const double* xb, double* yb, double beta, cudaStream_t st);
+// picks the fastest launch shape of batched_gemv on this problem (stored in c.gemv_cfg)
+cudaError_t autotune_gemv(Ctx& c, cudaStream_t st);
 
 // ---- Krylov helpers (krylov.cu) ------------------------------------------------
 // Rank-revealing pivoted Cholesky of Delta (m x m, column-major ld; only its
@@ -134,7 +136,7 @@ cudaError_t gemv_t(const double* W, int64_t ld, int64_t n, int k, const double* 
 cudaError_t gemv_dense(const double* A, int n, int ld, const double* x, double* y, double beta, cudaStream_t st);
 
 // ---- precision form (tc_apply.cu) -------------------------------------------------
-size_t tc_apply_smem_bytes();
+size_t tc_apply_smem_bytes(int passes);
 cudaError_t tc_prepare(const Ctx& c, cudaStream_t st);   // Fhat, Shat (FP32) and sqrt-diagonals
 // Yb = D^{1/2} Fhat D^{1/2} B^T X (tcgen05 kind::tf32); rows >= n_b untouched
 cudaError_t tc_apply_local(const Ctx& c, const double* X, int64_t ldx, int m, double* Yb, cudaStream_t st);
@@ -142,6 +144,18 @@ cudaError_t lowp_gemv_S(const Ctx& c, const double* xb, double* yb, cudaStream_t
 // Yb(s) += F_rc,s V[c_glob(s), :] with a thin kernel (no tile padding)
 cudaError_t corner_expand_thin(Ctx& c, const double* V, int m, double* Yb, cudaStream_t st);
 cudaError_t precond_apply_lowp(Ctx& c, const double* r, double* Z, int64_t ldz, double* z, cudaStream_t st);
+
+// ---- coarse problem over one or many problems (dual.cu) --------------------------
+cudaError_t coarse_assemble_batch(const Ctx& c, cudaStream_t st);
+cudaError_t coarse_matvec(const Ctx& c, const double* x, double* y, cudaStream_t st);
+cudaError_t coarse_apply(const Ctx& c, const double* Vraw, double* V, int m, cudaStream_t st);
+
+// ---- batching form (batch.cu) -----------------------------------------------------
+// out0[p] = a0.b0 and out1[p] = a1.b1 over each problem's index range off[p]..off[p+1)
+cudaError_t seg_dot2(const int64_t* d_off, int n_prob, const double* a0, const double* b0, const double* a1,
+                     const double* b1, double* part, double* out0, double* out1, cudaStream_t st);
+cudaError_t batch_pcg(Ctx& c, cudaStream_t user, double tol, int max_iter,
+                      feti_status (*apply)(Ctx&, const double*, double*), int* total_iters);
 
 // ---- recovery (recover.cu) ------------------------------------------------------
 cudaError_t recover_fetidp(Ctx& c, const double* lam, cudaStream_t st);

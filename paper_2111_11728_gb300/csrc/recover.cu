@@ -83,16 +83,16 @@ __global__ void k_write_uloc(const DevType* __restrict__ types, const DevSub* __
                              double* __restrict__ uloc) {
   const int s = blockIdx.y;
   const int a = blockIdx.x * blockDim.x + threadIdx.x;
-  if (a >= nld) return;
   const DevSub S = subs[s];
   const DevType T = types[S.type];
+  if (a >= T.n_loc || a >= nld) return;
   const int ci = T.cls_idx[a];
   const int cls = ci >> 24, idx = ci & 0xffffff;
   double v = 0.0;
   if (cls == CLS_I) v = xi[ioff[s] + idx];
   else if (cls == CLS_B) v = xb[S.b_off + idx];
   else if (cls == CLS_C) v = uc[cg[S.c_off + idx]];
-  uloc[(int64_t)s * nld + a] = v;
+  uloc[S.loc_off + a] = v;
 }
 
 }  // namespace
@@ -119,7 +119,8 @@ static cudaError_t recover_local(Ctx& c, const double* uc, cudaStream_t st) {
                                                           c.hp.n_sub);
   note_launches(1);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
-  const int nld = c.hp.n_loc_dofs;
+  int nld = 1;
+  for (auto& tt : c.h_types) nld = std::max(nld, tt.n_loc);
   k_write_uloc<<<dim3((nld + 127) / 128, c.hp.n_sub), 128, 0, st>>>(c.d_types, c.d_subs, nld, c.d_ioff, t, xb,
                                                                     c.d_c_glob, uc, c.d_uloc);
   note_launches(1);
@@ -135,7 +136,7 @@ cudaError_t recover_fetidp(Ctx& c, const double* lam, cudaStream_t st) {
   double* uc = c.d_V;
   if ((e = corner_reduce(c, c.d_Xb, 1, c.d_Cb, Vraw, st)) != cudaSuccess) return e;
   if ((e = axpby(np, 1.0, c.d_fbar, 1.0, Vraw, st)) != cudaSuccess) return e;
-  if ((e = gemv_dense(c.d_Kbar_inv, np, np, Vraw, uc, 0.0, st)) != cudaSuccess) return e;
+  if ((e = coarse_matvec(c, Vraw, uc, st)) != cudaSuccess) return e;
   return recover_local(c, uc, st);
 }
 

@@ -173,6 +173,10 @@ std::string build_host_problem(const feti_problem& prob, int method, int dedup,
       type_of_key.emplace(key, id);
       StructType T;
       T.n_loc = nld;
+      for (int a = 0; a < 3; ++a) {
+        T.e[a] = a < dim ? hp.elems[a] : 1;
+        T.ln[a] = hp.lnod[a];
+      }
       T.cls.resize(nld);
       T.idx.assign(nld, -1);
       std::vector<int> masks(nld);
@@ -413,6 +417,126 @@ std::string build_host_problem(const feti_problem& prob, int method, int dedup,
       for (int d = 0; d < dim; ++d) hp.dof_copy[pos[gn * dim + d]++] = (int64_t)s * nld + ln * dim + d;
     }
   }
+  // ---- single-problem placement tables ----------------------------------------
+  hp.loc_off.resize(hp.n_sub + 1);
+  for (int s2 = 0; s2 <= hp.n_sub; ++s2) hp.loc_off[s2] = (int64_t)s2 * nld;
+  hp.n_loc_total = (int64_t)hp.n_sub * nld;
+  hp.sub_prob.assign(hp.n_sub, 0);
+  hp.n_prob = 1;
+  hp.prob_dof_off = {0, hp.n_dofs};
+  hp.prob_el_off = {0, hp.n_elements};
+  hp.prob_lam_off = {0, hp.n_lam};
+  hp.prob_sub_off = {0, hp.n_sub};
+  hp.prob_primal_off = {0, hp.n_primal};
+  hp.prob_nel = {hp.nel[0], hp.nel[1], hp.nel[2]};
+  return "";
+}
+
+std::string merge_host_problems(std::vector<HostProblem>& parts, HostProblem& out) {
+  out = HostProblem();
+  if (parts.empty()) return "empty batch";
+  const HostProblem& f = parts[0];
+  out.dim = f.dim;
+  out.method = f.method;
+  out.E0 = f.E0; out.Emin = f.Emin; out.nu = f.nu; out.p = f.p;
+  out.n_rbm = f.n_rbm;
+  out.n_prob = (int)parts.size();
+  out.prob_dof_off.push_back(0);
+  out.prob_el_off.push_back(0);
+  out.prob_lam_off.push_back(0);
+  out.prob_sub_off.push_back(0);
+  out.prob_primal_off.push_back(0);
+  out.loc_off.push_back(0);
+  out.b_off.push_back(0);
+  out.c_off.push_back(0);
+  out.group_off.push_back(0);
+  out.prim_off.push_back(0);
+  out.dof_copy_off.push_back(0);
+  for (int q = 0; q < out.n_prob; ++q) {
+    HostProblem& P = parts[q];
+    if (P.dim != out.dim || P.method != out.method) return "batch problems differ in dim or method";
+    if (P.E0 != out.E0 || P.Emin != out.Emin || P.nu != out.nu || P.p != out.p)
+      return "batch problems must share E0, Emin, nu and p";
+    const int t0 = (int)out.types.size(), m0 = (int)out.module_rep.size(), s0 = out.n_sub;
+    const int64_t dof0 = out.n_dofs, el0 = out.n_elements, lam0 = out.n_lam, b0 = out.n_b_total;
+    const int pr0 = out.n_primal;
+    const int64_t c0 = out.c_off.back(), l0 = out.n_loc_total;
+    const int grp0 = (int)out.group_off.size() - 1;
+    const int64_t src0 = (int64_t)out.prim_src.size();
+    for (auto& T : P.types) out.types.push_back(T);
+    for (int s = 0; s < P.n_sub; ++s) {
+      out.sub_type.push_back(P.sub_type[s] + t0);
+      out.sub_module.push_back(P.sub_module[s] + m0);
+      out.sub_prob.push_back(q);
+      out.b_off.push_back(b0 + P.b_off[s + 1]);
+      out.c_off.push_back(c0 + P.c_off[s + 1]);
+      out.loc_off.push_back(l0 + P.loc_off[s + 1]);
+    }
+    for (size_t m = 0; m < P.module_rep.size(); ++m) {
+      out.module_rep.push_back(P.module_rep[m] + s0);
+      out.module_type.push_back(P.module_type[m] + t0);
+    }
+    for (int64_t b = 0; b < P.n_b_total; ++b) out.b_sub.push_back(P.b_sub[b] + s0);
+    for (int64_t l = 0; l < P.n_lam; ++l) {
+      out.lam_b0.push_back(P.lam_b0[l] + (int)b0);
+      out.lam_b1.push_back(P.lam_b1[l] >= 0 ? P.lam_b1[l] + (int)b0 : -1);
+      out.lam_s0.push_back(P.lam_s0[l]);
+      out.lam_s1.push_back(P.lam_s1[l]);
+      out.lam_group.push_back(P.lam_group[l] + grp0);
+    }
+    {
+      const int gb0 = (int)out.group_b.size();
+      for (size_t g = 1; g < P.group_off.size(); ++g) out.group_off.push_back(P.group_off[g] + gb0);
+      for (int v : P.group_b) out.group_b.push_back(v + (int)b0);
+    }
+    for (int v : P.c_glob) out.c_glob.push_back(v + pr0);
+    for (size_t g = 1; g < P.prim_off.size(); ++g) out.prim_off.push_back(P.prim_off[g] + (int)src0);
+    for (int v : P.prim_src) out.prim_src.push_back(v + (int)c0);
+    for (int64_t v : P.load_src) out.load_src.push_back(v >= 0 ? v + dof0 : -1);
+    const int64_t dc0 = (int64_t)out.dof_copy.size();
+    for (size_t g = 1; g < P.dof_copy_off.size(); ++g) out.dof_copy_off.push_back(P.dof_copy_off[g] + dc0);
+    for (int64_t v : P.dof_copy) out.dof_copy.push_back(v + l0);
+    for (unsigned char v : P.dirichlet) out.dirichlet.push_back(v);
+    out.n_sub += P.n_sub;
+    out.n_dofs += P.n_dofs;
+    out.n_nodes += P.n_nodes;
+    out.n_elements += P.n_elements;
+    out.n_lam += P.n_lam;
+    out.n_b_total += P.n_b_total;
+    out.n_primal += P.n_primal;
+    out.n_loc_total += P.n_loc_total;
+    out.prob_dof_off.push_back(out.n_dofs);
+    out.prob_el_off.push_back(out.n_elements);
+    out.prob_lam_off.push_back(out.n_lam);
+    out.prob_sub_off.push_back(out.n_sub);
+    out.prob_primal_off.push_back(out.n_primal);
+    for (int a = 0; a < 3; ++a) out.prob_nel.push_back(P.nel[a]);
+  }
+  // b -> lambda CSR of the merged multipliers
+  std::vector<int> cnt(out.n_b_total + 1, 0);
+  for (int64_t l = 0; l < out.n_lam; ++l) {
+    cnt[out.lam_b0[l] + 1]++;
+    if (out.lam_b1[l] >= 0) cnt[out.lam_b1[l] + 1]++;
+  }
+  out.b2l_off.assign(out.n_b_total + 1, 0);
+  for (int64_t b = 0; b < out.n_b_total; ++b) out.b2l_off[b + 1] = out.b2l_off[b] + cnt[b + 1];
+  out.b2l_lam.resize(out.b2l_off[out.n_b_total]);
+  out.b2l_sign.resize(out.b2l_off[out.n_b_total]);
+  std::vector<int> fill(out.b2l_off.begin(), out.b2l_off.end() - 1);
+  for (int64_t l = 0; l < out.n_lam; ++l) {
+    const int a = out.lam_b0[l];
+    out.b2l_lam[fill[a]] = (int)l; out.b2l_sign[fill[a]] = out.lam_s0[l]; fill[a]++;
+    const int b = out.lam_b1[l];
+    if (b >= 0) { out.b2l_lam[fill[b]] = (int)l; out.b2l_sign[fill[b]] = out.lam_s1[l]; fill[b]++; }
+  }
+  // the single-mesh fields describe the first problem (used only where a batch is not accepted)
+  for (int a = 0; a < 3; ++a) {
+    out.tiles[a] = f.tiles[a]; out.elems[a] = f.elems[a]; out.nel[a] = f.nel[a];
+    out.nnod[a] = f.nnod[a]; out.lnod[a] = f.lnod[a];
+  }
+  out.n_loc_nodes = f.n_loc_nodes;
+  out.n_loc_dofs = f.n_loc_dofs;
+  out.n_loc_elems = f.n_loc_elems;
   return "";
 }
 

@@ -79,6 +79,10 @@ __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t phase) {
   return false;
 }
 
+// PASSES = 1: one TF32 product.  PASSES = 3: the split-TF32 product
+// a b ~ a_hi b_hi + a_hi b_lo + a_lo b_hi with a_hi = tf32(a), a_lo =
+// tf32(a - a_hi), which carries FP32-class accuracy on the tensor cores.
+template <int PASSES>
 __global__ void __launch_bounds__(TC_THREADS) k_tc_apply_tf32(
     const DevType* __restrict__ types, const DevModule* __restrict__ mods, const DevSub* __restrict__ subs,
     const float* __restrict__ fmem, const double* __restrict__ X, int64_t ldx, int m,
@@ -86,9 +90,12 @@ __global__ void __launch_bounds__(TC_THREADS) k_tc_apply_tf32(
     const double* __restrict__ sqrtD, double* __restrict__ Yb, int64_t nbt, int* __restrict__ status) {
   extern __shared__ __align__(1024) unsigned char tc_smem_raw[];
   // 1024-byte aligned staging: A chunk [128 x 128 B], B chunk [256 x 128 B]
+  // (PASSES = 3: followed by the low parts A_lo, B_lo)
   unsigned char* base = tc_smem_raw + ((1024 - (smem_u32(tc_smem_raw) & 1023)) & 1023);
   unsigned char* As = base;
   unsigned char* Bs = base + TC_M * 128;
+  unsigned char* Al = Bs + TC_NMAX * 128;
+  unsigned char* Bl = Al + TC_M * 128;
   __shared__ __align__(8) uint64_t mbar;
   __shared__ uint32_t tmem_base_sh;
 
@@ -128,7 +135,9 @@ __global__ void __launch_bounds__(TC_THREADS) k_tc_apply_tf32(
       const int r = e >> 5, k = e & 31;
       const int gr = row0 + r, gk = k0 + k;
       const float v = (gr < nb && gk < nb) ? F[(int64_t)gr * nb + gk] : 0.0f;
-      *reinterpret_cast<float*>(As + sw128_offset(r, k)) = v;
+      const float hi = to_tf32(v);
+      *reinterpret_cast<float*>(As + sw128_offset(r, k)) = hi;
+      if (PASSES == 3) *reinterpret_cast<float*>(Al + sw128_offset(r, k)) = to_tf32(v - hi);
     }
     // ---- stage B: direction j, K index k: D^{1/2} (B^sT X)[b, j], b = b_off + k0 + k ----
     for (int e = tid; e < np * TC_KC; e += TC_THREADS) {
@@ -140,9 +149,11 @@ __global__ void __launch_bounds__(TC_THREADS) k_tc_apply_tf32(
         const double* x = X + (int64_t)gj * ldx;
         double acc = 0.0;
         for (int q = b2l_off[b]; q < b2l_off[b + 1]; ++q) acc += b2l_sign[q] > 0 ? x[b2l_lam[q]] : -x[b2l_lam[q]];
-        v = to_tf32(static_cast<float>(acc * sqrtD[b]));
+        v = static_cast<float>(acc * sqrtD[b]);
       }
-      *reinterpret_cast<float*>(Bs + sw128_offset(j, k)) = v;
+      const float hi = to_tf32(v);
+      *reinterpret_cast<float*>(Bs + sw128_offset(j, k)) = hi;
+      if (PASSES == 3) *reinterpret_cast<float*>(Bl + sw128_offset(j, k)) = to_tf32(v - hi);
     }
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     __syncthreads();
@@ -150,15 +161,21 @@ __global__ void __launch_bounds__(TC_THREADS) k_tc_apply_tf32(
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
 #pragma unroll
       for (int kk = 0; kk < TC_KC / 8; ++kk) {
-        const uint64_t ad = desc_sw128(smem_u32(As) + kk * 32);
-        const uint64_t bd = desc_sw128(smem_u32(Bs) + kk * 32);
-        const uint32_t acc = (k0 > 0 || kk > 0) ? 1u : 0u;
-        asm volatile(
-            "{\n\t.reg .pred p;\n\t"
-            "setp.ne.b32 p, %4, 0;\n\t"
-            "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem),
-            "l"(ad), "l"(bd), "r"(idesc), "r"(acc)
-            : "memory");
+#pragma unroll
+        for (int pass = 0; pass < PASSES; ++pass) {
+          // pass 0: lo x hi, pass 1: hi x lo, last pass: hi x hi (small terms first)
+          const unsigned char* Ap = (PASSES == 3 && pass == 0) ? Al : As;
+          const unsigned char* Bp = (PASSES == 3 && pass == 1) ? Bl : Bs;
+          const uint64_t ad = desc_sw128(smem_u32(Ap) + kk * 32);
+          const uint64_t bd = desc_sw128(smem_u32(Bp) + kk * 32);
+          const uint32_t acc = (k0 > 0 || kk > 0 || pass > 0) ? 1u : 0u;
+          asm volatile(
+              "{\n\t.reg .pred p;\n\t"
+              "setp.ne.b32 p, %4, 0;\n\t"
+              "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem),
+              "l"(ad), "l"(bd), "r"(idesc), "r"(acc)
+              : "memory");
+        }
       }
       asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar)
                    : "memory");
@@ -224,7 +241,7 @@ __global__ void k_make_lowp(const DevType* __restrict__ types, const DevModule* 
   for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
     const int i = (int)(e / n), j = (int)(e % n);
     const double fv = F[e] / sqrt(F[(int64_t)i * n + i] * F[(int64_t)j * n + j]);
-    fmem[M.F + e] = to_tf32(static_cast<float>(fv));
+    fmem[M.F + e] = static_cast<float>(fv);
     const double sv = Sm[(int64_t)i * nbc + j] / sqrt(Sm[(int64_t)i * nbc + i] * Sm[(int64_t)j * nbc + j]);
     fmem[M.W + e] = static_cast<float>(sv);
   }
@@ -267,7 +284,7 @@ __global__ void k_sub_gemv_lowp(const DevType* __restrict__ types, const DevModu
 
 }  // namespace
 
-size_t tc_apply_smem_bytes() { return 1024 + TC_M * 128 + TC_NMAX * 128; }
+size_t tc_apply_smem_bytes(int passes) { return 1024 + (passes == 3 ? 2 : 1) * (TC_M * 128 + TC_NMAX * 128); }
 
 cudaError_t tc_prepare(const Ctx& c, cudaStream_t st) {
   k_make_lowp<<<dim3(64, c.n_mod), 256, 0, st>>>(c.d_types, c.d_mods, c.d_modmem, c.d_fmem);
@@ -283,16 +300,23 @@ cudaError_t tc_prepare(const Ctx& c, cudaStream_t st) {
 // Yb = D^{1/2} Fhat D^{1/2} B^T X for every subdomain (tensor cores).
 cudaError_t tc_apply_local(const Ctx& c, const double* X, int64_t ldx, int m, double* Yb, cudaStream_t st) {
   static bool attr_set = false;
-  const size_t sm = tc_apply_smem_bytes();
+  const size_t sm1 = tc_apply_smem_bytes(1), sm3 = tc_apply_smem_bytes(3);
   if (!attr_set) {
-    cudaError_t e = cudaFuncSetAttribute(k_tc_apply_tf32, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    cudaError_t e = cudaFuncSetAttribute(k_tc_apply_tf32<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm1);
+    if (e == cudaSuccess)
+      e = cudaFuncSetAttribute(k_tc_apply_tf32<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm3);
     if (e != cudaSuccess) return e;
     attr_set = true;
   }
   dim3 grid((c.max_nb + TC_M - 1) / TC_M, c.hp.n_sub, (m + TC_NMAX - 1) / TC_NMAX);
-  k_tc_apply_tf32<<<grid, TC_THREADS, sm, st>>>(c.d_types, c.d_mods, c.d_subs, c.d_fmem, X, ldx, m, c.d_b2l_off,
-                                                c.d_b2l_lam, c.d_b2l_sign, c.d_sqrtDF, Yb, c.hp.n_b_total,
-                                                c.d_status);
+  if (c.opt.precision == FETI_TF32X3)
+    k_tc_apply_tf32<3><<<grid, TC_THREADS, sm3, st>>>(c.d_types, c.d_mods, c.d_subs, c.d_fmem, X, ldx, m,
+                                                      c.d_b2l_off, c.d_b2l_lam, c.d_b2l_sign, c.d_sqrtDF, Yb,
+                                                      c.hp.n_b_total, c.d_status);
+  else
+    k_tc_apply_tf32<1><<<grid, TC_THREADS, sm1, st>>>(c.d_types, c.d_mods, c.d_subs, c.d_fmem, X, ldx, m,
+                                                      c.d_b2l_off, c.d_b2l_lam, c.d_b2l_sign, c.d_sqrtDF, Yb,
+                                                      c.hp.n_b_total, c.d_status);
   note_launches(1);
   return cudaGetLastError();
 }

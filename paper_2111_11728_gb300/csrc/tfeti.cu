@@ -67,13 +67,16 @@ __device__ __forceinline__ double rbm(int dim, int q, const int c[3], int d) {
 }
 
 // e[(s, q)] = -sum_a R^s(a, q) f^s(a); one block per subdomain.
-__global__ void k_build_e(int dim, int nr, int ln0, int ln1, int nld, const double* __restrict__ floc,
-                          double* __restrict__ e) {
+__global__ void k_build_e(int dim, int nr, const DevType* __restrict__ types, const DevSub* __restrict__ subs,
+                          const double* __restrict__ floc, double* __restrict__ e) {
   const int s = blockIdx.x;
+  const DevSub S = subs[s];
+  const DevType T = types[S.type];
+  const int nld = T.n_loc, ln0 = T.ln[0], ln1 = T.ln[1];
   __shared__ double red[6][32];
   double acc[6] = {0, 0, 0, 0, 0, 0};
   for (int a = threadIdx.x; a < nld; a += blockDim.x) {
-    const double f = floc[(int64_t)s * nld + a];
+    const double f = floc[S.loc_off + a];
     if (f == 0.0) continue;
     const int node = a / dim, d = a % dim;
     const int c[3] = {node % ln0, (node / ln0) % ln1, node / (ln0 * ln1)};
@@ -93,16 +96,19 @@ __global__ void k_build_e(int dim, int nr, int ln0, int ln1, int nld, const doub
 }
 
 // uloc(s, a) += sum_q R^s(a, q) alpha(s, q)
-__global__ void k_add_rbm(int dim, int nr, int ln0, int ln1, int nld, const double* __restrict__ alpha,
-                          double* __restrict__ uloc) {
+__global__ void k_add_rbm(int dim, int nr, const DevType* __restrict__ types, const DevSub* __restrict__ subs,
+                          const double* __restrict__ alpha, double* __restrict__ uloc) {
   const int s = blockIdx.y;
   const int a = blockIdx.x * blockDim.x + threadIdx.x;
+  const DevSub S = subs[s];
+  const DevType T = types[S.type];
+  const int nld = T.n_loc, ln0 = T.ln[0], ln1 = T.ln[1];
   if (a >= nld) return;
   const int node = a / dim, d = a % dim;
   const int c[3] = {node % ln0, (node / ln0) % ln1, node / (ln0 * ln1)};
   double v = 0.0;
   for (int q = 0; q < nr; ++q) v = fma(rbm(dim, q, c, d), alpha[s * nr + q], v);
-  uloc[(int64_t)s * nld + a] += v;
+  uloc[S.loc_off + a] += v;
 }
 
 }  // namespace
@@ -124,16 +130,15 @@ cudaError_t tfeti_build_G(const Ctx& c, double* G, cudaStream_t st) {
 }
 
 cudaError_t tfeti_build_e(const Ctx& c, double* e, cudaStream_t st) {
-  k_build_e<<<c.hp.n_sub, 256, 0, st>>>(c.hp.dim, c.hp.n_rbm, c.hp.lnod[0], c.hp.lnod[1], c.hp.n_loc_dofs,
-                                         c.d_floc, e);
+  k_build_e<<<c.hp.n_sub, 256, 0, st>>>(c.hp.dim, c.hp.n_rbm, c.d_types, c.d_subs, c.d_floc, e);
   note_launches(1);
   return cudaGetLastError();
 }
 
 cudaError_t tfeti_add_rbm(const Ctx& c, const double* alpha, cudaStream_t st) {
   const int nld = c.hp.n_loc_dofs;
-  k_add_rbm<<<dim3((nld + 127) / 128, c.hp.n_sub), 128, 0, st>>>(c.hp.dim, c.hp.n_rbm, c.hp.lnod[0], c.hp.lnod[1],
-                                                                 nld, alpha, c.d_uloc);
+  k_add_rbm<<<dim3((nld + 127) / 128, c.hp.n_sub), 128, 0, st>>>(c.hp.dim, c.hp.n_rbm, c.d_types, c.d_subs,
+                                                                 alpha, c.d_uloc);
   note_launches(1);
   return cudaGetLastError();
 }

@@ -1,0 +1,81 @@
+"""The batching form: independent state problems of uneven size set up in one
+context, every launch covering the whole batch, one PCG per problem advanced
+by a replayed CUDA graph.  Each problem's displacement must match a direct
+solve of its own Eq. (2) and its iteration count the single-problem PCG."""
+import numpy as np
+import pytest
+
+import workloads
+from oracle.assemble import direct_solve
+
+pytestmark = pytest.mark.gpu
+
+fg = pytest.importorskip("paper_2111_11728_gb300")
+from gpu_helpers import rel, solve_u, torch_cuda  # noqa: E402
+
+
+def _batch(n=5, seed=8):
+    rng = np.random.default_rng(seed)
+    probs = []
+    for q in range(n):
+        t = (int(rng.integers(2, 5)), int(rng.integers(2, 5)))
+        e = (int(rng.integers(3, 9)), int(rng.integers(3, 9)))
+        rho = rng.uniform(0.05, 1.0, size=t[0] * e[0] * t[1] * e[1])
+        probs.append(workloads.tile_problem(f"b{q}", 2, t, e, rho, Emin=1e-6))
+    return probs
+
+
+def _solve_batch(probs, tol):
+    torch = torch_cuda()
+    o = fg.feti_options_default()
+    o.method, o.scaling, o.krylov, o.tol, o.max_iter = fg.FETI_FETIDP, fg.FETI_SCALING_K, fg.FETI_PCG, tol, 2000
+    ctx = fg.feti_create(o, torch.cuda.current_stream().cuda_stream)
+    keep, structs = [], []
+    for p in probs:
+        rho = torch.from_numpy(p.rho).cuda()
+        f = torch.from_numpy(p.f).cuda()
+        d = np.ascontiguousarray(p.dirichlet, np.uint8)
+        keep += [rho, f, d]
+        structs.append(fg.make_problem(p.dim, p.tiles, p.elems, p.E0, p.Emin, p.nu, p.p, rho, d, f, True))
+    fg.feti_setup_batch(ctx, structs)
+    assert fg.feti_query(ctx, fg.FETI_Q_N_PROBLEMS) == len(probs)
+    fg.feti_factorize(ctx)
+    status, st = fg.feti_solve_dual(ctx, allow_notconv=True)
+    n_total = sum(p.n_dofs for p in probs)
+    u = torch.empty(n_total, dtype=torch.float64, device="cuda")
+    fg.feti_recover_displacements(ctx, u, True)
+    res = [fg.feti_problem_result(ctx, q) for q in range(len(probs))]
+    fg.feti_destroy(ctx)
+    return u.cpu().numpy(), st, res
+
+
+def test_batch_matches_direct_and_single_solves():
+    probs = _batch()
+    u, st, res = _solve_batch(probs, 1e-12)
+    assert st.converged
+    for q, p in enumerate(probs):
+        off = res[q][0]
+        uq = u[off:off + p.n_dofs]
+        ud = direct_solve(p)
+        assert rel(uq, ud) <= 1e-8, q
+        assert res[q][4] == pytest.approx(p.f @ ud, rel=1e-8)
+        _, st1, _, _ = solve_u(p, krylov="pcg", tol=1e-12, max_iter=2000)
+        assert abs(res[q][3].iterations - st1.iterations) <= max(2, 0.1 * st1.iterations), (q, res[q][3].iterations,
+                                                                                          st1.iterations)
+
+
+def test_batch_of_one_equals_single_problem():
+    p = _batch(n=1)[0]
+    u, st, res = _solve_batch([p], 1e-10)
+    u1, st1, _, _ = solve_u(p, krylov="pcg", tol=1e-10)
+    assert st.iterations == st1.iterations
+    assert rel(u, u1) <= 1e-12
+
+
+def test_batching_workload_generator_small():
+    probs = workloads.config3(n_problems=6, tile_range=(2, 4), elem_range=(4, 8))
+    u, st, res = _solve_batch(probs, 1e-10)
+    assert st.converged
+    for q, p in enumerate(probs):
+        off = res[q][0]
+        assert rel(u[off:off + p.n_dofs], direct_solve(p)) <= 1e-6

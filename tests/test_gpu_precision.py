@@ -4,6 +4,8 @@ iterative refinement on the dual residual.
 
 * The tensor-core operator against the FP64 operator: normwise relative
   difference of F X within the TF32 rounding of the scaled blocks (<= 3e-3).
+* The three-pass split-TF32 operator (hi*hi + hi*lo + lo*hi) is FP32-class:
+  within 2e-5 of the FP64 operator and at least 20x closer than one pass.
 * At moderate stiffness contrast the refined solution reaches the FP64 bar
   (<= 1e-8 relative displacement error against a direct solve of Eq. 2).
 """
@@ -43,6 +45,35 @@ def test_tensor_core_operator_close_to_fp64(m):
     a, b = Y32.cpu().numpy(), Y64.cpu().numpy()
     assert rel(a, b) <= 3e-3
     assert rel(a, b) > 0.0          # the tensor-core path really ran in reduced precision
+
+
+@pytest.mark.parametrize("m", [1, 37, 256])
+def test_split_tf32_operator_is_fp32_class(m):
+    torch = torch_cuda()
+    p = moderate(tiles=5, elems=12)
+    s64 = make_solver(p)
+    s1 = make_solver(p, precision=fg.FETI_TF32)
+    s3 = make_solver(p, precision=fg.FETI_TF32X3)
+    for s in (s64, s1, s3):
+        fg.feti_factorize(s.ctx)
+    n = s64.query(fg.FETI_Q_N_LAMBDA)
+    X = torch.from_numpy(np.random.default_rng(100 + m).standard_normal((m, n))).cuda()
+    Ys = []
+    for s in (s64, s1, s3):
+        Y = torch.zeros_like(X)
+        fg.feti_apply_dual(s.ctx, X, n, m, Y, n)
+        Ys.append(Y.cpu().numpy())
+    d1, d3 = rel(Ys[1], Ys[0]), rel(Ys[2], Ys[0])
+    assert 0.0 < d3 <= 2e-5
+    assert d3 * 20 <= d1
+
+
+def test_refined_split_tf32_solve_needs_few_refinements():
+    p = moderate()
+    ud = direct_solve(p)
+    u, st, c, _ = solve_u(p, tol=1e-10, precision=fg.FETI_TF32X3)
+    assert st.converged and 1 <= st.refinements <= 4
+    assert rel(u, ud) <= 1e-8
 
 
 @pytest.mark.parametrize("method", ["fetidp", "tfeti"])
