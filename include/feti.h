@@ -74,9 +74,10 @@ typedef struct {
   int dedup_modules;   /* 1: factorize identical modules once (Section 1) */
   double tol;          /* relative tolerance on sqrt(r^T z) (default 1e-6) */
   double rr_tol;       /* rank-revealing cutoff on the remaining/initial pivot ratio (1e-10) */
-  double inner_tol;    /* FETI_TF32: relative tolerance of each low-precision inner solve (1e-2);
-                          each inner solve is also capped at 30 iterations */
-  int max_refine;      /* FETI_TF32: cap on the FP64 refinement steps (30) */
+  double inner_tol;    /* FETI_TF32 / FETI_TF32X3: relative tolerance of each low-precision inner
+                          solve; 0 (default) picks 1e-2 for FETI_TF32 and 1e-5 for FETI_TF32X3.
+                          Each inner solve is also capped at 30 iterations */
+  int max_refine;      /* FETI_TF32 / FETI_TF32X3: cap on the FP64 refinement steps (30) */
 } feti_options;
 
 typedef struct {

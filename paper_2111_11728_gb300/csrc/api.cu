@@ -123,6 +123,11 @@ feti_status ensure_blocks(Ctx& c, int m) {
     TRY(dalloc(c, c.d_ct1, (size_t)c.n_coarse * cap));
     TRY(dalloc(c, c.d_ct2, (size_t)c.n_coarse * cap));
   }
+  if (c.opt.precision != FETI_FP64) {
+    TRY(dalloc(c, c.d_xb_hi, (size_t)c.nbp_total * cap));
+    if (c.opt.precision == FETI_TF32X3) TRY(dalloc(c, c.d_xb_lo, (size_t)c.nbp_total * cap));
+    c.xb_cap = cap;
+  }
   c.blk_cap = cap;
   return build_block_descs(c);
 }
@@ -248,15 +253,15 @@ feti_status apply_dual(Ctx& c, const double* X, int64_t ldx, int m, double* Y, i
 // accumulation); the thin corner coupling and the coarse solve stay FP64.
 feti_status apply_dual_lowp(Ctx& c, const double* X, int64_t ldx, int m, double* Y, int64_t ldy) {
   TRY(ensure_blocks(c, m));
-  if (c.hp.method == FETI_FETIDP && c.hp.n_primal > 0) {
-    CU(gather_lam_to_b(c, X, ldx, m, c.d_Xb, c.stream));
-    CU(corner_reduce(c, c.d_Xb, m, c.d_Cb, c.d_Vraw, c.stream));
+  CU(tc_gather(c, X, ldx, m, c.stream));
+  if (c.tc_aug) {
+    // corner reduction (FP32), coarse solve (FP64), then the coarse
+    // correction rides in the K-extension of the one tensor-core product
+    CU(tc_corner_reduce(c, m, c.d_Vraw, c.stream));
     CU(coarse_apply(c, c.d_Vraw, c.d_V, m, c.stream));
-    CU(tc_apply_local(c, X, ldx, m, c.d_Yb, c.stream));
-    CU(corner_expand_thin(c, c.d_V, m, c.d_Yb, c.stream));
-  } else {
-    CU(tc_apply_local(c, X, ldx, m, c.d_Yb, c.stream));
+    CU(tc_put_v(c, c.d_V, m, c.stream));
   }
+  CU(tc_product(c, m, c.d_Yb, c.stream));
   CU(scatter_b_to_lam(c, c.d_Yb, m, Y, ldy, c.stream));
   return FETI_OK;
 }
@@ -332,7 +337,7 @@ feti_status feti_options_default(feti_options* opt) {
   opt->dedup_modules = 1;
   opt->tol = 1e-6;
   opt->rr_tol = 1e-10;
-  opt->inner_tol = 1e-2;
+  opt->inner_tol = 0.0;                 // automatic: 1e-2 (TF32), 1e-5 (split TF32)
   opt->max_refine = 30;
   return FETI_OK;
 }
@@ -348,7 +353,7 @@ feti_status feti_create(feti_ctx** out, const feti_options* opt, void* stream) {
       (o.krylov < FETI_PCG || o.krylov > FETI_RRS) || o.max_iter < 0 || !(o.tol >= 0.0) || !(o.rr_tol >= 0.0))
     return FETI_EINVAL;
   if (o.precision != FETI_FP64 && o.precision != FETI_TF32 && o.precision != FETI_TF32X3) return FETI_EINVAL;
-  if (o.precision != FETI_FP64 && !(o.inner_tol > 0.0 && o.inner_tol < 1.0 && o.max_refine > 0)) return FETI_EINVAL;
+  if (o.precision != FETI_FP64 && !(o.inner_tol >= 0.0 && o.inner_tol < 1.0 && o.max_refine > 0)) return FETI_EINVAL;
   feti_ctx* ctx = new (std::nothrow) feti_ctx;
   if (!ctx) return FETI_ENOMEM;
   Ctx& c = ctx->c;
@@ -589,6 +594,42 @@ static feti_status setup_impl(Ctx& c, const feti_problem* probs, int n) {
     TRY(dalloc(c, c.d_alpha, nco));
   }
   if (c.opt.precision != FETI_FP64) {
+    // tensor-core operand layout: module rows in one arena, padded interface space
+    std::vector<int> frow(c.n_mod);
+    int64_t rows = 0;
+    for (int q = 0; q < c.n_mod; ++q) {
+      frow[q] = (int)rows;
+      rows += c.h_types[c.h_mods[q].type].n_b;
+    }
+    c.tc_aug = (hp.method == FETI_FETIDP && hp.n_primal > 0 && c.max_nc <= 24) ? 1 : 0;
+    if (hp.method == FETI_FETIDP && hp.n_primal > 0 && !c.tc_aug) {
+      c.err = "precision form: more than 24 corner DOFs per subdomain";
+      return FETI_ENOTSUP;
+    }
+    std::vector<int64_t> bpad(hp.n_sub);
+    int64_t nbp = 0, kmax = 32;
+    for (int s = 0; s < hp.n_sub; ++s) {
+      const DevType& T = c.h_types[c.h_subs[s].type];
+      bpad[s] = nbp;
+      const int kx = tc_k_extent(T.n_b, T.n_c, c.tc_aug);
+      nbp += kx;
+      kmax = std::max<int64_t>(kmax, kx);
+    }
+    if (rows >= (int64_t)1 << 31 || nbp >= (int64_t)1 << 31) {
+      c.err = "precision form: interface space too large for 32-bit tensor coordinates";
+      return FETI_ENOTSUP;
+    }
+    c.fa_pitch = kmax;
+    c.fa_rows = std::max<int64_t>(rows, 1);
+    c.nbp_total = std::max<int64_t>(nbp, 32);
+    TRY(upload(c, c.d_frow, frow));
+    TRY(upload(c, c.d_bpad, bpad));
+    TRY(dalloc(c, c.d_fa_hi, (size_t)(c.fa_rows * c.fa_pitch)));
+    CU(cudaMemset(c.d_fa_hi, 0, (size_t)(c.fa_rows * c.fa_pitch) * sizeof(float)));
+    if (c.opt.precision == FETI_TF32X3) {
+      TRY(dalloc(c, c.d_fa_lo, (size_t)(c.fa_rows * c.fa_pitch)));
+      CU(cudaMemset(c.d_fa_lo, 0, (size_t)(c.fa_rows * c.fa_pitch) * sizeof(float)));
+    }
     TRY(dalloc(c, c.d_fmem, (size_t)c.modmem_len));
     TRY(dalloc(c, c.d_sqrtDF, nbt));
     TRY(dalloc(c, c.d_sqrtDS, nbt));
@@ -971,7 +1012,8 @@ static feti_status solve_impl(Ctx& c, double* lambda_inout, feti_stats* stats) {
       // each correction is capped (a stalled reduced-precision solve still
       // returns a useful correction; the FP64 outer loop decides convergence)
       const int cap = std::min(c.opt.max_iter - S.iterations, 30);
-      feti_status s2 = krylov_core(c, c.opt.inner_tol, cap, true, inner);
+      const double itol = c.opt.inner_tol > 0.0 ? c.opt.inner_tol : (c.opt.precision == FETI_TF32X3 ? 1e-5 : 1e-2);
+      feti_status s2 = krylov_core(c, itol, cap, true, inner);
       S.iterations += inner.iterations;
       S.f_applies += inner.f_applies;
       S.last_rank = inner.last_rank;

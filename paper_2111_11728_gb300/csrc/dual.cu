@@ -201,6 +201,11 @@ cudaError_t corner_reduce(Ctx& c, const double* /*Xb*/, int m, double* /*Cb*/, d
     e = dgemm_batched(c.d_gemm_FrcT, c.hp.n_sub, c.max_nc, c.max_nb, m, 1.0, 0.0, st, c.fl_FrcT * m);
   }
   if (e != cudaSuccess) return e;
+  return corner_assemble(c, m, Vraw, st);
+}
+
+// Vraw[g, j] = sum of Cb over the corner copies of primal DOF g.
+cudaError_t corner_assemble(const Ctx& c, int m, double* Vraw, cudaStream_t st) {
   const int np = c.hp.n_primal;
   dim3 g((np + 127) / 128, m);
   k_corner_gather<<<g, 128, 0, st>>>(np, m, c.d_prim_off, c.d_prim_src, c.d_Cb, c.n_c_total, Vraw);

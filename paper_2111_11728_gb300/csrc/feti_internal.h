@@ -218,7 +218,16 @@ struct Ctx {
   double* d_Kbar_inv = nullptr;  // [n_coarse^2] explicit inverse
   double* d_coarse_work = nullptr;   // blocked coarse factorisation work
   // precision form (FETI_TF32)
-  float* d_fmem = nullptr;       // FP32 copies at the module offsets: Fhat at M.F, Shat at M.W
+  float* d_fmem = nullptr;       // FP32 copies at the module offsets: Shat at M.W
+  float* d_fa_hi = nullptr;      // [fa_rows x fa_pitch] Fhat rows of every module, TF32, zero padded
+  float* d_fa_lo = nullptr;      // same layout: TF32 rounding of the remainder (split product)
+  int64_t fa_pitch = 0, fa_rows = 0;
+  int* d_frow = nullptr;         // [n_mod] first arena row of each module
+  int64_t nbp_total = 0;         // interface space with each subdomain padded to a multiple of 32
+  int64_t* d_bpad = nullptr;     // [n_sub] padded offsets
+  float *d_xb_hi = nullptr, *d_xb_lo = nullptr;   // [m x nbp_total] gathered scaled directions
+  int xb_cap = 0;
+  int tc_aug = 0;                // FETI-DP corner coupling appended to the operands (K-extension)
   double* d_sqrtDF = nullptr;    // [n_b_total] sqrt(diag F_s)
   double* d_sqrtDS = nullptr;    // [n_b_total] sqrt(diag S_s)
   double *d_rout = nullptr, *d_zout = nullptr, *d_dl = nullptr;   // refinement vectors

@@ -139,7 +139,12 @@ cudaError_t gemv_dense(const double* A, int n, int ld, const double* x, double* 
 size_t tc_apply_smem_bytes(int passes);
 cudaError_t tc_prepare(const Ctx& c, cudaStream_t st);   // Fhat, Shat (FP32) and sqrt-diagonals
 // Yb = D^{1/2} Fhat D^{1/2} B^T X (tcgen05 kind::tf32); rows >= n_b untouched
-cudaError_t tc_apply_local(const Ctx& c, const double* X, int64_t ldx, int m, double* Yb, cudaStream_t st);
+cudaError_t tc_gather(const Ctx& c, const double* X, int64_t ldx, int m, cudaStream_t st);
+cudaError_t tc_corner_reduce(const Ctx& c, int m, double* Vraw, cudaStream_t st);
+cudaError_t tc_put_v(const Ctx& c, const double* V, int m, cudaStream_t st);
+cudaError_t tc_product(const Ctx& c, int m, double* Yb, cudaStream_t st);
+int tc_k_extent(int nb, int nc, int aug);
+cudaError_t corner_assemble(const Ctx& c, int m, double* Vraw, cudaStream_t st);
 cudaError_t lowp_gemv_S(const Ctx& c, const double* xb, double* yb, cudaStream_t st);
 // Yb(s) += F_rc,s V[c_glob(s), :] with a thin kernel (no tile padding)
 cudaError_t corner_expand_thin(Ctx& c, const double* V, int m, double* Yb, cudaStream_t st);

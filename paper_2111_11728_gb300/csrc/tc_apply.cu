@@ -2,17 +2,13 @@
 //
 //   Y_b(s) = D_s^{1/2} Fhat_s D_s^{1/2} X_b(s),   Fhat_s = D_s^{-1/2} F_s D_s^{-1/2},
 //
-// with D_s = diag(F_s).  Fhat_s is stored in FP32 (rounded to TF32), the
-// product runs on the 5th-generation tensor cores (tcgen05.mma kind::tf32)
-// with FP32 accumulation in tensor memory.  X_b(s) = B^sT X is gathered from
-// the multiplier space straight into shared memory (signed, scaled by
-// D^{1/2}, rounded to TF32) -- no interface-space copy of X is written.
-//
-// One CTA of 128 threads computes a 128-row tile of one subdomain's output for
-// up to 256 direction columns.  K is streamed in chunks of 32 FP32 values (one
-// 128-byte swizzle row); thread 0 issues four K=8 MMAs per chunk and commits
-// them to an mbarrier that the CTA waits on (bounded: on time-out the kernel
-// records an error code, waits once more, frees its tensor memory and exits).
+// with D_s = diag(F_s).  Fhat_s is kept in TF32 (and, for the split product,
+// the TF32 rounding of its remainder), the product runs on the 5th-generation
+// tensor cores (tcgen05.mma kind::tf32) with FP32 accumulation in tensor
+// memory, operands staged by TMA into 128-byte-swizzled shared memory.
+#include <cuda.h>
+#include <cudaTypedefs.h>
+
 #include <cstdint>
 
 #include "kernels.h"
@@ -27,6 +23,8 @@ constexpr int TC_NMAX = 256;
 constexpr int TC_THREADS = 128;
 constexpr uint32_t TC_TMEM_COLS = 256;
 constexpr long long TC_SPIN_LIMIT = 1ll << 22;
+constexpr int TC_STAGES1 = 4;       // ring depth, one TF32 pass (48 KB per stage)
+constexpr int TC_STAGES3 = 2;       // ring depth, split product (96 KB per stage)
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
   return static_cast<uint32_t>(__cvta_generic_to_shared(p));
@@ -79,35 +77,100 @@ __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t phase) {
   return false;
 }
 
-// PASSES = 1: one TF32 product.  PASSES = 3: the split-TF32 product
-// a b ~ a_hi b_hi + a_hi b_lo + a_lo b_hi with a_hi = tf32(a), a_lo =
-// tf32(a - a_hi), which carries FP32-class accuracy on the tensor cores.
-template <int PASSES>
-__global__ void __launch_bounds__(TC_THREADS) k_tc_apply_tf32(
-    const DevType* __restrict__ types, const DevModule* __restrict__ mods, const DevSub* __restrict__ subs,
-    const float* __restrict__ fmem, const double* __restrict__ X, int64_t ldx, int m,
-    const int* __restrict__ b2l_off, const int* __restrict__ b2l_lam, const signed char* __restrict__ b2l_sign,
-    const double* __restrict__ sqrtD, double* __restrict__ Yb, int64_t nbt, int* __restrict__ status) {
-  extern __shared__ __align__(1024) unsigned char tc_smem_raw[];
-  // 1024-byte aligned staging: A chunk [128 x 128 B], B chunk [256 x 128 B]
-  // (PASSES = 3: followed by the low parts A_lo, B_lo)
-  unsigned char* base = tc_smem_raw + ((1024 - (smem_u32(tc_smem_raw) & 1023)) & 1023);
-  unsigned char* As = base;
-  unsigned char* Bs = base + TC_M * 128;
-  unsigned char* Al = Bs + TC_NMAX * 128;
-  unsigned char* Bl = Al + TC_M * 128;
-  __shared__ __align__(8) uint64_t mbar;
-  __shared__ uint32_t tmem_base_sh;
 
-  const DevSub S = subs[blockIdx.y];
+// K extent of a subdomain in the tensor-core operands: n_b rounded up to 32,
+// plus one 32-wide chunk for the corner coupling when it is appended.
+__host__ __device__ __forceinline__ int k_extent(int nb, int nc, int aug) {
+  return (nb + TC_KC - 1) / TC_KC * TC_KC + ((aug && nc > 0) ? TC_KC : 0);
+}
+
+__device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap* map, int x, int y, uint32_t bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::
+          "r"(dst),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(bar)
+      : "memory");
+}
+
+__device__ __forceinline__ void mma_tf32(uint32_t tmem, uint64_t ad, uint64_t bd, uint32_t idesc, uint32_t acc) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "setp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem),
+      "l"(ad), "l"(bd), "r"(idesc), "r"(acc)
+      : "memory");
+}
+
+// 32 consecutive FP32 columns of this warp's 32 TMEM lanes (one per thread).
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&v)[32]) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 "
+      "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+      "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+      : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
+        "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15]),
+        "=r"(v[16]), "=r"(v[17]), "=r"(v[18]), "=r"(v[19]), "=r"(v[20]), "=r"(v[21]), "=r"(v[22]),
+        "=r"(v[23]), "=r"(v[24]), "=r"(v[25]), "=r"(v[26]), "=r"(v[27]), "=r"(v[28]), "=r"(v[29]),
+        "=r"(v[30]), "=r"(v[31])
+      : "r"(taddr)
+      : "memory");
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+
+// Operands of the tensor-core product, laid out for TMA:
+//
+//   A: the scaled blocks Fhat_s of every module, one row of the "arena" per
+//      block row, a common pitch P and zero beyond n_b.  FETI-DP with corners
+//      appends, after n_b rounded up to 32, the row's scaled corner coupling
+//      Frc_hat_s = D_s^{-1/2} F_rc,s (n_c <= 24 columns, one more 32-wide K
+//      chunk).  Tensor map: dims {P, rows}, box {32, 128}, 128-byte swizzle.
+//   B: the gathered, scaled directions D_s^{1/2} B^sT X, one column per
+//      direction over the padded interface space (each subdomain's range
+//      rounded up to 32 entries, zero in the padding), followed for FETI-DP
+//      by the subdomain's coarse correction V_s (the K-extension matching
+//      Frc_hat).  Tensor map: dims {padded total, m}, box {32, 256}.
+//
+// With the K-extension one product gives the whole local FETI-DP operator
+// D^{1/2} [Fhat | Frc_hat] [D^{1/2} X_b ; V_s] = F_s X_b + F_rc,s V_s.
+//
+// Both are stored as TF32 high parts (and, for the split product, TF32 low
+// parts).  One CTA computes a 128-row x 256-column output tile of one
+// subdomain: thread 0 streams K chunks of 32 through a STAGES-deep ring of
+// shared-memory buffers (full / empty mbarriers), thread 32 issues the MMAs
+// (4 K=8 steps x PASSES per chunk) and frees a buffer by committing to its
+// empty barrier; the final commit releases the epilogue, in which each warp
+// reads its 32 TMEM lanes and writes FP64 rows scaled by D_s^{1/2}.
+// Every wait is bounded: on time-out the CTA records an error code, waits
+// (bounded) for its copies and MMAs in flight, frees its tensor memory and
+// returns.
+template <int PASSES, int STAGES>
+__global__ void __launch_bounds__(TC_THREADS, 1) k_tc_apply(
+    const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmAl,
+    const __grid_constant__ CUtensorMap tmB, const __grid_constant__ CUtensorMap tmBl,
+    const DevType* __restrict__ types, const DevSub* __restrict__ subs, const int* __restrict__ frow,
+    const int64_t* __restrict__ bpad, const double* __restrict__ sqrtD, double* __restrict__ Yb, int64_t nbt,
+    int m, int n_cb, int aug, int* __restrict__ status) {
+  constexpr uint32_t A_BYTES = TC_M * 128, B_BYTES = TC_NMAX * 128;
+  constexpr uint32_t STAGE_BYTES = (PASSES == 3 ? 2 : 1) * (A_BYTES + B_BYTES);
+  extern __shared__ __align__(1024) unsigned char tc_smem_raw[];
+  unsigned char* base = tc_smem_raw + ((1024 - (smem_u32(tc_smem_raw) & 1023)) & 1023);
+  __shared__ __align__(8) uint64_t full_bar[STAGES], empty_bar[STAGES], done_bar;
+  __shared__ uint32_t tmem_base_sh;
+  __shared__ int fail_sh, consumed_sh;
+
+  const int sidx = blockIdx.y;
+  const int cb = blockIdx.x % n_cb, rb = blockIdx.x / n_cb;
+  const DevSub S = subs[sidx];
   const DevType T = types[S.type];
   const int nb = T.n_b;
-  const int row0 = blockIdx.x * TC_M;
-  const int col0 = blockIdx.z * TC_NMAX;
-  if (row0 >= nb || col0 >= m) return;
+  const int row0 = rb * TC_M;
+  if (row0 >= nb) return;                              // block-uniform
+  const int col0 = cb * TC_NMAX;
   const int ncols = min(TC_NMAX, m - col0);
   const int np = ((ncols + 15) / 16) * 16;
-  const float* F = fmem + mods[S.module].F;          // Fhat_s, nb x nb row-major FP32
+  const int nk = k_extent(nb, T.n_c, aug) / TC_KC;
+  const int arow = frow[S.module] + row0;
+  const int bx0 = (int)bpad[sidx];
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
 
   if (warp == 0) {
@@ -116,107 +179,102 @@ __global__ void __launch_bounds__(TC_THREADS) k_tc_apply_tf32(
                  : "memory");
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
   }
-  if (tid == 0) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&mbar)) : "memory");
+  if (tid == 32) {
+    for (int i = 0; i < STAGES; ++i) {
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&full_bar[i])) : "memory");
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&empty_bar[i])) : "memory");
+    }
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&done_bar)) : "memory");
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    fail_sh = 0;
+    consumed_sh = 0;
   }
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   const uint32_t tmem = tmem_base_sh;
-  const uint32_t bar = smem_u32(&mbar);
-  const uint32_t idesc = idesc_tf32(np);
-  uint32_t phase = 0;
-  bool failed = false;
 
-  for (int k0 = 0; k0 < nb; k0 += TC_KC) {
-    // ---- stage A: 128 rows x 32 K of Fhat (zero outside the matrix) ----
-    for (int e = tid; e < TC_M * TC_KC; e += TC_THREADS) {
-      const int r = e >> 5, k = e & 31;
-      const int gr = row0 + r, gk = k0 + k;
-      const float v = (gr < nb && gk < nb) ? F[(int64_t)gr * nb + gk] : 0.0f;
-      const float hi = to_tf32(v);
-      *reinterpret_cast<float*>(As + sw128_offset(r, k)) = hi;
-      if (PASSES == 3) *reinterpret_cast<float*>(Al + sw128_offset(r, k)) = to_tf32(v - hi);
-    }
-    // ---- stage B: direction j, K index k: D^{1/2} (B^sT X)[b, j], b = b_off + k0 + k ----
-    for (int e = tid; e < np * TC_KC; e += TC_THREADS) {
-      const int j = e >> 5, k = e & 31;
-      const int gk = k0 + k, gj = col0 + j;
-      float v = 0.0f;
-      if (gk < nb && gj < m) {
-        const int64_t b = S.b_off + gk;
-        const double* x = X + (int64_t)gj * ldx;
-        double acc = 0.0;
-        for (int q = b2l_off[b]; q < b2l_off[b + 1]; ++q) acc += b2l_sign[q] > 0 ? x[b2l_lam[q]] : -x[b2l_lam[q]];
-        v = static_cast<float>(acc * sqrtD[b]);
+  int issued = 0;                                      // producer's count of chunks in flight or consumed
+  if (tid == 0) {
+    // ---- producer: TMA loads of A and B chunks into the ring ----
+    for (int kc = 0; kc < nk; ++kc) {
+      const int st = kc % STAGES, it = kc / STAGES;
+      if (kc >= STAGES && !mbar_wait(smem_u32(&empty_bar[st]), (uint32_t)((it - 1) & 1))) {
+        atomicExch(&fail_sh, 1);
+        break;
       }
-      const float hi = to_tf32(v);
-      *reinterpret_cast<float*>(Bs + sw128_offset(j, k)) = hi;
-      if (PASSES == 3) *reinterpret_cast<float*>(Bl + sw128_offset(j, k)) = to_tf32(v - hi);
+      if (*(volatile int*)&fail_sh) break;
+      unsigned char* sb = base + st * STAGE_BYTES;
+      const uint32_t fb = smem_u32(&full_bar[st]);
+      asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(fb), "r"(STAGE_BYTES) : "memory");
+      tma_load_2d(smem_u32(sb), &tmA, kc * TC_KC, arow, fb);
+      tma_load_2d(smem_u32(sb + A_BYTES), &tmB, bx0 + kc * TC_KC, col0, fb);
+      if (PASSES == 3) {
+        tma_load_2d(smem_u32(sb + A_BYTES + B_BYTES), &tmAl, kc * TC_KC, arow, fb);
+        tma_load_2d(smem_u32(sb + 2 * A_BYTES + B_BYTES), &tmBl, bx0 + kc * TC_KC, col0, fb);
+      }
+      issued = kc + 1;
     }
-    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-    __syncthreads();
-    if (tid == 0) {
+  } else if (tid == 32) {
+    // ---- MMA issuer ----
+    const uint32_t idesc = idesc_tf32(np);
+    int kc = 0;
+    for (; kc < nk; ++kc) {
+      const int st = kc % STAGES, it = kc / STAGES;
+      if (!mbar_wait(smem_u32(&full_bar[st]), (uint32_t)(it & 1))) {
+        atomicExch(&fail_sh, 1);
+        break;
+      }
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      const uint32_t sa = smem_u32(base + st * STAGE_BYTES);
+      const uint32_t sbh = sa + A_BYTES;
+      const uint32_t sal = sa + A_BYTES + B_BYTES;
+      const uint32_t sbl = sa + 2 * A_BYTES + B_BYTES;
 #pragma unroll
       for (int kk = 0; kk < TC_KC / 8; ++kk) {
 #pragma unroll
         for (int pass = 0; pass < PASSES; ++pass) {
-          // pass 0: lo x hi, pass 1: hi x lo, last pass: hi x hi (small terms first)
-          const unsigned char* Ap = (PASSES == 3 && pass == 0) ? Al : As;
-          const unsigned char* Bp = (PASSES == 3 && pass == 1) ? Bl : Bs;
-          const uint64_t ad = desc_sw128(smem_u32(Ap) + kk * 32);
-          const uint64_t bd = desc_sw128(smem_u32(Bp) + kk * 32);
-          const uint32_t acc = (k0 > 0 || kk > 0 || pass > 0) ? 1u : 0u;
-          asm volatile(
-              "{\n\t.reg .pred p;\n\t"
-              "setp.ne.b32 p, %4, 0;\n\t"
-              "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem),
-              "l"(ad), "l"(bd), "r"(idesc), "r"(acc)
-              : "memory");
+          // split product: lo x hi, hi x lo, then hi x hi (small terms first)
+          const uint32_t ap = (PASSES == 3 && pass == 0) ? sal : sa;
+          const uint32_t bp = (PASSES == 3 && pass == 1) ? sbl : sbh;
+          const uint32_t acc = (kc > 0 || kk > 0 || pass > 0) ? 1u : 0u;
+          mma_tf32(tmem, desc_sw128(ap + kk * 32), desc_sw128(bp + kk * 32), idesc, acc);
         }
       }
-      asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar)
+      asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                       smem_u32(&empty_bar[st]))
                    : "memory");
     }
-    __syncwarp();
-    const bool ok = mbar_wait(bar, phase);
-    if (__syncthreads_or(!ok)) {           // block-uniform decision
-      failed = true;
-      if (tid == 0) atomicCAS(status, 0, 3000000 + blockIdx.y);
-      if (!ok) mbar_wait(bar, phase);      // one more bounded wait for the MMAs in flight
-      break;
-    }
-    phase ^= 1u;
-    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    consumed_sh = kc;
+    // arrives once every MMA issued above has completed (also after a failure)
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                     smem_u32(&done_bar))
+                 : "memory");
   }
-
-  if (!failed) {
+  __syncwarp();
+  const bool ok = mbar_wait(smem_u32(&done_bar), 0u);
+  const bool failed = __syncthreads_or(!ok || fail_sh != 0);
+  if (failed) {
+    if (tid == 0) {
+      atomicCAS(status, 0, 3000000 + sidx);
+      // wait for the copies that were issued but never consumed
+      for (int kc = consumed_sh; kc < issued; ++kc)
+        mbar_wait(smem_u32(&full_bar[kc % STAGES]), (uint32_t)((kc / STAGES) & 1));
+    }
+    if (!ok) mbar_wait(smem_u32(&done_bar), 0u);
+  } else {
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     // ---- epilogue: warp w owns TMEM lanes [32w, 32w+32) = output rows ----
     const int r = row0 + warp * 32 + lane;
     const double sd = r < nb ? sqrtD[S.b_off + r] : 0.0;
+    double* yrow = Yb + S.b_off + r;
     for (int jc = 0; jc < np; jc += 32) {
       uint32_t v[32];
-      const uint32_t taddr = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)jc;
-      asm volatile(
-          "tcgen05.ld.sync.aligned.32x32b.x32.b32 "
-          "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
-          "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
-          : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
-            "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15]),
-            "=r"(v[16]), "=r"(v[17]), "=r"(v[18]), "=r"(v[19]), "=r"(v[20]), "=r"(v[21]), "=r"(v[22]),
-            "=r"(v[23]), "=r"(v[24]), "=r"(v[25]), "=r"(v[26]), "=r"(v[27]), "=r"(v[28]), "=r"(v[29]),
-            "=r"(v[30]), "=r"(v[31])
-          : "r"(taddr)
-          : "memory");
-      asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+      tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)jc, v);
       if (r < nb) {
 #pragma unroll
-        for (int c = 0; c < 32; ++c) {
-          const int gj = col0 + jc + c;
-          if (jc + c < ncols) Yb[S.b_off + r + (int64_t)gj * nbt] = sd * (double)__uint_as_float(v[c]);
-        }
+        for (int c = 0; c < 32; ++c)
+          if (jc + c < ncols) yrow[(int64_t)(col0 + jc + c) * nbt] = sd * (double)__uint_as_float(v[c]);
       }
     }
   }
@@ -228,20 +286,150 @@ __global__ void __launch_bounds__(TC_THREADS) k_tc_apply_tf32(
   }
 }
 
-// Fhat = D^{-1/2} F D^{-1/2} (FP32, rounded to TF32) and D^{1/2} per module;
-// Shat likewise for the preconditioner block S_bb (its own diagonal).
+// B operand: xb[j][bpad(s) + k] = tf32 parts of sqrt(D_s)[k] (B^sT X)[b, j]
+// for k < n_b(s), zero for the padding up to the next multiple of 32.
+template <int PASSES>
+__global__ void k_gather_tc(const DevType* __restrict__ types, const DevSub* __restrict__ subs,
+                            const int64_t* __restrict__ bpad, const double* __restrict__ X, int64_t ldx,
+                            const int* __restrict__ b2l_off, const int* __restrict__ b2l_lam,
+                            const signed char* __restrict__ b2l_sign, const double* __restrict__ sqrtD,
+                            float* __restrict__ xb_hi, float* __restrict__ xb_lo, int64_t nbp) {
+  const DevSub S = subs[blockIdx.y];
+  const int nb = types[S.type].n_b;
+  const int nbp_s = k_extent(nb, 0, 0);
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= nbp_s) return;
+  const int j = blockIdx.z;
+  float v = 0.0f;
+  if (k < nb) {
+    const int64_t b = S.b_off + k;
+    const double* x = X + (int64_t)j * ldx;
+    double acc = 0.0;
+    for (int q = b2l_off[b]; q < b2l_off[b + 1]; ++q) acc += b2l_sign[q] > 0 ? x[b2l_lam[q]] : -x[b2l_lam[q]];
+    v = static_cast<float>(acc * sqrtD[b]);
+  }
+  const int64_t o = (int64_t)j * nbp + bpad[blockIdx.y] + k;
+  const float hi = to_tf32(v);
+  xb_hi[o] = hi;
+  if (PASSES == 3) xb_lo[o] = to_tf32(v - hi);
+}
+
+// A operand: arena rows of Fhat_s = D^{-1/2} F_s D^{-1/2}, TF32 parts.
+// (and, with aug, Frc_hat_s = D^{-1/2} F_rc,s after column n_b rounded up to 32).
+__global__ void k_make_arena(const DevType* __restrict__ types, const DevModule* __restrict__ mods,
+                             const double* __restrict__ mem, const int* __restrict__ frow, int64_t pitch, int aug,
+                             float* __restrict__ fa_hi, float* __restrict__ fa_lo) {
+  const DevModule M = mods[blockIdx.y];
+  const DevType T = types[M.type];
+  const int n = T.n_b, nc = (aug ? T.n_c : 0);
+  const int ncol = n + nc;
+  const int c0 = k_extent(n, 0, 0);
+  const double* F = mem + M.F;
+  const double* Frc = mem + M.Frc;                  // [n x nc] row-major
+  const int64_t total = (int64_t)n * ncol;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+    const int i = (int)(e / ncol), j = (int)(e % ncol);
+    const double di = sqrt(F[(int64_t)i * n + i]);
+    float v;
+    int64_t o;
+    if (j < n) {
+      v = static_cast<float>(F[(int64_t)i * n + j] / (di * sqrt(F[(int64_t)j * n + j])));
+      o = (int64_t)(frow[blockIdx.y] + i) * pitch + j;
+    } else {
+      v = static_cast<float>(Frc[(int64_t)i * nc + (j - n)] / di);
+      o = (int64_t)(frow[blockIdx.y] + i) * pitch + c0 + (j - n);
+    }
+    const float hi = to_tf32(v);
+    fa_hi[o] = hi;
+    if (fa_lo) fa_lo[o] = to_tf32(v - hi);
+  }
+}
+
+// Corner reduction of the precision form, FP32 on the CUDA cores:
+// C_s = F_rc,s^T X_b(s) = Frc_hat_s^T (D^{1/2} X_b(s)), read from the gathered
+// operand (high + low parts).  One block per subdomain and 64 directions; the
+// K loop stages 64 rows of Frc_hat and of the operand in shared memory.
+__global__ void __launch_bounds__(256) k_frct_lowp(const DevType* __restrict__ types,
+                                                   const DevModule* __restrict__ mods,
+                                                   const DevSub* __restrict__ subs, const double* __restrict__ mem,
+                                                   const int64_t* __restrict__ bpad, const float* __restrict__ xb_hi,
+                                                   const float* __restrict__ xb_lo, int64_t nbp, int m,
+                                                   double* __restrict__ Cb, int64_t nct) {
+  __shared__ float fs[64][25];
+  __shared__ float xs[64][65];
+  const DevSub S = subs[blockIdx.y];
+  const DevType T = types[S.type];
+  const int nb = T.n_b, nc = T.n_c;
+  if (nc == 0) return;
+  const DevModule M = mods[S.module];
+  const double* F = mem + M.F;
+  const double* Frc = mem + M.Frc;
+  const int j0 = blockIdx.x * 64;
+  const int tid = threadIdx.x, jj = tid & 63, cg = tid >> 6;
+  const float* xh = xb_hi + bpad[blockIdx.y];
+  const float* xl = xb_lo ? xb_lo + bpad[blockIdx.y] : nullptr;
+  float acc[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+  for (int k0 = 0; k0 < nb; k0 += 64) {
+    for (int e = tid; e < 64 * nc; e += 256) {
+      const int kk = e / nc, c = e % nc, k = k0 + kk;
+      fs[kk][c] = k < nb ? static_cast<float>(Frc[(int64_t)k * nc + c] / sqrt(F[(int64_t)k * nb + k])) : 0.0f;
+    }
+    for (int e = tid; e < 64 * 64; e += 256) {
+      const int j2 = e >> 6, kk = e & 63, k = k0 + kk, j = j0 + j2;
+      float v = 0.0f;
+      if (j < m && k < nb) {
+        v = xh[(int64_t)j * nbp + k];
+        if (xl) v += xl[(int64_t)j * nbp + k];
+      }
+      xs[kk][j2] = v;
+    }
+    __syncthreads();
+#pragma unroll 8
+    for (int kk = 0; kk < 64; ++kk) {
+      const float x = xs[kk][jj];
+#pragma unroll
+      for (int q = 0; q < 6; ++q) acc[q] = fmaf(fs[kk][cg * 6 + q], x, acc[q]);
+    }
+    __syncthreads();
+  }
+  const int j = j0 + jj;
+  if (j < m) {
+#pragma unroll
+    for (int q = 0; q < 6; ++q) {
+      const int c = cg * 6 + q;
+      if (c < nc) Cb[S.c_off + c + (int64_t)j * nct] = static_cast<double>(acc[q]);
+    }
+  }
+}
+
+// The K-extension of the operand: V_s (the coarse correction at the
+// subdomain's corners) in the 32 slots after its b range, zero past n_c.
+template <int PASSES>
+__global__ void k_put_v(const DevType* __restrict__ types, const DevSub* __restrict__ subs,
+                        const int64_t* __restrict__ bpad, const int* __restrict__ cg, const double* __restrict__ V,
+                        int np, int m, float* __restrict__ xb_hi, float* __restrict__ xb_lo, int64_t nbp) {
+  const DevSub S = subs[blockIdx.y];
+  const DevType T = types[S.type];
+  const int c = threadIdx.x, j = blockIdx.x * blockDim.y + threadIdx.y;
+  if (j >= m || T.n_c == 0) return;
+  const float v = c < T.n_c ? static_cast<float>(V[cg[S.c_off + c] + (int64_t)j * np]) : 0.0f;
+  const int64_t o = (int64_t)j * nbp + bpad[blockIdx.y] + k_extent(T.n_b, 0, 0) + c;
+  const float hi = to_tf32(v);
+  xb_hi[o] = hi;
+  if (PASSES == 3) xb_lo[o] = to_tf32(v - hi);
+}
+
+// Shat = D_S^{-1/2} S_bb D_S^{-1/2} (FP32) per module, for the preconditioner
+// block of the precision form.
 __global__ void k_make_lowp(const DevType* __restrict__ types, const DevModule* __restrict__ mods,
                             const double* __restrict__ mem, float* __restrict__ fmem) {
   const DevModule M = mods[blockIdx.y];
   const DevType T = types[M.type];
   const int n = T.n_b, nbc = T.n_b + T.n_c;
-  const double* F = mem + M.F;
   const double* Sm = mem + M.S;
   const int64_t total = (int64_t)n * n;
   for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
     const int i = (int)(e / n), j = (int)(e % n);
-    const double fv = F[e] / sqrt(F[(int64_t)i * n + i] * F[(int64_t)j * n + j]);
-    fmem[M.F + e] = static_cast<float>(fv);
     const double sv = Sm[(int64_t)i * nbc + j] / sqrt(Sm[(int64_t)i * nbc + i] * Sm[(int64_t)j * nbc + j]);
     fmem[M.W + e] = static_cast<float>(sv);
   }
@@ -284,12 +472,20 @@ __global__ void k_sub_gemv_lowp(const DevType* __restrict__ types, const DevModu
 
 }  // namespace
 
-size_t tc_apply_smem_bytes(int passes) { return 1024 + (passes == 3 ? 2 : 1) * (TC_M * 128 + TC_NMAX * 128); }
+size_t tc_apply_smem_bytes(int passes) {
+  const size_t stage = (passes == 3 ? 2 : 1) * (size_t)(TC_M * 128 + TC_NMAX * 128);
+  return 1024 + (passes == 3 ? TC_STAGES3 : TC_STAGES1) * stage;
+}
 
 cudaError_t tc_prepare(const Ctx& c, cudaStream_t st) {
   k_make_lowp<<<dim3(64, c.n_mod), 256, 0, st>>>(c.d_types, c.d_mods, c.d_modmem, c.d_fmem);
   note_launches(1);
   cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  k_make_arena<<<dim3(64, c.n_mod), 256, 0, st>>>(c.d_types, c.d_mods, c.d_modmem, c.d_frow, c.fa_pitch, c.tc_aug,
+                                                 c.d_fa_hi, c.opt.precision == FETI_TF32X3 ? c.d_fa_lo : nullptr);
+  note_launches(1);
+  e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   k_sqrt_diag<<<dim3((c.max_nb + 127) / 128, c.hp.n_sub), 128, 0, st>>>(c.d_types, c.d_mods, c.d_subs, c.d_modmem,
                                                                         c.d_sqrtDF, c.d_sqrtDS);
@@ -297,28 +493,112 @@ cudaError_t tc_prepare(const Ctx& c, cudaStream_t st) {
   return cudaGetLastError();
 }
 
-// Yb = D^{1/2} Fhat D^{1/2} B^T X for every subdomain (tensor cores).
-cudaError_t tc_apply_local(const Ctx& c, const double* X, int64_t ldx, int m, double* Yb, cudaStream_t st) {
+namespace {
+
+PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  if (!fn) {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+  }
+  return fn;
+}
+
+// Row-major FP32 matrix [rows x pitch] read in boxes of 32 x box_rows with the
+// 128-byte swizzle; outside the matrix the box is filled with zeros.
+bool make_map(CUtensorMap* map, const float* base, int64_t pitch, int64_t rows, uint32_t box_rows) {
+  PFN_cuTensorMapEncodeTiled_v12000 fn = encode_fn();
+  if (!fn) return false;
+  const cuuint64_t dims[2] = {(cuuint64_t)pitch, (cuuint64_t)rows};
+  const cuuint64_t strides[1] = {(cuuint64_t)pitch * sizeof(float)};
+  const cuuint32_t box[2] = {(cuuint32_t)TC_KC, box_rows};
+  const cuuint32_t estr[2] = {1, 1};
+  return fn(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<float*>(base), dims, strides, box, estr,
+            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+template <int PASSES, int STAGES>
+cudaError_t launch_tc(const Ctx& c, int m, double* Yb, cudaStream_t st) {
   static bool attr_set = false;
-  const size_t sm1 = tc_apply_smem_bytes(1), sm3 = tc_apply_smem_bytes(3);
+  const size_t smem = tc_apply_smem_bytes(PASSES);
   if (!attr_set) {
-    cudaError_t e = cudaFuncSetAttribute(k_tc_apply_tf32<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm1);
-    if (e == cudaSuccess)
-      e = cudaFuncSetAttribute(k_tc_apply_tf32<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm3);
+    cudaError_t e = cudaFuncSetAttribute(k_tc_apply<PASSES, STAGES>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)smem);
     if (e != cudaSuccess) return e;
     attr_set = true;
   }
-  dim3 grid((c.max_nb + TC_M - 1) / TC_M, c.hp.n_sub, (m + TC_NMAX - 1) / TC_NMAX);
-  if (c.opt.precision == FETI_TF32X3)
-    k_tc_apply_tf32<3><<<grid, TC_THREADS, sm3, st>>>(c.d_types, c.d_mods, c.d_subs, c.d_fmem, X, ldx, m,
-                                                      c.d_b2l_off, c.d_b2l_lam, c.d_b2l_sign, c.d_sqrtDF, Yb,
-                                                      c.hp.n_b_total, c.d_status);
-  else
-    k_tc_apply_tf32<1><<<grid, TC_THREADS, sm1, st>>>(c.d_types, c.d_mods, c.d_subs, c.d_fmem, X, ldx, m,
-                                                      c.d_b2l_off, c.d_b2l_lam, c.d_b2l_sign, c.d_sqrtDF, Yb,
-                                                      c.hp.n_b_total, c.d_status);
+  CUtensorMap ta, tal, tb, tbl;
+  const float* alo = PASSES == 3 ? c.d_fa_lo : c.d_fa_hi;
+  const float* blo = PASSES == 3 ? c.d_xb_lo : c.d_xb_hi;
+  if (!make_map(&ta, c.d_fa_hi, c.fa_pitch, c.fa_rows, TC_M) || !make_map(&tal, alo, c.fa_pitch, c.fa_rows, TC_M) ||
+      !make_map(&tb, c.d_xb_hi, c.nbp_total, m, TC_NMAX) || !make_map(&tbl, blo, c.nbp_total, m, TC_NMAX))
+    return cudaErrorInvalidValue;
+  const int n_cb = (m + TC_NMAX - 1) / TC_NMAX;
+  const int n_rb = (c.max_nb + TC_M - 1) / TC_M;
+  dim3 grid(n_cb * n_rb, c.hp.n_sub);
+  k_tc_apply<PASSES, STAGES><<<grid, TC_THREADS, smem, st>>>(ta, tal, tb, tbl, c.d_types, c.d_subs, c.d_frow,
+                                                             c.d_bpad, c.d_sqrtDF, Yb, c.hp.n_b_total, m, n_cb,
+                                                             c.tc_aug, c.d_status);
   note_launches(1);
   return cudaGetLastError();
+}
+
+}  // namespace
+
+int tc_k_extent(int nb, int nc, int aug) { return k_extent(nb, nc, aug); }
+
+// xb = TF32 parts of D^{1/2} B^T X in the padded operand layout.
+cudaError_t tc_gather(const Ctx& c, const double* X, int64_t ldx, int m, cudaStream_t st) {
+  if (m <= 0) return cudaSuccess;
+  if (m > c.xb_cap) return cudaErrorInvalidValue;
+  const int max_nbp = k_extent(c.max_nb, 0, 0);
+  dim3 g((max_nbp + 127) / 128, c.hp.n_sub, m);
+  if (c.opt.precision == FETI_TF32X3)
+    k_gather_tc<3><<<g, 128, 0, st>>>(c.d_types, c.d_subs, c.d_bpad, X, ldx, c.d_b2l_off, c.d_b2l_lam, c.d_b2l_sign,
+                                      c.d_sqrtDF, c.d_xb_hi, c.d_xb_lo, c.nbp_total);
+  else
+    k_gather_tc<1><<<g, 128, 0, st>>>(c.d_types, c.d_subs, c.d_bpad, X, ldx, c.d_b2l_off, c.d_b2l_lam, c.d_b2l_sign,
+                                      c.d_sqrtDF, c.d_xb_hi, nullptr, c.nbp_total);
+  note_launches(1);
+  return cudaGetLastError();
+}
+
+// Cb = F_rc^T X_b per subdomain (FP32) from the gathered operand, then the
+// corner assembly Vraw = sum over the copies of each primal DOF.
+cudaError_t tc_corner_reduce(const Ctx& c, int m, double* Vraw, cudaStream_t st) {
+  if (c.max_nc > 24) return cudaErrorInvalidValue;
+  k_frct_lowp<<<dim3((m + 63) / 64, c.hp.n_sub), 256, 0, st>>>(
+      c.d_types, c.d_mods, c.d_subs, c.d_modmem, c.d_bpad, c.d_xb_hi,
+      c.opt.precision == FETI_TF32X3 ? c.d_xb_lo : nullptr, c.nbp_total, m, c.d_Cb, c.n_c_total);
+  note_launches(1);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  return corner_assemble(c, m, Vraw, st);
+}
+
+// The coarse correction V into the K-extension of the operand.
+cudaError_t tc_put_v(const Ctx& c, const double* V, int m, cudaStream_t st) {
+  if (!c.tc_aug) return cudaSuccess;
+  dim3 g((m + 7) / 8, c.hp.n_sub);
+  if (c.opt.precision == FETI_TF32X3)
+    k_put_v<3><<<g, dim3(32, 8), 0, st>>>(c.d_types, c.d_subs, c.d_bpad, c.d_c_glob, V, c.hp.n_primal, m, c.d_xb_hi,
+                                          c.d_xb_lo, c.nbp_total);
+  else
+    k_put_v<1><<<g, dim3(32, 8), 0, st>>>(c.d_types, c.d_subs, c.d_bpad, c.d_c_glob, V, c.hp.n_primal, m, c.d_xb_hi,
+                                          nullptr, c.nbp_total);
+  note_launches(1);
+  return cudaGetLastError();
+}
+
+// Yb = D^{1/2} [Fhat | Frc_hat] xb for every subdomain (tensor cores).
+cudaError_t tc_product(const Ctx& c, int m, double* Yb, cudaStream_t st) {
+  if (m <= 0) return cudaSuccess;
+  if (m > c.xb_cap) return cudaErrorInvalidValue;
+  return c.opt.precision == FETI_TF32X3 ? launch_tc<3, TC_STAGES3>(c, m, Yb, st) : launch_tc<1, TC_STAGES1>(c, m, Yb, st);
 }
 
 cudaError_t lowp_gemv_S(const Ctx& c, const double* xb, double* yb, cudaStream_t st) {
