@@ -75,7 +75,7 @@ typedef struct {
   double tol;          /* relative tolerance on sqrt(r^T z) (default 1e-6) */
   double rr_tol;       /* rank-revealing cutoff on the remaining/initial pivot ratio (1e-10) */
   double inner_tol;    /* FETI_TF32 / FETI_TF32X3: relative tolerance of each low-precision inner
-                          solve; 0 (default) picks 1e-2 for FETI_TF32 and 1e-5 for FETI_TF32X3.
+                          solve; 0 (default) picks 1e-2.
                           Each inner solve is also capped at 30 iterations */
   int max_refine;      /* FETI_TF32 / FETI_TF32X3: cap on the FP64 refinement steps (30) */
 } feti_options;
@@ -222,6 +222,13 @@ feti_status feti_query(const feti_ctx* ctx, int key, int64_t* value);
  * profiled launches.  One profile may be active per process. */
 feti_status feti_profile_begin(feti_ctx* ctx);
 feti_status feti_profile_end(feti_ctx* ctx, double* gemm_flops, double* gemm_ms, int64_t* gemm_launches);
+
+/* The tensor-core local products (FETI_TF32 / FETI_TF32X3) bracketed during
+ * the last completed profile of this context: their summed algorithmic flops
+ * (2 n_b (n_b + n_c) per subdomain and column, the corner coupling included
+ * for FETI-DP; the split product's three passes count once), device time in
+ * milliseconds and launch count.  Each pointer may be NULL. */
+feti_status feti_profile_tensor(const feti_ctx* ctx, double* flops, double* ms, int64_t* launches);
 
 /* Layout of the multipliers, for comparing lambda-space vectors with an
  * independent implementation: for each multiplier l, out[6*l .. 6*l+5] =

@@ -32,7 +32,7 @@ EXPORTS = [
     "feti_options_default", "feti_create", "feti_setup_subdomains", "feti_setup_batch", "feti_problem_result",
     "feti_set_density", "feti_factorize",
     "feti_solve_dual", "feti_recover_displacements", "feti_compliance_grad", "feti_apply_dual",
-    "feti_apply_precond", "feti_apply_precond_noalloc", "feti_query", "feti_profile_begin", "feti_profile_end", "feti_lambda_layout", "feti_local_blocks", "feti_last_error",
+    "feti_apply_precond", "feti_apply_precond_noalloc", "feti_query", "feti_profile_begin", "feti_profile_end", "feti_profile_tensor", "feti_lambda_layout", "feti_local_blocks", "feti_last_error",
     "feti_destroy",
 ]
 
@@ -86,6 +86,7 @@ def lib():
             "feti_query": ([vp, i, ctypes.POINTER(i64)], i),
             "feti_profile_begin": ([vp], i),
             "feti_profile_end": ([vp, ctypes.POINTER(d), ctypes.POINTER(d), ctypes.POINTER(i64)], i),
+            "feti_profile_tensor": ([vp, ctypes.POINTER(d), ctypes.POINTER(d), ctypes.POINTER(i64)], i),
             "feti_lambda_layout": ([vp, vp], i),
             "feti_local_blocks": ([vp, i, ctypes.POINTER(i), ctypes.POINTER(i), vp, vp, vp, vp, vp], i),
             "feti_last_error": ([vp], ctypes.c_char_p),
@@ -232,6 +233,13 @@ def feti_profile_end(ctx):
     """Returns (algorithmic flops, device ms, launches) of the profiled FP64 GEMMs."""
     f, t, n = ctypes.c_double(0), ctypes.c_double(0), ctypes.c_int64(0)
     _check(ctx, lib().feti_profile_end(ctx, ctypes.byref(f), ctypes.byref(t), ctypes.byref(n)))
+    return f.value, t.value, n.value
+
+
+def feti_profile_tensor(ctx):
+    """(flops, ms, launches) of the tensor-core products in the last completed profile."""
+    f, t, n = ctypes.c_double(0), ctypes.c_double(0), ctypes.c_int64(0)
+    _check(ctx, lib().feti_profile_tensor(ctx, ctypes.byref(f), ctypes.byref(t), ctypes.byref(n)))
     return f.value, t.value, n.value
 
 

@@ -125,6 +125,7 @@ feti_status ensure_blocks(Ctx& c, int m) {
   }
   if (c.opt.precision != FETI_FP64) {
     TRY(dalloc(c, c.d_xb_hi, (size_t)c.nbp_total * cap));
+    TRY(dalloc(c, c.d_Yb32, (size_t)nbt * cap));
     if (c.opt.precision == FETI_TF32X3) TRY(dalloc(c, c.d_xb_lo, (size_t)c.nbp_total * cap));
     c.xb_cap = cap;
   }
@@ -261,8 +262,8 @@ feti_status apply_dual_lowp(Ctx& c, const double* X, int64_t ldx, int m, double*
     CU(coarse_apply(c, c.d_Vraw, c.d_V, m, c.stream));
     CU(tc_put_v(c, c.d_V, m, c.stream));
   }
-  CU(tc_product(c, m, c.d_Yb, c.stream));
-  CU(scatter_b_to_lam(c, c.d_Yb, m, Y, ldy, c.stream));
+  CU(tc_product(c, m, c.d_Yb32, c.stream));
+  CU(scatter_b_to_lam32(c, c.d_Yb32, m, Y, ldy, c.stream));
   return FETI_OK;
 }
 
@@ -337,7 +338,7 @@ feti_status feti_options_default(feti_options* opt) {
   opt->dedup_modules = 1;
   opt->tol = 1e-6;
   opt->rr_tol = 1e-10;
-  opt->inner_tol = 0.0;                 // automatic: 1e-2 (TF32), 1e-5 (split TF32)
+  opt->inner_tol = 0.0;                 // automatic (1e-2)
   opt->max_refine = 30;
   return FETI_OK;
 }
@@ -620,6 +621,11 @@ static feti_status setup_impl(Ctx& c, const feti_problem* probs, int n) {
       return FETI_ENOTSUP;
     }
     c.fa_pitch = kmax;
+    c.fl_tc = 0.0;
+    for (int s = 0; s < hp.n_sub; ++s) {
+      const DevType& T = c.h_types[c.h_subs[s].type];
+      c.fl_tc += 2.0 * T.n_b * (T.n_b + (c.tc_aug ? T.n_c : 0));
+    }
     c.fa_rows = std::max<int64_t>(rows, 1);
     c.nbp_total = std::max<int64_t>(nbp, 32);
     TRY(upload(c, c.d_frow, frow));
@@ -1012,7 +1018,10 @@ static feti_status solve_impl(Ctx& c, double* lambda_inout, feti_stats* stats) {
       // each correction is capped (a stalled reduced-precision solve still
       // returns a useful correction; the FP64 outer loop decides convergence)
       const int cap = std::min(c.opt.max_iter - S.iterations, 30);
-      const double itol = c.opt.inner_tol > 0.0 ? c.opt.inner_tol : (c.opt.precision == FETI_TF32X3 ? 1e-5 : 1e-2);
+      // automatic inner tolerance: 1e-2 (measured best time-to-solve for both
+      // reduced-precision products: each restart costs the orthogonalization
+      // history, so long inner solves lose more than extra restarts)
+      const double itol = c.opt.inner_tol > 0.0 ? c.opt.inner_tol : 1e-2;
       feti_status s2 = krylov_core(c, itol, cap, true, inner);
       S.iterations += inner.iterations;
       S.f_applies += inner.f_applies;
@@ -1197,13 +1206,25 @@ feti_status feti_profile_end(feti_ctx* ctx, double* gemm_flops, double* gemm_ms,
   if (!c.prof) { c.err = "no active profile"; return FETI_ESTATE; }
   CU(cudaStreamSynchronize(c.stream));
   set_gemm_profile(nullptr);
-  double f = 0, t = 0;
-  int64_t n = 0;
-  finish_gemm_profile(static_cast<GemmProfile*>(c.prof), &f, &t, &n);
+  double f[2], t[2];
+  int64_t n[2];
+  finish_gemm_profile(static_cast<GemmProfile*>(c.prof), f, t, n);
   c.prof = nullptr;
-  if (gemm_flops) *gemm_flops = f;
-  if (gemm_ms) *gemm_ms = t;
-  if (gemm_launches) *gemm_launches = n;
+  c.prof_tc_flops = f[1];
+  c.prof_tc_ms = t[1];
+  c.prof_tc_launches = n[1];
+  if (gemm_flops) *gemm_flops = f[0];
+  if (gemm_ms) *gemm_ms = t[0];
+  if (gemm_launches) *gemm_launches = n[0];
+  return FETI_OK;
+}
+
+feti_status feti_profile_tensor(const feti_ctx* ctx, double* flops, double* ms, int64_t* launches) {
+  if (!ctx) return FETI_EINVAL;
+  const Ctx& c = ctx->c;
+  if (flops) *flops = c.prof_tc_flops;
+  if (ms) *ms = c.prof_tc_ms;
+  if (launches) *launches = c.prof_tc_launches;
   return FETI_OK;
 }
 

@@ -15,6 +15,7 @@ namespace feti {
 struct GemmProfile {
   std::vector<cudaEvent_t> ev;     // start/stop pairs
   std::vector<double> flops;
+  std::vector<int> kind;           // 0: FP64 GEMM, 1: tensor-core local product
 };
 
 namespace {
@@ -24,7 +25,7 @@ GemmProfile* g_prof = nullptr;
 struct ProfScope {
   cudaStream_t st;
   bool on;
-  ProfScope(cudaStream_t s, double fl) : st(s), on(g_prof != nullptr) {
+  ProfScope(cudaStream_t s, double fl, int kind = 0) : st(s), on(g_prof != nullptr) {
     if (!on) return;
     cudaEvent_t a, b;
     cudaEventCreate(&a);
@@ -32,6 +33,7 @@ struct ProfScope {
     g_prof->ev.push_back(a);
     g_prof->ev.push_back(b);
     g_prof->flops.push_back(fl);
+    g_prof->kind.push_back(kind);
     cudaEventRecord(a, st);
   }
   ~ProfScope() {
@@ -40,26 +42,42 @@ struct ProfScope {
 };
 }  // namespace
 
+void prof_begin(cudaStream_t st, double flops, int kind) {
+  if (!g_prof) return;
+  cudaEvent_t a, b;
+  cudaEventCreate(&a);
+  cudaEventCreate(&b);
+  g_prof->ev.push_back(a);
+  g_prof->ev.push_back(b);
+  g_prof->flops.push_back(flops);
+  g_prof->kind.push_back(kind);
+  cudaEventRecord(a, st);
+}
+
+void prof_end(cudaStream_t st) {
+  if (g_prof) cudaEventRecord(g_prof->ev.back(), st);
+}
+
 void note_launches(int n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
 int64_t launches() { return g_launches.load(std::memory_order_relaxed); }
 void set_gemm_profile(GemmProfile* p) { g_prof = p; }
 
 GemmProfile* new_gemm_profile() { return new GemmProfile(); }
 
-// Sum of the profiled durations (ms) and flops; releases the events.
+// Sums of the profiled durations (ms), flops and launches per kind (0: FP64
+// GEMM, 1: tensor-core product); releases the events.
 void finish_gemm_profile(GemmProfile* p, double* flops, double* ms, int64_t* count) {
-  double f = 0.0, t = 0.0;
-  for (size_t i = 0; i + 1 < p->ev.size(); i += 2) {
+  for (int k = 0; k < 2; ++k) { flops[k] = 0.0; ms[k] = 0.0; count[k] = 0; }
+  for (size_t i = 0; i < p->flops.size(); ++i) {
     float x = 0.f;
-    cudaEventElapsedTime(&x, p->ev[i], p->ev[i + 1]);
-    t += x;
-    cudaEventDestroy(p->ev[i]);
-    cudaEventDestroy(p->ev[i + 1]);
+    cudaEventElapsedTime(&x, p->ev[2 * i], p->ev[2 * i + 1]);
+    cudaEventDestroy(p->ev[2 * i]);
+    cudaEventDestroy(p->ev[2 * i + 1]);
+    const int k = p->kind[i] ? 1 : 0;
+    flops[k] += p->flops[i];
+    ms[k] += x;
+    count[k] += 1;
   }
-  for (double v : p->flops) f += v;
-  *flops = f;
-  *ms = t;
-  *count = (int64_t)p->flops.size();
   delete p;
 }
 

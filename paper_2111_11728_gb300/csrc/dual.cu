@@ -30,21 +30,30 @@ __global__ void k_gather(int64_t nbt, int m, const int* __restrict__ off, const 
   Xb[b + (int64_t)j * nbt] = v;
 }
 
+// Each thread serves SC_J consecutive columns, reading the row's entries once.
+constexpr int SC_J = 8;
+template <typename TY>
 __global__ void k_scatter(int64_t nl, int m, const int* __restrict__ b0, const signed char* __restrict__ s0,
                           const int* __restrict__ b1, const signed char* __restrict__ s1,
-                          const double* __restrict__ Yb, int64_t nbt, double* __restrict__ Y, int64_t ldy) {
+                          const TY* __restrict__ Yb, int64_t nbt, double* __restrict__ Y, int64_t ldy) {
   const int64_t l = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  const int j = blockIdx.y;
-  if (l >= nl || j >= m) return;
-  const double* yb = Yb + (int64_t)j * nbt;
-  const double a = yb[b0[l]];
-  double v = s0[l] > 0 ? a : -a;
-  const int q = b1[l];
-  if (q >= 0) {
-    const double c = yb[q];
-    v += s1[l] > 0 ? c : -c;
+  const int j0 = blockIdx.y * SC_J;
+  if (l >= nl) return;
+  const int jn = min(SC_J, m - j0);
+  const int p0 = b0[l], p1 = b1[l];
+  const bool n0 = s0[l] < 0, n1 = p1 >= 0 && s1[l] < 0;
+#pragma unroll
+  for (int u = 0; u < SC_J; ++u) {
+    if (u >= jn) break;
+    const TY* yb = Yb + (int64_t)(j0 + u) * nbt;
+    const double a = static_cast<double>(yb[p0]);
+    double v = n0 ? -a : a;
+    if (p1 >= 0) {
+      const double c = static_cast<double>(yb[p1]);
+      v += n1 ? -c : c;
+    }
+    Y[l + (int64_t)(j0 + u) * ldy] = v;
   }
-  Y[l + (int64_t)j * ldy] = v;
 }
 
 // rb[b] = sum over rows of b of w * sign * r  (B~^sT r)
@@ -174,8 +183,19 @@ cudaError_t gather_lam_to_b(const Ctx& c, const double* X, int64_t ldx, int m, d
 
 cudaError_t scatter_b_to_lam(const Ctx& c, const double* Yb, int m, double* Y, int64_t ldy, cudaStream_t st) {
   const int64_t nl = c.hp.n_lam;
-  dim3 g((unsigned)((nl + 255) / 256), m);
-  k_scatter<<<g, 256, 0, st>>>(nl, m, c.d_lam_b0, c.d_lam_s0, c.d_lam_b1, c.d_lam_s1, Yb, c.hp.n_b_total, Y, ldy);
+  dim3 g((unsigned)((nl + 255) / 256), (m + SC_J - 1) / SC_J);
+  k_scatter<double><<<g, 256, 0, st>>>(nl, m, c.d_lam_b0, c.d_lam_s0, c.d_lam_b1, c.d_lam_s1, Yb, c.hp.n_b_total, Y,
+                                       ldy);
+  note_launches(1);
+  return cudaGetLastError();
+}
+
+// Same, from an FP32 interface-space block (the tensor-core product's output).
+cudaError_t scatter_b_to_lam32(const Ctx& c, const float* Yb, int m, double* Y, int64_t ldy, cudaStream_t st) {
+  const int64_t nl = c.hp.n_lam;
+  dim3 g((unsigned)((nl + 255) / 256), (m + SC_J - 1) / SC_J);
+  k_scatter<float><<<g, 256, 0, st>>>(nl, m, c.d_lam_b0, c.d_lam_s0, c.d_lam_b1, c.d_lam_s1, Yb, c.hp.n_b_total, Y,
+                                      ldy);
   note_launches(1);
   return cudaGetLastError();
 }

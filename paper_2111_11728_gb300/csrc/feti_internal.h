@@ -226,8 +226,12 @@ struct Ctx {
   int64_t nbp_total = 0;         // interface space with each subdomain padded to a multiple of 32
   int64_t* d_bpad = nullptr;     // [n_sub] padded offsets
   float *d_xb_hi = nullptr, *d_xb_lo = nullptr;   // [m x nbp_total] gathered scaled directions
+  float* d_Yb32 = nullptr;       // [m x n_b_total] output of the tensor-core product (FP32)
   int xb_cap = 0;
   int tc_aug = 0;                // FETI-DP corner coupling appended to the operands (K-extension)
+  double fl_tc = 0.0;            // algorithmic flops of the tensor-core product per column
+  double prof_tc_flops = 0.0, prof_tc_ms = 0.0;   // tensor-core products of the last profile
+  int64_t prof_tc_launches = 0;
   double* d_sqrtDF = nullptr;    // [n_b_total] sqrt(diag F_s)
   double* d_sqrtDS = nullptr;    // [n_b_total] sqrt(diag S_s)
   double *d_rout = nullptr, *d_zout = nullptr, *d_dl = nullptr;   // refinement vectors

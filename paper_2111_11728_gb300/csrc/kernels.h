@@ -16,7 +16,9 @@ int64_t launches();
 struct GemmProfile;
 void set_gemm_profile(GemmProfile* p);
 GemmProfile* new_gemm_profile();
-void finish_gemm_profile(GemmProfile* p, double* flops, double* ms, int64_t* count);
+void finish_gemm_profile(GemmProfile* p, double* flops, double* ms, int64_t* count);   // [2] each: GEMM, tensor
+void prof_begin(cudaStream_t st, double flops, int kind);   // bracket one launch (no-op without a profile)
+void prof_end(cudaStream_t st);
 
 // C = alpha * A B + beta * C with element (i,k) of A at A[i*ars + k*acs],
 // (k,j) of B at B[k*brs + j*bcs] and (i,j) of C at C[i*crs + j*ccs].
@@ -142,7 +144,8 @@ cudaError_t tc_prepare(const Ctx& c, cudaStream_t st);   // Fhat, Shat (FP32) an
 cudaError_t tc_gather(const Ctx& c, const double* X, int64_t ldx, int m, cudaStream_t st);
 cudaError_t tc_corner_reduce(const Ctx& c, int m, double* Vraw, cudaStream_t st);
 cudaError_t tc_put_v(const Ctx& c, const double* V, int m, cudaStream_t st);
-cudaError_t tc_product(const Ctx& c, int m, double* Yb, cudaStream_t st);
+cudaError_t tc_product(const Ctx& c, int m, float* Yb, cudaStream_t st);
+cudaError_t scatter_b_to_lam32(const Ctx& c, const float* Yb, int m, double* Y, int64_t ldy, cudaStream_t st);
 int tc_k_extent(int nb, int nc, int aug);
 cudaError_t corner_assemble(const Ctx& c, int m, double* Vraw, cudaStream_t st);
 cudaError_t lowp_gemv_S(const Ctx& c, const double* xb, double* yb, cudaStream_t st);

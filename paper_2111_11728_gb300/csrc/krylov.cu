@@ -12,38 +12,50 @@ namespace {
 
 constexpr double EPS2 = 4.930380657631324e-32;   // (2^-52)^2
 
-// Single CTA.  work holds 2*m*m + m doubles.  Pivot rule: the largest ratio of
-// the remaining Schur-complement diagonal to the column's initial diagonal,
-// exact ties to the lowest original column; stop when it is <= rr_tol.
-// Only the lower triangle of the remaining block is updated; the current
-// column of L is staged in shared memory.
+// Single CTA of 1024 threads; work holds 2*m*m + m doubles.  Pivot rule: the
+// largest ratio of the remaining Schur-complement diagonal to the column's
+// initial diagonal, exact ties to the lowest original column; stop when it is
+// <= rr_tol.
+//
+// Blocked left-looking form.  Everything is indexed by the original column
+// (no physical swaps): A holds the lower triangle of Delta by original index,
+// updated once per panel of RR_PB pivots (a rank-RR_PB update of the rows and
+// columns still unchosen); within a panel the columns of L are kept in shared
+// memory and each new column subtracts only the panel's earlier columns; the
+// remaining diagonal d is updated after every column and drives the pivot
+// choice.  Every entry receives the same fused multiply-adds in the same
+// order as the unblocked right-looking elimination.
 // Output T (column-major, ld m, k columns) = N^T [L~^{-T}; 0] and *d_k = k.
-__global__ void __launch_bounds__(1024) k_rr_chol(const double* __restrict__ Delta, int m, int ld, double rr_tol,
-                                                  double* __restrict__ work, double* __restrict__ T,
-                                                  int* __restrict__ d_k, int* __restrict__ perm_out) {
-  double* A = work;              // m x m row-major, lower triangle live
-  double* L = work + (int64_t)m * m;
-  double* d0 = L + (int64_t)m * m;
+constexpr int RR_THREADS = 1024;
+constexpr int RR_PB = 16;                       // panel width (pivots per trailing update)
+
+__global__ void __launch_bounds__(RR_THREADS) k_rr_chol(const double* __restrict__ Delta, int m, int ld,
+                                                        double rr_tol, double* __restrict__ work,
+                                                        double* __restrict__ T, int* __restrict__ d_k,
+                                                        int* __restrict__ perm_out) {
+  double* A = work;                             // [m x m] by original index, lower triangle a >= b
+  double* Lg = work + (int64_t)m * m;           // [m x m] Lg[id*m + q] = L(position of id, q)
+  extern __shared__ double rr_sh[];             // Lp[q][id], q < RR_PB
+  double* Lp = rr_sh;
+  __shared__ double d[1024], d0[1024];
   __shared__ int perm[1024];
-  __shared__ unsigned char alive[1024];
-  __shared__ double lcol[1024];
+  __shared__ unsigned char alive[1024], chosen[1024];
   __shared__ double rv[32];
-  __shared__ int rp[32], rpos[32];
-  __shared__ int s_bt, s_k;
+  __shared__ int rp[32];
+  __shared__ int s_bp, s_k;
   __shared__ double s_best;
   const int tid = threadIdx.x, nt = blockDim.x;
   const int lane = tid & 31, wid = tid >> 5, nw = nt >> 5;
 
   for (int64_t e = tid; e < (int64_t)m * m; e += nt) {
-    const int i = (int)(e / m), j = (int)(e % m);
-    A[e] = j <= i ? Delta[i + (int64_t)j * ld] : 0.0;      // lower triangle of Delta
-    L[e] = 0.0;
+    const int a = (int)(e / m), b = (int)(e % m);
+    if (b <= a) A[e] = Delta[a + (int64_t)b * ld];
   }
   __syncthreads();
   double mx = 0.0;
   for (int t = tid; t < m; t += nt) {
-    perm[t] = t;
-    d0[t] = A[(int64_t)t * m + t];
+    d[t] = d0[t] = A[(int64_t)t * m + t];
+    chosen[t] = 0;
     mx = fmax(mx, d0[t]);
   }
   for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
@@ -60,88 +72,112 @@ __global__ void __launch_bounds__(1024) k_rr_chol(const double* __restrict__ Del
   for (int t = tid; t < m; t += nt) alive[t] = (dmax > 0.0 && d0[t] > EPS2 * dmax) ? 1 : 0;
   __syncthreads();
 
-  for (int j = 0; j < m; ++j) {
-    // --- pivot search -------------------------------------------------------
-    double bv = -1.0;
-    int bp = 0x7fffffff, bpos = -1;
-    for (int t = j + tid; t < m; t += nt) {
-      const int pt = perm[t];
-      if (!alive[pt]) continue;
-      const double ratio = A[(int64_t)t * m + t] / d0[pt];
-      if (ratio > bv || (ratio == bv && pt < bp)) { bv = ratio; bp = pt; bpos = t; }
-    }
-    for (int o = 16; o > 0; o >>= 1) {
-      const double ov = __shfl_xor_sync(0xffffffffu, bv, o);
-      const int op = __shfl_xor_sync(0xffffffffu, bp, o);
-      const int opos = __shfl_xor_sync(0xffffffffu, bpos, o);
-      if (ov > bv || (ov == bv && op < bp)) { bv = ov; bp = op; bpos = opos; }
-    }
-    if (lane == 0) { rv[wid] = bv; rp[wid] = bp; rpos[wid] = bpos; }
-    __syncthreads();
-    if (tid == 0) {
-      double v = -1.0;
-      int p = 0x7fffffff, pos = -1;
-      for (int w = 0; w < nw; ++w)
-        if (rv[w] > v || (rv[w] == v && rp[w] < p)) { v = rv[w]; p = rp[w]; pos = rpos[w]; }
-      s_best = v;
-      s_bt = pos;
-    }
-    __syncthreads();
-    if (s_bt < 0 || !(s_best > rr_tol)) break;
-    const int bt = s_bt;
-    // --- symmetric swap of positions j < bt in the live lower triangle --------
-    if (bt != j) {
-      for (int t = j + tid; t < m; t += nt) {
-        if (t == j) {
-          const double a = A[(int64_t)j * m + j];
-          A[(int64_t)j * m + j] = A[(int64_t)bt * m + bt];
-          A[(int64_t)bt * m + bt] = a;
-        } else if (t < bt) {          // (t, j) <-> (bt, t)
-          const double a = A[(int64_t)t * m + j];
-          A[(int64_t)t * m + j] = A[(int64_t)bt * m + t];
-          A[(int64_t)bt * m + t] = a;
-        } else if (t > bt) {          // (t, j) <-> (t, bt)
-          const double a = A[(int64_t)t * m + j];
-          A[(int64_t)t * m + j] = A[(int64_t)t * m + bt];
-          A[(int64_t)t * m + bt] = a;
-        }
+  bool stop = false;
+  for (int p0 = 0; p0 < m && !stop; p0 += RR_PB) {
+    const int pend = min(p0 + RR_PB, m);
+    int jn = 0;
+    for (int j = p0; j < pend; ++j) {
+      // --- pivot: max d/d0 over the unchosen live columns, ties to the lowest id
+      double bv = -1.0;
+      int bp = 0x7fffffff;
+      for (int t = tid; t < m; t += nt) {
+        if (!alive[t] || chosen[t]) continue;
+        const double ratio = d[t] / d0[t];
+        if (ratio > bv || (ratio == bv && t < bp)) { bv = ratio; bp = t; }
       }
-      for (int t = tid; t < j; t += nt) {
-        const double a = L[(int64_t)j * m + t];
-        L[(int64_t)j * m + t] = L[(int64_t)bt * m + t];
-        L[(int64_t)bt * m + t] = a;
+      for (int o = 16; o > 0; o >>= 1) {
+        const double ov = __shfl_xor_sync(0xffffffffu, bv, o);
+        const int op = __shfl_xor_sync(0xffffffffu, bp, o);
+        if (ov > bv || (ov == bv && op < bp)) { bv = ov; bp = op; }
       }
-      if (tid == 0) { const int p = perm[j]; perm[j] = perm[bt]; perm[bt] = p; }
+      if (lane == 0) { rv[wid] = bv; rp[wid] = bp; }
+      __syncthreads();
+      if (tid == 0) {
+        double v = -1.0;
+        int pp = 0x7fffffff;
+        for (int w = 0; w < nw; ++w)
+          if (rv[w] > v || (rv[w] == v && rp[w] < pp)) { v = rv[w]; pp = rp[w]; }
+        s_best = v;
+        s_bp = pp == 0x7fffffff ? -1 : pp;
+      }
+      __syncthreads();
+      if (s_bp < 0 || !(s_best > rr_tol)) { stop = true; break; }
+      const int pj = s_bp;
+      const int jq = j - p0;
+      const double piv = sqrt(d[pj]);
+      const double rpiv = 1.0 / piv;
+      // --- column j of L for every unchosen live column r != pj
+      for (int r = tid; r < m; r += nt) {
+        if (r == pj || !alive[r] || chosen[r]) continue;
+        double acc = r > pj ? A[(int64_t)r * m + pj] : A[(int64_t)pj * m + r];
+        for (int q = 0; q < jq; ++q) acc = fma(-Lp[q * m + r], Lp[q * m + pj], acc);
+        const double l = acc * rpiv;
+        Lp[jq * m + r] = l;
+        d[r] = fma(-l, l, d[r]);
+      }
+      if (tid == 0) {
+        Lp[jq * m + pj] = piv;
+        chosen[pj] = 1;
+        perm[j] = pj;
+        s_k = j + 1;
+      }
+      jn = jq + 1;
       __syncthreads();
     }
-    // --- column j of L and the trailing (lower) update -------------------------
-    const double piv = sqrt(A[(int64_t)j * m + j]);
-    const double rpiv = 1.0 / piv;
-    for (int t = j + tid; t < m; t += nt) {
-      const double v = t == j ? piv : A[(int64_t)t * m + j] * rpiv;
-      L[(int64_t)t * m + j] = v;
-      lcol[t] = v;
+    // --- the panel's columns into Lg (rows of ids chosen earlier in the panel
+    // hold stale values past their own column; those entries are never read)
+    for (int e = tid; e < jn * m; e += nt) {
+      const int q = e / m, id = e % m;
+      Lg[(int64_t)id * m + p0 + q] = Lp[q * m + id];
     }
-    __syncthreads();
-    for (int a = j + 1 + wid; a < m; a += nw) {
-      const double la = lcol[a];
-      double* row = A + (int64_t)a * m;
-      for (int b = j + 1 + lane; b <= a; b += 32) row[b] = fma(-la, lcol[b], row[b]);
+    // --- rank-jn update of the unchosen live rows and columns (lower triangle)
+    if (!stop) {
+      for (int a = wid; a < m; a += nw) {
+        if (!alive[a] || chosen[a]) continue;
+        double* row = A + (int64_t)a * m;
+        for (int b0 = 0; b0 <= a; b0 += 32 * 4) {
+          double v[4];
+          bool on[4];
+#pragma unroll
+          for (int u = 0; u < 4; ++u) {
+            const int b = b0 + u * 32 + lane;
+            on[u] = b <= a && alive[b] && !chosen[b];
+            v[u] = on[u] ? row[b] : 0.0;
+          }
+          for (int q = 0; q < jn; ++q) {
+            const double la = Lp[q * m + a];
+#pragma unroll
+            for (int u = 0; u < 4; ++u)
+              if (on[u]) v[u] = fma(-la, Lp[q * m + b0 + u * 32 + lane], v[u]);
+          }
+#pragma unroll
+          for (int u = 0; u < 4; ++u)
+            if (on[u]) row[b0 + u * 32 + lane] = v[u];
+        }
+      }
     }
-    if (tid == 0) s_k = j + 1;
     __syncthreads();
   }
   const int k = s_k;
+  // positions >= k: the remaining columns in increasing order
+  if (tid == 0) {
+    int pos = k;
+    for (int t = 0; t < m; ++t)
+      if (!chosen[t]) perm[pos++] = t;
+  }
+  __syncthreads();
   // --- X = L~^{-1} (k x k, row-major, ld m) into A, right-looking: row q of X
-  // is final once divided by L(q,q); it then updates every later row
-  // (warp per row, lanes over columns, row q staged in shared memory) ------
+  // is final once divided by L~(q,q); it then updates every later row (warp
+  // per row, lanes over columns, four loads in flight per lane, row q staged
+  // in shared memory).  L~(i, q) = Lg[perm[i]][q].
+  double* lcol = d;                             // reuse
   for (int64_t e = tid; e < (int64_t)k * k; e += nt) {
     const int i = (int)(e / k), c = (int)(e % k);
     A[(int64_t)i * m + c] = i == c ? 1.0 : 0.0;
   }
   __syncthreads();
   for (int q = 0; q < k; ++q) {
-    const double rq = 1.0 / L[(int64_t)q * m + q];
+    const double rq = 1.0 / Lg[(int64_t)perm[q] * m + q];
     for (int c = tid; c <= q; c += nt) {
       const double v = A[(int64_t)q * m + c] * rq;
       A[(int64_t)q * m + c] = v;
@@ -149,9 +185,21 @@ __global__ void __launch_bounds__(1024) k_rr_chol(const double* __restrict__ Del
     }
     __syncthreads();
     for (int i = q + 1 + wid; i < k; i += nw) {
-      const double li = L[(int64_t)i * m + q];
+      const double li = Lg[(int64_t)perm[i] * m + q];
       double* row = A + (int64_t)i * m;
-      for (int c = lane; c <= q; c += 32) row[c] = fma(-li, lcol[c], row[c]);
+      for (int c0 = 0; c0 <= q; c0 += 128) {
+        double v[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          const int cc = c0 + u * 32 + lane;
+          v[u] = cc <= q ? row[cc] : 0.0;
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          const int cc = c0 + u * 32 + lane;
+          if (cc <= q) row[cc] = fma(-li, lcol[cc], v[u]);
+        }
+      }
     }
     __syncthreads();
   }
@@ -247,7 +295,14 @@ __global__ void k_gemv_dense(const double* __restrict__ A, int n, int ld, const 
 cudaError_t rr_cholesky(const double* Delta, int m, int ld, double rr_tol, double* work, double* T, int* d_k,
                         int* d_perm, cudaStream_t st) {
   if (m > 1024) return cudaErrorInvalidValue;
-  k_rr_chol<<<1, 1024, 0, st>>>(Delta, m, ld, rr_tol, work, T, d_k, d_perm);
+  static bool attr_set = false;
+  const size_t smem = (size_t)RR_PB * 1024 * sizeof(double);
+  if (!attr_set) {
+    cudaError_t e = cudaFuncSetAttribute(k_rr_chol, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    attr_set = true;
+  }
+  k_rr_chol<<<1, RR_THREADS, (size_t)RR_PB * m * sizeof(double), st>>>(Delta, m, ld, rr_tol, work, T, d_k, d_perm);
   note_launches(1);
   return cudaGetLastError();
 }

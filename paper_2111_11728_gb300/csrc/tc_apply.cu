@@ -23,7 +23,7 @@ constexpr int TC_NMAX = 256;
 constexpr int TC_THREADS = 128;
 constexpr uint32_t TC_TMEM_COLS = 256;
 constexpr long long TC_SPIN_LIMIT = 1ll << 22;
-constexpr int TC_STAGES1 = 4;       // ring depth, one TF32 pass (48 KB per stage)
+constexpr int TC_STAGES1 = 2;       // ring depth, one TF32 pass (48 KB per stage; two CTAs per SM)
 constexpr int TC_STAGES3 = 2;       // ring depth, split product (96 KB per stage)
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
@@ -139,7 +139,7 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&v)[32]) {
 // shared-memory buffers (full / empty mbarriers), thread 32 issues the MMAs
 // (4 K=8 steps x PASSES per chunk) and frees a buffer by committing to its
 // empty barrier; the final commit releases the epilogue, in which each warp
-// reads its 32 TMEM lanes and writes FP64 rows scaled by D_s^{1/2}.
+// reads its 32 TMEM lanes and writes FP32 rows scaled by D_s^{1/2}.
 // Every wait is bounded: on time-out the CTA records an error code, waits
 // (bounded) for its copies and MMAs in flight, frees its tensor memory and
 // returns.
@@ -148,7 +148,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_tc_apply(
     const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmAl,
     const __grid_constant__ CUtensorMap tmB, const __grid_constant__ CUtensorMap tmBl,
     const DevType* __restrict__ types, const DevSub* __restrict__ subs, const int* __restrict__ frow,
-    const int64_t* __restrict__ bpad, const double* __restrict__ sqrtD, double* __restrict__ Yb, int64_t nbt,
+    const int64_t* __restrict__ bpad, const double* __restrict__ sqrtD, float* __restrict__ Yb, int64_t nbt,
     int m, int n_cb, int aug, int* __restrict__ status) {
   constexpr uint32_t A_BYTES = TC_M * 128, B_BYTES = TC_NMAX * 128;
   constexpr uint32_t STAGE_BYTES = (PASSES == 3 ? 2 : 1) * (A_BYTES + B_BYTES);
@@ -266,15 +266,15 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_tc_apply(
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     // ---- epilogue: warp w owns TMEM lanes [32w, 32w+32) = output rows ----
     const int r = row0 + warp * 32 + lane;
-    const double sd = r < nb ? sqrtD[S.b_off + r] : 0.0;
-    double* yrow = Yb + S.b_off + r;
+    const float sd = r < nb ? static_cast<float>(sqrtD[S.b_off + r]) : 0.0f;
+    float* yrow = Yb + S.b_off + r;
     for (int jc = 0; jc < np; jc += 32) {
       uint32_t v[32];
       tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)jc, v);
       if (r < nb) {
 #pragma unroll
         for (int c = 0; c < 32; ++c)
-          if (jc + c < ncols) yrow[(int64_t)(col0 + jc + c) * nbt] = sd * (double)__uint_as_float(v[c]);
+          if (jc + c < ncols) yrow[(int64_t)(col0 + jc + c) * nbt] = sd * __uint_as_float(v[c]);
       }
     }
   }
@@ -287,10 +287,13 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_tc_apply(
 }
 
 // B operand: xb[j][bpad(s) + k] = tf32 parts of sqrt(D_s)[k] (B^sT X)[b, j]
-// for k < n_b(s), zero for the padding up to the next multiple of 32.
+// for k < n_b(s), zero for the padding up to the next multiple of 32.  Each
+// thread serves TC_GJ consecutive directions, reading the row's multiplier
+// entries once.
+constexpr int TC_GJ = 8;
 template <int PASSES>
 __global__ void k_gather_tc(const DevType* __restrict__ types, const DevSub* __restrict__ subs,
-                            const int64_t* __restrict__ bpad, const double* __restrict__ X, int64_t ldx,
+                            const int64_t* __restrict__ bpad, const double* __restrict__ X, int64_t ldx, int m,
                             const int* __restrict__ b2l_off, const int* __restrict__ b2l_lam,
                             const signed char* __restrict__ b2l_sign, const double* __restrict__ sqrtD,
                             float* __restrict__ xb_hi, float* __restrict__ xb_lo, int64_t nbp) {
@@ -299,19 +302,35 @@ __global__ void k_gather_tc(const DevType* __restrict__ types, const DevSub* __r
   const int nbp_s = k_extent(nb, 0, 0);
   const int k = blockIdx.x * blockDim.x + threadIdx.x;
   if (k >= nbp_s) return;
-  const int j = blockIdx.z;
-  float v = 0.0f;
+  const int j0 = blockIdx.z * TC_GJ;
+  const int jn = min(TC_GJ, m - j0);
+  int q0 = 0, q1 = 0;
+  double sd = 0.0;
   if (k < nb) {
     const int64_t b = S.b_off + k;
-    const double* x = X + (int64_t)j * ldx;
-    double acc = 0.0;
-    for (int q = b2l_off[b]; q < b2l_off[b + 1]; ++q) acc += b2l_sign[q] > 0 ? x[b2l_lam[q]] : -x[b2l_lam[q]];
-    v = static_cast<float>(acc * sqrtD[b]);
+    q0 = b2l_off[b];
+    q1 = b2l_off[b + 1];
+    sd = sqrtD[b];
   }
-  const int64_t o = (int64_t)j * nbp + bpad[blockIdx.y] + k;
-  const float hi = to_tf32(v);
-  xb_hi[o] = hi;
-  if (PASSES == 3) xb_lo[o] = to_tf32(v - hi);
+  double acc[TC_GJ];
+#pragma unroll
+  for (int u = 0; u < TC_GJ; ++u) acc[u] = 0.0;
+  for (int q = q0; q < q1; ++q) {
+    const double* x = X + b2l_lam[q] + (int64_t)j0 * ldx;
+    const bool pos = b2l_sign[q] > 0;
+#pragma unroll
+    for (int u = 0; u < TC_GJ; ++u)
+      if (u < jn) acc[u] += pos ? x[(int64_t)u * ldx] : -x[(int64_t)u * ldx];
+  }
+  const int64_t o = (int64_t)j0 * nbp + bpad[blockIdx.y] + k;
+#pragma unroll
+  for (int u = 0; u < TC_GJ; ++u) {
+    if (u >= jn) break;
+    const float v = static_cast<float>(acc[u] * sd);
+    const float hi = to_tf32(v);
+    xb_hi[o + (int64_t)u * nbp] = hi;
+    if (PASSES == 3) xb_lo[o + (int64_t)u * nbp] = to_tf32(v - hi);
+  }
 }
 
 // A operand: arena rows of Fhat_s = D^{-1/2} F_s D^{-1/2}, TF32 parts.
@@ -347,35 +366,35 @@ __global__ void k_make_arena(const DevType* __restrict__ types, const DevModule*
 
 // Corner reduction of the precision form, FP32 on the CUDA cores:
 // C_s = F_rc,s^T X_b(s) = Frc_hat_s^T (D^{1/2} X_b(s)), read from the gathered
-// operand (high + low parts).  One block per subdomain and 64 directions; the
-// K loop stages 64 rows of Frc_hat and of the operand in shared memory.
+// operand (high + low parts) and the FP32 copy of Frc_hat.  One block per
+// subdomain and 128 directions; K is staged 32 rows at a time.
 __global__ void __launch_bounds__(256) k_frct_lowp(const DevType* __restrict__ types,
                                                    const DevModule* __restrict__ mods,
-                                                   const DevSub* __restrict__ subs, const double* __restrict__ mem,
+                                                   const DevSub* __restrict__ subs, const float* __restrict__ fmem,
                                                    const int64_t* __restrict__ bpad, const float* __restrict__ xb_hi,
                                                    const float* __restrict__ xb_lo, int64_t nbp, int m,
                                                    double* __restrict__ Cb, int64_t nct) {
-  __shared__ float fs[64][25];
-  __shared__ float xs[64][65];
+  __shared__ float fs[32][24];
+  __shared__ float xs[32][129];
   const DevSub S = subs[blockIdx.y];
   const DevType T = types[S.type];
   const int nb = T.n_b, nc = T.n_c;
   if (nc == 0) return;
-  const DevModule M = mods[S.module];
-  const double* F = mem + M.F;
-  const double* Frc = mem + M.Frc;
-  const int j0 = blockIdx.x * 64;
-  const int tid = threadIdx.x, jj = tid & 63, cg = tid >> 6;
+  const float* Fr = fmem + mods[S.module].Frc;      // [nb x nc] row-major
+  const int j0 = blockIdx.x * 128;
+  const int tid = threadIdx.x, jj = tid & 127, cg = tid >> 7;
   const float* xh = xb_hi + bpad[blockIdx.y];
   const float* xl = xb_lo ? xb_lo + bpad[blockIdx.y] : nullptr;
-  float acc[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-  for (int k0 = 0; k0 < nb; k0 += 64) {
-    for (int e = tid; e < 64 * nc; e += 256) {
-      const int kk = e / nc, c = e % nc, k = k0 + kk;
-      fs[kk][c] = k < nb ? static_cast<float>(Frc[(int64_t)k * nc + c] / sqrt(F[(int64_t)k * nb + k])) : 0.0f;
+  float acc[12];
+#pragma unroll
+  for (int q = 0; q < 12; ++q) acc[q] = 0.f;
+  for (int k0 = 0; k0 < nb; k0 += 32) {
+    for (int e = tid; e < 32 * 24; e += 256) {
+      const int kk = e / 24, c = e % 24, k = k0 + kk;
+      fs[kk][c] = (k < nb && c < nc) ? Fr[(int64_t)k * nc + c] : 0.0f;
     }
-    for (int e = tid; e < 64 * 64; e += 256) {
-      const int j2 = e >> 6, kk = e & 63, k = k0 + kk, j = j0 + j2;
+    for (int e = tid; e < 32 * 128; e += 256) {
+      const int j2 = e >> 5, kk = e & 31, k = k0 + kk, j = j0 + j2;
       float v = 0.0f;
       if (j < m && k < nb) {
         v = xh[(int64_t)j * nbp + k];
@@ -385,18 +404,18 @@ __global__ void __launch_bounds__(256) k_frct_lowp(const DevType* __restrict__ t
     }
     __syncthreads();
 #pragma unroll 8
-    for (int kk = 0; kk < 64; ++kk) {
+    for (int kk = 0; kk < 32; ++kk) {
       const float x = xs[kk][jj];
 #pragma unroll
-      for (int q = 0; q < 6; ++q) acc[q] = fmaf(fs[kk][cg * 6 + q], x, acc[q]);
+      for (int q = 0; q < 12; ++q) acc[q] = fmaf(fs[kk][cg * 12 + q], x, acc[q]);
     }
     __syncthreads();
   }
   const int j = j0 + jj;
   if (j < m) {
 #pragma unroll
-    for (int q = 0; q < 6; ++q) {
-      const int c = cg * 6 + q;
+    for (int q = 0; q < 12; ++q) {
+      const int c = cg * 12 + q;
       if (c < nc) Cb[S.c_off + c + (int64_t)j * nct] = static_cast<double>(acc[q]);
     }
   }
@@ -420,13 +439,24 @@ __global__ void k_put_v(const DevType* __restrict__ types, const DevSub* __restr
 }
 
 // Shat = D_S^{-1/2} S_bb D_S^{-1/2} (FP32) per module, for the preconditioner
-// block of the precision form.
+// block of the precision form, and Frc_hat = D_F^{-1/2} F_rc (FP32) for the
+// corner reduction.
 __global__ void k_make_lowp(const DevType* __restrict__ types, const DevModule* __restrict__ mods,
                             const double* __restrict__ mem, float* __restrict__ fmem) {
   const DevModule M = mods[blockIdx.y];
   const DevType T = types[M.type];
   const int n = T.n_b, nbc = T.n_b + T.n_c;
   const double* Sm = mem + M.S;
+  const double* F = mem + M.F;
+  const int nc = T.n_c;
+  if (nc > 0) {
+    const double* Frc = mem + M.Frc;
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < (int64_t)n * nc;
+         e += (int64_t)gridDim.x * blockDim.x) {
+      const int i = (int)(e / nc);
+      fmem[M.Frc + e] = static_cast<float>(Frc[e] / sqrt(F[(int64_t)i * n + i]));
+    }
+  }
   const int64_t total = (int64_t)n * n;
   for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
     const int i = (int)(e / n), j = (int)(e % n);
@@ -522,7 +552,7 @@ bool make_map(CUtensorMap* map, const float* base, int64_t pitch, int64_t rows, 
 }
 
 template <int PASSES, int STAGES>
-cudaError_t launch_tc(const Ctx& c, int m, double* Yb, cudaStream_t st) {
+cudaError_t launch_tc(const Ctx& c, int m, float* Yb, cudaStream_t st) {
   static bool attr_set = false;
   const size_t smem = tc_apply_smem_bytes(PASSES);
   if (!attr_set) {
@@ -556,13 +586,13 @@ cudaError_t tc_gather(const Ctx& c, const double* X, int64_t ldx, int m, cudaStr
   if (m <= 0) return cudaSuccess;
   if (m > c.xb_cap) return cudaErrorInvalidValue;
   const int max_nbp = k_extent(c.max_nb, 0, 0);
-  dim3 g((max_nbp + 127) / 128, c.hp.n_sub, m);
+  dim3 g((max_nbp + 127) / 128, c.hp.n_sub, (m + TC_GJ - 1) / TC_GJ);
   if (c.opt.precision == FETI_TF32X3)
-    k_gather_tc<3><<<g, 128, 0, st>>>(c.d_types, c.d_subs, c.d_bpad, X, ldx, c.d_b2l_off, c.d_b2l_lam, c.d_b2l_sign,
-                                      c.d_sqrtDF, c.d_xb_hi, c.d_xb_lo, c.nbp_total);
+    k_gather_tc<3><<<g, 128, 0, st>>>(c.d_types, c.d_subs, c.d_bpad, X, ldx, m, c.d_b2l_off, c.d_b2l_lam,
+                                      c.d_b2l_sign, c.d_sqrtDF, c.d_xb_hi, c.d_xb_lo, c.nbp_total);
   else
-    k_gather_tc<1><<<g, 128, 0, st>>>(c.d_types, c.d_subs, c.d_bpad, X, ldx, c.d_b2l_off, c.d_b2l_lam, c.d_b2l_sign,
-                                      c.d_sqrtDF, c.d_xb_hi, nullptr, c.nbp_total);
+    k_gather_tc<1><<<g, 128, 0, st>>>(c.d_types, c.d_subs, c.d_bpad, X, ldx, m, c.d_b2l_off, c.d_b2l_lam,
+                                      c.d_b2l_sign, c.d_sqrtDF, c.d_xb_hi, nullptr, c.nbp_total);
   note_launches(1);
   return cudaGetLastError();
 }
@@ -571,8 +601,8 @@ cudaError_t tc_gather(const Ctx& c, const double* X, int64_t ldx, int m, cudaStr
 // corner assembly Vraw = sum over the copies of each primal DOF.
 cudaError_t tc_corner_reduce(const Ctx& c, int m, double* Vraw, cudaStream_t st) {
   if (c.max_nc > 24) return cudaErrorInvalidValue;
-  k_frct_lowp<<<dim3((m + 63) / 64, c.hp.n_sub), 256, 0, st>>>(
-      c.d_types, c.d_mods, c.d_subs, c.d_modmem, c.d_bpad, c.d_xb_hi,
+  k_frct_lowp<<<dim3((m + 127) / 128, c.hp.n_sub), 256, 0, st>>>(
+      c.d_types, c.d_mods, c.d_subs, c.d_fmem, c.d_bpad, c.d_xb_hi,
       c.opt.precision == FETI_TF32X3 ? c.d_xb_lo : nullptr, c.nbp_total, m, c.d_Cb, c.n_c_total);
   note_launches(1);
   cudaError_t e = cudaGetLastError();
@@ -594,11 +624,15 @@ cudaError_t tc_put_v(const Ctx& c, const double* V, int m, cudaStream_t st) {
   return cudaGetLastError();
 }
 
-// Yb = D^{1/2} [Fhat | Frc_hat] xb for every subdomain (tensor cores).
-cudaError_t tc_product(const Ctx& c, int m, double* Yb, cudaStream_t st) {
+// Yb (FP32) = D^{1/2} [Fhat | Frc_hat] xb for every subdomain (tensor cores).
+cudaError_t tc_product(const Ctx& c, int m, float* Yb, cudaStream_t st) {
   if (m <= 0) return cudaSuccess;
   if (m > c.xb_cap) return cudaErrorInvalidValue;
-  return c.opt.precision == FETI_TF32X3 ? launch_tc<3, TC_STAGES3>(c, m, Yb, st) : launch_tc<1, TC_STAGES1>(c, m, Yb, st);
+  prof_begin(st, c.fl_tc * m, 1);
+  const cudaError_t e =
+      c.opt.precision == FETI_TF32X3 ? launch_tc<3, TC_STAGES3>(c, m, Yb, st) : launch_tc<1, TC_STAGES1>(c, m, Yb, st);
+  prof_end(st);
+  return e;
 }
 
 cudaError_t lowp_gemv_S(const Ctx& c, const double* xb, double* yb, cudaStream_t st) {

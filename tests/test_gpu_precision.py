@@ -69,11 +69,15 @@ def test_split_tf32_operator_is_fp32_class(m):
 
 
 def test_refined_split_tf32_solve_needs_few_refinements():
+    # with inner solves to 1e-5 (near the split product's accuracy) two or
+    # three FP64 refinement steps reach 1e-10; one TF32 pass cannot do that
     p = moderate()
     ud = direct_solve(p)
-    u, st, c, _ = solve_u(p, tol=1e-10, precision=fg.FETI_TF32X3)
+    u, st, c, _ = solve_u(p, tol=1e-10, precision=fg.FETI_TF32X3, inner_tol=1e-5)
     assert st.converged and 1 <= st.refinements <= 3
     assert rel(u, ud) <= 1e-8
+    _, st1, _, _ = solve_u(p, tol=1e-10, precision=fg.FETI_TF32, inner_tol=1e-5, max_iter=300)
+    assert st1.refinements > st.refinements or not st1.converged
 
 
 @pytest.mark.parametrize("method", ["fetidp", "tfeti"])
