@@ -53,6 +53,8 @@ def parse():
     ap.add_argument("--no-forms", action="store_true")
     ap.add_argument("--forms-rho-lo", type=float, default=0.1)
     ap.add_argument("--no-batch", action="store_true")
+    ap.add_argument("--forms-3d", action="store_true", help="also compare the forms on the 3D workload (minutes)")
+    ap.add_argument("--tiles-3d", type=int, default=8)
     ap.add_argument("--batch-problems", type=int, default=64)
     return ap.parse_args()
 
@@ -158,29 +160,20 @@ def apply_timing(fg, torch, stream, flush, s, n, m, reps=5):
     return float(np.median(ts))
 
 
-def compare_forms(a, fg, torch, dev, stream, flush):
-    """The precision form (tensor-core block products inside FP64 refinement on
-    the dual residual; one TF32 pass, or the three-pass split-TF32 product)
-    against the plain FP64 form at equal accuracy (same FP64 relative dual
-    residual), on the same modular layout with densities {rho_lo, 1}
-    (contrast (1/rho_lo)^3), where the reduced-precision blocks still carry the
-    information the solve needs.  Iterations are capped at 120 per solve."""
-    p = workloads.config2(tiles=a.tiles, elems=a.elems)
-    p.rho = np.where(p.rho < 0.5, a.forms_rho_lo, 1.0)
-    p.Emin = 1e-9
+def run_forms(p, a, fg, torch, dev, stream, flush, forms, max_iter, m_apply, reps=2):
+    """Time-to-solve (factorize + refined solve + recover) and the apply of m_apply
+    columns for each precision form on problem p, at the same FP64 relative dual
+    residual a.tol; solutions compared with the FP64 form's."""
     rho_d = torch.from_numpy(p.rho).to(dev)
     f_d = torch.from_numpy(p.f).to(dev)
-    out = {"workload": f"same layout, densities {{{a.forms_rho_lo}, 1}}, contrast {1 / a.forms_rho_lo ** 3:.0e}",
-           "rel_tol": a.tol, "max_iter": 120}
-    sols = {}
-    forms = (("fp64", fg.FETI_FP64), ("tf32x3", fg.FETI_TF32X3), ("tf32", fg.FETI_TF32))
+    out, sols = {}, {}
     for name, prec in forms:
-        s = fg.Solver(fg.FETI_FETIDP, fg.FETI_SCALING_K, fg.FETI_RRS, tol=a.tol, max_iter=120,
+        s = fg.Solver(fg.FETI_FETIDP, fg.FETI_SCALING_K, fg.FETI_RRS, tol=a.tol, max_iter=max_iter,
                       stream=stream.cuda_stream, precision=prec)
         s.setup(p, rho=rho_d, f=f_d, on_device=True)
         u = torch.empty(p.n_dofs, dtype=torch.float64, device=dev)
         times, st = [], None
-        for k in range(2):
+        for k in range(reps):
             flush.zero_()
             torch.cuda.synchronize()
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -190,20 +183,53 @@ def compare_forms(a, fg, torch, dev, stream, flush):
             fg.feti_recover_displacements(s.ctx, u, True)
             e1.record(stream)
             torch.cuda.synchronize()
-            if k >= 1:
+            if k >= reps - 1:
                 times.append(e0.elapsed_time(e1))
         n = fg.feti_query(s.ctx, fg.FETI_Q_N_LAMBDA)
-        ms_apply = apply_timing(fg, torch, stream, flush, s, n, 256)
+        ms_apply = apply_timing(fg, torch, stream, flush, s, n, m_apply)
         sols[name] = u.cpu().numpy()
         out[name] = {"time_to_solve_ms": float(np.median(times)), "iterations": st.iterations,
                      "refinements": st.refinements, "f_applies": st.f_applies, "converged": bool(st.converged),
-                     "apply_256_cols_ms": ms_apply, "apply_f_applies_per_s": 256 / (ms_apply / 1e3)}
+                     f"apply_{m_apply}_cols_ms": ms_apply, "apply_f_applies_per_s": m_apply / (ms_apply / 1e3)}
         s.close()
     ref = sols["fp64"]
+    t64 = out["fp64"]["time_to_solve_ms"]
+    a64 = out["fp64"][f"apply_{m_apply}_cols_ms"]
     for name, _ in forms[1:]:
         out[name]["rel_diff_vs_fp64"] = float(np.linalg.norm(sols[name] - ref) / np.linalg.norm(ref))
-        out[name]["speedup_time_to_solve"] = out["fp64"]["time_to_solve_ms"] / out[name]["time_to_solve_ms"]
-        out[name]["speedup_apply"] = out["fp64"]["apply_256_cols_ms"] / out[name]["apply_256_cols_ms"]
+        out[name]["speedup_time_to_solve"] = t64 / out[name]["time_to_solve_ms"]
+        out[name]["speedup_apply"] = a64 / out[name][f"apply_{m_apply}_cols_ms"]
+    return out
+
+
+def precision_forms(fg):
+    return (("fp64", fg.FETI_FP64), ("tf32x3", fg.FETI_TF32X3), ("tf32", fg.FETI_TF32),
+            ("bf16x3", fg.FETI_BF16X3), ("bf16", fg.FETI_BF16))
+
+
+def compare_forms(a, fg, torch, dev, stream, flush):
+    """The precision form (tensor-core block products inside FP64 refinement on
+    the dual residual; one TF32 / BF16 pass or the three-pass split products)
+    against the plain FP64 form at equal accuracy (same FP64 relative dual
+    residual), on the same modular layout with densities {rho_lo, 1}
+    (contrast (1/rho_lo)^3), where the reduced-precision blocks still carry the
+    information the solve needs.  Iterations are capped at 120 per solve."""
+    p = workloads.config2(tiles=a.tiles, elems=a.elems)
+    p.rho = np.where(p.rho < 0.5, a.forms_rho_lo, 1.0)
+    p.Emin = 1e-9
+    out = {"workload": f"same layout, densities {{{a.forms_rho_lo}, 1}}, contrast {1 / a.forms_rho_lo ** 3:.0e}",
+           "rel_tol": a.tol, "max_iter": 120}
+    out.update(run_forms(p, a, fg, torch, dev, stream, flush, precision_forms(fg), 120, 256))
+    return out
+
+
+def compare_forms_3d(a, fg, torch, dev, stream, flush):
+    """The same comparison on the 3D workload: 8^3 subdomains of 8^3 H8
+    elements, smoothed density field in [1e-3, 1] (823,875 DOF)."""
+    p = workloads.config4(tiles=a.tiles_3d, elems=8)
+    out = {"workload": f"3D H8: {a.tiles_3d}^3 subdomains of 8^3 elements, smoothed field in [1e-3, 1]",
+           "rel_tol": a.tol, "max_iter": 60}
+    out.update(run_forms(p, a, fg, torch, dev, stream, flush, precision_forms(fg), 60, 512, reps=1))
     return out
 
 
@@ -422,6 +448,9 @@ def run_ours(a, rank, world):
     forms = None
     if not a.no_forms:
         forms = compare_forms(a, fg, torch, dev, stream, flush)
+    forms3d = None
+    if a.forms_3d and world == 1:
+        forms3d = compare_forms_3d(a, fg, torch, dev, stream, flush)
     batch = None
     if not a.no_batch and world == 1:
         batch = compare_batch(a, fg, torch, dev, stream)
@@ -444,7 +473,7 @@ def run_ours(a, rank, world):
                      "kernel_share_of_step": (gms / 1e3) / t_steps if t_steps > 0 else None,
                      "launches": gn},
         "e2e": e2e, "gpu_launches": int(launches), "clocks": clk, "wall_s": wall,
-        "forms": forms, "batch_form": batch,
+        "forms": forms, "forms_3d": forms3d, "batch_form": batch,
     }
     s.close()
     return out

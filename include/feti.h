@@ -53,23 +53,26 @@ typedef enum {
   FETI_ENOTCONV = 4,    /* max_iter reached: outputs valid but unconverged */
   FETI_EBREAKDOWN = 5,  /* NaN/Inf or no independent search direction left */
   FETI_ECUDA = 6,       /* a CUDA runtime call or kernel launch failed */
-  FETI_ENOTSUP = 7      /* option combination not implemented */
+  FETI_ENOTSUP = 7,     /* option combination not implemented */
+  FETI_ETIMEOUT = 8     /* a bounded device-side wait (tensor-core pipeline) expired; the
+                           context stays usable, the results of that call are not */
 } feti_status;
 
 enum { FETI_TFETI = 0, FETI_FETIDP = 1 };                 /* Sections 2.1 / 2.2 */
 enum { FETI_SCALING_K = 0, FETI_SCALING_MULT = 1 };       /* Eq. 15 / multiplicity */
 enum { FETI_PCG = 0, FETI_FO = 1, FETI_RRS = 2 };         /* Sections 3.2, 3.3 */
-enum { FETI_FP64 = 0, FETI_TF32 = 1, FETI_TF32X3 = 2 };  /* dense block-product precision */
+enum { FETI_FP64 = 0, FETI_TF32 = 1, FETI_TF32X3 = 2, FETI_BF16 = 3, FETI_BF16X3 = 4 };  /* block products */
 
 typedef struct {
   int method;          /* FETI_TFETI or FETI_FETIDP */
   int scaling;         /* FETI_SCALING_K or FETI_SCALING_MULT */
   int krylov;          /* FETI_PCG, FETI_FO or FETI_RRS */
-  int precision;       /* FETI_FP64 (default), FETI_TF32 or FETI_TF32X3: the dense F_s block
-                          products on the tensor cores with FP32 accumulation -- one TF32 pass, or
-                          the three-pass split (hi*hi + hi*lo + lo*hi, FP32-class accuracy) --
-                          and FP32 S_s blocks, inside FP64 iterative refinement on the dual
-                          residual; Gram and orthogonalization stay FP64 */
+  int precision;       /* FETI_FP64 (default), FETI_TF32, FETI_TF32X3, FETI_BF16, FETI_BF16X3: the
+                          dense F_s (and F_rc) block products on the tensor cores with FP32
+                          accumulation -- one TF32 / BF16 pass, or the three-pass split
+                          (hi*hi + hi*lo + lo*hi) -- and FP32 S_s blocks, inside FP64 iterative
+                          refinement on the dual residual; factorizations, coarse problem, Gram
+                          and orthogonalization stay FP64 */
   int max_iter;        /* Krylov iteration cap (default 500) */
   int dedup_modules;   /* 1: factorize identical modules once (Section 1) */
   double tol;          /* relative tolerance on sqrt(r^T z) (default 1e-6) */

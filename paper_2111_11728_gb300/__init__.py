@@ -16,17 +16,19 @@ import numpy as np
 HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "libfeti_gb300.so")
 
-FETI_OK, FETI_EINVAL, FETI_ENOMEM, FETI_ESTATE, FETI_ENOTCONV, FETI_EBREAKDOWN, FETI_ECUDA, FETI_ENOTSUP = range(8)
+(FETI_OK, FETI_EINVAL, FETI_ENOMEM, FETI_ESTATE, FETI_ENOTCONV, FETI_EBREAKDOWN, FETI_ECUDA, FETI_ENOTSUP,
+ FETI_ETIMEOUT) = range(9)
 FETI_TFETI, FETI_FETIDP = 0, 1
 FETI_SCALING_K, FETI_SCALING_MULT = 0, 1
 FETI_PCG, FETI_FO, FETI_RRS = 0, 1, 2
-FETI_FP64, FETI_TF32, FETI_TF32X3 = 0, 1, 2
+FETI_FP64, FETI_TF32, FETI_TF32X3, FETI_BF16, FETI_BF16X3 = 0, 1, 2, 3, 4
 (FETI_Q_N_LAMBDA, FETI_Q_N_SUBDOMAINS, FETI_Q_N_PRIMAL, FETI_Q_N_MODULES, FETI_Q_N_B_TOTAL, FETI_Q_N_DOFS,
  FETI_Q_N_ELEMENTS, FETI_Q_MAX_NB, FETI_Q_DEVICE_BYTES, FETI_Q_N_RBM, FETI_Q_LAUNCHES, FETI_Q_N_PROBLEMS,
  FETI_Q_GEMV_CONFIG) = range(13)
 
 STATUS_NAMES = {0: "FETI_OK", 1: "FETI_EINVAL", 2: "FETI_ENOMEM", 3: "FETI_ESTATE", 4: "FETI_ENOTCONV",
-                5: "FETI_EBREAKDOWN", 6: "FETI_ECUDA", 7: "FETI_ENOTSUP"}
+                5: "FETI_EBREAKDOWN", 6: "FETI_ECUDA", 7: "FETI_ENOTSUP",
+                8: "FETI_ETIMEOUT"}
 
 EXPORTS = [
     "feti_options_default", "feti_create", "feti_setup_subdomains", "feti_setup_batch", "feti_problem_result",

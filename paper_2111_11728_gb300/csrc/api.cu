@@ -43,6 +43,15 @@ feti_status dalloc(Ctx& c, T*& p, size_t n) {
   return FETI_OK;
 }
 
+feti_status dalloc_bytes(Ctx& c, void*& p, size_t bytes) {
+  unsigned char* q = nullptr;
+  TRY(dalloc(c, q, bytes));
+  p = q;
+  return FETI_OK;
+}
+
+bool split_precision(int p) { return p == FETI_TF32X3 || p == FETI_BF16X3; }
+
 template <class T>
 feti_status upload(Ctx& c, T*& p, const std::vector<T>& v) {
   TRY(dalloc(c, p, v.size()));
@@ -124,9 +133,10 @@ feti_status ensure_blocks(Ctx& c, int m) {
     TRY(dalloc(c, c.d_ct2, (size_t)c.n_coarse * cap));
   }
   if (c.opt.precision != FETI_FP64) {
-    TRY(dalloc(c, c.d_xb_hi, (size_t)c.nbp_total * cap));
+    const size_t eb = tc_elem_bytes(c.opt.precision);
+    TRY(dalloc_bytes(c, c.d_xb_hi, (size_t)c.nbp_total * cap * eb));
     TRY(dalloc(c, c.d_Yb32, (size_t)nbt * cap));
-    if (c.opt.precision == FETI_TF32X3) TRY(dalloc(c, c.d_xb_lo, (size_t)c.nbp_total * cap));
+    if (split_precision(c.opt.precision)) TRY(dalloc_bytes(c, c.d_xb_lo, (size_t)c.nbp_total * cap * eb));
     c.xb_cap = cap;
   }
   c.blk_cap = cap;
@@ -273,10 +283,10 @@ feti_status check_status(Ctx& c, const char* where) {
   if (st != 0) {
     c.err = std::string(where) + ": non-positive pivot (";
     if (st >= 3000000) {
-      c.err = std::string(where) + ": a tensor-core product timed out waiting for its MMAs (subdomain " +
+      c.err = std::string(where) + ": a tensor-core product timed out waiting for its copies or MMAs (subdomain " +
               std::to_string(st - 3000000) + ")";
       CU(cudaMemset(c.d_status, 0, sizeof(int)));
-      return FETI_ECUDA;
+      return FETI_ETIMEOUT;
     }
     if (st >= 2000000) c.err += "dense factor, tag " + std::to_string(st - 2000000);
     else c.err += "banded factor of module " + std::to_string(st - 1000000);
@@ -353,7 +363,7 @@ feti_status feti_create(feti_ctx** out, const feti_options* opt, void* stream) {
       (o.scaling != FETI_SCALING_K && o.scaling != FETI_SCALING_MULT) ||
       (o.krylov < FETI_PCG || o.krylov > FETI_RRS) || o.max_iter < 0 || !(o.tol >= 0.0) || !(o.rr_tol >= 0.0))
     return FETI_EINVAL;
-  if (o.precision != FETI_FP64 && o.precision != FETI_TF32 && o.precision != FETI_TF32X3) return FETI_EINVAL;
+  if (o.precision < FETI_FP64 || o.precision > FETI_BF16X3) return FETI_EINVAL;
   if (o.precision != FETI_FP64 && !(o.inner_tol >= 0.0 && o.inner_tol < 1.0 && o.max_refine > 0)) return FETI_EINVAL;
   feti_ctx* ctx = new (std::nothrow) feti_ctx;
   if (!ctx) return FETI_ENOMEM;
@@ -607,12 +617,13 @@ static feti_status setup_impl(Ctx& c, const feti_problem* probs, int n) {
       c.err = "precision form: more than 24 corner DOFs per subdomain";
       return FETI_ENOTSUP;
     }
+    const int kc = tc_chunk(c.opt.precision);
     std::vector<int64_t> bpad(hp.n_sub);
-    int64_t nbp = 0, kmax = 32;
+    int64_t nbp = 0, kmax = kc;
     for (int s = 0; s < hp.n_sub; ++s) {
       const DevType& T = c.h_types[c.h_subs[s].type];
       bpad[s] = nbp;
-      const int kx = tc_k_extent(T.n_b, T.n_c, c.tc_aug);
+      const int kx = tc_k_extent(T.n_b, T.n_c, c.tc_aug, kc);
       nbp += kx;
       kmax = std::max<int64_t>(kmax, kx);
     }
@@ -627,14 +638,15 @@ static feti_status setup_impl(Ctx& c, const feti_problem* probs, int n) {
       c.fl_tc += 2.0 * T.n_b * (T.n_b + (c.tc_aug ? T.n_c : 0));
     }
     c.fa_rows = std::max<int64_t>(rows, 1);
-    c.nbp_total = std::max<int64_t>(nbp, 32);
+    c.nbp_total = std::max<int64_t>(nbp, kc);
     TRY(upload(c, c.d_frow, frow));
     TRY(upload(c, c.d_bpad, bpad));
-    TRY(dalloc(c, c.d_fa_hi, (size_t)(c.fa_rows * c.fa_pitch)));
-    CU(cudaMemset(c.d_fa_hi, 0, (size_t)(c.fa_rows * c.fa_pitch) * sizeof(float)));
-    if (c.opt.precision == FETI_TF32X3) {
-      TRY(dalloc(c, c.d_fa_lo, (size_t)(c.fa_rows * c.fa_pitch)));
-      CU(cudaMemset(c.d_fa_lo, 0, (size_t)(c.fa_rows * c.fa_pitch) * sizeof(float)));
+    const size_t fa_bytes = (size_t)(c.fa_rows * c.fa_pitch) * tc_elem_bytes(c.opt.precision);
+    TRY(dalloc_bytes(c, c.d_fa_hi, fa_bytes));
+    CU(cudaMemset(c.d_fa_hi, 0, fa_bytes));
+    if (split_precision(c.opt.precision)) {
+      TRY(dalloc_bytes(c, c.d_fa_lo, fa_bytes));
+      CU(cudaMemset(c.d_fa_lo, 0, fa_bytes));
     }
     TRY(dalloc(c, c.d_fmem, (size_t)c.modmem_len));
     TRY(dalloc(c, c.d_sqrtDF, nbt));
@@ -715,7 +727,9 @@ static feti_status setup_impl(Ctx& c, const feti_problem* probs, int n) {
       TRY(upload(c, c.d_gemm_coarse, gc));
     }
   }
-  TRY(ensure_blocks(c, std::max(64, hp.n_sub)));
+  // direction-block buffers: one column per subdomain for the simultaneous
+  // variant, a few for PCG / FO (grown on demand by feti_apply_dual)
+  TRY(ensure_blocks(c, c.opt.krylov == FETI_RRS ? std::max(64, hp.n_sub) : 64));
   TRY(sync_check(c));
   c.state = 1;
   return FETI_OK;

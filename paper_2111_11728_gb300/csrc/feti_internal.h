@@ -219,13 +219,13 @@ struct Ctx {
   double* d_coarse_work = nullptr;   // blocked coarse factorisation work
   // precision form (FETI_TF32)
   float* d_fmem = nullptr;       // FP32 copies at the module offsets: Shat at M.W
-  float* d_fa_hi = nullptr;      // [fa_rows x fa_pitch] Fhat rows of every module, TF32, zero padded
-  float* d_fa_lo = nullptr;      // same layout: TF32 rounding of the remainder (split product)
+  void* d_fa_hi = nullptr;       // [fa_rows x fa_pitch] Fhat rows of every module (TF32 or BF16), zero padded
+  void* d_fa_lo = nullptr;       // same layout: rounding of the remainder (split products)
   int64_t fa_pitch = 0, fa_rows = 0;
   int* d_frow = nullptr;         // [n_mod] first arena row of each module
-  int64_t nbp_total = 0;         // interface space with each subdomain padded to a multiple of 32
+  int64_t nbp_total = 0;         // interface space with each subdomain padded to the format's chunk
   int64_t* d_bpad = nullptr;     // [n_sub] padded offsets
-  float *d_xb_hi = nullptr, *d_xb_lo = nullptr;   // [m x nbp_total] gathered scaled directions
+  void *d_xb_hi = nullptr, *d_xb_lo = nullptr;    // [m x nbp_total] gathered scaled directions
   float* d_Yb32 = nullptr;       // [m x n_b_total] output of the tensor-core product (FP32)
   int xb_cap = 0;
   int tc_aug = 0;                // FETI-DP corner coupling appended to the operands (K-extension)

@@ -146,7 +146,9 @@ cudaError_t tc_corner_reduce(const Ctx& c, int m, double* Vraw, cudaStream_t st)
 cudaError_t tc_put_v(const Ctx& c, const double* V, int m, cudaStream_t st);
 cudaError_t tc_product(const Ctx& c, int m, float* Yb, cudaStream_t st);
 cudaError_t scatter_b_to_lam32(const Ctx& c, const float* Yb, int m, double* Y, int64_t ldy, cudaStream_t st);
-int tc_k_extent(int nb, int nc, int aug);
+int tc_k_extent(int nb, int nc, int aug, int kc);
+int tc_chunk(int precision);            // K chunk of the operand format: 32 (TF32) or 64 (BF16)
+size_t tc_elem_bytes(int precision);    // 4 (TF32) or 2 (BF16)
 cudaError_t corner_assemble(const Ctx& c, int m, double* Vraw, cudaStream_t st);
 cudaError_t lowp_gemv_S(const Ctx& c, const double* xb, double* yb, cudaStream_t st);
 // Yb(s) += F_rc,s V[c_glob(s), :] with a thin kernel (no tile padding)

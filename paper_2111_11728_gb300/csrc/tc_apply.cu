@@ -2,11 +2,13 @@
 //
 //   Y_b(s) = D_s^{1/2} Fhat_s D_s^{1/2} X_b(s),   Fhat_s = D_s^{-1/2} F_s D_s^{-1/2},
 //
-// with D_s = diag(F_s).  Fhat_s is kept in TF32 (and, for the split product,
-// the TF32 rounding of its remainder), the product runs on the 5th-generation
-// tensor cores (tcgen05.mma kind::tf32) with FP32 accumulation in tensor
-// memory, operands staged by TMA into 128-byte-swizzled shared memory.
+// with D_s = diag(F_s).  Fhat_s is kept in TF32 or BF16 (and, for the split
+// products, the rounding of its remainder to the same format), the product
+// runs on the 5th-generation tensor cores (tcgen05.mma kind::tf32, or
+// kind::f16 with BF16 inputs) with FP32 accumulation in tensor memory,
+// operands staged by TMA into 128-byte-swizzled shared memory.
 #include <cuda.h>
+#include <cuda_bf16.h>
 #include <cudaTypedefs.h>
 
 #include <cstdint>
@@ -18,12 +20,11 @@ namespace feti {
 namespace {
 
 constexpr int TC_M = 128;
-constexpr int TC_KC = 32;           // FP32 elements per 128-byte row
 constexpr int TC_NMAX = 256;
 constexpr int TC_THREADS = 128;
 constexpr uint32_t TC_TMEM_COLS = 256;
 constexpr long long TC_SPIN_LIMIT = 1ll << 22;
-constexpr int TC_STAGES1 = 2;       // ring depth, one TF32 pass (48 KB per stage; two CTAs per SM)
+constexpr int TC_STAGES1 = 2;       // ring depth, one pass (48 KB per stage; two CTAs per SM)
 constexpr int TC_STAGES3 = 2;       // ring depth, split product (96 KB per stage)
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
@@ -43,17 +44,13 @@ __device__ __forceinline__ uint64_t desc_sw128(uint32_t saddr) {
   return d;
 }
 
-// Instruction descriptor: D = F32, A = B = TF32, both K-major, M = 128, N = n.
-__device__ __forceinline__ uint32_t idesc_tf32(int n) {
-  return (1u << 4) | (2u << 7) | (2u << 10) | (static_cast<uint32_t>(n >> 3) << 17) |
+// Instruction descriptor: D = F32, A = B = TF32 (kind::tf32, format 2) or
+// BF16 (kind::f16, format 1), both K-major, M = 128, N = n.
+template <int FMT>
+__device__ __forceinline__ uint32_t idesc_of(int n) {
+  constexpr uint32_t ab = FMT == 0 ? 2u : 1u;
+  return (1u << 4) | (ab << 7) | (ab << 10) | (static_cast<uint32_t>(n >> 3) << 17) |
          (static_cast<uint32_t>(TC_M >> 4) << 24);
-}
-
-// Byte offset of element (row, k) of a K-major tile with 128-byte rows and the
-// 128-byte swizzle (16-byte chunk index XOR row % 8).
-__device__ __forceinline__ uint32_t sw128_offset(int row, int k) {
-  const int chunk = (k >> 2) ^ (row & 7);
-  return static_cast<uint32_t>((row >> 3) * 1024 + (row & 7) * 128 + chunk * 16 + (k & 3) * 4);
 }
 
 __device__ __forceinline__ float to_tf32(float x) {
@@ -78,10 +75,30 @@ __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t phase) {
 }
 
 
-// K extent of a subdomain in the tensor-core operands: n_b rounded up to 32,
-// plus one 32-wide chunk for the corner coupling when it is appended.
-__host__ __device__ __forceinline__ int k_extent(int nb, int nc, int aug) {
-  return (nb + TC_KC - 1) / TC_KC * TC_KC + ((aug && nc > 0) ? TC_KC : 0);
+// Operand formats.  FMT 0: TF32 values stored as FP32 bit patterns (32 per
+// 128-byte row, K = 8 per MMA); FMT 1: BF16 (64 per row, K = 16 per MMA).
+// Either way one MMA consumes 32 bytes of every operand row.
+template <int FMT>
+struct TcFmt;
+template <>
+struct TcFmt<0> {
+  using T = float;
+  static constexpr int KC = 32;
+  __device__ static T round(float v) { return to_tf32(v); }
+  __device__ static float value(T x) { return x; }
+};
+template <>
+struct TcFmt<1> {
+  using T = __nv_bfloat16;
+  static constexpr int KC = 64;
+  __device__ static T round(float v) { return __float2bfloat16_rn(v); }
+  __device__ static float value(T x) { return __bfloat162float(x); }
+};
+
+// K extent of a subdomain in the tensor-core operands: n_b rounded up to the
+// format's chunk kc, plus one chunk for the corner coupling when appended.
+__host__ __device__ __forceinline__ int k_extent(int nb, int nc, int aug, int kc) {
+  return (nb + kc - 1) / kc * kc + ((aug && nc > 0) ? kc : 0);
 }
 
 __device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap* map, int x, int y, uint32_t bar) {
@@ -92,13 +109,22 @@ __device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap* map
       : "memory");
 }
 
-__device__ __forceinline__ void mma_tf32(uint32_t tmem, uint64_t ad, uint64_t bd, uint32_t idesc, uint32_t acc) {
-  asm volatile(
-      "{\n\t.reg .pred p;\n\t"
-      "setp.ne.b32 p, %4, 0;\n\t"
-      "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem),
-      "l"(ad), "l"(bd), "r"(idesc), "r"(acc)
-      : "memory");
+template <int FMT>
+__device__ __forceinline__ void mma_issue(uint32_t tmem, uint64_t ad, uint64_t bd, uint32_t idesc, uint32_t acc) {
+  if (FMT == 0)
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "setp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem),
+        "l"(ad), "l"(bd), "r"(idesc), "r"(acc)
+        : "memory");
+  else
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "setp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem),
+        "l"(ad), "l"(bd), "r"(idesc), "r"(acc)
+        : "memory");
 }
 
 // 32 consecutive FP32 columns of this warp's 32 TMEM lanes (one per thread).
@@ -143,7 +169,7 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&v)[32]) {
 // Every wait is bounded: on time-out the CTA records an error code, waits
 // (bounded) for its copies and MMAs in flight, frees its tensor memory and
 // returns.
-template <int PASSES, int STAGES>
+template <int FMT, int PASSES, int STAGES>
 __global__ void __launch_bounds__(TC_THREADS, 1) k_tc_apply(
     const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmAl,
     const __grid_constant__ CUtensorMap tmB, const __grid_constant__ CUtensorMap tmBl,
@@ -152,6 +178,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_tc_apply(
     int m, int n_cb, int aug, int* __restrict__ status) {
   constexpr uint32_t A_BYTES = TC_M * 128, B_BYTES = TC_NMAX * 128;
   constexpr uint32_t STAGE_BYTES = (PASSES == 3 ? 2 : 1) * (A_BYTES + B_BYTES);
+  constexpr int KC = TcFmt<FMT>::KC;
   extern __shared__ __align__(1024) unsigned char tc_smem_raw[];
   unsigned char* base = tc_smem_raw + ((1024 - (smem_u32(tc_smem_raw) & 1023)) & 1023);
   __shared__ __align__(8) uint64_t full_bar[STAGES], empty_bar[STAGES], done_bar;
@@ -168,7 +195,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_tc_apply(
   const int col0 = cb * TC_NMAX;
   const int ncols = min(TC_NMAX, m - col0);
   const int np = ((ncols + 15) / 16) * 16;
-  const int nk = k_extent(nb, T.n_c, aug) / TC_KC;
+  const int nk = k_extent(nb, T.n_c, aug, KC) / KC;
   const int arow = frow[S.module] + row0;
   const int bx0 = (int)bpad[sidx];
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -207,17 +234,17 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_tc_apply(
       unsigned char* sb = base + st * STAGE_BYTES;
       const uint32_t fb = smem_u32(&full_bar[st]);
       asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(fb), "r"(STAGE_BYTES) : "memory");
-      tma_load_2d(smem_u32(sb), &tmA, kc * TC_KC, arow, fb);
-      tma_load_2d(smem_u32(sb + A_BYTES), &tmB, bx0 + kc * TC_KC, col0, fb);
+      tma_load_2d(smem_u32(sb), &tmA, kc * KC, arow, fb);
+      tma_load_2d(smem_u32(sb + A_BYTES), &tmB, bx0 + kc * KC, col0, fb);
       if (PASSES == 3) {
-        tma_load_2d(smem_u32(sb + A_BYTES + B_BYTES), &tmAl, kc * TC_KC, arow, fb);
-        tma_load_2d(smem_u32(sb + 2 * A_BYTES + B_BYTES), &tmBl, bx0 + kc * TC_KC, col0, fb);
+        tma_load_2d(smem_u32(sb + A_BYTES + B_BYTES), &tmAl, kc * KC, arow, fb);
+        tma_load_2d(smem_u32(sb + 2 * A_BYTES + B_BYTES), &tmBl, bx0 + kc * KC, col0, fb);
       }
       issued = kc + 1;
     }
   } else if (tid == 32) {
     // ---- MMA issuer ----
-    const uint32_t idesc = idesc_tf32(np);
+    const uint32_t idesc = idesc_of<FMT>(np);
     int kc = 0;
     for (; kc < nk; ++kc) {
       const int st = kc % STAGES, it = kc / STAGES;
@@ -231,14 +258,14 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_tc_apply(
       const uint32_t sal = sa + A_BYTES + B_BYTES;
       const uint32_t sbl = sa + 2 * A_BYTES + B_BYTES;
 #pragma unroll
-      for (int kk = 0; kk < TC_KC / 8; ++kk) {
+      for (int kk = 0; kk < 4; ++kk) {                 // 32 bytes of each row per MMA
 #pragma unroll
         for (int pass = 0; pass < PASSES; ++pass) {
           // split product: lo x hi, hi x lo, then hi x hi (small terms first)
           const uint32_t ap = (PASSES == 3 && pass == 0) ? sal : sa;
           const uint32_t bp = (PASSES == 3 && pass == 1) ? sbl : sbh;
           const uint32_t acc = (kc > 0 || kk > 0 || pass > 0) ? 1u : 0u;
-          mma_tf32(tmem, desc_sw128(ap + kk * 32), desc_sw128(bp + kk * 32), idesc, acc);
+          mma_issue<FMT>(tmem, desc_sw128(ap + kk * 32), desc_sw128(bp + kk * 32), idesc, acc);
         }
       }
       asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
@@ -286,20 +313,22 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_tc_apply(
   }
 }
 
-// B operand: xb[j][bpad(s) + k] = tf32 parts of sqrt(D_s)[k] (B^sT X)[b, j]
-// for k < n_b(s), zero for the padding up to the next multiple of 32.  Each
-// thread serves TC_GJ consecutive directions, reading the row's multiplier
-// entries once.
+// B operand: xb[j][bpad(s) + k] = parts of sqrt(D_s)[k] (B^sT X)[b, j] in
+// the operand format for k < n_b(s), zero for the padding up to the next
+// multiple of the format's chunk.  Each thread serves TC_GJ consecutive
+// directions, reading the row's multiplier entries once.
 constexpr int TC_GJ = 8;
-template <int PASSES>
+template <int FMT, int PASSES>
 __global__ void k_gather_tc(const DevType* __restrict__ types, const DevSub* __restrict__ subs,
                             const int64_t* __restrict__ bpad, const double* __restrict__ X, int64_t ldx, int m,
                             const int* __restrict__ b2l_off, const int* __restrict__ b2l_lam,
                             const signed char* __restrict__ b2l_sign, const double* __restrict__ sqrtD,
-                            float* __restrict__ xb_hi, float* __restrict__ xb_lo, int64_t nbp) {
+                            typename TcFmt<FMT>::T* __restrict__ xb_hi, typename TcFmt<FMT>::T* __restrict__ xb_lo,
+                            int64_t nbp) {
+  using F = TcFmt<FMT>;
   const DevSub S = subs[blockIdx.y];
   const int nb = types[S.type].n_b;
-  const int nbp_s = k_extent(nb, 0, 0);
+  const int nbp_s = k_extent(nb, 0, 0, F::KC);
   const int k = blockIdx.x * blockDim.x + threadIdx.x;
   if (k >= nbp_s) return;
   const int j0 = blockIdx.z * TC_GJ;
@@ -327,40 +356,43 @@ __global__ void k_gather_tc(const DevType* __restrict__ types, const DevSub* __r
   for (int u = 0; u < TC_GJ; ++u) {
     if (u >= jn) break;
     const float v = static_cast<float>(acc[u] * sd);
-    const float hi = to_tf32(v);
+    const typename F::T hi = F::round(v);
     xb_hi[o + (int64_t)u * nbp] = hi;
-    if (PASSES == 3) xb_lo[o + (int64_t)u * nbp] = to_tf32(v - hi);
+    if (PASSES == 3) xb_lo[o + (int64_t)u * nbp] = F::round(v - F::value(hi));
   }
 }
 
-// A operand: arena rows of Fhat_s = D^{-1/2} F_s D^{-1/2}, TF32 parts.
-// (and, with aug, Frc_hat_s = D^{-1/2} F_rc,s after column n_b rounded up to 32).
+// A operand: arena rows of Fhat_s = D^{-1/2} F_s D^{-1/2} in the operand
+// format (and, with aug, Frc_hat_s = D^{-1/2} F_rc,s after column n_b rounded
+// up to the format's chunk).
+template <int FMT>
 __global__ void k_make_arena(const DevType* __restrict__ types, const DevModule* __restrict__ mods,
                              const double* __restrict__ mem, const int* __restrict__ frow, int64_t pitch, int aug,
-                             float* __restrict__ fa_hi, float* __restrict__ fa_lo) {
+                             typename TcFmt<FMT>::T* __restrict__ fa_hi, typename TcFmt<FMT>::T* __restrict__ fa_lo) {
+  using F = TcFmt<FMT>;
   const DevModule M = mods[blockIdx.y];
   const DevType T = types[M.type];
   const int n = T.n_b, nc = (aug ? T.n_c : 0);
   const int ncol = n + nc;
-  const int c0 = k_extent(n, 0, 0);
-  const double* F = mem + M.F;
+  const int c0 = k_extent(n, 0, 0, F::KC);
+  const double* Fm = mem + M.F;
   const double* Frc = mem + M.Frc;                  // [n x nc] row-major
   const int64_t total = (int64_t)n * ncol;
   for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
     const int i = (int)(e / ncol), j = (int)(e % ncol);
-    const double di = sqrt(F[(int64_t)i * n + i]);
+    const double di = sqrt(Fm[(int64_t)i * n + i]);
     float v;
     int64_t o;
     if (j < n) {
-      v = static_cast<float>(F[(int64_t)i * n + j] / (di * sqrt(F[(int64_t)j * n + j])));
+      v = static_cast<float>(Fm[(int64_t)i * n + j] / (di * sqrt(Fm[(int64_t)j * n + j])));
       o = (int64_t)(frow[blockIdx.y] + i) * pitch + j;
     } else {
       v = static_cast<float>(Frc[(int64_t)i * nc + (j - n)] / di);
       o = (int64_t)(frow[blockIdx.y] + i) * pitch + c0 + (j - n);
     }
-    const float hi = to_tf32(v);
+    const typename F::T hi = F::round(v);
     fa_hi[o] = hi;
-    if (fa_lo) fa_lo[o] = to_tf32(v - hi);
+    if (fa_lo) fa_lo[o] = F::round(v - F::value(hi));
   }
 }
 
@@ -368,12 +400,15 @@ __global__ void k_make_arena(const DevType* __restrict__ types, const DevModule*
 // C_s = F_rc,s^T X_b(s) = Frc_hat_s^T (D^{1/2} X_b(s)), read from the gathered
 // operand (high + low parts) and the FP32 copy of Frc_hat.  One block per
 // subdomain and 128 directions; K is staged 32 rows at a time.
+template <int FMT>
 __global__ void __launch_bounds__(256) k_frct_lowp(const DevType* __restrict__ types,
                                                    const DevModule* __restrict__ mods,
                                                    const DevSub* __restrict__ subs, const float* __restrict__ fmem,
-                                                   const int64_t* __restrict__ bpad, const float* __restrict__ xb_hi,
-                                                   const float* __restrict__ xb_lo, int64_t nbp, int m,
-                                                   double* __restrict__ Cb, int64_t nct) {
+                                                   const int64_t* __restrict__ bpad,
+                                                   const typename TcFmt<FMT>::T* __restrict__ xb_hi,
+                                                   const typename TcFmt<FMT>::T* __restrict__ xb_lo, int64_t nbp,
+                                                   int m, double* __restrict__ Cb, int64_t nct) {
+  using F = TcFmt<FMT>;
   __shared__ float fs[32][24];
   __shared__ float xs[32][129];
   const DevSub S = subs[blockIdx.y];
@@ -383,8 +418,8 @@ __global__ void __launch_bounds__(256) k_frct_lowp(const DevType* __restrict__ t
   const float* Fr = fmem + mods[S.module].Frc;      // [nb x nc] row-major
   const int j0 = blockIdx.x * 128;
   const int tid = threadIdx.x, jj = tid & 127, cg = tid >> 7;
-  const float* xh = xb_hi + bpad[blockIdx.y];
-  const float* xl = xb_lo ? xb_lo + bpad[blockIdx.y] : nullptr;
+  const typename F::T* xh = xb_hi + bpad[blockIdx.y];
+  const typename F::T* xl = xb_lo ? xb_lo + bpad[blockIdx.y] : nullptr;
   float acc[12];
 #pragma unroll
   for (int q = 0; q < 12; ++q) acc[q] = 0.f;
@@ -397,8 +432,8 @@ __global__ void __launch_bounds__(256) k_frct_lowp(const DevType* __restrict__ t
       const int j2 = e >> 5, kk = e & 31, k = k0 + kk, j = j0 + j2;
       float v = 0.0f;
       if (j < m && k < nb) {
-        v = xh[(int64_t)j * nbp + k];
-        if (xl) v += xl[(int64_t)j * nbp + k];
+        v = F::value(xh[(int64_t)j * nbp + k]);
+        if (xl) v += F::value(xl[(int64_t)j * nbp + k]);
       }
       xs[kk][j2] = v;
     }
@@ -422,20 +457,22 @@ __global__ void __launch_bounds__(256) k_frct_lowp(const DevType* __restrict__ t
 }
 
 // The K-extension of the operand: V_s (the coarse correction at the
-// subdomain's corners) in the 32 slots after its b range, zero past n_c.
-template <int PASSES>
+// subdomain's corners) in the chunk after its b range, zero past n_c.
+template <int FMT, int PASSES>
 __global__ void k_put_v(const DevType* __restrict__ types, const DevSub* __restrict__ subs,
                         const int64_t* __restrict__ bpad, const int* __restrict__ cg, const double* __restrict__ V,
-                        int np, int m, float* __restrict__ xb_hi, float* __restrict__ xb_lo, int64_t nbp) {
+                        int np, int m, typename TcFmt<FMT>::T* __restrict__ xb_hi,
+                        typename TcFmt<FMT>::T* __restrict__ xb_lo, int64_t nbp) {
+  using F = TcFmt<FMT>;
   const DevSub S = subs[blockIdx.y];
   const DevType T = types[S.type];
   const int c = threadIdx.x, j = blockIdx.x * blockDim.y + threadIdx.y;
   if (j >= m || T.n_c == 0) return;
   const float v = c < T.n_c ? static_cast<float>(V[cg[S.c_off + c] + (int64_t)j * np]) : 0.0f;
-  const int64_t o = (int64_t)j * nbp + bpad[blockIdx.y] + k_extent(T.n_b, 0, 0) + c;
-  const float hi = to_tf32(v);
+  const int64_t o = (int64_t)j * nbp + bpad[blockIdx.y] + k_extent(T.n_b, 0, 0, F::KC) + c;
+  const typename F::T hi = F::round(v);
   xb_hi[o] = hi;
-  if (PASSES == 3) xb_lo[o] = to_tf32(v - hi);
+  if (PASSES == 3) xb_lo[o] = F::round(v - F::value(hi));
 }
 
 // Shat = D_S^{-1/2} S_bb D_S^{-1/2} (FP32) per module, for the preconditioner
@@ -507,13 +544,32 @@ size_t tc_apply_smem_bytes(int passes) {
   return 1024 + (passes == 3 ? TC_STAGES3 : TC_STAGES1) * stage;
 }
 
+namespace {
+
+// Format and pass count of the context's precision option.
+int tc_format(const Ctx& c) { return (c.opt.precision == FETI_BF16 || c.opt.precision == FETI_BF16X3) ? 1 : 0; }
+bool tc_split(const Ctx& c) { return c.opt.precision == FETI_TF32X3 || c.opt.precision == FETI_BF16X3; }
+
+}  // namespace
+
+int tc_chunk(int precision) { return (precision == FETI_BF16 || precision == FETI_BF16X3) ? 64 : 32; }
+size_t tc_elem_bytes(int precision) { return (precision == FETI_BF16 || precision == FETI_BF16X3) ? 2 : 4; }
+int tc_k_extent(int nb, int nc, int aug, int kc) { return k_extent(nb, nc, aug, kc); }
+
 cudaError_t tc_prepare(const Ctx& c, cudaStream_t st) {
   k_make_lowp<<<dim3(64, c.n_mod), 256, 0, st>>>(c.d_types, c.d_mods, c.d_modmem, c.d_fmem);
   note_launches(1);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
-  k_make_arena<<<dim3(64, c.n_mod), 256, 0, st>>>(c.d_types, c.d_mods, c.d_modmem, c.d_frow, c.fa_pitch, c.tc_aug,
-                                                 c.d_fa_hi, c.opt.precision == FETI_TF32X3 ? c.d_fa_lo : nullptr);
+  const bool split = tc_split(c);
+  if (tc_format(c) == 0)
+    k_make_arena<0><<<dim3(64, c.n_mod), 256, 0, st>>>(c.d_types, c.d_mods, c.d_modmem, c.d_frow, c.fa_pitch,
+                                                      c.tc_aug, static_cast<float*>(c.d_fa_hi),
+                                                      split ? static_cast<float*>(c.d_fa_lo) : nullptr);
+  else
+    k_make_arena<1><<<dim3(64, c.n_mod), 256, 0, st>>>(c.d_types, c.d_mods, c.d_modmem, c.d_frow, c.fa_pitch,
+                                                      c.tc_aug, static_cast<__nv_bfloat16*>(c.d_fa_hi),
+                                                      split ? static_cast<__nv_bfloat16*>(c.d_fa_lo) : nullptr);
   note_launches(1);
   e = cudaGetLastError();
   if (e != cudaSuccess) return e;
@@ -537,62 +593,80 @@ PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
   return fn;
 }
 
-// Row-major FP32 matrix [rows x pitch] read in boxes of 32 x box_rows with the
-// 128-byte swizzle; outside the matrix the box is filled with zeros.
-bool make_map(CUtensorMap* map, const float* base, int64_t pitch, int64_t rows, uint32_t box_rows) {
+// Row-major matrix [rows x pitch] of the operand format read in boxes of one
+// 128-byte row segment x box_rows with the 128-byte swizzle; outside the
+// matrix the box is filled with zeros.
+template <int FMT>
+bool make_map(CUtensorMap* map, const void* base, int64_t pitch, int64_t rows, uint32_t box_rows) {
   PFN_cuTensorMapEncodeTiled_v12000 fn = encode_fn();
   if (!fn) return false;
+  const size_t eb = FMT == 0 ? 4 : 2;
   const cuuint64_t dims[2] = {(cuuint64_t)pitch, (cuuint64_t)rows};
-  const cuuint64_t strides[1] = {(cuuint64_t)pitch * sizeof(float)};
-  const cuuint32_t box[2] = {(cuuint32_t)TC_KC, box_rows};
+  const cuuint64_t strides[1] = {(cuuint64_t)pitch * eb};
+  const cuuint32_t box[2] = {(cuuint32_t)TcFmt<FMT>::KC, box_rows};
   const cuuint32_t estr[2] = {1, 1};
-  return fn(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<float*>(base), dims, strides, box, estr,
-            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
-            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+  return fn(map, FMT == 0 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2,
+            const_cast<void*>(base), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+            CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) ==
+         CUDA_SUCCESS;
 }
 
-template <int PASSES, int STAGES>
+template <int FMT, int PASSES, int STAGES>
 cudaError_t launch_tc(const Ctx& c, int m, float* Yb, cudaStream_t st) {
   static bool attr_set = false;
   const size_t smem = tc_apply_smem_bytes(PASSES);
   if (!attr_set) {
-    cudaError_t e = cudaFuncSetAttribute(k_tc_apply<PASSES, STAGES>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)smem);
+    cudaError_t e = cudaFuncSetAttribute(k_tc_apply<FMT, PASSES, STAGES>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     attr_set = true;
   }
   CUtensorMap ta, tal, tb, tbl;
-  const float* alo = PASSES == 3 ? c.d_fa_lo : c.d_fa_hi;
-  const float* blo = PASSES == 3 ? c.d_xb_lo : c.d_xb_hi;
-  if (!make_map(&ta, c.d_fa_hi, c.fa_pitch, c.fa_rows, TC_M) || !make_map(&tal, alo, c.fa_pitch, c.fa_rows, TC_M) ||
-      !make_map(&tb, c.d_xb_hi, c.nbp_total, m, TC_NMAX) || !make_map(&tbl, blo, c.nbp_total, m, TC_NMAX))
+  const void* alo = PASSES == 3 ? c.d_fa_lo : c.d_fa_hi;
+  const void* blo = PASSES == 3 ? c.d_xb_lo : c.d_xb_hi;
+  if (!make_map<FMT>(&ta, c.d_fa_hi, c.fa_pitch, c.fa_rows, TC_M) ||
+      !make_map<FMT>(&tal, alo, c.fa_pitch, c.fa_rows, TC_M) ||
+      !make_map<FMT>(&tb, c.d_xb_hi, c.nbp_total, m, TC_NMAX) || !make_map<FMT>(&tbl, blo, c.nbp_total, m, TC_NMAX))
     return cudaErrorInvalidValue;
   const int n_cb = (m + TC_NMAX - 1) / TC_NMAX;
   const int n_rb = (c.max_nb + TC_M - 1) / TC_M;
   dim3 grid(n_cb * n_rb, c.hp.n_sub);
-  k_tc_apply<PASSES, STAGES><<<grid, TC_THREADS, smem, st>>>(ta, tal, tb, tbl, c.d_types, c.d_subs, c.d_frow,
-                                                             c.d_bpad, c.d_sqrtDF, Yb, c.hp.n_b_total, m, n_cb,
-                                                             c.tc_aug, c.d_status);
+  k_tc_apply<FMT, PASSES, STAGES><<<grid, TC_THREADS, smem, st>>>(ta, tal, tb, tbl, c.d_types, c.d_subs, c.d_frow,
+                                                                  c.d_bpad, c.d_sqrtDF, Yb, c.hp.n_b_total, m, n_cb,
+                                                                  c.tc_aug, c.d_status);
   note_launches(1);
   return cudaGetLastError();
 }
 
+template <int FMT, int PASSES>
+void launch_gather(const Ctx& c, const double* X, int64_t ldx, int m, cudaStream_t st) {
+  using T = typename TcFmt<FMT>::T;
+  const int max_nbp = k_extent(c.max_nb, 0, 0, TcFmt<FMT>::KC);
+  dim3 g((max_nbp + 127) / 128, c.hp.n_sub, (m + TC_GJ - 1) / TC_GJ);
+  k_gather_tc<FMT, PASSES><<<g, 128, 0, st>>>(c.d_types, c.d_subs, c.d_bpad, X, ldx, m, c.d_b2l_off, c.d_b2l_lam,
+                                              c.d_b2l_sign, c.d_sqrtDF, static_cast<T*>(c.d_xb_hi),
+                                              PASSES == 3 ? static_cast<T*>(c.d_xb_lo) : nullptr, c.nbp_total);
+}
+
+template <int FMT, int PASSES>
+void launch_put_v(const Ctx& c, const double* V, int m, cudaStream_t st) {
+  using T = typename TcFmt<FMT>::T;
+  dim3 g((m + 7) / 8, c.hp.n_sub);
+  k_put_v<FMT, PASSES><<<g, dim3(TcFmt<FMT>::KC, 8), 0, st>>>(
+      c.d_types, c.d_subs, c.d_bpad, c.d_c_glob, V, c.hp.n_primal, m, static_cast<T*>(c.d_xb_hi),
+      PASSES == 3 ? static_cast<T*>(c.d_xb_lo) : nullptr, c.nbp_total);
+}
+
 }  // namespace
 
-int tc_k_extent(int nb, int nc, int aug) { return k_extent(nb, nc, aug); }
-
-// xb = TF32 parts of D^{1/2} B^T X in the padded operand layout.
+// xb = parts of D^{1/2} B^T X in the operand format and padded layout.
 cudaError_t tc_gather(const Ctx& c, const double* X, int64_t ldx, int m, cudaStream_t st) {
   if (m <= 0) return cudaSuccess;
   if (m > c.xb_cap) return cudaErrorInvalidValue;
-  const int max_nbp = k_extent(c.max_nb, 0, 0);
-  dim3 g((max_nbp + 127) / 128, c.hp.n_sub, (m + TC_GJ - 1) / TC_GJ);
-  if (c.opt.precision == FETI_TF32X3)
-    k_gather_tc<3><<<g, 128, 0, st>>>(c.d_types, c.d_subs, c.d_bpad, X, ldx, m, c.d_b2l_off, c.d_b2l_lam,
-                                      c.d_b2l_sign, c.d_sqrtDF, c.d_xb_hi, c.d_xb_lo, c.nbp_total);
-  else
-    k_gather_tc<1><<<g, 128, 0, st>>>(c.d_types, c.d_subs, c.d_bpad, X, ldx, m, c.d_b2l_off, c.d_b2l_lam,
-                                      c.d_b2l_sign, c.d_sqrtDF, c.d_xb_hi, nullptr, c.nbp_total);
+  const int f = tc_format(c);
+  const bool split = tc_split(c);
+  if (f == 0) split ? launch_gather<0, 3>(c, X, ldx, m, st) : launch_gather<0, 1>(c, X, ldx, m, st);
+  else split ? launch_gather<1, 3>(c, X, ldx, m, st) : launch_gather<1, 1>(c, X, ldx, m, st);
   note_launches(1);
   return cudaGetLastError();
 }
@@ -601,9 +675,18 @@ cudaError_t tc_gather(const Ctx& c, const double* X, int64_t ldx, int m, cudaStr
 // corner assembly Vraw = sum over the copies of each primal DOF.
 cudaError_t tc_corner_reduce(const Ctx& c, int m, double* Vraw, cudaStream_t st) {
   if (c.max_nc > 24) return cudaErrorInvalidValue;
-  k_frct_lowp<<<dim3((m + 127) / 128, c.hp.n_sub), 256, 0, st>>>(
-      c.d_types, c.d_mods, c.d_subs, c.d_fmem, c.d_bpad, c.d_xb_hi,
-      c.opt.precision == FETI_TF32X3 ? c.d_xb_lo : nullptr, c.nbp_total, m, c.d_Cb, c.n_c_total);
+  dim3 g((m + 127) / 128, c.hp.n_sub);
+  const bool split = tc_split(c);
+  if (tc_format(c) == 0)
+    k_frct_lowp<0><<<g, 256, 0, st>>>(c.d_types, c.d_mods, c.d_subs, c.d_fmem, c.d_bpad,
+                                      static_cast<const float*>(c.d_xb_hi),
+                                      split ? static_cast<const float*>(c.d_xb_lo) : nullptr, c.nbp_total, m, c.d_Cb,
+                                      c.n_c_total);
+  else
+    k_frct_lowp<1><<<g, 256, 0, st>>>(c.d_types, c.d_mods, c.d_subs, c.d_fmem, c.d_bpad,
+                                      static_cast<const __nv_bfloat16*>(c.d_xb_hi),
+                                      split ? static_cast<const __nv_bfloat16*>(c.d_xb_lo) : nullptr, c.nbp_total, m,
+                                      c.d_Cb, c.n_c_total);
   note_launches(1);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
@@ -613,13 +696,10 @@ cudaError_t tc_corner_reduce(const Ctx& c, int m, double* Vraw, cudaStream_t st)
 // The coarse correction V into the K-extension of the operand.
 cudaError_t tc_put_v(const Ctx& c, const double* V, int m, cudaStream_t st) {
   if (!c.tc_aug) return cudaSuccess;
-  dim3 g((m + 7) / 8, c.hp.n_sub);
-  if (c.opt.precision == FETI_TF32X3)
-    k_put_v<3><<<g, dim3(32, 8), 0, st>>>(c.d_types, c.d_subs, c.d_bpad, c.d_c_glob, V, c.hp.n_primal, m, c.d_xb_hi,
-                                          c.d_xb_lo, c.nbp_total);
-  else
-    k_put_v<1><<<g, dim3(32, 8), 0, st>>>(c.d_types, c.d_subs, c.d_bpad, c.d_c_glob, V, c.hp.n_primal, m, c.d_xb_hi,
-                                          nullptr, c.nbp_total);
+  const int f = tc_format(c);
+  const bool split = tc_split(c);
+  if (f == 0) split ? launch_put_v<0, 3>(c, V, m, st) : launch_put_v<0, 1>(c, V, m, st);
+  else split ? launch_put_v<1, 3>(c, V, m, st) : launch_put_v<1, 1>(c, V, m, st);
   note_launches(1);
   return cudaGetLastError();
 }
@@ -629,8 +709,12 @@ cudaError_t tc_product(const Ctx& c, int m, float* Yb, cudaStream_t st) {
   if (m <= 0) return cudaSuccess;
   if (m > c.xb_cap) return cudaErrorInvalidValue;
   prof_begin(st, c.fl_tc * m, 1);
-  const cudaError_t e =
-      c.opt.precision == FETI_TF32X3 ? launch_tc<3, TC_STAGES3>(c, m, Yb, st) : launch_tc<1, TC_STAGES1>(c, m, Yb, st);
+  cudaError_t e;
+  const bool split = tc_split(c);
+  if (tc_format(c) == 0)
+    e = split ? launch_tc<0, 3, TC_STAGES3>(c, m, Yb, st) : launch_tc<0, 1, TC_STAGES1>(c, m, Yb, st);
+  else
+    e = split ? launch_tc<1, 3, TC_STAGES3>(c, m, Yb, st) : launch_tc<1, 1, TC_STAGES1>(c, m, Yb, st);
   prof_end(st);
   return e;
 }

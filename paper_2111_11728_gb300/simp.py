@@ -109,10 +109,8 @@ def _fd_check(problem, n_check, rel_h, tol, seed=7):
     refactorizes only the modules that changed."""
     import numpy as np
 
-    from . import FETI_RRS
-
     def comp(rho_np):
-        s = Solver(FETI_FETIDP, FETI_SCALING_K, FETI_RRS, tol=tol, max_iter=2000, dedup=True,
+        s = Solver(FETI_FETIDP, FETI_SCALING_K, FETI_PCG, tol=tol, max_iter=5000, dedup=True,
                    stream=torch.cuda.current_stream().cuda_stream)
         pr = problem
         old = pr.rho

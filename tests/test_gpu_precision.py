@@ -6,6 +6,9 @@ iterative refinement on the dual residual.
   difference of F X within the TF32 rounding of the scaled blocks (<= 3e-3).
 * The three-pass split-TF32 operator (hi*hi + hi*lo + lo*hi) is FP32-class:
   within 2e-5 of the FP64 operator and at least 20x closer than one pass.
+* BF16 (kind::f16 with BF16 inputs): one pass within the BF16 rounding of the
+  scaled blocks (<= 1e-2), the split product within 2e-4 and at least 20x
+  closer than one pass; the refined split-BF16 solve reaches the FP64 bar.
 * At moderate stiffness contrast the refined solution reaches the FP64 bar
   (<= 1e-8 relative displacement error against a direct solve of Eq. 2).
 """
@@ -89,3 +92,32 @@ def test_refined_tf32_solve_reaches_fp64_accuracy(method):
     assert rel(u, ud) <= 1e-8
     u64, st64, _, _ = solve_u(p, method=method, tol=1e-10)
     assert rel(u, u64) <= 1e-8
+
+
+@pytest.mark.parametrize("m", [1, 40, 300])
+def test_bf16_operators(m):
+    torch = torch_cuda()
+    p = moderate(tiles=5, elems=12)
+    solvers = [make_solver(p), make_solver(p, precision=fg.FETI_BF16), make_solver(p, precision=fg.FETI_BF16X3)]
+    for s in solvers:
+        fg.feti_factorize(s.ctx)
+    n = solvers[0].query(fg.FETI_Q_N_LAMBDA)
+    X = torch.from_numpy(np.random.default_rng(200 + m).standard_normal((m, n))).cuda()
+    Ys = []
+    for s in solvers:
+        Y = torch.zeros_like(X)
+        fg.feti_apply_dual(s.ctx, X, n, m, Y, n)
+        Ys.append(Y.cpu().numpy())
+    d1, d3 = rel(Ys[1], Ys[0]), rel(Ys[2], Ys[0])
+    assert 0.0 < d1 <= 1e-2
+    assert 0.0 < d3 <= 2e-4
+    assert d3 * 20 <= d1
+
+
+@pytest.mark.parametrize("method", ["fetidp", "tfeti"])
+def test_refined_split_bf16_solve_reaches_fp64_accuracy(method):
+    p = moderate() if method == "fetidp" else workloads.config1()
+    ud = direct_solve(p)
+    u, st, c, _ = solve_u(p, method=method, tol=1e-10, precision=fg.FETI_BF16X3, max_iter=600)
+    assert st.converged and st.refinements >= 1
+    assert rel(u, ud) <= 1e-8
