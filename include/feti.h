@@ -157,9 +157,13 @@ feti_status feti_factorize(feti_ctx* ctx);
 
 /* Run the Krylov solver (Algorithm 1 or its PCG/FO special cases) on the
  * dual problem.  lambda_inout: NULL, or a DEVICE array [n_lambda] used as the
- * initial multiplier (warm start) and overwritten with the result.  stats may
- * be NULL.  Returns FETI_ENOTCONV if max_iter was reached (results still
- * valid) and FETI_EBREAKDOWN if no direction survived the rank test. */
+ * initial multiplier (warm start) and overwritten with the result.  The
+ * relative stopping test sqrt(r^T z) <= tol * eps0 takes eps0 at the method's
+ * own initial multiplier (0 for FETI-DP, G^T (G G^T)^{-1} e for TFETI) also
+ * when a warm start is given, so a good initial guess shortens the solve
+ * (single problems; a batch measures each problem from its own start).
+ * stats may be NULL.  Returns FETI_ENOTCONV if max_iter was reached (results
+ * still valid) and FETI_EBREAKDOWN if no direction survived the rank test. */
 feti_status feti_solve_dual(feti_ctx* ctx, double* lambda_inout, feti_stats* stats);
 
 /* Recover the global displacement from the last solve: FETI-DP from the

@@ -27,7 +27,7 @@ def main(argv=None):
     ap.add_argument("--dim", type=int, default=3, choices=[2, 3])
     ap.add_argument("--tiles", type=int, default=8)
     ap.add_argument("--elems", type=int, default=None)
-    ap.add_argument("--precision", default="tf32x3", choices=["fp64", "tf32", "tf32x3"])
+    ap.add_argument("--precision", default="tf32x3", choices=["fp64", "tf32", "tf32x3", "bf16", "bf16x3"])
     ap.add_argument("--method", default="fetidp", choices=["fetidp", "tfeti"])
     ap.add_argument("--m", type=int, default=512)
     ap.add_argument("--reps", type=int, default=5)
@@ -43,7 +43,8 @@ def main(argv=None):
         p = workloads.config4(tiles=a.tiles, elems=a.elems or 8)
     else:
         p = workloads.config2(tiles=a.tiles, elems=a.elems or 32)
-    prec = {"fp64": fg.FETI_FP64, "tf32": fg.FETI_TF32, "tf32x3": fg.FETI_TF32X3}[a.precision]
+    prec = {"fp64": fg.FETI_FP64, "tf32": fg.FETI_TF32, "tf32x3": fg.FETI_TF32X3, "bf16": fg.FETI_BF16,
+            "bf16x3": fg.FETI_BF16X3}[a.precision]
     method = {"fetidp": fg.FETI_FETIDP, "tfeti": fg.FETI_TFETI}[a.method]
     stream = torch.cuda.current_stream()
     s = fg.Solver(method, fg.FETI_SCALING_K, fg.FETI_RRS, stream=stream.cuda_stream, precision=prec)

@@ -12,6 +12,7 @@
 // from the multiplier side: deterministic, no atomics.
 #include <algorithm>
 
+#include "fpconv.cuh"
 #include "kernels.h"
 
 namespace feti {
@@ -190,12 +191,41 @@ cudaError_t scatter_b_to_lam(const Ctx& c, const double* Yb, int m, double* Y, i
   return cudaGetLastError();
 }
 
+namespace {
+
+// Y[l, j] = sum of the signed FP32 interface entries of row l, summed in FP32
+// and widened exactly on the integer pipe (the reduced-precision operator's
+// scatter; FP64 arithmetic here would bind it to the small FP64 unit).
+__global__ void k_scatter32(int64_t nl, int m, const int* __restrict__ b0, const signed char* __restrict__ s0,
+                            const int* __restrict__ b1, const signed char* __restrict__ s1,
+                            const float* __restrict__ Yb, int64_t nbt, double* __restrict__ Y, int64_t ldy) {
+  const int64_t l = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  const int j0 = blockIdx.y * SC_J;
+  if (l >= nl) return;
+  const int jn = min(SC_J, m - j0);
+  const int p0 = b0[l], p1 = b1[l];
+  const bool n0 = s0[l] < 0, n1 = p1 >= 0 && s1[l] < 0;
+#pragma unroll
+  for (int u = 0; u < SC_J; ++u) {
+    if (u >= jn) break;
+    const float* yb = Yb + (int64_t)(j0 + u) * nbt;
+    const float a = yb[p0];
+    float v = n0 ? -a : a;
+    if (p1 >= 0) {
+      const float c = yb[p1];
+      v += n1 ? -c : c;
+    }
+    Y[l + (int64_t)(j0 + u) * ldy] = f32_to_f64(v);
+  }
+}
+
+}  // namespace
+
 // Same, from an FP32 interface-space block (the tensor-core product's output).
 cudaError_t scatter_b_to_lam32(const Ctx& c, const float* Yb, int m, double* Y, int64_t ldy, cudaStream_t st) {
   const int64_t nl = c.hp.n_lam;
   dim3 g((unsigned)((nl + 255) / 256), (m + SC_J - 1) / SC_J);
-  k_scatter<float><<<g, 256, 0, st>>>(nl, m, c.d_lam_b0, c.d_lam_s0, c.d_lam_b1, c.d_lam_s1, Yb, c.hp.n_b_total, Y,
-                                      ldy);
+  k_scatter32<<<g, 256, 0, st>>>(nl, m, c.d_lam_b0, c.d_lam_s0, c.d_lam_b1, c.d_lam_s1, Yb, c.hp.n_b_total, Y, ldy);
   note_launches(1);
   return cudaGetLastError();
 }

@@ -43,9 +43,13 @@ __global__ void __launch_bounds__(RR_THREADS) k_rr_chol(const double* __restrict
   __shared__ double rv[32];
   __shared__ int rp[32];
   __shared__ int s_bp, s_k;
-  __shared__ double s_best;
+  __shared__ double s_best, s_piv, s_rpiv;
   const int tid = threadIdx.x, nt = blockDim.x;
   const int lane = tid & 31, wid = tid >> 5, nw = nt >> 5;
+  // warps that own at least one column (m <= blockDim.x): only they take part
+  // in the pivot reduction -- FP64 work is scarce on this part, so nothing is
+  // computed redundantly by idle threads
+  const int aw = (m + 31) / 32;
 
   for (int64_t e = tid; e < (int64_t)m * m; e += nt) {
     const int a = (int)(e / m), b = (int)(e % m);
@@ -77,35 +81,47 @@ __global__ void __launch_bounds__(RR_THREADS) k_rr_chol(const double* __restrict
     const int pend = min(p0 + RR_PB, m);
     int jn = 0;
     for (int j = p0; j < pend; ++j) {
-      // --- pivot: max d/d0 over the unchosen live columns, ties to the lowest id
-      double bv = -1.0;
-      int bp = 0x7fffffff;
-      for (int t = tid; t < m; t += nt) {
-        if (!alive[t] || chosen[t]) continue;
-        const double ratio = d[t] / d0[t];
-        if (ratio > bv || (ratio == bv && t < bp)) { bv = ratio; bp = t; }
+      // --- pivot: max d/d0 over the unchosen live columns, ties to the lowest
+      // id.  Ratios <= 0 never qualify (the stop test needs > rr_tol >= 0), so
+      // they enter as 0 and the comparison runs on the bit patterns of the
+      // non-negative doubles (integer pipe; same order as the values).
+      if (wid < aw) {
+        long long bv = -1;
+        int bp = 0x7fffffff;
+        for (int t = tid; t < m; t += aw * 32) {
+          if (!alive[t] || chosen[t]) continue;
+          const double ratio = d[t] / d0[t];
+          const long long key = ratio > 0.0 ? __double_as_longlong(ratio) : 0ll;
+          if (key > bv || (key == bv && t < bp)) { bv = key; bp = t; }
+        }
+        for (int o = 16; o > 0; o >>= 1) {
+          const long long ov = __shfl_xor_sync(0xffffffffu, bv, o);
+          const int op = __shfl_xor_sync(0xffffffffu, bp, o);
+          if (ov > bv || (ov == bv && op < bp)) { bv = ov; bp = op; }
+        }
+        if (lane == 0) { rv[wid] = __longlong_as_double(bv < 0 ? 0ll : bv); rp[wid] = bv < 0 ? 0x7fffffff : bp; }
       }
-      for (int o = 16; o > 0; o >>= 1) {
-        const double ov = __shfl_xor_sync(0xffffffffu, bv, o);
-        const int op = __shfl_xor_sync(0xffffffffu, bp, o);
-        if (ov > bv || (ov == bv && op < bp)) { bv = ov; bp = op; }
-      }
-      if (lane == 0) { rv[wid] = bv; rp[wid] = bp; }
       __syncthreads();
       if (tid == 0) {
-        double v = -1.0;
+        long long v = -1;
         int pp = 0x7fffffff;
-        for (int w = 0; w < nw; ++w)
-          if (rv[w] > v || (rv[w] == v && rp[w] < pp)) { v = rv[w]; pp = rp[w]; }
-        s_best = v;
+        for (int w = 0; w < aw; ++w) {
+          const long long kw = rp[w] == 0x7fffffff ? -1 : __double_as_longlong(rv[w]);
+          if (kw > v || (kw == v && rp[w] < pp)) { v = kw; pp = rp[w]; }
+        }
+        s_best = v < 0 ? -1.0 : __longlong_as_double(v);
         s_bp = pp == 0x7fffffff ? -1 : pp;
+        if (s_bp >= 0 && s_best > rr_tol) {
+          s_piv = sqrt(d[s_bp]);
+          s_rpiv = 1.0 / s_piv;
+        }
       }
       __syncthreads();
       if (s_bp < 0 || !(s_best > rr_tol)) { stop = true; break; }
       const int pj = s_bp;
       const int jq = j - p0;
-      const double piv = sqrt(d[pj]);
-      const double rpiv = 1.0 / piv;
+      const double piv = s_piv;
+      const double rpiv = s_rpiv;
       // --- column j of L for every unchosen live column r != pj
       for (int r = tid; r < m; r += nt) {
         if (r == pj || !alive[r] || chosen[r]) continue;
@@ -171,13 +187,15 @@ __global__ void __launch_bounds__(RR_THREADS) k_rr_chol(const double* __restrict
   // per row, lanes over columns, four loads in flight per lane, row q staged
   // in shared memory).  L~(i, q) = Lg[perm[i]][q].
   double* lcol = d;                             // reuse
+  double* rdiag = d0;                           // reuse: 1 / L~(q, q), computed once
+  for (int q = tid; q < k; q += nt) rdiag[q] = 1.0 / Lg[(int64_t)perm[q] * m + q];
   for (int64_t e = tid; e < (int64_t)k * k; e += nt) {
     const int i = (int)(e / k), c = (int)(e % k);
     A[(int64_t)i * m + c] = i == c ? 1.0 : 0.0;
   }
   __syncthreads();
   for (int q = 0; q < k; ++q) {
-    const double rq = 1.0 / Lg[(int64_t)perm[q] * m + q];
+    const double rq = rdiag[q];
     for (int c = tid; c <= q; c += nt) {
       const double v = A[(int64_t)q * m + c] * rq;
       A[(int64_t)q * m + c] = v;

@@ -13,6 +13,7 @@
 
 #include <cstdint>
 
+#include "fpconv.cuh"
 #include "kernels.h"
 
 namespace feti {
@@ -333,29 +334,34 @@ __global__ void k_gather_tc(const DevType* __restrict__ types, const DevSub* __r
   if (k >= nbp_s) return;
   const int j0 = blockIdx.z * TC_GJ;
   const int jn = min(TC_GJ, m - j0);
+  // FP32 arithmetic, conversions on the integer pipe (the product rounds the
+  // operand to TF32 / BF16 anyway; see fpconv.cuh)
   int q0 = 0, q1 = 0;
-  double sd = 0.0;
+  float sd = 0.0f;
   if (k < nb) {
     const int64_t b = S.b_off + k;
     q0 = b2l_off[b];
     q1 = b2l_off[b + 1];
-    sd = sqrtD[b];
+    sd = f64_to_f32_rn(sqrtD[b]);
   }
-  double acc[TC_GJ];
+  float acc[TC_GJ];
 #pragma unroll
-  for (int u = 0; u < TC_GJ; ++u) acc[u] = 0.0;
+  for (int u = 0; u < TC_GJ; ++u) acc[u] = 0.0f;
   for (int q = q0; q < q1; ++q) {
     const double* x = X + b2l_lam[q] + (int64_t)j0 * ldx;
     const bool pos = b2l_sign[q] > 0;
 #pragma unroll
     for (int u = 0; u < TC_GJ; ++u)
-      if (u < jn) acc[u] += pos ? x[(int64_t)u * ldx] : -x[(int64_t)u * ldx];
+      if (u < jn) {
+        const float xv = f64_to_f32_rn(x[(int64_t)u * ldx]);
+        acc[u] += pos ? xv : -xv;
+      }
   }
   const int64_t o = (int64_t)j0 * nbp + bpad[blockIdx.y] + k;
 #pragma unroll
   for (int u = 0; u < TC_GJ; ++u) {
     if (u >= jn) break;
-    const float v = static_cast<float>(acc[u] * sd);
+    const float v = acc[u] * sd;
     const typename F::T hi = F::round(v);
     xb_hi[o + (int64_t)u * nbp] = hi;
     if (PASSES == 3) xb_lo[o + (int64_t)u * nbp] = F::round(v - F::value(hi));

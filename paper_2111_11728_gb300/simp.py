@@ -143,7 +143,13 @@ def _fd_check(problem, n_check, rel_h, tol, seed=7):
         err = abs(fd - g0[e]) / max(abs(g0[e]), 1e-300)
         worst = max(worst, err)
         rows.append({"element": int(e), "grad": float(g0[e]), "fd": float(fd), "rel_err": float(err)})
-    return {"compliance": c0, "elements": rows, "max_rel_err": worst, "rel_h": rel_h, "tol": tol}
+    gmax = max(abs(r["grad"]) for r in rows)
+    abs_err = max(abs(r["fd"] - r["grad"]) for r in rows)
+    big = [r["rel_err"] for r in rows if abs(r["grad"]) >= 1e-2 * gmax]
+    return {"compliance": c0, "elements": rows, "max_rel_err": worst,
+            "max_abs_err_over_max_grad": abs_err / gmax,
+            "max_rel_err_where_grad_ge_1pct_of_max": max(big) if big else None,
+            "rel_h": rel_h, "tol": tol}
 
 
 def main(argv=None):

@@ -57,3 +57,29 @@ def test_oc_loop_decreases_compliance_with_warm_start():
     assert cs[-1] < cs[0]
     assert abs(float(rho.mean()) - 0.4) <= 1e-3
     assert float(rho.min()) >= 1e-3 - 1e-12 and float(rho.max()) <= 1.0
+
+
+def test_warm_start_shortens_the_solve():
+    """The relative stopping test is measured from the method's own initial
+    multiplier, so restarting from the solution needs no iteration and a
+    nearby design needs fewer iterations than a cold start."""
+    import torch
+    from gpu_helpers import make_solver
+    p = workloads.config5(tiles=4, elems=8)
+    rng = np.random.default_rng(3)
+    p.rho = rng.uniform(0.3, 1.0, size=p.rho.size)
+    s = make_solver(p, krylov="pcg", tol=1e-8, dedup=False)
+    fg.feti_factorize(s.ctx)
+    n = s.query(fg.FETI_Q_N_LAMBDA)
+    lam = torch.zeros(n, dtype=torch.float64, device="cuda")
+    _, st_cold = fg.feti_solve_dual(s.ctx, lam)
+    assert st_cold.converged and st_cold.iterations > 5
+    _, st_again = fg.feti_solve_dual(s.ctx, lam)
+    assert st_again.converged and st_again.iterations <= 1
+    rho2 = torch.from_numpy(p.rho * (1.0 + 0.02 * rng.standard_normal(p.rho.size))).cuda()
+    fg.feti_set_density(s.ctx, rho2, True)
+    fg.feti_factorize(s.ctx)
+    _, st_warm = fg.feti_solve_dual(s.ctx, lam)
+    _, st_cold2 = fg.feti_solve_dual(s.ctx, None)
+    assert st_warm.converged and st_cold2.converged
+    assert st_warm.iterations < st_cold2.iterations
