@@ -71,6 +71,20 @@ def workload_config(a, extra=None):
     return cfg
 
 
+# ------------------------------------------------------------------ replicas
+def aggregate_replicas(seconds, work, world, device):
+    """Whole-job throughput of N independent replicas (no collective on the data
+    path): the slowest rank's time and the work summed over ranks."""
+    if world <= 1:
+        return float(seconds), float(work)
+    import torch
+    t = torch.tensor([float(seconds)], dtype=torch.float64, device=device)
+    torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+    w = torch.tensor([float(work)], dtype=torch.float64, device=device)
+    torch.distributed.all_reduce(w)
+    return float(t.item()), float(w.item())
+
+
 # ------------------------------------------------------------------ clocks
 class ClockSampler:
     FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
@@ -168,9 +182,9 @@ def run_forms(p, a, fg, torch, dev, stream, flush, forms, max_iter, m_apply, rep
     rho_d = torch.from_numpy(p.rho).to(dev)
     f_d = torch.from_numpy(p.f).to(dev)
     out, sols = {}, {}
-    for name, prec in forms:
+    for name, prec, repl in forms:
         s = fg.Solver(fg.FETI_FETIDP, fg.FETI_SCALING_K, fg.FETI_RRS, tol=a.tol, max_iter=max_iter,
-                      stream=stream.cuda_stream, precision=prec)
+                      stream=stream.cuda_stream, precision=prec, fp64_residual=repl)
         s.setup(p, rho=rho_d, f=f_d, on_device=True)
         u = torch.empty(p.n_dofs, dtype=torch.float64, device=dev)
         times, st = [], None
@@ -202,7 +216,7 @@ def run_forms(p, a, fg, torch, dev, stream, flush, forms, max_iter, m_apply, rep
     ref = sols["fp64"]
     t64 = out["fp64"]["time_to_solve_ms"]
     a64 = out["fp64"][f"apply_{m_apply}_cols_ms"]
-    for name, _ in forms[1:]:
+    for name, _, _ in forms[1:]:
         if name not in sols:
             continue
         out[name]["rel_diff_vs_fp64"] = float(np.linalg.norm(sols[name] - ref) / np.linalg.norm(ref))
@@ -212,8 +226,13 @@ def run_forms(p, a, fg, torch, dev, stream, flush, forms, max_iter, m_apply, rep
 
 
 def precision_forms(fg):
-    return (("fp64", fg.FETI_FP64), ("tf32x3", fg.FETI_TF32X3), ("tf32", fg.FETI_TF32),
-            ("bf16x3", fg.FETI_BF16X3), ("bf16", fg.FETI_BF16))
+    """(name, precision, FP64 residual replacement); "+r": one inner solve whose
+    residual is recomputed in FP64 every iteration, no restarts."""
+    return (("fp64", fg.FETI_FP64, False),
+            ("tf32x3", fg.FETI_TF32X3, False), ("tf32", fg.FETI_TF32, False),
+            ("bf16x3", fg.FETI_BF16X3, False), ("bf16", fg.FETI_BF16, False),
+            ("tf32x3+r", fg.FETI_TF32X3, True), ("tf32+r", fg.FETI_TF32, True), ("bf16x3+r", fg.FETI_BF16X3, True),
+            ("bf16+r", fg.FETI_BF16, True))
 
 
 def compare_forms(a, fg, torch, dev, stream, flush):
@@ -395,15 +414,7 @@ def run_ours(a, rank, world):
     step_ms = [e0.elapsed_time(e1) for e0, e1 in ev]
     t_steps = sum(step_ms) / 1e3
     # max over ranks
-    if world > 1:
-        t = torch.tensor([t_steps], dtype=torch.float64, device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        t_steps = float(t.item())
-        ap = torch.tensor([applies], dtype=torch.float64, device=dev)
-        torch.distributed.all_reduce(ap)
-        applies_total = float(ap.item())
-    else:
-        applies_total = float(applies)
+    t_steps, applies_total = aggregate_replicas(t_steps, applies, world, dev)
     value = applies_total / t_steps
 
     # solve-only time (factorization excluded), one extra measured step
@@ -451,13 +462,7 @@ def run_ours(a, rank, world):
             e2e_applies += st2.f_applies
             flush.zero_()
         s2.close()
-        if world > 1:
-            t = torch.tensor([e2e_t], dtype=torch.float64, device=dev)
-            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-            e2e_t = float(t.item())
-            ap = torch.tensor([e2e_applies], dtype=torch.float64, device=dev)
-            torch.distributed.all_reduce(ap)
-            e2e_applies = float(ap.item())
+        e2e_t, e2e_applies = aggregate_replicas(e2e_t, e2e_applies, world, dev)
         e2e = {"value": e2e_applies / e2e_t, "unit": "F-applies/s",
                "h2d_bytes_per_step": int(p.rho.nbytes + p.f.nbytes + p.dirichlet.nbytes),
                "d2h_bytes_per_step": int(p.f.nbytes + 8),

@@ -80,7 +80,11 @@ typedef struct {
   double inner_tol;    /* FETI_TF32 / FETI_TF32X3: relative tolerance of each low-precision inner
                           solve; 0 (default) picks 1e-2.
                           Each inner solve is also capped at 30 iterations */
-  int max_refine;      /* FETI_TF32 / FETI_TF32X3: cap on the FP64 refinement steps (30) */
+  int max_refine;      /* reduced precision: cap on the FP64 refinement steps (30) */
+  int fp64_residual;   /* reduced precision, 0 (default) or 1: every inner iteration replaces
+                          the recursive residual by the FP64 residual r_outer - P^T F lambda~
+                          (one FP64 single-column apply per iteration) and the inner solve
+                          aims at the final tolerance, so the Krylov space is not restarted */
 } feti_options;
 
 typedef struct {

@@ -43,7 +43,7 @@ class feti_options(ctypes.Structure):
     _fields_ = [("method", ctypes.c_int), ("scaling", ctypes.c_int), ("krylov", ctypes.c_int),
                 ("precision", ctypes.c_int), ("max_iter", ctypes.c_int), ("dedup_modules", ctypes.c_int),
                 ("tol", ctypes.c_double), ("rr_tol", ctypes.c_double), ("inner_tol", ctypes.c_double),
-                ("max_refine", ctypes.c_int)]
+                ("max_refine", ctypes.c_int), ("fp64_residual", ctypes.c_int)]
 
 
 class feti_problem(ctypes.Structure):
@@ -275,11 +275,12 @@ class Solver:
     """
 
     def __init__(self, method=FETI_FETIDP, scaling=FETI_SCALING_K, krylov=FETI_RRS, tol=1e-6, max_iter=500,
-                 rr_tol=1e-10, dedup=True, stream=None, precision=FETI_FP64, inner_tol=None):
+                 rr_tol=1e-10, dedup=True, stream=None, precision=FETI_FP64, inner_tol=None, fp64_residual=False):
         o = feti_options_default()
         o.method, o.scaling, o.krylov, o.precision = method, scaling, krylov, precision
         if inner_tol is not None:
             o.inner_tol = inner_tol
+        o.fp64_residual = int(bool(fp64_residual))
         o.tol, o.max_iter, o.rr_tol, o.dedup_modules = tol, max_iter, rr_tol, int(dedup)
         self.ctx = feti_create(o, stream)
 

@@ -350,6 +350,7 @@ feti_status feti_options_default(feti_options* opt) {
   opt->rr_tol = 1e-10;
   opt->inner_tol = 0.0;                 // automatic (1e-2)
   opt->max_refine = 30;
+  opt->fp64_residual = 0;
   return FETI_OK;
 }
 
@@ -365,6 +366,7 @@ feti_status feti_create(feti_ctx** out, const feti_options* opt, void* stream) {
     return FETI_EINVAL;
   if (o.precision < FETI_FP64 || o.precision > FETI_BF16X3) return FETI_EINVAL;
   if (o.precision != FETI_FP64 && !(o.inner_tol >= 0.0 && o.inner_tol < 1.0 && o.max_refine > 0)) return FETI_EINVAL;
+  if (o.fp64_residual != 0 && o.fp64_residual != 1) return FETI_EINVAL;
   feti_ctx* ctx = new (std::nothrow) feti_ctx;
   if (!ctx) return FETI_ENOMEM;
   Ctx& c = ctx->c;
@@ -877,7 +879,10 @@ static feti_status read_scalar(Ctx& c, const double* d, double* out) {
 // leaves lambda~ in c.d_lamt and the final residual in c.d_r.  lowp selects
 // the tensor-core local products and the FP32 preconditioner blocks.
 // eps_ref > 0 replaces the initial residual norm in the relative stopping test.
-static feti_status krylov_core(Ctx& c, double tol, int max_iter, bool lowp, feti_stats& S, double eps_ref = -1.0) {
+// r_base != NULL (reduced precision): after every step the residual is
+// recomputed in FP64 as r_base - P^T F lambda~ instead of updated recursively.
+static feti_status krylov_core(Ctx& c, double tol, int max_iter, bool lowp, feti_stats& S, double eps_ref = -1.0,
+                               const double* r_base = nullptr) {
   const HostProblem& hp = c.hp;
   const int64_t nl = hp.n_lam;
   const bool multi = c.opt.krylov == FETI_RRS;
@@ -938,6 +943,14 @@ static feti_status krylov_core(Ctx& c, double tol, int max_iter, bool lowp, feti
       CU(axpby(nl, -1.0, c.d_z, 1.0, c.d_r, st));
     } else {
       CU(step_update(Wi, Qi, nl, nl, k, c.d_gamma, c.d_lamt, c.d_r, nullptr, st));
+    }
+    if (r_base) {
+      // FP64 residual replacement: r = r_base - P^T F lambda~
+      TRY(apply_dual(c, c.d_lamt, nl, 1, c.d_z, nl));
+      TRY(project(c, c.d_z, nl, 1));
+      CU(cudaMemcpyAsync(c.d_r, r_base, nl * sizeof(double), cudaMemcpyDeviceToDevice, st));
+      CU(axpby(nl, -1.0, c.d_z, 1.0, c.d_r, st));
+      S.f_applies += 1;
     }
     // Z_{i+1}, W_{i+1} = P Z_{i+1}
     CU(precond(multi ? c.d_Wb : nullptr, c.d_z));
@@ -1052,12 +1065,15 @@ static feti_status solve_impl(Ctx& c, double* lambda_inout, feti_stats* stats) {
       feti_stats inner{};
       // each correction is capped (a stalled reduced-precision solve still
       // returns a useful correction; the FP64 outer loop decides convergence)
-      const int cap = std::min(c.opt.max_iter - S.iterations, 30);
+      const bool repl = c.opt.fp64_residual != 0;
+      const int cap = repl ? c.opt.max_iter - S.iterations : std::min(c.opt.max_iter - S.iterations, 30);
       // automatic inner tolerance: 1e-2 (measured best time-to-solve for both
       // reduced-precision products: each restart costs the orthogonalization
-      // history, so long inner solves lose more than extra restarts)
-      const double itol = c.opt.inner_tol > 0.0 ? c.opt.inner_tol : 1e-2;
-      feti_status s2 = krylov_core(c, itol, cap, true, inner);
+      // history, so long inner solves lose more than extra restarts).  With the
+      // FP64 residual the inner solve aims straight at the final tolerance.
+      double itol = c.opt.inner_tol > 0.0 ? c.opt.inner_tol : 1e-2;
+      if (repl) itol = std::min(0.5, c.opt.tol * eps0 / std::max(eps, 1e-300));
+      feti_status s2 = krylov_core(c, itol, cap, true, inner, -1.0, repl ? c.d_rout : nullptr);
       S.iterations += inner.iterations;
       S.f_applies += inner.f_applies;
       S.last_rank = inner.last_rank;

@@ -121,3 +121,13 @@ def test_refined_split_bf16_solve_reaches_fp64_accuracy(method):
     u, st, c, _ = solve_u(p, method=method, tol=1e-10, precision=fg.FETI_BF16X3, max_iter=600)
     assert st.converged and st.refinements >= 1
     assert rel(u, ud) <= 1e-8
+
+
+@pytest.mark.parametrize("prec", ["tf32", "tf32x3", "bf16x3"])
+def test_fp64_residual_replacement_reaches_fp64_accuracy(prec):
+    p = moderate()
+    ud = direct_solve(p)
+    pr = {"tf32": fg.FETI_TF32, "tf32x3": fg.FETI_TF32X3, "bf16x3": fg.FETI_BF16X3}[prec]
+    u, st, c, _ = solve_u(p, tol=1e-10, precision=pr, fp64_residual=True, max_iter=400)
+    assert st.converged
+    assert rel(u, ud) <= 1e-8
