@@ -226,13 +226,10 @@ def run_forms(p, a, fg, torch, dev, stream, flush, forms, max_iter, m_apply, rep
 
 
 def precision_forms(fg):
-    """(name, precision, FP64 residual replacement); "+r": one inner solve whose
-    residual is recomputed in FP64 every iteration, no restarts."""
+    """(name, precision, FP64 residual replacement) of the compared forms."""
     return (("fp64", fg.FETI_FP64, False),
             ("tf32x3", fg.FETI_TF32X3, False), ("tf32", fg.FETI_TF32, False),
-            ("bf16x3", fg.FETI_BF16X3, False), ("bf16", fg.FETI_BF16, False),
-            ("tf32x3+r", fg.FETI_TF32X3, True), ("tf32+r", fg.FETI_TF32, True), ("bf16x3+r", fg.FETI_BF16X3, True),
-            ("bf16+r", fg.FETI_BF16, True))
+            ("bf16x3", fg.FETI_BF16X3, False), ("bf16", fg.FETI_BF16, False))
 
 
 def compare_forms(a, fg, torch, dev, stream, flush):

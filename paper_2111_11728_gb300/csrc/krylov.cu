@@ -182,53 +182,65 @@ __global__ void __launch_bounds__(RR_THREADS) k_rr_chol(const double* __restrict
       if (!chosen[t]) perm[pos++] = t;
   }
   __syncthreads();
-  // --- X = L~^{-1} (k x k, row-major, ld m) into A, right-looking: row q of X
-  // is final once divided by L~(q,q); it then updates every later row (warp
-  // per row, lanes over columns, four loads in flight per lane, row q staged
-  // in shared memory).  L~(i, q) = Lg[perm[i]][q].
-  double* lcol = d;                             // reuse
-  double* rdiag = d0;                           // reuse: 1 / L~(q, q), computed once
-  for (int q = tid; q < k; q += nt) rdiag[q] = 1.0 / Lg[(int64_t)perm[q] * m + q];
-  for (int64_t e = tid; e < (int64_t)k * k; e += nt) {
-    const int i = (int)(e / k), c = (int)(e % k);
-    A[(int64_t)i * m + c] = i == c ? 1.0 : 0.0;
+  // --- reciprocals of the pivots (diagonal of L~) for the inverse kernel
+  double* rdiag_g = work + 2 * (int64_t)m * m;
+  for (int q = tid; q < k; q += nt) rdiag_g[q] = 1.0 / Lg[(int64_t)perm[q] * m + q];
+  for (int t = tid; t < m; t += nt) perm_out[t] = perm[t];
+  if (tid == 0) *d_k = k;
+}
+
+// U = L~^{-T} (upper triangular, column-major, ld m): T[jj + i*m] = X[i][jj]
+// with X = L~^{-1}, L~(i, q) = Lg[perm[i]][q].  Column blocks of X are
+// independent: CTA b owns columns [16b, 16b + 16) and runs the right-looking
+// elimination on them (row q of X is final once scaled by 1 / L~(q, q); it then
+// updates every later row), with column q + 1 of L~ prefetched into a shared
+// double buffer while step q computes.  Same fused multiply-adds in the same
+// order as a single-CTA right-looking inverse.
+constexpr int RI_CB = 16;
+constexpr int RI_THREADS = 256;
+
+__global__ void __launch_bounds__(RI_THREADS) k_rr_inverse(const double* __restrict__ work, int m,
+                                                           const int* __restrict__ perm_g,
+                                                           const int* __restrict__ d_k, double* __restrict__ T) {
+  extern __shared__ double ri_sh[];
+  const int k = *d_k;
+  const int c0 = blockIdx.x * RI_CB;
+  if (c0 >= k) return;                           // block-uniform
+  const double* Lg = work + (int64_t)m * m;
+  const double* rdiag = work + 2 * (int64_t)m * m;
+  const int rows = k - c0;
+  double* xs = ri_sh;                            // [rows x RI_CB]: X[c0 + r][c0 + cc]
+  double* lbuf = ri_sh + (int64_t)m * RI_CB;     // [2 x m]: column q of L~ over rows
+  const int tid = threadIdx.x;
+  for (int e = tid; e < rows * RI_CB; e += RI_THREADS) {
+    const int r = e / RI_CB, cc = e % RI_CB;
+    xs[e] = r == cc ? 1.0 : 0.0;
   }
+  for (int i = c0 + 1 + tid; i < k; i += RI_THREADS) lbuf[i] = Lg[(int64_t)perm_g[i] * m + c0];
   __syncthreads();
-  for (int q = 0; q < k; ++q) {
-    const double rq = rdiag[q];
-    for (int c = tid; c <= q; c += nt) {
-      const double v = A[(int64_t)q * m + c] * rq;
-      A[(int64_t)q * m + c] = v;
-      lcol[c] = v;
-    }
+  for (int q = c0; q < k; ++q) {
+    const int cur = (q - c0) & 1;
+    const double* lq = lbuf + cur * m;
+    double* lnext = lbuf + (cur ^ 1) * m;
+    if (tid < RI_CB && c0 + tid <= q) xs[(q - c0) * RI_CB + tid] *= rdiag[q];
+    for (int i = q + 2 + tid; i < k; i += RI_THREADS) lnext[i] = Lg[(int64_t)perm_g[i] * m + q + 1];
     __syncthreads();
-    for (int i = q + 1 + wid; i < k; i += nw) {
-      const double li = Lg[(int64_t)perm[i] * m + q];
-      double* row = A + (int64_t)i * m;
-      for (int c0 = 0; c0 <= q; c0 += 128) {
-        double v[4];
-#pragma unroll
-        for (int u = 0; u < 4; ++u) {
-          const int cc = c0 + u * 32 + lane;
-          v[u] = cc <= q ? row[cc] : 0.0;
-        }
-#pragma unroll
-        for (int u = 0; u < 4; ++u) {
-          const int cc = c0 + u * 32 + lane;
-          if (cc <= q) row[cc] = fma(-li, lcol[cc], v[u]);
-        }
+    const double* xq = xs + (q - c0) * RI_CB;
+    for (int e = tid; e < (k - q - 1) * RI_CB; e += RI_THREADS) {
+      const int i = q + 1 + e / RI_CB, cc = e % RI_CB;
+      if (c0 + cc <= q) {
+        double* xi = xs + (i - c0) * RI_CB + cc;
+        *xi = fma(-lq[i], xq[cc], *xi);
       }
     }
     __syncthreads();
   }
-  // --- U = L~^{-T}: U[jj + i*m] = Linv[i][jj] (upper triangular, column-major)
-  // and the pivot order; W N^T [L~^{-T}; 0] = W[:, perm[0..k)] U ------------
-  for (int64_t e = tid; e < (int64_t)k * k; e += nt) {
-    const int i = (int)(e / k), jj = (int)(e % k);
-    T[jj + (int64_t)i * m] = jj <= i ? A[(int64_t)i * m + jj] : 0.0;
+  // T[jj + i*m] for the block's columns jj, all rows i < k
+  const int nc = min(RI_CB, k - c0);
+  for (int e = tid; e < k * RI_CB; e += RI_THREADS) {
+    const int i = e / RI_CB, cc = e % RI_CB, jj = c0 + cc;
+    if (cc < nc) T[jj + (int64_t)i * m] = (i >= c0 && jj <= i) ? xs[(i - c0) * RI_CB + cc] : 0.0;
   }
-  for (int t = tid; t < m; t += nt) perm_out[t] = perm[t];
-  if (tid == 0) *d_k = k;
 }
 
 // out[j] = W[:, j] . r  (one block per column, fixed-order reduction)
@@ -321,6 +333,18 @@ cudaError_t rr_cholesky(const double* Delta, int m, int ld, double rr_tol, doubl
     attr_set = true;
   }
   k_rr_chol<<<1, RR_THREADS, (size_t)RR_PB * m * sizeof(double), st>>>(Delta, m, ld, rr_tol, work, T, d_k, d_perm);
+  note_launches(1);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  static bool inv_attr = false;
+  const size_t ismem = (size_t)(RI_CB + 2) * 1024 * sizeof(double);
+  if (!inv_attr) {
+    e = cudaFuncSetAttribute(k_rr_inverse, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ismem);
+    if (e != cudaSuccess) return e;
+    inv_attr = true;
+  }
+  k_rr_inverse<<<(m + RI_CB - 1) / RI_CB, RI_THREADS, (size_t)(RI_CB + 2) * m * sizeof(double), st>>>(work, m, d_perm,
+                                                                                                     d_k, T);
   note_launches(1);
   return cudaGetLastError();
 }
