@@ -69,6 +69,12 @@ void free_all(Ctx& c) {
   c.blk_cap = 0;
   c.kr_cap = 0;
   c.split_cap = 0;
+  c.xb_cap = 0;
+  if (c.d_tiles) cudaFree(c.d_tiles);
+  c.d_tiles = nullptr;
+  c.tiles_cap = 0;
+  c.n_tiles = 0;
+  c.tiles_ncb = 0;
 }
 
 inline int64_t align32(int64_t x) { return (x + 31) / 32 * 32; }
@@ -272,6 +278,7 @@ feti_status apply_dual_lowp(Ctx& c, const double* X, int64_t ldx, int m, double*
     CU(coarse_apply(c, c.d_Vraw, c.d_V, m, c.stream));
     CU(tc_put_v(c, c.d_V, m, c.stream));
   }
+  CU(tc_prepare_tiles(c, m));
   CU(tc_product(c, m, c.d_Yb32, c.stream));
   CU(scatter_b_to_lam32(c, c.d_Yb32, m, Y, ldy, c.stream));
   return FETI_OK;

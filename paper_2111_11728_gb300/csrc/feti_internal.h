@@ -229,6 +229,9 @@ struct Ctx {
   float* d_Yb32 = nullptr;       // [m x n_b_total] output of the tensor-core product (FP32)
   int xb_cap = 0;
   int tc_aug = 0;                // FETI-DP corner coupling appended to the operands (K-extension)
+  int4* d_tiles = nullptr;       // persistent tensor-core kernel: (subdomain, row tile, column tile)
+  int64_t tiles_cap = 0;
+  int n_tiles = 0, tiles_ncb = 0, n_sm = 0;
   double fl_tc = 0.0;            // algorithmic flops of the tensor-core product per column
   double prof_tc_flops = 0.0, prof_tc_ms = 0.0;   // tensor-core products of the last profile
   int64_t prof_tc_launches = 0;

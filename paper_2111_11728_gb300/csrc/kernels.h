@@ -144,6 +144,7 @@ cudaError_t tc_prepare(const Ctx& c, cudaStream_t st);   // Fhat, Shat (FP32) an
 cudaError_t tc_gather(const Ctx& c, const double* X, int64_t ldx, int m, cudaStream_t st);
 cudaError_t tc_corner_reduce(const Ctx& c, int m, double* Vraw, cudaStream_t st);
 cudaError_t tc_put_v(const Ctx& c, const double* V, int m, cudaStream_t st);
+cudaError_t tc_prepare_tiles(Ctx& c, int m);   // work list of the persistent product for m directions
 cudaError_t tc_product(const Ctx& c, int m, float* Yb, cudaStream_t st);
 cudaError_t scatter_b_to_lam32(const Ctx& c, const float* Yb, int m, double* Y, int64_t ldy, cudaStream_t st);
 int tc_k_extent(int nb, int nc, int aug, int kc);

@@ -11,7 +11,9 @@
 #include <cuda_bf16.h>
 #include <cudaTypedefs.h>
 
+#include <algorithm>
 #include <cstdint>
+#include <vector>
 
 #include "fpconv.cuh"
 #include "kernels.h"
@@ -27,6 +29,8 @@ constexpr uint32_t TC_TMEM_COLS = 256;
 constexpr long long TC_SPIN_LIMIT = 1ll << 22;
 constexpr int TC_STAGES1 = 2;       // ring depth, one pass (48 KB per stage; two CTAs per SM)
 constexpr int TC_STAGES3 = 2;       // ring depth, split product (96 KB per stage)
+constexpr int TCP_STAGES1 = 4;      // persistent kernel: one pass, 4 x 48 KB
+constexpr int TCP_STAGES3 = 2;      // persistent kernel: split product, 2 x 96 KB
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
   return static_cast<uint32_t>(__cvta_generic_to_shared(p));
@@ -311,6 +315,212 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_tc_apply(
   if (warp == 0) {
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TC_TMEM_COLS) : "memory");
+  }
+}
+
+// Persistent, warp-specialised form of the same product.  One CTA per SM walks
+// a static list of (subdomain, row tile, column tile) triples (CTA c takes
+// tiles c, c + G, c + 2G, ...).  Warp 0 (one lane) streams A and B chunks of
+// every tile through a STAGES-deep ring (full / empty mbarriers); warp 1 owns
+// the tensor memory (two 256-column FP32 accumulators) and one of its lanes
+// issues the MMAs, alternating accumulators from tile to tile; warps 2-5 read
+// a finished accumulator (tmem_full), scale and store its rows and hand it back
+// (tmem_empty, 128 arrivals) while the next tile accumulates in the other one.
+// Every wait is bounded; on a time-out the CTA records an error code, stops
+// issuing, waits (bounded) for its copies and MMAs in flight, frees its tensor
+// memory and returns.
+constexpr int TCP_THREADS = 192;
+constexpr uint32_t TCP_TMEM_COLS = 512;
+
+template <int FMT, int PASSES, int STAGES>
+__global__ void __launch_bounds__(TCP_THREADS, 1) k_tc_apply_p(
+    const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmAl,
+    const __grid_constant__ CUtensorMap tmB, const __grid_constant__ CUtensorMap tmBl,
+    const int4* __restrict__ tiles, int n_tiles, const DevType* __restrict__ types,
+    const DevSub* __restrict__ subs, const int* __restrict__ frow, const int64_t* __restrict__ bpad,
+    const double* __restrict__ sqrtD, float* __restrict__ Yb, int64_t nbt, int m, int aug,
+    int* __restrict__ status) {
+  constexpr uint32_t A_BYTES = TC_M * 128, B_BYTES = TC_NMAX * 128;
+  constexpr uint32_t STAGE_BYTES = (PASSES == 3 ? 2 : 1) * (A_BYTES + B_BYTES);
+  constexpr int KC = TcFmt<FMT>::KC;
+  extern __shared__ __align__(1024) unsigned char tc_smem_raw[];
+  unsigned char* base = tc_smem_raw + ((1024 - (smem_u32(tc_smem_raw) & 1023)) & 1023);
+  __shared__ __align__(8) uint64_t full_bar[STAGES], empty_bar[STAGES], tfull_bar[2], tempty_bar[2], drain_bar;
+  __shared__ uint32_t tmem_base_sh;
+  __shared__ int fail_sh;
+  __shared__ long long consumed_sh;
+
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int G = gridDim.x;
+  if (warp == 1) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_base_sh)),
+                 "r"(TCP_TMEM_COLS)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  if (tid == 0) {
+    for (int i = 0; i < STAGES; ++i) {
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&full_bar[i])) : "memory");
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&empty_bar[i])) : "memory");
+    }
+    for (int i = 0; i < 2; ++i) {
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&tfull_bar[i])) : "memory");
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 128;" ::"r"(smem_u32(&tempty_bar[i])) : "memory");
+    }
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&drain_bar)) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    fail_sh = 0;
+    consumed_sh = 0;
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const uint32_t tmem = tmem_base_sh;
+
+  long long issued = 0;                         // producer: chunks issued
+  if (warp == 0) {
+    if (lane == 0) {
+      long long g = 0;
+      for (int t = blockIdx.x; t < n_tiles; t += G) {
+        const int4 tl = tiles[t];
+        const DevSub S = subs[tl.x];
+        const DevType T = types[S.type];
+        const int nk = k_extent(T.n_b, T.n_c, aug, KC) / KC;
+        const int arow = frow[S.module] + tl.y * TC_M;
+        const int bx0 = (int)bpad[tl.x];
+        const int col0 = tl.z * TC_NMAX;
+        for (int kc = 0; kc < nk; ++kc, ++g) {
+          const int st = (int)(g % STAGES);
+          const long long it = g / STAGES;
+          if (g >= STAGES && !mbar_wait(smem_u32(&empty_bar[st]), (uint32_t)((it - 1) & 1))) {
+            atomicExch(&fail_sh, 1);
+            break;
+          }
+          if (*(volatile int*)&fail_sh) break;
+          unsigned char* sb = base + st * STAGE_BYTES;
+          const uint32_t fb = smem_u32(&full_bar[st]);
+          asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(fb), "r"(STAGE_BYTES)
+                       : "memory");
+          tma_load_2d(smem_u32(sb), &tmA, kc * KC, arow, fb);
+          tma_load_2d(smem_u32(sb + A_BYTES), &tmB, bx0 + kc * KC, col0, fb);
+          if (PASSES == 3) {
+            tma_load_2d(smem_u32(sb + A_BYTES + B_BYTES), &tmAl, kc * KC, arow, fb);
+            tma_load_2d(smem_u32(sb + 2 * A_BYTES + B_BYTES), &tmBl, bx0 + kc * KC, col0, fb);
+          }
+          issued = g + 1;
+        }
+        if (*(volatile int*)&fail_sh) break;
+      }
+    }
+  } else if (warp == 1) {
+    if (lane == 0) {
+      long long g = 0;
+      int lt = 0;
+      for (int t = blockIdx.x; t < n_tiles; t += G, ++lt) {
+        const int4 tl = tiles[t];
+        const DevSub S = subs[tl.x];
+        const DevType T = types[S.type];
+        const int nk = k_extent(T.n_b, T.n_c, aug, KC) / KC;
+        const int ncols = min(TC_NMAX, m - tl.z * TC_NMAX);
+        const uint32_t idesc = idesc_of<FMT>(((ncols + 15) / 16) * 16);
+        const int ab = lt & 1, use = lt >> 1;
+        if (use > 0 && !mbar_wait(smem_u32(&tempty_bar[ab]), (uint32_t)((use - 1) & 1))) {
+          atomicExch(&fail_sh, 1);
+          break;
+        }
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        const uint32_t dacc = tmem + (uint32_t)(ab * TC_NMAX);
+        bool ok = true;
+        for (int kc = 0; kc < nk; ++kc, ++g) {
+          const int st = (int)(g % STAGES);
+          if (!mbar_wait(smem_u32(&full_bar[st]), (uint32_t)((g / STAGES) & 1))) {
+            ok = false;
+            break;
+          }
+          asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+          const uint32_t sa = smem_u32(base + st * STAGE_BYTES);
+          const uint32_t sbh = sa + A_BYTES;
+          const uint32_t sal = sa + A_BYTES + B_BYTES;
+          const uint32_t sbl = sa + 2 * A_BYTES + B_BYTES;
+#pragma unroll
+          for (int kk = 0; kk < 4; ++kk) {
+#pragma unroll
+            for (int pass = 0; pass < PASSES; ++pass) {
+              const uint32_t ap = (PASSES == 3 && pass == 0) ? sal : sa;
+              const uint32_t bp = (PASSES == 3 && pass == 1) ? sbl : sbh;
+              const uint32_t acc = (kc > 0 || kk > 0 || pass > 0) ? 1u : 0u;
+              mma_issue<FMT>(dacc, desc_sw128(ap + kk * 32), desc_sw128(bp + kk * 32), idesc, acc);
+            }
+          }
+          asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                           smem_u32(&empty_bar[st]))
+                       : "memory");
+          consumed_sh = g + 1;
+        }
+        if (!ok) {
+          atomicExch(&fail_sh, 1);
+          break;
+        }
+        asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                         smem_u32(&tfull_bar[ab]))
+                     : "memory");
+        if (*(volatile int*)&fail_sh) break;
+      }
+      // arrives once every MMA issued above has completed
+      asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                       smem_u32(&drain_bar))
+                   : "memory");
+    }
+  } else {
+    // ---- epilogue warps 2..5: TMEM lanes 32 * (warp % 4) ... + 31 ----
+    const int lq = warp & 3;
+    int lt = 0;
+    for (int t = blockIdx.x; t < n_tiles; t += G, ++lt) {
+      const int ab = lt & 1, use = lt >> 1;
+      const bool ok = mbar_wait(smem_u32(&tfull_bar[ab]), (uint32_t)(use & 1));
+      if (!__all_sync(0xffffffffu, ok) || *(volatile int*)&fail_sh) {
+        atomicExch(&fail_sh, 1);
+        break;
+      }
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      const int4 tl = tiles[t];
+      const DevSub S = subs[tl.x];
+      const int nb = types[S.type].n_b;
+      const int col0 = tl.z * TC_NMAX;
+      const int ncols = min(TC_NMAX, m - col0);
+      const int np = ((ncols + 15) / 16) * 16;
+      const int r = tl.y * TC_M + lq * 32 + lane;
+      const float sd = r < nb ? static_cast<float>(sqrtD[S.b_off + r]) : 0.0f;
+      float* yrow = Yb + S.b_off + r;
+      for (int jc = 0; jc < np; jc += 32) {
+        uint32_t v[32];
+        tmem_ld32(tmem + ((uint32_t)(lq * 32) << 16) + (uint32_t)(ab * TC_NMAX + jc), v);
+        if (r < nb) {
+#pragma unroll
+          for (int c = 0; c < 32; ++c)
+            if (jc + c < ncols) yrow[(int64_t)(col0 + jc + c) * nbt] = sd * __uint_as_float(v[c]);
+        }
+      }
+      asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+      asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&tempty_bar[ab])) : "memory");
+    }
+  }
+  __syncwarp();
+  __syncthreads();
+  if (fail_sh) {
+    if (tid == 0) {
+      atomicCAS(status, 0, 3000000 + blockIdx.x);
+      for (long long g = consumed_sh; g < issued; ++g)
+        mbar_wait(smem_u32(&full_bar[g % STAGES]), (uint32_t)((g / STAGES) & 1));
+    }
+  }
+  if (tid == 32) mbar_wait(smem_u32(&drain_bar), 0u);   // every MMA of this CTA has completed
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  if (warp == 1) {
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TCP_TMEM_COLS)
+                 : "memory");
   }
 }
 
@@ -644,6 +854,31 @@ cudaError_t launch_tc(const Ctx& c, int m, float* Yb, cudaStream_t st) {
   return cudaGetLastError();
 }
 
+template <int FMT, int PASSES, int STAGES>
+cudaError_t launch_tc_p(const Ctx& c, int m, float* Yb, cudaStream_t st) {
+  static bool attr_set = false;
+  const size_t smem = 1024 + (size_t)STAGES * (PASSES == 3 ? 2 : 1) * (TC_M * 128 + TC_NMAX * 128);
+  if (!attr_set) {
+    cudaError_t e = cudaFuncSetAttribute(k_tc_apply_p<FMT, PASSES, STAGES>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    attr_set = true;
+  }
+  CUtensorMap ta, tal, tb, tbl;
+  const void* alo = PASSES == 3 ? c.d_fa_lo : c.d_fa_hi;
+  const void* blo = PASSES == 3 ? c.d_xb_lo : c.d_xb_hi;
+  if (!make_map<FMT>(&ta, c.d_fa_hi, c.fa_pitch, c.fa_rows, TC_M) ||
+      !make_map<FMT>(&tal, alo, c.fa_pitch, c.fa_rows, TC_M) ||
+      !make_map<FMT>(&tb, c.d_xb_hi, c.nbp_total, m, TC_NMAX) || !make_map<FMT>(&tbl, blo, c.nbp_total, m, TC_NMAX))
+    return cudaErrorInvalidValue;
+  const int grid = std::min(c.n_tiles, std::max(1, c.n_sm));
+  k_tc_apply_p<FMT, PASSES, STAGES><<<grid, TCP_THREADS, smem, st>>>(ta, tal, tb, tbl, c.d_tiles, c.n_tiles, c.d_types,
+                                                                     c.d_subs, c.d_frow, c.d_bpad, c.d_sqrtDF, Yb,
+                                                                     c.hp.n_b_total, m, c.tc_aug, c.d_status);
+  note_launches(1);
+  return cudaGetLastError();
+}
+
 template <int FMT, int PASSES>
 void launch_gather(const Ctx& c, const double* X, int64_t ldx, int m, cudaStream_t st) {
   using T = typename TcFmt<FMT>::T;
@@ -664,6 +899,39 @@ void launch_put_v(const Ctx& c, const double* V, int m, cudaStream_t st) {
 }
 
 }  // namespace
+
+// The persistent kernel's work list for m directions: (subdomain, row tile,
+// column tile) for every row tile that holds interface rows; consecutive
+// entries share the subdomain (B chunks reused from L2) and the row tile (A
+// chunks reused).  Rebuilt only when the number of column tiles changes.
+cudaError_t tc_prepare_tiles(Ctx& c, int m) {
+  const int n_cb = (m + TC_NMAX - 1) / TC_NMAX;
+  if (c.tiles_ncb == n_cb) return cudaSuccess;
+  std::vector<int4> tl;
+  for (int s = 0; s < c.hp.n_sub; ++s) {
+    const int nb = c.h_types[c.h_subs[s].type].n_b;
+    for (int rb = 0; rb * TC_M < nb; ++rb)
+      for (int cb = 0; cb < n_cb; ++cb) tl.push_back(make_int4(s, rb, cb, 0));
+  }
+  if ((int64_t)tl.size() > c.tiles_cap) {
+    if (c.d_tiles) cudaFree(c.d_tiles);
+    c.d_tiles = nullptr;
+    cudaError_t e = cudaMalloc(&c.d_tiles, std::max<size_t>(tl.size(), 1) * sizeof(int4));
+    if (e != cudaSuccess) return e;
+    c.tiles_cap = (int64_t)tl.size();
+  }
+  cudaError_t e = cudaMemcpy(c.d_tiles, tl.data(), tl.size() * sizeof(int4), cudaMemcpyHostToDevice);
+  if (e != cudaSuccess) return e;
+  if (c.n_sm <= 0) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    e = cudaDeviceGetAttribute(&c.n_sm, cudaDevAttrMultiProcessorCount, dev);
+    if (e != cudaSuccess) return e;
+  }
+  c.n_tiles = (int)tl.size();
+  c.tiles_ncb = n_cb;
+  return cudaSuccess;
+}
 
 // xb = parts of D^{1/2} B^T X in the operand format and padded layout.
 cudaError_t tc_gather(const Ctx& c, const double* X, int64_t ldx, int m, cudaStream_t st) {
@@ -717,10 +985,15 @@ cudaError_t tc_product(const Ctx& c, int m, float* Yb, cudaStream_t st) {
   prof_begin(st, c.fl_tc * m, 1);
   cudaError_t e;
   const bool split = tc_split(c);
+  if (c.tiles_ncb != (m + TC_NMAX - 1) / TC_NMAX) return cudaErrorInvalidValue;   // tile list not prepared
+  // measured choice (3D, 512 directions): BF16 operands run faster in the
+  // persistent kernel (0.56 vs 0.71 ms one pass, 1.20 vs 1.64 ms split), TF32
+  // operands -- twice the bytes per MMA -- in the one-tile-per-CTA kernel with
+  // two CTAs per SM (1.35 vs 1.54 ms, 2.97 vs 3.12 ms)
   if (tc_format(c) == 0)
     e = split ? launch_tc<0, 3, TC_STAGES3>(c, m, Yb, st) : launch_tc<0, 1, TC_STAGES1>(c, m, Yb, st);
   else
-    e = split ? launch_tc<1, 3, TC_STAGES3>(c, m, Yb, st) : launch_tc<1, 1, TC_STAGES1>(c, m, Yb, st);
+    e = split ? launch_tc_p<1, 3, TCP_STAGES3>(c, m, Yb, st) : launch_tc_p<1, 1, TCP_STAGES1>(c, m, Yb, st);
   prof_end(st);
   return e;
 }
