@@ -38,6 +38,18 @@ METRIC = "F-applies/s & time-to-solve @rel.res 1e-6 vs plain FP64; % of HBM roof
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.070e9 / 1e12   # 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz
 
 
+def tensor_peaks():
+    """Dense tensor peaks (TFLOP/s): the measured BF16 burst figure, and TF32 as
+    that times the nominal TF32/BF16 ratio 1.1 / 2.25."""
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            bf16 = float(json.load(f)["bf16_tflops"])
+        src = "measured"
+    except (OSError, KeyError, ValueError):
+        bf16, src = 1900.0, "fallback"
+    return {"bf16": bf16, "tf32": bf16 * 1.1 / 2.25, "source": src}
+
+
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -208,10 +220,26 @@ def run_forms(p, a, fg, torch, dev, stream, flush, forms, max_iter, m_apply, rep
             continue
         n = fg.feti_query(s.ctx, fg.FETI_Q_N_LAMBDA)
         ms_apply = apply_timing(fg, torch, stream, flush, s, n, m_apply)
+        tensor = None
+        if prec != fg.FETI_FP64:
+            # the tensor-core product of one more apply, bracketed by CUDA events
+            fg.feti_profile_begin(s.ctx)
+            apply_timing(fg, torch, stream, flush, s, n, m_apply, reps=1)
+            fg.feti_profile_end(s.ctx)
+            tf, tms, tn = fg.feti_profile_tensor(s.ctx)
+            if tn:
+                pk = tensor_peaks()
+                peak = pk["bf16"] if prec in (fg.FETI_BF16, fg.FETI_BF16X3) else pk["tf32"]
+                passes = 3 if prec in (fg.FETI_TF32X3, fg.FETI_BF16X3) else 1
+                ach = tf / (tms / 1e3) / 1e12
+                tensor = {"bound": "tensor", "ms_per_launch": tms / tn, "achieved": ach, "peak": peak,
+                          "unit": "TFLOP/s", "frac": ach / peak, "passes": passes,
+                          "frac_of_tensor_work": ach * passes / peak, "peak_source": pk["source"]}
         sols[name] = u.cpu().numpy()
         out[name] = {"time_to_solve_ms": float(np.median(times)), "iterations": st.iterations,
                      "refinements": st.refinements, "f_applies": st.f_applies, "converged": bool(st.converged),
-                     f"apply_{m_apply}_cols_ms": ms_apply, "apply_f_applies_per_s": m_apply / (ms_apply / 1e3)}
+                     f"apply_{m_apply}_cols_ms": ms_apply, "apply_f_applies_per_s": m_apply / (ms_apply / 1e3),
+                     "tensor_product_roofline": tensor}
         s.close()
     ref = sols["fp64"]
     t64 = out["fp64"]["time_to_solve_ms"]

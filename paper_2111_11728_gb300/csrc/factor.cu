@@ -28,26 +28,39 @@ __global__ void __launch_bounds__(NT) k_band_chol(const DevType* __restrict__ ty
   const int n = T.n_i, bw = T.bw, W = bw + 1;
   double* L = mem + M.lcol;
   extern __shared__ double col[];
-  const int tid = threadIdx.x;
+  __shared__ double s_dj, s_rd;
+  __shared__ int s_ok;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   for (int j = 0; j < n; ++j) {
     const int len = min(bw, n - 1 - j);
-    const double piv = L[(int64_t)j * W];
-    __syncthreads();   // every thread holds the pivot before column j is overwritten
-    if (!(piv > 0.0)) {
+    // one thread takes the pivot's square root and reciprocal (FP64 work is
+    // scarce on this part; 256 threads repeating it cost more than the update)
+    if (tid == 0) {
+      const double piv = L[(int64_t)j * W];
+      s_ok = piv > 0.0;
+      if (s_ok) {
+        s_dj = sqrt(piv);
+        s_rd = 1.0 / s_dj;
+      }
+    }
+    __syncthreads();   // the pivot is read before column j is overwritten
+    if (!s_ok) {
       if (tid == 0) atomicCAS(status, 0, 1000000 + blockIdx.x);
       return;
     }
-    const double dj = sqrt(piv);
-    const double rd = 1.0 / dj;
+    const double dj = s_dj, rd = s_rd;
     for (int t = tid; t <= len; t += NT) {
       const double v = t == 0 ? dj : L[(int64_t)j * W + t] * rd;
       col[t] = v;
       L[(int64_t)j * W + t] = v;
     }
     __syncthreads();
-    for (int e = tid; e < len * len; e += NT) {
-      const int a = e / len + 1, b = e % len + 1;
-      if (b >= a) L[(int64_t)(j + a) * W + (b - a)] = fma(-col[a], col[b], L[(int64_t)(j + a) * W + (b - a)]);
+    // trailing band: L(j+b, j+a) -= L(j+b, j) L(j+a, j) for 1 <= a <= b <= len,
+    // stored at Lcol[(j+a) W + (b-a)]; a warp per a, lanes over b
+    for (int a = 1 + warp; a <= len; a += NT / 32) {
+      const double ca = col[a];
+      double* row = L + (int64_t)(j + a) * W - a;
+      for (int b = a + lane; b <= len; b += 32) row[b] = fma(-ca, col[b], row[b]);
     }
     __syncthreads();
   }
@@ -113,16 +126,25 @@ __global__ void __launch_bounds__(NT) k_dense_chol(const DenseDesc* __restrict__
   const int nf = D.n_full > n ? D.n_full : n;
   double* A = D.A;
   extern __shared__ double col[];
+  __shared__ double s_dj, s_rd;
+  __shared__ int s_ok;
   const int tid = threadIdx.x;
   for (int j = 0; j < n; ++j) {
     const int len = nf - 1 - j;
-    const double piv = A[(int64_t)j * ld + j];
-    __syncthreads();   // every thread holds the pivot before column j is overwritten
-    if (!(piv > 0.0)) {
+    if (tid == 0) {                      // one thread: square root and reciprocal of the pivot
+      const double piv = A[(int64_t)j * ld + j];
+      s_ok = piv > 0.0;
+      if (s_ok) {
+        s_dj = sqrt(piv);
+        s_rd = 1.0 / s_dj;
+      }
+    }
+    __syncthreads();   // the pivot is read before column j is overwritten
+    if (!s_ok) {
       if (tid == 0) atomicCAS(status, 0, 2000000 + D.tag);
       return;
     }
-    const double dj = sqrt(piv), rd = 1.0 / dj;
+    const double dj = s_dj, rd = s_rd;
     for (int t = tid; t <= len; t += NT) {
       const double v = t == 0 ? dj : A[(int64_t)(j + t) * ld + j] * rd;
       col[t] = v;
@@ -304,14 +326,23 @@ __global__ void __launch_bounds__(256) k_diag_block(double* __restrict__ A, int 
     S[r][q] = A[(int64_t)(c0 + r) * n + c0 + q];
   }
   __syncthreads();
+  __shared__ double s_dj, s_rd;
+  __shared__ int s_ok;
   for (int j = 0; j < nb; ++j) {
-    const double piv = S[j][j];
+    if (tid == 0) {                      // one thread: square root and reciprocal of the pivot
+      const double piv = S[j][j];
+      s_ok = piv > 0.0;
+      if (s_ok) {
+        s_dj = sqrt(piv);
+        s_rd = 1.0 / s_dj;
+      }
+    }
     __syncthreads();
-    if (!(piv > 0.0)) {
+    if (!s_ok) {
       if (tid == 0) atomicCAS(status, 0, 2000000 + tag);
       return;
     }
-    const double dj = sqrt(piv), rd = 1.0 / dj;
+    const double dj = s_dj, rd = s_rd;
     for (int t = j + tid; t < nb; t += 256) S[t][j] = t == j ? dj : S[t][j] * rd;
     __syncthreads();
     for (int e = tid; e < (nb - 1 - j) * (nb - 1 - j); e += 256) {
