@@ -66,6 +66,7 @@ def parse():
     ap.add_argument("--forms-rho-lo", type=float, default=0.1)
     ap.add_argument("--no-batch", action="store_true")
     ap.add_argument("--forms-3d", action="store_true", help="also compare the forms on the 3D workload (minutes)")
+    ap.add_argument("--no-apply-3d", action="store_true", help="skip the 3D dual-operator apply rooflines")
     ap.add_argument("--tiles-3d", type=int, default=8)
     ap.add_argument("--batch-problems", type=int, default=64)
     ap.add_argument("--batch-max-iter", type=int, default=500)
@@ -286,6 +287,47 @@ def compare_forms_3d(a, fg, torch, dev, stream, flush):
     return out
 
 
+def apply_rooflines_3d(a, fg, torch, dev, stream, flush, m=512):
+    """The dual-operator block apply on the 3D workload (8^3 subdomains of 8^3
+    H8, 512 directions) in every precision: apply time and, for the
+    tensor-core forms, the product kernel's algorithmic TFLOP/s against its
+    peak (CUDA events around the launches)."""
+    p = workloads.config4(tiles=a.tiles_3d, elems=8)
+    rho_d = torch.from_numpy(p.rho).to(dev)
+    f_d = torch.from_numpy(p.f).to(dev)
+    pk = tensor_peaks()
+    out = {"workload": f"3D H8: {a.tiles_3d}^3 subdomains of 8^3 elements, {p.n_dofs} DOF", "m": m}
+    for name, prec, _ in precision_forms(fg):
+        s = fg.Solver(fg.FETI_FETIDP, fg.FETI_SCALING_K, fg.FETI_RRS, stream=stream.cuda_stream, precision=prec)
+        s.setup(p, rho=rho_d, f=f_d, on_device=True)
+        fg.feti_factorize(s.ctx)
+        n = fg.feti_query(s.ctx, fg.FETI_Q_N_LAMBDA)
+        ms = apply_timing(fg, torch, stream, flush, s, n, m, reps=3)
+        fg.feti_profile_begin(s.ctx)
+        apply_timing(fg, torch, stream, flush, s, n, m, reps=1)
+        gf, gms, gn = fg.feti_profile_end(s.ctx)
+        tf, tms, tn = fg.feti_profile_tensor(s.ctx)
+        row = {"apply_ms": ms, "f_applies_per_s": m / (ms / 1e3)}
+        if tn:
+            peak = pk["bf16"] if prec in (fg.FETI_BF16, fg.FETI_BF16X3) else pk["tf32"]
+            passes = 3 if prec in (fg.FETI_TF32X3, fg.FETI_BF16X3) else 1
+            ach = tf / (tms / 1e3) / 1e12
+            row["tensor_product_roofline"] = {"bound": "tensor", "ms_per_launch": tms / tn, "achieved": ach,
+                                              "peak": peak, "unit": "TFLOP/s", "frac": ach / peak,
+                                              "passes": passes, "frac_of_tensor_work": ach * passes / peak,
+                                              "peak_source": pk["source"]}
+        elif gn:
+            ach = gf / (gms / 1e3) / 1e12
+            row["fp64_gemm_roofline"] = {"bound": "alu", "achieved": ach, "peak": FP64_PEAK_TFLOPS,
+                                         "unit": "TFLOP/s", "frac": ach / FP64_PEAK_TFLOPS}
+        out[name] = row
+        s.close()
+    for name in list(out):
+        if isinstance(out[name], dict) and name != "fp64" and "apply_ms" in out[name]:
+            out[name]["speedup_vs_fp64"] = out["fp64"]["apply_ms"] / out[name]["apply_ms"]
+    return out
+
+
 def compare_batch(a, fg, torch, dev, stream):
     """The batching form: the uneven multi-problem workload (tile grids drawn
     from 4x4..24x24 subdomains of 16x16..48x48 elements, thresholded smoothed
@@ -496,6 +538,9 @@ def run_ours(a, rank, world):
     forms = None
     if not a.no_forms:
         forms = compare_forms(a, fg, torch, dev, stream, flush)
+    apply3d = None
+    if not a.no_apply_3d and world == 1:
+        apply3d = apply_rooflines_3d(a, fg, torch, dev, stream, flush)
     forms3d = None
     if a.forms_3d and world == 1:
         forms3d = compare_forms_3d(a, fg, torch, dev, stream, flush)
@@ -517,11 +562,15 @@ def run_ours(a, rank, world):
                                                "orthogonalization, Schur)",
                      "achieved": gemm_tflops, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
                      "frac": (gemm_tflops / FP64_PEAK_TFLOPS) if gemm_tflops else None,
-                     "traffic": None, "peak_source": "derived: 152 SMs x 2 FP64 FMA/clk x 2.07 GHz",
+                     "traffic": None,
+                     "traffic_note": "dram read+write per launch from the ncu capture of two launches: "
+                                     "91.5 MB (29,760 x 256 x 256 update), 125.3 MB (split-K product); "
+                                     "launch shapes vary, so no single per-launch figure",
+                     "peak_source": "derived: 152 SMs x 2 FP64 FMA/clk x 2.07 GHz",
                      "kernel_share_of_step": (gms / 1e3) / t_steps if t_steps > 0 else None,
                      "launches": gn},
         "e2e": e2e, "gpu_launches": int(launches), "clocks": clk, "wall_s": wall,
-        "forms": forms, "forms_3d": forms3d, "batch_form": batch,
+        "forms": forms, "apply_3d": apply3d, "forms_3d": forms3d, "batch_form": batch,
     }
     s.close()
     return out

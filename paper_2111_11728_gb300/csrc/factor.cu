@@ -81,16 +81,19 @@ __global__ void k_band_rows(const DevType* __restrict__ types, const DevModule* 
 }
 
 // Y = L^{-1} Y for the n_bc right-hand sides of one module; each thread
-// marches down one column keeping the last bw values in shared memory.
+// marches down one column keeping the last bw values in shared memory.  One
+// warp of FW_COLS columns per block, so that the few distinct modules still
+// spread over every SM (the substitution is FP64-bound per SM).
+constexpr int FW_COLS = 32;
 __global__ void k_band_fwd_multi(const DevType* __restrict__ types, const DevModule* __restrict__ mods,
                                  double* __restrict__ mem) {
   const DevModule M = mods[blockIdx.y];
   const DevType T = types[M.type];
   const int nbc = T.n_b + T.n_c;
-  const int col = blockIdx.x * 64 + threadIdx.x;
+  const int col = blockIdx.x * FW_COLS + threadIdx.x;
   if (col >= nbc) return;
   const int n = T.n_i, bw = T.bw, W = bw + 1;
-  extern __shared__ double win[];   // [W][64]
+  extern __shared__ double win[];   // [W][FW_COLS]
   const double* __restrict__ Lr = mem + M.lrow;
   const double* __restrict__ rd = mem + M.rdiag;
   double* __restrict__ Y = mem + M.Y;
@@ -104,16 +107,16 @@ __global__ void k_band_fwd_multi(const DevType* __restrict__ types, const DevMod
     int d = 1;
     for (; d + 1 <= dmax; d += 2) {
       sl = sl == 0 ? W - 1 : sl - 1;
-      acc0 = fma(-lr[d], win[sl * 64 + tc], acc0);
+      acc0 = fma(-lr[d], win[sl * FW_COLS + tc], acc0);
       sl = sl == 0 ? W - 1 : sl - 1;
-      acc1 = fma(-lr[d + 1], win[sl * 64 + tc], acc1);
+      acc1 = fma(-lr[d + 1], win[sl * FW_COLS + tc], acc1);
     }
     if (d <= dmax) {
       sl = sl == 0 ? W - 1 : sl - 1;
-      acc0 = fma(-lr[d], win[sl * 64 + tc], acc0);
+      acc0 = fma(-lr[d], win[sl * FW_COLS + tc], acc0);
     }
     const double y = (acc0 + acc1) * rd[j];
-    win[slot * 64 + tc] = y;
+    win[slot * FW_COLS + tc] = y;
     Y[(int64_t)j * nbc + col] = y;
     slot = slot + 1 == W ? 0 : slot + 1;
   }
@@ -456,12 +459,13 @@ cudaError_t launch_band_chol(const Ctx& c, cudaStream_t st) {
 cudaError_t launch_band_fwd_multi(const Ctx& c, cudaStream_t st) {
   int maxbw = 1, maxbc = 1;
   for (auto& t : c.h_types) { maxbw = std::max(maxbw, t.bw); maxbc = std::max(maxbc, t.n_b + t.n_c); }
-  size_t sm = (size_t)(maxbw + 1) * 64 * sizeof(double);
+  size_t sm = (size_t)(maxbw + 1) * FW_COLS * sizeof(double);
   if (sm > 48 * 1024) {
     cudaError_t e = cudaFuncSetAttribute(k_band_fwd_multi, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     if (e != cudaSuccess) return e;
   }
-  k_band_fwd_multi<<<dim3((maxbc + 63) / 64, c.n_mod), 64, sm, st>>>(c.d_types, c.d_mods, c.d_modmem);
+  k_band_fwd_multi<<<dim3((maxbc + FW_COLS - 1) / FW_COLS, c.n_mod), FW_COLS, sm, st>>>(c.d_types, c.d_mods,
+                                                                                      c.d_modmem);
   note_launches(1);
   return cudaGetLastError();
 }
