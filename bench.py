@@ -40,14 +40,39 @@ FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.070e9 / 1e12   # 152 SMs x 2 DFMA/clk x 2 flo
 
 def tensor_peaks():
     """Dense tensor peaks (TFLOP/s): the measured BF16 burst figure, and TF32 as
-    that times the nominal TF32/BF16 ratio 1.1 / 2.25."""
+    that times the nominal TF32/BF16 ratio 1.1 / 2.25; HBM copy bandwidth (GB/s)."""
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
-            bf16 = float(json.load(f)["bf16_tflops"])
-        src = "measured"
+            mp = json.load(f)
+        bf16, hbm, src = float(mp["bf16_tflops"]), float(mp["hbm_gbs"]), "measured"
     except (OSError, KeyError, ValueError):
-        bf16, src = 1900.0, "fallback"
-    return {"bf16": bf16, "tf32": bf16 * 1.1 / 2.25, "source": src}
+        bf16, hbm, src = 1900.0, 6800.0, "fallback"
+    return {"bf16": bf16, "tf32": bf16 * 1.1 / 2.25, "hbm_gbs": hbm, "source": src}
+
+
+def tensor_roofline(fg, s, prec, m):
+    """Roofline of the tensor-core product launches profiled last on solver s:
+    max(algorithmic bytes / HBM bandwidth, tensor work / tensor peak) against the
+    measured time (the split products' tensor work is three passes)."""
+    tf, tms, tn = fg.feti_profile_tensor(s.ctx)
+    if not tn:
+        return None
+    pk = tensor_peaks()
+    peak = pk["bf16"] if prec in (fg.FETI_BF16, fg.FETI_BF16X3) else pk["tf32"]
+    passes = 3 if prec in (fg.FETI_TF32X3, fg.FETI_BF16X3) else 1
+    t = tms / tn / 1e3                                         # seconds per launch
+    flops = tf / tn
+    nbytes = fg.feti_query(s.ctx, fg.FETI_Q_TC_BYTES_F) + m * fg.feti_query(s.ctx, fg.FETI_Q_TC_BYTES_PER_COL)
+    t_hbm = nbytes / (pk["hbm_gbs"] * 1e9)
+    t_tc = passes * flops / (peak * 1e12)
+    bound = "hbm" if t_hbm >= t_tc else "tensor"
+    return {"bound": bound, "ms_per_launch": t * 1e3,
+            "achieved": (nbytes / t / 1e9) if bound == "hbm" else (flops / t / 1e12),
+            "peak": pk["hbm_gbs"] if bound == "hbm" else peak,
+            "unit": "GB/s" if bound == "hbm" else "TFLOP/s",
+            "frac": max(t_hbm, t_tc) / t, "traffic": None,
+            "algorithmic_bytes": nbytes, "algorithmic_flops": flops, "passes": passes,
+            "hbm_frac": t_hbm / t, "tensor_frac": t_tc / t, "peak_source": pk["source"]}
 
 
 def parse():
@@ -227,15 +252,7 @@ def run_forms(p, a, fg, torch, dev, stream, flush, forms, max_iter, m_apply, rep
             fg.feti_profile_begin(s.ctx)
             apply_timing(fg, torch, stream, flush, s, n, m_apply, reps=1)
             fg.feti_profile_end(s.ctx)
-            tf, tms, tn = fg.feti_profile_tensor(s.ctx)
-            if tn:
-                pk = tensor_peaks()
-                peak = pk["bf16"] if prec in (fg.FETI_BF16, fg.FETI_BF16X3) else pk["tf32"]
-                passes = 3 if prec in (fg.FETI_TF32X3, fg.FETI_BF16X3) else 1
-                ach = tf / (tms / 1e3) / 1e12
-                tensor = {"bound": "tensor", "ms_per_launch": tms / tn, "achieved": ach, "peak": peak,
-                          "unit": "TFLOP/s", "frac": ach / peak, "passes": passes,
-                          "frac_of_tensor_work": ach * passes / peak, "peak_source": pk["source"]}
+            tensor = tensor_roofline(fg, s, prec, m_apply)
         sols[name] = u.cpu().numpy()
         out[name] = {"time_to_solve_ms": float(np.median(times)), "iterations": st.iterations,
                      "refinements": st.refinements, "f_applies": st.f_applies, "converged": bool(st.converged),
@@ -295,7 +312,6 @@ def apply_rooflines_3d(a, fg, torch, dev, stream, flush, m=512):
     p = workloads.config4(tiles=a.tiles_3d, elems=8)
     rho_d = torch.from_numpy(p.rho).to(dev)
     f_d = torch.from_numpy(p.f).to(dev)
-    pk = tensor_peaks()
     out = {"workload": f"3D H8: {a.tiles_3d}^3 subdomains of 8^3 elements, {p.n_dofs} DOF", "m": m}
     for name, prec, _ in precision_forms(fg):
         s = fg.Solver(fg.FETI_FETIDP, fg.FETI_SCALING_K, fg.FETI_RRS, stream=stream.cuda_stream, precision=prec)
@@ -306,16 +322,10 @@ def apply_rooflines_3d(a, fg, torch, dev, stream, flush, m=512):
         fg.feti_profile_begin(s.ctx)
         apply_timing(fg, torch, stream, flush, s, n, m, reps=1)
         gf, gms, gn = fg.feti_profile_end(s.ctx)
-        tf, tms, tn = fg.feti_profile_tensor(s.ctx)
         row = {"apply_ms": ms, "f_applies_per_s": m / (ms / 1e3)}
-        if tn:
-            peak = pk["bf16"] if prec in (fg.FETI_BF16, fg.FETI_BF16X3) else pk["tf32"]
-            passes = 3 if prec in (fg.FETI_TF32X3, fg.FETI_BF16X3) else 1
-            ach = tf / (tms / 1e3) / 1e12
-            row["tensor_product_roofline"] = {"bound": "tensor", "ms_per_launch": tms / tn, "achieved": ach,
-                                              "peak": peak, "unit": "TFLOP/s", "frac": ach / peak,
-                                              "passes": passes, "frac_of_tensor_work": ach * passes / peak,
-                                              "peak_source": pk["source"]}
+        tr = tensor_roofline(fg, s, prec, m)
+        if tr:
+            row["tensor_product_roofline"] = tr
         elif gn:
             ach = gf / (gms / 1e3) / 1e12
             row["fp64_gemm_roofline"] = {"bound": "alu", "achieved": ach, "peak": FP64_PEAK_TFLOPS,
@@ -498,13 +508,15 @@ def run_ours(a, rank, world):
 
     # accuracy: relative displacement error against a direct sparse solve of
     # Eq. (2) assembled by the oracle (CPU, outside the timed region)
-    rel_err = None
+    rel_err, primal_res = None, None
     if rank == 0 and not a.no_accuracy:
         try:
-            from oracle.assemble import direct_solve
+            from oracle.assemble import direct_solve, global_stiffness
             ud = direct_solve(p)
             u = u_d.cpu().numpy()
             rel_err = float(np.linalg.norm(u - ud) / np.linalg.norm(ud))
+            free = ~np.asarray(p.dirichlet, bool)
+            primal_res = float(np.linalg.norm((global_stiffness(p) @ u - p.f)[free]) / np.linalg.norm(p.f))
         except Exception as exc:  # pragma: no cover - diagnostics only
             rel_err = f"unavailable: {exc}"
 
@@ -557,7 +569,7 @@ def run_ours(a, rank, world):
         "time_to_solve_ms": 1e3 * t_steps / a.steps,
         "solve_and_recover_ms": solve_ms,
         "iterations": iters, "converged": conv, "f_applies_per_step": applies // max(1, a.steps),
-        "rel_error_vs_direct_solve": rel_err,
+        "rel_error_vs_direct_solve": rel_err, "primal_residual": primal_res,
         "roofline": {"bound": "alu", "kernel": "dgemm_kernel (FP64 GEMM: dual-operator blocks, Gram, "
                                                "orthogonalization, Schur)",
                      "achieved": gemm_tflops, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",

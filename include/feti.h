@@ -219,8 +219,12 @@ enum {
   FETI_Q_DEVICE_BYTES = 8, FETI_Q_N_RBM = 9,
   FETI_Q_LAUNCHES = 10,  /* process-wide count of kernels this library has launched (any ctx state) */
   FETI_Q_N_PROBLEMS = 11,
-  FETI_Q_GEMV_CONFIG = 12  /* autotuned launch shape of the per-subdomain matrix-vector kernel (batches):
+  FETI_Q_GEMV_CONFIG = 12,  /* autotuned launch shape of the per-subdomain matrix-vector kernel (batches):
                               warps per CTA + 100 if vector loads; 0 = default */
+  FETI_Q_TC_BYTES_F = 13,      /* reduced precision: bytes of the tensor-core product's stationary operand
+                                  (every module's scaled blocks, all parts), read once per apply */
+  FETI_Q_TC_BYTES_PER_COL = 14 /* reduced precision: bytes the product moves per direction: the
+                                  gathered operand in (all parts) and the FP32 interface result out */
 };
 feti_status feti_query(const feti_ctx* ctx, int key, int64_t* value);
 

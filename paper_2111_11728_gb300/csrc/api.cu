@@ -642,9 +642,19 @@ static feti_status setup_impl(Ctx& c, const feti_problem* probs, int n) {
     }
     c.fa_pitch = kmax;
     c.fl_tc = 0.0;
+    const int64_t parts = split_precision(c.opt.precision) ? 2 : 1;
+    const int64_t eb = (int64_t)tc_elem_bytes(c.opt.precision);
+    c.tc_bytes_col = 0;
     for (int s = 0; s < hp.n_sub; ++s) {
       const DevType& T = c.h_types[c.h_subs[s].type];
-      c.fl_tc += 2.0 * T.n_b * (T.n_b + (c.tc_aug ? T.n_c : 0));
+      const int ncx = c.tc_aug ? T.n_c : 0;
+      c.fl_tc += 2.0 * T.n_b * (T.n_b + ncx);
+      c.tc_bytes_col += (int64_t)(T.n_b + ncx) * eb * parts + (int64_t)T.n_b * 4;
+    }
+    c.tc_bytes_f = 0;
+    for (int q = 0; q < c.n_mod; ++q) {
+      const DevType& T = c.h_types[c.h_mods[q].type];
+      c.tc_bytes_f += (int64_t)T.n_b * (T.n_b + (c.tc_aug ? T.n_c : 0)) * eb * parts;
     }
     c.fa_rows = std::max<int64_t>(rows, 1);
     c.nbp_total = std::max<int64_t>(nbp, kc);
@@ -1237,6 +1247,8 @@ feti_status feti_query(const feti_ctx* ctx, int key, int64_t* value) {
     case FETI_Q_LAUNCHES: *value = launches(); break;
     case FETI_Q_N_PROBLEMS: *value = hp.n_prob; break;
     case FETI_Q_GEMV_CONFIG: *value = c.gemv_cfg; break;
+    case FETI_Q_TC_BYTES_F: *value = c.tc_bytes_f; break;
+    case FETI_Q_TC_BYTES_PER_COL: *value = c.tc_bytes_col; break;
     default: return FETI_EINVAL;
   }
   return FETI_OK;

@@ -233,6 +233,8 @@ struct Ctx {
   int64_t tiles_cap = 0;
   int n_tiles = 0, tiles_ncb = 0, n_sm = 0;
   double fl_tc = 0.0;            // algorithmic flops of the tensor-core product per column
+  int64_t tc_bytes_f = 0;        // algorithmic bytes: scaled blocks (read once per apply)
+  int64_t tc_bytes_col = 0;      // algorithmic bytes per column: operand in + FP32 result out
   double prof_tc_flops = 0.0, prof_tc_ms = 0.0;   // tensor-core products of the last profile
   int64_t prof_tc_launches = 0;
   double* d_sqrtDF = nullptr;    // [n_b_total] sqrt(diag F_s)
