@@ -38,6 +38,9 @@ from .scaling import Constraints, pairwise_rows, row_weights
 from .tfeti import schur_complement
 
 
+PRECONDS = ("dirichlet", "lumped", "superlumped")
+
+
 class _Module:
     """Per-distinct-subdomain factorisation data (shared by identical modules)."""
 
@@ -56,10 +59,14 @@ class _Module:
         self.Frc_b = self.KinvKrc[b_in_r]                              # [K_rr^{-1} K_rc]_b
         self.Kbar = self.Kcc - self.Krc.T @ self.KinvKrc               # local Kbar_cc^s
         self.S = schur_complement(self.Krr, b_in_r)                    # Eq. (13) on r-DOFs
+        self.Kbb = self.Krr[np.ix_(b_in_r, b_in_r)]                    # lumped: K_bb instead of S
 
 
 class FETIDP:
-    def __init__(self, problem, scaling="k", dedup=True):
+    def __init__(self, problem, scaling="k", dedup=True, precond="dirichlet"):
+        if precond not in PRECONDS:
+            raise ValueError(precond)
+        self.precond = precond
         self.problem = problem
         mesh = self.mesh = mesh_of(problem)
         dim = self.dim = problem.dim
@@ -195,12 +202,24 @@ class FETIDP:
 
     project_T = project
 
+    def precond_block(self, s):
+        """The local block of the preconditioner: the Dirichlet choice S^s of
+        Eq. 13 (Schur complement onto the interface), the lumped choice K_bb
+        (the interface block of the stiffness, no interior solve) or the
+        super-lumped choice diag(K_bb) (Section 3)."""
+        M = self.mod(s)
+        if self.precond == "dirichlet":
+            return M.S
+        if self.precond == "lumped":
+            return M.Kbb
+        return np.diag(np.diag(M.Kbb))
+
     def precond_columns(self, r):
-        """Z = [..., B~_r^s S^s B~_r^sT r, ...]: one column per subdomain (Eq. 13 on r-DOFs)."""
+        """Z = [..., B~_r^s P^s B~_r^sT r, ...]: one column per subdomain (Eq. 13 on r-DOFs)."""
         Z = np.zeros((self.n_lam, self.n_sub))
         for s in range(self.n_sub):
             Bb = self.Brt[s][:, self.bset[s]]
-            Z[:, s] = Bb @ (self.mod(s).S @ (Bb.T @ r))
+            Z[:, s] = Bb @ (self.precond_block(s) @ (Bb.T @ r))
         return Z
 
     # -- recovery (second row of Eq. 12, then the second row of Eq. 11) ----------

@@ -5,17 +5,17 @@ from .krylov import solve_dual
 from .tfeti import TFETI
 
 
-def build(problem, method="fetidp", scaling="k"):
+def build(problem, method="fetidp", scaling="k", precond="dirichlet"):
     if method == "tfeti":
-        return TFETI(problem, scaling)
+        return TFETI(problem, scaling, precond=precond)
     if method == "fetidp":
-        return FETIDP(problem, scaling)
+        return FETIDP(problem, scaling, precond=precond)
     raise ValueError(method)
 
 
 def solve(problem, method="fetidp", scaling="k", krylov="rrs", tol=1e-6, max_iter=500,
-          rr_tol=1e-10, op=None):
+          rr_tol=1e-10, op=None, precond="dirichlet"):
     """Returns (u_global, lambda, info, op)."""
-    op = op or build(problem, method, scaling)
+    op = op or build(problem, method, scaling, precond)
     lam, info = solve_dual(op, tol=tol, max_iter=max_iter, rr_tol=rr_tol, variant=krylov)
     return op.recover(lam), lam, info, op

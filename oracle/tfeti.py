@@ -54,7 +54,10 @@ def schur_complement(K, bset):
 
 
 class TFETI:
-    def __init__(self, problem, scaling="k"):
+    def __init__(self, problem, scaling="k", precond="dirichlet"):
+        if precond not in ("dirichlet", "lumped", "superlumped"):
+            raise ValueError(precond)
+        self.precond = precond
         self.problem = problem
         mesh = self.mesh = mesh_of(problem)
         dim = self.dim = problem.dim
@@ -92,6 +95,7 @@ class TFETI:
         # --- Dirichlet preconditioner pieces (Eq. 13): b = DOFs touched by B ---
         self.bset = [np.unique(self.B[s].indices) for s in range(ns)]
         self.S = [schur_complement(self.K[s], self.bset[s]) for s in range(ns)]
+        self.Kbb = [self.K[s][np.ix_(self.bset[s], self.bset[s])] for s in range(ns)]
         # --- G, e, d (Eq. 7) and the coarse matrix G G^T ---
         nr = self.R[0].shape[1]
         self.n_rbm = nr
@@ -114,12 +118,20 @@ class TFETI:
 
     project_T = project   # P is symmetric
 
+    def precond_block(self, s):
+        """Dirichlet S^s (Eq. 13), lumped K_bb or super-lumped diag(K_bb)."""
+        if self.precond == "dirichlet":
+            return self.S[s]
+        if self.precond == "lumped":
+            return self.Kbb[s]
+        return np.diag(np.diag(self.Kbb[s]))
+
     def precond_columns(self, r):
-        """Z = [... , B~^s S^s B~^sT r, ...] one column per subdomain (the block preconditioner of Algorithm 1)."""
+        """Z = [... , B~^s P^s B~^sT r, ...] one column per subdomain (the block preconditioner of Algorithm 1)."""
         Z = np.zeros((self.n_lam, self.n_sub))
         for s in range(self.n_sub):
             Bb = self.Bt[s][:, self.bset[s]]
-            Z[:, s] = Bb @ (self.S[s] @ (Bb.T @ r))
+            Z[:, s] = Bb @ (self.precond_block(s) @ (Bb.T @ r))
         return Z
 
     # -- dense forms for tiny problems (brute-force pins) -----------------------
