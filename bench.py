@@ -516,7 +516,11 @@ def run_ours(a, rank, world):
             u = u_d.cpu().numpy()
             rel_err = float(np.linalg.norm(u - ud) / np.linalg.norm(ud))
             free = ~np.asarray(p.dirichlet, bool)
-            primal_res = float(np.linalg.norm((global_stiffness(p) @ u - p.f)[free]) / np.linalg.norm(p.f))
+            K = global_stiffness(p)
+            res = (K @ u - p.f)[free]
+            primal_res = {"vs_f": float(np.linalg.norm(res) / np.linalg.norm(p.f)),
+                          "backward_error": float(np.linalg.norm(res) / (np.linalg.norm((abs(K) @ np.abs(u))[free])
+                                                                        + np.linalg.norm(p.f)))}
         except Exception as exc:  # pragma: no cover - diagnostics only
             rel_err = f"unavailable: {exc}"
 

@@ -62,6 +62,7 @@ enum { FETI_TFETI = 0, FETI_FETIDP = 1 };                 /* Sections 2.1 / 2.2 
 enum { FETI_SCALING_K = 0, FETI_SCALING_MULT = 1 };       /* Eq. 15 / multiplicity */
 enum { FETI_PCG = 0, FETI_FO = 1, FETI_RRS = 2 };         /* Sections 3.2, 3.3 */
 enum { FETI_FP64 = 0, FETI_TF32 = 1, FETI_TF32X3 = 2, FETI_BF16 = 3, FETI_BF16X3 = 4 };  /* block products */
+enum { FETI_PRECOND_DIRICHLET = 0, FETI_PRECOND_LUMPED = 1, FETI_PRECOND_SUPERLUMPED = 2 };
 
 typedef struct {
   int method;          /* FETI_TFETI or FETI_FETIDP */
@@ -81,6 +82,10 @@ typedef struct {
                           solve; 0 (default) picks 1e-2.
                           Each inner solve is also capped at 30 iterations */
   int max_refine;      /* reduced precision: cap on the FP64 refinement steps (30) */
+  int precond;         /* local block of the preconditioner (Section 3): FETI_PRECOND_DIRICHLET
+                          (default; the interface Schur complement S_s of Eq. 13), FETI_PRECOND_LUMPED
+                          (the interface stiffness block K_bb: no interior solve) or
+                          FETI_PRECOND_SUPERLUMPED (diag K_bb) */
   int fp64_residual;   /* reduced precision, 0 (default) or 1: every inner iteration replaces
                           the recursive residual by the FP64 residual r_outer - P^T F lambda~
                           (one FP64 single-column apply per iteration) and the inner solve

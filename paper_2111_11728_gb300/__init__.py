@@ -22,6 +22,7 @@ FETI_TFETI, FETI_FETIDP = 0, 1
 FETI_SCALING_K, FETI_SCALING_MULT = 0, 1
 FETI_PCG, FETI_FO, FETI_RRS = 0, 1, 2
 FETI_FP64, FETI_TF32, FETI_TF32X3, FETI_BF16, FETI_BF16X3 = 0, 1, 2, 3, 4
+FETI_PRECOND_DIRICHLET, FETI_PRECOND_LUMPED, FETI_PRECOND_SUPERLUMPED = 0, 1, 2
 (FETI_Q_N_LAMBDA, FETI_Q_N_SUBDOMAINS, FETI_Q_N_PRIMAL, FETI_Q_N_MODULES, FETI_Q_N_B_TOTAL, FETI_Q_N_DOFS,
  FETI_Q_N_ELEMENTS, FETI_Q_MAX_NB, FETI_Q_DEVICE_BYTES, FETI_Q_N_RBM, FETI_Q_LAUNCHES, FETI_Q_N_PROBLEMS,
  FETI_Q_GEMV_CONFIG, FETI_Q_TC_BYTES_F, FETI_Q_TC_BYTES_PER_COL) = range(15)
@@ -43,7 +44,7 @@ class feti_options(ctypes.Structure):
     _fields_ = [("method", ctypes.c_int), ("scaling", ctypes.c_int), ("krylov", ctypes.c_int),
                 ("precision", ctypes.c_int), ("max_iter", ctypes.c_int), ("dedup_modules", ctypes.c_int),
                 ("tol", ctypes.c_double), ("rr_tol", ctypes.c_double), ("inner_tol", ctypes.c_double),
-                ("max_refine", ctypes.c_int), ("fp64_residual", ctypes.c_int)]
+                ("max_refine", ctypes.c_int), ("precond", ctypes.c_int), ("fp64_residual", ctypes.c_int)]
 
 
 class feti_problem(ctypes.Structure):
@@ -275,9 +276,11 @@ class Solver:
     """
 
     def __init__(self, method=FETI_FETIDP, scaling=FETI_SCALING_K, krylov=FETI_RRS, tol=1e-6, max_iter=500,
-                 rr_tol=1e-10, dedup=True, stream=None, precision=FETI_FP64, inner_tol=None, fp64_residual=False):
+                 rr_tol=1e-10, dedup=True, stream=None, precision=FETI_FP64, inner_tol=None, fp64_residual=False,
+                 precond=FETI_PRECOND_DIRICHLET):
         o = feti_options_default()
         o.method, o.scaling, o.krylov, o.precision = method, scaling, krylov, precision
+        o.precond = precond
         if inner_tol is not None:
             o.inner_tol = inner_tol
         o.fp64_residual = int(bool(fp64_residual))

@@ -358,6 +358,7 @@ feti_status feti_options_default(feti_options* opt) {
   opt->inner_tol = 0.0;                 // automatic (1e-2)
   opt->max_refine = 30;
   opt->fp64_residual = 0;
+  opt->precond = FETI_PRECOND_DIRICHLET;
   return FETI_OK;
 }
 
@@ -374,6 +375,7 @@ feti_status feti_create(feti_ctx** out, const feti_options* opt, void* stream) {
   if (o.precision < FETI_FP64 || o.precision > FETI_BF16X3) return FETI_EINVAL;
   if (o.precision != FETI_FP64 && !(o.inner_tol >= 0.0 && o.inner_tol < 1.0 && o.max_refine > 0)) return FETI_EINVAL;
   if (o.fp64_residual != 0 && o.fp64_residual != 1) return FETI_EINVAL;
+  if (o.precond < FETI_PRECOND_DIRICHLET || o.precond > FETI_PRECOND_SUPERLUMPED) return FETI_EINVAL;
   feti_ctx* ctx = new (std::nothrow) feti_ctx;
   if (!ctx) return FETI_ENOMEM;
   Ctx& c = ctx->c;
@@ -505,6 +507,8 @@ static feti_status setup_impl(Ctx& c, const feti_problem* probs, int n) {
     M.Frc = off; off = align32(off + (int64_t)T.n_b * T.n_c);
     M.Kb = off; off = align32(off + (int64_t)T.n_c * T.n_c);
     M.Rb = off; off = align32(off + (int64_t)T.n_b * hp.n_rbm);
+    M.Kl = -1;
+    if (c.opt.precond == FETI_PRECOND_LUMPED) { M.Kl = off; off = align32(off + (int64_t)T.n_b * T.n_b); }
     c.h_mods[m] = M;
   }
   c.modmem_len = off;
@@ -794,6 +798,7 @@ feti_status feti_factorize(feti_ctx* ctx) {
   CU(cudaMemsetAsync(c.d_modmem, 0, c.modmem_len * sizeof(double), st));
   CU(launch_assemble_with(c, c.d_E, st));
   CU(launch_gather_diag_b(c, st));
+  if (c.opt.precond == FETI_PRECOND_LUMPED) CU(launch_copy_kbb(c, st));   // K_bb before the Schur update
   CU(launch_scaling_weights(c, c.opt.scaling, st));
   // interior factor and Schur complement onto b + c
   CU(launch_band_chol(c, st));

@@ -109,8 +109,9 @@ __global__ void k_sub_gemv(const DevType* __restrict__ types, const DevModule* _
   const int lane = threadIdx.x & 31;
   const int n = T.n_b;
   if (row >= n) return;
-  const double* A = mem + (which == 0 ? M.F : M.S);
-  const int64_t ld = which == 0 ? n : (int64_t)(T.n_b + T.n_c);
+  // which: 0 F_s, 1 S_s (b-b block of the n_bc-wide Schur complement), 2 K_bb (lumped)
+  const double* A = mem + (which == 0 ? M.F : which == 1 ? M.S : M.Kl);
+  const int64_t ld = which == 1 ? (int64_t)(T.n_b + T.n_c) : n;
   const double* a = A + (int64_t)row * ld;
   const double* xs = x + S.b_off;
   double acc = 0.0;
@@ -295,8 +296,9 @@ __global__ void k_sub_gemv2(const DevType* __restrict__ types, const DevModule* 
   const int lane = threadIdx.x & 31;
   const int n = T.n_b;
   if (row >= n) return;
-  const double* A = mem + (which == 0 ? M.F : M.S);
-  const int64_t ld = which == 0 ? n : (int64_t)(T.n_b + T.n_c);
+  // which: 0 F_s, 1 S_s (b-b block of the n_bc-wide Schur complement), 2 K_bb (lumped)
+  const double* A = mem + (which == 0 ? M.F : which == 1 ? M.S : M.Kl);
+  const int64_t ld = which == 1 ? (int64_t)(T.n_b + T.n_c) : n;
   const double* a = A + (int64_t)row * ld;
   const double* xs = x + S.b_off;
   double acc = 0.0;
@@ -371,6 +373,30 @@ cudaError_t batched_gemv_F(Ctx& c, const double* xb, double* yb, cudaStream_t st
   return batched_gemv(c, 0, xb, yb, 0.0, st);
 }
 
+namespace {
+
+// zb = diag(K_bb) rb: the super-lumped local block (diagonal stiffness of each
+// interface copy, also the k-scaling weight source).
+__global__ void k_diag_mul(int64_t n, const double* __restrict__ d, const double* __restrict__ x,
+                           double* __restrict__ y) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i < n) y[i] = d[i] * x[i];
+}
+
+}  // namespace
+
+// zb = P_s rb per subdomain with the configured local block (Dirichlet S_s,
+// lumped K_bb or super-lumped diag K_bb).
+static cudaError_t local_precond_block(const Ctx& c, const double* rb, double* zb, cudaStream_t st) {
+  if (c.opt.precond == FETI_PRECOND_SUPERLUMPED) {
+    const int64_t nbt = c.hp.n_b_total;
+    k_diag_mul<<<(unsigned)((nbt + 255) / 256), 256, 0, st>>>(nbt, c.d_diagKb, rb, zb);
+    note_launches(1);
+    return cudaGetLastError();
+  }
+  return batched_gemv(c, c.opt.precond == FETI_PRECOND_LUMPED ? 2 : 1, rb, zb, 0.0, st);
+}
+
 cudaError_t precond_apply(Ctx& c, const double* r, double* Z, int64_t ldz, double* z, cudaStream_t st) {
   const int64_t nbt = c.hp.n_b_total, nl = c.hp.n_lam;
   double* rb = c.d_pb0;
@@ -380,7 +406,7 @@ cudaError_t precond_apply(Ctx& c, const double* r, double* Z, int64_t ldz, doubl
   note_launches(1);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
-  e = batched_gemv(c, 1, rb, zb, 0.0, st);
+  e = local_precond_block(c, rb, zb, st);
   if (e != cudaSuccess) return e;
   if (Z) {
     e = cudaMemsetAsync(Z, 0, sizeof(double) * (size_t)ldz * c.hp.n_sub, st);
@@ -402,7 +428,7 @@ cudaError_t precond_apply_scratch(const Ctx& c, const double* r, double* Z, int6
   note_launches(1);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
-  e = batched_gemv(c, 1, rb, zb, 0.0, st);
+  e = local_precond_block(c, rb, zb, st);
   if (e != cudaSuccess) return e;
   if (Z) {
     e = cudaMemsetAsync(Z, 0, sizeof(double) * (size_t)ldz * c.hp.n_sub, st);
@@ -452,6 +478,9 @@ cudaError_t corner_expand_thin(Ctx& c, const double* V, int m, double* Yb, cudaS
 }
 
 cudaError_t precond_apply_lowp(Ctx& c, const double* r, double* Z, int64_t ldz, double* z, cudaStream_t st) {
+  // the reduced-precision copy exists for the Dirichlet block only; the lumped
+  // blocks are cheap enough in FP64
+  if (c.opt.precond != FETI_PRECOND_DIRICHLET) return precond_apply(c, r, Z, ldz, z, st);
   const int64_t nbt = c.hp.n_b_total, nl = c.hp.n_lam;
   double* rb = c.d_pb0;
   double* zb = c.d_pb1;

@@ -121,6 +121,20 @@ __global__ void k_diag_b(const DevType* __restrict__ types, const DevModule* __r
   diagKb[S.b_off + k] = mem[M.S + (int64_t)k * nbc + k];
 }
 
+// Kl = K_bb, the interface block of the assembled local stiffness (held in
+// the S slot until the Schur update): the lumped preconditioner's block.
+__global__ void k_copy_kbb(const DevType* __restrict__ types, const DevModule* __restrict__ mods,
+                           double* __restrict__ mem) {
+  const DevModule M = mods[blockIdx.y];
+  const DevType T = types[M.type];
+  const int n = T.n_b, nbc = T.n_b + T.n_c;
+  const int64_t total = (int64_t)n * n;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+    const int i = (int)(e / n), j = (int)(e % n);
+    mem[M.Kl + e] = mem[M.S + (int64_t)i * nbc + j];
+  }
+}
+
 // Eq. (15) with summed denominators (k-scaling) or 1/multiplicity.
 __global__ void k_weights(int64_t n_lam, const int* __restrict__ b0, const int* __restrict__ b1,
                           const int* __restrict__ grp, const int* __restrict__ goff,
@@ -291,6 +305,12 @@ cudaError_t launch_gather_diag_b(const Ctx& c, cudaStream_t st) {
   for (auto& t : c.h_types) maxb = std::max(maxb, t.n_b);
   dim3 grid((maxb + 127) / 128, c.hp.n_sub);
   k_diag_b<<<grid, 128, 0, st>>>(c.d_types, c.d_mods, c.d_subs, c.d_modmem, c.d_diagKb);
+  note_launches(1);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_copy_kbb(const Ctx& c, cudaStream_t st) {
+  k_copy_kbb<<<dim3(32, c.n_mod), 256, 0, st>>>(c.d_types, c.d_mods, c.d_modmem);
   note_launches(1);
   return cudaGetLastError();
 }

@@ -137,6 +137,7 @@ struct DevModule {
   int64_t Frc;                   // [n_b x n_c] row-major (FETI-DP)
   int64_t Kb;                    // [n_c x n_c] local Kbar_cc (FETI-DP)
   int64_t Rb;                    // [n_b x n_rbm] orthonormal rigid modes on b (TFETI)
+  int64_t Kl;                    // [n_b x n_b] row-major K_bb (lumped preconditioner; -1 if unused)
 };
 
 // Per-subdomain device info.

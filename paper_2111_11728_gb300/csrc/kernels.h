@@ -58,6 +58,7 @@ void element_stiffness_host(int dim, double nu, double* k0);
 cudaError_t launch_moduli(const Ctx& c, double* E, cudaStream_t st);
 cudaError_t launch_assemble_with(const Ctx& c, const double* E, cudaStream_t st);
 cudaError_t launch_gather_diag_b(const Ctx& c, cudaStream_t st);
+cudaError_t launch_copy_kbb(const Ctx& c, cudaStream_t st);   // K_bb for the lumped preconditioner
 cudaError_t launch_scaling_weights(const Ctx& c, int kind, cudaStream_t st);
 cudaError_t launch_load_gather(const Ctx& c, cudaStream_t st);
 cudaError_t launch_gather_u(const Ctx& c, cudaStream_t st);
