@@ -15,6 +15,15 @@ second over the whole step ("F-applies/s"); time-to-solve is reported beside
 it.  ``e2e`` repeats the step through the public API from host buffers
 (set-up with host->device copies, result copied back).
 
+Beside the headline (rank 0, one GPU), the line carries:
+  ``forms``      the precision forms (TF32 / BF16 block products, one pass or split,
+                 FP64 refinement) against FP64 at equal accuracy on the same layout at
+                 contrast 1e3: time to solve, apply time, tensor-core roofline;
+  ``apply_3d``   the dual-operator apply of 512 directions on the 3D workload (8^3
+                 subdomains of 8^3 H8) in every precision, with rooflines;
+  ``batch_form`` 64 uneven problems in one context against one context per problem;
+  ``forms_3d``   (``--forms-3d``, minutes) the precision forms' time to solve in 3D.
+
 ``--impl reference`` times the FP64 CPU oracle on a bounded sample of the
 same workload instead (rank 0 only).
 """

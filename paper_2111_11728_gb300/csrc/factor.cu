@@ -19,7 +19,15 @@ namespace {
 
 constexpr int NT = 256;
 
-// Right-looking banded Cholesky in the column band (Lcol[j*W + t] = L(j+t, j)).
+// Banded Cholesky in the column band (Lcol[j*W + t] = L(j+t, j)), blocked by
+// panels of BC_PB columns.  Warp 0 factors a panel (each column first takes the
+// panel's earlier columns, then its pivot); then all warps apply the panel's
+// rank-BC_PB update to the band columns that follow it.  Every entry receives
+// the updates of the columns before it in ascending column order, as in the
+// unblocked right-looking elimination, so the factor is the same bit for bit;
+// the block-wide barriers drop from three per column to two per panel.
+constexpr int BC_PB = 8;
+
 __global__ void __launch_bounds__(NT) k_band_chol(const DevType* __restrict__ types,
                                                   const DevModule* __restrict__ mods, double* __restrict__ mem,
                                                   int* __restrict__ status) {
@@ -27,40 +35,62 @@ __global__ void __launch_bounds__(NT) k_band_chol(const DevType* __restrict__ ty
   const DevType T = types[M.type];
   const int n = T.n_i, bw = T.bw, W = bw + 1;
   double* L = mem + M.lcol;
-  extern __shared__ double col[];
-  __shared__ double s_dj, s_rd;
   __shared__ int s_ok;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  for (int j = 0; j < n; ++j) {
-    const int len = min(bw, n - 1 - j);
-    // one thread takes the pivot's square root and reciprocal (FP64 work is
-    // scarce on this part; 256 threads repeating it cost more than the update)
-    if (tid == 0) {
-      const double piv = L[(int64_t)j * W];
-      s_ok = piv > 0.0;
-      if (s_ok) {
-        s_dj = sqrt(piv);
-        s_rd = 1.0 / s_dj;
+  if (tid == 0) s_ok = 1;
+  __syncthreads();
+  for (int p0 = 0; p0 < n; p0 += BC_PB) {
+    const int pw = min(BC_PB, n - p0);
+    if (warp == 0) {
+      for (int j = p0; j < p0 + pw; ++j) {
+        const int len = min(bw, n - 1 - j);
+        // updates from the panel's earlier columns k (ascending): L(j+t, j) -= L(j+t, k) L(j, k)
+        for (int k = max(p0, j - bw); k < j; ++k) {   // L(j, k) = 0 outside the band
+          const double ljk = L[(int64_t)k * W + (j - k)];
+          for (int t = lane; t <= len; t += 32) {
+            const int off = j + t - k;               // row j+t in column k
+            if (off <= bw) L[(int64_t)j * W + t] = fma(-ljk, L[(int64_t)k * W + off], L[(int64_t)j * W + t]);
+          }
+          __syncwarp();
+        }
+        double dj = 0.0, rd = 0.0;
+        int ok = 1;
+        if (lane == 0) {
+          const double piv = L[(int64_t)j * W];
+          ok = piv > 0.0;
+          if (ok) {
+            dj = sqrt(piv);
+            rd = 1.0 / dj;
+          }
+        }
+        ok = __shfl_sync(0xffffffffu, ok, 0);
+        if (!ok) {
+          if (lane == 0) {
+            s_ok = 0;
+            atomicCAS(status, 0, 1000000 + blockIdx.x);
+          }
+          break;
+        }
+        dj = __shfl_sync(0xffffffffu, dj, 0);
+        rd = __shfl_sync(0xffffffffu, rd, 0);
+        for (int t = lane; t <= len; t += 32) L[(int64_t)j * W + t] = t == 0 ? dj : L[(int64_t)j * W + t] * rd;
+        __syncwarp();
       }
     }
-    __syncthreads();   // the pivot is read before column j is overwritten
-    if (!s_ok) {
-      if (tid == 0) atomicCAS(status, 0, 1000000 + blockIdx.x);
-      return;
-    }
-    const double dj = s_dj, rd = s_rd;
-    for (int t = tid; t <= len; t += NT) {
-      const double v = t == 0 ? dj : L[(int64_t)j * W + t] * rd;
-      col[t] = v;
-      L[(int64_t)j * W + t] = v;
-    }
     __syncthreads();
-    // trailing band: L(j+b, j+a) -= L(j+b, j) L(j+a, j) for 1 <= a <= b <= len,
-    // stored at Lcol[(j+a) W + (b-a)]; a warp per a, lanes over b
-    for (int a = 1 + warp; a <= len; a += NT / 32) {
-      const double ca = col[a];
-      double* row = L + (int64_t)(j + a) * W - a;
-      for (int b = a + lane; b <= len; b += 32) row[b] = fma(-ca, col[b], row[b]);
+    if (!s_ok) return;
+    // rank-pw update of band columns l in [p0+pw, p0+pw-1+bw]: for i >= l,
+    // L(i, l) -= sum_k L(i, k) L(l, k) over the panel columns k (ascending)
+    const int c0 = p0 + pw, c1 = min(n - 1, p0 + pw - 1 + bw);
+    for (int l = c0 + warp; l <= c1; l += NT / 32) {
+      const int imax = min(c1, l + bw);
+      for (int i = l + lane; i <= imax; i += 32) {
+        double acc = L[(int64_t)l * W + (i - l)];
+        for (int k = p0; k < p0 + pw; ++k) {
+          if (i - k <= bw && l - k <= bw) acc = fma(-L[(int64_t)k * W + (l - k)], L[(int64_t)k * W + (i - k)], acc);
+        }
+        L[(int64_t)l * W + (i - l)] = acc;
+      }
     }
     __syncthreads();
   }
