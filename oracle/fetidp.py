@@ -17,9 +17,23 @@ Eq. 12) the dual problem on lambda alone:
     (F_rr + F_rc Kbar_cc^{-1} F_rc^T) lambda = d_r - F_rc Kbar_cc^{-1} fbar_c.
 
 Readings:
-* Primal set: every non-fixed DOF at a vertex of the tile grid ("corner nodes
-  in a regular subdomain partitioning", Section 2.2), including vertices on
-  the outer boundary.
+* Primal set: every non-fixed DOF at a vertex of the tile grid (the corner
+  nodes of the regular partition, Section 2.2), including vertices on the
+  outer boundary.
+* Optional richer primal set (primal="edges"; the paper names richer and
+  adaptive primal sets as future work, Section 5): in addition, one average
+  per component over the interior nodes of every tile-grid edge shared by two
+  or more subdomains (3D: the edges of the tiles; 2D: their sides) whose
+  nodes are all free in that component.  It is introduced by a change of
+  basis on each such edge with nodes e_1 .. e_n (ordered by the global
+  coordinate along the edge): the new variables are the average ubar (stored
+  in the slot of e_1) and the fluctuations v_j (j >= 2, in the slots of e_j),
+  u_{e_1} = ubar - sum_j v_j,  u_{e_j} = ubar + v_j,  so u = T u^ with T
+  identical on every sharer.  K^s and f^s are replaced by T^T K^s T and
+  T^T f^s; ubar joins the primal DOFs (global, one per edge and component)
+  and the fluctuations keep the pair-wise rows of B_r; the recovered u^ is
+  mapped back by T.  The k-scaling weights use the diagonal of the
+  untransformed K^s.
 * The printed fbar_c carries the index "kk" on K^{-1}; it is read as K_rr.
 * Fixed (Dirichlet) DOFs are eliminated from K^s; FETI-DP has no c-vector.
 * K_rr^{-1} is only ever needed on the DOFs that B_r touches (the "b" DOFs)
@@ -62,11 +76,43 @@ class _Module:
         self.Kbb = self.Krr[np.ix_(b_in_r, b_in_r)]                    # lumped: K_bb instead of S
 
 
+PRIMALS = ("corners", "edges")
+
+
+def edge_averages(problem, mesh):
+    """The averaged edges of the primal="edges" reading: a list of
+    (nodes along the edge in increasing coordinate, component), one entry per
+    edge and free component, for every tile-grid edge (nodes with exactly
+    dim - 1 coordinates on tile-grid planes) shared by two or more subdomains."""
+    dim = problem.dim
+    coords = mesh.node_coords()
+    edges = {}
+    for gn in range(mesh.n_nodes):
+        ijk = coords[gn]
+        on = [ijk[a] % mesh.elems[a] == 0 for a in range(dim)]
+        if sum(on) != dim - 1 or len(mesh.owners[gn]) < 2:
+            continue
+        run = on.index(False)
+        start = list(ijk)
+        start[run] -= ijk[run] % mesh.elems[run]
+        edges.setdefault((run, tuple(start)), []).append((int(ijk[run]), gn))
+    out = []
+    for key in sorted(edges):
+        nodes = [gn for _, gn in sorted(edges[key])]
+        for d in range(dim):
+            if not any(problem.dirichlet[gn * dim + d] for gn in nodes):
+                out.append((nodes, d))
+    return out
+
+
 class FETIDP:
-    def __init__(self, problem, scaling="k", dedup=True, precond="dirichlet"):
+    def __init__(self, problem, scaling="k", dedup=True, precond="dirichlet", primal="corners"):
         if precond not in PRECONDS:
             raise ValueError(precond)
+        if primal not in PRIMALS:
+            raise ValueError(primal)
         self.precond = precond
+        self.primal_set = primal
         self.problem = problem
         mesh = self.mesh = mesh_of(problem)
         dim = self.dim = problem.dim
@@ -80,6 +126,12 @@ class FETIDP:
             for d in range(dim):
                 if not problem.dirichlet[gn * dim + d]:
                     self.primal[gn * dim + d] = len(self.primal)
+        # edge averages: the primal unknown sits in the slot of the first edge node
+        self.edges = edge_averages(problem, mesh) if primal == "edges" else []
+        avg_dofs = set()
+        for nodes, d in self.edges:
+            self.primal[nodes[0] * dim + d] = len(self.primal)
+            avg_dofs.add(nodes[0] * dim + d)
         self.n_c = len(self.primal)
         # --- per-subdomain split (Eq. 8) ---
         self.r_loc, self.c_loc, self.c_glob = [], [], []
@@ -88,6 +140,7 @@ class FETIDP:
         self.mod_key = []
         self.modules = {}
         Ks_cache = {}
+        self.T = []
         for s in range(ns):
             Ks = local_stiffness(problem, mesh, s, k0, E)
             fs = local_load(problem, mesh, s)
@@ -95,6 +148,23 @@ class FETIDP:
             g2 = mesh.local_to_global_nodes(s)
             is_corner = np.repeat(np.array([mesh.is_tile_vertex(g) for g in g2]), dim)
             gdofs = (g2[:, None] * dim + np.arange(dim)[None, :]).ravel()
+            self.diagK.append(np.diag(Ks).copy())          # weights from the untransformed K^s
+            Ts = None
+            if self.edges:
+                loc_of = {int(g): ln for ln, g in enumerate(g2)}
+                Ts = np.eye(mesh.n_loc_dofs)
+                for nodes, d in self.edges:
+                    if nodes[0] not in loc_of:
+                        continue
+                    l1 = loc_of[nodes[0]] * dim + d
+                    for gn in nodes[1:]:
+                        lj = loc_of[gn] * dim + d
+                        Ts[l1, lj] = -1.0
+                        Ts[lj, l1] = 1.0
+                    is_corner[l1] = True                   # the average joins the primal set
+                Ks = Ts.T @ Ks @ Ts
+                fs = Ts.T @ fs
+            self.T.append(Ts)
             r_loc = np.flatnonzero(~fixed & ~is_corner)
             c_loc = np.flatnonzero(~fixed & is_corner)
             self.r_loc.append(r_loc)
@@ -102,7 +172,6 @@ class FETIDP:
             self.c_glob.append(np.array([self.primal[g] for g in gdofs[c_loc]], dtype=np.int64))
             self.f_r.append(fs[r_loc])
             self.f_c.append(fs[c_loc])
-            self.diagK.append(np.diag(Ks).copy())
             Ks_cache[s] = Ks
         # --- B_r rows (Eq. 10): pair-wise rows at shared non-corner, non-fixed DOFs ---
         pos_in_r = []
@@ -116,7 +185,7 @@ class FETIDP:
             if len(own) < 2 or mesh.is_tile_vertex(gn):
                 continue
             for d in range(dim):
-                if problem.dirichlet[gn * dim + d]:
+                if problem.dirichlet[gn * dim + d] or gn * dim + d in avg_dofs:
                     continue
                 copies = [(s, ln * dim + d) for (s, ln) in own]
                 for row in pairwise_rows(copies):
@@ -233,6 +302,8 @@ class FETIDP:
             u = np.zeros(self.mesh.n_loc_dofs)
             u[self.r_loc[s]] = ur
             u[self.c_loc[s]] = ucs
+            if self.T[s] is not None:
+                u = self.T[s] @ u                          # back to nodal values
             us.append(u)
         return us, uc
 

@@ -34,6 +34,7 @@ import numpy as np
 __all__ = [
     "Problem", "tile_problem", "gaussian_field", "binary_patterns",
     "config1", "config2", "config3", "config4", "config5",
+    "layered_beam", "layered_grid", "inclusion_grid",
 ]
 
 
@@ -119,6 +120,20 @@ def tile_problem(name, dim, tiles, elems, rho, *, bc="clamped_left", E0=1.0,
                     n = nid(0, j, k)
                     dmask[3 * n:3 * n + 3] = 1
             f[3 * nid(nn[0] - 1, (nn[1] - 1) // 2, (nn[2] - 1) // 2) + 2] = -1.0
+    elif bc == "traction_right":
+        # clamped x = 0 edge; uniform traction on the x = max edge with a unit
+        # tensile normal (+x) and a unit tangential (-y) resultant, lumped to
+        # the edge nodes by the trapezoidal rule (end nodes carry half)
+        assert dim == 2
+        for j in range(nn[1]):
+            n = nid(0, j)
+            dmask[2 * n:2 * n + 2] = 1
+        h = 1.0 / (nn[1] - 1)
+        for j in range(nn[1]):
+            w = h * (0.5 if j in (0, nn[1] - 1) else 1.0)
+            n = nid(nn[0] - 1, j)
+            f[2 * n] += w
+            f[2 * n + 1] -= w
     elif bc == "mbb":
         assert dim == 2
         for n in (nid(0, 0), nid(nn[0] - 1, 0)):
@@ -218,3 +233,53 @@ def config5(tiles: int = 32, elems: int = 64, volfrac: float = 0.4) -> Problem:
     rho = np.full(n * n, volfrac)
     return tile_problem(f"MBB beam {tiles}x{tiles} tiles of {elems}x{elems}", 2, (tiles, tiles),
                         (elems, elems), rho, bc="mbb", Emin=1e-6)
+
+
+# ---- stand-ins for the academic problems of Section 4 ---------------------------
+# Regular partitions built from the prose only (the figure with the geometry and
+# the material values is not available): element moduli E = rho (p = 1, Emin = 0)
+# with rho in {contrast^-1, 1}; clamped left edge, tensile and tangential
+# traction on the right edge.
+
+def _layers(elems: int, layers: int, contrast: float) -> np.ndarray:
+    """One square module of ``layers`` horizontal laminae (stiff, compliant, ...)."""
+    y = (np.arange(elems) + 0.5) / elems
+    lam = np.minimum((y * layers).astype(int), layers - 1)
+    row = np.where(lam % 2 == 0, 1.0, 1.0 / contrast)
+    return np.tile(row[None, :], (elems, 1))          # axis 0 = x
+
+
+def _inclusion(elems: int, frac: float, contrast: float) -> np.ndarray:
+    """A compliant square module with a centred stiff square inclusion of side frac * elems."""
+    c = (np.arange(elems) + 0.5) / elems
+    inside = np.abs(c - 0.5) < frac / 2
+    return np.where(inside[:, None] & inside[None, :], 1.0, 1.0 / contrast)
+
+
+def _academic(name, tiles, elems, module, contrast):
+    rho = _assemble_tiles([module] * (tiles[0] * tiles[1]), tiles, (elems, elems))
+    return tile_problem(name, 2, tiles, (elems, elems), rho, bc="traction_right", E0=1.0, Emin=0.0, p=1.0)
+
+
+def layered_beam(elems: int = 14, layers: int = 7, contrast: float = 1e3, n: int = 9) -> Problem:
+    """A beam of ``n`` square subdomains in a row, each of ``layers`` alternating
+    stiff / compliant laminae running along the beam (the jumps reach every
+    interface)."""
+    return _academic(f"laminated beam 1x{n}, {layers} layers, contrast {contrast:g}", (n, 1), elems,
+                     _layers(elems, layers, contrast), contrast)
+
+
+def layered_grid(elems: int = 16, layers: int = 8, contrast: float = 1e3, n: int = 3) -> Problem:
+    """An n x n grid of the same laminated modules (interior cross points).  With
+    an even number of laminae a module starts stiff and ends compliant, so the
+    horizontal interfaces and the cross points join a compliant lamina to a
+    stiff one."""
+    return _academic(f"laminated {n}x{n} grid, {layers} layers, contrast {contrast:g}", (n, n), elems,
+                     _layers(elems, layers, contrast), contrast)
+
+
+def inclusion_grid(elems: int = 16, frac: float = 0.5, contrast: float = 1e3, n: int = 4) -> Problem:
+    """An n x n grid of compliant modules, each with a centred stiff inclusion
+    (homogeneous material along every interface)."""
+    return _academic(f"{n}x{n} grid with stiff inclusions, contrast {contrast:g}", (n, n), elems,
+                     _inclusion(elems, frac, contrast), contrast)
