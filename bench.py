@@ -21,8 +21,12 @@ Beside the headline (rank 0, one GPU), the line carries:
                  contrast 1e3: time to solve, apply time, tensor-core roofline;
   ``apply_3d``   the dual-operator apply of 512 directions on the 3D workload (8^3
                  subdomains of 8^3 H8) in every precision, with rooflines;
-  ``batch_form`` 64 uneven problems in one context against one context per problem;
-  ``forms_3d``   (``--forms-3d``, minutes) the precision forms' time to solve in 3D.
+  ``batch_form`` 64 uneven problems in one context against one context per problem (PCG);
+  ``batch_form_rrs`` the same with Algorithm 1, a block of directions per problem;
+  ``academic``   the 12 variants on stand-ins for the paper's academic problems;
+  ``phases``     time share and roofline fraction of every phase of the timed step;
+  ``forms_3d``   (``--forms-3d``, minutes) the precision forms' time to solve in 3D;
+  ``primal_3d``  (``--primal-3d``, minutes) corners against corners + edge averages in 3D.
 
 ``--impl reference`` times the FP64 CPU oracle on a bounded sample of the
 same workload instead (rank 0 only).
@@ -57,6 +61,35 @@ def tensor_peaks():
     except (OSError, KeyError, ValueError):
         bf16, hbm, src = 1900.0, 6800.0, "fallback"
     return {"bf16": bf16, "tf32": bf16 * 1.1 / 2.25, "hbm_gbs": hbm, "source": src}
+
+
+PHASE_BOUND = {"apply": "alu", "gram": "alu", "ortho": "alu", "precond": "hbm", "project": "hbm", "step": "hbm",
+               "factor": None, "recover": None}
+
+
+def phase_rooflines(prof, steps, t_steps):
+    """Per phase of the timed steps (regions bracketed by CUDA events on the
+    library's stream): time per step, share of the step, and against its own
+    roofline the algorithmic rate -- FP64 TFLOP/s for the FP64-pipe phases
+    (peak derived from the SM count and clock), GB/s for the memory-bound ones
+    (measured copy bandwidth)."""
+    hbm = tensor_peaks()["hbm_gbs"]
+    out = {}
+    for name, (work, ms, n) in prof.items():
+        if not n:
+            continue
+        row = {"ms_per_step": ms / steps, "share_of_step": (ms / 1e3) / t_steps if t_steps > 0 else None,
+               "regions": n}
+        bound = PHASE_BOUND[name]
+        if bound == "alu" and work > 0 and ms > 0:
+            ach = work / (ms / 1e3) / 1e12
+            row.update({"bound": "alu", "achieved": ach, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                        "frac": ach / FP64_PEAK_TFLOPS})
+        elif bound == "hbm" and work > 0 and ms > 0:
+            ach = work / (ms / 1e3) / 1e9
+            row.update({"bound": "hbm", "achieved": ach, "peak": hbm, "unit": "GB/s", "frac": ach / hbm})
+        out[name] = row
+    return out
 
 
 def tensor_roofline(fg, s, prec, m):
@@ -104,6 +137,11 @@ def parse():
     ap.add_argument("--tiles-3d", type=int, default=8)
     ap.add_argument("--batch-problems", type=int, default=64)
     ap.add_argument("--batch-max-iter", type=int, default=500)
+    ap.add_argument("--batch-rrs-max-iter", type=int, default=60)
+    ap.add_argument("--batch-krylov", default="both", choices=["pcg", "rrs", "both"])
+    ap.add_argument("--no-academic", action="store_true")
+    ap.add_argument("--primal-3d", action="store_true",
+                    help="also compare corners with corners + edge averages on the 3D workload (minutes)")
     return ap.parse_args()
 
 
@@ -313,6 +351,49 @@ def compare_forms_3d(a, fg, torch, dev, stream, flush):
     return out
 
 
+def compare_primal_3d(a, fg, torch, dev, stream, flush):
+    """The richer FETI-DP primal set on the 3D workload (8^3 subdomains of 8^3
+    H8): corners only against corners plus edge averages, both FP64 FETI-DP +
+    k-scaling with PCG and with the simultaneous variant at the same relative
+    dual residual: iterations, coarse size and time to solve (factorize +
+    solve + recover); displacements compared with each other."""
+    p = workloads.config4(tiles=a.tiles_3d, elems=8)
+    rho_d = torch.from_numpy(p.rho).to(dev)
+    f_d = torch.from_numpy(p.f).to(dev)
+    out = {"workload": f"3D H8: {a.tiles_3d}^3 subdomains of 8^3 elements, smoothed field in [1e-3, 1]",
+           "rel_tol": a.tol}
+    sols = {}
+    for kname, krylov, cap in (("rrs", fg.FETI_RRS, 60), ("pcg", fg.FETI_PCG, 2000)):
+        for pname, primal in (("corners", fg.FETI_PRIMAL_CORNERS), ("edges", fg.FETI_PRIMAL_EDGES)):
+            s = fg.Solver(fg.FETI_FETIDP, fg.FETI_SCALING_K, krylov, tol=a.tol, max_iter=cap,
+                          stream=stream.cuda_stream, primal=primal)
+            s.setup(p, rho=rho_d, f=f_d, on_device=True)
+            u = torch.empty(p.n_dofs, dtype=torch.float64, device=dev)
+            flush.zero_()
+            torch.cuda.synchronize()
+            e = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+            e[0].record(stream)
+            fg.feti_factorize(s.ctx)
+            e[1].record(stream)
+            _, st = fg.feti_solve_dual(s.ctx, allow_notconv=True)
+            fg.feti_recover_displacements(s.ctx, u, True)
+            e[2].record(stream)
+            torch.cuda.synchronize()
+            sols[kname, pname] = u.cpu().numpy()
+            out[f"{kname}/{pname}"] = {"iterations": st.iterations, "converged": bool(st.converged),
+                                       "f_applies": st.f_applies, "n_primal": s.query(fg.FETI_Q_N_PRIMAL),
+                                       "n_lambda": s.query(fg.FETI_Q_N_LAMBDA),
+                                       "factorize_ms": e[0].elapsed_time(e[1]),
+                                       "solve_and_recover_ms": e[1].elapsed_time(e[2]),
+                                       "time_to_solve_ms": e[0].elapsed_time(e[2])}
+            s.close()
+        c, g = out[f"{kname}/corners"], out[f"{kname}/edges"]
+        g["speedup_time_to_solve"] = c["time_to_solve_ms"] / g["time_to_solve_ms"]
+        ref = sols[kname, "corners"]
+        g["rel_diff_vs_corners"] = float(np.linalg.norm(sols[kname, "edges"] - ref) / np.linalg.norm(ref))
+    return out
+
+
 def apply_rooflines_3d(a, fg, torch, dev, stream, flush, m=512):
     """The dual-operator block apply on the 3D workload (8^3 subdomains of 8^3
     H8, 512 directions) in every precision: apply time and, for the
@@ -347,14 +428,17 @@ def apply_rooflines_3d(a, fg, torch, dev, stream, flush, m=512):
     return out
 
 
-def compare_batch(a, fg, torch, dev, stream):
+def compare_batch(a, fg, torch, dev, stream, krylov="pcg"):
     """The batching form: the uneven multi-problem workload (tile grids drawn
     from 4x4..24x24 subdomains of 16x16..48x48 elements, thresholded smoothed
     Gaussian densities, Emin 1e-6) solved in one context -- every launch covers
-    all problems, one PCG per problem advanced by a replayed CUDA graph --
-    against the same problems solved one context at a time, both FETI-DP +
-    k-scaling + PCG in FP64 at the same relative dual residual."""
+    all problems: one PCG per problem advanced by a replayed CUDA graph
+    (krylov "pcg"), or Algorithm 1 with one direction per subdomain of each
+    problem (krylov "rrs") -- against the same problems solved one context at
+    a time with the same variant, all FETI-DP + k-scaling in FP64 at the same
+    relative dual residual and iteration cap."""
     probs = workloads.config3(n_problems=a.batch_problems)
+    max_iter = a.batch_max_iter if krylov == "pcg" else a.batch_rrs_max_iter
     keep, structs = [], []
     for p in probs:
         rho = torch.from_numpy(p.rho).to(dev)
@@ -365,8 +449,8 @@ def compare_batch(a, fg, torch, dev, stream):
 
     def opts():
         o = fg.feti_options_default()
-        o.method, o.scaling, o.krylov, o.tol, o.max_iter = (fg.FETI_FETIDP, fg.FETI_SCALING_K, fg.FETI_PCG, a.tol,
-                                                            a.batch_max_iter)
+        o.method, o.scaling, o.tol, o.max_iter = fg.FETI_FETIDP, fg.FETI_SCALING_K, a.tol, max_iter
+        o.krylov = fg.FETI_PCG if krylov == "pcg" else fg.FETI_RRS
         return o
 
     def ev():
@@ -375,7 +459,8 @@ def compare_batch(a, fg, torch, dev, stream):
     n_dofs = sum(p.n_dofs for p in probs)
     out = {"workload": f"{len(probs)} uneven 2D Q4 problems, {n_dofs} DOF, "
                        f"{sum(p.tiles[0] * p.tiles[1] for p in probs)} subdomains", "rel_tol": a.tol,
-           "max_iter": a.batch_max_iter}
+           "krylov": {"pcg": "PCG", "rrs": "simultaneous FETI (Algorithm 1), one direction per subdomain"}[krylov],
+           "max_iter": max_iter}
     # batched: one context
     ctx = fg.feti_create(opts(), stream.cuda_stream)
     t0 = time.perf_counter()
@@ -400,13 +485,14 @@ def compare_batch(a, fg, torch, dev, stream):
                       "total_ms": e[0].elapsed_time(e[2]), "host_setup_s": setup_s,
                       "iterations_max": max(its), "iterations_sum": sum(its),
                       "converged": all(conv_b), "problems_converged": sum(conv_b),
-                      "f_applies_per_s": sum(its) / (e[1].elapsed_time(e[2]) / 1e3)}
+                      "f_applies": sum(r[3].f_applies for r in res),
+                      "f_applies_per_s": sum(r[3].f_applies for r in res) / (e[1].elapsed_time(e[2]) / 1e3)}
     out["batched"]["problems_per_s"] = len(probs) / (out["batched"]["total_ms"] / 1e3)
     u_b = u_b.cpu().numpy()
     offs = [r[0] for r in res]
     fg.feti_destroy(ctx)
     # one context per problem, solved in turn
-    fact_ms, solve_ms, its1, worst, worst_conv, conv1 = 0.0, 0.0, [], 0.0, 0.0, []
+    fact_ms, solve_ms, its1, fap1, worst, worst_conv, conv1 = 0.0, 0.0, [], [], 0.0, 0.0, []
     for q, p in enumerate(probs):
         c1 = fg.feti_create(opts(), stream.cuda_stream)
         fg.feti_setup_batch(c1, [structs[q]])
@@ -424,6 +510,7 @@ def compare_batch(a, fg, torch, dev, stream):
         fact_ms += e[0].elapsed_time(e[1])
         solve_ms += e[1].elapsed_time(e[2])
         its1.append(st1.iterations)
+        fap1.append(st1.f_applies)
         conv1.append(bool(st1.converged))
         uq = u1.cpu().numpy()
         d = float(np.linalg.norm(u_b[offs[q]:offs[q] + p.n_dofs] - uq) / np.linalg.norm(uq))
@@ -433,13 +520,49 @@ def compare_batch(a, fg, torch, dev, stream):
         fg.feti_destroy(c1)
     out["one_at_a_time"] = {"factorize_ms": fact_ms, "solve_and_recover_ms": solve_ms, "total_ms": fact_ms + solve_ms,
                             "iterations_max": max(its1), "iterations_sum": sum(its1),
-                            "problems_converged": sum(conv1),
-                            "f_applies_per_s": sum(its1) / (solve_ms / 1e3),
+                            "problems_converged": sum(conv1), "f_applies": sum(fap1),
+                            "f_applies_per_s": sum(fap1) / (solve_ms / 1e3),
                             "problems_per_s": len(probs) / ((fact_ms + solve_ms) / 1e3)}
     out["max_rel_diff_batched_vs_single"] = worst
     out["max_rel_diff_batched_vs_single_converged"] = worst_conv
     out["speedup_total"] = out["one_at_a_time"]["total_ms"] / out["batched"]["total_ms"]
     out["speedup_solve"] = out["one_at_a_time"]["solve_and_recover_ms"] / out["batched"]["solve_and_recover_ms"]
+    return out
+
+
+def compare_academic(a, fg, torch, dev, stream):
+    """Stand-ins for the academic problems of Section 4 (laminated beam of 9
+    subdomains, laminated 3x3 grid, 4x4 grid of stiff inclusions; 14x14 or 16x16
+    elements per subdomain, contrast 1e3, clamped left, traction on the right):
+    iterations and GPU time to solve of the 12 variants at relative residual
+    1e-6 (the paper's convergence comparison of these problems)."""
+    probs = {"laminated_beam_1x9": workloads.layered_beam(), "laminated_grid_3x3": workloads.layered_grid(),
+             "inclusions_4x4": workloads.inclusion_grid()}
+    out = {"rel_tol": a.tol, "contrast": 1e3}
+    for name, p in probs.items():
+        rho = torch.from_numpy(p.rho).to(dev)
+        f = torch.from_numpy(p.f).to(dev)
+        u = torch.empty(p.n_dofs, dtype=torch.float64, device=dev)
+        rows = {}
+        for mname, method in (("tfeti", fg.FETI_TFETI), ("fetidp", fg.FETI_FETIDP)):
+            for sname, scaling in (("k", fg.FETI_SCALING_K), ("mult", fg.FETI_SCALING_MULT)):
+                for kname, krylov in (("pcg", fg.FETI_PCG), ("fo", fg.FETI_FO), ("rrs", fg.FETI_RRS)):
+                    s = fg.Solver(method, scaling, krylov, tol=a.tol, max_iter=400, stream=stream.cuda_stream)
+                    s.setup(p, rho=rho, f=f, on_device=True)
+                    for rep in range(2):            # the second run is timed
+                        torch.cuda.synchronize()
+                        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                        e0.record(stream)
+                        fg.feti_factorize(s.ctx)
+                        _, st = fg.feti_solve_dual(s.ctx, allow_notconv=True)
+                        fg.feti_recover_displacements(s.ctx, u, True)
+                        e1.record(stream)
+                        torch.cuda.synchronize()
+                    rows[f"{mname}/{sname}/{kname}"] = {"iterations": st.iterations, "converged": bool(st.converged),
+                                                        "f_applies": st.f_applies,
+                                                        "time_to_solve_ms": e0.elapsed_time(e1)}
+                    s.close()
+        out[name] = {"dofs": p.n_dofs, "subdomains": p.n_subdomains, "variants": rows}
     return out
 
 
@@ -492,6 +615,7 @@ def run_ours(a, rank, world):
     torch.cuda.synchronize()
     wall = time.perf_counter() - t_wall0
     gf, gms, gn = fg.feti_profile_end(s.ctx)
+    phase_prof = fg.feti_profile_phases(s.ctx)
     launches = fg.feti_query(s.ctx, fg.FETI_Q_LAUNCHES) - l0
     if world > 1:
         torch.distributed.barrier()
@@ -499,6 +623,7 @@ def run_ours(a, rank, world):
     clk = clocks.stop()
     step_ms = [e0.elapsed_time(e1) for e0, e1 in ev]
     t_steps = sum(step_ms) / 1e3
+    phases = phase_rooflines(phase_prof, a.steps, t_steps)
     # max over ranks
     t_steps, applies_total = aggregate_replicas(t_steps, applies, world, dev)
     value = applies_total / t_steps
@@ -569,9 +694,21 @@ def run_ours(a, rank, world):
     forms3d = None
     if a.forms_3d and world == 1:
         forms3d = compare_forms_3d(a, fg, torch, dev, stream, flush)
-    batch = None
+    primal3d = None
+    if a.primal_3d and world == 1:
+        primal3d = compare_primal_3d(a, fg, torch, dev, stream, flush)
+    academic = None
+    if not a.no_academic and world == 1:
+        academic = compare_academic(a, fg, torch, dev, stream)
+    batch = batch_rrs = None
     if not a.no_batch and world == 1:
-        batch = compare_batch(a, fg, torch, dev, stream)
+        if a.batch_krylov in ("pcg", "both"):
+            batch = compare_batch(a, fg, torch, dev, stream, "pcg")
+        if a.batch_krylov in ("rrs", "both"):
+            try:
+                batch_rrs = compare_batch(a, fg, torch, dev, stream, "rrs")
+            except Exception as exc:   # e.g. the direction history does not fit on the device
+                batch_rrs = {"error": str(exc)[:300]}
 
     gemm_tflops = gf / (gms / 1e3) / 1e12 if gms > 0 else None
     out = {
@@ -595,7 +732,8 @@ def run_ours(a, rank, world):
                      "kernel_share_of_step": (gms / 1e3) / t_steps if t_steps > 0 else None,
                      "launches": gn},
         "e2e": e2e, "gpu_launches": int(launches), "clocks": clk, "wall_s": wall,
-        "forms": forms, "apply_3d": apply3d, "forms_3d": forms3d, "batch_form": batch,
+        "forms": forms, "apply_3d": apply3d, "forms_3d": forms3d, "batch_form": batch, "batch_form_rrs": batch_rrs,
+        "academic": academic, "primal_3d": primal3d, "phases": phases,
     }
     s.close()
     return out

@@ -63,6 +63,8 @@ enum { FETI_SCALING_K = 0, FETI_SCALING_MULT = 1 };       /* Eq. 15 / multiplici
 enum { FETI_PCG = 0, FETI_FO = 1, FETI_RRS = 2 };         /* Sections 3.2, 3.3 */
 enum { FETI_FP64 = 0, FETI_TF32 = 1, FETI_TF32X3 = 2, FETI_BF16 = 3, FETI_BF16X3 = 4 };  /* block products */
 enum { FETI_PRECOND_DIRICHLET = 0, FETI_PRECOND_LUMPED = 1, FETI_PRECOND_SUPERLUMPED = 2 };
+enum { FETI_PRIMAL_CORNERS = 0, FETI_PRIMAL_EDGES = 1 };  /* FETI-DP primal set (Section 2.2; richer
+                                                             sets: Section 5, future work) */
 
 typedef struct {
   int method;          /* FETI_TFETI or FETI_FETIDP */
@@ -90,6 +92,12 @@ typedef struct {
                           the recursive residual by the FP64 residual r_outer - P^T F lambda~
                           (one FP64 single-column apply per iteration) and the inner solve
                           aims at the final tolerance, so the Krylov space is not restarted */
+  int primal;          /* FETI-DP primal set: FETI_PRIMAL_CORNERS (default; the DOFs at the vertices
+                          of the tile grid) or FETI_PRIMAL_EDGES (also one average per component over
+                          the interior nodes of every tile-grid edge shared by two or more
+                          subdomains -- 3D: tile edges, 2D: tile sides -- whose nodes are all free in
+                          that component; introduced by a change of basis on each edge, with the
+                          Dirichlet preconditioner only).  TFETI: must be FETI_PRIMAL_CORNERS */
 } feti_options;
 
 typedef struct {
@@ -249,6 +257,26 @@ feti_status feti_profile_end(feti_ctx* ctx, double* gemm_flops, double* gemm_ms,
  * for FETI-DP; the split product's three passes count once), device time in
  * milliseconds and launch count.  Each pointer may be NULL. */
 feti_status feti_profile_tensor(const feti_ctx* ctx, double* flops, double* ms, int64_t* launches);
+
+/* Phases of the last completed profile (instrumentation): each phase region is
+ * bracketed by CUDA events on the context stream (every launch inside counts),
+ * with its algorithmic work -- flops for the FP64-pipe phases, bytes for the
+ * memory-bound ones.  Arrays of FETI_N_PHASES entries, indexed by the enum:
+ *   APPLY    dual-operator block apply Q = F W (Eq. 12; flops: sum_s 2 n_b^2 m plus
+ *            the corner coupling 4 n_b n_c m and the coarse solve 2 n_c^2 m)
+ *   PRECOND  preconditioner Z (Eq. 13; bytes: the distinct local blocks once, the
+ *            residual and interface vectors, the dense Z of the simultaneous variant)
+ *   PROJECT  TFETI projector (bytes: G twice, the block in and out)
+ *   GRAM     Gram matrix, rank-revealing factorization and F-orthonormal transform
+ *            (Algorithm 1; flops n_lambda m (m + 1) + 2 n_lambda k (k + 1))
+ *   STEP     step length, multiplier and residual update, residual norm (bytes)
+ *   ORTHO    full orthogonalization against the stored blocks (flops sum_j 4 n_lambda k_j m)
+ *   FACTOR   local factorizations and coarse problem (time only: work 0)
+ *   RECOVER  primal recovery (time only) */
+enum { FETI_PHASE_APPLY = 0, FETI_PHASE_PRECOND = 1, FETI_PHASE_PROJECT = 2, FETI_PHASE_GRAM = 3,
+       FETI_PHASE_STEP = 4, FETI_PHASE_ORTHO = 5, FETI_PHASE_FACTOR = 6, FETI_PHASE_RECOVER = 7,
+       FETI_N_PHASES = 8 };
+feti_status feti_profile_phases(const feti_ctx* ctx, double* work, double* ms, int64_t* count);
 
 /* Layout of the multipliers, for comparing lambda-space vectors with an
  * independent implementation: for each multiplier l, out[6*l .. 6*l+5] =

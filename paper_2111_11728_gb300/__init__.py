@@ -23,6 +23,7 @@ FETI_SCALING_K, FETI_SCALING_MULT = 0, 1
 FETI_PCG, FETI_FO, FETI_RRS = 0, 1, 2
 FETI_FP64, FETI_TF32, FETI_TF32X3, FETI_BF16, FETI_BF16X3 = 0, 1, 2, 3, 4
 FETI_PRECOND_DIRICHLET, FETI_PRECOND_LUMPED, FETI_PRECOND_SUPERLUMPED = 0, 1, 2
+FETI_PRIMAL_CORNERS, FETI_PRIMAL_EDGES = 0, 1
 (FETI_Q_N_LAMBDA, FETI_Q_N_SUBDOMAINS, FETI_Q_N_PRIMAL, FETI_Q_N_MODULES, FETI_Q_N_B_TOTAL, FETI_Q_N_DOFS,
  FETI_Q_N_ELEMENTS, FETI_Q_MAX_NB, FETI_Q_DEVICE_BYTES, FETI_Q_N_RBM, FETI_Q_LAUNCHES, FETI_Q_N_PROBLEMS,
  FETI_Q_GEMV_CONFIG, FETI_Q_TC_BYTES_F, FETI_Q_TC_BYTES_PER_COL) = range(15)
@@ -35,7 +36,7 @@ EXPORTS = [
     "feti_options_default", "feti_create", "feti_setup_subdomains", "feti_setup_batch", "feti_problem_result",
     "feti_set_density", "feti_factorize",
     "feti_solve_dual", "feti_recover_displacements", "feti_compliance_grad", "feti_apply_dual",
-    "feti_apply_precond", "feti_apply_precond_noalloc", "feti_query", "feti_profile_begin", "feti_profile_end", "feti_profile_tensor", "feti_lambda_layout", "feti_local_blocks", "feti_last_error",
+    "feti_apply_precond", "feti_apply_precond_noalloc", "feti_query", "feti_profile_begin", "feti_profile_end", "feti_profile_tensor", "feti_profile_phases", "feti_lambda_layout", "feti_local_blocks", "feti_last_error",
     "feti_destroy",
 ]
 
@@ -44,7 +45,8 @@ class feti_options(ctypes.Structure):
     _fields_ = [("method", ctypes.c_int), ("scaling", ctypes.c_int), ("krylov", ctypes.c_int),
                 ("precision", ctypes.c_int), ("max_iter", ctypes.c_int), ("dedup_modules", ctypes.c_int),
                 ("tol", ctypes.c_double), ("rr_tol", ctypes.c_double), ("inner_tol", ctypes.c_double),
-                ("max_refine", ctypes.c_int), ("precond", ctypes.c_int), ("fp64_residual", ctypes.c_int)]
+                ("max_refine", ctypes.c_int), ("precond", ctypes.c_int), ("fp64_residual", ctypes.c_int),
+                ("primal", ctypes.c_int)]
 
 
 class feti_problem(ctypes.Structure):
@@ -90,6 +92,7 @@ def lib():
             "feti_profile_begin": ([vp], i),
             "feti_profile_end": ([vp, ctypes.POINTER(d), ctypes.POINTER(d), ctypes.POINTER(i64)], i),
             "feti_profile_tensor": ([vp, ctypes.POINTER(d), ctypes.POINTER(d), ctypes.POINTER(i64)], i),
+            "feti_profile_phases": ([vp, ctypes.POINTER(d), ctypes.POINTER(d), ctypes.POINTER(i64)], i),
             "feti_lambda_layout": ([vp, vp], i),
             "feti_local_blocks": ([vp, i, ctypes.POINTER(i), ctypes.POINTER(i), vp, vp, vp, vp, vp], i),
             "feti_last_error": ([vp], ctypes.c_char_p),
@@ -239,6 +242,18 @@ def feti_profile_end(ctx):
     return f.value, t.value, n.value
 
 
+PHASES = ("apply", "precond", "project", "gram", "step", "ortho", "factor", "recover")
+
+
+def feti_profile_phases(ctx):
+    """Per phase of the last profile: {name: (work, ms, regions)}; work is flops or bytes."""
+    w = (ctypes.c_double * 8)()
+    t = (ctypes.c_double * 8)()
+    n = (ctypes.c_int64 * 8)()
+    _check(ctx, lib().feti_profile_phases(ctx, w, t, n))
+    return {PHASES[q]: (w[q], t[q], n[q]) for q in range(8)}
+
+
 def feti_profile_tensor(ctx):
     """(flops, ms, launches) of the tensor-core products in the last completed profile."""
     f, t, n = ctypes.c_double(0), ctypes.c_double(0), ctypes.c_int64(0)
@@ -277,10 +292,11 @@ class Solver:
 
     def __init__(self, method=FETI_FETIDP, scaling=FETI_SCALING_K, krylov=FETI_RRS, tol=1e-6, max_iter=500,
                  rr_tol=1e-10, dedup=True, stream=None, precision=FETI_FP64, inner_tol=None, fp64_residual=False,
-                 precond=FETI_PRECOND_DIRICHLET):
+                 precond=FETI_PRECOND_DIRICHLET, primal=FETI_PRIMAL_CORNERS):
         o = feti_options_default()
         o.method, o.scaling, o.krylov, o.precision = method, scaling, krylov, precision
         o.precond = precond
+        o.primal = primal
         if inner_tol is not None:
             o.inner_tol = inner_tol
         o.fp64_residual = int(bool(fp64_residual))

@@ -4,6 +4,7 @@
 // (the retained rank k_i and sqrt(r^T z)); every arithmetic step runs on the
 // device in FP64.
 #include <algorithm>
+#include <memory>
 #include <cmath>
 #include <cstring>
 #include <new>
@@ -79,6 +80,10 @@ void free_all(Ctx& c) {
 
 inline int64_t align32(int64_t x) { return (x + 31) / 32 * 32; }
 
+constexpr int BATCH_CHUNK = 128;        // columns per dual-operator apply in the batched Algorithm 1
+constexpr int64_t BATCH_KCHUNK = 8192;  // rows per split-K chunk of its Gram products
+constexpr int64_t BATCH_RCHUNK = 4096;  // rows per entry of its block updates
+
 feti_status sync_check(Ctx& c) {
   CU(cudaStreamSynchronize(c.stream));
   CU(cudaGetLastError());
@@ -118,6 +123,21 @@ feti_status build_block_descs(Ctx& c) {
   CU(cudaMemcpy(c.d_gemm_F, dF.data(), dF.size() * sizeof(GemmDesc), cudaMemcpyHostToDevice));
   CU(cudaMemcpy(c.d_gemm_FrcT, dFrcT.data(), dFrcT.size() * sizeof(GemmDesc), cudaMemcpyHostToDevice));
   CU(cudaMemcpy(c.d_gemm_Frc, dFrc.data(), dFrc.size() * sizeof(GemmDesc), cudaMemcpyHostToDevice));
+  if (hp.n_prob > 1 && c.d_gemm_coarse) {
+    // per-problem coarse solves of a batch: V_p = Kbar_p^{-1} Vraw_p on the
+    // (re)allocated corner buffers
+    std::vector<GemmDesc> gc(hp.n_prob);
+    const int np = hp.n_primal;
+    for (int q = 0; q < hp.n_prob; ++q) {
+      const int o = hp.prob_primal_off[q], npq = hp.prob_primal_off[q + 1] - o;
+      GemmDesc g{};
+      g.A = c.d_Kbar_inv + c.h_kbar_off[q]; g.B = c.d_Vraw + o; g.C = c.d_V + o;
+      g.M = npq; g.N = 1; g.K = npq;
+      g.ars = npq; g.acs = 1; g.brs = 1; g.bcs = np; g.crs = 1; g.ccs = np;
+      gc[q] = g;
+    }
+    CU(cudaMemcpy(c.d_gemm_coarse, gc.data(), gc.size() * sizeof(GemmDesc), cudaMemcpyHostToDevice));
+  }
   return FETI_OK;
 }
 
@@ -359,6 +379,7 @@ feti_status feti_options_default(feti_options* opt) {
   opt->max_refine = 30;
   opt->fp64_residual = 0;
   opt->precond = FETI_PRECOND_DIRICHLET;
+  opt->primal = FETI_PRIMAL_CORNERS;
   return FETI_OK;
 }
 
@@ -376,6 +397,9 @@ feti_status feti_create(feti_ctx** out, const feti_options* opt, void* stream) {
   if (o.precision != FETI_FP64 && !(o.inner_tol >= 0.0 && o.inner_tol < 1.0 && o.max_refine > 0)) return FETI_EINVAL;
   if (o.fp64_residual != 0 && o.fp64_residual != 1) return FETI_EINVAL;
   if (o.precond < FETI_PRECOND_DIRICHLET || o.precond > FETI_PRECOND_SUPERLUMPED) return FETI_EINVAL;
+  if (o.primal != FETI_PRIMAL_CORNERS && o.primal != FETI_PRIMAL_EDGES) return FETI_EINVAL;
+  if (o.primal == FETI_PRIMAL_EDGES && o.method != FETI_FETIDP) return FETI_EINVAL;
+  if (o.primal == FETI_PRIMAL_EDGES && o.precond != FETI_PRECOND_DIRICHLET) return FETI_ENOTSUP;
   feti_ctx* ctx = new (std::nothrow) feti_ctx;
   if (!ctx) return FETI_ENOMEM;
   Ctx& c = ctx->c;
@@ -410,8 +434,8 @@ static feti_status setup_impl(Ctx& c, const feti_problem* probs, int n) {
   if (n < 1) { c.err = "n_problems must be >= 1"; return FETI_EINVAL; }
   for (int q = 0; q < n; ++q)
     if (!probs[q].rho || !probs[q].dirichlet || !probs[q].f) { c.err = "null problem array"; return FETI_EINVAL; }
-  if (n > 1 && (c.opt.method != FETI_FETIDP || c.opt.krylov != FETI_PCG || c.opt.precision != FETI_FP64)) {
-    c.err = "batches of problems are solved with FETI-DP, PCG and FP64 block products";
+  if (n > 1 && (c.opt.method != FETI_FETIDP || c.opt.krylov == FETI_FO || c.opt.precision != FETI_FP64)) {
+    c.err = "batches of problems are solved with FETI-DP, PCG or the simultaneous variant, and FP64 block products";
     return FETI_ENOTSUP;
   }
   free_all(c);
@@ -430,7 +454,8 @@ static feti_status setup_impl(Ctx& c, const feti_problem* probs, int n) {
     else std::memcpy(rho_h.data(), prob->rho, nel * sizeof(double));
     for (double r : rho_h)
       if (!(r >= 0.0 && r <= 1.0)) { c.err = "densities must lie in [0, 1]"; return FETI_EINVAL; }
-    std::string msg = build_host_problem(*prob, c.opt.method, c.opt.dedup_modules, rho_h.data(), parts[q]);
+    std::string msg = build_host_problem(*prob, c.opt.method, c.opt.dedup_modules, rho_h.data(), parts[q],
+                                         c.opt.primal == FETI_PRIMAL_EDGES);
     if (!msg.empty()) { c.err = (n > 1 ? "problem " + std::to_string(q) + ": " : std::string()) + msg; return FETI_EINVAL; }
     rho_all.insert(rho_all.end(), rho_h.begin(), rho_h.end());
   }
@@ -473,6 +498,15 @@ static feti_status setup_impl(Ctx& c, const feti_problem* probs, int n) {
     TRY(upload(c, p3, T.blist));
     TRY(upload(c, p4, T.clist));
     d.cls_idx = p1; d.ilist = p2; d.blist = p3; d.clist = p4;
+    d.n_avg = (int)T.avg_c.size();
+    if (d.n_avg > 0) {
+      int *a1, *a2, *a3;
+      TRY(upload(c, a1, T.avg_c));
+      TRY(upload(c, a2, T.avg_off));
+      TRY(upload(c, a3, T.avg_b));
+      d.avg_c = a1; d.avg_off = a2; d.avg_b = a3;
+      c.max_avg = std::max(c.max_avg, d.n_avg);
+    }
     if (hp.n_rbm > 0) {
       std::vector<double> raw, hat;
       type_rigid_modes(hp, T, raw, hat);
@@ -560,11 +594,22 @@ static feti_status setup_impl(Ctx& c, const feti_problem* probs, int n) {
   TRY(upload(c, c.d_b2l_lam, hp.b2l_lam));
   TRY(upload(c, c.d_b2l_sign, hp.b2l_sign));
   TRY(upload(c, c.d_b_sub, hp.b_sub));
+  {
+    std::vector<int> lcol(hp.b_sub.size());
+    for (size_t b = 0; b < lcol.size(); ++b) lcol[b] = hp.b_sub[b] - hp.prob_sub_off[hp.sub_prob[hp.b_sub[b]]];
+    TRY(upload(c, c.d_b_lcol, lcol));
+  }
   TRY(upload(c, c.d_c_glob, hp.c_glob));
   std::vector<int> csub(c.n_c_total);
   for (int s = 0; s < hp.n_sub; ++s)
     for (int64_t k = hp.c_off.empty() ? 0 : hp.c_off[s]; !hp.c_off.empty() && k < hp.c_off[s + 1]; ++k) csub[k] = s;
   TRY(upload(c, c.d_c_sub, csub));
+  if (c.max_avg > 0) {
+    std::vector<int> iota(std::max<int64_t>(c.n_c_total, 1));
+    for (size_t k = 0; k < iota.size(); ++k) iota[k] = (int)k;
+    TRY(upload(c, c.d_c_iota, iota));
+    TRY(dalloc(c, c.d_ucl, (size_t)std::max<int64_t>(c.n_c_total, 1)));
+  }
   TRY(upload(c, c.d_prim_off, hp.prim_off.empty() ? std::vector<int>{0} : hp.prim_off));
   TRY(upload(c, c.d_prim_src, hp.prim_src));
   TRY(upload(c, c.d_load_src, hp.load_src));
@@ -594,6 +639,12 @@ static feti_status setup_impl(Ctx& c, const feti_problem* probs, int n) {
     for (int r = hp.prob_primal_off[q]; r < hp.prob_primal_off[q + 1]; ++r) row_prob[r] = q;
   }
   const int64_t kb_len = std::max<int64_t>(c.h_kbar_off[hp.n_prob], 1);
+  c.fl_coarse = hp.method == FETI_FETIDP ? 2.0 * (double)c.h_kbar_off[hp.n_prob] : 0.0;
+  c.bytes_S = 0.0;
+  for (int q = 0; q < (int)hp.module_type.size(); ++q) {
+    const double nb = hp.types[hp.module_type[q]].n_b;
+    c.bytes_S += 8.0 * nb * nb;
+  }
   TRY(dalloc(c, c.d_Kbar, kb_len));
   TRY(dalloc(c, c.d_Kbar_L, kb_len));
   TRY(dalloc(c, c.d_Kbar_inv, kb_len));
@@ -732,27 +783,23 @@ static feti_status setup_impl(Ctx& c, const feti_problem* probs, int n) {
     TRY(upload(c, c.d_dense_coarse, dc));
     if (hp.n_prob > 1) {
       std::vector<DenseDesc> db(hp.n_prob);
-      std::vector<GemmDesc> gc(hp.n_prob);
-      const int np = hp.n_primal;
       for (int q = 0; q < hp.n_prob; ++q) {
-        const int o = hp.prob_primal_off[q], npq = hp.prob_primal_off[q + 1] - o;
+        const int npq = hp.prob_primal_off[q + 1] - hp.prob_primal_off[q];
         db[q].A = c.d_Kbar + c.h_kbar_off[q];
         db[q].Linv = c.d_Kbar_L + c.h_kbar_off[q];
         db[q].out = c.d_Kbar_inv + c.h_kbar_off[q];
         db[q].n = npq; db[q].ld = npq; db[q].tag = 900000 + q; db[q].n_full = npq;
-        GemmDesc g{};
-        g.A = c.d_Kbar_inv + c.h_kbar_off[q]; g.B = c.d_Vraw + o; g.C = c.d_V + o;
-        g.M = npq; g.N = 1; g.K = npq;
-        g.ars = npq; g.acs = 1; g.brs = 1; g.bcs = np; g.crs = 1; g.ccs = np;
-        gc[q] = g;
       }
       TRY(upload(c, c.d_dense_coarse_batch, db));
-      TRY(upload(c, c.d_gemm_coarse, gc));
+      // the coarse-solve descriptors point at the block buffers: written by
+      // build_block_descs whenever those are (re)allocated
+      TRY(dalloc(c, c.d_gemm_coarse, (size_t)hp.n_prob));
     }
   }
   // direction-block buffers: one column per subdomain for the simultaneous
   // variant, a few for PCG / FO (grown on demand by feti_apply_dual)
-  TRY(ensure_blocks(c, c.opt.krylov == FETI_RRS ? std::max(64, hp.n_sub) : 64));
+  // (batches apply their direction blocks in column chunks of BATCH_CHUNK)
+  TRY(ensure_blocks(c, hp.n_prob > 1 ? BATCH_CHUNK : c.opt.krylov == FETI_RRS ? std::max(64, hp.n_sub) : 64));
   TRY(sync_check(c));
   c.state = 1;
   return FETI_OK;
@@ -793,6 +840,7 @@ feti_status feti_factorize(feti_ctx* ctx) {
   const HostProblem& hp = c.hp;
   cudaStream_t st = c.stream;
   const bool dp = hp.method == FETI_FETIDP;
+  PhaseScope phase(st, FETI_PHASE_FACTOR, 0.0);
   // local stiffness (Eqs. 1, 3)
   CU(launch_moduli(c, c.d_E, st));
   CU(cudaMemsetAsync(c.d_modmem, 0, c.modmem_len * sizeof(double), st));
@@ -806,6 +854,7 @@ feti_status feti_factorize(feti_ctx* ctx) {
   int max_bc = 1;
   for (auto& t : hp.types) max_bc = std::max(max_bc, t.n_bc());
   CU(dgemm_batched(c.d_gemm_schur, c.n_mod, max_bc, max_bc, 0, -1.0, 1.0, st, c.fl_schur));
+  if (c.max_avg > 0) CU(launch_edge_transform(c, max_bc, st));   // edge averages: S <- T^T S T
   // local dual block F_s = S_bb^{-1} (FETI-DP) or (S_b + Rhat Rhat^T)^{-1} (TFETI):
   // Cholesky of the whole b+c Schur complement with only the b columns
   // eliminated, so the corner block is Schur-complemented in the same
@@ -833,6 +882,7 @@ feti_status feti_factorize(feti_ctx* ctx) {
   CU(launch_load_gather(c, st));
   CU(launch_band_fwd_single(c, st));
   CU(launch_condense_load(c, st));
+  if (c.max_avg > 0) CU(launch_edge_load(c, c.max_avg, st));      // f~ <- T^T f~
   const int64_t nl = hp.n_lam, nbt = hp.n_b_total;
   // d_r (FETI-DP) or d = B K^# f (TFETI, c = 0): x_b = F f~_b, scattered
   CU(batched_gemv(c, 0, c.d_ft, c.d_pb0, 0.0, st));
@@ -912,15 +962,23 @@ static feti_status krylov_core(Ctx& c, double tol, int max_iter, bool lowp, feti
   const int m = multi ? hp.n_sub : 1;
   cudaStream_t st = c.stream;
   auto applyF = [&](const double* X, int mm, double* Y) {
+    PhaseScope ph(st, FETI_PHASE_APPLY, mm * (c.fl_F + c.fl_FrcT + c.fl_Frc + c.fl_coarse));
     return lowp ? apply_dual_lowp(c, X, nl, mm, Y, nl) : apply_dual(c, X, nl, mm, Y, nl);
   };
+  const double prec_bytes = c.bytes_S + 8.0 * (2.0 * nl + 2.0 * hp.n_b_total + (multi ? (double)nl * m : 0.0));
   auto precond = [&](double* Z, double* z) -> cudaError_t {
+    PhaseScope ph(st, FETI_PHASE_PRECOND, prec_bytes);
     return lowp ? precond_apply_lowp(c, c.d_r, Z, nl, z, st) : precond_apply(c, c.d_r, Z, nl, z, st);
+  };
+  auto projectW = [&]() -> feti_status {
+    if (hp.method != FETI_TFETI) return FETI_OK;
+    PhaseScope ph(st, FETI_PHASE_PROJECT, 8.0 * (2.0 * c.n_coarse * (double)nl + 2.0 * (double)nl * m));
+    return project(c, c.d_Wb, nl, m);
   };
   // Z_0, W_0 = P Z_0
   CU(precond(multi ? c.d_Wb : nullptr, c.d_z));
   if (!multi) CU(cudaMemcpyAsync(c.d_Wb, c.d_z, nl * sizeof(double), cudaMemcpyDeviceToDevice, st));
-  TRY(project(c, c.d_Wb, nl, m));
+  TRY(projectW());
   CU(cudaMemsetAsync(c.d_lamt, 0, nl * sizeof(double), st));
   CU(dot(c.d_r, c.d_z, nl, c.d_red, c.d_scalar, st));
   double rz = 0.0;
@@ -933,12 +991,15 @@ static feti_status krylov_core(Ctx& c, double tol, int max_iter, bool lowp, feti
   while (eps > tol * eps0 && it < max_iter) {
     // Q = F W, Delta = Q^T W (symmetric: lower-triangular tiles suffice)
     TRY(applyF(c.d_Wb, m, c.d_Qb));
-    TRY(gemm_tn(c, c.d_Qb, nl, c.d_Wb, nl, c.d_Delta, m, m, m, (int)nl, 1.0, 0.0, 1));
-    // rank-revealing factorization and F-orthonormal transform: N^T [L~^{-T}; 0]
-    // applied as (W with columns in pivot order) times the upper-triangular L~^{-T}
-    CU(rr_cholesky(c.d_Delta, m, m, c.opt.rr_tol, c.d_rrwork, c.d_T, c.d_kdev, c.d_perm, st));
     int k = 0;
-    CU(cudaMemcpyAsync(c.h_pin, c.d_kdev, sizeof(int), cudaMemcpyDeviceToHost, st));
+    {
+      PhaseScope ph(st, FETI_PHASE_GRAM, (double)nl * m * (m + 1.0));
+      TRY(gemm_tn(c, c.d_Qb, nl, c.d_Wb, nl, c.d_Delta, m, m, m, (int)nl, 1.0, 0.0, 1));
+      // rank-revealing factorization and F-orthonormal transform: N^T [L~^{-T}; 0]
+      // applied as (W with columns in pivot order) times the upper-triangular L~^{-T}
+      CU(rr_cholesky(c.d_Delta, m, m, c.opt.rr_tol, c.d_rrwork, c.d_T, c.d_kdev, c.d_perm, st));
+      CU(cudaMemcpyAsync(c.h_pin, c.d_kdev, sizeof(int), cudaMemcpyDeviceToHost, st));
+    }
     CU(cudaStreamSynchronize(st));
     std::memcpy(&k, c.h_pin, sizeof(int));
     S.last_rank = k;
@@ -954,17 +1015,23 @@ static feti_status krylov_core(Ctx& c, double tol, int max_iter, bool lowp, feti
     double* Qi = c.hist_Q[it];
     c.hist_k.push_back(k);
     const double fl_T = (double)nl * k * (k + 1.0);   // 2 n nnz(U)
-    TRY(gemm_perm_upper(c, c.d_Wb, nl, c.d_perm, c.d_T, m, Wi, nl, (int)nl, k, fl_T));
-    TRY(gemm_perm_upper(c, c.d_Qb, nl, c.d_perm, c.d_T, m, Qi, nl, (int)nl, k, fl_T));
+    {
+      PhaseScope ph(st, FETI_PHASE_GRAM, 2.0 * fl_T);
+      TRY(gemm_perm_upper(c, c.d_Wb, nl, c.d_perm, c.d_T, m, Wi, nl, (int)nl, k, fl_T));
+      TRY(gemm_perm_upper(c, c.d_Qb, nl, c.d_perm, c.d_T, m, Qi, nl, (int)nl, k, fl_T));
+    }
     S.f_applies += m;
     // gamma = W^T r; lambda~ += W gamma; r -= P^T Q gamma
-    CU(gemv_t(Wi, nl, nl, k, c.d_r, c.d_gamma, st));
-    if (hp.method == FETI_TFETI) {
-      CU(step_update(Wi, Qi, nl, nl, k, c.d_gamma, c.d_lamt, c.d_r, c.d_z, st));
-      TRY(project(c, c.d_z, nl, 1));
-      CU(axpby(nl, -1.0, c.d_z, 1.0, c.d_r, st));
-    } else {
-      CU(step_update(Wi, Qi, nl, nl, k, c.d_gamma, c.d_lamt, c.d_r, nullptr, st));
+    {
+      PhaseScope ph(st, FETI_PHASE_STEP, 8.0 * (double)nl * (3.0 * k + 4.0));
+      CU(gemv_t(Wi, nl, nl, k, c.d_r, c.d_gamma, st));
+      if (hp.method == FETI_TFETI) {
+        CU(step_update(Wi, Qi, nl, nl, k, c.d_gamma, c.d_lamt, c.d_r, c.d_z, st));
+        TRY(project(c, c.d_z, nl, 1));
+        CU(axpby(nl, -1.0, c.d_z, 1.0, c.d_r, st));
+      } else {
+        CU(step_update(Wi, Qi, nl, nl, k, c.d_gamma, c.d_lamt, c.d_r, nullptr, st));
+      }
     }
     if (r_base) {
       // FP64 residual replacement: r = r_base - P^T F lambda~
@@ -977,14 +1044,22 @@ static feti_status krylov_core(Ctx& c, double tol, int max_iter, bool lowp, feti
     // Z_{i+1}, W_{i+1} = P Z_{i+1}
     CU(precond(multi ? c.d_Wb : nullptr, c.d_z));
     if (!multi) CU(cudaMemcpyAsync(c.d_Wb, c.d_z, nl * sizeof(double), cudaMemcpyDeviceToDevice, st));
-    TRY(project(c, c.d_Wb, nl, m));
+    TRY(projectW());
     // F-orthogonalise against the stored blocks, oldest first (modified Gram-Schmidt)
-    for (int j = full ? 0 : it; j <= it; ++j) {
-      const int kj = c.hist_k[j];
-      TRY(gemm_tn(c, c.hist_Q[j], nl, c.d_Wb, nl, c.d_Delta, kj, kj, m, (int)nl, 1.0, 0.0));
-      TRY(gemm_nn(c, c.hist_W[j], nl, c.d_Delta, kj, c.d_Wb, nl, (int)nl, m, kj, -1.0, 1.0));
+    {
+      double fl_o = 0.0;
+      for (int j = full ? 0 : it; j <= it; ++j) fl_o += 4.0 * (double)nl * c.hist_k[j] * m;
+      PhaseScope ph(st, FETI_PHASE_ORTHO, fl_o);
+      for (int j = full ? 0 : it; j <= it; ++j) {
+        const int kj = c.hist_k[j];
+        TRY(gemm_tn(c, c.hist_Q[j], nl, c.d_Wb, nl, c.d_Delta, kj, kj, m, (int)nl, 1.0, 0.0));
+        TRY(gemm_nn(c, c.hist_W[j], nl, c.d_Delta, kj, c.d_Wb, nl, (int)nl, m, kj, -1.0, 1.0));
+      }
     }
-    CU(dot(c.d_r, c.d_z, nl, c.d_red, c.d_scalar, st));
+    {
+      PhaseScope ph(st, FETI_PHASE_STEP, 16.0 * (double)nl);
+      CU(dot(c.d_r, c.d_z, nl, c.d_red, c.d_scalar, st));
+    }
     TRY(read_scalar(c, c.d_scalar, &rz));
     ++it;
     eps = std::sqrt(std::max(rz, 0.0));
@@ -994,6 +1069,274 @@ static feti_status krylov_core(Ctx& c, double tol, int max_iter, bool lowp, feti
   S.eps0 = eps0;
   S.eps = eps;
   S.converged = eps <= tol * eps0;
+  return result;
+}
+
+// Device buffer of at least `need` elements: grown geometrically (the old
+// buffer stays with the context until it is destroyed).
+template <class T>
+static feti_status grow(Ctx& c, T*& p, int64_t& cap, int64_t need) {
+  if (need <= cap && p) return FETI_OK;
+  const int64_t n = std::max<int64_t>(need, 2 * cap);
+  TRY(dalloc(c, p, (size_t)n));
+  cap = n;
+  return FETI_OK;
+}
+
+// C_p = alpha A_p^T B_p + beta C_p for every entry of ops (split over K in
+// fixed chunks, reduced in order).
+static feti_status run_seg_tn(Ctx& c, const std::vector<SegTN>& ops, double alpha, double beta) {
+  std::vector<GemmDesc> descs;
+  std::vector<int64_t> coff;
+  std::vector<SegRed> reds;
+  int64_t plen = 0;
+  int mm = 0, mn = 0;
+  seg_tn_plan(ops, BATCH_KCHUNK, descs, coff, reds, &plen, &mm, &mn);
+  if (descs.empty()) return FETI_OK;
+  if (descs.size() > 65535 || reds.size() > 65535) { c.err = "batch too large for one launch"; return FETI_ENOTSUP; }
+  TRY(grow(c, c.d_bk_split, c.bk_split_cap, plen));
+  TRY(grow(c, c.d_bk_desc, c.bk_desc_cap, (int64_t)descs.size()));
+  TRY(grow(c, c.d_bk_red, c.bk_red_cap, (int64_t)reds.size()));
+  seg_tn_bind(descs, coff, c.d_bk_split);
+  double fl = 0.0;
+  for (const SegTN& o : ops) fl += 2.0 * o.M * (double)o.N * (double)o.K;
+  CU(cudaMemcpyAsync(c.d_bk_desc, descs.data(), descs.size() * sizeof(GemmDesc), cudaMemcpyHostToDevice, c.stream));
+  CU(cudaMemcpyAsync(c.d_bk_red, reds.data(), reds.size() * sizeof(SegRed), cudaMemcpyHostToDevice, c.stream));
+  CU(seg_tn_run(c.d_bk_desc, (int)descs.size(), c.d_bk_red, (int)reds.size(), mm, mn, c.d_bk_split, alpha, beta, fl,
+                c.stream));
+  return FETI_OK;
+}
+
+// Batched C_p (+)= alpha A_p B_p over the descriptors in `descs` (one per row
+// chunk of a problem), as one launch.
+static feti_status run_row_chunks(Ctx& c, const std::vector<GemmDesc>& descs, double alpha, double beta) {
+  if (descs.empty()) return FETI_OK;
+  if (descs.size() > 65535) { c.err = "batch too large for one launch"; return FETI_ENOTSUP; }
+  TRY(grow(c, c.d_bk_desc, c.bk_desc_cap, (int64_t)descs.size()));
+  int mm = 0, mn = 0;
+  double fl = 0.0;
+  for (const GemmDesc& d : descs) {
+    mm = std::max(mm, d.M);
+    mn = std::max(mn, d.N);
+    fl += d.tri == 2 ? (double)d.M * d.N * (d.N + 1.0) : 2.0 * d.M * (double)d.N * d.K;
+  }
+  CU(cudaMemcpyAsync(c.d_bk_desc, descs.data(), descs.size() * sizeof(GemmDesc), cudaMemcpyHostToDevice, c.stream));
+  CU(dgemm_batched(c.d_bk_desc, (int)descs.size(), mm, mn, 0, alpha, beta, c.stream, fl));
+  return FETI_OK;
+}
+
+// Algorithm 1 for every problem of a batch at once (FETI-DP, no projector).
+// Problem p keeps its own block of m_p = N_s(p) directions, one per subdomain;
+// the current blocks W, Q are stored stacked (all problems' multiplier rows,
+// max_p m_p columns, problem p in its own rows and first m_p columns, so that
+// one dual-operator apply covers the batch), the stored blocks W_i, Q_i packed
+// per problem (n_lambda(p) x k_p each).  Every step is one launch over the
+// problems still iterating: the Gram matrices (split-K, reduced in order),
+// the rank-revealing factorizations, the F-orthonormal transforms, the step,
+// the preconditioner and the modified Gram-Schmidt sweep over the stored
+// blocks, oldest first.  Expects r_0 in c.d_r; leaves lambda~ in c.d_lamt.
+static feti_status batch_rrs(Ctx& c, double tol, int max_iter, feti_stats& S) {
+  const HostProblem& hp = c.hp;
+  const int np = hp.n_prob;
+  const int64_t nl = hp.n_lam;
+  cudaStream_t st = c.stream;
+  std::vector<int64_t> l0(np), nlp(np), doff(np), woff(np), moff(np);
+  std::vector<int> mp(np);
+  int M = 0;
+  int64_t sm2 = 0, sw = 0, sm = 0;
+  for (int p = 0; p < np; ++p) {
+    l0[p] = hp.prob_lam_off[p];
+    nlp[p] = hp.prob_lam_off[p + 1] - l0[p];
+    mp[p] = hp.prob_sub_off[p + 1] - hp.prob_sub_off[p];
+    M = std::max(M, mp[p]);
+    doff[p] = sm2;
+    woff[p] = sw;
+    moff[p] = sm;
+    sm2 += (int64_t)mp[p] * mp[p];
+    sw += 2 * (int64_t)mp[p] * mp[p] + mp[p];
+    sm += mp[p];
+  }
+  if (M > 1024) { c.err = "more than 1024 subdomains in one problem of the batch"; return FETI_ENOTSUP; }
+  TRY(ensure_krylov(c, M));
+  TRY(ensure_blocks(c, std::min(M, BATCH_CHUNK)));
+  if (!c.d_bk_delta) {
+    TRY(dalloc(c, c.d_bk_delta, (size_t)sm2));
+    TRY(dalloc(c, c.d_bk_T, (size_t)sm2));
+    TRY(dalloc(c, c.d_bk_work, (size_t)sw));
+    TRY(dalloc(c, c.d_bk_gam, (size_t)sm));
+    TRY(dalloc(c, c.d_bk_perm, (size_t)sm));
+    TRY(dalloc(c, c.d_bk_k, (size_t)np));
+    TRY(dalloc(c, c.d_bk_rz, (size_t)np));
+    TRY(dalloc(c, c.d_bk_part, (size_t)np * 32));
+    TRY(dalloc(c, c.d_bk_rr, (size_t)np));
+    TRY(dalloc(c, c.d_bk_vec, (size_t)np));
+  }
+  double* W = c.d_Wb;
+  double* Q = c.d_Qb;
+  auto read_rz = [&](std::vector<double>& rz) -> feti_status {
+    CU(seg_dot2(c.d_prob_lam_off, np, c.d_r, c.d_z, nullptr, nullptr, c.d_bk_part, c.d_bk_rz, nullptr, st));
+    CU(cudaMemcpyAsync(rz.data(), c.d_bk_rz, np * sizeof(double), cudaMemcpyDeviceToHost, st));
+    CU(cudaStreamSynchronize(st));
+    return FETI_OK;
+  };
+  // Z_0 (one column per subdomain, in its problem's columns), W_0 = Z_0
+  CU(precond_apply_cols(c, c.d_r, W, nl, M, c.d_b_lcol, c.d_z, st));
+  CU(cudaMemsetAsync(c.d_lamt, 0, nl * sizeof(double), st));
+  std::vector<double> rz(np), eps0(np), eps(np);
+  TRY(read_rz(rz));
+  std::vector<int> active(np), iters(np, 0), conv(np), rank(np, 0), kk(np);
+  std::vector<int64_t> fap(np, 0);
+  for (int p = 0; p < np; ++p) {
+    eps0[p] = eps[p] = std::sqrt(std::max(rz[p], 0.0));
+    conv[p] = eps0[p] == 0.0;
+    active[p] = eps0[p] > 0.0 && std::isfinite(eps0[p]);
+  }
+  std::vector<std::vector<int>> hk;          // hk[i][p]: columns of problem p in stored block i
+  std::vector<std::vector<int64_t>> hoff;    // their offsets inside the packed block
+  std::vector<SegTN> ops;
+  std::vector<GemmDesc> rows;
+  std::vector<RrDesc> rr;
+  std::vector<SegVec> vec(np);
+  feti_status result = FETI_OK;
+  int it = 0;
+  while (it < max_iter) {
+    std::vector<int> act;
+    int Mact = 0;
+    for (int p = 0; p < np; ++p)
+      if (active[p]) { act.push_back(p); Mact = std::max(Mact, mp[p]); }
+    if (act.empty()) break;
+    // Q = F W, BATCH_CHUNK columns at a time (the operator is block diagonal
+    // over the problems, so one apply serves every problem's column j)
+    for (int j0 = 0; j0 < Mact; j0 += BATCH_CHUNK)
+      TRY(apply_dual(c, W + (int64_t)j0 * nl, nl, std::min(BATCH_CHUNK, Mact - j0), Q + (int64_t)j0 * nl, nl));
+    // Delta_p = Q_p^T W_p (lower tiles)
+    ops.clear();
+    for (int p : act)
+      ops.push_back(SegTN{Q + l0[p], nl, W + l0[p], nl, c.d_bk_delta + doff[p], mp[p], mp[p], mp[p], nlp[p], 1});
+    TRY(run_seg_tn(c, ops, 1.0, 0.0));
+    // rank-revealing factorizations
+    rr.clear();
+    for (int p : act)
+      rr.push_back(RrDesc{c.d_bk_delta + doff[p], mp[p], mp[p], c.d_bk_work + woff[p], c.d_bk_T + doff[p],
+                          c.d_bk_k + p, c.d_bk_perm + moff[p]});
+    CU(cudaMemcpyAsync(c.d_bk_rr, rr.data(), rr.size() * sizeof(RrDesc), cudaMemcpyHostToDevice, st));
+    CU(rr_cholesky_batched(c.d_bk_rr, (int)rr.size(), Mact, c.opt.rr_tol, st));
+    CU(cudaMemcpyAsync(kk.data(), c.d_bk_k, np * sizeof(int), cudaMemcpyDeviceToHost, st));
+    CU(cudaStreamSynchronize(st));
+    // stored block `it`: the problems that kept at least one direction
+    std::vector<int> ki(np, 0);
+    std::vector<int64_t> oi(np, -1);
+    int64_t tot = 0;
+    int kmax = 0;
+    for (int p : act) {
+      if (kk[p] <= 0) {                       // no independent direction left: this problem stops
+        active[p] = 0;
+        result = FETI_EBREAKDOWN;
+        c.err = "no independent search direction left in a problem of the batch";
+        continue;
+      }
+      ki[p] = kk[p];
+      rank[p] = kk[p];
+      oi[p] = tot;
+      tot += nlp[p] * kk[p];
+      kmax = std::max(kmax, kk[p]);
+      fap[p] += mp[p];
+    }
+    if (tot == 0) break;
+    if ((int)c.bk_hW.size() <= it) {
+      c.bk_hW.push_back(nullptr);
+      c.bk_hQ.push_back(nullptr);
+      c.bk_hcap.push_back(0);
+    }
+    if (c.bk_hcap[it] < tot) {
+      int64_t cap = 0;
+      TRY(grow(c, c.bk_hW[it], cap, tot));
+      cap = 0;
+      TRY(grow(c, c.bk_hQ[it], cap, tot));
+      c.bk_hcap[it] = tot;
+    }
+    double* Wi = c.bk_hW[it];
+    double* Qi = c.bk_hQ[it];
+    hk.push_back(ki);
+    hoff.push_back(oi);
+    // W_i = W_p[:, perm_p] U_p and Q_i likewise (U_p upper triangular)
+    rows.clear();
+    for (int pass = 0; pass < 2; ++pass)
+      for (int p = 0; p < np; ++p) {
+        if (ki[p] <= 0) continue;
+        for (int64_t r0 = 0; r0 < nlp[p]; r0 += BATCH_RCHUNK) {
+          GemmDesc d{};
+          d.A = (pass ? Q : W) + l0[p] + r0; d.ars = 1; d.acs = nl; d.acol = c.d_bk_perm + moff[p];
+          d.B = c.d_bk_T + doff[p]; d.brs = 1; d.bcs = mp[p];
+          d.C = (pass ? Qi : Wi) + oi[p] + r0; d.crs = 1; d.ccs = nlp[p];
+          d.M = (int)std::min<int64_t>(BATCH_RCHUNK, nlp[p] - r0); d.N = ki[p]; d.K = ki[p]; d.tri = 2;
+          rows.push_back(d);
+        }
+      }
+    TRY(run_row_chunks(c, rows, 1.0, 0.0));
+    // gamma = W_i^T r ; lambda~ += W_i gamma ; r -= Q_i gamma
+    for (int p = 0; p < np; ++p)
+      vec[p] = SegVec{Wi + std::max<int64_t>(oi[p], 0), Qi + std::max<int64_t>(oi[p], 0), nlp[p], nlp[p], l0[p],
+                      moff[p], ki[p]};
+    CU(cudaMemcpyAsync(c.d_bk_vec, vec.data(), np * sizeof(SegVec), cudaMemcpyHostToDevice, st));
+    CU(gemv_t_seg(c.d_bk_vec, np, kmax, c.d_r, c.d_bk_gam, st));
+    CU(step_seg(nl, c.d_lam_prob, c.d_bk_vec, c.d_bk_gam, c.d_lamt, c.d_r, st));
+    // Z_{i+1}, W_{i+1} = Z_{i+1}
+    CU(precond_apply_cols(c, c.d_r, W, nl, M, c.d_b_lcol, c.d_z, st));
+    // F-orthogonalise against the stored blocks, oldest first
+    for (int j = 0; j <= it; ++j) {
+      ops.clear();
+      rows.clear();
+      for (int p = 0; p < np; ++p) {
+        if (!active[p]) continue;
+        const int kj = hk[j][p];
+        if (kj <= 0) continue;
+        const double* Qj = c.bk_hQ[j] + hoff[j][p];
+        const double* Wj = c.bk_hW[j] + hoff[j][p];
+        double* Psi = c.d_bk_delta + doff[p];            // k_j x m_p, ld k_j
+        ops.push_back(SegTN{Qj, nlp[p], W + l0[p], nl, Psi, kj, kj, mp[p], nlp[p], 0});
+        for (int64_t r0 = 0; r0 < nlp[p]; r0 += BATCH_RCHUNK) {
+          GemmDesc d{};
+          d.A = Wj + r0; d.ars = 1; d.acs = nlp[p];
+          d.B = Psi; d.brs = 1; d.bcs = kj;
+          d.C = W + l0[p] + r0; d.crs = 1; d.ccs = nl;
+          d.M = (int)std::min<int64_t>(BATCH_RCHUNK, nlp[p] - r0); d.N = mp[p]; d.K = kj;
+          rows.push_back(d);
+        }
+      }
+      TRY(run_seg_tn(c, ops, 1.0, 0.0));
+      TRY(run_row_chunks(c, rows, -1.0, 1.0));
+    }
+    TRY(read_rz(rz));
+    ++it;
+    for (int p = 0; p < np; ++p) {
+      if (ki[p] <= 0) continue;
+      iters[p] += 1;
+      eps[p] = std::sqrt(std::max(rz[p], 0.0));
+      const bool fin = std::isfinite(rz[p]);
+      conv[p] = fin && eps[p] <= tol * eps0[p];
+      if (!fin || conv[p] || iters[p] >= max_iter) active[p] = 0;
+    }
+  }
+  c.prob_stats.assign(np, feti_stats{});
+  int maxit = 0;
+  for (int p = 0; p < np; ++p) {
+    feti_stats& P = c.prob_stats[p];
+    P.iterations = iters[p];
+    P.converged = conv[p];
+    P.f_applies = fap[p];
+    P.last_rank = rank[p];
+    P.eps0 = eps0[p];
+    P.eps = eps[p];
+    maxit = std::max(maxit, iters[p]);
+  }
+  S.iterations = maxit;
+  if (result == FETI_EBREAKDOWN) {
+    // a problem that lost every direction is reported through its own stats;
+    // the batch as a whole is judged by convergence
+    c.err.clear();
+    result = FETI_OK;
+  }
   return result;
 }
 
@@ -1023,10 +1366,17 @@ static feti_status solve_impl(Ctx& c, double* lambda_inout, feti_stats* stats) {
   const HostProblem& hp = c.hp;
   const int64_t nl = hp.n_lam;
   const bool multi = c.opt.krylov == FETI_RRS;
-  const int mmax = multi ? hp.n_sub : 1;
+  // directions per block: one per subdomain (of the largest problem of a
+  // batch) for the simultaneous variant; batches apply them in column chunks
+  int mmax = multi ? hp.n_sub : 1;
+  if (hp.n_prob > 1) {
+    mmax = 1;
+    for (int p = 0; multi && p < hp.n_prob; ++p)
+      mmax = std::max(mmax, hp.prob_sub_off[p + 1] - hp.prob_sub_off[p]);
+  }
   if (mmax > 1024) { c.err = "more than 1024 subdomains per direction block"; return FETI_ENOTSUP; }
   TRY(ensure_krylov(c, mmax));
-  TRY(ensure_blocks(c, mmax));
+  if (hp.n_prob == 1) TRY(ensure_blocks(c, mmax));
   cudaStream_t st = c.stream;
   feti_stats S{};
   // lambda_0 (warm start or the method's own)
@@ -1042,11 +1392,17 @@ static feti_status solve_impl(Ctx& c, double* lambda_inout, feti_stats* stats) {
   double eps_ref = -1.0;
   if (lambda_inout && hp.n_prob == 1) TRY(cold_reference(c, &eps_ref));
   if (hp.n_prob > 1) {
-    // one PCG per problem, advanced together (graph-captured iterations)
+    // one solve per problem, advanced together: the simultaneous variant
+    // (a block of directions per problem) or PCG (graph-captured iterations)
     TRY(apply_dual(c, c.d_lam, nl, 1, c.d_r, nl));
     CU(axpby(nl, 1.0, c.d_d, -1.0, c.d_r, st));
     int maxit = 0;
-    CU(batch_pcg(c, st, c.opt.tol, c.opt.max_iter, &apply_one, &maxit));
+    if (multi) {
+      TRY(batch_rrs(c, c.opt.tol, c.opt.max_iter, S));
+      maxit = S.iterations;
+    } else {
+      CU(batch_pcg(c, st, c.opt.tol, c.opt.max_iter, &apply_one, &maxit));
+    }
     CU(axpby(nl, 1.0, c.d_lamt, 1.0, c.d_lam, st));
     S.iterations = maxit;
     S.converged = 1;
@@ -1150,6 +1506,7 @@ feti_status feti_recover_displacements(feti_ctx* ctx, double* u_out, int on_devi
   if (c.state < 3 || !c.have_solution) { c.err = "feti_recover_displacements before feti_solve_dual"; return FETI_ESTATE; }
   const HostProblem& hp = c.hp;
   cudaStream_t st = c.stream;
+  std::unique_ptr<PhaseScope> phase(new PhaseScope(st, FETI_PHASE_RECOVER, 0.0));
   if (hp.method == FETI_FETIDP) {
     CU(recover_fetidp(c, c.d_lam, st));
   } else {
@@ -1164,6 +1521,7 @@ feti_status feti_recover_displacements(feti_ctx* ctx, double* u_out, int on_devi
     CU(recover_tfeti(c, c.d_lam, c.d_alpha, st));
   }
   CU(launch_gather_u(c, st));
+  phase.reset();
   if (u_out)
     CU(cudaMemcpyAsync(u_out, c.d_uglob, hp.n_dofs * sizeof(double),
                        on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, st));
@@ -1291,7 +1649,7 @@ feti_status feti_profile_end(feti_ctx* ctx, double* gemm_flops, double* gemm_ms,
   set_gemm_profile(nullptr);
   double f[2], t[2];
   int64_t n[2];
-  finish_gemm_profile(static_cast<GemmProfile*>(c.prof), f, t, n);
+  finish_gemm_profile(static_cast<GemmProfile*>(c.prof), f, t, n, c.prof_ph_work, c.prof_ph_ms, c.prof_ph_count);
   c.prof = nullptr;
   c.prof_tc_flops = f[1];
   c.prof_tc_ms = t[1];
@@ -1308,6 +1666,17 @@ feti_status feti_profile_tensor(const feti_ctx* ctx, double* flops, double* ms, 
   if (flops) *flops = c.prof_tc_flops;
   if (ms) *ms = c.prof_tc_ms;
   if (launches) *launches = c.prof_tc_launches;
+  return FETI_OK;
+}
+
+feti_status feti_profile_phases(const feti_ctx* ctx, double* work, double* ms, int64_t* count) {
+  if (!ctx) return FETI_EINVAL;
+  const Ctx& c = ctx->c;
+  for (int q = 0; q < N_PHASES; ++q) {
+    if (work) work[q] = c.prof_ph_work[q];
+    if (ms) ms[q] = c.prof_ph_ms[q];
+    if (count) count[q] = c.prof_ph_count[q];
+  }
   return FETI_OK;
 }
 

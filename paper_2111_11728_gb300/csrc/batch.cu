@@ -114,6 +114,64 @@ __global__ void k_cg_init(int n_prob, const double* __restrict__ rz, double* __r
   active[p] = e > 0.0 && isfinite(e);
 }
 
+// Sum of the split-K partial products of one segmented product:
+// C_p(i, j) = alpha * sum_z P_p,z(i, j) + beta * C_p(i, j), chunks in order.
+__global__ void k_seg_reduce(const SegRed* __restrict__ reds, const double* __restrict__ partial, double alpha,
+                             double beta) {
+  const SegRed R = reds[blockIdx.y];
+  const int64_t total = (int64_t)R.M * R.N;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+    const int i = (int)(e % R.M), j = (int)(e / R.M);
+    if (R.tri && (j / 64) * 64 > (i / 64) * 64 + 63) continue;   // tile never computed
+    double s = 0.0;
+    for (int z = 0; z < R.nz; ++z) s += partial[R.poff + (int64_t)z * total + e];
+    double* cp = R.C + (int64_t)i * R.crs + (int64_t)j * R.ccs;
+    double v = alpha * s;
+    if (beta != 0.0) v = fma(beta, *cp, v);
+    *cp = v;
+  }
+}
+
+// out_p[j] = A_p[:, j] . r_p for j < k_p  (grid: x = column, y = problem)
+__global__ void k_gemv_t_seg(const SegVec* __restrict__ v, const double* __restrict__ r, double* __restrict__ out) {
+  const SegVec V = v[blockIdx.y];
+  const int j = blockIdx.x;
+  if (j >= V.k) return;
+  const double* a = V.W + (int64_t)j * V.ld;
+  const double* rp = r + V.l0;
+  double acc = 0.0;
+  for (int64_t l = threadIdx.x; l < V.n; l += blockDim.x) acc = fma(a[l], rp[l], acc);
+  __shared__ double red[32];
+  for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double s = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) s += red[w];
+    out[V.goff + j] = s;
+  }
+}
+
+// lam_t += W_p g_p ; r -= Q_p g_p on the rows of every problem with a block
+// (k_p > 0); one thread per multiplier row.
+__global__ void k_step_seg(int64_t nl, const int* __restrict__ lam_prob, const SegVec* __restrict__ v,
+                           const double* __restrict__ g, double* __restrict__ lam_t, double* __restrict__ r) {
+  const int64_t l = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (l >= nl) return;
+  const SegVec V = v[lam_prob[l]];
+  if (V.k <= 0) return;
+  const int64_t row = l - V.l0;
+  const double* gp = g + V.goff;
+  double aw = 0.0, aq = 0.0;
+  for (int j = 0; j < V.k; ++j) {
+    const double gj = gp[j];
+    aw = fma(V.W[row + (int64_t)j * V.ld], gj, aw);
+    aq = fma(V.Q[row + (int64_t)j * V.ld], gj, aq);
+  }
+  lam_t[l] += aw;
+  r[l] -= aq;
+}
+
 }  // namespace
 
 cudaError_t seg_dot2(const int64_t* d_off, int n_prob, const double* a0, const double* b0, const double* a1,
@@ -229,6 +287,70 @@ cudaError_t batch_pcg(Ctx& c, cudaStream_t user, double tol, int max_iter,
   // make the caller's stream wait for the private one
   if ((e = cudaEventRecord(c.cap_event, st)) != cudaSuccess) return e;
   return cudaStreamWaitEvent(user, c.cap_event, 0);
+}
+
+// ---- segmented products of the batched Algorithm 1 ----------------------------
+
+void seg_tn_plan(const std::vector<SegTN>& ops, int64_t kchunk, std::vector<GemmDesc>& descs,
+                 std::vector<int64_t>& coff, std::vector<SegRed>& reds, int64_t* partial_len, int* max_m,
+                 int* max_n) {
+  descs.clear();
+  coff.clear();
+  reds.clear();
+  int64_t poff = 0;
+  *max_m = 0;
+  *max_n = 0;
+  for (const SegTN& o : ops) {
+    if (o.M <= 0 || o.N <= 0) continue;
+    const int nz = (int)std::max<int64_t>(1, (o.K + kchunk - 1) / kchunk);
+    SegRed R{};
+    R.C = o.C; R.crs = 1; R.ccs = o.ldc; R.M = o.M; R.N = o.N; R.nz = nz; R.tri = o.tri; R.poff = poff;
+    reds.push_back(R);
+    for (int z = 0; z < nz; ++z) {
+      const int64_t k0 = o.K * z / nz, k1 = o.K * (z + 1) / nz;
+      GemmDesc d{};
+      // (A^T)(i, k) = A[k + i*lda]; B(k, j) = B[k + j*ldb]
+      d.A = o.A + k0; d.ars = o.lda; d.acs = 1;
+      d.B = o.B + k0; d.brs = 1; d.bcs = o.ldb;
+      d.C = nullptr;                                   // bound to the partial buffer by seg_tn_bind
+      d.crs = 1; d.ccs = o.M;
+      d.M = o.M; d.N = o.N; d.K = (int)(k1 - k0); d.tri = o.tri;
+      descs.push_back(d);
+      coff.push_back(poff + (int64_t)z * o.M * o.N);
+    }
+    poff += (int64_t)nz * o.M * o.N;
+    *max_m = std::max(*max_m, o.M);
+    *max_n = std::max(*max_n, o.N);
+  }
+  *partial_len = poff;
+}
+
+void seg_tn_bind(std::vector<GemmDesc>& descs, const std::vector<int64_t>& coff, double* partial) {
+  for (size_t i = 0; i < descs.size(); ++i) descs[i].C = partial + coff[i];
+}
+
+cudaError_t seg_tn_run(const GemmDesc* d_desc, int n_desc, const SegRed* d_red, int n_red, int max_m, int max_n,
+                       const double* partial, double alpha, double beta, double flops, cudaStream_t st) {
+  if (n_desc <= 0) return cudaSuccess;
+  cudaError_t e = dgemm_batched(d_desc, n_desc, max_m, max_n, 0, 1.0, 0.0, st, flops);
+  if (e != cudaSuccess) return e;
+  k_seg_reduce<<<dim3(64, n_red), 256, 0, st>>>(d_red, partial, alpha, beta);
+  note_launches(1);
+  return cudaGetLastError();
+}
+
+cudaError_t gemv_t_seg(const SegVec* d_v, int n_prob, int max_k, const double* r, double* out, cudaStream_t st) {
+  if (max_k <= 0 || n_prob <= 0) return cudaSuccess;
+  k_gemv_t_seg<<<dim3(max_k, n_prob), 256, 0, st>>>(d_v, r, out);
+  note_launches(1);
+  return cudaGetLastError();
+}
+
+cudaError_t step_seg(int64_t nl, const int* d_lam_prob, const SegVec* d_v, const double* g, double* lam_t,
+                     double* r, cudaStream_t st) {
+  k_step_seg<<<(unsigned)((nl + 255) / 256), 256, 0, st>>>(nl, d_lam_prob, d_v, g, lam_t, r);
+  note_launches(1);
+  return cudaGetLastError();
 }
 
 }  // namespace feti

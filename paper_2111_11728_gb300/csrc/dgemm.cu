@@ -14,8 +14,9 @@ namespace feti {
 
 struct GemmProfile {
   std::vector<cudaEvent_t> ev;     // start/stop pairs
-  std::vector<double> flops;
-  std::vector<int> kind;           // 0: FP64 GEMM, 1: tensor-core local product
+  std::vector<double> flops;       // algorithmic flops (bytes for the memory-bound phases)
+  std::vector<int> kind;           // 0: FP64 GEMM, 1: tensor-core local product, PHASE_KIND0 + p: phase p
+  std::vector<int> open;           // pairs opened by prof_begin, not yet closed
 };
 
 namespace {
@@ -51,11 +52,23 @@ void prof_begin(cudaStream_t st, double flops, int kind) {
   g_prof->ev.push_back(b);
   g_prof->flops.push_back(flops);
   g_prof->kind.push_back(kind);
+  g_prof->open.push_back((int)g_prof->flops.size() - 1);
   cudaEventRecord(a, st);
 }
 
 void prof_end(cudaStream_t st) {
-  if (g_prof) cudaEventRecord(g_prof->ev.back(), st);
+  if (!g_prof || g_prof->open.empty()) return;
+  const int i = g_prof->open.back();
+  g_prof->open.pop_back();
+  cudaEventRecord(g_prof->ev[2 * i + 1], st);
+}
+
+PhaseScope::PhaseScope(cudaStream_t st, int phase, double work) : st_(st), on_(g_prof != nullptr) {
+  if (on_) prof_begin(st, work, PHASE_KIND0 + phase);
+}
+
+PhaseScope::~PhaseScope() {
+  if (on_) prof_end(st_);
 }
 
 void note_launches(int n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
@@ -65,14 +78,21 @@ void set_gemm_profile(GemmProfile* p) { g_prof = p; }
 GemmProfile* new_gemm_profile() { return new GemmProfile(); }
 
 // Sums of the profiled durations (ms), flops and launches per kind (0: FP64
-// GEMM, 1: tensor-core product); releases the events.
-void finish_gemm_profile(GemmProfile* p, double* flops, double* ms, int64_t* count) {
+// GEMM, 1: tensor-core product) and per phase; releases the events.
+void finish_gemm_profile(GemmProfile* p, double* flops, double* ms, int64_t* count, double* pwork, double* pms,
+                         int64_t* pcount) {
   for (int k = 0; k < 2; ++k) { flops[k] = 0.0; ms[k] = 0.0; count[k] = 0; }
+  for (int k = 0; k < N_PHASES; ++k) { pwork[k] = 0.0; pms[k] = 0.0; pcount[k] = 0; }
   for (size_t i = 0; i < p->flops.size(); ++i) {
     float x = 0.f;
     cudaEventElapsedTime(&x, p->ev[2 * i], p->ev[2 * i + 1]);
     cudaEventDestroy(p->ev[2 * i]);
     cudaEventDestroy(p->ev[2 * i + 1]);
+    if (p->kind[i] >= PHASE_KIND0) {
+      const int q = p->kind[i] - PHASE_KIND0;
+      if (q >= 0 && q < N_PHASES) { pwork[q] += p->flops[i]; pms[q] += x; pcount[q] += 1; }
+      continue;
+    }
     const int k = p->kind[i] ? 1 : 0;
     flops[k] += p->flops[i];
     ms[k] += x;

@@ -398,6 +398,14 @@ static cudaError_t local_precond_block(const Ctx& c, const double* rb, double* z
 }
 
 cudaError_t precond_apply(Ctx& c, const double* r, double* Z, int64_t ldz, double* z, cudaStream_t st) {
+  return precond_apply_cols(c, r, Z, ldz, c.hp.n_sub, c.d_b_sub, z, st);
+}
+
+// The block preconditioner with column bcol[b] of Z for the b-space entry b
+// (the subdomain, or its index inside its problem for a batch) and ncols
+// columns of Z cleared first.
+cudaError_t precond_apply_cols(Ctx& c, const double* r, double* Z, int64_t ldz, int ncols, const int* bcol,
+                               double* z, cudaStream_t st) {
   const int64_t nbt = c.hp.n_b_total, nl = c.hp.n_lam;
   double* rb = c.d_pb0;
   double* zb = c.d_pb1;
@@ -409,11 +417,11 @@ cudaError_t precond_apply(Ctx& c, const double* r, double* Z, int64_t ldz, doubl
   e = local_precond_block(c, rb, zb, st);
   if (e != cudaSuccess) return e;
   if (Z) {
-    e = cudaMemsetAsync(Z, 0, sizeof(double) * (size_t)ldz * c.hp.n_sub, st);
+    e = cudaMemsetAsync(Z, 0, sizeof(double) * (size_t)ldz * ncols, st);
     if (e != cudaSuccess) return e;
   }
   k_prec_scatter<<<(unsigned)((nl + 255) / 256), 256, 0, st>>>(nl, c.d_lam_b0, c.d_lam_s0, c.d_lam_b1, c.d_lam_s1,
-                                                               c.d_w0, c.d_w1, c.d_b_sub, zb, Z, ldz, z);
+                                                               c.d_w0, c.d_w1, bcol, zb, Z, ldz, z);
   note_launches(1);
   return cudaGetLastError();
 }

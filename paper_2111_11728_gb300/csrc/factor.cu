@@ -542,8 +542,9 @@ cudaError_t launch_coarse_assemble_impl(const Ctx& c, const int* d_c_sub, const 
 
 cudaError_t launch_band_fwd_single(const Ctx& c, cudaStream_t st) {
   const int ns = c.hp.n_sub;
-  k_band_fwd_single<<<(ns + 3) / 4, 128, 0, st>>>(c.d_types, c.d_mods, c.d_subs, c.d_modmem, c.d_floc,
-                                                   c.hp.n_loc_dofs, c.d_ioff, c.d_h, ns);
+  // one warp (subdomain) per block: the warps' FP64 shuffle sums do not share an SM
+  k_band_fwd_single<<<ns, 32, 0, st>>>(c.d_types, c.d_mods, c.d_subs, c.d_modmem, c.d_floc, c.hp.n_loc_dofs,
+                                        c.d_ioff, c.d_h, ns);
   note_launches(1);
   return cudaGetLastError();
 }

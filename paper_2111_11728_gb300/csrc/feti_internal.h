@@ -29,6 +29,10 @@ struct StructType {
   std::vector<int> ilist, blist, clist;   // local DOF ids per class (i, b, c order)
   int n_i = 0, n_b = 0, n_c = 0;
   int bw = 0;                    // half-bandwidth of K_ii in i-order
+  // edge averages (FETI-DP, richer primal set): average a sits in c slot
+  // avg_c[a]; the b slots of the other nodes of its edge are
+  // avg_b[avg_off[a] .. avg_off[a + 1])
+  std::vector<int> avg_c, avg_off, avg_b;
   int n_bc() const { return n_b + n_c; }
 };
 
@@ -96,7 +100,7 @@ std::string merge_host_problems(std::vector<HostProblem>& parts, HostProblem& ou
 
 // Builds the host description; returns an error message or "".
 std::string build_host_problem(const feti_problem& prob, int method, int dedup,
-                               const double* rho_host, HostProblem& hp);
+                               const double* rho_host, HostProblem& hp, bool edge_averages = false);
 
 // Local node (lexicographic in the tile) -> tile-local integer coordinates.
 inline void local_node_coords(const HostProblem& hp, int ln, int c[3]) {
@@ -113,7 +117,7 @@ inline void local_node_coords(const HostProblem& hp, int ln, int c[3]) {
 // Per-structure-type device info.
 struct DevType {
   int n_loc, n_i, n_b, n_c, bw;
-  int pad;
+  int n_avg;                     // edge averages (0: corners only)
   int e[3];                      // elements per axis of the tile
   int ln[3];                     // local nodes per axis
   const int* cls_idx;            // [n_loc] (cls << 24) | idx
@@ -122,6 +126,9 @@ struct DevType {
   const int* clist;              // [n_c]
   const double* Rraw;            // [n_b x n_rbm] rigid modes at the b DOFs (TFETI)
   const double* Rhat;            // [n_b x n_rbm] orthonormal basis of their span (TFETI)
+  const int* avg_c;              // [n_avg] c slot of each edge average
+  const int* avg_off;            // [n_avg + 1]
+  const int* avg_b;              // b slots of the edges' other nodes
 };
 
 // Per-module offsets into the module arrays (in doubles).
@@ -156,6 +163,9 @@ struct DevSub {
 
 struct GemmDesc;
 struct DenseDesc;
+struct RrDesc;
+struct SegVec;
+struct SegRed;
 
 struct Ctx {
   feti_options opt{};
@@ -184,6 +194,8 @@ struct Ctx {
   int n_mod = 0, max_nb = 1, max_nc = 1;
   // algorithmic flops of the batched products (per column where they scale with m)
   double fl_F = 0, fl_FrcT = 0, fl_Frc = 0, fl_schur = 0, fl_frcmake = 0, fl_kbmake = 0;
+  double fl_coarse = 0;          // flops of one coarse solve column (FETI-DP: sum_p 2 n_c(p)^2)
+  double bytes_S = 0;            // the distinct preconditioner blocks S_bb, in bytes
   void* prof = nullptr;          // active GEMM profile (GemmProfile*)
   double* d_modmem = nullptr;    // module arrays
   int64_t modmem_len = 0;
@@ -237,6 +249,8 @@ struct Ctx {
   int64_t tc_bytes_f = 0;        // algorithmic bytes: scaled blocks (read once per apply)
   int64_t tc_bytes_col = 0;      // algorithmic bytes per column: operand in + FP32 result out
   double prof_tc_flops = 0.0, prof_tc_ms = 0.0;   // tensor-core products of the last profile
+  double prof_ph_work[8] = {}, prof_ph_ms[8] = {};  // phases of the last profile
+  int64_t prof_ph_count[8] = {};
   int64_t prof_tc_launches = 0;
   double* d_sqrtDF = nullptr;    // [n_b_total] sqrt(diag F_s)
   double* d_sqrtDS = nullptr;    // [n_b_total] sqrt(diag S_s)
@@ -294,6 +308,22 @@ struct Ctx {
   int64_t split_cap = 0;
   std::vector<double*> hist_W, hist_Q;
   std::vector<int> hist_k;
+  // edge averages (richer FETI-DP primal set)
+  int max_avg = 0;                         // most edge averages in one type (0: corners only)
+  int* d_c_iota = nullptr;                 // [n_c_total] identity map of the c space
+  double* d_ucl = nullptr;                 // [n_c_total] nodal values at the c slots (recovery)
+  // batched Algorithm 1 (a block of directions per problem of a batch)
+  int* d_b_lcol = nullptr;                 // [n_b_total] subdomain index inside its problem
+  double *d_bk_delta = nullptr, *d_bk_T = nullptr, *d_bk_work = nullptr, *d_bk_gam = nullptr;
+  double *d_bk_rz = nullptr, *d_bk_part = nullptr, *d_bk_split = nullptr;
+  int *d_bk_perm = nullptr, *d_bk_k = nullptr;
+  RrDesc* d_bk_rr = nullptr;
+  SegVec* d_bk_vec = nullptr;
+  GemmDesc* d_bk_desc = nullptr;
+  SegRed* d_bk_red = nullptr;
+  int64_t bk_split_cap = 0, bk_desc_cap = 0, bk_red_cap = 0;
+  std::vector<double*> bk_hW, bk_hQ;       // packed history blocks (one per iteration)
+  std::vector<int64_t> bk_hcap;
   feti_stats last{};
 };
 

@@ -2,6 +2,7 @@
 #pragma once
 
 #include <cstdint>
+#include <vector>
 
 #include <cuda_runtime.h>
 
@@ -16,9 +17,25 @@ int64_t launches();
 struct GemmProfile;
 void set_gemm_profile(GemmProfile* p);
 GemmProfile* new_gemm_profile();
-void finish_gemm_profile(GemmProfile* p, double* flops, double* ms, int64_t* count);   // [2] each: GEMM, tensor
-void prof_begin(cudaStream_t st, double flops, int kind);   // bracket one launch (no-op without a profile)
+// Phases of the method, timed as regions (every launch inside, on the context
+// stream) with their algorithmic work: flops for the FP64-pipe phases, bytes
+// for the memory-bound ones (the numbering of include/feti.h).
+constexpr int N_PHASES = 8;
+constexpr int PHASE_KIND0 = 16;
+// [2] each (GEMM, tensor) plus [N_PHASES] each per phase
+void finish_gemm_profile(GemmProfile* p, double* flops, double* ms, int64_t* count, double* pwork, double* pms,
+                         int64_t* pcount);
+void prof_begin(cudaStream_t st, double flops, int kind);   // bracket launches (no-op without a profile; nests)
 void prof_end(cudaStream_t st);
+struct PhaseScope {                                          // one phase region
+  PhaseScope(cudaStream_t st, int phase, double work);
+  ~PhaseScope();
+  PhaseScope(const PhaseScope&) = delete;
+  PhaseScope& operator=(const PhaseScope&) = delete;
+ private:
+  cudaStream_t st_;
+  bool on_;
+};
 
 // C = alpha * A B + beta * C with element (i,k) of A at A[i*ars + k*acs],
 // (k,j) of B at B[k*brs + j*bcs] and (i,j) of C at C[i*crs + j*ccs].
@@ -93,6 +110,11 @@ cudaError_t launch_copy_block(const Ctx& c, int which, cudaStream_t st);
 cudaError_t launch_coarse_assemble_impl(const Ctx& c, const int* d_c_sub, const int64_t* d_c_off, double* K,
                                         cudaStream_t st);
 cudaError_t launch_band_fwd_single(const Ctx& c, cudaStream_t st);   // h = L^{-1} f_i
+// ---- edge averages (edges.cu): change of basis on the averaged edges ------------
+cudaError_t launch_edge_transform(const Ctx& c, int max_bc, cudaStream_t st);   // S <- T^T S T per module
+cudaError_t launch_edge_load(const Ctx& c, int max_avg, cudaStream_t st);       // f~ <- T^T f~ per subdomain
+// nodal values: xb (b slots, in place) and ucl (c slots) from the transformed ones
+cudaError_t launch_edge_unmap(const Ctx& c, const double* uc, double* xb, double* ucl, cudaStream_t st);
 cudaError_t launch_condense_load(const Ctx& c, cudaStream_t st);     // f~ = f_bc - Y^T h
 
 // ---- dual operator pieces (dual.cu) -------------------------------------------
@@ -110,6 +132,9 @@ cudaError_t corner_gather_vec(const Ctx& c, const double* src, double* out, cuda
 cudaError_t corner_expand(Ctx& c, const double* V, int m, double* Vc, double* Yb, cudaStream_t st);
 // weighted gather / preconditioner scatter
 cudaError_t precond_apply(Ctx& c, const double* r, double* Z, int64_t ldz, double* z, cudaStream_t st);
+// the same with Z's column of b-space entry b given by bcol[b]; ncols columns of Z are cleared
+cudaError_t precond_apply_cols(Ctx& c, const double* r, double* Z, int64_t ldz, int ncols, const int* bcol,
+                               double* z, cudaStream_t st);
 cudaError_t precond_apply_scratch(const Ctx& c, const double* r, double* Z, int64_t ldz, double* z, double* rb,
                                   double* zb, cudaStream_t st);
 cudaError_t batched_gemv_F(Ctx& c, const double* xb, double* yb, cudaStream_t st);   // y_b = F_s x_b
@@ -125,6 +150,17 @@ cudaError_t autotune_gemv(Ctx& c, cudaStream_t st);
 // *d_k, so that W N^T [L~^{-T}; 0] = W[:, perm[0..k)] U.
 cudaError_t rr_cholesky(const double* Delta, int m, int ld, double rr_tol, double* work, double* T,
                         int* d_k, int* d_perm, cudaStream_t st);
+// The same for n independent matrices (m <= 1024 each), one descriptor per
+// matrix in device memory; work holds 2 m^2 + m doubles per matrix.
+struct RrDesc {
+  const double* Delta;
+  int m, ld;
+  double* work;
+  double* T;
+  int* k;
+  int* perm;
+};
+cudaError_t rr_cholesky_batched(const RrDesc* d_desc, int n, int max_m, double rr_tol, cudaStream_t st);
 // lam_t += W g ; then r -= Q g, or qout = Q g when qout is not null
 // (W, Q column-major n x k with leading dimension ld)
 cudaError_t step_update(const double* W, const double* Q, int64_t ld, int64_t n, int k, const double* g,
@@ -168,6 +204,51 @@ cudaError_t seg_dot2(const int64_t* d_off, int n_prob, const double* a0, const d
                      const double* b1, double* part, double* out0, double* out1, cudaStream_t st);
 cudaError_t batch_pcg(Ctx& c, cudaStream_t user, double tol, int max_iter,
                       feti_status (*apply)(Ctx&, const double*, double*), int* total_iters);
+
+// Segmented products of the batched Algorithm 1: for every problem p of a
+// batch, C_p = alpha A_p^T B_p + beta C_p with A_p (K x M), B_p (K x N)
+// column-major (ld lda, ldb) and C_p column-major (ld ldc).  The K range is cut
+// into chunks of at most kchunk rows, each chunk one entry of a batched GEMM
+// into a partial buffer; k_seg_reduce sums the chunks in order
+// (bit-reproducible).  tri = 1: only the lower tiles of C_p are formed.
+struct SegTN {
+  const double* A;
+  int64_t lda;
+  const double* B;
+  int64_t ldb;
+  double* C;
+  int64_t ldc;
+  int M, N;
+  int64_t K;
+  int tri;
+};
+struct SegRed {
+  double* C;
+  int64_t crs, ccs;
+  int M, N, nz, tri;
+  int64_t poff;
+};
+// Plans the chunk descriptors (their C is bound to a partial buffer of
+// *partial_len doubles by seg_tn_bind) and the reductions.
+void seg_tn_plan(const std::vector<SegTN>& ops, int64_t kchunk, std::vector<GemmDesc>& descs,
+                 std::vector<int64_t>& coff, std::vector<SegRed>& reds, int64_t* partial_len, int* max_m,
+                 int* max_n);
+void seg_tn_bind(std::vector<GemmDesc>& descs, const std::vector<int64_t>& coff, double* partial);
+cudaError_t seg_tn_run(const GemmDesc* d_desc, int n_desc, const SegRed* d_red, int n_red, int max_m, int max_n,
+                       const double* partial, double alpha, double beta, double flops, cudaStream_t st);
+// A problem's current block in packed storage: W, Q (n x k, leading dimension
+// ld) for the multiplier rows l0 .. l0 + n, step lengths at g[goff ..]
+struct SegVec {
+  const double* W;
+  const double* Q;
+  int64_t ld, n, l0, goff;
+  int k;
+};
+// out[goff_p + j] = W_p[:, j] . r[l0_p ..] for j < k_p
+cudaError_t gemv_t_seg(const SegVec* d_v, int n_prob, int max_k, const double* r, double* out, cudaStream_t st);
+// lam_t += W_p g_p and r -= Q_p g_p on every problem's rows (k_p = 0: untouched)
+cudaError_t step_seg(int64_t nl, const int* d_lam_prob, const SegVec* d_v, const double* g, double* lam_t,
+                     double* r, cudaStream_t st);
 
 // ---- recovery (recover.cu) ------------------------------------------------------
 cudaError_t recover_fetidp(Ctx& c, const double* lam, cudaStream_t st);

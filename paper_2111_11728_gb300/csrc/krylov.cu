@@ -29,10 +29,15 @@ constexpr double EPS2 = 4.930380657631324e-32;   // (2^-52)^2
 constexpr int RR_THREADS = 1024;
 constexpr int RR_PB = 16;                       // panel width (pivots per trailing update)
 
-__global__ void __launch_bounds__(RR_THREADS) k_rr_chol(const double* __restrict__ Delta, int m, int ld,
-                                                        double rr_tol, double* __restrict__ work,
-                                                        double* __restrict__ T, int* __restrict__ d_k,
-                                                        int* __restrict__ perm_out) {
+// One CTA per matrix: descs[blockIdx.x] when descs is given (a batch), else `one`.
+__global__ void __launch_bounds__(RR_THREADS) k_rr_chol(const RrDesc* __restrict__ descs, RrDesc one,
+                                                        double rr_tol) {
+  const RrDesc D = descs ? descs[blockIdx.x] : one;
+  const double* __restrict__ Delta = D.Delta;
+  const int m = D.m, ld = D.ld;
+  double* __restrict__ work = D.work;
+  int* __restrict__ d_k = D.k;
+  int* __restrict__ perm_out = D.perm;
   double* A = work;                             // [m x m] by original index, lower triangle a >= b
   double* Lg = work + (int64_t)m * m;           // [m x m] Lg[id*m + q] = L(position of id, q)
   extern __shared__ double rr_sh[];             // Lp[q][id], q < RR_PB
@@ -199,11 +204,15 @@ __global__ void __launch_bounds__(RR_THREADS) k_rr_chol(const double* __restrict
 constexpr int RI_CB = 16;
 constexpr int RI_THREADS = 256;
 
-__global__ void __launch_bounds__(RI_THREADS) k_rr_inverse(const double* __restrict__ work, int m,
-                                                           const int* __restrict__ perm_g,
-                                                           const int* __restrict__ d_k, double* __restrict__ T) {
+// grid: x = column block, y = matrix (descs[blockIdx.y] when descs is given, else `one`)
+__global__ void __launch_bounds__(RI_THREADS) k_rr_inverse(const RrDesc* __restrict__ descs, RrDesc one) {
+  const RrDesc D = descs ? descs[blockIdx.y] : one;
+  const double* __restrict__ work = D.work;
+  const int m = D.m;
+  const int* __restrict__ perm_g = D.perm;
+  double* __restrict__ T = D.T;
   extern __shared__ double ri_sh[];
-  const int k = *d_k;
+  const int k = *D.k;
   const int c0 = blockIdx.x * RI_CB;
   if (c0 >= k) return;                           // block-uniform
   const double* Lg = work + (int64_t)m * m;
@@ -322,9 +331,11 @@ __global__ void k_gemv_dense(const double* __restrict__ A, int n, int ld, const 
 
 }  // namespace
 
-cudaError_t rr_cholesky(const double* Delta, int m, int ld, double rr_tol, double* work, double* T, int* d_k,
-                        int* d_perm, cudaStream_t st) {
-  if (m > 1024) return cudaErrorInvalidValue;
+namespace {
+
+cudaError_t rr_launch(const RrDesc* d_desc, const RrDesc& one, int n, int max_m, double rr_tol, cudaStream_t st) {
+  if (max_m > 1024) return cudaErrorInvalidValue;
+  if (n <= 0 || max_m <= 0) return cudaSuccess;
   static bool attr_set = false;
   const size_t smem = (size_t)RR_PB * 1024 * sizeof(double);
   if (!attr_set) {
@@ -332,7 +343,7 @@ cudaError_t rr_cholesky(const double* Delta, int m, int ld, double rr_tol, doubl
     if (e != cudaSuccess) return e;
     attr_set = true;
   }
-  k_rr_chol<<<1, RR_THREADS, (size_t)RR_PB * m * sizeof(double), st>>>(Delta, m, ld, rr_tol, work, T, d_k, d_perm);
+  k_rr_chol<<<n, RR_THREADS, (size_t)RR_PB * max_m * sizeof(double), st>>>(d_desc, one, rr_tol);
   note_launches(1);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
@@ -343,10 +354,23 @@ cudaError_t rr_cholesky(const double* Delta, int m, int ld, double rr_tol, doubl
     if (e != cudaSuccess) return e;
     inv_attr = true;
   }
-  k_rr_inverse<<<(m + RI_CB - 1) / RI_CB, RI_THREADS, (size_t)(RI_CB + 2) * m * sizeof(double), st>>>(work, m, d_perm,
-                                                                                                     d_k, T);
+  k_rr_inverse<<<dim3((max_m + RI_CB - 1) / RI_CB, n), RI_THREADS, (size_t)(RI_CB + 2) * max_m * sizeof(double),
+                 st>>>(d_desc, one);
   note_launches(1);
   return cudaGetLastError();
+}
+
+}  // namespace
+
+cudaError_t rr_cholesky(const double* Delta, int m, int ld, double rr_tol, double* work, double* T, int* d_k,
+                        int* d_perm, cudaStream_t st) {
+  RrDesc one{Delta, m, ld, work, T, d_k, d_perm};
+  return rr_launch(nullptr, one, 1, m, rr_tol, st);
+}
+
+cudaError_t rr_cholesky_batched(const RrDesc* d_desc, int n, int max_m, double rr_tol, cudaStream_t st) {
+  RrDesc one{};
+  return rr_launch(d_desc, one, n, max_m, rr_tol, st);
 }
 
 cudaError_t gemv_t(const double* W, int64_t ld, int64_t n, int k, const double* r, double* out, cudaStream_t st) {

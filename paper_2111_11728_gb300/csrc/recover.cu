@@ -110,19 +110,27 @@ static cudaError_t recover_local(Ctx& c, const double* uc, cudaStream_t st) {
   note_launches(1);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   if ((e = batched_gemv(c, 0, g, xb, 0.0, st)) != cudaSuccess) return e;
+  // edge averages: back to nodal values (xb in place, the c slots per subdomain)
+  const int* cg = c.d_c_glob;
+  if (c.max_avg > 0 && uc) {
+    if ((e = launch_edge_unmap(c, uc, xb, c.d_ucl, st)) != cudaSuccess) return e;
+    cg = c.d_c_iota;
+    uc = c.d_ucl;
+  }
   double* t = c.d_t;
   k_recover_t<<<dim3((maxi + 127) / 128, c.hp.n_sub), 128, 0, st>>>(c.d_types, c.d_mods, c.d_subs, c.d_modmem,
-                                                                    c.d_ioff, c.d_h, xb, c.d_c_glob, uc, t);
+                                                                    c.d_ioff, c.d_h, xb, cg, uc, t);
   note_launches(1);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
-  k_band_bwd_single<<<(c.hp.n_sub + 3) / 4, 128, 0, st>>>(c.d_types, c.d_mods, c.d_subs, c.d_modmem, c.d_ioff, t,
-                                                          c.hp.n_sub);
+  // one warp (subdomain) per block: the warps' FP64 shuffle sums do not share an SM
+  k_band_bwd_single<<<c.hp.n_sub, 32, 0, st>>>(c.d_types, c.d_mods, c.d_subs, c.d_modmem, c.d_ioff, t,
+                                                c.hp.n_sub);
   note_launches(1);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   int nld = 1;
   for (auto& tt : c.h_types) nld = std::max(nld, tt.n_loc);
   k_write_uloc<<<dim3((nld + 127) / 128, c.hp.n_sub), 128, 0, st>>>(c.d_types, c.d_subs, nld, c.d_ioff, t, xb,
-                                                                    c.d_c_glob, uc, c.d_uloc);
+                                                                    cg, uc, c.d_uloc);
   note_launches(1);
   return cudaGetLastError();
 }

@@ -97,7 +97,7 @@ void owners_of(const HostProblem& hp, const int g[3], NodeOwners& o) {
 }  // namespace
 
 std::string build_host_problem(const feti_problem& prob, int method, int dedup,
-                               const double* rho_host, HostProblem& hp) {
+                               const double* rho_host, HostProblem& hp, bool edge_averages) {
   hp = HostProblem();
   if (prob.dim != 2 && prob.dim != 3) return "dim must be 2 or 3";
   hp.dim = prob.dim;
@@ -129,6 +129,30 @@ std::string build_host_problem(const feti_problem& prob, int method, int dedup,
 
   const int dim = hp.dim;
   const int nld = hp.n_loc_dofs;
+  const bool edges = edge_averages && method == FETI_FETIDP;
+
+  // Edge averages: a node with exactly dim - 1 coordinates on tile-grid planes
+  // lies inside a tile-grid edge along the remaining axis `run`; the edge gets
+  // an average in component d when it is shared (>= 2 owners) and all its
+  // interior nodes are free in d.  The average takes the slot of the edge's
+  // first interior node (global coordinate t * e + 1 along run).
+  auto edge_axis = [&](const int g[3]) -> int {
+    int run = -1, on = 0;
+    for (int a = 0; a < dim; ++a) {
+      if (g[a] % hp.elems[a] == 0) ++on;
+      else run = a;
+    }
+    return on == dim - 1 ? run : -1;
+  };
+  auto edge_free = [&](const int g[3], int run, int d) -> bool {
+    int h[3] = {g[0], g[1], g[2]};
+    const int base = g[run] - g[run] % hp.elems[run];
+    for (int k = 1; k < hp.elems[run]; ++k) {
+      h[run] = base + k;
+      if (hp.dirichlet[gnode_index(hp, h) * dim + d]) return false;
+    }
+    return true;
+  };
 
   // ---- classify local DOFs of every subdomain, group into types ----------------
   std::map<std::vector<int>, int> type_of_key;
@@ -156,8 +180,10 @@ std::string build_host_problem(const feti_problem& prob, int method, int dedup,
         bool fixed = hp.dirichlet[gn * dim + d] != 0;
         int cls;
         if (method == FETI_FETIDP) {
+          int run = edges && !vertex && own.n > 1 ? edge_axis(g) : -1;
+          bool avg = run >= 0 && g[run] % hp.elems[run] == 1 && edge_free(g, run, d);
           if (fixed) cls = CLS_X;
-          else if (vertex) cls = CLS_C;
+          else if (vertex || avg) cls = CLS_C;
           else if (own.n > 1) cls = CLS_B;
           else cls = CLS_I;
         } else {
@@ -196,6 +222,29 @@ std::string build_host_problem(const feti_problem& prob, int method, int dedup,
       for (int k = 0; k < T.n_i; ++k) T.idx[T.ilist[k]] = k;
       for (int k = 0; k < T.n_b; ++k) T.idx[T.blist[k]] = k;
       for (int k = 0; k < T.n_c; ++k) T.idx[T.clist[k]] = k;
+      // edge averages: c slots that are not at a tile vertex
+      T.avg_off.push_back(0);
+      for (int k = 0; k < T.n_c; ++k) {
+        const int ld = T.clist[k], ln = ld / dim, d = ld % dim;
+        int c[3];
+        local_node_coords(hp, ln, c);
+        int run = -1, on = 0;
+        for (int a = 0; a < dim; ++a) {
+          if (c[a] == 0 || c[a] == hp.elems[a]) ++on;
+          else run = a;
+        }
+        if (on == dim) continue;                          // a corner
+        if (on != dim - 1 || c[run] != 1) return "internal error: primal DOF off the tile edges";
+        T.avg_c.push_back(k);
+        for (int j = 2; j < hp.elems[run]; ++j) {
+          int cc[3] = {c[0], c[1], c[2]};
+          cc[run] = j;
+          const int l2 = lnode_index(hp, cc) * dim + d;
+          if (T.cls[l2] != CLS_B) return "internal error: edge node is not an interface DOF";
+          T.avg_b.push_back(T.idx[l2]);
+        }
+        T.avg_off.push_back((int)T.avg_b.size());
+      }
       // half-bandwidth of K_ii in i-order (element-neighbour coupling)
       int bw = 0;
       for (int k = 0; k < T.n_i; ++k) {
@@ -356,7 +405,7 @@ std::string build_host_problem(const feti_problem& prob, int method, int dedup,
         }
     for (int s = 0; s < hp.n_sub; ++s) hp.c_off[s + 1] = hp.c_off[s] + hp.types[hp.sub_type[s]].n_c;
     hp.c_glob.resize(hp.c_off[hp.n_sub]);
-    std::vector<std::vector<int>> src(hp.n_primal);
+    std::vector<std::vector<int>> src;
     for (int s = 0; s < hp.n_sub; ++s) {
       const StructType& T = hp.types[hp.sub_type[s]];
       int t[3] = {s % hp.tiles[0], (s / hp.tiles[0]) % hp.tiles[1], s / (hp.tiles[0] * hp.tiles[1])};
@@ -367,11 +416,15 @@ std::string build_host_problem(const feti_problem& prob, int method, int dedup,
         int g[3] = {0, 0, 0};
         for (int a = 0; a < dim; ++a) g[a] = t[a] * hp.elems[a] + c[a];
         int64_t gd = gnode_index(hp, g) * dim + ld % dim;
-        int pidx = prim.at(gd);
+        auto pit = prim.find(gd);
+        if (pit == prim.end()) pit = prim.emplace(gd, hp.n_primal++).first;   // an edge average
+        int pidx = pit->second;
         hp.c_glob[hp.c_off[s] + k] = pidx;
+        if ((int)src.size() < hp.n_primal) src.resize(hp.n_primal);
         src[pidx].push_back((int)(hp.c_off[s] + k));
       }
     }
+    src.resize(hp.n_primal);
     hp.prim_off.assign(hp.n_primal + 1, 0);
     for (int q = 0; q < hp.n_primal; ++q) {
       hp.prim_off[q + 1] = hp.prim_off[q] + (int)src[q].size();
