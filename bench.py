@@ -140,6 +140,7 @@ def parse():
     ap.add_argument("--batch-rrs-max-iter", type=int, default=60)
     ap.add_argument("--batch-krylov", default="both", choices=["pcg", "rrs", "both"])
     ap.add_argument("--no-academic", action="store_true")
+    ap.add_argument("--forms-3d-primal", default="corners", choices=["corners", "edges"])
     ap.add_argument("--primal-3d", action="store_true",
                     help="also compare corners with corners + edge averages on the 3D workload (minutes)")
     return ap.parse_args()
@@ -260,7 +261,7 @@ def apply_timing(fg, torch, stream, flush, s, n, m, reps=5):
     return float(np.median(ts))
 
 
-def run_forms(p, a, fg, torch, dev, stream, flush, forms, max_iter, m_apply, reps=2):
+def run_forms(p, a, fg, torch, dev, stream, flush, forms, max_iter, m_apply, reps=2, primal=0):
     """Time-to-solve (factorize + refined solve + recover) and the apply of m_apply
     columns for each precision form on problem p, at the same FP64 relative dual
     residual a.tol; solutions compared with the FP64 form's."""
@@ -269,7 +270,7 @@ def run_forms(p, a, fg, torch, dev, stream, flush, forms, max_iter, m_apply, rep
     out, sols = {}, {}
     for name, prec, repl in forms:
         s = fg.Solver(fg.FETI_FETIDP, fg.FETI_SCALING_K, fg.FETI_RRS, tol=a.tol, max_iter=max_iter,
-                      stream=stream.cuda_stream, precision=prec, fp64_residual=repl)
+                      stream=stream.cuda_stream, precision=prec, fp64_residual=repl, primal=primal)
         s.setup(p, rho=rho_d, f=f_d, on_device=True)
         u = torch.empty(p.n_dofs, dtype=torch.float64, device=dev)
         times, st = [], None
@@ -345,9 +346,11 @@ def compare_forms_3d(a, fg, torch, dev, stream, flush):
     """The same comparison on the 3D workload: 8^3 subdomains of 8^3 H8
     elements, smoothed density field in [1e-3, 1] (823,875 DOF)."""
     p = workloads.config4(tiles=a.tiles_3d, elems=8)
+    edges = a.forms_3d_primal == "edges"
     out = {"workload": f"3D H8: {a.tiles_3d}^3 subdomains of 8^3 elements, smoothed field in [1e-3, 1]",
-           "rel_tol": a.tol, "max_iter": 60}
-    out.update(run_forms(p, a, fg, torch, dev, stream, flush, precision_forms(fg), 60, 512, reps=1))
+           "rel_tol": a.tol, "max_iter": 60, "primal": "corners + edge averages" if edges else "corners"}
+    out.update(run_forms(p, a, fg, torch, dev, stream, flush, precision_forms(fg), 60, 512, reps=1,
+                         primal=fg.FETI_PRIMAL_EDGES if edges else fg.FETI_PRIMAL_CORNERS))
     return out
 
 
@@ -470,6 +473,8 @@ def compare_batch(a, fg, torch, dev, stream, krylov="pcg"):
     u_b = torch.empty(n_dofs, dtype=torch.float64, device=dev)
     for k in range(2):
         torch.cuda.synchronize()
+        if k == 1 and krylov == "rrs":          # (the PCG arm captures its iteration as a CUDA graph)
+            fg.feti_profile_begin(ctx)
         e = [ev() for _ in range(3)]
         e[0].record(stream)
         fg.feti_factorize(ctx)
@@ -478,6 +483,10 @@ def compare_batch(a, fg, torch, dev, stream, krylov="pcg"):
         fg.feti_recover_displacements(ctx, u_b, True)
         e[2].record(stream)
         torch.cuda.synchronize()
+    batch_phases = None
+    if krylov == "rrs":
+        fg.feti_profile_end(ctx)
+        batch_phases = phase_rooflines(fg.feti_profile_phases(ctx), 1, e[0].elapsed_time(e[2]) / 1e3)
     res = [fg.feti_problem_result(ctx, q) for q in range(len(probs))]
     its = [r[3].iterations for r in res]
     conv_b = [bool(r[3].converged) for r in res]
@@ -488,6 +497,7 @@ def compare_batch(a, fg, torch, dev, stream, krylov="pcg"):
                       "f_applies": sum(r[3].f_applies for r in res),
                       "f_applies_per_s": sum(r[3].f_applies for r in res) / (e[1].elapsed_time(e[2]) / 1e3)}
     out["batched"]["problems_per_s"] = len(probs) / (out["batched"]["total_ms"] / 1e3)
+    out["batched"]["phases"] = batch_phases
     u_b = u_b.cpu().numpy()
     offs = [r[0] for r in res]
     fg.feti_destroy(ctx)

@@ -676,9 +676,9 @@ static feti_status setup_impl(Ctx& c, const feti_problem* probs, int n) {
       frow[q] = (int)rows;
       rows += c.h_types[c.h_mods[q].type].n_b;
     }
-    c.tc_aug = (hp.method == FETI_FETIDP && hp.n_primal > 0 && c.max_nc <= 24) ? 1 : 0;
+    c.tc_aug = (hp.method == FETI_FETIDP && hp.n_primal > 0 && c.max_nc <= 64) ? 1 : 0;
     if (hp.method == FETI_FETIDP && hp.n_primal > 0 && !c.tc_aug) {
-      c.err = "precision form: more than 24 corner DOFs per subdomain";
+      c.err = "precision form: more than 64 primal DOFs per subdomain";
       return FETI_ENOTSUP;
     }
     const int kc = tc_chunk(c.opt.precision);
@@ -1207,21 +1207,33 @@ static feti_status batch_rrs(Ctx& c, double tol, int max_iter, feti_stats& S) {
     if (act.empty()) break;
     // Q = F W, BATCH_CHUNK columns at a time (the operator is block diagonal
     // over the problems, so one apply serves every problem's column j)
-    for (int j0 = 0; j0 < Mact; j0 += BATCH_CHUNK)
-      TRY(apply_dual(c, W + (int64_t)j0 * nl, nl, std::min(BATCH_CHUNK, Mact - j0), Q + (int64_t)j0 * nl, nl));
-    // Delta_p = Q_p^T W_p (lower tiles)
-    ops.clear();
-    for (int p : act)
-      ops.push_back(SegTN{Q + l0[p], nl, W + l0[p], nl, c.d_bk_delta + doff[p], mp[p], mp[p], mp[p], nlp[p], 1});
-    TRY(run_seg_tn(c, ops, 1.0, 0.0));
-    // rank-revealing factorizations
-    rr.clear();
-    for (int p : act)
-      rr.push_back(RrDesc{c.d_bk_delta + doff[p], mp[p], mp[p], c.d_bk_work + woff[p], c.d_bk_T + doff[p],
-                          c.d_bk_k + p, c.d_bk_perm + moff[p]});
-    CU(cudaMemcpyAsync(c.d_bk_rr, rr.data(), rr.size() * sizeof(RrDesc), cudaMemcpyHostToDevice, st));
-    CU(rr_cholesky_batched(c.d_bk_rr, (int)rr.size(), Mact, c.opt.rr_tol, st));
-    CU(cudaMemcpyAsync(kk.data(), c.d_bk_k, np * sizeof(int), cudaMemcpyDeviceToHost, st));
+    {
+      // the stacked apply computes all Mact columns of every subdomain (the
+      // algorithmic count takes each problem's own m_p)
+      double fl = 0.0;
+      for (int p : act) fl += (double)mp[p] * mp[p] * (c.fl_F + c.fl_FrcT + c.fl_Frc + c.fl_coarse) / hp.n_sub;
+      PhaseScope ph(st, FETI_PHASE_APPLY, fl);
+      for (int j0 = 0; j0 < Mact; j0 += BATCH_CHUNK)
+        TRY(apply_dual(c, W + (int64_t)j0 * nl, nl, std::min(BATCH_CHUNK, Mact - j0), Q + (int64_t)j0 * nl, nl));
+    }
+    {
+      double fl = 0.0;
+      for (int p : act) fl += (double)nlp[p] * mp[p] * (mp[p] + 1.0);
+      PhaseScope ph(st, FETI_PHASE_GRAM, fl);
+      // Delta_p = Q_p^T W_p (lower tiles)
+      ops.clear();
+      for (int p : act)
+        ops.push_back(SegTN{Q + l0[p], nl, W + l0[p], nl, c.d_bk_delta + doff[p], mp[p], mp[p], mp[p], nlp[p], 1});
+      TRY(run_seg_tn(c, ops, 1.0, 0.0));
+      // rank-revealing factorizations
+      rr.clear();
+      for (int p : act)
+        rr.push_back(RrDesc{c.d_bk_delta + doff[p], mp[p], mp[p], c.d_bk_work + woff[p], c.d_bk_T + doff[p],
+                            c.d_bk_k + p, c.d_bk_perm + moff[p]});
+      CU(cudaMemcpyAsync(c.d_bk_rr, rr.data(), rr.size() * sizeof(RrDesc), cudaMemcpyHostToDevice, st));
+      CU(rr_cholesky_batched(c.d_bk_rr, (int)rr.size(), Mact, c.opt.rr_tol, st));
+      CU(cudaMemcpyAsync(kk.data(), c.d_bk_k, np * sizeof(int), cudaMemcpyDeviceToHost, st));
+    }
     CU(cudaStreamSynchronize(st));
     // stored block `it`: the problems that kept at least one direction
     std::vector<int> ki(np, 0);
@@ -1273,17 +1285,35 @@ static feti_status batch_rrs(Ctx& c, double tol, int max_iter, feti_stats& S) {
           rows.push_back(d);
         }
       }
-    TRY(run_row_chunks(c, rows, 1.0, 0.0));
+    {
+      double fl = 0.0;
+      for (int p = 0; p < np; ++p) fl += 2.0 * nlp[p] * ki[p] * (ki[p] + 1.0);
+      PhaseScope ph(st, FETI_PHASE_GRAM, fl);
+      TRY(run_row_chunks(c, rows, 1.0, 0.0));
+    }
     // gamma = W_i^T r ; lambda~ += W_i gamma ; r -= Q_i gamma
     for (int p = 0; p < np; ++p)
       vec[p] = SegVec{Wi + std::max<int64_t>(oi[p], 0), Qi + std::max<int64_t>(oi[p], 0), nlp[p], nlp[p], l0[p],
                       moff[p], ki[p]};
-    CU(cudaMemcpyAsync(c.d_bk_vec, vec.data(), np * sizeof(SegVec), cudaMemcpyHostToDevice, st));
-    CU(gemv_t_seg(c.d_bk_vec, np, kmax, c.d_r, c.d_bk_gam, st));
-    CU(step_seg(nl, c.d_lam_prob, c.d_bk_vec, c.d_bk_gam, c.d_lamt, c.d_r, st));
+    {
+      double by = 0.0;
+      for (int p = 0; p < np; ++p) by += 8.0 * nlp[p] * (3.0 * ki[p] + 4.0);
+      PhaseScope ph(st, FETI_PHASE_STEP, by);
+      CU(cudaMemcpyAsync(c.d_bk_vec, vec.data(), np * sizeof(SegVec), cudaMemcpyHostToDevice, st));
+      CU(gemv_t_seg(c.d_bk_vec, np, kmax, c.d_r, c.d_bk_gam, st));
+      CU(step_seg(nl, c.d_lam_prob, c.d_bk_vec, c.d_bk_gam, c.d_lamt, c.d_r, st));
+    }
     // Z_{i+1}, W_{i+1} = Z_{i+1}
-    CU(precond_apply_cols(c, c.d_r, W, nl, M, c.d_b_lcol, c.d_z, st));
+    {
+      PhaseScope ph(st, FETI_PHASE_PRECOND, c.bytes_S + 8.0 * (2.0 * nl + 2.0 * hp.n_b_total + (double)nl * M));
+      CU(precond_apply_cols(c, c.d_r, W, nl, M, c.d_b_lcol, c.d_z, st));
+    }
     // F-orthogonalise against the stored blocks, oldest first
+    double fl_o = 0.0;
+    for (int j = 0; j <= it; ++j)
+      for (int p = 0; p < np; ++p)
+        if (active[p] && hk[j][p] > 0) fl_o += 4.0 * nlp[p] * hk[j][p] * mp[p];
+    std::unique_ptr<PhaseScope> ph_o(new PhaseScope(st, FETI_PHASE_ORTHO, fl_o));
     for (int j = 0; j <= it; ++j) {
       ops.clear();
       rows.clear();
@@ -1307,6 +1337,7 @@ static feti_status batch_rrs(Ctx& c, double tol, int max_iter, feti_stats& S) {
       TRY(run_seg_tn(c, ops, 1.0, 0.0));
       TRY(run_row_chunks(c, rows, -1.0, 1.0));
     }
+    ph_o.reset();
     TRY(read_rz(rz));
     ++it;
     for (int p = 0; p < np; ++p) {

@@ -24,6 +24,7 @@ namespace {
 
 constexpr int TC_M = 128;
 constexpr int TC_NMAX = 256;
+constexpr int TC_MAX_NC = 64;        // primal DOFs per subdomain carried in the K-extension
 constexpr int TC_THREADS = 128;
 constexpr uint32_t TC_TMEM_COLS = 256;
 constexpr long long TC_SPIN_LIMIT = 1ll << 22;
@@ -101,9 +102,10 @@ struct TcFmt<1> {
 };
 
 // K extent of a subdomain in the tensor-core operands: n_b rounded up to the
-// format's chunk kc, plus one chunk for the corner coupling when appended.
+// format's chunk kc, plus the corner coupling (n_c columns, rounded up to kc)
+// when appended.
 __host__ __device__ __forceinline__ int k_extent(int nb, int nc, int aug, int kc) {
-  return (nb + kc - 1) / kc * kc + ((aug && nc > 0) ? kc : 0);
+  return (nb + kc - 1) / kc * kc + ((aug && nc > 0) ? (nc + kc - 1) / kc * kc : 0);
 }
 
 __device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap* map, int x, int y, uint32_t bar) {
@@ -616,7 +618,7 @@ __global__ void k_make_arena(const DevType* __restrict__ types, const DevModule*
 // C_s = F_rc,s^T X_b(s) = Frc_hat_s^T (D^{1/2} X_b(s)), read from the gathered
 // operand (high + low parts) and the FP32 copy of Frc_hat.  One block per
 // subdomain and 128 directions; K is staged 32 rows at a time.
-template <int FMT>
+template <int FMT, int NCM>
 __global__ void __launch_bounds__(256) k_frct_lowp(const DevType* __restrict__ types,
                                                    const DevModule* __restrict__ mods,
                                                    const DevSub* __restrict__ subs, const float* __restrict__ fmem,
@@ -625,7 +627,8 @@ __global__ void __launch_bounds__(256) k_frct_lowp(const DevType* __restrict__ t
                                                    const typename TcFmt<FMT>::T* __restrict__ xb_lo, int64_t nbp,
                                                    int m, double* __restrict__ Cb, int64_t nct) {
   using F = TcFmt<FMT>;
-  __shared__ float fs[32][24];
+  constexpr int NQ = NCM / 2;                       // corner columns per thread group
+  __shared__ float fs[32][NCM];
   __shared__ float xs[32][129];
   const DevSub S = subs[blockIdx.y];
   const DevType T = types[S.type];
@@ -636,12 +639,12 @@ __global__ void __launch_bounds__(256) k_frct_lowp(const DevType* __restrict__ t
   const int tid = threadIdx.x, jj = tid & 127, cg = tid >> 7;
   const typename F::T* xh = xb_hi + bpad[blockIdx.y];
   const typename F::T* xl = xb_lo ? xb_lo + bpad[blockIdx.y] : nullptr;
-  float acc[12];
+  float acc[NQ];
 #pragma unroll
-  for (int q = 0; q < 12; ++q) acc[q] = 0.f;
+  for (int q = 0; q < NQ; ++q) acc[q] = 0.f;
   for (int k0 = 0; k0 < nb; k0 += 32) {
-    for (int e = tid; e < 32 * 24; e += 256) {
-      const int kk = e / 24, c = e % 24, k = k0 + kk;
+    for (int e = tid; e < 32 * NCM; e += 256) {
+      const int kk = e / NCM, c = e % NCM, k = k0 + kk;
       fs[kk][c] = (k < nb && c < nc) ? Fr[(int64_t)k * nc + c] : 0.0f;
     }
     for (int e = tid; e < 32 * 128; e += 256) {
@@ -658,22 +661,23 @@ __global__ void __launch_bounds__(256) k_frct_lowp(const DevType* __restrict__ t
     for (int kk = 0; kk < 32; ++kk) {
       const float x = xs[kk][jj];
 #pragma unroll
-      for (int q = 0; q < 12; ++q) acc[q] = fmaf(fs[kk][cg * 12 + q], x, acc[q]);
+      for (int q = 0; q < NQ; ++q) acc[q] = fmaf(fs[kk][cg * NQ + q], x, acc[q]);
     }
     __syncthreads();
   }
   const int j = j0 + jj;
   if (j < m) {
 #pragma unroll
-    for (int q = 0; q < 12; ++q) {
-      const int c = cg * 12 + q;
+    for (int q = 0; q < NQ; ++q) {
+      const int c = cg * NQ + q;
       if (c < nc) Cb[S.c_off + c + (int64_t)j * nct] = static_cast<double>(acc[q]);
     }
   }
 }
 
 // The K-extension of the operand: V_s (the coarse correction at the
-// subdomain's corners) in the chunk after its b range, zero past n_c.
+// subdomain's corners) in the chunks after its b range, zero past n_c.
+// blockDim.x covers the widest extension; each subdomain writes its own.
 template <int FMT, int PASSES>
 __global__ void k_put_v(const DevType* __restrict__ types, const DevSub* __restrict__ subs,
                         const int64_t* __restrict__ bpad, const int* __restrict__ cg, const double* __restrict__ V,
@@ -683,7 +687,7 @@ __global__ void k_put_v(const DevType* __restrict__ types, const DevSub* __restr
   const DevSub S = subs[blockIdx.y];
   const DevType T = types[S.type];
   const int c = threadIdx.x, j = blockIdx.x * blockDim.y + threadIdx.y;
-  if (j >= m || T.n_c == 0) return;
+  if (j >= m || T.n_c == 0 || c >= (T.n_c + F::KC - 1) / F::KC * F::KC) return;
   const float v = c < T.n_c ? static_cast<float>(V[cg[S.c_off + c] + (int64_t)j * np]) : 0.0f;
   const int64_t o = (int64_t)j * nbp + bpad[blockIdx.y] + k_extent(T.n_b, 0, 0, F::KC) + c;
   const typename F::T hi = F::round(v);
@@ -892,8 +896,10 @@ void launch_gather(const Ctx& c, const double* X, int64_t ldx, int m, cudaStream
 template <int FMT, int PASSES>
 void launch_put_v(const Ctx& c, const double* V, int m, cudaStream_t st) {
   using T = typename TcFmt<FMT>::T;
+  constexpr int KC = TcFmt<FMT>::KC;
+  const int ext = (c.max_nc + KC - 1) / KC * KC;      // widest corner extension (<= 64)
   dim3 g((m + 7) / 8, c.hp.n_sub);
-  k_put_v<FMT, PASSES><<<g, dim3(TcFmt<FMT>::KC, 8), 0, st>>>(
+  k_put_v<FMT, PASSES><<<g, dim3(ext, 8), 0, st>>>(
       c.d_types, c.d_subs, c.d_bpad, c.d_c_glob, V, c.hp.n_primal, m, static_cast<T*>(c.d_xb_hi),
       PASSES == 3 ? static_cast<T*>(c.d_xb_lo) : nullptr, c.nbp_total);
 }
@@ -947,20 +953,21 @@ cudaError_t tc_gather(const Ctx& c, const double* X, int64_t ldx, int m, cudaStr
 
 // Cb = F_rc^T X_b per subdomain (FP32) from the gathered operand, then the
 // corner assembly Vraw = sum over the copies of each primal DOF.
-cudaError_t tc_corner_reduce(const Ctx& c, int m, double* Vraw, cudaStream_t st) {
-  if (c.max_nc > 24) return cudaErrorInvalidValue;
+template <int FMT, int NCM>
+void launch_frct_lowp(const Ctx& c, int m, cudaStream_t st) {
+  using T = typename TcFmt<FMT>::T;
   dim3 g((m + 127) / 128, c.hp.n_sub);
-  const bool split = tc_split(c);
-  if (tc_format(c) == 0)
-    k_frct_lowp<0><<<g, 256, 0, st>>>(c.d_types, c.d_mods, c.d_subs, c.d_fmem, c.d_bpad,
-                                      static_cast<const float*>(c.d_xb_hi),
-                                      split ? static_cast<const float*>(c.d_xb_lo) : nullptr, c.nbp_total, m, c.d_Cb,
-                                      c.n_c_total);
-  else
-    k_frct_lowp<1><<<g, 256, 0, st>>>(c.d_types, c.d_mods, c.d_subs, c.d_fmem, c.d_bpad,
-                                      static_cast<const __nv_bfloat16*>(c.d_xb_hi),
-                                      split ? static_cast<const __nv_bfloat16*>(c.d_xb_lo) : nullptr, c.nbp_total, m,
-                                      c.d_Cb, c.n_c_total);
+  k_frct_lowp<FMT, NCM><<<g, 256, 0, st>>>(c.d_types, c.d_mods, c.d_subs, c.d_fmem, c.d_bpad,
+                                           static_cast<const T*>(c.d_xb_hi),
+                                           tc_split(c) ? static_cast<const T*>(c.d_xb_lo) : nullptr, c.nbp_total, m,
+                                           c.d_Cb, c.n_c_total);
+}
+
+cudaError_t tc_corner_reduce(const Ctx& c, int m, double* Vraw, cudaStream_t st) {
+  if (c.max_nc > TC_MAX_NC) return cudaErrorInvalidValue;
+  const bool wide = c.max_nc > 24;                   // edge averages: up to 64 primal DOFs per subdomain
+  if (tc_format(c) == 0) wide ? launch_frct_lowp<0, 64>(c, m, st) : launch_frct_lowp<0, 24>(c, m, st);
+  else wide ? launch_frct_lowp<1, 64>(c, m, st) : launch_frct_lowp<1, 24>(c, m, st);
   note_launches(1);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
@@ -982,10 +989,10 @@ cudaError_t tc_put_v(const Ctx& c, const double* V, int m, cudaStream_t st) {
 cudaError_t tc_product(const Ctx& c, int m, float* Yb, cudaStream_t st) {
   if (m <= 0) return cudaSuccess;
   if (m > c.xb_cap) return cudaErrorInvalidValue;
+  if (c.tiles_ncb != (m + TC_NMAX - 1) / TC_NMAX) return cudaErrorInvalidValue;   // tile list not prepared
   prof_begin(st, c.fl_tc * m, 1);
   cudaError_t e;
   const bool split = tc_split(c);
-  if (c.tiles_ncb != (m + TC_NMAX - 1) / TC_NMAX) return cudaErrorInvalidValue;   // tile list not prepared
   // measured choice (3D, 512 directions): BF16 operands run faster in the
   // persistent kernel (0.56 vs 0.71 ms one pass, 1.20 vs 1.64 ms split), TF32
   // operands -- twice the bytes per MMA -- in the one-tile-per-CTA kernel with

@@ -64,6 +64,17 @@ def test_edges_with_mult_scaling_and_precision_form_2d():
     assert st.converged and rel(u, ud) <= 1e-7
 
 
+@pytest.mark.parametrize("precision", ["tf32x3", "bf16x3"])
+def test_edges_precision_form_3d(precision):
+    """3D with edges: up to 60 primal DOFs per subdomain in the tensor-core
+    operand's K-extension (two 32-wide TF32 chunks, one 64-wide BF16 chunk)."""
+    p = workloads.config4(tiles=3, elems=4)
+    prec = {"tf32x3": fg.FETI_TF32X3, "bf16x3": fg.FETI_BF16X3}[precision]
+    u, st, _ = _gpu_solve(p, "rrs", precision=prec, tol=1e-10)
+    assert st.converged
+    assert rel(u, direct_solve(p)) <= 1e-6
+
+
 def test_edges_need_the_dirichlet_block():
     o = fg.feti_options_default()
     o.primal = fg.FETI_PRIMAL_EDGES
