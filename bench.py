@@ -235,6 +235,24 @@ def oracle_sample(a, tiles=8):
                                      f"{info.iterations} iterations, {dt:.1f} s")
 
 
+def oracle_sample_single_thread(a, tiles):
+    """The same oracle sample in a child process with every BLAS / OpenMP pool
+    limited to one thread (the single-core figure beside the all-core one).
+    Returns (F-applies/s, seconds) or None if the child fails."""
+    env = dict(os.environ)
+    for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS", "BLIS_NUM_THREADS"):
+        env[k] = "1"
+    code = ("import sys, json; sys.path.insert(0, %r); import bench, argparse; "
+            "a = argparse.Namespace(elems=%d, tol=%r); v, dt, _ = bench.oracle_sample(a, %d); "
+            "print(json.dumps([v, dt]))" % (ROOT, a.elems, a.tol, tiles))
+    try:
+        r = subprocess.run([sys.executable, "-c", code], env=env, capture_output=True, text=True, timeout=600)
+        v, dt = json.loads(r.stdout.strip().splitlines()[-1])
+        return v, dt
+    except (subprocess.SubprocessError, ValueError, IndexError, OSError):
+        return None
+
+
 def cpu_threads():
     try:
         return len(os.sched_getaffinity(0))
@@ -783,6 +801,10 @@ def main():
             v, dt, desc = oracle_sample(a, tiles=6)
             out["cpu_baseline"] = {"value": v, "unit": "F-applies/s", "cores": cpu_threads(), "kind": "oracle",
                                    "sample": desc}
+            one = oracle_sample_single_thread(a, tiles=6)
+            if one:
+                out["cpu_baseline"]["single_thread"] = {"value": one[0], "unit": "F-applies/s", "cores": 1,
+                                                        "seconds": one[1]}
         print(json.dumps(out))
     if world > 1:
         import torch

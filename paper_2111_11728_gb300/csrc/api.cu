@@ -474,10 +474,6 @@ static feti_status setup_impl(Ctx& c, const feti_problem* probs, int n) {
     CU(cudaMemcpy(c.d_fglob + hp.prob_dof_off[q], probs[q].f,
                   (hp.prob_dof_off[q + 1] - hp.prob_dof_off[q]) * sizeof(double),
                   probs[q].on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice));
-  {
-    const bool dummy = true;
-    (void)dummy;
-  }
   c.h_k0.assign((size_t)(hp.dim == 2 ? 64 : 576), 0.0);
   element_stiffness_host(hp.dim, hp.nu, c.h_k0.data());
   TRY(upload(c, c.d_k0, c.h_k0));
