@@ -723,7 +723,7 @@ static feti_status setup_impl(Ctx& c, const feti_problem* probs, int n) {
     TRY(dalloc(c, c.d_sqrtDS, nbt));
     TRY(dalloc(c, c.d_rout, nl));
     TRY(dalloc(c, c.d_zout, nl));
-    TRY(dalloc(c, c.d_dl, nl));
+    TRY(dalloc(c, c.d_dl, nl));           // the best refined multipliers so far
   }
   TRY(dalloc(c, c.d_d, nl));
   TRY(dalloc(c, c.d_lam0, nl));
@@ -1451,7 +1451,7 @@ static feti_status solve_impl(Ctx& c, double* lambda_inout, feti_stats* stats) {
     // FP64 iterative refinement on the dual residual: r = P^T (d - F lambda)
     // with the FP64 operator; each correction solves F dl = r with the
     // low-precision local products to inner_tol.
-    double eps0 = -1.0, eps = 0.0;
+    double eps0 = -1.0, eps = 0.0, best = 0.0;
     int outer = 0;
     for (;;) {
       TRY(apply_dual(c, c.d_lam, nl, 1, c.d_rout, nl));
@@ -1464,7 +1464,23 @@ static feti_status solve_impl(Ctx& c, double* lambda_inout, feti_stats* stats) {
       eps = std::sqrt(std::max(rz, 0.0));
       if (eps0 < 0.0) eps0 = eps_ref > 0.0 ? eps_ref : eps;
       S.f_applies += 1;
+      // a correction that blew the FP64 residual up (a reduced-precision
+      // operator too inaccurate for the problem) is undone: the best
+      // multipliers so far are kept and the refinement stops unconverged
+      const bool blown = outer > 0 && (!std::isfinite(rz) || eps > 100.0 * best);
+      if (blown) {
+        CU(cudaMemcpyAsync(c.d_lam, c.d_dl, nl * sizeof(double), cudaMemcpyDeviceToDevice, st));
+        eps = best;
+        c.err = std::isfinite(rz) ? "the refinement diverged; the best multipliers are returned"
+                                  : "NaN or Inf in the refined residual; the best multipliers are returned";
+        if (!std::isfinite(rz)) result = FETI_EBREAKDOWN;
+        break;
+      }
       if (!std::isfinite(rz)) { result = FETI_EBREAKDOWN; c.err = "NaN or Inf in the refined residual"; break; }
+      if (outer == 0 || eps < best) {
+        best = eps;
+        CU(cudaMemcpyAsync(c.d_dl, c.d_lam, nl * sizeof(double), cudaMemcpyDeviceToDevice, st));
+      }
       if (eps <= c.opt.tol * eps0 || outer >= c.opt.max_refine || S.iterations >= c.opt.max_iter) break;
       CU(cudaMemcpyAsync(c.d_r, c.d_rout, nl * sizeof(double), cudaMemcpyDeviceToDevice, st));
       feti_stats inner{};
@@ -1504,7 +1520,7 @@ static feti_status solve_impl(Ctx& c, double* lambda_inout, feti_stats* stats) {
   TRY(check_status(c, "solve"));
   if (result == FETI_OK && !S.converged) {
     result = FETI_ENOTCONV;
-    c.err = "max_iter reached";
+    if (c.err.empty()) c.err = "max_iter reached";
   }
   c.last = S;
   if (stats) *stats = S;
