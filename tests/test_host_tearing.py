@@ -1,0 +1,148 @@
+"""CPU pin of the library's host-side tearing (csrc/setup.cpp, compiled here as
+plain C++ with no GPU): for TFETI and FETI-DP (corners, and corners plus edge
+averages) in 2D and 3D, the multiplier rows it emits -- as (subdomain, local
+DOF, sign) pairs -- are exactly the oracle's pair-wise rows of Eqs. (4) / (10),
+its primal count is the oracle's, and its b space is the set of local DOFs the
+oracle's B touches."""
+import json
+import os
+import shutil
+import subprocess
+
+import numpy as np
+import pytest
+
+import workloads
+from oracle.fetidp import FETIDP
+from oracle.tfeti import TFETI
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+CSRC = os.path.join(os.path.dirname(HERE), "paper_2111_11728_gb300", "csrc")
+CUDA_INC = "/usr/local/cuda/include"
+
+HARNESS = r'''
+#include <cstdio>
+#include <vector>
+#include "feti_internal.h"
+using namespace feti;
+int main(int argc, char** argv) {
+  FILE* fi = fopen(argv[1], "rb");
+  int hdr[10];
+  fread(hdr, sizeof(int), 10, fi);            // dim, tiles[3], elems[3], method, edges, n_el
+  double par[4];
+  fread(par, sizeof(double), 4, fi);
+  const int dim = hdr[0], n_el = hdr[9];
+  long n_nodes = 1;
+  for (int a = 0; a < dim; ++a) n_nodes *= (long)hdr[1 + a] * hdr[4 + a] + 1;
+  std::vector<double> rho(n_el), f(n_nodes * dim);
+  std::vector<unsigned char> dir(n_nodes * dim);
+  fread(rho.data(), sizeof(double), n_el, fi);
+  fread(dir.data(), 1, dir.size(), fi);
+  fread(f.data(), sizeof(double), f.size(), fi);
+  fclose(fi);
+  feti_problem p{};
+  p.dim = dim;
+  for (int a = 0; a < 3; ++a) { p.tiles[a] = hdr[1 + a]; p.elems[a] = hdr[4 + a]; }
+  p.E0 = par[0]; p.Emin = par[1]; p.nu = par[2]; p.p = par[3];
+  p.rho = rho.data(); p.dirichlet = dir.data(); p.f = f.data(); p.on_device = 0;
+  HostProblem hp;
+  std::string msg = build_host_problem(p, hdr[7], 1, rho.data(), hp, hdr[8] != 0);
+  if (!msg.empty()) { printf("{\"error\": \"%s\"}\n", msg.c_str()); return 1; }
+  FILE* fo = fopen(argv[2], "w");
+  fprintf(fo, "{\"n_lam\": %lld, \"n_primal\": %d, \"rows\": [", (long long)hp.n_lam, hp.n_primal);
+  auto loc = [&](int b, int& s, int& ld) {
+    s = hp.b_sub[b];
+    const StructType& T = hp.types[hp.sub_type[s]];
+    ld = T.blist[b - hp.b_off[s]];
+  };
+  for (long long l = 0; l < hp.n_lam; ++l) {
+    int s0, d0;
+    loc(hp.lam_b0[l], s0, d0);
+    fprintf(fo, "%s[[%d, %d, %d]", l ? ", " : "", s0, d0, (int)hp.lam_s0[l]);
+    if (hp.lam_b1[l] >= 0) {
+      int s1, d1;
+      loc(hp.lam_b1[l], s1, d1);
+      fprintf(fo, ", [%d, %d, %d]", s1, d1, (int)hp.lam_s1[l]);
+    }
+    fprintf(fo, "]");
+  }
+  fprintf(fo, "], \"bsets\": [");
+  for (int s = 0; s < hp.n_sub; ++s) {
+    const StructType& T = hp.types[hp.sub_type[s]];
+    fprintf(fo, "%s[", s ? ", " : "");
+    for (int k = 0; k < T.n_b; ++k) fprintf(fo, "%s%d", k ? ", " : "", T.blist[k]);
+    fprintf(fo, "]");
+  }
+  fprintf(fo, "]}\n");
+  fclose(fo);
+  return 0;
+}
+'''
+
+
+@pytest.fixture(scope="module")
+def harness(tmp_path_factory):
+    gxx = shutil.which("g++")
+    if gxx is None or not os.path.isdir(CUDA_INC):
+        pytest.skip("g++ or the CUDA headers not available")
+    d = tmp_path_factory.mktemp("tearing")
+    src = d / "main.cpp"
+    src.write_text(HARNESS)
+    exe = d / "tear"
+    subprocess.run([gxx, "-O1", "-std=c++17", "-I", CSRC, "-I", CUDA_INC, str(src),
+                    os.path.join(CSRC, "setup.cpp"), "-o", str(exe)], check=True, capture_output=True)
+    return exe, d
+
+
+def _run(harness, p, method, edges):
+    exe, d = harness
+    inp, out = d / "in.bin", d / "out.json"
+    tiles = list(p.tiles) + [1] * (3 - p.dim)
+    elems = list(p.elems) + [1] * (3 - p.dim)
+    hdr = np.array([p.dim, *tiles, *elems, 1 if method == "fetidp" else 0, int(edges), p.n_elements], np.int32)
+    with open(inp, "wb") as f:
+        f.write(hdr.tobytes())
+        f.write(np.array([p.E0, p.Emin, p.nu, p.p], np.float64).tobytes())
+        f.write(np.ascontiguousarray(p.rho, np.float64).tobytes())
+        f.write(np.ascontiguousarray(p.dirichlet, np.uint8).tobytes())
+        f.write(np.ascontiguousarray(p.f, np.float64).tobytes())
+    subprocess.run([str(exe), str(inp), str(out)], check=True, capture_output=True)
+    return json.loads(out.read_text())
+
+
+def _canon(rows):
+    out = []
+    for r in rows:
+        ents = sorted((int(s), int(k), int(np.sign(g))) for s, k, g in r)
+        if ents[0][2] < 0:                       # fix the overall sign of a row
+            ents = sorted((s, k, -g) for s, k, g in ents)
+        out.append(tuple(ents))
+    return sorted(out)
+
+
+CASES = [
+    ("tfeti", False, lambda: workloads.config1()),
+    ("fetidp", False, lambda: workloads.config2(tiles=3, elems=4)),
+    ("fetidp", True, lambda: workloads.layered_grid(elems=4, layers=4)),
+    ("fetidp", False, lambda: workloads.config4(tiles=2, elems=2)),
+    ("fetidp", True, lambda: workloads.config4(tiles=2, elems=3)),
+    ("tfeti", False, lambda: workloads.config4(tiles=2, elems=2)),
+]
+
+
+@pytest.mark.parametrize("method,edges,make", CASES)
+def test_library_tearing_matches_oracle(harness, method, edges, make):
+    p = make()
+    got = _run(harness, p, method, edges)
+    if method == "tfeti":
+        op = TFETI(p, "k")
+        rows = [[(s, k, g) for (s, k, g) in ent] for ent in op.cons.entries]
+        bsets = [sorted({k for ent in op.cons.entries for (s2, k, _) in ent if s2 == s}) for s in range(op.n_sub)]
+    else:
+        op = FETIDP(p, "k", primal="edges" if edges else "corners")
+        rows = [[(s, int(op.r_loc[s][k]), g) for (s, k, g) in ent] for ent in op.cons.entries]
+        bsets = [sorted(int(op.r_loc[s][k]) for k in op.bset[s]) for s in range(op.n_sub)]
+        assert got["n_primal"] == op.n_c
+    assert got["n_lam"] == op.n_lam
+    assert _canon(got["rows"]) == _canon(rows)
+    assert [sorted(b) for b in got["bsets"]] == bsets
