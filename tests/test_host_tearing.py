@@ -27,27 +27,38 @@ HARNESS = r'''
 using namespace feti;
 int main(int argc, char** argv) {
   FILE* fi = fopen(argv[1], "rb");
-  int hdr[10];
-  fread(hdr, sizeof(int), 10, fi);            // dim, tiles[3], elems[3], method, edges, n_el
-  double par[4];
-  fread(par, sizeof(double), 4, fi);
-  const int dim = hdr[0], n_el = hdr[9];
-  long n_nodes = 1;
-  for (int a = 0; a < dim; ++a) n_nodes *= (long)hdr[1 + a] * hdr[4 + a] + 1;
-  std::vector<double> rho(n_el), f(n_nodes * dim);
-  std::vector<unsigned char> dir(n_nodes * dim);
-  fread(rho.data(), sizeof(double), n_el, fi);
-  fread(dir.data(), 1, dir.size(), fi);
-  fread(f.data(), sizeof(double), f.size(), fi);
+  int n_prob = 0;
+  fread(&n_prob, sizeof(int), 1, fi);
+  std::vector<HostProblem> parts(n_prob);
+  for (int q = 0; q < n_prob; ++q) {
+    int hdr[10];
+    fread(hdr, sizeof(int), 10, fi);          // dim, tiles[3], elems[3], method, edges, n_el
+    double par[4];
+    fread(par, sizeof(double), 4, fi);
+    const int dim = hdr[0], n_el = hdr[9];
+    long n_nodes = 1;
+    for (int a = 0; a < dim; ++a) n_nodes *= (long)hdr[1 + a] * hdr[4 + a] + 1;
+    std::vector<double> rho(n_el), f(n_nodes * dim);
+    std::vector<unsigned char> dir(n_nodes * dim);
+    fread(rho.data(), sizeof(double), n_el, fi);
+    fread(dir.data(), 1, dir.size(), fi);
+    fread(f.data(), sizeof(double), f.size(), fi);
+    feti_problem p{};
+    p.dim = dim;
+    for (int a = 0; a < 3; ++a) { p.tiles[a] = hdr[1 + a]; p.elems[a] = hdr[4 + a]; }
+    p.E0 = par[0]; p.Emin = par[1]; p.nu = par[2]; p.p = par[3];
+    p.rho = rho.data(); p.dirichlet = dir.data(); p.f = f.data(); p.on_device = 0;
+    std::string msg = build_host_problem(p, hdr[7], 1, rho.data(), parts[q], hdr[8] != 0);
+    if (!msg.empty()) { printf("{\"error\": \"%s\"}\n", msg.c_str()); return 1; }
+  }
   fclose(fi);
-  feti_problem p{};
-  p.dim = dim;
-  for (int a = 0; a < 3; ++a) { p.tiles[a] = hdr[1 + a]; p.elems[a] = hdr[4 + a]; }
-  p.E0 = par[0]; p.Emin = par[1]; p.nu = par[2]; p.p = par[3];
-  p.rho = rho.data(); p.dirichlet = dir.data(); p.f = f.data(); p.on_device = 0;
   HostProblem hp;
-  std::string msg = build_host_problem(p, hdr[7], 1, rho.data(), hp, hdr[8] != 0);
-  if (!msg.empty()) { printf("{\"error\": \"%s\"}\n", msg.c_str()); return 1; }
+  if (n_prob == 1) {
+    hp = parts[0];
+  } else {
+    std::string msg = merge_host_problems(parts, hp);
+    if (!msg.empty()) { printf("{\"error\": \"%s\"}\n", msg.c_str()); return 1; }
+  }
   FILE* fo = fopen(argv[2], "w");
   fprintf(fo, "{\"n_lam\": %lld, \"n_primal\": %d, \"rows\": [", (long long)hp.n_lam, hp.n_primal);
   auto loc = [&](int b, int& s, int& ld) {
@@ -94,20 +105,36 @@ def harness(tmp_path_factory):
     return exe, d
 
 
-def _run(harness, p, method, edges):
+def _run(harness, probs, method, edges):
     exe, d = harness
     inp, out = d / "in.bin", d / "out.json"
-    tiles = list(p.tiles) + [1] * (3 - p.dim)
-    elems = list(p.elems) + [1] * (3 - p.dim)
-    hdr = np.array([p.dim, *tiles, *elems, 1 if method == "fetidp" else 0, int(edges), p.n_elements], np.int32)
     with open(inp, "wb") as f:
-        f.write(hdr.tobytes())
-        f.write(np.array([p.E0, p.Emin, p.nu, p.p], np.float64).tobytes())
-        f.write(np.ascontiguousarray(p.rho, np.float64).tobytes())
-        f.write(np.ascontiguousarray(p.dirichlet, np.uint8).tobytes())
-        f.write(np.ascontiguousarray(p.f, np.float64).tobytes())
+        f.write(np.array([len(probs)], np.int32).tobytes())
+        for p in probs:
+            tiles = list(p.tiles) + [1] * (3 - p.dim)
+            elems = list(p.elems) + [1] * (3 - p.dim)
+            hdr = np.array([p.dim, *tiles, *elems, 1 if method == "fetidp" else 0, int(edges), p.n_elements],
+                           np.int32)
+            f.write(hdr.tobytes())
+            f.write(np.array([p.E0, p.Emin, p.nu, p.p], np.float64).tobytes())
+            f.write(np.ascontiguousarray(p.rho, np.float64).tobytes())
+            f.write(np.ascontiguousarray(p.dirichlet, np.uint8).tobytes())
+            f.write(np.ascontiguousarray(p.f, np.float64).tobytes())
     subprocess.run([str(exe), str(inp), str(out)], check=True, capture_output=True)
     return json.loads(out.read_text())
+
+
+def _oracle_rows(p, method, edges, s0=0):
+    """Pair-wise rows as (subdomain + s0, local DOF, sign), the interface sets and the primal count."""
+    if method == "tfeti":
+        op = TFETI(p, "k")
+        rows = [[(s + s0, k, g) for (s, k, g) in ent] for ent in op.cons.entries]
+        bsets = [sorted({k for ent in op.cons.entries for (s2, k, _) in ent if s2 == s}) for s in range(op.n_sub)]
+        return rows, bsets, None, op.n_lam
+    op = FETIDP(p, "k", primal="edges" if edges else "corners")
+    rows = [[(s + s0, int(op.r_loc[s][k]), g) for (s, k, g) in ent] for ent in op.cons.entries]
+    bsets = [sorted(int(op.r_loc[s][k]) for k in op.bset[s]) for s in range(op.n_sub)]
+    return rows, bsets, op.n_c, op.n_lam
 
 
 def _canon(rows):
@@ -133,16 +160,29 @@ CASES = [
 @pytest.mark.parametrize("method,edges,make", CASES)
 def test_library_tearing_matches_oracle(harness, method, edges, make):
     p = make()
-    got = _run(harness, p, method, edges)
-    if method == "tfeti":
-        op = TFETI(p, "k")
-        rows = [[(s, k, g) for (s, k, g) in ent] for ent in op.cons.entries]
-        bsets = [sorted({k for ent in op.cons.entries for (s2, k, _) in ent if s2 == s}) for s in range(op.n_sub)]
-    else:
-        op = FETIDP(p, "k", primal="edges" if edges else "corners")
-        rows = [[(s, int(op.r_loc[s][k]), g) for (s, k, g) in ent] for ent in op.cons.entries]
-        bsets = [sorted(int(op.r_loc[s][k]) for k in op.bset[s]) for s in range(op.n_sub)]
-        assert got["n_primal"] == op.n_c
-    assert got["n_lam"] == op.n_lam
+    got = _run(harness, [p], method, edges)
+    rows, bsets, n_c, n_lam = _oracle_rows(p, method, edges)
+    if n_c is not None:
+        assert got["n_primal"] == n_c
+    assert got["n_lam"] == n_lam
+    assert _canon(got["rows"]) == _canon(rows)
+    assert [sorted(b) for b in got["bsets"]] == bsets
+
+
+@pytest.mark.parametrize("edges", [False, True])
+def test_batch_merge_keeps_each_problems_tearing(harness, edges):
+    """A batch of uneven problems merged into one description: the rows are
+    each problem's own rows, its subdomains shifted by the preceding problems'."""
+    probs = workloads.config3(n_problems=3, tile_range=(2, 3), elem_range=(3, 5), seed=7)
+    got = _run(harness, probs, "fetidp", edges)
+    rows, bsets, n_c, n_lam, s0 = [], [], 0, 0, 0
+    for p in probs:
+        r, b, c, n = _oracle_rows(p, "fetidp", edges, s0)
+        rows += r
+        bsets += b
+        n_c += c
+        n_lam += n
+        s0 += p.n_subdomains
+    assert got["n_primal"] == n_c and got["n_lam"] == n_lam
     assert _canon(got["rows"]) == _canon(rows)
     assert [sorted(b) for b in got["bsets"]] == bsets
