@@ -1169,6 +1169,30 @@ static feti_status batch_rrs(Ctx& c, double tol, int max_iter, feti_stats& S) {
   }
   double* W = c.d_Wb;
   double* Q = c.d_Qb;
+  // local products per column chunk [j0, j0 + BATCH_CHUNK): subdomain s computes
+  // only the columns its problem uses (min(N_s(p) - j0, chunk), possibly none)
+  const int n_chunks = (M + BATCH_CHUNK - 1) / BATCH_CHUNK;
+  {
+    const int64_t nbt = hp.n_b_total;
+    std::vector<GemmDesc> fc((size_t)n_chunks * hp.n_sub);
+    for (int t = 0; t < n_chunks; ++t)
+      for (int s2 = 0; s2 < hp.n_sub; ++s2) {
+        const DevSub& Sd = c.h_subs[s2];
+        const DevType& Td = c.h_types[Sd.type];
+        GemmDesc g{};
+        g.A = c.d_modmem + c.h_mods[Sd.module].F; g.B = c.d_Xb + Sd.b_off; g.C = c.d_Yb + Sd.b_off;
+        g.M = Td.n_b; g.K = Td.n_b;
+        g.N = std::max(0, std::min(BATCH_CHUNK, mp[hp.sub_prob[s2]] - t * BATCH_CHUNK));
+        g.ars = Td.n_b; g.acs = 1; g.brs = 1; g.bcs = nbt; g.crs = 1; g.ccs = nbt;
+        fc[(size_t)t * hp.n_sub + s2] = g;
+      }
+    TRY(grow(c, c.d_bk_fchunks, c.bk_fchunks_cap, (int64_t)fc.size()));
+    CU(cudaMemcpy(c.d_bk_fchunks, fc.data(), fc.size() * sizeof(GemmDesc), cudaMemcpyHostToDevice));
+  }
+  struct ActiveF {
+    Ctx& c;
+    ~ActiveF() { c.gemm_F_active = nullptr; }
+  } active_guard{c};
   auto read_rz = [&](std::vector<double>& rz) -> feti_status {
     CU(seg_dot2(c.d_prob_lam_off, np, c.d_r, c.d_z, nullptr, nullptr, c.d_bk_part, c.d_bk_rz, nullptr, st));
     CU(cudaMemcpyAsync(rz.data(), c.d_bk_rz, np * sizeof(double), cudaMemcpyDeviceToHost, st));
@@ -1209,8 +1233,11 @@ static feti_status batch_rrs(Ctx& c, double tol, int max_iter, feti_stats& S) {
       double fl = 0.0;
       for (int p : act) fl += (double)mp[p] * mp[p] * (c.fl_F + c.fl_FrcT + c.fl_Frc + c.fl_coarse) / hp.n_sub;
       PhaseScope ph(st, FETI_PHASE_APPLY, fl);
-      for (int j0 = 0; j0 < Mact; j0 += BATCH_CHUNK)
+      for (int j0 = 0; j0 < Mact; j0 += BATCH_CHUNK) {
+        c.gemm_F_active = c.d_bk_fchunks + (int64_t)(j0 / BATCH_CHUNK) * hp.n_sub;
         TRY(apply_dual(c, W + (int64_t)j0 * nl, nl, std::min(BATCH_CHUNK, Mact - j0), Q + (int64_t)j0 * nl, nl));
+      }
+      c.gemm_F_active = nullptr;
     }
     {
       double fl = 0.0;

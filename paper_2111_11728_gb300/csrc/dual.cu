@@ -232,7 +232,9 @@ cudaError_t scatter_b_to_lam32(const Ctx& c, const float* Yb, int m, double* Y, 
 }
 
 cudaError_t apply_local_F(Ctx& c, const double* /*Xb*/, double* /*Yb*/, int m, double beta, cudaStream_t st) {
-  // descriptors point at c.d_Xb / c.d_Yb (fixed buffers)
+  // descriptors point at c.d_Xb / c.d_Yb (fixed buffers); a batch's column
+  // chunk may cap each subdomain's N at its own problem's directions
+  if (c.gemm_F_active) return dgemm_batched(c.gemm_F_active, c.hp.n_sub, c.max_nb, m, 0, 1.0, beta, st, c.fl_F * m);
   return dgemm_batched(c.d_gemm_F, c.hp.n_sub, c.max_nb, c.max_nb, m, 1.0, beta, st, c.fl_F * m);
 }
 

@@ -322,6 +322,9 @@ struct Ctx {
   GemmDesc* d_bk_desc = nullptr;
   SegRed* d_bk_red = nullptr;
   int64_t bk_split_cap = 0, bk_desc_cap = 0, bk_red_cap = 0;
+  GemmDesc* d_bk_fchunks = nullptr;        // local F_s products per column chunk, N capped per subdomain
+  int64_t bk_fchunks_cap = 0;
+  const GemmDesc* gemm_F_active = nullptr; // when set, the local products use these descriptors
   std::vector<double*> bk_hW, bk_hQ;       // packed history blocks (one per iteration)
   std::vector<int64_t> bk_hcap;
   feti_stats last{};
