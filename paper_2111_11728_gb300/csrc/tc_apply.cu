@@ -153,21 +153,22 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&v)[32]) {
 // Operands of the tensor-core product, laid out for TMA:
 //
 //   A: the scaled blocks Fhat_s of every module, one row of the "arena" per
-//      block row, a common pitch P and zero beyond n_b.  FETI-DP with corners
-//      appends, after n_b rounded up to 32, the row's scaled corner coupling
-//      Frc_hat_s = D_s^{-1/2} F_rc,s (n_c <= 24 columns, one more 32-wide K
-//      chunk).  Tensor map: dims {P, rows}, box {32, 128}, 128-byte swizzle.
+//      block row, a common pitch P and zero beyond n_b.  FETI-DP appends,
+//      after n_b rounded up to the K chunk KC (32 TF32 or 64 BF16 values), the
+//      row's scaled primal coupling Frc_hat_s = D_s^{-1/2} F_rc,s (n_c <= 64
+//      columns -- 8 to 24 corners, up to 60 with edge averages -- rounded up
+//      to KC).  Tensor map: dims {P, rows}, box {KC, 128}, 128-byte swizzle.
 //   B: the gathered, scaled directions D_s^{1/2} B^sT X, one column per
 //      direction over the padded interface space (each subdomain's range
-//      rounded up to 32 entries, zero in the padding), followed for FETI-DP
+//      rounded up to KC entries, zero in the padding), followed for FETI-DP
 //      by the subdomain's coarse correction V_s (the K-extension matching
-//      Frc_hat).  Tensor map: dims {padded total, m}, box {32, 256}.
+//      Frc_hat).  Tensor map: dims {padded total, m}, box {KC, 256}.
 //
 // With the K-extension one product gives the whole local FETI-DP operator
 // D^{1/2} [Fhat | Frc_hat] [D^{1/2} X_b ; V_s] = F_s X_b + F_rc,s V_s.
 //
-// Both are stored as TF32 high parts (and, for the split product, TF32 low
-// parts).  One CTA computes a 128-row x 256-column output tile of one
+// Both are stored as TF32 or BF16 high parts (and, for the split product,
+// low parts in the same format).  One CTA computes a 128-row x 256-column output tile of one
 // subdomain: thread 0 streams K chunks of 32 through a STAGES-deep ring of
 // shared-memory buffers (full / empty mbarriers), thread 32 issues the MMAs
 // (4 K=8 steps x PASSES per chunk) and frees a buffer by committing to its
