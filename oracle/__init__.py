@@ -19,9 +19,13 @@ mesh         Regular tile meshes: global <-> subdomain numbering.
 assemble     Global system (Eq. 2) and local systems (Eq. 3), direct solve.
 scaling      k-scaling (Eq. 15) and multiplicity scaling (Section 3.1).
 tfeti        Total FETI (Section 2.1, Eqs. 4-7) and its projector.
-fetidp       FETI-DP (Section 2.2, Eqs. 8-12) with corner primal DOFs.
+fetidp       FETI-DP (Section 2.2, Eqs. 8-12) with corner primal DOFs, optionally
+             with edge averages (a richer primal set, Section 5).
 krylov       PCG, full orthogonalization, and Algorithm 1 (RR-S-FETI).
 sensitivity  Compliance and the SIMP sensitivity.
+sharded      Algorithm 1 for FETI-DP on CPU ranks of torch.distributed with the
+             multi-GPU layout (subdomain blocks per rank, row-partitioned
+             directions, halo exchanges and all-reduces); imported on demand.
 
 Parity status of each function is stated in its docstring; functions without
 an independent pin say "parity unpinned".
