@@ -26,7 +26,8 @@ Beside the headline (rank 0, one GPU), the line carries:
   ``academic``   the 12 variants on stand-ins for the paper's academic problems;
   ``phases``     time share and roofline fraction of every phase of the timed step;
   ``forms_3d``   (``--forms-3d``, minutes) the precision forms' time to solve in 3D;
-  ``primal_3d``  (``--primal-3d``, minutes) corners against corners + edge averages in 3D.
+  ``primal_3d``  (``--primal-3d``, minutes) corners against corners + edge averages in 3D;
+  ``pcg_3d``     (``--pcg-3d``) phase rooflines of the FP64 PCG solve in 3D (HBM-bound phases).
 
 ``--impl reference`` times the FP64 CPU oracle on a bounded sample of the
 same workload instead (rank 0 only).
@@ -141,6 +142,7 @@ def parse():
     ap.add_argument("--batch-krylov", default="both", choices=["pcg", "rrs", "both"])
     ap.add_argument("--no-academic", action="store_true")
     ap.add_argument("--forms-3d-primal", default="corners", choices=["corners", "edges"])
+    ap.add_argument("--pcg-3d", action="store_true", help="phase rooflines of the FP64 PCG solve in 3D")
     ap.add_argument("--primal-3d", action="store_true",
                     help="also compare corners with corners + edge averages on the 3D workload (minutes)")
     return ap.parse_args()
@@ -412,6 +414,45 @@ def compare_primal_3d(a, fg, torch, dev, stream, flush):
         g["speedup_time_to_solve"] = c["time_to_solve_ms"] / g["time_to_solve_ms"]
         ref = sols[kname, "corners"]
         g["rel_diff_vs_corners"] = float(np.linalg.norm(sols[kname, "edges"] - ref) / np.linalg.norm(ref))
+    return out
+
+
+def pcg_phases_3d(a, fg, torch, dev, stream, flush):
+    """FP64 FETI-DP + k-scaling + PCG on the 3D workload with the phase profile:
+    a PCG iteration streams every local block once in the one-direction apply
+    and once in the preconditioner, so both phases are HBM-bound here; their
+    algorithmic bytes over the measured time against the measured copy
+    bandwidth."""
+    p = workloads.config4(tiles=a.tiles_3d, elems=8)
+    s = fg.Solver(fg.FETI_FETIDP, fg.FETI_SCALING_K, fg.FETI_PCG, tol=a.tol, max_iter=2000,
+                  stream=stream.cuda_stream)
+    s.setup(p, rho=torch.from_numpy(p.rho).to(dev), f=torch.from_numpy(p.f).to(dev), on_device=True)
+    u = torch.empty(p.n_dofs, dtype=torch.float64, device=dev)
+    for k in range(2):
+        flush.zero_()
+        torch.cuda.synchronize()
+        if k == 1:
+            fg.feti_profile_begin(s.ctx)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        fg.feti_factorize(s.ctx)
+        _, st = fg.feti_solve_dual(s.ctx, allow_notconv=True)
+        fg.feti_recover_displacements(s.ctx, u, True)
+        e1.record(stream)
+        torch.cuda.synchronize()
+    fg.feti_profile_end(s.ctx)
+    prof = fg.feti_profile_phases(s.ctx)
+    total = e0.elapsed_time(e1)
+    out = {"workload": f"3D H8: {a.tiles_3d}^3 subdomains of 8^3 elements, FETI-DP + k + PCG, FP64",
+           "iterations": st.iterations, "converged": bool(st.converged), "time_to_solve_ms": total,
+           "phases": phase_rooflines(prof, 1, total / 1e3)}
+    _, ams, an = prof["apply"]
+    if an and ams > 0:                       # one direction: the apply is HBM-bound, rate it in bytes
+        hbm = tensor_peaks()["hbm_gbs"]
+        gbs = fg.feti_query(s.ctx, fg.FETI_Q_APPLY1_BYTES) * an / (ams / 1e3) / 1e9
+        out["phases"]["apply"].update({"bound": "hbm", "achieved": gbs, "peak": hbm, "unit": "GB/s",
+                                       "frac": gbs / hbm})
+    s.close()
     return out
 
 
@@ -725,6 +766,9 @@ def run_ours(a, rank, world):
     primal3d = None
     if a.primal_3d and world == 1:
         primal3d = compare_primal_3d(a, fg, torch, dev, stream, flush)
+    pcg3d = None
+    if a.pcg_3d and world == 1:
+        pcg3d = pcg_phases_3d(a, fg, torch, dev, stream, flush)
     academic = None
     if not a.no_academic and world == 1:
         academic = compare_academic(a, fg, torch, dev, stream)
@@ -761,7 +805,7 @@ def run_ours(a, rank, world):
                      "launches": gn},
         "e2e": e2e, "gpu_launches": int(launches), "clocks": clk, "wall_s": wall,
         "forms": forms, "apply_3d": apply3d, "forms_3d": forms3d, "batch_form": batch, "batch_form_rrs": batch_rrs,
-        "academic": academic, "primal_3d": primal3d, "phases": phases,
+        "academic": academic, "primal_3d": primal3d, "pcg_3d": pcg3d, "phases": phases,
     }
     s.close()
     return out

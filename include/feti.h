@@ -236,8 +236,11 @@ enum {
                               warps per CTA + 100 if vector loads; 0 = default */
   FETI_Q_TC_BYTES_F = 13,      /* reduced precision: bytes of the tensor-core product's stationary operand
                                   (every module's scaled blocks, all parts), read once per apply */
-  FETI_Q_TC_BYTES_PER_COL = 14 /* reduced precision: bytes the product moves per direction: the
-                                  gathered operand in (all parts) and the FP32 interface result out */
+  FETI_Q_TC_BYTES_PER_COL = 14, /* reduced precision: bytes the product moves per direction: the
+                                   gathered operand in (all parts) and the FP32 interface result out */
+  FETI_Q_APPLY1_BYTES = 15     /* FP64: algorithmic bytes of a one-direction dual-operator apply (PCG):
+                                  every distinct module's F_s and F_rc read once, the coarse inverse
+                                  (FETI-DP), the multiplier and interface vectors in and out */
 };
 feti_status feti_query(const feti_ctx* ctx, int key, int64_t* value);
 

@@ -180,6 +180,10 @@ feti_status ensure_split(Ctx& c, int64_t need) {
 // B (K x N) column-major (ld lda, ldb): the Gram products of Algorithm 1.
 feti_status gemm_tn(Ctx& c, const double* A, int64_t lda, const double* B, int64_t ldb, double* C, int64_t ldc,
                     int M, int N, int K, double alpha, double beta, int lower = 0) {
+  if (M == 1 && N == 1 && alpha == 1.0 && beta == 0.0) {   // one direction: an inner product
+    CU(dot(A, B, K, c.d_red, C, c.stream));
+    return FETI_OK;
+  }
   GemmDesc d{};
   d.A = A; d.B = B; d.C = C; d.M = M; d.N = N; d.K = K;
   d.ars = lda; d.acs = 1; d.brs = 1; d.bcs = ldb; d.crs = 1; d.ccs = ldc;
@@ -196,6 +200,10 @@ feti_status gemm_tn(Ctx& c, const double* A, int64_t lda, const double* B, int64
 // column-major ld ldu), A column-major n x m.
 feti_status gemm_perm_upper(Ctx& c, const double* A, int64_t lda, const int* perm, const double* U, int64_t ldu,
                             double* C, int64_t ldc, int M, int N, double alg_flops) {
+  if (N == 1) {                                              // one direction: a scaled column
+    CU(scale_col(M, A, lda, perm, U, C, c.stream));
+    return FETI_OK;
+  }
   GemmDesc d{};
   d.A = A; d.B = U; d.C = C; d.M = M; d.N = N; d.K = N;
   d.ars = 1; d.acs = lda; d.brs = 1; d.bcs = ldu; d.crs = 1; d.ccs = ldc;
@@ -208,6 +216,10 @@ feti_status gemm_perm_upper(Ctx& c, const double* A, int64_t lda, const int* per
 // C (col-major M x N) = alpha * A B + beta * C, A (M x K), B (K x N) column-major.
 feti_status gemm_nn(Ctx& c, const double* A, int64_t lda, const double* B, int64_t ldb, double* C, int64_t ldc,
                     int M, int N, int K, double alpha, double beta, double alg_flops = -1.0) {
+  if (N == 1 && K == 1) {                                    // one direction: a rank-one update
+    CU(axpy_scalar(M, alpha, A, B, beta, C, c.stream));
+    return FETI_OK;
+  }
   GemmDesc d{};
   d.A = A; d.B = B; d.C = C; d.M = M; d.N = N; d.K = K;
   d.ars = 1; d.acs = lda; d.brs = 1; d.bcs = ldb; d.crs = 1; d.ccs = ldc;
@@ -637,10 +649,14 @@ static feti_status setup_impl(Ctx& c, const feti_problem* probs, int n) {
   const int64_t kb_len = std::max<int64_t>(c.h_kbar_off[hp.n_prob], 1);
   c.fl_coarse = hp.method == FETI_FETIDP ? 2.0 * (double)c.h_kbar_off[hp.n_prob] : 0.0;
   c.bytes_S = 0.0;
+  c.bytes_apply1 = 0.0;
   for (int q = 0; q < (int)hp.module_type.size(); ++q) {
-    const double nb = hp.types[hp.module_type[q]].n_b;
+    const double nb = hp.types[hp.module_type[q]].n_b, nc = hp.types[hp.module_type[q]].n_c;
     c.bytes_S += 8.0 * nb * nb;
+    c.bytes_apply1 += 8.0 * (nb * nb + (hp.method == FETI_FETIDP ? nb * nc : 0.0));
   }
+  c.bytes_apply1 += 8.0 * ((hp.method == FETI_FETIDP ? (double)c.h_kbar_off[hp.n_prob] : 0.0) +
+                           2.0 * hp.n_lam + 2.0 * hp.n_b_total);
   TRY(dalloc(c, c.d_Kbar, kb_len));
   TRY(dalloc(c, c.d_Kbar_L, kb_len));
   TRY(dalloc(c, c.d_Kbar_inv, kb_len));
@@ -1682,6 +1698,7 @@ feti_status feti_query(const feti_ctx* ctx, int key, int64_t* value) {
     case FETI_Q_GEMV_CONFIG: *value = c.gemv_cfg; break;
     case FETI_Q_TC_BYTES_F: *value = c.tc_bytes_f; break;
     case FETI_Q_TC_BYTES_PER_COL: *value = c.tc_bytes_col; break;
+    case FETI_Q_APPLY1_BYTES: *value = (int64_t)c.bytes_apply1; break;
     default: return FETI_EINVAL;
   }
   return FETI_OK;

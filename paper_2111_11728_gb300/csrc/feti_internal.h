@@ -196,6 +196,7 @@ struct Ctx {
   double fl_F = 0, fl_FrcT = 0, fl_Frc = 0, fl_schur = 0, fl_frcmake = 0, fl_kbmake = 0;
   double fl_coarse = 0;          // flops of one coarse solve column (FETI-DP: sum_p 2 n_c(p)^2)
   double bytes_S = 0;            // the distinct preconditioner blocks S_bb, in bytes
+  double bytes_apply1 = 0;       // algorithmic bytes of a one-direction FP64 apply
   void* prof = nullptr;          // active GEMM profile (GemmProfile*)
   double* d_modmem = nullptr;    // module arrays
   int64_t modmem_len = 0;

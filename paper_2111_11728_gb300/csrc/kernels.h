@@ -169,6 +169,12 @@ cudaError_t step_update(const double* W, const double* Q, int64_t ld, int64_t n,
 cudaError_t dot(const double* x, const double* y, int64_t n, double* work, double* out, cudaStream_t st);
 // y = a*x + b*y
 cudaError_t axpby(int64_t n, double a, const double* x, double b, double* y, cudaStream_t st);
+// C[i] = A[i + perm[0] * lda] * U[0] for i < n (one-direction transform)
+cudaError_t scale_col(int64_t n, const double* A, int64_t lda, const int* perm, const double* U, double* C,
+                      cudaStream_t st);
+// C[i] = alpha * A[i] * b[0] + beta * C[i] for i < n (beta == 0 never reads C)
+cudaError_t axpy_scalar(int64_t n, double alpha, const double* A, const double* b, double beta, double* C,
+                        cudaStream_t st);
 // out[j] = W[:, j] . r for j < k
 cudaError_t gemv_t(const double* W, int64_t ld, int64_t n, int k, const double* r, double* out, cudaStream_t st);
 // y = A x (+ beta y), A row-major n x n with leading dimension ld

@@ -312,6 +312,24 @@ __global__ void k_sum(const double* __restrict__ part, int n, double* __restrict
   }
 }
 
+// One-direction forms of the block products (PCG and FO carry one direction):
+// C = A[:, perm[0]] * U[0] (the F-orthonormal transform), and
+// C = alpha * A[:, 0] * b[0] + beta * C (a rank-one update).  Padded 64 x 64
+// GEMM tiles would spend 4096 FP64 FMAs per useful one here.
+__global__ void k_scale_col(int64_t n, const double* __restrict__ A, int64_t lda, const int* __restrict__ perm,
+                            const double* __restrict__ U, double* __restrict__ C) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i < n) C[i] = A[i + (int64_t)perm[0] * lda] * U[0];
+}
+
+__global__ void k_axpy_scalar(int64_t n, double alpha, const double* __restrict__ A, const double* __restrict__ b,
+                              double beta, double* __restrict__ C) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const double v = alpha * A[i] * b[0];
+  C[i] = beta != 0.0 ? fma(beta, C[i], v) : v;
+}
+
 __global__ void k_axpby(int64_t n, double a, const double* __restrict__ x, double b, double* __restrict__ y) {
   const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (i < n) y[i] = fma(a, x[i], b * y[i]);
@@ -393,6 +411,20 @@ cudaError_t dot(const double* x, const double* y, int64_t n, double* work, doubl
   k_dot_partial<<<blocks, 256, 0, st>>>(x, y, n, work);
   note_launches(1);
   k_sum<<<1, 32, 0, st>>>(work, blocks, out);
+  note_launches(1);
+  return cudaGetLastError();
+}
+
+cudaError_t scale_col(int64_t n, const double* A, int64_t lda, const int* perm, const double* U, double* C,
+                      cudaStream_t st) {
+  k_scale_col<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(n, A, lda, perm, U, C);
+  note_launches(1);
+  return cudaGetLastError();
+}
+
+cudaError_t axpy_scalar(int64_t n, double alpha, const double* A, const double* b, double beta, double* C,
+                        cudaStream_t st) {
+  k_axpy_scalar<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(n, alpha, A, b, beta, C);
   note_launches(1);
   return cudaGetLastError();
 }
