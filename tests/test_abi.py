@@ -49,3 +49,25 @@ def test_create_without_gpu_fails_cleanly():
     with pytest.raises(fg.FetiError) as e:
         fg.feti_create(fg.feti_options_default())
     assert e.value.status == fg.FETI_ECUDA
+
+
+def test_option_combinations_rejected_before_any_device_call():
+    o = fg.feti_options_default()
+    assert o.primal == fg.FETI_PRIMAL_CORNERS and o.precond == fg.FETI_PRECOND_DIRICHLET
+    cases = []
+    a = fg.feti_options_default()
+    a.primal = 2                                        # no such primal set
+    cases.append((a, fg.FETI_EINVAL))
+    b = fg.feti_options_default()
+    b.primal, b.method = fg.FETI_PRIMAL_EDGES, fg.FETI_TFETI   # primal sets are a FETI-DP choice
+    cases.append((b, fg.FETI_EINVAL))
+    c = fg.feti_options_default()
+    c.primal, c.precond = fg.FETI_PRIMAL_EDGES, fg.FETI_PRECOND_LUMPED
+    cases.append((c, fg.FETI_ENOTSUP))
+    d = fg.feti_options_default()
+    d.precision = 5
+    cases.append((d, fg.FETI_EINVAL))
+    for opt, status in cases:
+        with pytest.raises(fg.FetiError) as e:
+            fg.feti_create(opt)
+        assert e.value.status == status
