@@ -7,6 +7,10 @@ definition of what every FETI variant must reproduce; ``direct_solve`` solves
 it with a sparse direct factorisation after eliminating the Dirichlet DOFs.
 ``local_stiffness`` builds K^s of Eq. (3) for one subdomain as a dense
 matrix, including all of its DOFs (Dirichlet ones too; TFETI keeps them).
+
+Pins: tests/test_oracle_dual.py (the direct solve's residual of Eq. 2; every
+FETI variant reaches it), tests/test_oracle_sensitivity.py (compliance equal
+to the strain energy).
 """
 import numpy as np
 import scipy.sparse as sp

@@ -10,7 +10,8 @@ Test infrastructure only (see the package docstring).
 
 k0 is integrated with the 2-point (per axis) Gauss rule, which is exact for
 the bilinear / trilinear element on an undistorted square / cube; the tests
-pin it against exact symbolic integration and the rigid-body null space.
+(tests/test_oracle_fem.py) pin it against exact symbolic integration, the
+patch test and the rigid-body null space, and Eq. (1) against its closed form.
 
 Element node order (local to the oracle):
   Q4: (0,0) (1,0) (1,1) (0,1)

@@ -39,6 +39,12 @@ Readings:
 * K_rr^{-1} is only ever needed on the DOFs that B_r touches (the "b" DOFs)
   and on K_rc; the oracle forms those restrictions once per distinct
   subdomain matrix (identical modules share them, Section 1).
+
+Pins: tests/test_oracle_dual.py (the blocks of Eq. 12 against the dense Eq. 11
+and global inverses, module deduplication exact, the direct solution),
+tests/test_oracle_precond.py (the three preconditioner blocks),
+tests/test_oracle_edges.py (the edge-average reading: direct solution,
+closed-form sizes, the primal value is the edge mean on every sharer).
 """
 import hashlib
 

@@ -31,6 +31,12 @@ Readings (the paper is silent on them):
   the largest ratio is taken next, exact ties going to the lowest original
   column; stop when the best ratio is <= rr_tol.  Columns with
   Delta_jj <= (2^-52)^2 * max Delta are treated as zero and never taken.
+
+Pins (tests/test_oracle_dual.py): the PCG variant equals a textbook projected
+PCG; F-orthonormality of every kept block and F-orthogonality to every stored
+block; the rank-revealing factorization against a brute-force subset search;
+all twelve variants reach the direct solution; the qualitative finding that
+plain TFETI stalls at high contrast while FETI-DP + k + Algorithm 1 converges.
 """
 import dataclasses
 from typing import List

@@ -7,6 +7,10 @@ Section 4.2: in modular problems every module (tile) is one subdomain, so
 the partition is fixed and regular.  Subdomain s is the tile with
 lexicographic index s (x fastest).  Inside a subdomain, nodes and elements
 are numbered lexicographically as well, and local DOF = dim * node + d.
+
+Pins (tests/test_oracle_mesh.py): the torn DOF count Section 4.2 prints
+(96 modules of 31 x 31 interior-edge nodes: 184,512), lexicographic global
+numbering, owner multiplicities, workload shapes.
 """
 import itertools
 from functools import cached_property

@@ -4,8 +4,8 @@ Test infrastructure only (see the package docstring).
 
 Constraint rows (Eq. 4 for TFETI, Eq. 10 for FETI-DP) are kept as explicit
 lists of (subdomain, local DOF, sign).  A DOF shared by more than two
-subdomains gets one row per pair of copies ("pair-wise constraints despite
-the introduced redundancies", Section 3.1), each row being
+subdomains gets one row per pair of copies (Section 3.1 keeps the pair-wise
+rows although they are redundant at cross points), each row being
 u^a - u^b = 0 with a < b.  A fixed DOF in TFETI gets one row per copy,
 u^s = 0 (the Dirichlet part of c in Eq. 4).
 
@@ -17,6 +17,11 @@ Scaling (Section 3.1): B~^s = W^s B^s with W^s diagonal over the rows.
 * multiplicity scaling: W^s = 1 / (number of sharers).
 A single-subdomain (Dirichlet) row has weight 1.  Both choices satisfy the
 admissibility condition Eq. (14); the tests pin that identity.
+
+Pins: tests/test_oracle_dual.py (Eq. 14 for both scalings and methods; k equal
+to multiplicity for homogeneous material), tests/test_oracle_academic.py
+(equal weights on homogeneous interfaces, unequal across laminae), and the
+library's own tearing against these rows (tests/test_host_tearing.py).
 """
 import dataclasses
 from typing import List, Tuple

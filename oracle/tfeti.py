@@ -19,6 +19,10 @@ first row of Eq. (7): G^T alpha = d - F lambda.
 Reading (a DOF that is both fixed and shared): each copy of a fixed DOF gets
 its own Dirichlet row and no continuity row is added for it, so B has full
 row rank apart from the pair-wise redundancy at cross points.
+
+Pins (tests/test_oracle_dual.py): the dense saddle systems of Eqs. (6)-(7),
+K^+ against an SVD pseudo-inverse, the rigid-body null space of floating
+subdomains, the projector identities and G lambda_0 = e, the direct solution.
 """
 import numpy as np
 import scipy.linalg as sla
