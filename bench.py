@@ -237,6 +237,23 @@ def oracle_sample(a, tiles=8):
                                      f"{info.iterations} iterations, {dt:.1f} s")
 
 
+def oracle_apply_sample(a, tiles=6, reps=3):
+    """The oracle's dual-operator block apply alone (Eq. 12 on one block of
+    N_s directions, NumPy products per subdomain) on the same tiles x tiles
+    sample.  Returns (F-applies/s, seconds per block, description)."""
+    import oracle
+    p = workloads.config2(tiles=tiles, elems=a.elems)
+    op = oracle.build(p, "fetidp", "k")
+    X = np.random.default_rng(0).standard_normal((op.n_lam, op.n_sub))
+    op.apply_F(X)
+    t0 = time.perf_counter()
+    for _ in range(reps):
+        op.apply_F(X)
+    dt = (time.perf_counter() - t0) / reps
+    return op.n_sub / dt, dt, (f"oracle apply of one block of {op.n_sub} directions (n_lambda {op.n_lam}) on the "
+                               f"{tiles}x{tiles}-tile sample, {1e3 * dt:.1f} ms per block")
+
+
 def oracle_sample_single_thread(a, tiles):
     """The same oracle sample in a child process with every BLAS / OpenMP pool
     limited to one thread (the single-core figure beside the all-core one).
@@ -849,6 +866,9 @@ def main():
             if one:
                 out["cpu_baseline"]["single_thread"] = {"value": one[0], "unit": "F-applies/s", "cores": 1,
                                                         "seconds": one[1]}
+            av, adt, adesc = oracle_apply_sample(a, tiles=6)
+            out["cpu_baseline"]["apply_only"] = {"value": av, "unit": "F-applies/s", "cores": cpu_threads(),
+                                                 "sample": adesc}
         print(json.dumps(out))
     if world > 1:
         import torch
