@@ -29,6 +29,11 @@ Beside the headline (rank 0, one GPU), the line carries:
   ``primal_3d``  (``--primal-3d``, minutes) corners against corners + edge averages in 3D;
   ``pcg_3d``     (``--pcg-3d``) phase rooflines of the FP64 PCG solve in 3D (HBM-bound phases).
 
+After the GPU measurements, the CPU-baseline leg (rank 0) checks the GPU
+solution against the oracle's direct solve of Eq. (2) (``rel_error_vs_direct_solve``,
+``primal_residual``) and times the oracle on a 6x6-tile sample of the workload
+(``cpu_baseline``: all cores, one thread, and the block apply alone).
+
 ``--impl reference`` times the FP64 CPU oracle on a bounded sample of the
 same workload instead (rank 0 only).
 """
