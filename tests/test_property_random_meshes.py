@@ -72,3 +72,34 @@ def test_library_tearing_matches_oracle_on_random_meshes(harness, p, method, edg
     assert got["n_lam"] == n_lam
     assert _canon(got["rows"]) == _canon(rows)
     assert [sorted(b) for b in got["bsets"]] == bsets
+
+
+@st.composite
+def batches(draw):
+    dim = draw(st.sampled_from([2, 3]))
+    probs = []
+    for _ in range(draw(st.integers(2, 3))):
+        p = draw(meshes())
+        while p.dim != dim:
+            p = draw(meshes())
+        probs.append(p)
+    return probs
+
+
+@settings(**{**SETTINGS, "max_examples": 25})
+@given(probs=batches(), edges=st.booleans())
+def test_library_batch_tearing_matches_oracle_on_random_meshes(harness, probs, edges):  # noqa: F811
+    rows, bsets, n_c, n_lam, s0 = [], [], 0, 0, 0
+    for p in probs:
+        r, b, c, n = _oracle_rows(p, "fetidp", edges, s0)
+        rows += r
+        bsets += b
+        n_c += c
+        n_lam += n
+        s0 += p.n_subdomains
+    if any(_oracle_rows(p, "fetidp", edges)[3] == 0 for p in probs):
+        return                          # a problem without multipliers is refused (see above)
+    got = _run(harness, probs, "fetidp", edges)
+    assert got["n_primal"] == n_c and got["n_lam"] == n_lam
+    assert _canon(got["rows"]) == _canon(rows)
+    assert [sorted(b) for b in got["bsets"]] == bsets
