@@ -84,6 +84,17 @@ int main(int argc, char** argv) {
     for (int k = 0; k < T.n_b; ++k) fprintf(fo, "%s%d", k ? ", " : "", T.blist[k]);
     fprintf(fo, "]");
   }
+  fprintf(fo, "], \"avgs\": [");
+  for (int s = 0; s < hp.n_sub; ++s) {
+    const StructType& T = hp.types[hp.sub_type[s]];
+    fprintf(fo, "%s[", s ? ", " : "");
+    for (size_t a = 0; a < T.avg_c.size(); ++a) {
+      fprintf(fo, "%s[%d", a ? ", " : "", T.clist[T.avg_c[a]]);
+      for (int k = T.avg_off[a]; k < T.avg_off[a + 1]; ++k) fprintf(fo, ", %d", T.blist[T.avg_b[k]]);
+      fprintf(fo, "]");
+    }
+    fprintf(fo, "]");
+  }
   fprintf(fo, "]}\n");
   fclose(fo);
   return 0;
@@ -167,6 +178,21 @@ def test_library_tearing_matches_oracle(harness, method, edges, make):
     assert got["n_lam"] == n_lam
     assert _canon(got["rows"]) == _canon(rows)
     assert [sorted(b) for b in got["bsets"]] == bsets
+
+
+@pytest.mark.parametrize("make", [lambda: workloads.config4(tiles=2, elems=3), lambda: workloads.config4(tiles=3, elems=2),
+                                  lambda: workloads.layered_grid(elems=4, layers=4)])
+def test_edge_average_tables_match_oracle(harness, make):
+    """The change-of-basis tables of every subdomain (the average's slot, then
+    the slots of the edge's other nodes, as local DOFs) are the oracle's edges."""
+    p = make()
+    got = _run(harness, [p], "fetidp", True)
+    op = FETIDP(p, "k", primal="edges")
+    mesh = op.mesh
+    for s in range(op.n_sub):
+        g2 = list(mesh.local_to_global_nodes(s))
+        want = sorted([g2.index(gn) * p.dim + d for gn in nodes] for nodes, d in op.edges if nodes[0] in g2)
+        assert sorted(got["avgs"][s]) == want, s
 
 
 @pytest.mark.parametrize("edges", [False, True])
