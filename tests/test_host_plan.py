@@ -4,7 +4,7 @@ library with no GPU): for every problem's C_p = A_p^T B_p the split-K chunks
 partition [0, K) in order, each at most the chunk length, each reading its own
 rows of A_p and B_p with the right strides; every chunk's partial tile has its
 own disjoint slot of the partial buffer; the reduction of each problem sums
-exactly its chunks into C_p."""
+exactly its chunks into C_p.  Also the tensor-core operand layout rules."""
 import json
 import os
 import shutil
@@ -125,3 +125,42 @@ def test_segmented_plan(harness):
     assert di == len(descs) and out["plen"] == poff
     slots.sort()
     assert all(a1 <= b0 for (_, a1), (b0, _) in zip(slots, slots[1:]))   # disjoint partial slots
+
+
+LAYOUT = r'''
+#include <cstdio>
+#include "kernels.h"
+int main() {
+  for (int p = 1; p <= 4; ++p) printf("%d %d %zu\n", p, feti::tc_chunk(p), feti::tc_elem_bytes(p));
+  for (int nb = 0; nb <= 300; nb += 7)
+    for (int nc = 0; nc <= 64; nc += 3)
+      for (int aug = 0; aug <= 1; ++aug)
+        for (int kc : {32, 64}) printf("k %d %d %d %d %d\n", nb, nc, aug, kc, feti::tc_k_extent(nb, nc, aug, kc));
+  return 0;
+}
+'''
+
+
+def test_tensor_operand_layout_rules(harness, tmp_path):
+    """The tensor-core operand layout (csrc/tc_apply.cu): K chunk of 32 TF32 or 64
+    BF16 values (one 128-byte swizzle row), and a subdomain's K extent = n_b
+    rounded up to the chunk plus, with the primal coupling, n_c rounded up to
+    the chunk -- so every TMA x coordinate is a whole number of 128-byte rows."""
+    gxx = shutil.which("g++")
+    src = tmp_path / "layout.cpp"
+    src.write_text(LAYOUT)
+    exe = tmp_path / "layout"
+    libdir = os.path.dirname(fg.LIB_PATH)
+    subprocess.run([gxx, "-O1", "-std=c++17", "-I", CSRC, "-I", CUDA_INC, str(src), "-L", libdir,
+                    "-l" + os.path.basename(fg.LIB_PATH)[3:-3], "-Wl,-rpath," + libdir, "-o", str(exe)],
+                   check=True, capture_output=True)
+    lines = subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.splitlines()
+    fmt = {int(a): (int(b), int(c)) for a, b, c in (ln.split() for ln in lines if not ln.startswith("k"))}
+    assert fmt == {fg.FETI_TF32: (32, 4), fg.FETI_TF32X3: (32, 4), fg.FETI_BF16: (64, 2), fg.FETI_BF16X3: (64, 2)}
+    for ln in lines:
+        if not ln.startswith("k"):
+            continue
+        nb, nc, aug, kc, ext = map(int, ln.split()[1:])
+        up = lambda x: -(-x // kc) * kc
+        assert ext == up(nb) + (up(nc) if aug and nc > 0 else 0)
+        assert ext % kc == 0
