@@ -71,3 +71,18 @@ def test_option_combinations_rejected_before_any_device_call():
         with pytest.raises(fg.FetiError) as e:
             fg.feti_create(opt)
         assert e.value.status == status
+
+
+def test_binding_constants_match_the_header():
+    """Enumerations of include/feti.h and the binding's constants agree (name and value)."""
+    text = open(os.path.join(ROOT, "include", "feti.h")).read()
+    values = {name: int(v) for name, v in re.findall(r"\b(FETI_[A-Z0-9_]+)\s*=\s*(\d+)", text)}
+    checked = 0
+    for name, v in values.items():
+        if hasattr(fg, name):
+            assert getattr(fg, name) == v, name
+            checked += 1
+    assert checked >= 40
+    phases = sorted((v, n) for n, v in values.items() if n.startswith("FETI_PHASE_"))
+    assert [n[len("FETI_PHASE_"):].lower() for _, n in phases] == list(fg.PHASES)
+    assert values["FETI_N_PHASES"] == len(fg.PHASES)
