@@ -243,6 +243,9 @@ def feti_profile_end(ctx):
 
 
 PHASES = ("apply", "precond", "project", "gram", "step", "ortho", "factor", "recover")
+(FETI_PHASE_APPLY, FETI_PHASE_PRECOND, FETI_PHASE_PROJECT, FETI_PHASE_GRAM, FETI_PHASE_STEP, FETI_PHASE_ORTHO,
+ FETI_PHASE_FACTOR, FETI_PHASE_RECOVER) = range(8)
+FETI_N_PHASES = len(PHASES)
 
 
 def feti_profile_phases(ctx):
