@@ -1,6 +1,8 @@
-"""Host-side arithmetic of bench.py's per-phase rooflines (no GPU): FP64-pipe
+"""Host-side arithmetic of bench.py's rooflines (no GPU): per phase, FP64-pipe
 phases are rated in TFLOP/s against the derived FP64 peak, memory-bound phases
-in GB/s against the measured copy bandwidth, time-only phases carry no rate."""
+in GB/s against the measured copy bandwidth, time-only phases carry no rate;
+for the tensor-core products the binding limit of max(bytes / HBM bandwidth,
+passes x flops / tensor peak) is reported."""
 import os
 import sys
 
@@ -29,3 +31,36 @@ def test_phase_rooflines():
     assert p["frac"] == pytest.approx(3000.0 / bench.tensor_peaks()["hbm_gbs"])
     assert "achieved" not in out["factor"] and "achieved" not in out["ortho"]   # no work recorded
     assert "project" not in out                                                 # never entered
+
+
+class _FakeLib:
+    """Stands in for the binding: a profile of 2 launches of 1 ms, fixed byte counts."""
+    FETI_TF32, FETI_TF32X3, FETI_BF16, FETI_BF16X3 = 1, 2, 3, 4
+    FETI_Q_TC_BYTES_F, FETI_Q_TC_BYTES_PER_COL = 13, 14
+
+    def __init__(self, flops):
+        self.flops = flops
+
+    def feti_profile_tensor(self, ctx):
+        return 2 * self.flops, 2.0, 2
+
+    def feti_query(self, ctx, key):
+        return {13: 2_000_000_000, 14: 4_000_000}[key]
+
+
+class _S:
+    ctx = None
+
+
+def test_tensor_roofline_picks_the_binding_limit():
+    pk = bench.tensor_peaks()
+    # one BF16 pass: 2.0 GB + 512 x 4 MB = 4.048 GB in 1 ms vs 5e11 flops -> HBM-bound
+    r = bench.tensor_roofline(_FakeLib(5e11), _S(), 3, 512)
+    assert r["bound"] == "hbm" and r["passes"] == 1
+    assert r["achieved"] == pytest.approx(4.048e9 / 1e-3 / 1e9)
+    assert r["frac"] == pytest.approx(4.048e9 / (pk["hbm_gbs"] * 1e9) / 1e-3)
+    # split TF32: three passes of 5e11 flops against the TF32 peak -> tensor-bound
+    r = bench.tensor_roofline(_FakeLib(5e11), _S(), 2, 512)
+    assert r["bound"] == "tensor" and r["passes"] == 3
+    assert r["frac"] == pytest.approx(3 * 5e11 / (pk["tf32"] * 1e12) / 1e-3)
+    assert pk["tf32"] == pytest.approx(pk["bf16"] * 1.1 / 2.25)
