@@ -1,4 +1,4 @@
-"""Subdomain-sharded Algorithm 1 for FETI-DP on CPU ranks (oracle).
+"""Subdomain-sharded Algorithm 1 for FETI-DP and TFETI on CPU ranks (oracle).
 
 Test infrastructure only (see the package docstring): a check, on gloo ranks
 of torch.distributed, that the multi-GPU layout of the method gives the
@@ -18,7 +18,10 @@ The layout (one rank per GPU):
   W it touches that other ranks own (a halo), produces its local products, a
   partial coarse right-hand side sum_s F_rc,s^T X_b(s) (all-reduced, then the
   coarse solve is replicated) and contributions to rows owned elsewhere
-  (returned to their owners); the preconditioner columns (Eq. 13) likewise.
+  (returned to their owners); the preconditioner columns (Eq. 13) likewise;
+* TFETI: the rows of G = -R^T B^T belong to their subdomain's rank; G X is a
+  partial (rigid modes x m) block per rank, all-reduced, and the small solve
+  with G G^T is replicated; G^T t is row-local.
 Here each exchange is written as a sum-all-reduce of a full-length array in
 which every rank fills only what it contributes (a row is contributed by its
 owner, a column of Z by the owner of its subdomain); the bytes a real halo
@@ -63,15 +66,18 @@ def partition(op, world):
 
 def solve_dual_sharded(op, tol=1e-6, max_iter=500, rr_tol=1e-10):
     """Algorithm 1 (one direction per subdomain, full orthogonalization) on the
-    current process group.  Returns (lambda on every rank, KrylovInfo, ShardStats)."""
+    current process group, for a FETIDP or TFETI operator object.  Returns
+    (lambda on every rank, KrylovInfo, ShardStats)."""
+    tfeti = hasattr(op, "G")
     rank, world = dist.get_rank(), dist.get_world_size()
     sub_owner, row_owner = partition(op, world)
     mine = np.flatnonzero(sub_owner == rank)
     own = row_owner == rank
     nl = op.n_lam
+    Bsub = op.B if tfeti else op.Br                 # signed B^s (TFETI) or B_r^s (FETI-DP)
     touched = np.zeros(nl, bool)
     for s in mine:
-        touched[np.unique(op.Br[s].tocoo().row)] = True
+        touched[np.unique(Bsub[s].tocoo().row)] = True
     stats = ShardStats(halo_rows=int(np.count_nonzero(touched & ~own)), owned_rows=int(own.sum()),
                        owned_subdomains=int(mine.size))
 
@@ -87,6 +93,12 @@ def solve_dual_sharded(op, tol=1e-6, max_iter=500, rr_tol=1e-10):
     def apply_F(W_part):
         m = W_part.shape[1]
         X = gather_full(W_part, m)
+        if tfeti:                   # F = sum_s B^s K^+_s B^sT (Eq. 7)
+            Yp = np.zeros((nl, m))
+            for s in mine:
+                Yp += op.B[s] @ (op.Kp[s] @ (op.B[s].T @ X))
+            stats.halo_bytes += 2 * stats.halo_rows * m * 8
+            return rows(_allreduce(Yp))
         Vp = np.zeros((op.n_c, m))
         for s in mine:
             Bb = op.Br[s][:, op.bset[s]]
@@ -105,10 +117,23 @@ def solve_dual_sharded(op, tol=1e-6, max_iter=500, rr_tol=1e-10):
         r = gather_full(r_part[:, None], 1)[:, 0]
         Zp = np.zeros((nl, op.n_sub))
         for s in mine:
-            Bt = op.Brt[s][:, op.bset[s]]
+            Bt = (op.Bt if tfeti else op.Brt)[s][:, op.bset[s]]
             Zp[:, s] = Bt @ (op.precond_block(s) @ (Bt.T @ r))
         stats.halo_bytes += 2 * stats.halo_rows * mine.size * 8
         return rows(_allreduce(Zp))
+
+    def project(X_part):            # P X = X - G^T (G G^T)^{-1} G X (TFETI; identity for FETI-DP)
+        if not tfeti:
+            return X_part
+        m = X_part.shape[1]
+        X = gather_full(X_part, m)
+        nr = op.n_rbm
+        GXp = np.zeros((op.G.shape[0], m))
+        for s in mine:
+            GXp[s * nr:(s + 1) * nr] = op.G[s * nr:(s + 1) * nr] @ X
+        stats.allreduce_bytes += GXp.size * 8
+        t = sla.cho_solve(op.GGt_cho, _allreduce(GXp))
+        return X_part - rows(op.G.T @ t)
 
     def dot(a, b):
         stats.allreduce_bytes += 8
@@ -120,10 +145,11 @@ def solve_dual_sharded(op, tol=1e-6, max_iter=500, rr_tol=1e-10):
         return _allreduce(p)
 
     info = KrylovInfo()
-    lam0 = op.lam0
-    r = rows(op.d.copy())           # FETI-DP: lambda_0 = 0, so r_0 = d (Eq. 12)
+    lam0 = op.lam0                  # FETI-DP: 0; TFETI: G^T (G G^T)^{-1} e (replicated set-up)
+    r0 = rows(op.d)[:, None] - apply_F(rows(lam0)[:, None])      # d - F lambda_0 on the owned rows
+    r = project(r0)[:, 0]
     Z = precond_columns(r)
-    W = Z.copy()
+    W = project(Z)
     lam_t = np.zeros(nl)
     hist = []
     eps = np.sqrt(max(dot(r, Z.sum(axis=1)), 0.0))
@@ -145,10 +171,10 @@ def solve_dual_sharded(op, tol=1e-6, max_iter=500, rr_tol=1e-10):
         W, Q = W @ T, Q @ T
         gamma = gram(W, r[:, None])[:, 0]
         lam_t = lam_t + W @ gamma
-        r = r - Q @ gamma
+        r = r - project((Q @ gamma)[:, None])[:, 0]
         Z = precond_columns(r)
         hist.append((W, Q))
-        Wn = Z.copy()
+        Wn = project(Z)
         for Wj, Qj in hist:
             Wn = Wn - Wj @ gram(Qj, Wn)
         W = Wn

@@ -1,8 +1,9 @@
-"""The multi-GPU layout of FETI-DP + Algorithm 1, checked on gloo ranks of
+"""The multi-GPU layout of FETI-DP / TFETI + Algorithm 1, checked on gloo ranks of
 torch.distributed (CPU): subdomains in contiguous blocks per rank, multiplier
 rows owned by the rank of their lowest subdomain, halo exchanges around the
 dual-operator apply and the preconditioner, all-reduces of the coarse
-right-hand side and of the Gram-type blocks.  On 2 and 3 ranks the sharded
+right-hand side (FETI-DP) or of G X (TFETI) and of the Gram-type blocks.  On
+2 and 3 ranks the sharded
 solve takes the serial oracle's iterations and reaches its solution."""
 import os
 import socket
@@ -30,13 +31,13 @@ def _problem():
     return p
 
 
-def _worker(rank, world, port, out):
+def _worker(rank, world, port, method, out):
     os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port))
     sys.path.insert(0, ROOT)
     dist.init_process_group("gloo", rank=rank, world_size=world)
-    from oracle.fetidp import FETIDP
+    from oracle.solve import build
     from oracle.sharded import solve_dual_sharded
-    op = FETIDP(_problem(), "k")
+    op = build(_problem(), method, "k")
     lam, info, st = solve_dual_sharded(op, tol=1e-10)
     out[rank] = (op.recover(lam), info.iterations, info.ranks, st.halo_rows, st.owned_rows, st.owned_subdomains,
                  st.halo_bytes, st.allreduce_bytes)
@@ -44,13 +45,13 @@ def _worker(rank, world, port, out):
     dist.destroy_process_group()
 
 
-@pytest.mark.parametrize("world", [2, 3])
-def test_sharded_algorithm1_matches_serial(world):
+@pytest.mark.parametrize("method,world", [("fetidp", 2), ("fetidp", 3), ("tfeti", 2)])
+def test_sharded_algorithm1_matches_serial(method, world):
     sys.path.insert(0, ROOT)
     from oracle.solve import solve
     out = mp.Manager().dict()
-    mp.spawn(_worker, args=(world, _free_port(), out), nprocs=world, join=True)
-    u_ser, _, info, op = solve(_problem(), "fetidp", "k", "rrs", tol=1e-10)
+    mp.spawn(_worker, args=(world, _free_port(), method, out), nprocs=world, join=True)
+    u_ser, _, info, op = solve(_problem(), method, "k", "rrs", tol=1e-10)
     for r in range(world):
         u, its, ranks, halo, owned, nsub, hb, ab = out[r]
         assert its == info.iterations and ranks == info.ranks
