@@ -9,6 +9,9 @@ the self-adjoint SIMP sensitivity -p rho_e^(p-1) (E0 - Emin) u_e^T k0 u_e from
 the recovered displacement: no adjoint solve is needed because the
 compliance problem is self-adjoint.  This module only marshals tensors.
 """
+import os
+
+import numpy as np
 import torch
 
 from . import (FETI_ENOTCONV, FETI_FETIDP, FETI_OK, FETI_PCG, FETI_SCALING_K, FETI_Q_N_LAMBDA, Solver,
@@ -85,12 +88,37 @@ def oc_update(rho, dc, volfrac, move=0.2, eta=0.5, rho_min=1e-3):
     return new
 
 
-def optimize(cp, rho0, volfrac, iterations=50, callback=None):
-    """Run `iterations` OC steps; returns the final densities and the history
-    of (compliance, Krylov iterations)."""
+def save_checkpoint(path, iteration, rho, lam, history):
+    """The whole state of the design loop after `iteration` completed steps:
+    the densities, the multiplier that warm-starts the next state solve (or
+    None) and the history of (compliance, Krylov iterations).  Written to a
+    temporary file first and renamed, so an interrupted save leaves the
+    previous checkpoint intact."""
+    arrays = {"iteration": np.array(iteration), "rho": rho.detach().cpu().numpy(),
+              "history": np.array(history, dtype=np.float64).reshape(-1, 2)}
+    if lam is not None:
+        arrays["lam"] = lam.detach().cpu().numpy()
+    tmp = str(path) + ".tmp.npz"
+    np.savez(tmp, **arrays)
+    os.replace(tmp, str(path))
+
+
+def load_checkpoint(path, device="cuda"):
+    """(iteration, densities, multiplier or None, history) saved by save_checkpoint."""
+    with np.load(str(path)) as z:
+        lam = torch.as_tensor(z["lam"], device=device) if "lam" in z.files else None
+        hist = [(float(c), int(k)) for c, k in z["history"]]
+        return int(z["iteration"]), torch.as_tensor(z["rho"], device=device), lam, hist
+
+
+def optimize(cp, rho0, volfrac, iterations=50, callback=None, checkpoint=None, start=0, history=None):
+    """Run OC steps `start` .. `iterations` - 1; returns the final densities and
+    the history of (compliance, Krylov iterations).  With `checkpoint` (a path)
+    the state is saved after every step; resume with load_checkpoint and pass
+    its iteration, history and multiplier (cp.lam) back."""
     rho = rho0.clone()
-    hist = []
-    for it in range(iterations):
+    hist = list(history or [])
+    for it in range(start, iterations):
         r = rho.clone().requires_grad_(True)
         c = compliance(r, cp)
         c.backward()
@@ -99,6 +127,8 @@ def optimize(cp, rho0, volfrac, iterations=50, callback=None):
         if callback:
             callback(it, rho, cval, cp.last_stats)
         rho = oc_update(rho, r.grad, volfrac)
+        if checkpoint is not None:
+            save_checkpoint(checkpoint, it + 1, rho, cp.lam, hist)
     return rho, hist
 
 
@@ -176,6 +206,8 @@ def main(argv=None):
     ap.add_argument("--fd", type=int, default=20)
     ap.add_argument("--fd-rel-h", type=float, default=1e-3)
     ap.add_argument("--fd-tol", type=float, default=1e-12)
+    ap.add_argument("--checkpoint", default=None, help="save the loop's state (.npz) after every design step")
+    ap.add_argument("--resume", action="store_true", help="continue from --checkpoint")
     a = ap.parse_args(argv)
 
     p = workloads.config5(tiles=a.tiles, elems=a.elems, volfrac=a.volfrac)
@@ -187,6 +219,11 @@ def main(argv=None):
         print(json.dumps({"fd_check": fd}), flush=True)
     cp = ComplianceProblem(p, krylov=FETI_PCG, tol=a.tol, warm_start=True)
     rho = torch.tensor(p.rho, dtype=torch.float64, device="cuda")
+    start, history = 0, None
+    if a.resume and a.checkpoint and os.path.exists(a.checkpoint):
+        start, rho, lam, history = load_checkpoint(a.checkpoint)
+        if lam is not None:
+            cp.lam.copy_(lam)
     t_last = [time.perf_counter()]
 
     def cb(it, r, c, st):
@@ -197,7 +234,8 @@ def main(argv=None):
         t_last[0] = now
 
     t0 = time.perf_counter()
-    rho, hist = optimize(cp, rho, a.volfrac, iterations=a.iterations, callback=cb)
+    rho, hist = optimize(cp, rho, a.volfrac, iterations=a.iterations, callback=cb, checkpoint=a.checkpoint,
+                         start=start, history=history)
     torch.cuda.synchronize()
     total = time.perf_counter() - t0
     # the same final state solve without the warm start, for comparison
