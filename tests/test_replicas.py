@@ -34,7 +34,7 @@ def _worker(rank, world, port, out):
 
 def test_two_replicas_aggregate_on_gloo():
     world = 2
-    with mp.Manager() as mgr:
+    with mp.get_context("spawn").Manager() as mgr:
         out = mgr.dict()
         mp.spawn(_worker, args=(world, _free_port(), out), nprocs=world, join=True)
         res = dict(out)

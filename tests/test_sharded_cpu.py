@@ -49,8 +49,10 @@ def _worker(rank, world, port, method, out):
 def test_sharded_algorithm1_matches_serial(method, world):
     sys.path.insert(0, ROOT)
     from oracle.solve import solve
-    out = mp.Manager().dict()
-    mp.spawn(_worker, args=(world, _free_port(), method, out), nprocs=world, join=True)
+    with mp.get_context("spawn").Manager() as mgr:          # no fork of this (threaded) process
+        out = mgr.dict()
+        mp.spawn(_worker, args=(world, _free_port(), method, out), nprocs=world, join=True)
+        out = dict(out)
     u_ser, _, info, op = solve(_problem(), method, "k", "rrs", tol=1e-10)
     for r in range(world):
         u, its, ranks, halo, owned, nsub, hb, ab = out[r]
