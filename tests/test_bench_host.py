@@ -64,3 +64,20 @@ def test_tensor_roofline_picks_the_binding_limit():
     assert r["bound"] == "tensor" and r["passes"] == 3
     assert r["frac"] == pytest.approx(3 * 5e11 / (pk["tf32"] * 1e12) / 1e-3)
     assert pk["tf32"] == pytest.approx(pk["bf16"] * 1.1 / 2.25)
+
+
+def test_reference_arm_line_contract():
+    """`bench.py --impl reference` (the CPU oracle, as it stands) prints one JSON
+    line with the contract's keys, the reference marker and zero copy bytes."""
+    import json
+    import subprocess
+    r = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference", "--steps", "1",
+                        "--warmup", "0"], capture_output=True, text=True, timeout=600, cwd=ROOT)
+    assert r.returncode == 0, r.stderr[-2000:]
+    line = json.loads(r.stdout.strip().splitlines()[-1])
+    for key in ("metric", "value", "unit", "n_gpus", "steps", "warmup", "ms_per_step", "higher_is_better", "scaling",
+                "vs_baseline", "dtype", "data", "config", "cpu_baseline", "e2e"):
+        assert key in line, key
+    assert line["impl"] == "reference" and line["value"] > 0 and line["unit"] == "F-applies/s"
+    assert line["cpu_baseline"]["kind"] == "oracle" and line["cpu_baseline"]["value"] == line["value"]
+    assert line["e2e"]["h2d_bytes_per_step"] == 0 and line["e2e"]["d2h_bytes_per_step"] == 0
