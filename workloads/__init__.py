@@ -21,7 +21,10 @@ format, not a method choice):
 The paper's own benchmark geometries (the laminated academic problems and
 the modular MBB-beam snapshots, Section 4) are not available; the seeded
 random fields below stand in for them with the same structure: fixed regular
-modular partitioning and stiffness contrast that reaches the interfaces.
+modular partitioning and stiffness contrast that reaches the interfaces.  The
+academic problems also get stand-ins built from the section's prose only
+(laminated beam, laminated grid, grid of stiff inclusions; the material
+values and exact geometry are readings).
 """
 from __future__ import annotations
 
