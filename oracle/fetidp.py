@@ -62,9 +62,15 @@ PRECONDS = ("dirichlet", "lumped", "superlumped")
 
 
 class _Module:
-    """Per-distinct-subdomain factorisation data (shared by identical modules)."""
+    """Per-distinct-subdomain factorisation data (shared by identical modules).
 
-    def __init__(self, Ks, r_loc, c_loc, b_in_r):
+    ``keep_factor=False`` keeps only the dense blocks the dual operator and the
+    preconditioner use (F_s, F_rc restricted to b, the local Kbar_cc, S and
+    K_bb) and releases K_rr, K_rc and the Cholesky factor: same blocks, less
+    host memory (the right-hand sides and the recovery need the factor);
+    K_bb is then kept only for the lumped preconditioners (keep_kbb)."""
+
+    def __init__(self, Ks, r_loc, c_loc, b_in_r, keep_factor=True, keep_kbb=True):
         self.Krr = Ks[np.ix_(r_loc, r_loc)]
         self.Krc = Ks[np.ix_(r_loc, c_loc)]
         self.Kcc = Ks[np.ix_(c_loc, c_loc)]
@@ -80,6 +86,10 @@ class _Module:
         self.Kbar = self.Kcc - self.Krc.T @ self.KinvKrc               # local Kbar_cc^s
         self.S = schur_complement(self.Krr, b_in_r)                    # Eq. (13) on r-DOFs
         self.Kbb = self.Krr[np.ix_(b_in_r, b_in_r)]                    # lumped: K_bb instead of S
+        if not keep_factor:
+            del self.Krr, self.Krc, self.Kcc, self.cho, self.KinvKrc
+            if not keep_kbb:
+                del self.Kbb
 
 
 PRIMALS = ("corners", "edges")
@@ -112,7 +122,13 @@ def edge_averages(problem, mesh):
 
 
 class FETIDP:
-    def __init__(self, problem, scaling="k", dedup=True, precond="dirichlet", primal="corners"):
+    def __init__(self, problem, scaling="k", dedup=True, precond="dirichlet", primal="corners",
+                 operator_only=False):
+        """``operator_only``: build the blocks of the dual operator, the coarse
+        matrix and the preconditioner only (no right-hand sides, no recovery),
+        releasing each module's factor after use -- for operator-level checks at
+        sizes where keeping every factor would not fit in host memory."""
+        self.operator_only = operator_only
         if precond not in PRECONDS:
             raise ValueError(precond)
         if primal not in PRIMALS:
@@ -217,7 +233,9 @@ class FETIDP:
                 h.update(np.ascontiguousarray(a).tobytes())
             key = h.hexdigest() if dedup else s
             if key not in self.modules:
-                self.modules[key] = _Module(Ks, self.r_loc[s], self.c_loc[s], self.bset[s])
+                self.modules[key] = _Module(Ks, self.r_loc[s], self.c_loc[s], self.bset[s],
+                                            keep_factor=not operator_only,
+                                            keep_kbb=not operator_only or precond != "dirichlet")
             self.mod_key.append(key)
         # --- coarse problem and right-hand sides (Eq. 12) ---
         Kbar = np.zeros((self.n_c, self.n_c))
@@ -227,15 +245,20 @@ class FETIDP:
             M = self.mod(s)
             cg = self.c_glob[s]
             Kbar[np.ix_(cg, cg)] += M.Kbar
+            if operator_only:
+                continue
             y = sla.cho_solve(M.cho, self.f_r[s])                      # K_rr^{-1} f_r^s
             np.add.at(fbar, cg, self.f_c[s] - M.Krc.T @ y)
             d_r += self.Br[s] @ y
         self.Kbar = 0.5 * (Kbar + Kbar.T)
         self.Kbar_cho = sla.cho_factor(self.Kbar, lower=True)
+        self.lam0 = np.zeros(self.n_lam)
+        if operator_only:
+            self.fbar = self.d_r = self.d = None
+            return
         self.fbar = fbar
         self.d_r = d_r
         self.d = d_r - self.apply_Frc(sla.cho_solve(self.Kbar_cho, fbar)[:, None])[:, 0]
-        self.lam0 = np.zeros(self.n_lam)
 
     def mod(self, s):
         return self.modules[self.mod_key[s]]
@@ -271,6 +294,36 @@ class FETIDP:
         X = np.atleast_2d(X.T).T
         V = sla.cho_solve(self.Kbar_cho, self.apply_FrcT(X))
         return self.apply_Frr(X) + self.apply_Frc(V)
+
+    def apply_F_rows(self, X, rows):
+        """Rows ``rows`` of apply_F(X): the same sums restricted to those
+        multipliers.  Only the subdomains that own one of the rows contribute
+        their local term; the coarse correction V = Kbar_cc^{-1} F_rc^T X still
+        gathers every subdomain.  For operator checks at sizes where forming
+        all of F X is too slow.  Pinned against apply_F (tests/test_oracle_dual.py)."""
+        X = np.atleast_2d(X.T).T
+        rows = np.asarray(rows, dtype=np.int64)
+        V = sla.cho_solve(self.Kbar_cho, self.apply_FrcT(X))
+        Y = np.zeros((rows.size, X.shape[1]))
+        for s in range(self.n_sub):
+            b = self.bset[s]
+            Bb_R = self.Br[s][rows][:, b]
+            if Bb_R.nnz == 0:
+                continue
+            M = self.mod(s)
+            xb = self.Br[s][:, b].T @ X
+            Y += Bb_R @ (M.Fb @ xb + M.Frc_b @ V[self.c_glob[s]])
+        return Y
+
+    def row_entries(self):
+        """The multipliers as int64 [n_lam, 6] rows (s1, local dof1, sign1,
+        s2, local dof2, sign2), local DOFs numbered in the subdomain (not in
+        its r-set); s2 = -1 for a single-subdomain row."""
+        out = -np.ones((self.n_lam, 6), np.int64)
+        for l, ent in enumerate(self.cons.entries):
+            for t, (s, k, sg) in enumerate(ent):
+                out[l, 3 * t:3 * t + 3] = (s, int(self.r_loc[s][k]), int(sg))
+        return out
 
     def project(self, X):
         return X            # FETI-DP needs no projector

@@ -40,15 +40,23 @@ class Constraints:
     def n_lam(self):
         return len(self.entries)
 
+    def entries_of(self, s):
+        """(row, position in the row, local dof, sign) of every entry of subdomain
+        s, in row order (indexed once for all subdomains)."""
+        if not hasattr(self, "_by_sub"):
+            self._by_sub = {}
+            for l, ent in enumerate(self.entries):
+                for t, (q, k, sg) in enumerate(ent):
+                    self._by_sub.setdefault(q, []).append((l, t, k, sg))
+        return self._by_sub.get(s, [])
+
     def B_sub(self, s, n_loc, weights=None):
         """B^s (or B~^s when ``weights`` is given) as CSR [n_lam, n_loc]."""
         rows, cols, vals = [], [], []
-        for l, ent in enumerate(self.entries):
-            for t, (q, k, sg) in enumerate(ent):
-                if q == s:
-                    rows.append(l)
-                    cols.append(k)
-                    vals.append(sg * (1.0 if weights is None else weights[l][t]))
+        for l, t, k, sg in self.entries_of(s):
+            rows.append(l)
+            cols.append(k)
+            vals.append(sg * (1.0 if weights is None else weights[l][t]))
         return sp.csr_matrix((vals, (rows, cols)), shape=(self.n_lam, n_loc))
 
 

@@ -180,6 +180,62 @@ def test_fetidp_eq11_and_eq12_blocks():
     assert np.abs(Br @ ur2).max() <= 1e-9 * np.abs(ur2).max()            # B_r u_r = 0
 
 
+def test_fetidp_row_restricted_apply_and_operator_only_build():
+    """apply_F_rows against the dense condensed operator of Eq. (12) built from
+    global inverses; the operator-only build gives the same operator and
+    preconditioner bit for bit; row_entries reproduces B_r."""
+    p = tiny(tiles=(3, 3), elems=(2, 2))
+    op = FETIDP(p, "k", dedup=False)
+    ns = op.n_sub
+    Krr = sla.block_diag(*[op.mod(s).Krr for s in range(ns)])
+    Br = np.hstack([op.Br[s].toarray() for s in range(ns)])
+    Bc = [op.Bc[s].toarray() for s in range(ns)]
+    Kcc = sum(Bc[s].T @ op.mod(s).Kcc @ Bc[s] for s in range(ns))
+    Kcr = np.hstack([Bc[s].T @ op.mod(s).Krc.T for s in range(ns)])
+    Kinv = np.linalg.inv(Krr)
+    Frc = Br @ Kinv @ Kcr.T
+    F = Br @ Kinv @ Br.T + Frc @ np.linalg.solve(Kcc - Kcr @ Kinv @ Kcr.T, Frc.T)
+    rng = np.random.default_rng(5)
+    X = rng.standard_normal((op.n_lam, 5))
+    rows = np.sort(rng.choice(op.n_lam, 7, replace=False))
+    assert rel(op.apply_F_rows(X, rows), (F @ X)[rows]) <= 1e-10
+    lean = FETIDP(p, "k", dedup=False, operator_only=True)
+    assert lean.d is None and not hasattr(lean.mod(0), "cho")
+    assert np.array_equal(lean.apply_F(X), op.apply_F(X))
+    assert np.array_equal(lean.precond_columns(X[:, 0]), op.precond_columns(X[:, 0]))
+    # row_entries: the signed jumps of local vectors (full local numbering) equal B_r u_r
+    ent = op.row_entries()
+    us = [rng.standard_normal(op.mesh.n_loc_dofs) for _ in range(ns)]
+    jump = np.zeros(op.n_lam)
+    for t in (0, 3):
+        for l in range(op.n_lam):
+            if ent[l, t] >= 0:
+                jump[l] += ent[l, t + 2] * us[ent[l, t]][ent[l, t + 1]]
+    ur = np.concatenate([us[s][op.r_loc[s]] for s in range(ns)])
+    assert np.allclose(jump, Br @ ur, rtol=0, atol=1e-14)
+
+
+def test_multiplier_block_is_independent_of_row_order_and_orientation():
+    """Two numberings of the same multipliers (rows permuted, some rows with the
+    copies listed the other way round and negated) get the same test block up to
+    that permutation and sign, so B^T X is the same interface vector."""
+    op = FETIDP(tiny(tiles=(3, 2), elems=(2, 2)), "k")
+    ent = op.row_entries()
+    rng = np.random.default_rng(1)
+    perm = rng.permutation(op.n_lam)
+    flip = rng.random(op.n_lam) < 0.5
+    other = ent[perm].copy()
+    f = flip[perm]
+    other[f] = other[f][:, [3, 4, 5, 0, 1, 2]]
+    other[f, 2] *= -1
+    other[f, 5] *= -1
+    Xa = workloads.multiplier_block(*workloads.multiplier_pairs(ent), 4, seed=9)
+    Xb = workloads.multiplier_block(*workloads.multiplier_pairs(other), 4, seed=9)
+    sgn = np.where(f, -1.0, 1.0)[:, None]
+    assert np.array_equal(Xb, sgn * Xa[perm])
+    assert np.all(np.abs(Xa) <= 1.0) and Xa.std() > 0.4
+
+
 def test_fetidp_dedup_is_exact():
     p = workloads.config2(tiles=4, elems=4)
     a = FETIDP(p, "k", dedup=True)

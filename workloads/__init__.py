@@ -37,7 +37,7 @@ import numpy as np
 __all__ = [
     "Problem", "tile_problem", "gaussian_field", "binary_patterns",
     "config1", "config2", "config3", "config4", "config5",
-    "layered_beam", "layered_grid", "inclusion_grid",
+    "layered_beam", "layered_grid", "inclusion_grid", "multiplier_pairs", "multiplier_block",
 ]
 
 
@@ -286,3 +286,58 @@ def inclusion_grid(elems: int = 16, frac: float = 0.5, contrast: float = 1e3, n:
     (homogeneous material along every interface)."""
     return _academic(f"{n}x{n} grid with stiff inclusions, contrast {contrast:g}", (n, n), elems,
                      _inclusion(elems, frac, contrast), contrast)
+
+
+# ---- seeded test blocks on a multiplier space ------------------------------------
+# Two implementations may number and orient the multipliers differently.  A row
+# is identified by the (subdomain, local DOF) copies it joins, so test blocks are
+# generated from that identity (not from the row's position) and every row is
+# multiplied by the sign its implementation gives the canonically first copy:
+# B^T X is then the same interface vector on both sides.
+
+_SM_GAMMA = np.uint64(0x9E3779B97F4A7C15)
+
+
+def _splitmix64(x: np.ndarray) -> np.ndarray:
+    """The SplitMix64 output function (Steele, Lea and Flood, "Fast splittable
+    pseudorandom number generators", OOPSLA 2014) applied to uint64 arrays."""
+    with np.errstate(over="ignore"):
+        z = x + _SM_GAMMA
+        z = (z ^ (z >> np.uint64(30))) * np.uint64(0xBF58476D1CE4E5B9)
+        z = (z ^ (z >> np.uint64(27))) * np.uint64(0x94D049BB133111EB)
+        return z ^ (z >> np.uint64(31))
+
+
+def multiplier_pairs(layout: np.ndarray):
+    """Canonical identity of each multiplier row.
+
+    ``layout``: int [n, 6] rows (s1, dof1, sign1, s2, dof2, sign2), s2 = -1 for a
+    single-subdomain row.  Returns (keys int64 [n, 4] = the two (s, dof) copies in
+    increasing order, (-1, -1) for a missing second copy; sign float64 [n] = the
+    row's sign on its first key copy)."""
+    L = np.asarray(layout, dtype=np.int64)
+    a = L[:, 0:2]
+    b = L[:, 3:5]
+    has_b = L[:, 3] >= 0
+    swap = has_b & ((b[:, 0] < a[:, 0]) | ((b[:, 0] == a[:, 0]) & (b[:, 1] < a[:, 1])))
+    first = np.where(swap[:, None], b, a)
+    second = np.where(swap[:, None], a, b)
+    second = np.where(has_b[:, None], second, -1)
+    keys = np.concatenate([first, second], axis=1)
+    sign = np.where(swap, L[:, 5], L[:, 2]).astype(np.float64)
+    return keys, sign
+
+
+def multiplier_block(keys: np.ndarray, sign: np.ndarray, m: int, seed: int, col0: int = 0) -> np.ndarray:
+    """Test block X [n, m] on a multiplier space: X[l, j] = sign[l] * U(keys[l], col0 + j)
+    with U uniform in [-1, 1) from SplitMix64 of the seed, the row's canonical key and
+    the column -- the same values whatever order either implementation gives its rows."""
+    k = np.asarray(keys, dtype=np.int64).astype(np.uint64)
+    h = _splitmix64(np.full(k.shape[0], np.uint64(seed)))
+    for c in range(4):
+        h = _splitmix64(h ^ k[:, c])
+    out = np.empty((k.shape[0], m), np.float64)
+    for j in range(m):
+        z = _splitmix64(h ^ np.uint64(((col0 + j) * int(_SM_GAMMA)) & 0xFFFFFFFFFFFFFFFF))
+        out[:, j] = (z >> np.uint64(11)).astype(np.float64) * (2.0 ** -52) - 1.0
+    return out * np.asarray(sign, np.float64)[:, None]
