@@ -222,10 +222,14 @@ def config3(n_problems: int = 64, seed: int = 3, tile_range=(4, 24), elem_range=
 
 
 def config4(tiles: int = 8, elems: int = 8, seed: int = 4, sigma: float = 8.0) -> Problem:
-    """3D H8: tiles^3 subdomains of elems^3 elements, smoothed field clipped to [1e-3, 1]."""
+    """3D H8: tiles^3 subdomains of elems^3 elements, smoothed field clipped to [1e-3, 1].
+
+    The field is rounded to a multiple of 2^-20 before clipping: the FFT and the
+    normal CDF may differ in their last bits between machines, and the rounding
+    makes the densities (and their hash) the same on every host."""
     rng = np.random.Generator(np.random.PCG64(seed))
     n = tiles * elems
-    fld = np.clip(gaussian_field((n, n, n), sigma, rng), 1e-3, 1.0)
+    fld = np.clip(np.round(gaussian_field((n, n, n), sigma, rng) * 2.0 ** 20) * 2.0 ** -20, 1e-3, 1.0)
     return tile_problem(f"{tiles}^3 tiles of {elems}^3 H8, smoothed field", 3,
                         (tiles,) * 3, (elems,) * 3, fld.ravel(order="F"), Emin=0.0)
 
