@@ -26,7 +26,10 @@
  * - Ownership: the caller owns every buffer it passes; the library copies
  *   what it needs during the call (or, for device outputs, writes into the
  *   caller's memory on the context stream).  The library owns the context
- *   and all internal device memory, released by feti_destroy.
+ *   and all internal device memory, released by feti_destroy.  That memory is
+ *   taken from the caller's allocator when one is installed with
+ *   feti_set_allocator (e.g. a framework's caching allocator), otherwise
+ *   stream-ordered (cudaMallocAsync / cudaFreeAsync) on the context stream.
  * - Errors: no entry point aborts or exits.  A non-OK status leaves a
  *   human-readable message in feti_last_error(ctx).  FETI_ESTATE means the
  *   call order setup -> factorize -> solve -> recover was not respected.
@@ -63,8 +66,9 @@ enum { FETI_SCALING_K = 0, FETI_SCALING_MULT = 1 };       /* Eq. 15 / multiplici
 enum { FETI_PCG = 0, FETI_FO = 1, FETI_RRS = 2 };         /* Sections 3.2, 3.3 */
 enum { FETI_FP64 = 0, FETI_TF32 = 1, FETI_TF32X3 = 2, FETI_BF16 = 3, FETI_BF16X3 = 4 };  /* block products */
 enum { FETI_PRECOND_DIRICHLET = 0, FETI_PRECOND_LUMPED = 1, FETI_PRECOND_SUPERLUMPED = 2 };
-enum { FETI_PRIMAL_CORNERS = 0, FETI_PRIMAL_EDGES = 1 };  /* FETI-DP primal set (Section 2.2; richer
-                                                             sets: Section 5, future work) */
+enum { FETI_PRIMAL_CORNERS = 0, FETI_PRIMAL_EDGES = 1, FETI_PRIMAL_ADAPTIVE = 2 };
+                                               /* FETI-DP primal set (Section 2.2; richer and adaptive
+                                                  sets: Section 5, future work) */
 
 typedef struct {
   int method;          /* FETI_TFETI or FETI_FETIDP */
@@ -88,16 +92,17 @@ typedef struct {
                           (default; the interface Schur complement S_s of Eq. 13), FETI_PRECOND_LUMPED
                           (the interface stiffness block K_bb: no interior solve) or
                           FETI_PRECOND_SUPERLUMPED (diag K_bb) */
-  int fp64_residual;   /* reduced precision, 0 (default) or 1: every inner iteration replaces
-                          the recursive residual by the FP64 residual r_outer - P^T F lambda~
-                          (one FP64 single-column apply per iteration) and the inner solve
-                          aims at the final tolerance, so the Krylov space is not restarted */
   int primal;          /* FETI-DP primal set: FETI_PRIMAL_CORNERS (default; the DOFs at the vertices
                           of the tile grid) or FETI_PRIMAL_EDGES (also one average per component over
                           the interior nodes of every tile-grid edge shared by two or more
                           subdomains -- 3D: tile edges, 2D: tile sides -- whose nodes are all free in
                           that component; introduced by a change of basis on each edge, with the
-                          Dirichlet preconditioner only).  TFETI: must be FETI_PRIMAL_CORNERS */
+                          Dirichlet preconditioner only) or FETI_PRIMAL_ADAPTIVE (the same averages
+                          only on the edges across which the stiffness jumps: on some interior node
+                          of the edge the sharers' diagonal stiffness entries -- the quantities
+                          k-scaling weighs -- differ by a factor >= primal_jump; chosen from the
+                          densities given at set-up).  TFETI: must be FETI_PRIMAL_CORNERS */
+  double primal_jump;  /* FETI_PRIMAL_ADAPTIVE: the jump ratio that selects an edge (default 10; >= 1) */
 } feti_options;
 
 typedef struct {
@@ -120,6 +125,19 @@ typedef struct {
   int refinements;      /* FETI_TF32: FP64 refinement steps taken (0 for FETI_FP64) */
 } feti_stats;
 
+/* Caller-supplied device allocator for a context's internal memory.
+ * alloc(user, bytes, stream) returns device memory of the context's device
+ * usable on `stream` (the context stream), or NULL on failure (the library then
+ * returns FETI_ENOMEM); free(user, ptr, bytes, stream) releases a pointer that
+ * alloc returned, with the same byte count.  The library frees every pointer
+ * it was given, at the latest in feti_destroy, after synchronising the stream.
+ * The callbacks are called from the thread that calls the library. */
+typedef struct {
+  void* (*alloc)(void* user, size_t bytes, void* stream);
+  void (*free)(void* user, void* ptr, size_t bytes, void* stream);
+  void* user;
+} feti_allocator;
+
 /* Fill *opt with the defaults listed above.  Never fails for non-null opt. */
 feti_status feti_options_default(feti_options* opt);
 
@@ -127,6 +145,14 @@ feti_status feti_options_default(feti_options* opt);
  * (a cudaStream_t; NULL = the legacy default stream).  *out receives the
  * context (owned by the library until feti_destroy). */
 feti_status feti_create(feti_ctx** out, const feti_options* opt, void* stream);
+
+/* Install (a != NULL, both callbacks set) or remove (a == NULL: back to
+ * cudaMallocAsync on the context stream) the allocator of the context's
+ * internal device memory.  Allowed only while the context holds no device
+ * memory -- after feti_create, before feti_setup_subdomains / feti_setup_batch
+ * (FETI_ESTATE otherwise); FETI_EINVAL for a null callback.  Not part of the
+ * paper's method: the ownership rule of the boundary. */
+feti_status feti_set_allocator(feti_ctx* ctx, const feti_allocator* a);
 
 /* Tear the mesh into subdomains and build every index map on the host
  * (Eqs. 4-5 for TFETI; Eqs. 8-10 and the corner primal set for FETI-DP;
@@ -205,6 +231,16 @@ feti_status feti_compliance_grad(feti_ctx* ctx, double* dc_drho, int on_device);
  * feti_factorize. */
 feti_status feti_apply_dual(feti_ctx* ctx, const double* X, int ldx, int m, double* Y, int ldy);
 
+/* Test hook of the failure path (not part of the method).  The next
+ * tensor-core product of ctx that runs in the one-tile-per-CTA kernel (the
+ * FETI_TF32 and FETI_TF32X3 precisions) skips, in its first tile only, the
+ * copy of K chunk `chunk` (0-based) and every later one, so that the MMA
+ * lane's bounded wait (1 s) for it runs out: that product records the
+ * time-out, frees its tensor memory and returns, and the call that launched it
+ * returns FETI_ETIMEOUT; the context stays usable.  The hook is used by one
+ * product and then cleared; chunk < 0 clears it.  No copy is left in flight. */
+feti_status feti_test_skip_copy(feti_ctx* ctx, int chunk);
+
 /* The block Dirichlet preconditioner of Algorithm 1: column s of Z is
  * B~^s S^s B~^sT r (Eq. 13 with the scaled B~ of Section 3.1), z = Z 1.
  * r: DEVICE [n_lambda]; Z: DEVICE column-major [n_lambda x n_subdomains] with
@@ -221,8 +257,11 @@ feti_status feti_apply_precond(feti_ctx* ctx, const double* r, double* Z, int ld
  * than 262144 entries (FETI_Q_N_B_TOTAL) are rejected with FETI_EINVAL.
  * All calls share that array: calls whose kernels overlap on the GPU race,
  * so serialise them.  The first call on a device looks up the array's device
- * address; make that first call before any stream capture.  No CUDA or other
- * allocation is made by this call. */
+ * address; make that first call before any stream capture.  That address
+ * belongs to the device's primary context: after cudaDeviceReset the process
+ * must not call this entry point on that device again.  Problems too large
+ * for the array are rejected as soon as they are set up (before any device
+ * work).  No CUDA or other allocation is made by this call. */
 feti_status feti_apply_precond_noalloc(feti_ctx* ctx, const double* r, double* Z, int ldz, double* z);
 
 /* Integer facts about the set-up problem; key is one of FETI_Q_*. */
@@ -269,7 +308,8 @@ feti_status feti_profile_tensor(const feti_ctx* ctx, double* flops, double* ms, 
  *            the corner coupling 4 n_b n_c m and the coarse solve 2 n_c^2 m)
  *   PRECOND  preconditioner Z (Eq. 13; bytes: the distinct local blocks once, the
  *            residual and interface vectors, the dense Z of the simultaneous variant)
- *   PROJECT  TFETI projector (bytes: G twice, the block in and out)
+ *   PROJECT  TFETI projector (bytes: the block read for G X and read and written for
+ *            the G^T update, its interface copy written and read)
  *   GRAM     Gram matrix, rank-revealing factorization and F-orthonormal transform
  *            (Algorithm 1; flops n_lambda m (m + 1) + 2 n_lambda k (k + 1))
  *   STEP     step length, multiplier and residual update, residual norm (bytes)

@@ -34,6 +34,13 @@ Readings:
   and the fluctuations keep the pair-wise rows of B_r; the recovered u^ is
   mapped back by T.  The k-scaling weights use the diagonal of the
   untransformed K^s.
+* Adaptive selection (primal="adaptive"; the paper names adaptive primal sets
+  as future work, Section 5, without a rule): an edge of the "edges" reading
+  gets its average in component d only where the stiffness jumps across it,
+  i.e. where on some interior node of the edge the sharers' diagonal stiffness
+  entries K^s_dd (the quantities k-scaling weighs) differ by a factor of at
+  least ``jump_ratio`` (default 10).  Edges inside homogeneous material keep
+  corners only; an edge where a stiff region meets a compliant one is averaged.
 * The printed fbar_c carries the index "kk" on K^{-1}; it is read as K_rr.
 * Fixed (Dirichlet) DOFs are eliminated from K^s; FETI-DP has no c-vector.
 * K_rr^{-1} is only ever needed on the DOFs that B_r touches (the "b" DOFs)
@@ -44,7 +51,9 @@ Pins: tests/test_oracle_dual.py (the blocks of Eq. 12 against the dense Eq. 11
 and global inverses, module deduplication exact, the direct solution),
 tests/test_oracle_precond.py (the three preconditioner blocks),
 tests/test_oracle_edges.py (the edge-average reading: direct solution,
-closed-form sizes, the primal value is the edge mean on every sharer).
+closed-form sizes, the primal value is the edge mean on every sharer; the
+adaptive selection: its limits equal corners and all edges, direct solution,
+fewer iterations than corners where the laminae meet the interfaces).
 """
 import hashlib
 
@@ -92,7 +101,18 @@ class _Module:
                 del self.Kbb
 
 
-PRIMALS = ("corners", "edges")
+PRIMALS = ("corners", "edges", "adaptive")
+
+
+def edge_stiffness_jump(mesh, dim, diagK, nodes, d):
+    """The stiffness jump across an edge in component d: the largest, over the
+    edge's interior nodes, ratio between the sharers' diagonal stiffness entries
+    K^s_dd of that node (the quantities k-scaling weighs, Eq. 15)."""
+    jump = 1.0
+    for gn in nodes:
+        vals = [diagK[s][ln * dim + d] for (s, ln) in mesh.owners[gn]]
+        jump = max(jump, max(vals) / min(vals))
+    return jump
 
 
 def edge_averages(problem, mesh):
@@ -123,7 +143,7 @@ def edge_averages(problem, mesh):
 
 class FETIDP:
     def __init__(self, problem, scaling="k", dedup=True, precond="dirichlet", primal="corners",
-                 operator_only=False):
+                 operator_only=False, jump_ratio=10.0):
         """``operator_only``: build the blocks of the dual operator, the coarse
         matrix and the preconditioner only (no right-hand sides, no recovery),
         releasing each module's factor after use -- for operator-level checks at
@@ -148,8 +168,15 @@ class FETIDP:
             for d in range(dim):
                 if not problem.dirichlet[gn * dim + d]:
                     self.primal[gn * dim + d] = len(self.primal)
+        # the untransformed local stiffness (its diagonal gives the k-scaling weights
+        # and the adaptive selection's stiffness jumps)
+        Ks_raw = [local_stiffness(problem, mesh, s, k0, E) for s in range(ns)]
+        self.diagK = [np.diag(K).copy() for K in Ks_raw]
         # edge averages: the primal unknown sits in the slot of the first edge node
-        self.edges = edge_averages(problem, mesh) if primal == "edges" else []
+        self.edges = edge_averages(problem, mesh) if primal in ("edges", "adaptive") else []
+        if primal == "adaptive":
+            self.edges = [(nodes, d) for nodes, d in self.edges
+                          if edge_stiffness_jump(mesh, dim, self.diagK, nodes, d) >= jump_ratio]
         avg_dofs = set()
         for nodes, d in self.edges:
             self.primal[nodes[0] * dim + d] = len(self.primal)
@@ -158,19 +185,18 @@ class FETIDP:
         # --- per-subdomain split (Eq. 8) ---
         self.r_loc, self.c_loc, self.c_glob = [], [], []
         self.f_r, self.f_c = [], []
-        self.diagK = []
         self.mod_key = []
         self.modules = {}
         Ks_cache = {}
         self.T = []
         for s in range(ns):
-            Ks = local_stiffness(problem, mesh, s, k0, E)
+            Ks = Ks_raw[s]
+            Ks_raw[s] = None
             fs = local_load(problem, mesh, s)
             fixed = local_dirichlet(problem, mesh, s)
             g2 = mesh.local_to_global_nodes(s)
             is_corner = np.repeat(np.array([mesh.is_tile_vertex(g) for g in g2]), dim)
             gdofs = (g2[:, None] * dim + np.arange(dim)[None, :]).ravel()
-            self.diagK.append(np.diag(Ks).copy())          # weights from the untransformed K^s
             Ts = None
             if self.edges:
                 loc_of = {int(g): ln for ln, g in enumerate(g2)}

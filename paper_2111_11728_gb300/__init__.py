@@ -23,7 +23,7 @@ FETI_SCALING_K, FETI_SCALING_MULT = 0, 1
 FETI_PCG, FETI_FO, FETI_RRS = 0, 1, 2
 FETI_FP64, FETI_TF32, FETI_TF32X3, FETI_BF16, FETI_BF16X3 = 0, 1, 2, 3, 4
 FETI_PRECOND_DIRICHLET, FETI_PRECOND_LUMPED, FETI_PRECOND_SUPERLUMPED = 0, 1, 2
-FETI_PRIMAL_CORNERS, FETI_PRIMAL_EDGES = 0, 1
+FETI_PRIMAL_CORNERS, FETI_PRIMAL_EDGES, FETI_PRIMAL_ADAPTIVE = 0, 1, 2
 (FETI_Q_N_LAMBDA, FETI_Q_N_SUBDOMAINS, FETI_Q_N_PRIMAL, FETI_Q_N_MODULES, FETI_Q_N_B_TOTAL, FETI_Q_N_DOFS,
  FETI_Q_N_ELEMENTS, FETI_Q_MAX_NB, FETI_Q_DEVICE_BYTES, FETI_Q_N_RBM, FETI_Q_LAUNCHES, FETI_Q_N_PROBLEMS,
  FETI_Q_GEMV_CONFIG, FETI_Q_TC_BYTES_F, FETI_Q_TC_BYTES_PER_COL, FETI_Q_APPLY1_BYTES) = range(16)
@@ -33,10 +33,10 @@ STATUS_NAMES = {0: "FETI_OK", 1: "FETI_EINVAL", 2: "FETI_ENOMEM", 3: "FETI_ESTAT
                 8: "FETI_ETIMEOUT"}
 
 EXPORTS = [
-    "feti_options_default", "feti_create", "feti_setup_subdomains", "feti_setup_batch", "feti_problem_result",
+    "feti_options_default", "feti_create", "feti_set_allocator", "feti_setup_subdomains", "feti_setup_batch", "feti_problem_result",
     "feti_set_density", "feti_factorize",
     "feti_solve_dual", "feti_recover_displacements", "feti_compliance_grad", "feti_apply_dual",
-    "feti_apply_precond", "feti_apply_precond_noalloc", "feti_query", "feti_profile_begin", "feti_profile_end", "feti_profile_tensor", "feti_profile_phases", "feti_lambda_layout", "feti_local_blocks", "feti_last_error",
+    "feti_apply_precond", "feti_apply_precond_noalloc", "feti_test_skip_copy", "feti_query", "feti_profile_begin", "feti_profile_end", "feti_profile_tensor", "feti_profile_phases", "feti_lambda_layout", "feti_local_blocks", "feti_last_error",
     "feti_destroy",
 ]
 
@@ -45,8 +45,8 @@ class feti_options(ctypes.Structure):
     _fields_ = [("method", ctypes.c_int), ("scaling", ctypes.c_int), ("krylov", ctypes.c_int),
                 ("precision", ctypes.c_int), ("max_iter", ctypes.c_int), ("dedup_modules", ctypes.c_int),
                 ("tol", ctypes.c_double), ("rr_tol", ctypes.c_double), ("inner_tol", ctypes.c_double),
-                ("max_refine", ctypes.c_int), ("precond", ctypes.c_int), ("fp64_residual", ctypes.c_int),
-                ("primal", ctypes.c_int)]
+                ("max_refine", ctypes.c_int), ("precond", ctypes.c_int),
+                ("primal", ctypes.c_int), ("primal_jump", ctypes.c_double)]
 
 
 class feti_problem(ctypes.Structure):
@@ -54,6 +54,14 @@ class feti_problem(ctypes.Structure):
                 ("E0", ctypes.c_double), ("Emin", ctypes.c_double), ("nu", ctypes.c_double),
                 ("p", ctypes.c_double), ("rho", ctypes.c_void_p), ("dirichlet", ctypes.c_void_p),
                 ("f", ctypes.c_void_p), ("on_device", ctypes.c_int)]
+
+
+ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p)
+FREE_FN = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p)
+
+
+class feti_allocator(ctypes.Structure):
+    _fields_ = [("alloc", ALLOC_FN), ("free", FREE_FN), ("user", ctypes.c_void_p)]
 
 
 class feti_stats(ctypes.Structure):
@@ -76,6 +84,7 @@ def lib():
         sig = {
             "feti_options_default": ([ctypes.POINTER(feti_options)], i),
             "feti_create": ([ctypes.POINTER(vp), ctypes.POINTER(feti_options), vp], i),
+            "feti_set_allocator": ([vp, ctypes.POINTER(feti_allocator)], i),
             "feti_setup_subdomains": ([vp, ctypes.POINTER(feti_problem)], i),
             "feti_setup_batch": ([vp, ctypes.POINTER(feti_problem), i], i),
             "feti_problem_result": ([vp, i, ctypes.POINTER(i64), ctypes.POINTER(i64), ctypes.POINTER(i64),
@@ -88,6 +97,7 @@ def lib():
             "feti_apply_dual": ([vp, vp, i, i, vp, i], i),
             "feti_apply_precond": ([vp, vp, vp, i, vp], i),
             "feti_apply_precond_noalloc": ([vp, vp, vp, i, vp], i),
+            "feti_test_skip_copy": ([vp, i], i),
             "feti_query": ([vp, i, ctypes.POINTER(i64)], i),
             "feti_profile_begin": ([vp], i),
             "feti_profile_end": ([vp, ctypes.POINTER(d), ctypes.POINTER(d), ctypes.POINTER(i64)], i),
@@ -168,6 +178,48 @@ def make_problem(dim, tiles, elems, E0, Emin, nu, p, rho, dirichlet, f, on_devic
     return pr
 
 
+class TorchAllocator:
+    """A feti_allocator backed by PyTorch's caching allocator (device memory of
+    the current CUDA device, on the stream the library passes).  Counts the
+    allocations and the bytes still held, for tests.  Keep the object alive as
+    long as any context that uses it."""
+
+    def __init__(self):
+        import torch
+        self._torch = torch
+        self.live = {}
+        self.n_alloc = 0
+        self.n_free = 0
+
+        def _alloc(user, nbytes, stream):
+            try:
+                ptr = self._torch.cuda.caching_allocator_alloc(int(nbytes), stream=int(stream or 0))
+            except Exception:            # out of memory: the library reports FETI_ENOMEM
+                return None
+            self.live[ptr] = int(nbytes)
+            self.n_alloc += 1
+            return ptr
+
+        def _free(user, ptr, nbytes, stream):
+            self._torch.cuda.caching_allocator_delete(ptr)
+            self.live.pop(ptr, None)
+            self.n_free += 1
+
+        self._cb_alloc = ALLOC_FN(_alloc)
+        self._cb_free = FREE_FN(_free)
+        self.struct = feti_allocator(self._cb_alloc, self._cb_free, None)
+
+    @property
+    def bytes_held(self):
+        return sum(self.live.values())
+
+
+def feti_set_allocator(ctx, allocator):
+    """allocator: a TorchAllocator (or any object with a feti_allocator ``struct``), or None."""
+    ptr = ctypes.byref(allocator.struct) if allocator is not None else None
+    _check(ctx, lib().feti_set_allocator(ctx, ptr))
+
+
 def feti_setup_subdomains(ctx, problem):
     return _check(ctx, lib().feti_setup_subdomains(ctx, ctypes.byref(problem)))
 
@@ -223,6 +275,10 @@ def feti_apply_precond(ctx, r, Z, ldz, z):
 
 def feti_apply_precond_noalloc(ctx, r, Z, ldz, z):
     return _check(ctx, lib().feti_apply_precond_noalloc(ctx, _ptr(r), _ptr(Z), int(ldz), _ptr(z)))
+
+
+def feti_test_skip_copy(ctx, chunk):
+    _check(ctx, lib().feti_test_skip_copy(ctx, int(chunk)))
 
 
 def feti_query(ctx, key):
@@ -294,17 +350,21 @@ class Solver:
     """
 
     def __init__(self, method=FETI_FETIDP, scaling=FETI_SCALING_K, krylov=FETI_RRS, tol=1e-6, max_iter=500,
-                 rr_tol=1e-10, dedup=True, stream=None, precision=FETI_FP64, inner_tol=None, fp64_residual=False,
-                 precond=FETI_PRECOND_DIRICHLET, primal=FETI_PRIMAL_CORNERS):
+                 rr_tol=1e-10, dedup=True, stream=None, precision=FETI_FP64, inner_tol=None,
+                 precond=FETI_PRECOND_DIRICHLET, primal=FETI_PRIMAL_CORNERS, allocator=None, primal_jump=None):
         o = feti_options_default()
         o.method, o.scaling, o.krylov, o.precision = method, scaling, krylov, precision
         o.precond = precond
         o.primal = primal
+        if primal_jump is not None:
+            o.primal_jump = primal_jump
         if inner_tol is not None:
             o.inner_tol = inner_tol
-        o.fp64_residual = int(bool(fp64_residual))
         o.tol, o.max_iter, o.rr_tol, o.dedup_modules = tol, max_iter, rr_tol, int(dedup)
         self.ctx = feti_create(o, stream)
+        self.allocator = allocator
+        if allocator is not None:
+            feti_set_allocator(self.ctx, allocator)
 
     def setup(self, problem, rho=None, dirichlet=None, f=None, on_device=False):
         rho = problem.rho if rho is None else rho

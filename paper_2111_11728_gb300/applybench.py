@@ -76,6 +76,12 @@ def main(argv=None):
            "apply_ms_min": min(times), "f_applies_per_s": a.m / (statistics.median(times) / 1e3)}
     if tn:
         out["tensor_product"] = {"launches": tn, "ms_per_launch": tms / tn, "alg_tflops": tf / (tms / 1e3) / 1e12}
+        # the whole apply against the HBM roofline: the scaled local blocks read once,
+        # the FP32 interface vectors in and out, the FP64 multiplier block in and out
+        nbytes = (s.query(fg.FETI_Q_TC_BYTES_F) + 2.0 * 4 * s.query(fg.FETI_Q_N_B_TOTAL) * a.m
+                  + 2.0 * 8 * n * a.m)
+        out["apply_hbm"] = {"algorithmic_bytes": nbytes,
+                            "achieved_gbs": nbytes / (statistics.median(times) / 1e3) / 1e9}
     if gn:
         out["fp64_gemm"] = {"launches": gn, "ms": gms / a.reps, "alg_tflops": gf / (gms / 1e3) / 1e12}
     s.close()

@@ -18,6 +18,29 @@ struct feti_ctx {
   Ctx c;
 };
 
+namespace feti {
+
+cudaError_t dev_alloc(Ctx& c, void** p, size_t bytes) {
+  *p = nullptr;
+  if (c.have_user_alloc) {
+    *p = c.user_alloc.alloc(c.user_alloc.user, bytes, static_cast<void*>(c.stream));
+    return *p ? cudaSuccess : cudaErrorMemoryAllocation;
+  }
+  cudaError_t e = cudaMallocAsync(p, bytes, c.stream);
+  if (e != cudaSuccess) return e;
+  // ordered on the context stream; synchronised so that host-side copies made
+  // right after the allocation (set-up uploads) may use it too
+  return cudaStreamSynchronize(c.stream);
+}
+
+void dev_free(Ctx& c, void* p, size_t bytes) {
+  if (!p) return;
+  if (c.have_user_alloc) c.user_alloc.free(c.user_alloc.user, p, bytes, static_cast<void*>(c.stream));
+  else cudaFreeAsync(p, c.stream);
+}
+
+}  // namespace feti
+
 namespace {
 
 #define TRY(expr)                              \
@@ -32,13 +55,14 @@ feti_status dalloc(Ctx& c, T*& p, size_t n) {
   p = nullptr;
   if (n == 0) n = 1;
   void* q = nullptr;
-  cudaError_t e = cudaMalloc(&q, n * sizeof(T));
+  cudaError_t e = dev_alloc(c, &q, n * sizeof(T));
   if (e != cudaSuccess) {
     cudaGetLastError();
     c.err = "device allocation of " + std::to_string(n * sizeof(T)) + " bytes failed: " + cudaGetErrorString(e);
     return FETI_ENOMEM;
   }
   c.allocs.push_back(q);
+  c.alloc_bytes.push_back(n * sizeof(T));
   c.device_bytes += n * sizeof(T);
   p = static_cast<T*>(q);
   return FETI_OK;
@@ -61,8 +85,10 @@ feti_status upload(Ctx& c, T*& p, const std::vector<T>& v) {
 }
 
 void free_all(Ctx& c) {
-  for (void* p : c.allocs) cudaFree(p);
+  cudaStreamSynchronize(c.stream);        // nothing in flight uses the memory any more
+  for (size_t i = 0; i < c.allocs.size(); ++i) dev_free(c, c.allocs[i], c.alloc_bytes[i]);
   c.allocs.clear();
+  c.alloc_bytes.clear();
   c.device_bytes = 0;
   c.hist_W.clear();
   c.hist_Q.clear();
@@ -71,15 +97,18 @@ void free_all(Ctx& c) {
   c.kr_cap = 0;
   c.split_cap = 0;
   c.xb_cap = 0;
-  if (c.d_tiles) cudaFree(c.d_tiles);
+  if (c.d_tiles) dev_free(c, c.d_tiles, (size_t)c.tiles_cap * sizeof(int4));
   c.d_tiles = nullptr;
   c.tiles_cap = 0;
+  cudaStreamSynchronize(c.stream);
+  cudaGetLastError();
   c.n_tiles = 0;
   c.tiles_ncb = 0;
 }
 
 inline int64_t align32(int64_t x) { return (x + 31) / 32 * 32; }
 
+constexpr int kGgtCols = 64;           // coarse columns per block when G G^T is formed (TFETI)
 constexpr int BATCH_CHUNK = 128;        // columns per dual-operator apply in the batched Algorithm 1
 constexpr int64_t BATCH_KCHUNK = 8192;  // rows per split-K chunk of its Gram products
 constexpr int64_t BATCH_RCHUNK = 4096;  // rows per entry of its block updates
@@ -228,20 +257,17 @@ feti_status gemm_nn(Ctx& c, const double* A, int64_t lda, const double* B, int64
 }
 
 // TFETI projector P X = X - G^T (G G^T)^{-1} G X, X column-major [n_lam x m].
+// G = -R^T B^T is never read as a dense matrix here: G X is a per-subdomain
+// reduction of the gathered block B^T X against the rigid modes at the
+// interface, G^T t a per-multiplier combination of the modes at the row's
+// two entries -- O(n_lambda m) traffic instead of O(n_coarse n_lambda).
 feti_status project(Ctx& c, double* X, int64_t ldx, int m) {
   if (c.hp.method != FETI_TFETI) return FETI_OK;
   TRY(ensure_blocks(c, m));
   const int nco = c.n_coarse;
-  const int64_t nl = c.hp.n_lam;
-  // t1 = G X  (G row-major nco x nl)
-  {
-    GemmDesc d{};
-    d.A = c.d_G; d.B = X; d.C = c.d_ct1; d.M = nco; d.N = m; d.K = (int)nl;
-    d.ars = nl; d.acs = 1; d.brs = 1; d.bcs = ldx; d.crs = 1; d.ccs = nco;
-    const int splits = split_for(nco, m, (int)nl);
-    if (splits > 1) TRY(ensure_split(c, (int64_t)splits * nco * m));
-    CU(dgemm_split(d, splits, c.d_split, 1.0, 0.0, c.stream));
-  }
+  // t1 = G X
+  CU(gather_lam_to_b(c, X, ldx, m, c.d_Xb, c.stream));
+  CU(tfeti_G_apply(c, c.d_Xb, m, c.d_ct1, c.stream));
   // t2 = (G G^T)^{-1} t1
   {
     GemmDesc d{};
@@ -250,12 +276,7 @@ feti_status project(Ctx& c, double* X, int64_t ldx, int m) {
     CU(dgemm_split(d, 1, nullptr, 1.0, 0.0, c.stream));
   }
   // X -= G^T t2
-  {
-    GemmDesc d{};
-    d.A = c.d_G; d.B = c.d_ct2; d.C = X; d.M = (int)nl; d.N = m; d.K = nco;
-    d.ars = 1; d.acs = nl; d.brs = 1; d.bcs = nco; d.crs = 1; d.ccs = ldx;
-    CU(dgemm_split(d, 1, nullptr, -1.0, 1.0, c.stream));
-  }
+  CU(tfeti_Gt_sub(c, c.d_ct2, m, X, ldx, c.stream));
   return FETI_OK;
 }
 
@@ -298,20 +319,26 @@ feti_status apply_dual(Ctx& c, const double* X, int64_t ldx, int m, double* Y, i
   return FETI_OK;
 }
 
-// Y = F X with the local blocks on the tensor cores (TF32 inputs, FP32
-// accumulation); the thin corner coupling and the coarse solve stay FP64.
+// Y = F X with the local blocks on the tensor cores (TF32 / BF16 inputs,
+// FP32 accumulation).  The corner reduction F_rc^T X and the coarse
+// correction Kbar_cc^{-1} (F_rc^T X) of a block are FP32 products too (the
+// coarse matrix is factorized and inverted in FP64 at feti_factorize; only
+// its application is rounded, like the local blocks').
 feti_status apply_dual_lowp(Ctx& c, const double* X, int64_t ldx, int m, double* Y, int64_t ldy) {
   TRY(ensure_blocks(c, m));
   CU(tc_gather(c, X, ldx, m, c.stream));
   if (c.tc_aug) {
-    // corner reduction (FP32), coarse solve (FP64), then the coarse
-    // correction rides in the K-extension of the one tensor-core product
+    // corner reduction, coarse solve, then the coarse correction rides in
+    // the K-extension of the one tensor-core product
     CU(tc_corner_reduce(c, m, c.d_Vraw, c.stream));
-    CU(coarse_apply(c, c.d_Vraw, c.d_V, m, c.stream));
+    if (m > 1 && c.d_Kbar_inv32) CU(tc_coarse_apply(c, c.d_Vraw, c.d_V, m, c.stream));
+    else CU(coarse_apply(c, c.d_Vraw, c.d_V, m, c.stream));
     CU(tc_put_v(c, c.d_V, m, c.stream));
   }
   CU(tc_prepare_tiles(c, m));
-  CU(tc_product(c, m, c.d_Yb32, c.stream));
+  const cudaError_t pe = tc_product(c, m, c.d_Yb32, c.stream);
+  c.test_skip_chunk = -1;                          // the test hook acts on one product only
+  CU(pe);
   CU(scatter_b_to_lam32(c, c.d_Yb32, m, Y, ldy, c.stream));
   return FETI_OK;
 }
@@ -389,9 +416,9 @@ feti_status feti_options_default(feti_options* opt) {
   opt->rr_tol = 1e-10;
   opt->inner_tol = 0.0;                 // automatic (1e-2)
   opt->max_refine = 30;
-  opt->fp64_residual = 0;
   opt->precond = FETI_PRECOND_DIRICHLET;
   opt->primal = FETI_PRIMAL_CORNERS;
+  opt->primal_jump = 10.0;
   return FETI_OK;
 }
 
@@ -407,11 +434,12 @@ feti_status feti_create(feti_ctx** out, const feti_options* opt, void* stream) {
     return FETI_EINVAL;
   if (o.precision < FETI_FP64 || o.precision > FETI_BF16X3) return FETI_EINVAL;
   if (o.precision != FETI_FP64 && !(o.inner_tol >= 0.0 && o.inner_tol < 1.0 && o.max_refine > 0)) return FETI_EINVAL;
-  if (o.fp64_residual != 0 && o.fp64_residual != 1) return FETI_EINVAL;
   if (o.precond < FETI_PRECOND_DIRICHLET || o.precond > FETI_PRECOND_SUPERLUMPED) return FETI_EINVAL;
-  if (o.primal != FETI_PRIMAL_CORNERS && o.primal != FETI_PRIMAL_EDGES) return FETI_EINVAL;
-  if (o.primal == FETI_PRIMAL_EDGES && o.method != FETI_FETIDP) return FETI_EINVAL;
-  if (o.primal == FETI_PRIMAL_EDGES && o.precond != FETI_PRECOND_DIRICHLET) return FETI_ENOTSUP;
+  if (o.primal != FETI_PRIMAL_CORNERS && o.primal != FETI_PRIMAL_EDGES && o.primal != FETI_PRIMAL_ADAPTIVE)
+    return FETI_EINVAL;
+  if (o.primal != FETI_PRIMAL_CORNERS && o.method != FETI_FETIDP) return FETI_EINVAL;
+  if (o.primal != FETI_PRIMAL_CORNERS && o.precond != FETI_PRECOND_DIRICHLET) return FETI_ENOTSUP;
+  if (o.primal == FETI_PRIMAL_ADAPTIVE && !(o.primal_jump >= 1.0)) return FETI_EINVAL;
   feti_ctx* ctx = new (std::nothrow) feti_ctx;
   if (!ctx) return FETI_ENOMEM;
   Ctx& c = ctx->c;
@@ -437,6 +465,28 @@ void feti_destroy(feti_ctx* ctx) {
 
 const char* feti_last_error(const feti_ctx* ctx) { return ctx ? ctx->c.err.c_str() : "null context"; }
 
+feti_status feti_set_allocator(feti_ctx* ctx, const feti_allocator* a) {
+  if (!ctx) return FETI_EINVAL;
+  Ctx& c = ctx->c;
+  c.err.clear();
+  if (!c.allocs.empty() || c.d_tiles) {
+    c.err = "feti_set_allocator: the context already holds device memory (install the allocator before set-up)";
+    return FETI_ESTATE;
+  }
+  if (!a) {
+    c.have_user_alloc = 0;
+    c.user_alloc = feti_allocator{};
+    return FETI_OK;
+  }
+  if (!a->alloc || !a->free) {
+    c.err = "feti_set_allocator: null callback";
+    return FETI_EINVAL;
+  }
+  c.user_alloc = *a;
+  c.have_user_alloc = 1;
+  return FETI_OK;
+}
+
 }  // extern "C"
 
 // Set-up of one problem or of a batch of independent problems (merged into
@@ -453,7 +503,16 @@ static feti_status setup_impl(Ctx& c, const feti_problem* probs, int n) {
   free_all(c);
   if (c.cap_stream) { cudaStreamDestroy(c.cap_stream); c.cap_stream = nullptr; }
   if (c.cap_event) { cudaEventDestroy(c.cap_event); c.cap_event = nullptr; }
-  c = Ctx{c.opt, c.stream, std::string(), 0, c.device, HostProblem(), {}, 0, c.h_pin};
+  {
+    Ctx fresh;
+    fresh.opt = c.opt;
+    fresh.stream = c.stream;
+    fresh.device = c.device;
+    fresh.h_pin = c.h_pin;
+    fresh.user_alloc = c.user_alloc;
+    fresh.have_user_alloc = c.have_user_alloc;
+    c = std::move(fresh);
+  }
   std::vector<HostProblem> parts(n);
   std::vector<double> rho_all;
   for (int q = 0; q < n; ++q) {
@@ -467,7 +526,7 @@ static feti_status setup_impl(Ctx& c, const feti_problem* probs, int n) {
     for (double r : rho_h)
       if (!(r >= 0.0 && r <= 1.0)) { c.err = "densities must lie in [0, 1]"; return FETI_EINVAL; }
     std::string msg = build_host_problem(*prob, c.opt.method, c.opt.dedup_modules, rho_h.data(), parts[q],
-                                         c.opt.primal == FETI_PRIMAL_EDGES);
+                                         c.opt.primal, c.opt.primal_jump);
     if (!msg.empty()) { c.err = (n > 1 ? "problem " + std::to_string(q) + ": " : std::string()) + msg; return FETI_EINVAL; }
     rho_all.insert(rho_all.end(), rho_h.begin(), rho_h.end());
   }
@@ -660,6 +719,8 @@ static feti_status setup_impl(Ctx& c, const feti_problem* probs, int n) {
   TRY(dalloc(c, c.d_Kbar, kb_len));
   TRY(dalloc(c, c.d_Kbar_L, kb_len));
   TRY(dalloc(c, c.d_Kbar_inv, kb_len));
+  if (c.opt.precision != FETI_FP64 && hp.method == FETI_FETIDP && hp.n_prob == 1 && hp.n_primal > 0)
+    TRY(dalloc(c, c.d_Kbar_inv32, kb_len));
   TRY(upload(c, c.d_kbar_off, c.h_kbar_off));
   TRY(upload(c, c.d_row_prob, row_prob));
   TRY(upload(c, c.d_prob_el_off, hp.prob_el_off));
@@ -676,7 +737,7 @@ static feti_status setup_impl(Ctx& c, const feti_problem* probs, int n) {
   TRY(dalloc(c, c.d_fbar, std::max(hp.n_primal, 1)));
   TRY(dalloc(c, c.d_coarse_work, (size_t)128 * nco + (size_t)((nco + 63) / 64) * 4096));
   if (hp.method == FETI_TFETI) {
-    TRY(dalloc(c, c.d_G, (size_t)nco * nl));
+    TRY(dalloc(c, c.d_gwork, (size_t)kGgtCols * nl));
     TRY(dalloc(c, c.d_e, nco));
     TRY(dalloc(c, c.d_alpha, nco));
   }
@@ -905,6 +966,7 @@ feti_status feti_factorize(feti_ctx* ctx) {
     // coarse matrix Kbar_cc (Eq. 12) and its inverse
     CU(coarse_assemble_batch(c, st));
     CU(coarse_inverse(c));
+    if (c.d_Kbar_inv32) CU(tc_coarse_prepare(c, st));
     // fbar_c = sum_s B_c^sT (f~_c - F_rc,s^T f~_b)
     CU(cudaMemcpyAsync(c.d_Xb, c.d_ft, nbt * sizeof(double), cudaMemcpyDeviceToDevice, st));
     CU(corner_reduce(c, c.d_Xb, 1, c.d_Cb, c.d_Vraw, st));
@@ -917,14 +979,17 @@ feti_status feti_factorize(feti_ctx* ctx) {
     CU(scatter_b_to_lam(c, c.d_Yb, 1, c.d_lam, nl, st));
     CU(axpby(nl, -1.0, c.d_lam, 1.0, c.d_d, st));
   } else {
-    // TFETI coarse space: G = -R^T B^T, G G^T, e = -R^T f, lambda_0 = G^T (G G^T)^{-1} e
+    // TFETI coarse space: G = -R^T B^T (applied, never stored), G G^T, e = -R^T f,
+    // lambda_0 = G^T (G G^T)^{-1} e
     const int nco = c.n_coarse;
-    CU(tfeti_build_G(c, c.d_G, st));
-    TRY(gemm_tn(c, c.d_G, nl, c.d_G, nl, c.d_Kbar, nco, nco, nco, (int)nl, 1.0, 0.0));
+    TRY(ensure_blocks(c, kGgtCols));
+    CU(tfeti_ggt(c, c.d_gwork, kGgtCols, c.d_ct1, c.d_ct2, c.d_Xb, c.d_Kbar, st));
     CU(coarse_inverse(c));
     CU(tfeti_build_e(c, c.d_e, st));
     CU(gemv_dense(c.d_Kbar_inv, nco, nco, c.d_e, c.d_alpha, 0.0, st));
-    TRY(gemm_nn(c, c.d_G, nl, c.d_alpha, nco, c.d_lam0, nl, (int)nl, 1, nco, 1.0, 0.0));
+    // lambda_0 = G^T alpha: the G^T kernel subtracts, so from 0 it leaves -G^T alpha
+    CU(tfeti_Gt_sub(c, c.d_alpha, 1, c.d_lam0, nl, st));
+    CU(axpby(nl, -1.0, c.d_lam0, 0.0, c.d_lam0, st));
   }
   TRY(sync_check(c));
   TRY(check_status(c, "coarse factorization"));
@@ -963,10 +1028,7 @@ static feti_status read_scalar(Ctx& c, const double* d, double* out) {
 // leaves lambda~ in c.d_lamt and the final residual in c.d_r.  lowp selects
 // the tensor-core local products and the FP32 preconditioner blocks.
 // eps_ref > 0 replaces the initial residual norm in the relative stopping test.
-// r_base != NULL (reduced precision): after every step the residual is
-// recomputed in FP64 as r_base - P^T F lambda~ instead of updated recursively.
-static feti_status krylov_core(Ctx& c, double tol, int max_iter, bool lowp, feti_stats& S, double eps_ref = -1.0,
-                               const double* r_base = nullptr) {
+static feti_status krylov_core(Ctx& c, double tol, int max_iter, bool lowp, feti_stats& S, double eps_ref = -1.0) {
   const HostProblem& hp = c.hp;
   const int64_t nl = hp.n_lam;
   const bool multi = c.opt.krylov == FETI_RRS;
@@ -984,7 +1046,7 @@ static feti_status krylov_core(Ctx& c, double tol, int max_iter, bool lowp, feti
   };
   auto projectW = [&]() -> feti_status {
     if (hp.method != FETI_TFETI) return FETI_OK;
-    PhaseScope ph(st, FETI_PHASE_PROJECT, 8.0 * (2.0 * c.n_coarse * (double)nl + 2.0 * (double)nl * m));
+    PhaseScope ph(st, FETI_PHASE_PROJECT, 8.0 * (3.0 * (double)nl * m + 2.0 * (double)hp.n_b_total * m));
     return project(c, c.d_Wb, nl, m);
   };
   // Z_0, W_0 = P Z_0
@@ -1045,14 +1107,6 @@ static feti_status krylov_core(Ctx& c, double tol, int max_iter, bool lowp, feti
         CU(step_update(Wi, Qi, nl, nl, k, c.d_gamma, c.d_lamt, c.d_r, nullptr, st));
       }
     }
-    if (r_base) {
-      // FP64 residual replacement: r = r_base - P^T F lambda~
-      TRY(apply_dual(c, c.d_lamt, nl, 1, c.d_z, nl));
-      TRY(project(c, c.d_z, nl, 1));
-      CU(cudaMemcpyAsync(c.d_r, r_base, nl * sizeof(double), cudaMemcpyDeviceToDevice, st));
-      CU(axpby(nl, -1.0, c.d_z, 1.0, c.d_r, st));
-      S.f_applies += 1;
-    }
     // Z_{i+1}, W_{i+1} = P Z_{i+1}
     CU(precond(multi ? c.d_Wb : nullptr, c.d_z));
     if (!multi) CU(cudaMemcpyAsync(c.d_Wb, c.d_z, nl * sizeof(double), cudaMemcpyDeviceToDevice, st));
@@ -1064,8 +1118,11 @@ static feti_status krylov_core(Ctx& c, double tol, int max_iter, bool lowp, feti
       PhaseScope ph(st, FETI_PHASE_ORTHO, fl_o);
       for (int j = full ? 0 : it; j <= it; ++j) {
         const int kj = c.hist_k[j];
+        // Psi_j = Q_j^T W (FP64 inner products), then W -= W_j Psi_j: FP64, or
+        // inside a reduced-precision inner solve an FP32 block update
         TRY(gemm_tn(c, c.hist_Q[j], nl, c.d_Wb, nl, c.d_Delta, kj, kj, m, (int)nl, 1.0, 0.0));
-        TRY(gemm_nn(c, c.hist_W[j], nl, c.d_Delta, kj, c.d_Wb, nl, (int)nl, m, kj, -1.0, 1.0));
+        if (lowp && m > 1) CU(sgemm_sub(nl, m, kj, c.hist_W[j], nl, c.d_Delta, kj, c.d_Wb, nl, st));
+        else TRY(gemm_nn(c, c.hist_W[j], nl, c.d_Delta, kj, c.d_Wb, nl, (int)nl, m, kj, -1.0, 1.0));
       }
     }
     {
@@ -1446,7 +1503,8 @@ static feti_status solve_impl(Ctx& c, double* lambda_inout, feti_stats* stats) {
   }
   if (mmax > 1024) { c.err = "more than 1024 subdomains per direction block"; return FETI_ENOTSUP; }
   TRY(ensure_krylov(c, mmax));
-  if (hp.n_prob == 1) TRY(ensure_blocks(c, mmax));
+  // block buffers before any capture (a batch's PCG iteration is recorded as a graph)
+  TRY(ensure_blocks(c, hp.n_prob == 1 ? mmax : 1));
   cudaStream_t st = c.stream;
   feti_stats S{};
   // lambda_0 (warm start or the method's own)
@@ -1529,15 +1587,12 @@ static feti_status solve_impl(Ctx& c, double* lambda_inout, feti_stats* stats) {
       feti_stats inner{};
       // each correction is capped (a stalled reduced-precision solve still
       // returns a useful correction; the FP64 outer loop decides convergence)
-      const bool repl = c.opt.fp64_residual != 0;
-      const int cap = repl ? c.opt.max_iter - S.iterations : std::min(c.opt.max_iter - S.iterations, 30);
+      const int cap = std::min(c.opt.max_iter - S.iterations, 30);
       // automatic inner tolerance: 1e-2 (measured best time-to-solve for both
       // reduced-precision products: each restart costs the orthogonalization
-      // history, so long inner solves lose more than extra restarts).  With the
-      // FP64 residual the inner solve aims straight at the final tolerance.
-      double itol = c.opt.inner_tol > 0.0 ? c.opt.inner_tol : 1e-2;
-      if (repl) itol = std::min(0.5, c.opt.tol * eps0 / std::max(eps, 1e-300));
-      feti_status s2 = krylov_core(c, itol, cap, true, inner, -1.0, repl ? c.d_rout : nullptr);
+      // history, so long inner solves lose more than extra restarts)
+      const double itol = c.opt.inner_tol > 0.0 ? c.opt.inner_tol : 1e-2;
+      feti_status s2 = krylov_core(c, itol, cap, true, inner, -1.0);
       S.iterations += inner.iterations;
       S.f_applies += inner.f_applies;
       S.last_rank = inner.last_rank;
@@ -1602,7 +1657,9 @@ feti_status feti_recover_displacements(feti_ctx* ctx, double* u_out, int on_devi
     TRY(ensure_krylov(c, 1));
     TRY(apply_dual(c, c.d_lam, nl, 1, c.d_r, nl));
     CU(axpby(nl, 1.0, c.d_d, -1.0, c.d_r, st));
-    TRY(gemm_tn(c, c.d_G, nl, c.d_r, nl, c.d_ct1, nco, nco, 1, (int)nl, 1.0, 0.0));
+    TRY(ensure_blocks(c, 1));
+    CU(gather_lam_to_b(c, c.d_r, nl, 1, c.d_Xb, st));
+    CU(tfeti_G_apply(c, c.d_Xb, 1, c.d_ct1, st));
     CU(gemv_dense(c.d_Kbar_inv, nco, nco, c.d_ct1, c.d_alpha, 0.0, st));
     CU(recover_tfeti(c, c.d_lam, c.d_alpha, st));
   }
@@ -1660,8 +1717,11 @@ feti_status feti_apply_dual(feti_ctx* ctx, const double* X, int ldx, int m, doub
   TRY(sync_check(c));
   TRY(check_status(c, "feti_apply_dual"));
   return FETI_OK;
-  TRY(apply_dual(c, X, ldx, m, Y, ldy));
-  TRY(sync_check(c));
+}
+
+feti_status feti_test_skip_copy(feti_ctx* ctx, int chunk) {
+  if (!ctx) return FETI_EINVAL;
+  ctx->c.test_skip_chunk = chunk < 0 ? -1 : chunk;
   return FETI_OK;
 }
 

@@ -153,6 +153,42 @@ __global__ void k_frct(const DevType* __restrict__ types, const DevModule* __res
     if (c < nc) out[c] = acc[c];
 }
 
+// One direction: C_s = F_rc,s^T x_b(s) with one block of 128 threads per
+// subdomain (the rows split across the threads, partial sums reduced in a
+// fixed order): the one-direction variants would otherwise leave a single
+// thread per subdomain walking every row.
+template <int NC>
+__global__ void __launch_bounds__(128) k_frct_one(const DevType* __restrict__ types,
+                                                  const DevModule* __restrict__ mods,
+                                                  const DevSub* __restrict__ subs, const double* __restrict__ mem,
+                                                  const double* __restrict__ Xb, double* __restrict__ Cb) {
+  const DevSub S = subs[blockIdx.x];
+  const DevType T = types[S.type];
+  const int nc = T.n_c, nb = T.n_b;
+  const double* F = mem + mods[S.module].Frc;    // [nb x nc] row-major
+  const double* x = Xb + S.b_off;
+  double acc[NC];
+#pragma unroll
+  for (int c = 0; c < NC; ++c) acc[c] = 0.0;
+  for (int k = threadIdx.x; k < nb; k += blockDim.x) {
+    const double xv = x[k];
+    const double* fr = F + (int64_t)k * nc;
+#pragma unroll
+    for (int c = 0; c < NC; ++c)
+      if (c < nc) acc[c] = fma(fr[c], xv, acc[c]);
+  }
+  __shared__ double red[NC][4];
+#pragma unroll
+  for (int c = 0; c < NC; ++c) {
+    double v = acc[c];
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    if ((threadIdx.x & 31) == 0) red[c][threadIdx.x >> 5] = v;
+  }
+  __syncthreads();
+  if ((int)threadIdx.x < nc)
+    Cb[S.c_off + threadIdx.x] = (red[threadIdx.x][0] + red[threadIdx.x][1]) + (red[threadIdx.x][2] + red[threadIdx.x][3]);
+}
+
 // Vraw[g + j*np] = sum over the corner copies of g of Cb[src + j*nct]
 __global__ void k_corner_gather(int np, int m, const int* __restrict__ poff, const int* __restrict__ psrc,
                                 const double* __restrict__ Cb, int64_t nct, double* __restrict__ V) {
@@ -240,7 +276,12 @@ cudaError_t apply_local_F(Ctx& c, const double* /*Xb*/, double* /*Yb*/, int m, d
 
 cudaError_t corner_reduce(Ctx& c, const double* /*Xb*/, int m, double* /*Cb*/, double* Vraw, cudaStream_t st) {
   cudaError_t e;
-  if (c.max_nc <= 8) {
+  if (m == 1 && c.max_nc <= 24) {
+    if (c.max_nc <= 8) k_frct_one<8><<<c.hp.n_sub, 128, 0, st>>>(c.d_types, c.d_mods, c.d_subs, c.d_modmem, c.d_Xb, c.d_Cb);
+    else k_frct_one<24><<<c.hp.n_sub, 128, 0, st>>>(c.d_types, c.d_mods, c.d_subs, c.d_modmem, c.d_Xb, c.d_Cb);
+    note_launches(1);
+    e = cudaGetLastError();
+  } else if (c.max_nc <= 8) {
     k_frct<8><<<dim3((m + 63) / 64, c.hp.n_sub), 64, 0, st>>>(c.d_types, c.d_mods, c.d_subs, c.d_modmem, c.d_Xb,
                                                              c.hp.n_b_total, m, c.d_Cb, c.n_c_total);
     note_launches(1);
@@ -403,14 +444,12 @@ cudaError_t precond_apply(Ctx& c, const double* r, double* Z, int64_t ldz, doubl
   return precond_apply_cols(c, r, Z, ldz, c.hp.n_sub, c.d_b_sub, z, st);
 }
 
-// The block preconditioner with column bcol[b] of Z for the b-space entry b
-// (the subdomain, or its index inside its problem for a batch) and ncols
-// columns of Z cleared first.
-cudaError_t precond_apply_cols(Ctx& c, const double* r, double* Z, int64_t ldz, int ncols, const int* bcol,
-                               double* z, cudaStream_t st) {
+// The block preconditioner in the work vectors rb, zb ([n_b_total] each, fully
+// overwritten): column bcol[b] of Z for the b-space entry b (the subdomain, or
+// its index inside its problem for a batch), ncols columns of Z cleared first.
+static cudaError_t precond_core(const Ctx& c, const double* r, double* Z, int64_t ldz, int ncols, const int* bcol,
+                                double* z, double* rb, double* zb, cudaStream_t st) {
   const int64_t nbt = c.hp.n_b_total, nl = c.hp.n_lam;
-  double* rb = c.d_pb0;
-  double* zb = c.d_pb1;
   k_gather_weighted<<<(unsigned)((nbt + 255) / 256), 256, 0, st>>>(nbt, c.d_b2l_off, c.d_b2l_lam, c.d_b2l_sign,
                                                                    c.d_lam_b0, c.d_w0, c.d_w1, r, rb);
   note_launches(1);
@@ -428,26 +467,17 @@ cudaError_t precond_apply_cols(Ctx& c, const double* r, double* Z, int64_t ldz, 
   return cudaGetLastError();
 }
 
-// The block preconditioner with caller-provided work vectors rb, zb
-// ([n_b_total] each, fully overwritten); used by the allocation-free entry point.
+// The block preconditioner in the context's own work vectors.
+cudaError_t precond_apply_cols(Ctx& c, const double* r, double* Z, int64_t ldz, int ncols, const int* bcol,
+                               double* z, cudaStream_t st) {
+  return precond_core(c, r, Z, ldz, ncols, bcol, z, c.d_pb0, c.d_pb1, st);
+}
+
+// The block preconditioner (one column per subdomain) with caller-provided
+// work vectors rb, zb; used by the allocation-free entry point.
 cudaError_t precond_apply_scratch(const Ctx& c, const double* r, double* Z, int64_t ldz, double* z, double* rb,
                                   double* zb, cudaStream_t st) {
-  const int64_t nbt = c.hp.n_b_total, nl = c.hp.n_lam;
-  k_gather_weighted<<<(unsigned)((nbt + 255) / 256), 256, 0, st>>>(nbt, c.d_b2l_off, c.d_b2l_lam, c.d_b2l_sign,
-                                                                   c.d_lam_b0, c.d_w0, c.d_w1, r, rb);
-  note_launches(1);
-  cudaError_t e = cudaGetLastError();
-  if (e != cudaSuccess) return e;
-  e = local_precond_block(c, rb, zb, st);
-  if (e != cudaSuccess) return e;
-  if (Z) {
-    e = cudaMemsetAsync(Z, 0, sizeof(double) * (size_t)ldz * c.hp.n_sub, st);
-    if (e != cudaSuccess) return e;
-  }
-  k_prec_scatter<<<(unsigned)((nl + 255) / 256), 256, 0, st>>>(nl, c.d_lam_b0, c.d_lam_s0, c.d_lam_b1, c.d_lam_s1,
-                                                               c.d_w0, c.d_w1, c.d_b_sub, zb, Z, ldz, z);
-  note_launches(1);
-  return cudaGetLastError();
+  return precond_core(c, r, Z, ldz, c.hp.n_sub, c.d_b_sub, z, rb, zb, st);
 }
 
 namespace {

@@ -98,9 +98,12 @@ struct HostProblem {
 // DOFs).  All parts must share dim and method.
 std::string merge_host_problems(std::vector<HostProblem>& parts, HostProblem& out);
 
-// Builds the host description; returns an error message or "".
+// Builds the host description; returns an error message or "".  edge_mode:
+// 0 corners only, 1 every shared tile-grid edge averaged, 2 only the edges
+// across which the sharers' diagonal stiffness jumps by >= jump_ratio.
 std::string build_host_problem(const feti_problem& prob, int method, int dedup,
-                               const double* rho_host, HostProblem& hp, bool edge_averages = false);
+                               const double* rho_host, HostProblem& hp, int edge_mode = 0,
+                               double jump_ratio = 10.0);
 
 // Local node (lexicographic in the tile) -> tile-local integer coordinates.
 inline void local_node_coords(const HostProblem& hp, int ln, int c[3]) {
@@ -175,6 +178,9 @@ struct Ctx {
   int device = 0;
   HostProblem hp;
   std::vector<void*> allocs;     // every device allocation (freed at destroy)
+  std::vector<size_t> alloc_bytes;   // their sizes
+  feti_allocator user_alloc{};   // caller's allocator (feti_set_allocator), if installed
+  int have_user_alloc = 0;
   size_t device_bytes = 0;
   double* h_pin = nullptr;       // pinned host scalars
 
@@ -230,6 +236,7 @@ struct Ctx {
   double* d_Kbar = nullptr;      // [n_coarse^2]
   double* d_Kbar_L = nullptr;    // [n_coarse^2] inverse Cholesky factor (work)
   double* d_Kbar_inv = nullptr;  // [n_coarse^2] explicit inverse
+  float* d_Kbar_inv32 = nullptr; // precision form, one problem: FP32 copy of the inverse
   double* d_coarse_work = nullptr;   // blocked coarse factorisation work
   // precision form (FETI_TF32)
   float* d_fmem = nullptr;       // FP32 copies at the module offsets: Shat at M.W
@@ -247,6 +254,7 @@ struct Ctx {
   int64_t tiles_cap = 0;
   int n_tiles = 0, tiles_ncb = 0, n_sm = 0;
   double fl_tc = 0.0;            // algorithmic flops of the tensor-core product per column
+  int test_skip_chunk = -1;      // test hook: K chunk whose copy the next TF32 product's first tile skips
   int64_t tc_bytes_f = 0;        // algorithmic bytes: scaled blocks (read once per apply)
   int64_t tc_bytes_col = 0;      // algorithmic bytes per column: operand in + FP32 result out
   double prof_tc_flops = 0.0, prof_tc_ms = 0.0;   // tensor-core products of the last profile
@@ -277,7 +285,7 @@ struct Ctx {
   std::vector<double> prob_compliance;
   double* d_fbar = nullptr;      // [n_primal]
   int n_coarse = 0;
-  double* d_G = nullptr;         // TFETI: dense G [n_coarse x n_lam]
+  double* d_gwork = nullptr;     // TFETI: [n_lam x 64] work block for forming G G^T
   double* d_e = nullptr;         // TFETI: e = -R^T f
   double* d_alpha = nullptr;     // TFETI: rigid-body amplitudes
   double *d_ct1 = nullptr, *d_ct2 = nullptr;   // [n_coarse x blk] projector work

@@ -74,23 +74,24 @@ FETI_HD int fpc_clz32(uint32_t v) {
 }
 
 FETI_HD float f64_to_f32_rn(double x) {
+  // Branch-free for FP32-normal results: bits 30..0 of the FP32 pattern are the
+  // FP64 pattern shifted right by 29 (the low 8 exponent bits and the top 23
+  // mantissa bits) with the exponent's top bit flipped (e - 896 = E for the
+  // exponents 897..1150 of the FP32 normals); the 29 dropped mantissa bits round
+  // to nearest, ties to even, a carry moving into the exponent (and to the
+  // infinity pattern past the largest FP32).
   const uint64_t b = fpc_bits64(x);
-  const uint32_t sign = static_cast<uint32_t>(b >> 32) & 0x80000000u;
-  const int e = static_cast<int>((b >> 52) & 0x7FF);
-  const uint64_t mant = b & 0xFFFFFFFFFFFFFull;
-  if (e == 0x7FF) return fpc_from32(sign | 0x7F800000u | (mant ? 0x400000u : 0u));
-  int ef = e - 1023 + 127;
-  if (ef <= 0) return fpc_from32(sign);                          // below FP32 normals: signed zero
-  uint32_t m = static_cast<uint32_t>(mant >> 29);
-  const uint32_t rem = static_cast<uint32_t>(mant & 0x1FFFFFFFull);
-  if (rem > 0x10000000u || (rem == 0x10000000u && (m & 1u))) {
-    if (++m == 0x800000u) {
-      m = 0;
-      ++ef;
-    }
+  const uint32_t hi = static_cast<uint32_t>(b >> 32);
+  const uint32_t sign = hi & 0x80000000u;
+  const uint32_t e = (hi >> 20) & 0x7FFu;
+  uint32_t r = (static_cast<uint32_t>(b >> 29) ^ 0x40000000u) & 0x7FFFFFFFu;
+  const uint32_t rem = static_cast<uint32_t>(b) & 0x1FFFFFFFu;
+  r += (rem + 0x0FFFFFFFu + (r & 1u)) >> 29;
+  if (e - 897u > 253u) {                            // outside the FP32 normal exponents
+    if (e < 897u) r = 0u;                                          // below FP32 normals: signed zero
+    else r = (e == 0x7FFu && (b & 0xFFFFFFFFFFFFFull)) ? 0x7FC00000u : 0x7F800000u;   // NaN; infinity
   }
-  if (ef >= 255) return fpc_from32(sign | 0x7F800000u);           // overflow: signed infinity
-  return fpc_from32(sign | (static_cast<uint32_t>(ef) << 23) | m);
+  return fpc_from32(sign | r);
 }
 
 FETI_HD double f32_to_f64(float x) {

@@ -180,6 +180,15 @@ cudaError_t gemv_t(const double* W, int64_t ld, int64_t n, int k, const double* 
 // y = A x (+ beta y), A row-major n x n with leading dimension ld
 cudaError_t gemv_dense(const double* A, int n, int ld, const double* x, double* y, double beta, cudaStream_t st);
 
+// ---- internal device memory (api.cu): the caller's allocator if installed,
+// otherwise stream-ordered allocation on the context stream
+cudaError_t dev_alloc(Ctx& c, void** p, size_t bytes);
+void dev_free(Ctx& c, void* p, size_t bytes);
+
+// ---- precision form: FP32 block update C -= A B of FP64 blocks (lowp_blas.cu)
+cudaError_t sgemm_sub(int64_t n, int m, int k, const double* A, int64_t lda, const double* B, int64_t ldb, double* C,
+                      int64_t ldc, cudaStream_t st);
+
 // ---- precision form (tc_apply.cu) -------------------------------------------------
 size_t tc_apply_smem_bytes(int passes);
 cudaError_t tc_prepare(const Ctx& c, cudaStream_t st);   // Fhat, Shat (FP32) and sqrt-diagonals
@@ -187,6 +196,8 @@ cudaError_t tc_prepare(const Ctx& c, cudaStream_t st);   // Fhat, Shat (FP32) an
 cudaError_t tc_gather(const Ctx& c, const double* X, int64_t ldx, int m, cudaStream_t st);
 cudaError_t tc_corner_reduce(const Ctx& c, int m, double* Vraw, cudaStream_t st);
 cudaError_t tc_put_v(const Ctx& c, const double* V, int m, cudaStream_t st);
+cudaError_t tc_coarse_prepare(const Ctx& c, cudaStream_t st);   // FP32 copy of Kbar_cc^{-1}
+cudaError_t tc_coarse_apply(const Ctx& c, const double* Vraw, double* V, int m, cudaStream_t st);
 cudaError_t tc_prepare_tiles(Ctx& c, int m);   // work list of the persistent product for m directions
 cudaError_t tc_product(const Ctx& c, int m, float* Yb, cudaStream_t st);
 cudaError_t scatter_b_to_lam32(const Ctx& c, const float* Yb, int m, double* Y, int64_t ldy, cudaStream_t st);
@@ -263,7 +274,11 @@ cudaError_t recover_tfeti(Ctx& c, const double* lam, const double* alpha, cudaSt
 
 // ---- TFETI (tfeti.cu) -------------------------------------------------------------
 cudaError_t tfeti_add_rrt(const Ctx& c, cudaStream_t st);                 // W += Rhat Rhat^T per module
-cudaError_t tfeti_build_G(const Ctx& c, double* G, cudaStream_t st);      // dense G [n_coarse x n_lam]
+cudaError_t tfeti_ggt(const Ctx& c, double* W, int ldw, double* t1, double* t2, double* Xb, double* Kbar,
+                      cudaStream_t st);   // G G^T through the sparse G, ldw coarse columns at a time
 cudaError_t tfeti_build_e(const Ctx& c, double* e, cudaStream_t st);      // e = -R^T f
+// t = G X from the gathered block Xb = B^T X (no dense G); X -= G^T t
+cudaError_t tfeti_G_apply(const Ctx& c, const double* Xb, int m, double* t, cudaStream_t st);
+cudaError_t tfeti_Gt_sub(const Ctx& c, const double* t, int m, double* X, int64_t ldx, cudaStream_t st);
 
 }  // namespace feti

@@ -22,7 +22,10 @@
 // * Host code cannot use the array's name as a device address.  The first
 //   call on a device looks the address up with cudaGetSymbolAddress (with that
 //   device current) and caches it, so make that first call before any stream
-//   capture begins.
+//   capture begins.  The cached address belongs to the device's primary
+//   context: after cudaDeviceReset (or anything else that replaces that
+//   context) the process must not call this entry point on that device again.
+// * Like every entry point, the call returns after its stream has synchronized.
 #include <mutex>
 #include <string>
 
@@ -38,7 +41,8 @@ constexpr int kMaxDevices = 64;
 std::mutex g_lookup_mutex;
 double* g_scratch_ptr[kMaxDevices] = {nullptr};
 
-// Device address of g_precond_scratch on `device` (which is current).
+// Device address of g_precond_scratch on `device` (which is current): looked
+// up once per device, then cached.
 cudaError_t scratch_address(int device, double** out) {
   if (device < 0 || device >= kMaxDevices) return cudaErrorInvalidDevice;
   std::lock_guard<std::mutex> lock(g_lookup_mutex);
@@ -62,18 +66,23 @@ extern "C" feti_status feti_apply_precond_noalloc(feti_ctx* ctx, const double* r
   if (!ctx || !r) return FETI_EINVAL;
   feti::Ctx& c = ctx->c;
   c.err.clear();
+  if (c.state < 1) {
+    c.err = "feti_apply_precond_noalloc before feti_setup_subdomains";
+    return FETI_ESTATE;
+  }
+  // the size limit is known once the problem is set up: reject before anything else
+  if (2 * c.hp.n_b_total > kNoallocScratch) {
+    c.err = "feti_apply_precond_noalloc: the interface space has " + std::to_string(c.hp.n_b_total) +
+            " entries, more than the static scratch holds (" + std::to_string(kNoallocScratch / 2) +
+            "); use feti_apply_precond";
+    return FETI_EINVAL;
+  }
   if (c.state < 2) {
     c.err = "feti_apply_precond_noalloc before feti_factorize";
     return FETI_ESTATE;
   }
   if (Z && ldz < c.hp.n_lam) {
     c.err = "ldz smaller than n_lambda";
-    return FETI_EINVAL;
-  }
-  if (2 * c.hp.n_b_total > kNoallocScratch) {
-    c.err = "feti_apply_precond_noalloc: the interface space has " + std::to_string(c.hp.n_b_total) +
-            " entries, more than the static scratch holds (" + std::to_string(kNoallocScratch / 2) +
-            "); use feti_apply_precond";
     return FETI_EINVAL;
   }
   int device = -1;
@@ -86,6 +95,7 @@ extern "C" feti_status feti_apply_precond_noalloc(feti_ctx* ctx, const double* r
   if (e == cudaSuccess) e = cudaStreamSynchronize(c.stream);
   if (device >= 0 && device != c.device) cudaSetDevice(device);
   if (e != cudaSuccess) {
+    cudaGetLastError();
     c.err = std::string("feti_apply_precond_noalloc: ") + cudaGetErrorString(e);
     return FETI_ECUDA;
   }

@@ -14,6 +14,7 @@
 // subdomains of one type whose element densities are also identical share a
 // "module" (one factorization, Section 1: repeated modules are reused).
 #include <algorithm>
+#include <cmath>
 #include <cstring>
 #include <map>
 #include <string>
@@ -97,7 +98,7 @@ void owners_of(const HostProblem& hp, const int g[3], NodeOwners& o) {
 }  // namespace
 
 std::string build_host_problem(const feti_problem& prob, int method, int dedup,
-                               const double* rho_host, HostProblem& hp, bool edge_averages) {
+                               const double* rho_host, HostProblem& hp, int edge_mode, double jump_ratio) {
   hp = HostProblem();
   if (prob.dim != 2 && prob.dim != 3) return "dim must be 2 or 3";
   hp.dim = prob.dim;
@@ -129,7 +130,8 @@ std::string build_host_problem(const feti_problem& prob, int method, int dedup,
 
   const int dim = hp.dim;
   const int nld = hp.n_loc_dofs;
-  const bool edges = edge_averages && method == FETI_FETIDP;
+  const bool edges = edge_mode != 0 && method == FETI_FETIDP;
+  const bool adaptive = edges && edge_mode == 2;
 
   // Edge averages: a node with exactly dim - 1 coordinates on tile-grid planes
   // lies inside a tile-grid edge along the remaining axis `run`; the edge gets
@@ -143,6 +145,44 @@ std::string build_host_problem(const feti_problem& prob, int method, int dedup,
       else run = a;
     }
     return on == dim - 1 ? run : -1;
+  };
+  // Adaptive selection: the stiffness jump across the edge through node g --
+  // over its interior nodes, the largest ratio between the sharers' diagonal
+  // stiffness entries of the node.  On these square / cubic elements the
+  // element stiffness has one diagonal value, so a sharer's entry is that value
+  // times the sum of the SIMP moduli of its elements around the node.
+  auto modulus = [&](int64_t e) {
+    return hp.Emin + std::pow(rho_host[e], hp.p) * (hp.E0 - hp.Emin);
+  };
+  auto edge_jump = [&](const int g[3], int run) -> double {
+    int h[3] = {g[0], g[1], g[2]};
+    const int base = g[run] - g[run] % hp.elems[run];
+    double jump = 1.0;
+    NodeOwners on;
+    for (int k = 1; k < hp.elems[run]; ++k) {
+      h[run] = base + k;
+      owners_of(hp, h, on);
+      double lo = 0.0, hi = 0.0;
+      for (int q = 0; q < on.n; ++q) {
+        const int s = on.sub[q];
+        const int ts[3] = {s % hp.tiles[0], (s / hp.tiles[0]) % hp.tiles[1], s / (hp.tiles[0] * hp.tiles[1])};
+        double sum = 0.0;
+        for (int dz = (dim == 3 ? -1 : 0); dz <= 0; ++dz)
+          for (int dy = -1; dy <= 0; ++dy)
+            for (int dx = -1; dx <= 0; ++dx) {
+              const int e3[3] = {h[0] + dx, h[1] + dy, dim == 3 ? h[2] + dz : 0};
+              bool inside = true;
+              for (int a = 0; a < dim; ++a)
+                if (e3[a] < ts[a] * hp.elems[a] || e3[a] >= (ts[a] + 1) * hp.elems[a]) inside = false;
+              if (inside) sum += modulus(e3[0] + (int64_t)hp.nel[0] * (e3[1] + (int64_t)hp.nel[1] * e3[2]));
+            }
+        if (q == 0 || sum < lo) lo = sum;
+        if (q == 0 || sum > hi) hi = sum;
+      }
+      if (lo > 0.0) jump = std::max(jump, hi / lo);
+      else if (hi > 0.0) jump = HUGE_VAL;
+    }
+    return jump;
   };
   auto edge_free = [&](const int g[3], int run, int d) -> bool {
     int h[3] = {g[0], g[1], g[2]};
@@ -181,7 +221,8 @@ std::string build_host_problem(const feti_problem& prob, int method, int dedup,
         int cls;
         if (method == FETI_FETIDP) {
           int run = edges && !vertex && own.n > 1 ? edge_axis(g) : -1;
-          bool avg = run >= 0 && g[run] % hp.elems[run] == 1 && edge_free(g, run, d);
+          bool avg = run >= 0 && g[run] % hp.elems[run] == 1 && edge_free(g, run, d) &&
+                     (!adaptive || edge_jump(g, run) >= jump_ratio);
           if (fixed) cls = CLS_X;
           else if (vertex || avg) cls = CLS_C;
           else if (own.n > 1) cls = CLS_B;

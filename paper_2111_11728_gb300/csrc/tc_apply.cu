@@ -27,7 +27,8 @@ constexpr int TC_NMAX = 256;
 constexpr int TC_MAX_NC = 64;        // primal DOFs per subdomain carried in the K-extension
 constexpr int TC_THREADS = 128;
 constexpr uint32_t TC_TMEM_COLS = 256;
-constexpr long long TC_SPIN_LIMIT = 1ll << 22;
+constexpr unsigned long long TC_WAIT_NS = 1000000000ull;   // every pipeline wait gives up after 1 s
+constexpr long long TC_SPIN_LIMIT = 1ll << 32;              // backstop on the number of polls
 constexpr int TC_STAGES1 = 2;       // ring depth, one pass (48 KB per stage; two CTAs per SM)
 constexpr int TC_STAGES3 = 2;       // ring depth, split product (96 KB per stage)
 constexpr int TCP_STAGES1 = 4;      // persistent kernel: one pass, 4 x 48 KB
@@ -65,8 +66,18 @@ __device__ __forceinline__ float to_tf32(float x) {
   return __uint_as_float(r);
 }
 
+__device__ __forceinline__ unsigned long long global_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+// Bounded wait for the phase `phase` of an mbarrier: true when it completed,
+// false after TC_WAIT_NS of wall time (measured on the global nanosecond timer).
 __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t phase) {
+  const unsigned long long t0 = global_ns();
   for (long long it = 0; it < TC_SPIN_LIMIT; ++it) {
+    if ((it & 15) == 15 && global_ns() - t0 > TC_WAIT_NS) return false;
     uint32_t ok;
     asm volatile(
         "{\n\t.reg .pred p;\n\t"
@@ -183,7 +194,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_tc_apply(
     const __grid_constant__ CUtensorMap tmB, const __grid_constant__ CUtensorMap tmBl,
     const DevType* __restrict__ types, const DevSub* __restrict__ subs, const int* __restrict__ frow,
     const int64_t* __restrict__ bpad, const double* __restrict__ sqrtD, float* __restrict__ Yb, int64_t nbt,
-    int m, int n_cb, int aug, int* __restrict__ status) {
+    int m, int n_cb, int aug, int* __restrict__ status, int skip_chunk) {
   constexpr uint32_t A_BYTES = TC_M * 128, B_BYTES = TC_NMAX * 128;
   constexpr uint32_t STAGE_BYTES = (PASSES == 3 ? 2 : 1) * (A_BYTES + B_BYTES);
   constexpr int KC = TcFmt<FMT>::KC;
@@ -234,6 +245,9 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_tc_apply(
     // ---- producer: TMA loads of A and B chunks into the ring ----
     for (int kc = 0; kc < nk; ++kc) {
       const int st = kc % STAGES, it = kc / STAGES;
+      // test hook: the first tile stops before this chunk's copy, so the MMA
+      // lane's bounded wait for it runs out (nothing is left in flight)
+      if (kc == skip_chunk && blockIdx.x == 0 && blockIdx.y == 0) break;
       if (kc >= STAGES && !mbar_wait(smem_u32(&empty_bar[st]), (uint32_t)((it - 1) & 1))) {
         atomicExch(&fail_sh, 1);
         break;
@@ -529,9 +543,18 @@ __global__ void __launch_bounds__(TCP_THREADS, 1) k_tc_apply_p(
 
 // B operand: xb[j][bpad(s) + k] = parts of sqrt(D_s)[k] (B^sT X)[b, j] in
 // the operand format for k < n_b(s), zero for the padding up to the next
-// multiple of the format's chunk.  Each thread serves TC_GJ consecutive
-// directions, reading the row's multiplier entries once.
+// multiple of the format's chunk.  Each thread serves two consecutive rows k
+// (stored as one pair: the padded offsets and the chunk are even) and TC_GJ
+// consecutive directions, reading each row's multiplier entries once.
 constexpr int TC_GJ = 8;
+
+__device__ __forceinline__ void store_pair(float* p, float a, float b) {
+  *reinterpret_cast<float2*>(p) = make_float2(a, b);
+}
+__device__ __forceinline__ void store_pair(__nv_bfloat16* p, __nv_bfloat16 a, __nv_bfloat16 b) {
+  *reinterpret_cast<__nv_bfloat162*>(p) = __halves2bfloat162(a, b);
+}
+
 template <int FMT, int PASSES>
 __global__ void k_gather_tc(const DevType* __restrict__ types, const DevSub* __restrict__ subs,
                             const int64_t* __restrict__ bpad, const double* __restrict__ X, int64_t ldx, int m,
@@ -543,41 +566,43 @@ __global__ void k_gather_tc(const DevType* __restrict__ types, const DevSub* __r
   const DevSub S = subs[blockIdx.y];
   const int nb = types[S.type].n_b;
   const int nbp_s = k_extent(nb, 0, 0, F::KC);
-  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  const int k = 2 * (blockIdx.x * blockDim.x + threadIdx.x);
   if (k >= nbp_s) return;
   const int j0 = blockIdx.z * TC_GJ;
   const int jn = min(TC_GJ, m - j0);
   // FP32 arithmetic, conversions on the integer pipe (the product rounds the
   // operand to TF32 / BF16 anyway; see fpconv.cuh)
-  int q0 = 0, q1 = 0;
-  float sd = 0.0f;
-  if (k < nb) {
-    const int64_t b = S.b_off + k;
-    q0 = b2l_off[b];
-    q1 = b2l_off[b + 1];
-    sd = f64_to_f32_rn(sqrtD[b]);
-  }
-  float acc[TC_GJ];
+  float acc[2][TC_GJ];
+  float sd[2];
 #pragma unroll
-  for (int u = 0; u < TC_GJ; ++u) acc[u] = 0.0f;
-  for (int q = q0; q < q1; ++q) {
-    const double* x = X + b2l_lam[q] + (int64_t)j0 * ldx;
-    const bool pos = b2l_sign[q] > 0;
+  for (int h = 0; h < 2; ++h) {
 #pragma unroll
-    for (int u = 0; u < TC_GJ; ++u)
-      if (u < jn) {
-        const float xv = f64_to_f32_rn(x[(int64_t)u * ldx]);
-        acc[u] += pos ? xv : -xv;
-      }
+    for (int u = 0; u < TC_GJ; ++u) acc[h][u] = 0.0f;
+    sd[h] = 0.0f;
+    const int kk = k + h;
+    if (kk >= nb) continue;
+    const int64_t b = S.b_off + kk;
+    const int q0 = b2l_off[b], q1 = b2l_off[b + 1];
+    sd[h] = f64_to_f32_rn(sqrtD[b]);
+    for (int q = q0; q < q1; ++q) {
+      const double* x = X + b2l_lam[q] + (int64_t)j0 * ldx;
+      const bool pos = b2l_sign[q] > 0;
+#pragma unroll
+      for (int u = 0; u < TC_GJ; ++u)
+        if (u < jn) {
+          const float xv = f64_to_f32_rn(x[(int64_t)u * ldx]);
+          acc[h][u] += pos ? xv : -xv;
+        }
+    }
   }
   const int64_t o = (int64_t)j0 * nbp + bpad[blockIdx.y] + k;
 #pragma unroll
   for (int u = 0; u < TC_GJ; ++u) {
     if (u >= jn) break;
-    const float v = acc[u] * sd;
-    const typename F::T hi = F::round(v);
-    xb_hi[o + (int64_t)u * nbp] = hi;
-    if (PASSES == 3) xb_lo[o + (int64_t)u * nbp] = F::round(v - F::value(hi));
+    const float v0 = acc[0][u] * sd[0], v1 = acc[1][u] * sd[1];
+    const typename F::T h0 = F::round(v0), h1 = F::round(v1);
+    store_pair(xb_hi + o + (int64_t)u * nbp, h0, h1);
+    if (PASSES == 3) store_pair(xb_lo + o + (int64_t)u * nbp, F::round(v0 - F::value(h0)), F::round(v1 - F::value(h1)));
   }
 }
 
@@ -618,7 +643,10 @@ __global__ void k_make_arena(const DevType* __restrict__ types, const DevModule*
 // Corner reduction of the precision form, FP32 on the CUDA cores:
 // C_s = F_rc,s^T X_b(s) = Frc_hat_s^T (D^{1/2} X_b(s)), read from the gathered
 // operand (high + low parts) and the FP32 copy of Frc_hat.  One block per
-// subdomain and 128 directions; K is staged 32 rows at a time.
+// subdomain and 128 directions; K is staged 32 rows at a time.  A thread owns
+// 4 directions x NCM/NCH corner columns over one of KS interleaved K slices
+// (register tile), the slices are summed by warp shuffles at the end (fixed
+// order: deterministic).
 template <int FMT, int NCM>
 __global__ void __launch_bounds__(256) k_frct_lowp(const DevType* __restrict__ types,
                                                    const DevModule* __restrict__ mods,
@@ -628,21 +656,26 @@ __global__ void __launch_bounds__(256) k_frct_lowp(const DevType* __restrict__ t
                                                    const typename TcFmt<FMT>::T* __restrict__ xb_lo, int64_t nbp,
                                                    int m, double* __restrict__ Cb, int64_t nct) {
   using F = TcFmt<FMT>;
-  constexpr int NQ = NCM / 2;                       // corner columns per thread group
-  __shared__ float fs[32][NCM];
-  __shared__ float xs[32][129];
+  constexpr int NCH = NCM == 64 ? 4 : 2;            // corner groups
+  constexpr int NQ = NCM / NCH;                     // corner columns per thread (12 or 16)
+  constexpr int KS = 8 / NCH;                       // K slices (4 or 2)
+  __shared__ __align__(16) float fs[32][NCM];
+  __shared__ float xs[128][33];
   const DevSub S = subs[blockIdx.y];
   const DevType T = types[S.type];
   const int nb = T.n_b, nc = T.n_c;
   if (nc == 0) return;
   const float* Fr = fmem + mods[S.module].Frc;      // [nb x nc] row-major
   const int j0 = blockIdx.x * 128;
-  const int tid = threadIdx.x, jj = tid & 127, cg = tid >> 7;
+  const int tid = threadIdx.x;
+  const int ks = tid % KS, cq = (tid / KS) % 32, ch = tid / (KS * 32);
   const typename F::T* xh = xb_hi + bpad[blockIdx.y];
   const typename F::T* xl = xb_lo ? xb_lo + bpad[blockIdx.y] : nullptr;
-  float acc[NQ];
+  float acc[4][NQ];
 #pragma unroll
-  for (int q = 0; q < NQ; ++q) acc[q] = 0.f;
+  for (int c = 0; c < 4; ++c)
+#pragma unroll
+    for (int q = 0; q < NQ; ++q) acc[c][q] = 0.f;
   for (int k0 = 0; k0 < nb; k0 += 32) {
     for (int e = tid; e < 32 * NCM; e += 256) {
       const int kk = e / NCM, c = e % NCM, k = k0 + kk;
@@ -655,23 +688,45 @@ __global__ void __launch_bounds__(256) k_frct_lowp(const DevType* __restrict__ t
         v = F::value(xh[(int64_t)j * nbp + k]);
         if (xl) v += F::value(xl[(int64_t)j * nbp + k]);
       }
-      xs[kk][j2] = v;
+      xs[j2][kk] = v;
     }
     __syncthreads();
-#pragma unroll 8
-    for (int kk = 0; kk < 32; ++kk) {
-      const float x = xs[kk][jj];
 #pragma unroll
-      for (int q = 0; q < NQ; ++q) acc[q] = fmaf(fs[kk][cg * NQ + q], x, acc[q]);
+    for (int t = 0; t < 32 / KS; ++t) {
+      const int kk = ks + KS * t;
+      float x[4];
+#pragma unroll
+      for (int c = 0; c < 4; ++c) x[c] = xs[cq * 4 + c][kk];
+#pragma unroll
+      for (int q4 = 0; q4 < NQ / 4; ++q4) {
+        const float4 f = *reinterpret_cast<const float4*>(&fs[kk][ch * NQ + q4 * 4]);
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+          acc[c][q4 * 4 + 0] = fmaf(f.x, x[c], acc[c][q4 * 4 + 0]);
+          acc[c][q4 * 4 + 1] = fmaf(f.y, x[c], acc[c][q4 * 4 + 1]);
+          acc[c][q4 * 4 + 2] = fmaf(f.z, x[c], acc[c][q4 * 4 + 2]);
+          acc[c][q4 * 4 + 3] = fmaf(f.w, x[c], acc[c][q4 * 4 + 3]);
+        }
+      }
     }
     __syncthreads();
   }
-  const int j = j0 + jj;
-  if (j < m) {
+  // sum the K slices (adjacent lanes), slice 0 writes
+#pragma unroll
+  for (int o = 1; o < KS; o <<= 1)
+#pragma unroll
+    for (int c = 0; c < 4; ++c)
+#pragma unroll
+      for (int q = 0; q < NQ; ++q) acc[c][q] += __shfl_xor_sync(0xffffffffu, acc[c][q], o);
+  if (ks != 0) return;
+#pragma unroll
+  for (int c = 0; c < 4; ++c) {
+    const int j = j0 + cq * 4 + c;
+    if (j >= m) continue;
 #pragma unroll
     for (int q = 0; q < NQ; ++q) {
-      const int c = cg * NQ + q;
-      if (c < nc) Cb[S.c_off + c + (int64_t)j * nct] = static_cast<double>(acc[q]);
+      const int cc = ch * NQ + q;
+      if (cc < nc) Cb[S.c_off + cc + (int64_t)j * nct] = static_cast<double>(acc[c][q]);
     }
   }
 }
@@ -694,6 +749,62 @@ __global__ void k_put_v(const DevType* __restrict__ types, const DevSub* __restr
   const typename F::T hi = F::round(v);
   xb_hi[o] = hi;
   if (PASSES == 3) xb_lo[o] = F::round(v - F::value(hi));
+}
+
+// FP32 copy of the coarse inverse (precision form).
+__global__ void k_to_f32(int64_t n, const double* __restrict__ x, float* __restrict__ y) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    y[i] = static_cast<float>(x[i]);
+}
+
+// V = Kbar^{-1} Vraw in FP32 arithmetic (the precision form's coarse
+// correction).  A = Kbar^{-1} in FP32 (n x n, symmetric: read as row k gives
+// column k), B = Vraw and C = V FP64 column-major (n x m, ld n).  64 x 64
+// output tiles, 256 threads with 4 x 4 outputs each, K staged 16 at a time.
+constexpr int CG_T = 64, CG_K = 16;
+__global__ void __launch_bounds__(256) k_sgemm_coarse(int n, int m, const float* __restrict__ A,
+                                                      const double* __restrict__ B, double* __restrict__ C) {
+  __shared__ __align__(16) float As[CG_K][CG_T];
+  __shared__ __align__(16) float Bs[CG_K][CG_T];
+  const int i0 = blockIdx.x * CG_T, j0 = blockIdx.y * CG_T;
+  const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
+  float acc[4][4];
+#pragma unroll
+  for (int r = 0; r < 4; ++r)
+#pragma unroll
+    for (int q = 0; q < 4; ++q) acc[r][q] = 0.0f;
+  for (int k0 = 0; k0 < n; k0 += CG_K) {
+    for (int e = tid; e < CG_K * CG_T; e += 256) {
+      const int kk = e / CG_T, ii = e % CG_T, i = i0 + ii, k = k0 + kk;
+      As[kk][ii] = (i < n && k < n) ? A[(int64_t)k * n + i] : 0.0f;
+    }
+    for (int e = tid; e < CG_K * CG_T; e += 256) {
+      const int kk = e % CG_K, jj = e / CG_K, k = k0 + kk, j = j0 + jj;
+      Bs[kk][jj] = (k < n && j < m) ? static_cast<float>(B[(int64_t)j * n + k]) : 0.0f;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int kk = 0; kk < CG_K; ++kk) {
+      const float4 a = *reinterpret_cast<const float4*>(&As[kk][ty * 4]);
+      const float4 b = *reinterpret_cast<const float4*>(&Bs[kk][tx * 4]);
+      const float av[4] = {a.x, a.y, a.z, a.w}, bv[4] = {b.x, b.y, b.z, b.w};
+#pragma unroll
+      for (int r = 0; r < 4; ++r)
+#pragma unroll
+        for (int q = 0; q < 4; ++q) acc[r][q] = fmaf(av[r], bv[q], acc[r][q]);
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int r = 0; r < 4; ++r) {
+    const int i = i0 + ty * 4 + r;
+    if (i >= n) continue;
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const int j = j0 + tx * 4 + q;
+      if (j < m) C[(int64_t)j * n + i] = static_cast<double>(acc[r][q]);
+    }
+  }
 }
 
 // Shat = D_S^{-1/2} S_bb D_S^{-1/2} (FP32) per module, for the preconditioner
@@ -854,7 +965,7 @@ cudaError_t launch_tc(const Ctx& c, int m, float* Yb, cudaStream_t st) {
   dim3 grid(n_cb * n_rb, c.hp.n_sub);
   k_tc_apply<FMT, PASSES, STAGES><<<grid, TC_THREADS, smem, st>>>(ta, tal, tb, tbl, c.d_types, c.d_subs, c.d_frow,
                                                                   c.d_bpad, c.d_sqrtDF, Yb, c.hp.n_b_total, m, n_cb,
-                                                                  c.tc_aug, c.d_status);
+                                                                  c.tc_aug, c.d_status, c.test_skip_chunk);
   note_launches(1);
   return cudaGetLastError();
 }
@@ -888,7 +999,7 @@ template <int FMT, int PASSES>
 void launch_gather(const Ctx& c, const double* X, int64_t ldx, int m, cudaStream_t st) {
   using T = typename TcFmt<FMT>::T;
   const int max_nbp = k_extent(c.max_nb, 0, 0, TcFmt<FMT>::KC);
-  dim3 g((max_nbp + 127) / 128, c.hp.n_sub, (m + TC_GJ - 1) / TC_GJ);
+  dim3 g((max_nbp / 2 + 127) / 128, c.hp.n_sub, (m + TC_GJ - 1) / TC_GJ);
   k_gather_tc<FMT, PASSES><<<g, 128, 0, st>>>(c.d_types, c.d_subs, c.d_bpad, X, ldx, m, c.d_b2l_off, c.d_b2l_lam,
                                               c.d_b2l_sign, c.d_sqrtDF, static_cast<T*>(c.d_xb_hi),
                                               PASSES == 3 ? static_cast<T*>(c.d_xb_lo) : nullptr, c.nbp_total);
@@ -921,11 +1032,18 @@ cudaError_t tc_prepare_tiles(Ctx& c, int m) {
       for (int cb = 0; cb < n_cb; ++cb) tl.push_back(make_int4(s, rb, cb, 0));
   }
   if ((int64_t)tl.size() > c.tiles_cap) {
-    if (c.d_tiles) cudaFree(c.d_tiles);
+    if (c.d_tiles) {
+      cudaError_t e = cudaStreamSynchronize(c.stream);
+      if (e != cudaSuccess) return e;
+      dev_free(c, c.d_tiles, (size_t)c.tiles_cap * sizeof(int4));
+    }
     c.d_tiles = nullptr;
-    cudaError_t e = cudaMalloc(&c.d_tiles, std::max<size_t>(tl.size(), 1) * sizeof(int4));
+    c.tiles_cap = 0;
+    void* q = nullptr;
+    cudaError_t e = dev_alloc(c, &q, std::max<size_t>(tl.size(), 1) * sizeof(int4));
     if (e != cudaSuccess) return e;
-    c.tiles_cap = (int64_t)tl.size();
+    c.d_tiles = static_cast<int4*>(q);
+    c.tiles_cap = (int64_t)std::max<size_t>(tl.size(), 1);
   }
   cudaError_t e = cudaMemcpy(c.d_tiles, tl.data(), tl.size() * sizeof(int4), cudaMemcpyHostToDevice);
   if (e != cudaSuccess) return e;
@@ -982,6 +1100,22 @@ cudaError_t tc_put_v(const Ctx& c, const double* V, int m, cudaStream_t st) {
   const bool split = tc_split(c);
   if (f == 0) split ? launch_put_v<0, 3>(c, V, m, st) : launch_put_v<0, 1>(c, V, m, st);
   else split ? launch_put_v<1, 3>(c, V, m, st) : launch_put_v<1, 1>(c, V, m, st);
+  note_launches(1);
+  return cudaGetLastError();
+}
+
+cudaError_t tc_coarse_prepare(const Ctx& c, cudaStream_t st) {
+  const int64_t n = (int64_t)c.hp.n_primal * c.hp.n_primal;
+  k_to_f32<<<(unsigned)std::min<int64_t>((n + 255) / 256, 4096), 256, 0, st>>>(n, c.d_Kbar_inv, c.d_Kbar_inv32);
+  note_launches(1);
+  return cudaGetLastError();
+}
+
+cudaError_t tc_coarse_apply(const Ctx& c, const double* Vraw, double* V, int m, cudaStream_t st) {
+  const int n = c.hp.n_primal;
+  if (!c.d_Kbar_inv32 || n <= 0 || m <= 0) return cudaErrorInvalidValue;
+  dim3 g((n + CG_T - 1) / CG_T, (m + CG_T - 1) / CG_T);
+  k_sgemm_coarse<<<g, 256, 0, st>>>(n, m, c.d_Kbar_inv32, Vraw, V);
   note_launches(1);
   return cudaGetLastError();
 }

@@ -31,26 +31,70 @@ __global__ void k_add_rrt(const DevType* __restrict__ types, const DevModule* __
   }
 }
 
-// G[(s*nr + q) * n_lam + l] = -sign * R_b^s(k, q) for each entry (b, sign) of row l.
-__global__ void k_build_G(int64_t n_lam, int nr, const int* __restrict__ b0, const signed char* __restrict__ s0,
-                          const int* __restrict__ b1, const signed char* __restrict__ s1,
-                          const int* __restrict__ bsub, const DevSub* __restrict__ subs,
-                          const DevType* __restrict__ types, double* __restrict__ G) {
+// t[:, jj] = v e_{J0 + jj} for jj < nj (t column-major, ld n).
+__global__ void k_unit_cols(int n, int nj, int J0, double v, double* __restrict__ t) {
+  const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (e >= (int64_t)n * nj) return;
+  const int i = (int)(e % n), jj = (int)(e / n);
+  t[e] = i == J0 + jj ? v : 0.0;
+}
+
+// The projector's coarse products without forming G: G X is a per-subdomain
+// reduction of the gathered block, t[(s, q), j] = -sum_k R_b^s(k, q) (B^sT X)(k, j),
+// and G^T t a per-multiplier combination of the rigid modes at the row's
+// entries.  One block per (subdomain, column); the rigid modes are read per
+// type (nr <= 6).
+__global__ void __launch_bounds__(128) k_G_apply(int nr, const DevType* __restrict__ types,
+                                                 const DevSub* __restrict__ subs, const double* __restrict__ Xb,
+                                                 int64_t nbt, double* __restrict__ t, int n_coarse) {
+  const int s = blockIdx.x, j = blockIdx.y;
+  const DevSub S = subs[s];
+  const DevType T = types[S.type];
+  const double* R = T.Rraw;
+  const double* x = Xb + (int64_t)j * nbt + S.b_off;
+  double acc[6] = {0, 0, 0, 0, 0, 0};
+  for (int k = threadIdx.x; k < T.n_b; k += blockDim.x) {
+    const double v = x[k];
+#pragma unroll
+    for (int q = 0; q < 6; ++q)
+      if (q < nr) acc[q] = fma(R[k * nr + q], v, acc[q]);
+  }
+  __shared__ double red[6][4];
+#pragma unroll
+  for (int q = 0; q < 6; ++q) {
+    double v = acc[q];
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    if ((threadIdx.x & 31) == 0) red[q][threadIdx.x >> 5] = v;
+  }
+  __syncthreads();
+  if (threadIdx.x < nr)
+    t[(int64_t)j * n_coarse + s * nr + threadIdx.x] =
+        -(red[threadIdx.x][0] + red[threadIdx.x][1] + red[threadIdx.x][2] + red[threadIdx.x][3]);
+}
+
+// X[l, j] -= (G^T t)[l, j] = sum over the entries (b, sign) of row l of
+// sign * sum_q R_b^s(k, q) t[(s, q), j]   (G = -R^T B^T).
+__global__ void k_Gt_sub(int64_t n_lam, int m, int nr, const int* __restrict__ b0, const signed char* __restrict__ s0,
+                         const int* __restrict__ b1, const signed char* __restrict__ s1,
+                         const int* __restrict__ bsub, const DevSub* __restrict__ subs,
+                         const DevType* __restrict__ types, const double* __restrict__ t, int n_coarse,
+                         double* __restrict__ X, int64_t ldx) {
   const int64_t l = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (l >= n_lam) return;
-  for (int t = 0; t < 2; ++t) {
-    const int b = t == 0 ? b0[l] : b1[l];
+  const int j = blockIdx.y;
+  if (l >= n_lam || j >= m) return;
+  double v = 0.0;
+  for (int e = 0; e < 2; ++e) {
+    const int b = e == 0 ? b0[l] : b1[l];
     if (b < 0) continue;
-    const int sg = t == 0 ? s0[l] : s1[l];
     const int s = bsub[b];
     const DevSub S = subs[s];
-    const int k = (int)(b - S.b_off);
-    const double* R = types[S.type].Rraw;
-    for (int q = 0; q < nr; ++q) {
-      const double v = R[k * nr + q];
-      G[((int64_t)s * nr + q) * n_lam + l] = sg > 0 ? -v : v;
-    }
+    const double* R = types[S.type].Rraw + (int64_t)(b - S.b_off) * nr;
+    const double* ts = t + (int64_t)j * n_coarse + s * nr;
+    double y = 0.0;
+    for (int q = 0; q < nr; ++q) y = fma(R[q], ts[q], y);
+    v += (e == 0 ? s0[l] : s1[l]) > 0 ? y : -y;
   }
+  X[(int64_t)j * ldx + l] += v;
 }
 
 // Rigid mode q of a subdomain at local DOF (node coordinates c, direction d).
@@ -119,12 +163,42 @@ cudaError_t tfeti_add_rrt(const Ctx& c, cudaStream_t st) {
   return cudaGetLastError();
 }
 
-cudaError_t tfeti_build_G(const Ctx& c, double* G, cudaStream_t st) {
-  cudaError_t e = cudaMemsetAsync(G, 0, sizeof(double) * (size_t)c.n_coarse * c.hp.n_lam, st);
-  if (e != cudaSuccess) return e;
+// G G^T (column-major n_coarse^2 in Kbar) from the sparse G, nj <= ldw coarse
+// columns at a time through the multiplier-space work block W [n_lam x ldw]:
+// W = G^T E_J (as X -= G^T t with t = -E_J on a zero block), then G W.
+cudaError_t tfeti_ggt(const Ctx& c, double* W, int ldw, double* t1, double* t2, double* Xb, double* Kbar,
+                      cudaStream_t st) {
+  const int nco = c.n_coarse;
+  const int64_t nl = c.hp.n_lam;
+  for (int J0 = 0; J0 < nco; J0 += ldw) {
+    const int nj = std::min(ldw, nco - J0);
+    const int64_t ne = (int64_t)nco * nj;
+    k_unit_cols<<<(unsigned)((ne + 255) / 256), 256, 0, st>>>(nco, nj, J0, -1.0, t1);
+    note_launches(1);
+    cudaError_t e = cudaMemsetAsync(W, 0, sizeof(double) * (size_t)nl * nj, st);
+    if (e == cudaSuccess) e = tfeti_Gt_sub(c, t1, nj, W, nl, st);
+    if (e == cudaSuccess) e = gather_lam_to_b(c, W, nl, nj, Xb, st);
+    if (e == cudaSuccess) e = tfeti_G_apply(c, Xb, nj, t2, st);
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(Kbar + (int64_t)J0 * nco, t2, sizeof(double) * (size_t)ne, cudaMemcpyDeviceToDevice, st);
+    if (e != cudaSuccess) return e;
+  }
+  return cudaSuccess;
+}
+
+cudaError_t tfeti_G_apply(const Ctx& c, const double* Xb, int m, double* t, cudaStream_t st) {
+  if (c.hp.n_rbm > 6) return cudaErrorInvalidValue;
+  k_G_apply<<<dim3(c.hp.n_sub, m), 128, 0, st>>>(c.hp.n_rbm, c.d_types, c.d_subs, Xb, c.hp.n_b_total, t,
+                                                 c.n_coarse);
+  note_launches(1);
+  return cudaGetLastError();
+}
+
+cudaError_t tfeti_Gt_sub(const Ctx& c, const double* t, int m, double* X, int64_t ldx, cudaStream_t st) {
   const int64_t n = c.hp.n_lam;
-  k_build_G<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(n, c.hp.n_rbm, c.d_lam_b0, c.d_lam_s0, c.d_lam_b1,
-                                                         c.d_lam_s1, c.d_b_sub, c.d_subs, c.d_types, G);
+  k_Gt_sub<<<dim3((unsigned)((n + 255) / 256), m), 256, 0, st>>>(n, m, c.hp.n_rbm, c.d_lam_b0, c.d_lam_s0,
+                                                                 c.d_lam_b1, c.d_lam_s1, c.d_b_sub, c.d_subs,
+                                                                 c.d_types, t, c.n_coarse, X, ldx);
   note_launches(1);
   return cudaGetLastError();
 }

@@ -16,11 +16,11 @@ def torch_cuda():
 
 
 def make_solver(problem, method="fetidp", scaling="k", krylov="rrs", tol=1e-10, max_iter=500, dedup=True,
-                on_device=True, rr_tol=1e-10, precision=0, inner_tol=None, fp64_residual=False, precond=0):
+                on_device=True, rr_tol=1e-10, precision=0, inner_tol=None, precond=0):
     torch = torch_cuda()
     s = fg.Solver(METHOD[method], SCALING[scaling], KRYLOV[krylov], tol=tol, max_iter=max_iter, rr_tol=rr_tol,
                   dedup=dedup, stream=torch.cuda.current_stream().cuda_stream, precision=precision,
-                  inner_tol=inner_tol, fp64_residual=fp64_residual, precond=precond)
+                  inner_tol=inner_tol, precond=precond)
     if on_device:
         rho = torch.from_numpy(problem.rho).cuda()
         f = torch.from_numpy(problem.f).cuda()

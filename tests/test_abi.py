@@ -40,6 +40,7 @@ def test_defaults_and_invalid_options():
         fg.feti_create(bad)
     assert e.value.status == fg.FETI_EINVAL
     assert fg.lib().feti_options_default(None) == fg.FETI_EINVAL
+    assert fg.lib().feti_set_allocator(None, None) == fg.FETI_EINVAL
 
 
 def test_create_without_gpu_fails_cleanly():
@@ -56,8 +57,14 @@ def test_option_combinations_rejected_before_any_device_call():
     assert o.primal == fg.FETI_PRIMAL_CORNERS and o.precond == fg.FETI_PRECOND_DIRICHLET
     cases = []
     a = fg.feti_options_default()
-    a.primal = 2                                        # no such primal set
+    a.primal = 3                                        # no such primal set
     cases.append((a, fg.FETI_EINVAL))
+    a2 = fg.feti_options_default()
+    a2.primal, a2.primal_jump = fg.FETI_PRIMAL_ADAPTIVE, 0.5   # a jump ratio below 1 selects nothing sensible
+    cases.append((a2, fg.FETI_EINVAL))
+    a3 = fg.feti_options_default()
+    a3.primal, a3.method = fg.FETI_PRIMAL_ADAPTIVE, fg.FETI_TFETI
+    cases.append((a3, fg.FETI_EINVAL))
     b = fg.feti_options_default()
     b.primal, b.method = fg.FETI_PRIMAL_EDGES, fg.FETI_TFETI   # primal sets are a FETI-DP choice
     cases.append((b, fg.FETI_EINVAL))

@@ -61,12 +61,18 @@ def test_f64_to_f32_matches_ieee_round_to_nearest_even(conv):
     x = np.concatenate([
         rng.standard_normal(200000) * 10.0 ** rng.uniform(-30, 30, 200000),
         rng.standard_normal(1000),
+        # arbitrary bit patterns (every exponent, NaNs removed below)
+        rng.integers(0, 2 ** 63, 200000, dtype=np.uint64).view(np.float64) * rng.choice([-1.0, 1.0], 200000),
+        # around the edges of the FP32 normal range
+        2.0 ** rng.uniform(-127.5, -125.5, 20000) * rng.choice([-1.0, 1.0], 20000),
+        2.0 ** rng.uniform(127.5, 128.5, 20000) * rng.choice([-1.0, 1.0], 20000),
         # exact ties: a float32 value plus half an ulp (even and odd mantissas)
         (lambda f: f.astype(np.float64) + np.spacing(f).astype(np.float64) / 2)(
             rng.standard_normal(1000).astype(np.float32)),
         np.array([0.0, -0.0, 1.0, -1.0, 3.4028234663852886e38, 3.4028235677973366e38, 1e39, -1e39,
                   np.inf, -np.inf, 1.1754943508222875e-38, 2.0 ** -126, 2.0 ** -126 * (1 - 2 ** -30)]),
     ])
+    x = x[~np.isnan(x)]
     y, _ = conv(x, np.zeros(0, np.float32))
     with np.errstate(over="ignore"):
         ref = x.astype(np.float32)

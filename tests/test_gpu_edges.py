@@ -81,3 +81,20 @@ def test_edges_need_the_dirichlet_block():
     o.precond = fg.FETI_PRECOND_LUMPED
     with pytest.raises(fg.FetiError):
         fg.feti_create(o, None)
+
+
+@pytest.mark.parametrize("case", ["cube3", "grid2d"])
+def test_adaptive_selection_matches_oracle(case):
+    """The adaptive primal set (edge averages only where the stiffness jumps by
+    >= 10 across the edge): the same primal and multiplier counts as the oracle's
+    selection, the direct solution to 1e-8, the oracle's iteration count."""
+    p = {"cube3": lambda: workloads.config4(tiles=3, elems=4),
+         "grid2d": lambda: workloads.layered_grid(elems=8, layers=8)}[case]()
+    op = FETIDP(p, "k", primal="adaptive")
+    u, st, (n_c, n_lam) = _gpu_solve(p, "rrs", primal=fg.FETI_PRIMAL_ADAPTIVE)
+    assert (n_c, n_lam) == (op.n_c, op.n_lam)
+    corners = FETIDP(p, "k", primal="corners")
+    assert corners.n_c < n_c < FETIDP(p, "k", primal="edges").n_c
+    assert st.converged and rel(u, direct_solve(p)) <= 1e-8
+    _, _, info, _ = solve(p, "fetidp", "k", "rrs", tol=1e-10, op=op)
+    assert abs(st.iterations - info.iterations) <= max(2, 0.1 * info.iterations), (st.iterations, info.iterations)

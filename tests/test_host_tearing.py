@@ -48,7 +48,7 @@ int main(int argc, char** argv) {
     for (int a = 0; a < 3; ++a) { p.tiles[a] = hdr[1 + a]; p.elems[a] = hdr[4 + a]; }
     p.E0 = par[0]; p.Emin = par[1]; p.nu = par[2]; p.p = par[3];
     p.rho = rho.data(); p.dirichlet = dir.data(); p.f = f.data(); p.on_device = 0;
-    std::string msg = build_host_problem(p, hdr[7], 1, rho.data(), parts[q], hdr[8] != 0);
+    std::string msg = build_host_problem(p, hdr[7], 1, rho.data(), parts[q], hdr[8]);
     if (!msg.empty()) { printf("{\"error\": \"%s\"}\n", msg.c_str()); return 1; }
   }
   fclose(fi);
@@ -124,7 +124,8 @@ def _run(harness, probs, method, edges):
         for p in probs:
             tiles = list(p.tiles) + [1] * (3 - p.dim)
             elems = list(p.elems) + [1] * (3 - p.dim)
-            hdr = np.array([p.dim, *tiles, *elems, 1 if method == "fetidp" else 0, int(edges), p.n_elements],
+            mode = 2 if edges == "adaptive" else int(bool(edges))
+            hdr = np.array([p.dim, *tiles, *elems, 1 if method == "fetidp" else 0, mode, p.n_elements],
                            np.int32)
             f.write(hdr.tobytes())
             f.write(np.array([p.E0, p.Emin, p.nu, p.p], np.float64).tobytes())
@@ -142,7 +143,7 @@ def _oracle_rows(p, method, edges, s0=0):
         rows = [[(s + s0, k, g) for (s, k, g) in ent] for ent in op.cons.entries]
         bsets = [sorted({k for ent in op.cons.entries for (s2, k, _) in ent if s2 == s}) for s in range(op.n_sub)]
         return rows, bsets, None, op.n_lam
-    op = FETIDP(p, "k", primal="edges" if edges else "corners")
+    op = FETIDP(p, "k", primal="adaptive" if edges == "adaptive" else ("edges" if edges else "corners"))
     rows = [[(s + s0, int(op.r_loc[s][k]), g) for (s, k, g) in ent] for ent in op.cons.entries]
     bsets = [sorted(int(op.r_loc[s][k]) for k in op.bset[s]) for s in range(op.n_sub)]
     return rows, bsets, op.n_c, op.n_lam
@@ -165,6 +166,8 @@ CASES = [
     ("fetidp", False, lambda: workloads.config4(tiles=2, elems=2)),
     ("fetidp", True, lambda: workloads.config4(tiles=2, elems=3)),
     ("tfeti", False, lambda: workloads.config4(tiles=2, elems=2)),
+    ("fetidp", "adaptive", lambda: workloads.layered_grid(elems=4, layers=4)),
+    ("fetidp", "adaptive", lambda: workloads.config4(tiles=2, elems=3)),
 ]
 
 
@@ -180,14 +183,16 @@ def test_library_tearing_matches_oracle(harness, method, edges, make):
     assert [sorted(b) for b in got["bsets"]] == bsets
 
 
+@pytest.mark.parametrize("mode", [True, "adaptive"])
 @pytest.mark.parametrize("make", [lambda: workloads.config4(tiles=2, elems=3), lambda: workloads.config4(tiles=3, elems=2),
                                   lambda: workloads.layered_grid(elems=4, layers=4)])
-def test_edge_average_tables_match_oracle(harness, make):
+def test_edge_average_tables_match_oracle(harness, make, mode):
     """The change-of-basis tables of every subdomain (the average's slot, then
-    the slots of the edge's other nodes, as local DOFs) are the oracle's edges."""
+    the slots of the edge's other nodes, as local DOFs) are the oracle's edges,
+    for every shared edge and for the adaptive selection."""
     p = make()
-    got = _run(harness, [p], "fetidp", True)
-    op = FETIDP(p, "k", primal="edges")
+    got = _run(harness, [p], "fetidp", mode)
+    op = FETIDP(p, "k", primal="adaptive" if mode == "adaptive" else "edges")
     mesh = op.mesh
     for s in range(op.n_sub):
         g2 = list(mesh.local_to_global_nodes(s))

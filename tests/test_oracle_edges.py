@@ -13,7 +13,12 @@ change of basis on each edge (the reading stated in oracle/fetidp.py):
   values along an averaged edge have the primal value as their mean, the same
   on every sharer;
 * the richer coarse space pays off in 3D: fewer PCG and simultaneous-variant
-  iterations than corners alone.
+  iterations than corners alone;
+* the adaptive selection (averages only across stiffness jumps): its limits are
+  the two fixed sets bit for bit; on the laminated grid it averages exactly the
+  horizontal tile sides (where a stiff lamina meets a compliant one), on the grid
+  of inclusions nothing; it reaches the direct solution in 2D and 3D with fewer
+  PCG iterations than corners alone.
 """
 import itertools
 
@@ -96,3 +101,54 @@ def test_edge_averages_reduce_iterations_in_3d(krylov):
     _, _, ic, _ = solve(p, "fetidp", "k", krylov, tol=1e-8, primal="corners")
     _, _, ie, _ = solve(p, "fetidp", "k", krylov, tol=1e-8, primal="edges")
     assert ie.iterations < ic.iterations
+
+
+# ---- adaptive selection (primal="adaptive") ------------------------------------------
+def test_adaptive_selection_limits_are_corners_and_all_edges():
+    """A jump ratio of 1 selects every shared edge, an infinite one none: the
+    operators then equal those of the two fixed primal sets bit for bit."""
+    p = workloads.layered_grid(elems=6, layers=6)
+    X = np.random.default_rng(3).standard_normal
+    all_edges = FETIDP(p, "k", primal="edges")
+    none = FETIDP(p, "k", primal="corners")
+    a1 = FETIDP(p, "k", primal="adaptive", jump_ratio=1.0)
+    ainf = FETIDP(p, "k", primal="adaptive", jump_ratio=np.inf)
+    assert a1.edges == all_edges.edges and not ainf.edges
+    for got, want in ((a1, all_edges), (ainf, none)):
+        assert got.n_c == want.n_c and got.n_lam == want.n_lam
+        Y = X((want.n_lam, 3))
+        assert np.array_equal(got.apply_F(Y), want.apply_F(Y))
+
+
+def test_adaptive_selection_follows_the_stiffness_jumps():
+    """On the laminated grid the horizontal interfaces join a stiff lamina to a
+    compliant one and the vertical ones join equal laminae: exactly the
+    horizontal tile sides are averaged.  On the grid of inclusions every
+    interface is homogeneous: nothing is.  The selection still solves Eq. (2)
+    and needs fewer PCG iterations than corners alone."""
+    p = workloads.layered_grid(elems=8, layers=8)
+    op = FETIDP(p, "k", primal="adaptive")
+    mesh = op.mesh
+    coords = mesh.node_coords()
+    assert op.edges
+    for nodes, d in op.edges:
+        ys = {int(coords[g][1]) for g in nodes}
+        assert len(ys) == 1 and next(iter(ys)) % p.elems[1] == 0        # runs along x: a horizontal side
+    horizontal = [e for e in edge_averages(p, mesh) if len({int(coords[g][1]) for g in e[0]}) == 1]
+    assert sorted(op.edges) == sorted(horizontal)
+    ud = direct_solve(p)
+    u, _, info, _ = solve(p, "fetidp", "k", "pcg", tol=1e-10, max_iter=500, primal="adaptive")
+    _, _, info_c, _ = solve(p, "fetidp", "k", "pcg", tol=1e-10, max_iter=500, primal="corners")
+    assert info.converged and np.linalg.norm(u - ud) <= 1e-8 * np.linalg.norm(ud)
+    assert info.iterations < info_c.iterations
+    q = workloads.inclusion_grid(elems=8)
+    assert not FETIDP(q, "k", primal="adaptive").edges
+
+
+def test_adaptive_selection_reaches_the_direct_solution_3d():
+    p = _cube()
+    u, _, info, op = solve(p, "fetidp", "k", "rrs", tol=1e-10, max_iter=500, primal="adaptive")
+    assert 0 < len(op.edges) < len(edge_averages(p, op.mesh))
+    assert info.converged
+    ud = direct_solve(p)
+    assert np.linalg.norm(u - ud) <= 1e-8 * np.linalg.norm(ud)
