@@ -60,6 +60,9 @@ import workloads  # noqa: E402
 
 METRIC = "F-applies/s & time-to-solve @rel.res 1e-6 vs plain FP64; % of HBM roofline"
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.070e9 / 1e12   # 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz
+# DRAM bytes per dgemm_kernel launch on the bench workload, mean over one step's 113
+# launches, from the ncu capture summarised in profiles/dgemm_traffic_fetidp_16x16x32.md
+DGEMM_TRAFFIC_PER_LAUNCH = 88.86e6
 
 
 def tensor_peaks():
@@ -344,11 +347,15 @@ def run_forms(p, a, fg, torch, dev, stream, flush, forms, max_iter, m_apply, rep
                       stream=stream.cuda_stream, precision=prec, primal=primal)
         s.setup(p, rho=rho_d, f=f_d, on_device=True)
         u = torch.empty(p.n_dofs, dtype=torch.float64, device=dev)
-        times, st = [], None
+        times, st, phases = [], None, None
         try:
             for k in range(reps):
                 flush.zero_()
                 torch.cuda.synchronize()
+                # with two runs the untimed first one carries the phase profile
+                profiled = reps > 1 and k == 0
+                if profiled:
+                    fg.feti_profile_begin(s.ctx)
                 e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
                 e0.record(stream)
                 fg.feti_factorize(s.ctx)
@@ -356,6 +363,9 @@ def run_forms(p, a, fg, torch, dev, stream, flush, forms, max_iter, m_apply, rep
                 fg.feti_recover_displacements(s.ctx, u, True)
                 e1.record(stream)
                 torch.cuda.synchronize()
+                if profiled:
+                    fg.feti_profile_end(s.ctx)
+                    phases = phase_rooflines(fg.feti_profile_phases(s.ctx), 1, e0.elapsed_time(e1) / 1e3)
                 if k >= reps - 1:
                     times.append(e0.elapsed_time(e1))
         except fg.FetiError as exc:          # a form that cannot reach the tolerance is reported, not fatal
@@ -376,7 +386,7 @@ def run_forms(p, a, fg, torch, dev, stream, flush, forms, max_iter, m_apply, rep
         out[name] = {"time_to_solve_ms": float(np.median(times)), "iterations": st.iterations,
                      "refinements": st.refinements, "f_applies": st.f_applies, "converged": bool(st.converged),
                      f"apply_{m_apply}_cols_ms": ms_apply, "apply_f_applies_per_s": m_apply / (ms_apply / 1e3),
-                     "tensor_product_roofline": tensor}
+                     "tensor_product_roofline": tensor, "phases_of_untimed_run": phases}
         s.close()
     ref = sols["fp64"]
     t64 = out["fp64"]["time_to_solve_ms"]
@@ -864,10 +874,10 @@ def run_ours(a, rank, world):
                                                "orthogonalization, Schur)",
                      "achieved": gemm_tflops, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
                      "frac": (gemm_tflops / FP64_PEAK_TFLOPS) if gemm_tflops else None,
-                     "traffic": None,
-                     "traffic_note": "dram read+write per launch from the ncu capture of two launches: "
-                                     "91.5 MB (29,760 x 256 x 256 update), 125.3 MB (split-K product); "
-                                     "launch shapes vary, so no single per-launch figure",
+                     "traffic": DGEMM_TRAFFIC_PER_LAUNCH,
+                     "traffic_note": "dram__bytes_read.sum + dram__bytes_write.sum, mean over the 113 "
+                                     "dgemm_kernel launches of one step (ncu capture, "
+                                     "profiles/dgemm_traffic_fetidp_16x16x32.md)",
                      "peak_source": "derived: 152 SMs x 2 FP64 FMA/clk x 2.07 GHz",
                      "kernel_share_of_step": (gms / 1e3) / prof_step_s if prof_step_s > 0 else None,
                      "launches_per_step": gn,

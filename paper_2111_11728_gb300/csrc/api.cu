@@ -187,6 +187,7 @@ feti_status ensure_blocks(Ctx& c, int m) {
     TRY(dalloc(c, c.d_ct1, (size_t)c.n_coarse * cap));
     TRY(dalloc(c, c.d_ct2, (size_t)c.n_coarse * cap));
   }
+  if (c.d_Kbar_inv32) TRY(dalloc(c, c.d_coarse_part, (size_t)tc_coarse_split() * np * cap));
   if (c.opt.precision != FETI_FP64) {
     const size_t eb = tc_elem_bytes(c.opt.precision);
     TRY(dalloc_bytes(c, c.d_xb_hi, (size_t)c.nbp_total * cap * eb));

@@ -237,6 +237,7 @@ struct Ctx {
   double* d_Kbar_L = nullptr;    // [n_coarse^2] inverse Cholesky factor (work)
   double* d_Kbar_inv = nullptr;  // [n_coarse^2] explicit inverse
   float* d_Kbar_inv32 = nullptr; // precision form, one problem: FP32 copy of the inverse
+  float* d_coarse_part = nullptr;   // its split-K partial products [split x n_primal x blk_cap]
   double* d_coarse_work = nullptr;   // blocked coarse factorisation work
   // precision form (FETI_TF32)
   float* d_fmem = nullptr;       // FP32 copies at the module offsets: Shat at M.W

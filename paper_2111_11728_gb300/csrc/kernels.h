@@ -197,6 +197,7 @@ cudaError_t tc_gather(const Ctx& c, const double* X, int64_t ldx, int m, cudaStr
 cudaError_t tc_corner_reduce(const Ctx& c, int m, double* Vraw, cudaStream_t st);
 cudaError_t tc_put_v(const Ctx& c, const double* V, int m, cudaStream_t st);
 cudaError_t tc_coarse_prepare(const Ctx& c, cudaStream_t st);   // FP32 copy of Kbar_cc^{-1}
+int tc_coarse_split();   // K ranges of the FP32 coarse product (partials per column block)
 cudaError_t tc_coarse_apply(const Ctx& c, const double* Vraw, double* V, int m, cudaStream_t st);
 cudaError_t tc_prepare_tiles(Ctx& c, int m);   // work list of the persistent product for m directions
 cudaError_t tc_product(const Ctx& c, int m, float* Yb, cudaStream_t st);

@@ -643,10 +643,11 @@ __global__ void k_make_arena(const DevType* __restrict__ types, const DevModule*
 // Corner reduction of the precision form, FP32 on the CUDA cores:
 // C_s = F_rc,s^T X_b(s) = Frc_hat_s^T (D^{1/2} X_b(s)), read from the gathered
 // operand (high + low parts) and the FP32 copy of Frc_hat.  One block per
-// subdomain and 128 directions; K is staged 32 rows at a time.  A thread owns
-// 4 directions x NCM/NCH corner columns over one of KS interleaved K slices
-// (register tile), the slices are summed by warp shuffles at the end (fixed
-// order: deterministic).
+// subdomain and 128 directions; K is staged 32 rows at a time, the next chunk's
+// operand loaded into registers (16-byte loads) while the current one is
+// multiplied.  A thread owns 4 directions x NCM/NCH corner columns over one of
+// KS interleaved K slices (register tile); the slices are summed by warp
+// shuffles at the end (fixed order: deterministic).
 template <int FMT, int NCM>
 __global__ void __launch_bounds__(256) k_frct_lowp(const DevType* __restrict__ types,
                                                    const DevModule* __restrict__ mods,
@@ -656,41 +657,70 @@ __global__ void __launch_bounds__(256) k_frct_lowp(const DevType* __restrict__ t
                                                    const typename TcFmt<FMT>::T* __restrict__ xb_lo, int64_t nbp,
                                                    int m, double* __restrict__ Cb, int64_t nct) {
   using F = TcFmt<FMT>;
+  using T = typename F::T;
   constexpr int NCH = NCM == 64 ? 4 : 2;            // corner groups
   constexpr int NQ = NCM / NCH;                     // corner columns per thread (12 or 16)
   constexpr int KS = 8 / NCH;                       // K slices (4 or 2)
+  constexpr int EV = 16 / sizeof(T);                // operand elements per 16-byte load (8 or 4)
+  constexpr int NV = 32 * 128 / EV / 256;           // 16-byte loads per thread per chunk (2 or 4)
+  constexpr int NF = 32 * NCM / 256;                // corner-block entries per thread per chunk (3 or 8)
   __shared__ __align__(16) float fs[32][NCM];
   __shared__ float xs[128][33];
   const DevSub S = subs[blockIdx.y];
-  const DevType T = types[S.type];
-  const int nb = T.n_b, nc = T.n_c;
+  const DevType Tt = types[S.type];
+  const int nb = Tt.n_b, nc = Tt.n_c;
   if (nc == 0) return;
   const float* Fr = fmem + mods[S.module].Frc;      // [nb x nc] row-major
   const int j0 = blockIdx.x * 128;
   const int tid = threadIdx.x;
   const int ks = tid % KS, cq = (tid / KS) % 32, ch = tid / (KS * 32);
-  const typename F::T* xh = xb_hi + bpad[blockIdx.y];
-  const typename F::T* xl = xb_lo ? xb_lo + bpad[blockIdx.y] : nullptr;
+  const T* xh = xb_hi + bpad[blockIdx.y];
+  const T* xl = xb_lo ? xb_lo + bpad[blockIdx.y] : nullptr;
+  // the padded operand extends to a multiple of the format's chunk (>= 32 rows):
+  // a 16-byte load at k0 + 8 i stays inside it and the padding reads as zero
+  const int nbp_s = k_extent(nb, 0, 0, F::KC);
+  uint4 vh[NV], vl[NV];
+  float vf[NF];
+  auto load_chunk = [&](int k0) {
+#pragma unroll
+    for (int t = 0; t < NV; ++t) {
+      const int v = tid + 256 * t, j = v / (32 / EV), kk = (v % (32 / EV)) * EV;
+      const int64_t o = (int64_t)(j0 + j) * nbp + k0 + kk;
+      const bool ok = j0 + j < m && k0 + kk < nbp_s;
+      vh[t] = ok ? *reinterpret_cast<const uint4*>(xh + o) : make_uint4(0, 0, 0, 0);
+      vl[t] = (ok && xl) ? *reinterpret_cast<const uint4*>(xl + o) : make_uint4(0, 0, 0, 0);
+    }
+#pragma unroll
+    for (int t = 0; t < NF; ++t) {
+      const int e = tid + 256 * t, kk = e / NCM, c = e % NCM, k = k0 + kk;
+      vf[t] = (k < nb && c < nc) ? Fr[(int64_t)k * nc + c] : 0.0f;
+    }
+  };
+  auto store_chunk = [&]() {
+#pragma unroll
+    for (int t = 0; t < NV; ++t) {
+      const int v = tid + 256 * t, j = v / (32 / EV), kk = (v % (32 / EV)) * EV;
+      const T* ph = reinterpret_cast<const T*>(&vh[t]);
+      const T* pl = reinterpret_cast<const T*>(&vl[t]);
+#pragma unroll
+      for (int i = 0; i < EV; ++i) xs[j][kk + i] = F::value(ph[i]) + F::value(pl[i]);
+    }
+#pragma unroll
+    for (int t = 0; t < NF; ++t) {
+      const int e = tid + 256 * t;
+      fs[e / NCM][e % NCM] = vf[t];
+    }
+  };
   float acc[4][NQ];
 #pragma unroll
   for (int c = 0; c < 4; ++c)
 #pragma unroll
     for (int q = 0; q < NQ; ++q) acc[c][q] = 0.f;
+  load_chunk(0);
   for (int k0 = 0; k0 < nb; k0 += 32) {
-    for (int e = tid; e < 32 * NCM; e += 256) {
-      const int kk = e / NCM, c = e % NCM, k = k0 + kk;
-      fs[kk][c] = (k < nb && c < nc) ? Fr[(int64_t)k * nc + c] : 0.0f;
-    }
-    for (int e = tid; e < 32 * 128; e += 256) {
-      const int j2 = e >> 5, kk = e & 31, k = k0 + kk, j = j0 + j2;
-      float v = 0.0f;
-      if (j < m && k < nb) {
-        v = F::value(xh[(int64_t)j * nbp + k]);
-        if (xl) v += F::value(xl[(int64_t)j * nbp + k]);
-      }
-      xs[j2][kk] = v;
-    }
+    store_chunk();
     __syncthreads();
+    if (k0 + 32 < nb) load_chunk(k0 + 32);            // in flight while this chunk is multiplied
 #pragma unroll
     for (int t = 0; t < 32 / KS; ++t) {
       const int kk = ks + KS * t;
@@ -759,11 +789,13 @@ __global__ void k_to_f32(int64_t n, const double* __restrict__ x, float* __restr
 
 // V = Kbar^{-1} Vraw in FP32 arithmetic (the precision form's coarse
 // correction).  A = Kbar^{-1} in FP32 (n x n, symmetric: read as row k gives
-// column k), B = Vraw and C = V FP64 column-major (n x m, ld n).  64 x 64
-// output tiles, 256 threads with 4 x 4 outputs each, K staged 16 at a time.
-constexpr int CG_T = 64, CG_K = 16;
+// column k), B = Vraw FP64 column-major (n x m, ld n).  64 x 64 output tiles,
+// 256 threads with 4 x 4 outputs each, K staged 16 at a time and split in
+// CG_SPLIT ranges (blockIdx.z) whose FP32 partial products go to P
+// [CG_SPLIT x n x m]; k_coarse_sum adds them in a fixed order into V (FP64).
+constexpr int CG_T = 64, CG_K = 16, CG_SPLIT = 4;
 __global__ void __launch_bounds__(256) k_sgemm_coarse(int n, int m, const float* __restrict__ A,
-                                                      const double* __restrict__ B, double* __restrict__ C) {
+                                                      const double* __restrict__ B, float* __restrict__ P) {
   __shared__ __align__(16) float As[CG_K][CG_T];
   __shared__ __align__(16) float Bs[CG_K][CG_T];
   const int i0 = blockIdx.x * CG_T, j0 = blockIdx.y * CG_T;
@@ -773,14 +805,16 @@ __global__ void __launch_bounds__(256) k_sgemm_coarse(int n, int m, const float*
   for (int r = 0; r < 4; ++r)
 #pragma unroll
     for (int q = 0; q < 4; ++q) acc[r][q] = 0.0f;
-  for (int k0 = 0; k0 < n; k0 += CG_K) {
+  const int kper = ((n + CG_SPLIT * CG_K - 1) / (CG_SPLIT * CG_K)) * CG_K;
+  const int kbeg = blockIdx.z * kper, kend = min(n, kbeg + kper);
+  for (int k0 = kbeg; k0 < kend; k0 += CG_K) {
     for (int e = tid; e < CG_K * CG_T; e += 256) {
       const int kk = e / CG_T, ii = e % CG_T, i = i0 + ii, k = k0 + kk;
-      As[kk][ii] = (i < n && k < n) ? A[(int64_t)k * n + i] : 0.0f;
+      As[kk][ii] = (i < n && k < kend) ? A[(int64_t)k * n + i] : 0.0f;
     }
     for (int e = tid; e < CG_K * CG_T; e += 256) {
       const int kk = e % CG_K, jj = e / CG_K, k = k0 + kk, j = j0 + jj;
-      Bs[kk][jj] = (k < n && j < m) ? static_cast<float>(B[(int64_t)j * n + k]) : 0.0f;
+      Bs[kk][jj] = (k < kend && j < m) ? f64_to_f32_rn(B[(int64_t)j * n + k]) : 0.0f;
     }
     __syncthreads();
 #pragma unroll
@@ -795,6 +829,7 @@ __global__ void __launch_bounds__(256) k_sgemm_coarse(int n, int m, const float*
     }
     __syncthreads();
   }
+  float* Pz = P + (int64_t)blockIdx.z * n * m;
 #pragma unroll
   for (int r = 0; r < 4; ++r) {
     const int i = i0 + ty * 4 + r;
@@ -802,9 +837,18 @@ __global__ void __launch_bounds__(256) k_sgemm_coarse(int n, int m, const float*
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
       const int j = j0 + tx * 4 + q;
-      if (j < m) C[(int64_t)j * n + i] = static_cast<double>(acc[r][q]);
+      if (j < m) Pz[(int64_t)j * n + i] = acc[r][q];
     }
   }
+}
+
+__global__ void k_coarse_sum(int64_t nm, const float* __restrict__ P, double* __restrict__ V) {
+  const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (e >= nm) return;
+  float v = 0.0f;
+#pragma unroll
+  for (int z = 0; z < CG_SPLIT; ++z) v += P[z * nm + e];
+  V[e] = f32_to_f64(v);
 }
 
 // Shat = D_S^{-1/2} S_bb D_S^{-1/2} (FP32) per module, for the preconditioner
@@ -1104,6 +1148,8 @@ cudaError_t tc_put_v(const Ctx& c, const double* V, int m, cudaStream_t st) {
   return cudaGetLastError();
 }
 
+int tc_coarse_split() { return CG_SPLIT; }
+
 cudaError_t tc_coarse_prepare(const Ctx& c, cudaStream_t st) {
   const int64_t n = (int64_t)c.hp.n_primal * c.hp.n_primal;
   k_to_f32<<<(unsigned)std::min<int64_t>((n + 255) / 256, 4096), 256, 0, st>>>(n, c.d_Kbar_inv, c.d_Kbar_inv32);
@@ -1114,9 +1160,12 @@ cudaError_t tc_coarse_prepare(const Ctx& c, cudaStream_t st) {
 cudaError_t tc_coarse_apply(const Ctx& c, const double* Vraw, double* V, int m, cudaStream_t st) {
   const int n = c.hp.n_primal;
   if (!c.d_Kbar_inv32 || n <= 0 || m <= 0) return cudaErrorInvalidValue;
-  dim3 g((n + CG_T - 1) / CG_T, (m + CG_T - 1) / CG_T);
-  k_sgemm_coarse<<<g, 256, 0, st>>>(n, m, c.d_Kbar_inv32, Vraw, V);
-  note_launches(1);
+  if (!c.d_coarse_part || m > c.blk_cap) return cudaErrorInvalidValue;
+  dim3 g((n + CG_T - 1) / CG_T, (m + CG_T - 1) / CG_T, CG_SPLIT);
+  k_sgemm_coarse<<<g, 256, 0, st>>>(n, m, c.d_Kbar_inv32, Vraw, c.d_coarse_part);
+  const int64_t nm = (int64_t)n * m;
+  k_coarse_sum<<<(unsigned)((nm + 255) / 256), 256, 0, st>>>(nm, c.d_coarse_part, V);
+  note_launches(2);
   return cudaGetLastError();
 }
 

@@ -8,6 +8,9 @@
                          rows (Eq. 13), and the error-bound scales below
   fullsize_config4.npz   8^3 tiles of 8^3 H8, smoothed field (contrast 1e9):
                          sampled rows of F X for a 512-column block and the bound scales
+  solve_config2.npz      the bench workload's own solve (FETI-DP + k + Algorithm 1,
+                         tol 1e-6) at 4096 sampled DOFs and its compliance, and the same
+                         for the solve with the moduli perturbed at the unit roundoff
   solve_config4_4x4x4.npz  4^3 tiles of 8^3 H8 (same field recipe): Algorithm 1
                          (FETI-DP, k-scaling) solution at tol 1e-10, the same solve
                          with the densities perturbed at the unit roundoff (below), the
@@ -41,7 +44,7 @@ vector of subdomain s; V = Kbar_cc^{-1} F_rc^T X the coarse correction):
           (a factorization's backward error is ~n u rather than 2u).
 
 Run from the repository root:
-    python tests/golden/make_fullsize_goldens.py config2|config4|solve4
+    python tests/golden/make_fullsize_goldens.py config2|config4|solve4|solve2
 """
 import gc
 import os

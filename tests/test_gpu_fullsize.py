@@ -227,3 +227,30 @@ def test_config4_4x4x4_solution_matches_oracle(gold4s, precision):
     assert c == pytest.approx(float(p.f @ uo), rel=bar)
     if precision == fg.FETI_FP64:     # Algorithm 1 on both sides: iteration counts within 10% or 2
         assert abs(st.iterations - int(g["iterations"])) <= max(2, 0.1 * int(g["iterations"]))
+
+
+# ------------------------------------------------------------------ 2D bench solve
+def test_config2_bench_solve_matches_oracle():
+    """The bench workload's own solve (FETI-DP + k + Algorithm 1, tol 1e-6, the
+    launch configuration bench.py times) against the oracle's at 4,096 sampled
+    DOFs and in the compliance.  At contrast 1e9 the solve amplifies round-off:
+    the oracle's own solution moves by ||u_pert - u|| when the SIMP moduli are
+    perturbed by 2u; both solutions carry the round-off of n_r-sized local
+    solves, so the bar is (n_r / 2) times that change (elementwise: times its
+    largest entry; the compliance: times the change of the compliance)."""
+    g = load("solve_config2.npz")
+    p = workloads.config2()
+    assert rho_hash_ok(p, g)
+    u, st, c, s = solve_u(p, tol=float(g["tol"]))
+    s.close()
+    idx = g["dof"]
+    scale = 0.5 * float(g["n_r_max"])
+    d_el = np.abs(u[idx] - g["u_oracle"]).max()
+    report("config2_bench_solve", iterations=st.iterations, oracle_iterations=int(g["iterations"]),
+           rel_sampled=rel(u[idx], g["u_oracle"]), pert_rel=float(g["pert_norm"] / g["u_norm"]),
+           ratio_elem=float(d_el / (scale * g["pert_max"])),
+           ratio_compliance=float(abs(c - g["compliance"]) / (scale * abs(g["compliance_pert"] - g["compliance"]))))
+    assert st.converged
+    assert abs(st.iterations - int(g["iterations"])) <= max(2, 0.1 * int(g["iterations"]))
+    assert d_el <= scale * float(g["pert_max"])
+    assert abs(c - float(g["compliance"])) <= scale * abs(float(g["compliance_pert"]) - float(g["compliance"]))
