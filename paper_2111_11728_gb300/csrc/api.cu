@@ -321,12 +321,14 @@ feti_status apply_dual(Ctx& c, const double* X, int64_t ldx, int m, double* Y, i
 }
 
 // Y = F X with the local blocks on the tensor cores (TF32 / BF16 inputs,
-// FP32 accumulation).  The corner reduction F_rc^T X and the coarse
-// correction Kbar_cc^{-1} (F_rc^T X) of a block are FP32 products too (the
-// coarse matrix is factorized and inverted in FP64 at feti_factorize; only
-// its application is rounded, like the local blocks').
+// FP32 accumulation).  The corner reduction F_rc^T X runs on the tensor cores
+// too (corner tiles of the same product kernel) and the coarse correction
+// Kbar_cc^{-1} (F_rc^T X) is an FP32 product (the coarse matrix is factorized
+// and inverted in FP64 at feti_factorize; only its application is rounded,
+// like the local blocks').
 feti_status apply_dual_lowp(Ctx& c, const double* X, int64_t ldx, int m, double* Y, int64_t ldy) {
   TRY(ensure_blocks(c, m));
+  CU(tc_prepare_tiles(c, m));
   CU(tc_gather(c, X, ldx, m, c.stream));
   if (c.tc_aug) {
     // corner reduction, coarse solve, then the coarse correction rides in
@@ -336,7 +338,6 @@ feti_status apply_dual_lowp(Ctx& c, const double* X, int64_t ldx, int m, double*
     else CU(coarse_apply(c, c.d_Vraw, c.d_V, m, c.stream));
     CU(tc_put_v(c, c.d_V, m, c.stream));
   }
-  CU(tc_prepare_tiles(c, m));
   const cudaError_t pe = tc_product(c, m, c.d_Yb32, c.stream);
   c.test_skip_chunk = -1;                          // the test hook acts on one product only
   CU(pe);
@@ -661,6 +662,16 @@ static feti_status setup_impl(Ctx& c, const feti_problem* probs, int n) {
   TRY(upload(c, c.d_b2l_off, hp.b2l_off));
   TRY(upload(c, c.d_b2l_lam, hp.b2l_lam));
   TRY(upload(c, c.d_b2l_sign, hp.b2l_sign));
+  {
+    std::vector<int> first(std::max<int64_t>(hp.n_b_total, 1), -1);
+    for (int64_t b = 0; b < hp.n_b_total; ++b)
+      if (hp.b2l_off[b + 1] - hp.b2l_off[b] == 1) {
+        const int q = hp.b2l_off[b];
+        first[b] = (hp.b2l_lam[q] << 1) | (hp.b2l_sign[q] < 0 ? 1 : 0);
+      }
+    if (hp.n_lam >= ((int64_t)1 << 30)) { c.err = "more than 2^30 multipliers"; return FETI_ENOTSUP; }
+    TRY(upload(c, c.d_b2l_first, first));
+  }
   TRY(upload(c, c.d_b_sub, hp.b_sub));
   {
     std::vector<int> lcol(hp.b_sub.size());
@@ -784,6 +795,15 @@ static feti_status setup_impl(Ctx& c, const feti_problem* probs, int n) {
     for (int q = 0; q < c.n_mod; ++q) {
       const DevType& T = c.h_types[c.h_mods[q].type];
       c.tc_bytes_f += (int64_t)T.n_b * (T.n_b + (c.tc_aug ? T.n_c : 0)) * eb * parts;
+    }
+    // FETI-DP: a block of tile rows per module holding Frc_hat^T, for the corner
+    // reduction on the tensor cores
+    c.n_ctiles_rows = c.tc_aug ? 1 : 0;
+    c.fcrow0 = (int)rows;
+    if (c.tc_aug) rows += (int64_t)c.n_mod * tc_tile_rows();
+    if (rows >= (int64_t)1 << 31) {
+      c.err = "precision form: operand arena too large for 32-bit tensor coordinates";
+      return FETI_ENOTSUP;
     }
     c.fa_rows = std::max<int64_t>(rows, 1);
     c.nbp_total = std::max<int64_t>(nbp, kc);

@@ -33,6 +33,7 @@ __global__ void k_gather(int64_t nbt, int m, const int* __restrict__ off, const 
 
 // Each thread serves SC_J consecutive columns, reading the row's entries once.
 constexpr int SC_J = 8;
+constexpr int SC_Z = 64;            // FP32 scatter: directions per block
 template <typename TY>
 __global__ void k_scatter(int64_t nl, int m, const int* __restrict__ b0, const signed char* __restrict__ s0,
                           const int* __restrict__ b1, const signed char* __restrict__ s1,
@@ -237,22 +238,25 @@ __global__ void k_scatter32(int64_t nl, int m, const int* __restrict__ b0, const
                             const int* __restrict__ b1, const signed char* __restrict__ s1,
                             const float* __restrict__ Yb, int64_t nbt, double* __restrict__ Y, int64_t ldy) {
   const int64_t l = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  const int j0 = blockIdx.y * SC_J;
   if (l >= nl) return;
-  const int jn = min(SC_J, m - j0);
   const int p0 = b0[l], p1 = b1[l];
   const bool n0 = s0[l] < 0, n1 = p1 >= 0 && s1[l] < 0;
+  // SC_Z directions per block in groups of SC_J (few, long-lived blocks)
+  const int jend = min(m, (int)(blockIdx.y + 1) * SC_Z);
+  for (int j0 = blockIdx.y * SC_Z; j0 < jend; j0 += SC_J) {
+    const int jn = min(SC_J, m - j0);
 #pragma unroll
-  for (int u = 0; u < SC_J; ++u) {
-    if (u >= jn) break;
-    const float* yb = Yb + (int64_t)(j0 + u) * nbt;
-    const float a = yb[p0];
-    float v = n0 ? -a : a;
-    if (p1 >= 0) {
-      const float c = yb[p1];
-      v += n1 ? -c : c;
+    for (int u = 0; u < SC_J; ++u) {
+      if (u >= jn) break;
+      const float* yb = Yb + (int64_t)(j0 + u) * nbt;
+      const float a = yb[p0];
+      float v = n0 ? -a : a;
+      if (p1 >= 0) {
+        const float c = yb[p1];
+        v += n1 ? -c : c;
+      }
+      Y[l + (int64_t)(j0 + u) * ldy] = f32_to_f64(v);
     }
-    Y[l + (int64_t)(j0 + u) * ldy] = f32_to_f64(v);
   }
 }
 
@@ -261,7 +265,7 @@ __global__ void k_scatter32(int64_t nl, int m, const int* __restrict__ b0, const
 // Same, from an FP32 interface-space block (the tensor-core product's output).
 cudaError_t scatter_b_to_lam32(const Ctx& c, const float* Yb, int m, double* Y, int64_t ldy, cudaStream_t st) {
   const int64_t nl = c.hp.n_lam;
-  dim3 g((unsigned)((nl + 255) / 256), (m + SC_J - 1) / SC_J);
+  dim3 g((unsigned)((nl + 255) / 256), (m + SC_Z - 1) / SC_Z);
   k_scatter32<<<g, 256, 0, st>>>(nl, m, c.d_lam_b0, c.d_lam_s0, c.d_lam_b1, c.d_lam_s1, Yb, c.hp.n_b_total, Y, ldy);
   note_launches(1);
   return cudaGetLastError();

@@ -211,6 +211,7 @@ struct Ctx {
   signed char *d_lam_s0 = nullptr, *d_lam_s1 = nullptr;
   int *d_group_off = nullptr, *d_group_b = nullptr;
   int *d_b2l_off = nullptr, *d_b2l_lam = nullptr;
+  int* d_b2l_first = nullptr;    // [n_b_total] the single multiplier row (l << 1 | negative), -1 if several
   signed char* d_b2l_sign = nullptr;
   int* d_b_sub = nullptr;
   int* d_c_glob = nullptr;
@@ -254,6 +255,9 @@ struct Ctx {
   int4* d_tiles = nullptr;       // persistent tensor-core kernel: (subdomain, row tile, column tile)
   int64_t tiles_cap = 0;
   int n_tiles = 0, tiles_ncb = 0, n_sm = 0;
+  int n_ctiles = 0;              // corner tiles after the n_tiles product tiles in d_tiles
+  int fcrow0 = 0;                // first arena row of the corner blocks (128 rows per module)
+  int n_ctiles_rows = 0;         // 1 when the arena carries corner blocks
   double fl_tc = 0.0;            // algorithmic flops of the tensor-core product per column
   int test_skip_chunk = -1;      // test hook: K chunk whose copy the next TF32 product's first tile skips
   int64_t tc_bytes_f = 0;        // algorithmic bytes: scaled blocks (read once per apply)

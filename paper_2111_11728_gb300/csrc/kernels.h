@@ -191,6 +191,7 @@ cudaError_t sgemm_sub(int64_t n, int m, int k, const double* A, int64_t lda, con
 
 // ---- precision form (tc_apply.cu) -------------------------------------------------
 size_t tc_apply_smem_bytes(int passes);
+int tc_tile_rows();                     // rows of one tensor-core tile (and of a module's corner block)
 cudaError_t tc_prepare(const Ctx& c, cudaStream_t st);   // Fhat, Shat (FP32) and sqrt-diagonals
 // Yb = D^{1/2} Fhat D^{1/2} B^T X (tcgen05 kind::tf32); rows >= n_b untouched
 cudaError_t tc_gather(const Ctx& c, const double* X, int64_t ldx, int m, cudaStream_t st);

@@ -356,7 +356,7 @@ __global__ void __launch_bounds__(TCP_THREADS, 1) k_tc_apply_p(
     const int4* __restrict__ tiles, int n_tiles, const DevType* __restrict__ types,
     const DevSub* __restrict__ subs, const int* __restrict__ frow, const int64_t* __restrict__ bpad,
     const double* __restrict__ sqrtD, float* __restrict__ Yb, int64_t nbt, int m, int aug,
-    int* __restrict__ status) {
+    int* __restrict__ status, int fcrow0, double* __restrict__ Cb, int64_t nct) {
   constexpr uint32_t A_BYTES = TC_M * 128, B_BYTES = TC_NMAX * 128;
   constexpr uint32_t STAGE_BYTES = (PASSES == 3 ? 2 : 1) * (A_BYTES + B_BYTES);
   constexpr int KC = TcFmt<FMT>::KC;
@@ -402,8 +402,9 @@ __global__ void __launch_bounds__(TCP_THREADS, 1) k_tc_apply_p(
         const int4 tl = tiles[t];
         const DevSub S = subs[tl.x];
         const DevType T = types[S.type];
-        const int nk = k_extent(T.n_b, T.n_c, aug, KC) / KC;
-        const int arow = frow[S.module] + tl.y * TC_M;
+        // corner tile (tl.w = 1): the module's Frc_hat^T block times the operand's b part
+        const int nk = tl.w ? k_extent(T.n_b, 0, 0, KC) / KC : k_extent(T.n_b, T.n_c, aug, KC) / KC;
+        const int arow = tl.w ? fcrow0 + S.module * TC_M : frow[S.module] + tl.y * TC_M;
         const int bx0 = (int)bpad[tl.x];
         const int col0 = tl.z * TC_NMAX;
         for (int kc = 0; kc < nk; ++kc, ++g) {
@@ -437,7 +438,7 @@ __global__ void __launch_bounds__(TCP_THREADS, 1) k_tc_apply_p(
         const int4 tl = tiles[t];
         const DevSub S = subs[tl.x];
         const DevType T = types[S.type];
-        const int nk = k_extent(T.n_b, T.n_c, aug, KC) / KC;
+        const int nk = tl.w ? k_extent(T.n_b, 0, 0, KC) / KC : k_extent(T.n_b, T.n_c, aug, KC) / KC;
         const int ncols = min(TC_NMAX, m - tl.z * TC_NMAX);
         const uint32_t idesc = idesc_of<FMT>(((ncols + 15) / 16) * 16);
         const int ab = lt & 1, use = lt >> 1;
@@ -506,16 +507,32 @@ __global__ void __launch_bounds__(TCP_THREADS, 1) k_tc_apply_p(
       const int col0 = tl.z * TC_NMAX;
       const int ncols = min(TC_NMAX, m - col0);
       const int np = ((ncols + 15) / 16) * 16;
-      const int r = tl.y * TC_M + lq * 32 + lane;
-      const float sd = r < nb ? static_cast<float>(sqrtD[S.b_off + r]) : 0.0f;
-      float* yrow = Yb + S.b_off + r;
-      for (int jc = 0; jc < np; jc += 32) {
-        uint32_t v[32];
-        tmem_ld32(tmem + ((uint32_t)(lq * 32) << 16) + (uint32_t)(ab * TC_NMAX + jc), v);
-        if (r < nb) {
+      if (tl.w) {
+        // corner tile: row r of the accumulator is C_s(r, .) = (F_rc^T X_b)(r, .)
+        const int r = lq * 32 + lane;
+        const bool live = r < types[S.type].n_c;
+        double* crow = Cb + S.c_off + r;
+        for (int jc = 0; jc < np; jc += 32) {
+          uint32_t v[32];
+          tmem_ld32(tmem + ((uint32_t)(lq * 32) << 16) + (uint32_t)(ab * TC_NMAX + jc), v);
+          if (live) {
 #pragma unroll
-          for (int c = 0; c < 32; ++c)
-            if (jc + c < ncols) yrow[(int64_t)(col0 + jc + c) * nbt] = sd * __uint_as_float(v[c]);
+            for (int c = 0; c < 32; ++c)
+              if (jc + c < ncols) crow[(int64_t)(col0 + jc + c) * nct] = static_cast<double>(__uint_as_float(v[c]));
+          }
+        }
+      } else {
+        const int r = tl.y * TC_M + lq * 32 + lane;
+        const float sd = r < nb ? static_cast<float>(sqrtD[S.b_off + r]) : 0.0f;
+        float* yrow = Yb + S.b_off + r;
+        for (int jc = 0; jc < np; jc += 32) {
+          uint32_t v[32];
+          tmem_ld32(tmem + ((uint32_t)(lq * 32) << 16) + (uint32_t)(ab * TC_NMAX + jc), v);
+          if (r < nb) {
+#pragma unroll
+            for (int c = 0; c < 32; ++c)
+              if (jc + c < ncols) yrow[(int64_t)(col0 + jc + c) * nbt] = sd * __uint_as_float(v[c]);
+          }
         }
       }
       asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
@@ -543,10 +560,14 @@ __global__ void __launch_bounds__(TCP_THREADS, 1) k_tc_apply_p(
 
 // B operand: xb[j][bpad(s) + k] = parts of sqrt(D_s)[k] (B^sT X)[b, j] in
 // the operand format for k < n_b(s), zero for the padding up to the next
-// multiple of the format's chunk.  Each thread serves two consecutive rows k
-// (stored as one pair: the padded offsets and the chunk are even) and TC_GJ
-// consecutive directions, reading each row's multiplier entries once.
+// multiple of the format's chunk.  One row k per thread (consecutive threads
+// read consecutive multiplier rows: coalesced) and TC_GJ consecutive
+// directions; a row with a single multiplier entry (the usual case) reads it
+// from b2l_first in one load, the cross-point rows walk their CSR list.  Even
+// lanes store the pair (k, k + 1) as one 4- or 8-byte word (the padded offsets
+// and the chunk are even).
 constexpr int TC_GJ = 8;
+constexpr int TC_GZ = 8;             // directions per block
 
 __device__ __forceinline__ void store_pair(float* p, float a, float b) {
   *reinterpret_cast<float2*>(p) = make_float2(a, b);
@@ -558,51 +579,70 @@ __device__ __forceinline__ void store_pair(__nv_bfloat16* p, __nv_bfloat16 a, __
 template <int FMT, int PASSES>
 __global__ void k_gather_tc(const DevType* __restrict__ types, const DevSub* __restrict__ subs,
                             const int64_t* __restrict__ bpad, const double* __restrict__ X, int64_t ldx, int m,
-                            const int* __restrict__ b2l_off, const int* __restrict__ b2l_lam,
-                            const signed char* __restrict__ b2l_sign, const double* __restrict__ sqrtD,
-                            typename TcFmt<FMT>::T* __restrict__ xb_hi, typename TcFmt<FMT>::T* __restrict__ xb_lo,
-                            int64_t nbp) {
+                            const int* __restrict__ b2l_first, const int* __restrict__ b2l_off,
+                            const int* __restrict__ b2l_lam, const signed char* __restrict__ b2l_sign,
+                            const double* __restrict__ sqrtD, typename TcFmt<FMT>::T* __restrict__ xb_hi,
+                            typename TcFmt<FMT>::T* __restrict__ xb_lo, int64_t nbp) {
   using F = TcFmt<FMT>;
   const DevSub S = subs[blockIdx.y];
   const int nb = types[S.type].n_b;
   const int nbp_s = k_extent(nb, 0, 0, F::KC);
-  const int k = 2 * (blockIdx.x * blockDim.x + threadIdx.x);
-  if (k >= nbp_s) return;
-  const int j0 = blockIdx.z * TC_GJ;
-  const int jn = min(TC_GJ, m - j0);
-  // FP32 arithmetic, conversions on the integer pipe (the product rounds the
-  // operand to TF32 / BF16 anyway; see fpconv.cuh)
-  float acc[2][TC_GJ];
-  float sd[2];
-#pragma unroll
-  for (int h = 0; h < 2; ++h) {
-#pragma unroll
-    for (int u = 0; u < TC_GJ; ++u) acc[h][u] = 0.0f;
-    sd[h] = 0.0f;
-    const int kk = k + h;
-    if (kk >= nb) continue;
-    const int64_t b = S.b_off + kk;
-    const int q0 = b2l_off[b], q1 = b2l_off[b + 1];
-    sd[h] = f64_to_f32_rn(sqrtD[b]);
-    for (int q = q0; q < q1; ++q) {
-      const double* x = X + b2l_lam[q] + (int64_t)j0 * ldx;
-      const bool pos = b2l_sign[q] > 0;
-#pragma unroll
-      for (int u = 0; u < TC_GJ; ++u)
-        if (u < jn) {
-          const float xv = f64_to_f32_rn(x[(int64_t)u * ldx]);
-          acc[h][u] += pos ? xv : -xv;
-        }
-    }
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  // the row's entry and scale once, then TC_GZ directions in groups of TC_GJ
+  // (few, long-lived blocks: the block count, not the bytes, bounded the
+  // one-group-per-block form)
+  int first = -1, q0 = 0, q1 = 0;
+  float sd = 0.0f;
+  if (k < nb) {
+    const int64_t b = S.b_off + k;
+    first = b2l_first[b];
+    sd = f64_to_f32_rn(sqrtD[b]);
+    if (first < 0) { q0 = b2l_off[b]; q1 = b2l_off[b + 1]; }
   }
-  const int64_t o = (int64_t)j0 * nbp + bpad[blockIdx.y] + k;
+  const int jend = min(m, (blockIdx.z + 1) * TC_GZ);
+  for (int j0 = blockIdx.z * TC_GZ; j0 < jend; j0 += TC_GJ) {
+    const int jn = min(TC_GJ, m - j0);
+    // FP32 arithmetic, conversions on the integer pipe (the product rounds the
+    // operand to TF32 / BF16 anyway; see fpconv.cuh)
+    float acc[TC_GJ];
 #pragma unroll
-  for (int u = 0; u < TC_GJ; ++u) {
-    if (u >= jn) break;
-    const float v0 = acc[0][u] * sd[0], v1 = acc[1][u] * sd[1];
-    const typename F::T h0 = F::round(v0), h1 = F::round(v1);
-    store_pair(xb_hi + o + (int64_t)u * nbp, h0, h1);
-    if (PASSES == 3) store_pair(xb_lo + o + (int64_t)u * nbp, F::round(v0 - F::value(h0)), F::round(v1 - F::value(h1)));
+    for (int u = 0; u < TC_GJ; ++u) acc[u] = 0.0f;
+    if (k < nb) {
+      if (first >= 0) {
+        const double* x = X + (first >> 1) + (int64_t)j0 * ldx;
+        const bool neg = first & 1;
+#pragma unroll
+        for (int u = 0; u < TC_GJ; ++u)
+          if (u < jn) {
+            const float xv = f64_to_f32_rn(x[(int64_t)u * ldx]);
+            acc[u] = neg ? -xv : xv;
+          }
+      } else {
+        for (int q = q0; q < q1; ++q) {
+          const double* x = X + b2l_lam[q] + (int64_t)j0 * ldx;
+          const bool pos = b2l_sign[q] > 0;
+#pragma unroll
+          for (int u = 0; u < TC_GJ; ++u)
+            if (u < jn) {
+              const float xv = f64_to_f32_rn(x[(int64_t)u * ldx]);
+              acc[u] += pos ? xv : -xv;
+            }
+        }
+      }
+    }
+    const bool store = k < nbp_s && (k & 1) == 0;
+    const int64_t o = (int64_t)j0 * nbp + bpad[blockIdx.y] + k;
+#pragma unroll
+    for (int u = 0; u < TC_GJ; ++u) {
+      const float v0 = acc[u] * sd;
+      const float v1 = __shfl_down_sync(0xffffffffu, v0, 1);   // row k + 1 (same warp: k even)
+      if (store && u < jn) {
+        const typename F::T h0 = F::round(v0), h1 = F::round(v1);
+        store_pair(xb_hi + o + (int64_t)u * nbp, h0, h1);
+        if (PASSES == 3)
+          store_pair(xb_lo + o + (int64_t)u * nbp, F::round(v0 - F::value(h0)), F::round(v1 - F::value(h1)));
+      }
+    }
   }
 }
 
@@ -634,6 +674,32 @@ __global__ void k_make_arena(const DevType* __restrict__ types, const DevModule*
       v = static_cast<float>(Frc[(int64_t)i * nc + (j - n)] / di);
       o = (int64_t)(frow[blockIdx.y] + i) * pitch + c0 + (j - n);
     }
+    const typename F::T hi = F::round(v);
+    fa_hi[o] = hi;
+    if (fa_lo) fa_lo[o] = F::round(v - F::value(hi));
+  }
+}
+
+// Corner blocks of the arena (FETI-DP): module q's rows fcrow0 + 128 q + c hold
+// Frc_hat_s^T (c < n_c): entry k < n_b is F_rc(k, c) / sqrt(F_s(k, k)); the rest of
+// the 128-row block stays zero.  A corner tile multiplies it with the gathered
+// operand's b part: C_s = Frc_hat^T (D^{1/2} X_b) = F_rc^T X_b.
+template <int FMT>
+__global__ void k_make_arena_corner(const DevType* __restrict__ types, const DevModule* __restrict__ mods,
+                                    const double* __restrict__ mem, int fcrow0, int64_t pitch,
+                                    typename TcFmt<FMT>::T* __restrict__ fa_hi,
+                                    typename TcFmt<FMT>::T* __restrict__ fa_lo) {
+  using F = TcFmt<FMT>;
+  const DevModule M = mods[blockIdx.y];
+  const DevType T = types[M.type];
+  const int n = T.n_b, nc = T.n_c;
+  const double* Fm = mem + M.F;
+  const double* Frc = mem + M.Frc;                  // [n x nc] row-major
+  const int64_t total = (int64_t)nc * n;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+    const int c = (int)(e / n), k = (int)(e % n);
+    const float v = static_cast<float>(Frc[(int64_t)k * nc + c] / sqrt(Fm[(int64_t)k * n + k]));
+    const int64_t o = (int64_t)(fcrow0 + blockIdx.y * TC_M + c) * pitch + k;
     const typename F::T hi = F::round(v);
     fa_hi[o] = hi;
     if (fa_lo) fa_lo[o] = F::round(v - F::value(hi));
@@ -793,7 +859,7 @@ __global__ void k_to_f32(int64_t n, const double* __restrict__ x, float* __restr
 // 256 threads with 4 x 4 outputs each, K staged 16 at a time and split in
 // CG_SPLIT ranges (blockIdx.z) whose FP32 partial products go to P
 // [CG_SPLIT x n x m]; k_coarse_sum adds them in a fixed order into V (FP64).
-constexpr int CG_T = 64, CG_K = 16, CG_SPLIT = 4;
+constexpr int CG_T = 64, CG_K = 16, CG_SPLIT = 8;
 __global__ void __launch_bounds__(256) k_sgemm_coarse(int n, int m, const float* __restrict__ A,
                                                       const double* __restrict__ B, float* __restrict__ P) {
   __shared__ __align__(16) float As[CG_K][CG_T];
@@ -915,6 +981,8 @@ __global__ void k_sub_gemv_lowp(const DevType* __restrict__ types, const DevModu
 
 }  // namespace
 
+int tc_tile_rows() { return TC_M; }
+
 size_t tc_apply_smem_bytes(int passes) {
   const size_t stage = (passes == 3 ? 2 : 1) * (size_t)(TC_M * 128 + TC_NMAX * 128);
   return 1024 + (passes == 3 ? TC_STAGES3 : TC_STAGES1) * stage;
@@ -949,6 +1017,20 @@ cudaError_t tc_prepare(const Ctx& c, cudaStream_t st) {
   note_launches(1);
   e = cudaGetLastError();
   if (e != cudaSuccess) return e;
+  if (c.n_ctiles_rows > 0) {
+    if (tc_format(c) == 0)
+      k_make_arena_corner<0><<<dim3(32, c.n_mod), 256, 0, st>>>(c.d_types, c.d_mods, c.d_modmem, c.fcrow0,
+                                                               c.fa_pitch, static_cast<float*>(c.d_fa_hi),
+                                                               split ? static_cast<float*>(c.d_fa_lo) : nullptr);
+    else
+      k_make_arena_corner<1><<<dim3(32, c.n_mod), 256, 0, st>>>(c.d_types, c.d_mods, c.d_modmem, c.fcrow0,
+                                                               c.fa_pitch, static_cast<__nv_bfloat16*>(c.d_fa_hi),
+                                                               split ? static_cast<__nv_bfloat16*>(c.d_fa_lo)
+                                                                     : nullptr);
+    note_launches(1);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+  }
   k_sqrt_diag<<<dim3((c.max_nb + 127) / 128, c.hp.n_sub), 128, 0, st>>>(c.d_types, c.d_mods, c.d_subs, c.d_modmem,
                                                                         c.d_sqrtDF, c.d_sqrtDS);
   note_launches(1);
@@ -1015,7 +1097,7 @@ cudaError_t launch_tc(const Ctx& c, int m, float* Yb, cudaStream_t st) {
 }
 
 template <int FMT, int PASSES, int STAGES>
-cudaError_t launch_tc_p(const Ctx& c, int m, float* Yb, cudaStream_t st) {
+cudaError_t launch_tc_p(const Ctx& c, int m, float* Yb, cudaStream_t st, bool corner = false) {
   static bool attr_set = false;
   const size_t smem = 1024 + (size_t)STAGES * (PASSES == 3 ? 2 : 1) * (TC_M * 128 + TC_NMAX * 128);
   if (!attr_set) {
@@ -1031,10 +1113,14 @@ cudaError_t launch_tc_p(const Ctx& c, int m, float* Yb, cudaStream_t st) {
       !make_map<FMT>(&tal, alo, c.fa_pitch, c.fa_rows, TC_M) ||
       !make_map<FMT>(&tb, c.d_xb_hi, c.nbp_total, m, TC_NMAX) || !make_map<FMT>(&tbl, blo, c.nbp_total, m, TC_NMAX))
     return cudaErrorInvalidValue;
-  const int grid = std::min(c.n_tiles, std::max(1, c.n_sm));
-  k_tc_apply_p<FMT, PASSES, STAGES><<<grid, TCP_THREADS, smem, st>>>(ta, tal, tb, tbl, c.d_tiles, c.n_tiles, c.d_types,
+  const int ntl = corner ? c.n_ctiles : c.n_tiles;
+  const int4* tl = corner ? c.d_tiles + c.n_tiles : c.d_tiles;
+  const int grid = std::min(ntl, std::max(1, c.n_sm));
+  if (grid <= 0) return cudaSuccess;
+  k_tc_apply_p<FMT, PASSES, STAGES><<<grid, TCP_THREADS, smem, st>>>(ta, tal, tb, tbl, tl, ntl, c.d_types,
                                                                      c.d_subs, c.d_frow, c.d_bpad, c.d_sqrtDF, Yb,
-                                                                     c.hp.n_b_total, m, c.tc_aug, c.d_status);
+                                                                     c.hp.n_b_total, m, c.tc_aug, c.d_status,
+                                                                     c.fcrow0, c.d_Cb, c.n_c_total);
   note_launches(1);
   return cudaGetLastError();
 }
@@ -1043,9 +1129,9 @@ template <int FMT, int PASSES>
 void launch_gather(const Ctx& c, const double* X, int64_t ldx, int m, cudaStream_t st) {
   using T = typename TcFmt<FMT>::T;
   const int max_nbp = k_extent(c.max_nb, 0, 0, TcFmt<FMT>::KC);
-  dim3 g((max_nbp / 2 + 127) / 128, c.hp.n_sub, (m + TC_GJ - 1) / TC_GJ);
-  k_gather_tc<FMT, PASSES><<<g, 128, 0, st>>>(c.d_types, c.d_subs, c.d_bpad, X, ldx, m, c.d_b2l_off, c.d_b2l_lam,
-                                              c.d_b2l_sign, c.d_sqrtDF, static_cast<T*>(c.d_xb_hi),
+  dim3 g((max_nbp + 127) / 128, c.hp.n_sub, (m + TC_GZ - 1) / TC_GZ);
+  k_gather_tc<FMT, PASSES><<<g, 128, 0, st>>>(c.d_types, c.d_subs, c.d_bpad, X, ldx, m, c.d_b2l_first, c.d_b2l_off,
+                                              c.d_b2l_lam, c.d_b2l_sign, c.d_sqrtDF, static_cast<T*>(c.d_xb_hi),
                                               PASSES == 3 ? static_cast<T*>(c.d_xb_lo) : nullptr, c.nbp_total);
 }
 
@@ -1075,6 +1161,12 @@ cudaError_t tc_prepare_tiles(Ctx& c, int m) {
     for (int rb = 0; rb * TC_M < nb; ++rb)
       for (int cb = 0; cb < n_cb; ++cb) tl.push_back(make_int4(s, rb, cb, 0));
   }
+  const int n_main = (int)tl.size();
+  // corner tiles (FETI-DP): one row tile per subdomain with primal DOFs
+  if (c.n_ctiles_rows > 0)
+    for (int s = 0; s < c.hp.n_sub; ++s)
+      if (c.h_types[c.h_subs[s].type].n_c > 0)
+        for (int cb = 0; cb < n_cb; ++cb) tl.push_back(make_int4(s, 0, cb, 1));
   if ((int64_t)tl.size() > c.tiles_cap) {
     if (c.d_tiles) {
       cudaError_t e = cudaStreamSynchronize(c.stream);
@@ -1097,7 +1189,8 @@ cudaError_t tc_prepare_tiles(Ctx& c, int m) {
     e = cudaDeviceGetAttribute(&c.n_sm, cudaDevAttrMultiProcessorCount, dev);
     if (e != cudaSuccess) return e;
   }
-  c.n_tiles = (int)tl.size();
+  c.n_tiles = n_main;
+  c.n_ctiles = (int)tl.size() - n_main;
   c.tiles_ncb = n_cb;
   return cudaSuccess;
 }
@@ -1128,6 +1221,19 @@ void launch_frct_lowp(const Ctx& c, int m, cudaStream_t st) {
 
 cudaError_t tc_corner_reduce(const Ctx& c, int m, double* Vraw, cudaStream_t st) {
   if (c.max_nc > TC_MAX_NC) return cudaErrorInvalidValue;
+  if (c.n_ctiles > 0 && c.tiles_ncb == (m + TC_NMAX - 1) / TC_NMAX) {
+    // on the tensor cores: the corner tiles of the persistent product
+    const bool split = tc_split(c);
+    cudaError_t e;
+    if (tc_format(c) == 0)
+      e = split ? launch_tc_p<0, 3, TCP_STAGES3>(c, m, nullptr, st, true)
+                : launch_tc_p<0, 1, TCP_STAGES1>(c, m, nullptr, st, true);
+    else
+      e = split ? launch_tc_p<1, 3, TCP_STAGES3>(c, m, nullptr, st, true)
+                : launch_tc_p<1, 1, TCP_STAGES1>(c, m, nullptr, st, true);
+    if (e != cudaSuccess) return e;
+    return corner_assemble(c, m, Vraw, st);
+  }
   const bool wide = c.max_nc > 24;                   // edge averages: up to 64 primal DOFs per subdomain
   if (tc_format(c) == 0) wide ? launch_frct_lowp<0, 64>(c, m, st) : launch_frct_lowp<0, 24>(c, m, st);
   else wide ? launch_frct_lowp<1, 64>(c, m, st) : launch_frct_lowp<1, 24>(c, m, st);

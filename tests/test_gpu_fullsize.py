@@ -24,8 +24,9 @@ Tolerances (per element; derivations in the golden script's docstring):
   and Laub 1994), so the element bar is (n_r / 2) max_i delta_ij.
 * rounding of the products: (2 u_f + (K + 8) u_32) A_loc for operands rounded to
   a format of unit roundoff u_f and FP32 accumulation over K terms, plus
-  (u_f + (n_b + n_c + 8) u_32) A_cc (n_c <= 64) for the FP32 corner reduction and
-  FP32 coarse correction; u_f = 2^-11 (TF32), 2^-8 (BF16), 3 t^2 for the three-pass
+  (2 u_f + (n_b + n_c + 8) u_32) A_cc (n_c <= 64) for the corner reduction (the
+  same rounded operands on the tensor cores) and the FP32 coarse correction;
+  u_f = 2^-11 (TF32), 2^-8 (BF16), 3 t^2 for the three-pass
   split of a format with unit roundoff t (its representation error t^2 and the
   dropped lo*lo term).
 """
@@ -115,7 +116,7 @@ def check_apply(name, Y, gold, precision):
     else:
         uf = FORMATS[precision][1]
         tol = (fp64_scale(gold) + (2 * uf + (K + 8) * U32) * A_loc
-               + (uf + (int(gold["n_b_max"]) + 72) * U32) * A_cc)
+               + (2 * uf + (int(gold["n_b_max"]) + 72) * U32) * A_cc)
     err = np.abs(Y - Yo)
     ratio = err / tol
     report(name, precision=precision, max_ratio=float(ratio.max()), median_ratio=float(np.median(ratio)),
