@@ -190,9 +190,14 @@ feti_status ensure_blocks(Ctx& c, int m) {
   if (c.d_Kbar_inv32) TRY(dalloc(c, c.d_coarse_part, (size_t)tc_coarse_split() * np * cap));
   if (c.opt.precision != FETI_FP64) {
     const size_t eb = tc_elem_bytes(c.opt.precision);
+    // the padding of the operand stays zero: the gather writes only the DOF slots
     TRY(dalloc_bytes(c, c.d_xb_hi, (size_t)c.nbp_total * cap * eb));
+    CU(cudaMemsetAsync(c.d_xb_hi, 0, (size_t)c.nbp_total * cap * eb, c.stream));
     TRY(dalloc(c, c.d_Yb32, (size_t)nbt * cap));
-    if (split_precision(c.opt.precision)) TRY(dalloc_bytes(c, c.d_xb_lo, (size_t)c.nbp_total * cap * eb));
+    if (split_precision(c.opt.precision)) {
+      TRY(dalloc_bytes(c, c.d_xb_lo, (size_t)c.nbp_total * cap * eb));
+      CU(cudaMemsetAsync(c.d_xb_lo, 0, (size_t)c.nbp_total * cap * eb, c.stream));
+    }
     c.xb_cap = cap;
   }
   c.blk_cap = cap;
@@ -662,16 +667,7 @@ static feti_status setup_impl(Ctx& c, const feti_problem* probs, int n) {
   TRY(upload(c, c.d_b2l_off, hp.b2l_off));
   TRY(upload(c, c.d_b2l_lam, hp.b2l_lam));
   TRY(upload(c, c.d_b2l_sign, hp.b2l_sign));
-  {
-    std::vector<int> first(std::max<int64_t>(hp.n_b_total, 1), -1);
-    for (int64_t b = 0; b < hp.n_b_total; ++b)
-      if (hp.b2l_off[b + 1] - hp.b2l_off[b] == 1) {
-        const int q = hp.b2l_off[b];
-        first[b] = (hp.b2l_lam[q] << 1) | (hp.b2l_sign[q] < 0 ? 1 : 0);
-      }
-    if (hp.n_lam >= ((int64_t)1 << 30)) { c.err = "more than 2^30 multipliers"; return FETI_ENOTSUP; }
-    TRY(upload(c, c.d_b2l_first, first));
-  }
+
   TRY(upload(c, c.d_b_sub, hp.b_sub));
   {
     std::vector<int> lcol(hp.b_sub.size());
@@ -809,6 +805,25 @@ static feti_status setup_impl(Ctx& c, const feti_problem* probs, int n) {
     c.nbp_total = std::max<int64_t>(nbp, kc);
     TRY(upload(c, c.d_frow, frow));
     TRY(upload(c, c.d_bpad, bpad));
+    {
+      // operand slots seen from the multiplier rows; DOFs with several rows apart
+      auto xpos = [&](int b) { const int s = hp.b_sub[b]; return (int)(bpad[s] + (b - hp.b_off[s])); };
+      auto single = [&](int b) { return hp.b2l_off[b + 1] - hp.b2l_off[b] == 1; };
+      std::vector<int> xp0(std::max<int64_t>(nl, 1), -1), xp1(std::max<int64_t>(nl, 1), -1), bm, bmp;
+      for (int64_t l = 0; l < nl; ++l) {
+        if (single(hp.lam_b0[l])) xp0[l] = xpos(hp.lam_b0[l]);
+        if (hp.lam_b1[l] >= 0 && single(hp.lam_b1[l])) xp1[l] = xpos(hp.lam_b1[l]);
+      }
+      for (int64_t b = 0; b < hp.n_b_total; ++b)
+        if (!single((int)b)) { bm.push_back((int)b); bmp.push_back(xpos((int)b)); }
+      c.n_bmulti = (int)bm.size();
+      TRY(upload(c, c.d_lam_xp0, xp0));
+      TRY(upload(c, c.d_lam_xp1, xp1));
+      TRY(upload(c, c.d_bmulti, bm));
+      TRY(upload(c, c.d_bmulti_pos, bmp));
+      TRY(dalloc(c, c.d_lam_w0f, std::max<int64_t>(nl, 1)));
+      TRY(dalloc(c, c.d_lam_w1f, std::max<int64_t>(nl, 1)));
+    }
     const size_t fa_bytes = (size_t)(c.fa_rows * c.fa_pitch) * tc_elem_bytes(c.opt.precision);
     TRY(dalloc_bytes(c, c.d_fa_hi, fa_bytes));
     CU(cudaMemset(c.d_fa_hi, 0, fa_bytes));

@@ -211,7 +211,12 @@ struct Ctx {
   signed char *d_lam_s0 = nullptr, *d_lam_s1 = nullptr;
   int *d_group_off = nullptr, *d_group_b = nullptr;
   int *d_b2l_off = nullptr, *d_b2l_lam = nullptr;
-  int* d_b2l_first = nullptr;    // [n_b_total] the single multiplier row (l << 1 | negative), -1 if several
+  // precision form, operand from the multiplier side: per row l the operand slots of
+  // its two entries (-1 for an entry whose DOF has several rows) and sign * sqrt(D)
+  int *d_lam_xp0 = nullptr, *d_lam_xp1 = nullptr;
+  float *d_lam_w0f = nullptr, *d_lam_w1f = nullptr;
+  int *d_bmulti = nullptr, *d_bmulti_pos = nullptr;   // DOFs with several rows, their operand slots
+  int n_bmulti = 0;
   signed char* d_b2l_sign = nullptr;
   int* d_b_sub = nullptr;
   int* d_c_glob = nullptr;

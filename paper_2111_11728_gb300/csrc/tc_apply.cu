@@ -560,90 +560,106 @@ __global__ void __launch_bounds__(TCP_THREADS, 1) k_tc_apply_p(
 
 // B operand: xb[j][bpad(s) + k] = parts of sqrt(D_s)[k] (B^sT X)[b, j] in
 // the operand format for k < n_b(s), zero for the padding up to the next
-// multiple of the format's chunk.  One row k per thread (consecutive threads
-// read consecutive multiplier rows: coalesced) and TC_GJ consecutive
-// directions; a row with a single multiplier entry (the usual case) reads it
-// from b2l_first in one load, the cross-point rows walk their CSR list.  Even
-// lanes store the pair (k, k + 1) as one 4- or 8-byte word (the padded offsets
-// and the chunk are even).
-constexpr int TC_GJ = 8;
-constexpr int TC_GZ = 8;             // directions per block
+// multiple of the format's chunk (zeroed once when the buffer is allocated).
+constexpr int TC_GJ = 8;              // directions per thread
 
-__device__ __forceinline__ void store_pair(float* p, float a, float b) {
-  *reinterpret_cast<float2*>(p) = make_float2(a, b);
-}
-__device__ __forceinline__ void store_pair(__nv_bfloat16* p, __nv_bfloat16 a, __nv_bfloat16 b) {
-  *reinterpret_cast<__nv_bfloat162*>(p) = __halves2bfloat162(a, b);
-}
-
+// It is built from the multiplier side: one multiplier row l per
+// thread reads X(l, j) once (consecutive threads, consecutive rows: coalesced)
+// and writes w0(l) X(l, j) and w1(l) X(l, j) to the operand slots xp0(l) and
+// xp1(l) of its two entries, w = sign * sqrt(D) of the entry.  Only entries
+// whose interface DOF has this single multiplier row get a slot (-1
+// otherwise); the DOFs with several rows (cross points) are summed by
+// k_gather_multi.  TC_GJ directions per thread.
 template <int FMT, int PASSES>
-__global__ void k_gather_tc(const DevType* __restrict__ types, const DevSub* __restrict__ subs,
-                            const int64_t* __restrict__ bpad, const double* __restrict__ X, int64_t ldx, int m,
-                            const int* __restrict__ b2l_first, const int* __restrict__ b2l_off,
-                            const int* __restrict__ b2l_lam, const signed char* __restrict__ b2l_sign,
-                            const double* __restrict__ sqrtD, typename TcFmt<FMT>::T* __restrict__ xb_hi,
+__global__ void k_spread_tc(int64_t nl, int m, const int* __restrict__ xp0, const int* __restrict__ xp1,
+                            const float* __restrict__ w0, const float* __restrict__ w1,
+                            const double* __restrict__ X, int64_t ldx, typename TcFmt<FMT>::T* __restrict__ xb_hi,
                             typename TcFmt<FMT>::T* __restrict__ xb_lo, int64_t nbp) {
   using F = TcFmt<FMT>;
-  const DevSub S = subs[blockIdx.y];
-  const int nb = types[S.type].n_b;
-  const int nbp_s = k_extent(nb, 0, 0, F::KC);
-  const int k = blockIdx.x * blockDim.x + threadIdx.x;
-  // the row's entry and scale once, then TC_GZ directions in groups of TC_GJ
-  // (few, long-lived blocks: the block count, not the bytes, bounded the
-  // one-group-per-block form)
-  int first = -1, q0 = 0, q1 = 0;
-  float sd = 0.0f;
-  if (k < nb) {
-    const int64_t b = S.b_off + k;
-    first = b2l_first[b];
-    sd = f64_to_f32_rn(sqrtD[b]);
-    if (first < 0) { q0 = b2l_off[b]; q1 = b2l_off[b + 1]; }
-  }
-  const int jend = min(m, (blockIdx.z + 1) * TC_GZ);
-  for (int j0 = blockIdx.z * TC_GZ; j0 < jend; j0 += TC_GJ) {
-    const int jn = min(TC_GJ, m - j0);
-    // FP32 arithmetic, conversions on the integer pipe (the product rounds the
-    // operand to TF32 / BF16 anyway; see fpconv.cuh)
-    float acc[TC_GJ];
+  const int64_t l = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (l >= nl) return;
+  const int p0 = xp0[l], p1 = xp1[l];
+  if (p0 < 0 && p1 < 0) return;
+  const float a0 = w0[l], a1 = w1[l];
+  const int j0 = blockIdx.y * TC_GJ;
+  const int jn = min(TC_GJ, m - j0);
+  float v[TC_GJ];
 #pragma unroll
-    for (int u = 0; u < TC_GJ; ++u) acc[u] = 0.0f;
-    if (k < nb) {
-      if (first >= 0) {
-        const double* x = X + (first >> 1) + (int64_t)j0 * ldx;
-        const bool neg = first & 1;
+  for (int u = 0; u < TC_GJ; ++u) v[u] = u < jn ? f64_to_f32_rn(X[l + (int64_t)(j0 + u) * ldx]) : 0.0f;
 #pragma unroll
-        for (int u = 0; u < TC_GJ; ++u)
-          if (u < jn) {
-            const float xv = f64_to_f32_rn(x[(int64_t)u * ldx]);
-            acc[u] = neg ? -xv : xv;
-          }
-      } else {
-        for (int q = q0; q < q1; ++q) {
-          const double* x = X + b2l_lam[q] + (int64_t)j0 * ldx;
-          const bool pos = b2l_sign[q] > 0;
-#pragma unroll
-          for (int u = 0; u < TC_GJ; ++u)
-            if (u < jn) {
-              const float xv = f64_to_f32_rn(x[(int64_t)u * ldx]);
-              acc[u] += pos ? xv : -xv;
-            }
-        }
-      }
+  for (int u = 0; u < TC_GJ; ++u) {
+    if (u >= jn) break;
+    const int64_t o = (int64_t)(j0 + u) * nbp;
+    if (p0 >= 0) {
+      const float y = a0 * v[u];
+      const typename F::T h = F::round(y);
+      xb_hi[o + p0] = h;
+      if (PASSES == 3) xb_lo[o + p0] = F::round(y - F::value(h));
     }
-    const bool store = k < nbp_s && (k & 1) == 0;
-    const int64_t o = (int64_t)j0 * nbp + bpad[blockIdx.y] + k;
-#pragma unroll
-    for (int u = 0; u < TC_GJ; ++u) {
-      const float v0 = acc[u] * sd;
-      const float v1 = __shfl_down_sync(0xffffffffu, v0, 1);   // row k + 1 (same warp: k even)
-      if (store && u < jn) {
-        const typename F::T h0 = F::round(v0), h1 = F::round(v1);
-        store_pair(xb_hi + o + (int64_t)u * nbp, h0, h1);
-        if (PASSES == 3)
-          store_pair(xb_lo + o + (int64_t)u * nbp, F::round(v0 - F::value(h0)), F::round(v1 - F::value(h1)));
-      }
+    if (p1 >= 0) {
+      const float y = a1 * v[u];
+      const typename F::T h = F::round(y);
+      xb_hi[o + p1] = h;
+      if (PASSES == 3) xb_lo[o + p1] = F::round(y - F::value(h));
     }
   }
+}
+
+// The interface DOFs with several multiplier rows: x = sqrt(D) sum of the
+// signed rows, one DOF per thread (list bm), TC_GJ directions per thread.
+template <int FMT, int PASSES>
+__global__ void k_gather_multi(int nbm, int m, const int* __restrict__ bm, const int* __restrict__ bpos,
+                               const int* __restrict__ b2l_off, const int* __restrict__ b2l_lam,
+                               const signed char* __restrict__ b2l_sign, const double* __restrict__ sqrtD,
+                               const double* __restrict__ X, int64_t ldx, typename TcFmt<FMT>::T* __restrict__ xb_hi,
+                               typename TcFmt<FMT>::T* __restrict__ xb_lo, int64_t nbp) {
+  using F = TcFmt<FMT>;
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= nbm) return;
+  const int b = bm[i], p = bpos[i];
+  const int j0 = blockIdx.y * TC_GJ;
+  const int jn = min(TC_GJ, m - j0);
+  const float sd = f64_to_f32_rn(sqrtD[b]);
+  float acc[TC_GJ];
+#pragma unroll
+  for (int u = 0; u < TC_GJ; ++u) acc[u] = 0.0f;
+  for (int q = b2l_off[b]; q < b2l_off[b + 1]; ++q) {
+    const double* x = X + b2l_lam[q] + (int64_t)j0 * ldx;
+    const bool pos = b2l_sign[q] > 0;
+#pragma unroll
+    for (int u = 0; u < TC_GJ; ++u)
+      if (u < jn) {
+        const float xv = f64_to_f32_rn(x[(int64_t)u * ldx]);
+        acc[u] += pos ? xv : -xv;
+      }
+  }
+#pragma unroll
+  for (int u = 0; u < TC_GJ; ++u) {
+    if (u >= jn) break;
+    const float y = acc[u] * sd;
+    const int64_t o = (int64_t)(j0 + u) * nbp + p;
+    const typename F::T h = F::round(y);
+    xb_hi[o] = h;
+    if (PASSES == 3) xb_lo[o] = F::round(y - F::value(h));
+  }
+}
+
+// w0(l), w1(l) = sign * sqrt(D) of the entries of multiplier row l, in FP32
+// (refreshed at every factorization with the new diagonal).
+__global__ void k_spread_weights(int64_t nl, const int* __restrict__ b0, const signed char* __restrict__ s0,
+                                 const int* __restrict__ b1, const signed char* __restrict__ s1,
+                                 const double* __restrict__ sqrtD, float* __restrict__ w0, float* __restrict__ w1) {
+  const int64_t l = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (l >= nl) return;
+  const float d0 = f64_to_f32_rn(sqrtD[b0[l]]);
+  w0[l] = s0[l] < 0 ? -d0 : d0;
+  const int q = b1[l];
+  float d1 = 0.0f;
+  if (q >= 0) {
+    d1 = f64_to_f32_rn(sqrtD[q]);
+    if (s1[l] < 0) d1 = -d1;
+  }
+  w1[l] = d1;
 }
 
 // A operand: arena rows of Fhat_s = D^{-1/2} F_s D^{-1/2} in the operand
@@ -1034,6 +1050,10 @@ cudaError_t tc_prepare(const Ctx& c, cudaStream_t st) {
   k_sqrt_diag<<<dim3((c.max_nb + 127) / 128, c.hp.n_sub), 128, 0, st>>>(c.d_types, c.d_mods, c.d_subs, c.d_modmem,
                                                                         c.d_sqrtDF, c.d_sqrtDS);
   note_launches(1);
+  const int64_t nl = c.hp.n_lam;
+  k_spread_weights<<<(unsigned)((nl + 255) / 256), 256, 0, st>>>(nl, c.d_lam_b0, c.d_lam_s0, c.d_lam_b1, c.d_lam_s1,
+                                                                 c.d_sqrtDF, c.d_lam_w0f, c.d_lam_w1f);
+  note_launches(1);
   return cudaGetLastError();
 }
 
@@ -1128,11 +1148,18 @@ cudaError_t launch_tc_p(const Ctx& c, int m, float* Yb, cudaStream_t st, bool co
 template <int FMT, int PASSES>
 void launch_gather(const Ctx& c, const double* X, int64_t ldx, int m, cudaStream_t st) {
   using T = typename TcFmt<FMT>::T;
-  const int max_nbp = k_extent(c.max_nb, 0, 0, TcFmt<FMT>::KC);
-  dim3 g((max_nbp + 127) / 128, c.hp.n_sub, (m + TC_GZ - 1) / TC_GZ);
-  k_gather_tc<FMT, PASSES><<<g, 128, 0, st>>>(c.d_types, c.d_subs, c.d_bpad, X, ldx, m, c.d_b2l_first, c.d_b2l_off,
-                                              c.d_b2l_lam, c.d_b2l_sign, c.d_sqrtDF, static_cast<T*>(c.d_xb_hi),
+  const int64_t nl = c.hp.n_lam;
+  dim3 g((unsigned)((nl + 255) / 256), (m + TC_GJ - 1) / TC_GJ);
+  k_spread_tc<FMT, PASSES><<<g, 256, 0, st>>>(nl, m, c.d_lam_xp0, c.d_lam_xp1, c.d_lam_w0f, c.d_lam_w1f, X, ldx,
+                                              static_cast<T*>(c.d_xb_hi),
                                               PASSES == 3 ? static_cast<T*>(c.d_xb_lo) : nullptr, c.nbp_total);
+  if (c.n_bmulti > 0) {
+    dim3 gm((unsigned)((c.n_bmulti + 127) / 128), (m + TC_GJ - 1) / TC_GJ);
+    k_gather_multi<FMT, PASSES><<<gm, 128, 0, st>>>(c.n_bmulti, m, c.d_bmulti, c.d_bmulti_pos, c.d_b2l_off,
+                                                    c.d_b2l_lam, c.d_b2l_sign, c.d_sqrtDF, X, ldx,
+                                                    static_cast<T*>(c.d_xb_hi),
+                                                    PASSES == 3 ? static_cast<T*>(c.d_xb_lo) : nullptr, c.nbp_total);
+  }
 }
 
 template <int FMT, int PASSES>
@@ -1203,7 +1230,7 @@ cudaError_t tc_gather(const Ctx& c, const double* X, int64_t ldx, int m, cudaStr
   const bool split = tc_split(c);
   if (f == 0) split ? launch_gather<0, 3>(c, X, ldx, m, st) : launch_gather<0, 1>(c, X, ldx, m, st);
   else split ? launch_gather<1, 3>(c, X, ldx, m, st) : launch_gather<1, 1>(c, X, ldx, m, st);
-  note_launches(1);
+  note_launches(c.n_bmulti > 0 ? 2 : 1);
   return cudaGetLastError();
 }
 
