@@ -637,6 +637,8 @@ def compare_batch(a, fg, torch, dev, stream, krylov="pcg"):
                       "f_applies_per_s": sum(r[3].f_applies for r in res) / (e[1].elapsed_time(e[2]) / 1e3)}
     out["batched"]["problems_per_s"] = len(probs) / (out["batched"]["total_ms"] / 1e3)
     out["batched"]["phases"] = batch_phases
+    out["batched"]["autotuned"] = {"gemv_config": fg.feti_query(ctx, fg.FETI_Q_GEMV_CONFIG),
+                                   "row_tile": fg.feti_query(ctx, fg.FETI_Q_BATCH_ROW_TILE)}
     u_b = u_b.cpu().numpy()
     offs = [r[0] for r in res]
     fg.feti_destroy(ctx)

@@ -277,9 +277,13 @@ enum {
                                   (every module's scaled blocks, all parts), read once per apply */
   FETI_Q_TC_BYTES_PER_COL = 14, /* reduced precision: bytes the product moves per direction: the
                                    gathered operand in (all parts) and the FP32 interface result out */
-  FETI_Q_APPLY1_BYTES = 15     /* FP64: algorithmic bytes of a one-direction dual-operator apply (PCG):
+  FETI_Q_APPLY1_BYTES = 15,    /* FP64: algorithmic bytes of a one-direction dual-operator apply (PCG):
                                   every distinct module's F_s and F_rc read once, the coarse inverse
                                   (FETI-DP), the multiplier and interface vectors in and out */
+  FETI_Q_BATCH_ROW_TILE = 16   /* batches, Algorithm 1: multiplier rows per work item of the block
+                                  updates (W T, Q T, W -= W_j Psi_j), autotuned on the first batched
+                                  solve by timing 1024..16384 (the split of the rows into work items
+                                  changes the time, not the result); 0 before it */
 };
 feti_status feti_query(const feti_ctx* ctx, int key, int64_t* value);
 

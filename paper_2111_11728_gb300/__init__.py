@@ -26,7 +26,8 @@ FETI_PRECOND_DIRICHLET, FETI_PRECOND_LUMPED, FETI_PRECOND_SUPERLUMPED = 0, 1, 2
 FETI_PRIMAL_CORNERS, FETI_PRIMAL_EDGES, FETI_PRIMAL_ADAPTIVE = 0, 1, 2
 (FETI_Q_N_LAMBDA, FETI_Q_N_SUBDOMAINS, FETI_Q_N_PRIMAL, FETI_Q_N_MODULES, FETI_Q_N_B_TOTAL, FETI_Q_N_DOFS,
  FETI_Q_N_ELEMENTS, FETI_Q_MAX_NB, FETI_Q_DEVICE_BYTES, FETI_Q_N_RBM, FETI_Q_LAUNCHES, FETI_Q_N_PROBLEMS,
- FETI_Q_GEMV_CONFIG, FETI_Q_TC_BYTES_F, FETI_Q_TC_BYTES_PER_COL, FETI_Q_APPLY1_BYTES) = range(16)
+ FETI_Q_GEMV_CONFIG, FETI_Q_TC_BYTES_F, FETI_Q_TC_BYTES_PER_COL, FETI_Q_APPLY1_BYTES,
+ FETI_Q_BATCH_ROW_TILE) = range(17)
 
 STATUS_NAMES = {0: "FETI_OK", 1: "FETI_EINVAL", 2: "FETI_ENOMEM", 3: "FETI_ESTATE", 4: "FETI_ENOTCONV",
                 5: "FETI_EBREAKDOWN", 6: "FETI_ECUDA", 7: "FETI_ENOTSUP",

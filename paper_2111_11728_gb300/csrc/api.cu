@@ -111,7 +111,7 @@ inline int64_t align32(int64_t x) { return (x + 31) / 32 * 32; }
 constexpr int kGgtCols = 64;           // coarse columns per block when G G^T is formed (TFETI)
 constexpr int BATCH_CHUNK = 128;        // columns per dual-operator apply in the batched Algorithm 1
 constexpr int64_t BATCH_KCHUNK = 8192;  // rows per split-K chunk of its Gram products
-constexpr int64_t BATCH_RCHUNK = 4096;  // rows per entry of its block updates
+constexpr int64_t BATCH_RCHUNK = 4096;  // rows per entry of its block updates, until autotuned
 
 feti_status sync_check(Ctx& c) {
   CU(cudaStreamSynchronize(c.stream));
@@ -187,7 +187,7 @@ feti_status ensure_blocks(Ctx& c, int m) {
     TRY(dalloc(c, c.d_ct1, (size_t)c.n_coarse * cap));
     TRY(dalloc(c, c.d_ct2, (size_t)c.n_coarse * cap));
   }
-  if (c.d_Kbar_inv32) TRY(dalloc(c, c.d_coarse_part, (size_t)tc_coarse_split() * np * cap));
+  if (c.d_Kbar_inv32) TRY(dalloc(c, c.d_coarse_part, (size_t)tc_coarse_scratch((int)np, (int)cap)));
   if (c.opt.precision != FETI_FP64) {
     const size_t eb = tc_elem_bytes(c.opt.precision);
     // the padding of the operand stays zero: the gather writes only the DOF slots
@@ -701,6 +701,7 @@ static feti_status setup_impl(Ctx& c, const feti_problem* probs, int n) {
   TRY(dalloc(c, c.d_ft, nbt + c.n_c_total));
   TRY(dalloc(c, c.d_pb0, nbt));
   TRY(dalloc(c, c.d_pb1, nbt));
+  TRY(dalloc(c, c.d_pbh, nbt));
   c.n_coarse = hp.method == FETI_FETIDP ? hp.n_primal : hp.n_rbm * hp.n_sub;
   const int64_t nco = std::max(c.n_coarse, 1);
   // coarse blocks: one per problem (FETI-DP), one for TFETI
@@ -806,23 +807,76 @@ static feti_status setup_impl(Ctx& c, const feti_problem* probs, int n) {
     TRY(upload(c, c.d_frow, frow));
     TRY(upload(c, c.d_bpad, bpad));
     {
-      // operand slots seen from the multiplier rows; DOFs with several rows apart
-      auto xpos = [&](int b) { const int s = hp.b_sub[b]; return (int)(bpad[s] + (b - hp.b_off[s])); };
-      auto single = [&](int b) { return hp.b2l_off[b + 1] - hp.b2l_off[b] == 1; };
-      std::vector<int> xp0(std::max<int64_t>(nl, 1), -1), xp1(std::max<int64_t>(nl, 1), -1), bm, bmp;
-      for (int64_t l = 0; l < nl; ++l) {
-        if (single(hp.lam_b0[l])) xp0[l] = xpos(hp.lam_b0[l]);
-        if (hp.lam_b1[l] >= 0 && single(hp.lam_b1[l])) xp1[l] = xpos(hp.lam_b1[l]);
+      // Operand slots seen from the multiplier rows.  The rows are cut into
+      // ranges of at most kSpreadRows consecutive rows such that every
+      // interface DOF has all its rows in one range (the rows of a shared DOF
+      // are consecutive: they are emitted together); each range lists the
+      // slots whose rows it holds, in slot order, with their signed rows.
+      auto xpos = [&](int b) { const int s = hp.b_sub[b]; return (int64_t)(bpad[s] + (b - hp.b_off[s])); };
+      const int64_t nbt = hp.n_b_total;
+      std::vector<int> cut_bad(nl + 2, 0);    // > 0: no cut between rows l-1 and l
+      for (int64_t b = 0; b < nbt; ++b) {
+        const int q0 = hp.b2l_off[b], q1 = hp.b2l_off[b + 1];
+        if (q1 - q0 < 2) continue;
+        int lo = hp.b2l_lam[q0], hi = lo;
+        for (int q = q0; q < q1; ++q) { lo = std::min(lo, hp.b2l_lam[q]); hi = std::max(hi, hp.b2l_lam[q]); }
+        cut_bad[lo + 1]++;
+        cut_bad[hi + 1]--;
       }
-      for (int64_t b = 0; b < hp.n_b_total; ++b)
-        if (!single((int)b)) { bm.push_back((int)b); bmp.push_back(xpos((int)b)); }
-      c.n_bmulti = (int)bm.size();
-      TRY(upload(c, c.d_lam_xp0, xp0));
-      TRY(upload(c, c.d_lam_xp1, xp1));
-      TRY(upload(c, c.d_bmulti, bm));
-      TRY(upload(c, c.d_bmulti_pos, bmp));
-      TRY(dalloc(c, c.d_lam_w0f, std::max<int64_t>(nl, 1)));
-      TRY(dalloc(c, c.d_lam_w1f, std::max<int64_t>(nl, 1)));
+      for (int64_t l = 1; l <= nl; ++l) cut_bad[l] += cut_bad[l - 1];
+      std::vector<int> row0{0};
+      for (int64_t l0 = 0; l0 < nl;) {
+        int64_t l1 = std::min<int64_t>(l0 + kSpreadRows, nl);
+        while (l1 > l0 && l1 < nl && cut_bad[l1] > 0) --l1;
+        if (l1 == l0) {
+          c.err = "precision form: an interface DOF has multiplier rows more than " +
+                  std::to_string(kSpreadRows) + " rows apart";
+          return FETI_ENOTSUP;
+        }
+        row0.push_back((int)l1);
+        l0 = l1;
+      }
+      const int nr = (int)row0.size() - 1;
+      // slots by range (the range of their first row), then those with one row
+      // before those with several, each by position
+      std::vector<std::vector<std::pair<int64_t, int>>> by_range(nr);
+      {
+        std::vector<int> range_of(std::max<int64_t>(nl, 1));
+        for (int r = 0; r < nr; ++r)
+          for (int l = row0[r]; l < row0[r + 1]; ++l) range_of[l] = r;
+        for (int64_t b = 0; b < nbt; ++b) {
+          if (hp.b2l_off[b + 1] == hp.b2l_off[b]) continue;
+          int lo = hp.b2l_lam[hp.b2l_off[b]];
+          for (int q = hp.b2l_off[b]; q < hp.b2l_off[b + 1]; ++q) lo = std::min(lo, hp.b2l_lam[q]);
+          const bool multi = hp.b2l_off[b + 1] - hp.b2l_off[b] > 1;
+          by_range[range_of[lo]].push_back({xpos((int)b) + (multi ? ((int64_t)1 << 40) : 0), (int)b});
+        }
+      }
+      std::vector<int> slot_off{0}, slot_pos, slot_b, ent_off{0};
+      std::vector<short> ent;
+      for (int r = 0; r < nr; ++r) {
+        std::sort(by_range[r].begin(), by_range[r].end());
+        for (const auto& pb : by_range[r]) {
+          const int b = pb.second;
+          slot_pos.push_back((int)(pb.first & (((int64_t)1 << 40) - 1)));
+          slot_b.push_back(b);
+          for (int q = hp.b2l_off[b]; q < hp.b2l_off[b + 1]; ++q) {
+            const int rel = hp.b2l_lam[q] - row0[r];
+            ent.push_back((short)(hp.b2l_sign[q] > 0 ? rel : ~rel));
+          }
+          ent_off.push_back((int)ent.size());
+        }
+        slot_off.push_back((int)slot_pos.size());
+      }
+      c.n_spread_ranges = nr;
+      c.n_spread_slots = (int)slot_pos.size();
+      TRY(upload(c, c.d_sp_row0, row0));
+      TRY(upload(c, c.d_sp_slot_off, slot_off));
+      TRY(upload(c, c.d_sp_pos, slot_pos));
+      TRY(upload(c, c.d_sp_b, slot_b));
+      TRY(upload(c, c.d_sp_ent_off, ent_off));
+      TRY(upload(c, c.d_sp_ent, ent));
+      TRY(dalloc(c, c.d_sp_sd, std::max<size_t>(slot_pos.size(), 1)));
     }
     const size_t fa_bytes = (size_t)(c.fa_rows * c.fa_pitch) * tc_elem_bytes(c.opt.precision);
     TRY(dalloc_bytes(c, c.d_fa_hi, fa_bytes));
@@ -1404,19 +1458,57 @@ static feti_status batch_rrs(Ctx& c, double tol, int max_iter, feti_stats& S) {
     hk.push_back(ki);
     hoff.push_back(oi);
     // W_i = W_p[:, perm_p] U_p and Q_i likewise (U_p upper triangular)
-    rows.clear();
-    for (int pass = 0; pass < 2; ++pass)
-      for (int p = 0; p < np; ++p) {
-        if (ki[p] <= 0) continue;
-        for (int64_t r0 = 0; r0 < nlp[p]; r0 += BATCH_RCHUNK) {
-          GemmDesc d{};
-          d.A = (pass ? Q : W) + l0[p] + r0; d.ars = 1; d.acs = nl; d.acol = c.d_bk_perm + moff[p];
-          d.B = c.d_bk_T + doff[p]; d.brs = 1; d.bcs = mp[p];
-          d.C = (pass ? Qi : Wi) + oi[p] + r0; d.crs = 1; d.ccs = nlp[p];
-          d.M = (int)std::min<int64_t>(BATCH_RCHUNK, nlp[p] - r0); d.N = ki[p]; d.K = ki[p]; d.tri = 2;
-          rows.push_back(d);
+    auto transform_rows = [&](int64_t rt) {
+      rows.clear();
+      for (int pass = 0; pass < 2; ++pass)
+        for (int p = 0; p < np; ++p) {
+          if (ki[p] <= 0) continue;
+          for (int64_t r0 = 0; r0 < nlp[p]; r0 += rt) {
+            GemmDesc d{};
+            d.A = (pass ? Q : W) + l0[p] + r0; d.ars = 1; d.acs = nl; d.acol = c.d_bk_perm + moff[p];
+            d.B = c.d_bk_T + doff[p]; d.brs = 1; d.bcs = mp[p];
+            d.C = (pass ? Qi : Wi) + oi[p] + r0; d.crs = 1; d.ccs = nlp[p];
+            d.M = (int)std::min<int64_t>(rt, nlp[p] - r0); d.N = ki[p]; d.K = ki[p]; d.tri = 2;
+            rows.push_back(d);
+          }
         }
+    };
+    if (c.bk_rtile == 0) {
+      // Autotune the row tile of the block updates on this batch's first
+      // transform: every candidate computes the same rows in the same order
+      // (only the split of the rows into work items differs), so the choice
+      // changes the time, never the result.
+      const int64_t cands[5] = {1024, 2048, 4096, 8192, 16384};
+      cudaEvent_t e0, e1;
+      CU(cudaEventCreate(&e0));
+      CU(cudaEventCreate(&e1));
+      float best = 1e30f;
+      int64_t best_rt = BATCH_RCHUNK;
+      feti_status tst = FETI_OK;
+      for (int ci = 0; ci < 5 && tst == FETI_OK; ++ci) {
+        transform_rows(cands[ci]);
+        if (rows.size() > 65535) continue;
+        float ts[3];
+        for (int r = 0; r < 3 && tst == FETI_OK; ++r) {
+          cudaEventRecord(e0, st);
+          tst = run_row_chunks(c, rows, 1.0, 0.0);
+          cudaEventRecord(e1, st);
+          if (tst == FETI_OK && cudaEventSynchronize(e1) != cudaSuccess) {
+            c.err = "batched Algorithm 1: row-tile autotuning failed";
+            tst = FETI_ECUDA;
+          }
+          if (tst == FETI_OK) cudaEventElapsedTime(&ts[r], e0, e1);
+        }
+        if (tst != FETI_OK) break;
+        std::sort(ts, ts + 3);
+        if (ts[1] < best) { best = ts[1]; best_rt = cands[ci]; }
       }
+      cudaEventDestroy(e0);
+      cudaEventDestroy(e1);
+      TRY(tst);
+      c.bk_rtile = best_rt;
+    }
+    transform_rows(c.bk_rtile);
     {
       double fl = 0.0;
       for (int p = 0; p < np; ++p) fl += 2.0 * nlp[p] * ki[p] * (ki[p] + 1.0);
@@ -1457,12 +1549,12 @@ static feti_status batch_rrs(Ctx& c, double tol, int max_iter, feti_stats& S) {
         const double* Wj = c.bk_hW[j] + hoff[j][p];
         double* Psi = c.d_bk_delta + doff[p];            // k_j x m_p, ld k_j
         ops.push_back(SegTN{Qj, nlp[p], W + l0[p], nl, Psi, kj, kj, mp[p], nlp[p], 0});
-        for (int64_t r0 = 0; r0 < nlp[p]; r0 += BATCH_RCHUNK) {
+        for (int64_t r0 = 0; r0 < nlp[p]; r0 += c.bk_rtile) {
           GemmDesc d{};
           d.A = Wj + r0; d.ars = 1; d.acs = nlp[p];
           d.B = Psi; d.brs = 1; d.bcs = kj;
           d.C = W + l0[p] + r0; d.crs = 1; d.ccs = nl;
-          d.M = (int)std::min<int64_t>(BATCH_RCHUNK, nlp[p] - r0); d.N = mp[p]; d.K = kj;
+          d.M = (int)std::min<int64_t>(c.bk_rtile, nlp[p] - r0); d.N = mp[p]; d.K = kj;
           rows.push_back(d);
         }
       }
@@ -1792,6 +1884,7 @@ feti_status feti_query(const feti_ctx* ctx, int key, int64_t* value) {
     case FETI_Q_LAUNCHES: *value = launches(); break;
     case FETI_Q_N_PROBLEMS: *value = hp.n_prob; break;
     case FETI_Q_GEMV_CONFIG: *value = c.gemv_cfg; break;
+    case FETI_Q_BATCH_ROW_TILE: *value = c.bk_rtile; break;
     case FETI_Q_TC_BYTES_F: *value = c.tc_bytes_f; break;
     case FETI_Q_TC_BYTES_PER_COL: *value = c.tc_bytes_col; break;
     case FETI_Q_APPLY1_BYTES: *value = (int64_t)c.bytes_apply1; break;

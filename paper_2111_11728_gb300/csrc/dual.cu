@@ -533,7 +533,7 @@ cudaError_t precond_apply_lowp(Ctx& c, const double* r, double* Z, int64_t ldz, 
   note_launches(1);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
-  e = lowp_gemv_S(c, rb, zb, st);
+  e = lowp_gemv_S(c, rb, c.d_pbh, zb, st);
   if (e != cudaSuccess) return e;
   if (Z) {
     e = cudaMemsetAsync(Z, 0, sizeof(double) * (size_t)ldz * c.hp.n_sub, st);

@@ -211,12 +211,15 @@ struct Ctx {
   signed char *d_lam_s0 = nullptr, *d_lam_s1 = nullptr;
   int *d_group_off = nullptr, *d_group_b = nullptr;
   int *d_b2l_off = nullptr, *d_b2l_lam = nullptr;
-  // precision form, operand from the multiplier side: per row l the operand slots of
-  // its two entries (-1 for an entry whose DOF has several rows) and sign * sqrt(D)
-  int *d_lam_xp0 = nullptr, *d_lam_xp1 = nullptr;
-  float *d_lam_w0f = nullptr, *d_lam_w1f = nullptr;
-  int *d_bmulti = nullptr, *d_bmulti_pos = nullptr;   // DOFs with several rows, their operand slots
-  int n_bmulti = 0;
+  // precision form, operand built from the multiplier side: ranges of consecutive
+  // rows (d_sp_row0), the operand slots whose rows lie in each range
+  // (d_sp_slot_off: position, interface DOF, FP32 sqrt(D)) and each slot's rows
+  // relative to its range (d_sp_ent_off; ~rel for a row entering with sign -1)
+  int *d_sp_row0 = nullptr, *d_sp_slot_off = nullptr, *d_sp_pos = nullptr, *d_sp_b = nullptr;
+  int* d_sp_ent_off = nullptr;
+  short* d_sp_ent = nullptr;
+  float* d_sp_sd = nullptr;
+  int n_spread_ranges = 0, n_spread_slots = 0;
   signed char* d_b2l_sign = nullptr;
   int* d_b_sub = nullptr;
   int* d_c_glob = nullptr;
@@ -243,7 +246,7 @@ struct Ctx {
   double* d_Kbar_L = nullptr;    // [n_coarse^2] inverse Cholesky factor (work)
   double* d_Kbar_inv = nullptr;  // [n_coarse^2] explicit inverse
   float* d_Kbar_inv32 = nullptr; // precision form, one problem: FP32 copy of the inverse
-  float* d_coarse_part = nullptr;   // its split-K partial products [split x n_primal x blk_cap]
+  float* d_coarse_part = nullptr;   // its split-K partials and FP32 right-hand sides (tc_coarse_scratch)
   double* d_coarse_work = nullptr;   // blocked coarse factorisation work
   // precision form (FETI_TF32)
   float* d_fmem = nullptr;       // FP32 copies at the module offsets: Shat at M.W
@@ -284,6 +287,7 @@ struct Ctx {
   GemmDesc* d_gemm_coarse = nullptr; // per-problem coarse GEMMs (batches)
   DenseDesc* d_dense_coarse_batch = nullptr;
   int max_np = 0;
+  int64_t bk_rtile = 0;             // autotuned row tile of the batched Algorithm 1's block updates (0: not yet)
   int gemv_cfg = 0;                  // autotuned launch shape of the per-subdomain GEMV (0: default)
   float gemv_ms = 0.f;
   // batched PCG state
@@ -316,6 +320,7 @@ struct Ctx {
   int blk_cap = 0;
   double *d_Xb = nullptr, *d_Yb = nullptr, *d_Cb = nullptr, *d_Vraw = nullptr, *d_V = nullptr, *d_Vc = nullptr;
   double *d_pb0 = nullptr, *d_pb1 = nullptr;   // [n_b_total] vectors
+  float* d_pbh = nullptr;                      // [n_b_total] FP32 scratch (precision form)
   // GEMM descriptors (device)
   GemmDesc *d_gemm_F = nullptr, *d_gemm_FrcT = nullptr, *d_gemm_Frc = nullptr;
   GemmDesc *d_gemm_schur = nullptr, *d_gemm_frcmake = nullptr, *d_gemm_kbmake = nullptr;

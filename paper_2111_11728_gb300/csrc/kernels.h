@@ -194,11 +194,13 @@ size_t tc_apply_smem_bytes(int passes);
 int tc_tile_rows();                     // rows of one tensor-core tile (and of a module's corner block)
 cudaError_t tc_prepare(const Ctx& c, cudaStream_t st);   // Fhat, Shat (FP32) and sqrt-diagonals
 // Yb = D^{1/2} Fhat D^{1/2} B^T X (tcgen05 kind::tf32); rows >= n_b untouched
+// Multiplier rows per range of the precision form's operand construction.
+constexpr int kSpreadRows = 128;
 cudaError_t tc_gather(const Ctx& c, const double* X, int64_t ldx, int m, cudaStream_t st);
 cudaError_t tc_corner_reduce(const Ctx& c, int m, double* Vraw, cudaStream_t st);
 cudaError_t tc_put_v(const Ctx& c, const double* V, int m, cudaStream_t st);
 cudaError_t tc_coarse_prepare(const Ctx& c, cudaStream_t st);   // FP32 copy of Kbar_cc^{-1}
-int tc_coarse_split();   // K ranges of the FP32 coarse product (partials per column block)
+int64_t tc_coarse_scratch(int n, int cap);   // floats of the FP32 coarse product's scratch
 cudaError_t tc_coarse_apply(const Ctx& c, const double* Vraw, double* V, int m, cudaStream_t st);
 cudaError_t tc_prepare_tiles(Ctx& c, int m);   // work list of the persistent product for m directions
 cudaError_t tc_product(const Ctx& c, int m, float* Yb, cudaStream_t st);
@@ -207,7 +209,7 @@ int tc_k_extent(int nb, int nc, int aug, int kc);
 int tc_chunk(int precision);            // K chunk of the operand format: 32 (TF32) or 64 (BF16)
 size_t tc_elem_bytes(int precision);    // 4 (TF32) or 2 (BF16)
 cudaError_t corner_assemble(const Ctx& c, int m, double* Vraw, cudaStream_t st);
-cudaError_t lowp_gemv_S(const Ctx& c, const double* xb, double* yb, cudaStream_t st);
+cudaError_t lowp_gemv_S(const Ctx& c, const double* xb, float* xh, double* yb, cudaStream_t st);
 // Yb(s) += F_rc,s V[c_glob(s), :] with a thin kernel (no tile padding)
 cudaError_t corner_expand_thin(Ctx& c, const double* V, int m, double* Yb, cudaStream_t st);
 cudaError_t precond_apply_lowp(Ctx& c, const double* r, double* Z, int64_t ldz, double* z, cudaStream_t st);

@@ -561,105 +561,102 @@ __global__ void __launch_bounds__(TCP_THREADS, 1) k_tc_apply_p(
 // B operand: xb[j][bpad(s) + k] = parts of sqrt(D_s)[k] (B^sT X)[b, j] in
 // the operand format for k < n_b(s), zero for the padding up to the next
 // multiple of the format's chunk (zeroed once when the buffer is allocated).
-constexpr int TC_GJ = 8;              // directions per thread
+constexpr int SP_J = 32;               // directions per block
+constexpr int SP_THREADS = 512;
+constexpr int SP_LD = SP_J * kSpreadRows / SP_THREADS;   // loads per thread
+constexpr int SP_QL = 64;              // slots handled side by side
+constexpr int SP_ME = 4;               // rows of a cross-point slot held in registers
 
-// It is built from the multiplier side: one multiplier row l per
-// thread reads X(l, j) once (consecutive threads, consecutive rows: coalesced)
-// and writes w0(l) X(l, j) and w1(l) X(l, j) to the operand slots xp0(l) and
-// xp1(l) of its two entries, w = sign * sqrt(D) of the entry.  Only entries
-// whose interface DOF has this single multiplier row get a slot (-1
-// otherwise); the DOFs with several rows (cross points) are summed by
-// k_gather_multi.  TC_GJ directions per thread.
+// It is built from the multiplier side, one range of consecutive multiplier
+// rows (at most kSpreadRows, every interface DOF's rows inside one range) and
+// SP_J directions per block: the block reads X(l, j) of its rows once
+// (consecutive threads, consecutive rows: coalesced; all SP_LD loads of a
+// thread in flight together; FP64 -> FP32) into shared memory, then writes
+// every operand slot of the range, x = sqrt(D) * (sum of its signed rows):
+// SP_QL consecutive slots side by side (those with one row first, each class
+// in position order), each group of SP_QL threads a share of the directions.
+// A DOF with one row takes that row, a cross-point DOF the sum of its rows,
+// summed in the order of its row list.
 template <int FMT, int PASSES>
-__global__ void k_spread_tc(int64_t nl, int m, const int* __restrict__ xp0, const int* __restrict__ xp1,
-                            const float* __restrict__ w0, const float* __restrict__ w1,
-                            const double* __restrict__ X, int64_t ldx, typename TcFmt<FMT>::T* __restrict__ xb_hi,
-                            typename TcFmt<FMT>::T* __restrict__ xb_lo, int64_t nbp) {
+__global__ void __launch_bounds__(SP_THREADS) k_spread_tc(int m, const int* __restrict__ row0,
+                                                          const int* __restrict__ slot_off,
+                                                          const int* __restrict__ pos, const float* __restrict__ sd,
+                                                          const int* __restrict__ ent_off,
+                                                          const short* __restrict__ ent,
+                                                          const double* __restrict__ X, int64_t ldx,
+                                                          typename TcFmt<FMT>::T* __restrict__ xb_hi,
+                                                          typename TcFmt<FMT>::T* __restrict__ xb_lo, int64_t nbp) {
   using F = TcFmt<FMT>;
-  const int64_t l = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (l >= nl) return;
-  const int p0 = xp0[l], p1 = xp1[l];
-  if (p0 < 0 && p1 < 0) return;
-  const float a0 = w0[l], a1 = w1[l];
-  const int j0 = blockIdx.y * TC_GJ;
-  const int jn = min(TC_GJ, m - j0);
-  float v[TC_GJ];
+  static_assert(SP_THREADS % kSpreadRows == 0 && SP_THREADS % SP_QL == 0, "block shape");
+  constexpr int CSTEP = SP_THREADS / kSpreadRows, NG = SP_THREADS / SP_QL;
+  __shared__ float xs[SP_J][kSpreadRows + 1];
+  const int r = blockIdx.x;
+  const int l0 = row0[r], nr = row0[r + 1] - l0;
+  const int j0 = blockIdx.y * SP_J, jn = min(SP_J, m - j0);
+  {
+    const int i = threadIdx.x % kSpreadRows, cb = threadIdx.x / kSpreadRows;
+    double v[SP_LD];
+    const double* x = X + (int64_t)(l0 + i) + (int64_t)(j0 + cb) * ldx;
 #pragma unroll
-  for (int u = 0; u < TC_GJ; ++u) v[u] = u < jn ? f64_to_f32_rn(X[l + (int64_t)(j0 + u) * ldx]) : 0.0f;
+    for (int t = 0; t < SP_LD; ++t)
+      v[t] = (i < nr && cb + CSTEP * t < jn) ? __ldcs(x + (int64_t)(CSTEP * t) * ldx) : 0.0;
 #pragma unroll
-  for (int u = 0; u < TC_GJ; ++u) {
-    if (u >= jn) break;
-    const int64_t o = (int64_t)(j0 + u) * nbp;
-    if (p0 >= 0) {
-      const float y = a0 * v[u];
-      const typename F::T h = F::round(y);
-      xb_hi[o + p0] = h;
-      if (PASSES == 3) xb_lo[o + p0] = F::round(y - F::value(h));
-    }
-    if (p1 >= 0) {
-      const float y = a1 * v[u];
-      const typename F::T h = F::round(y);
-      xb_hi[o + p1] = h;
-      if (PASSES == 3) xb_lo[o + p1] = F::round(y - F::value(h));
-    }
+    for (int t = 0; t < SP_LD; ++t) xs[cb + CSTEP * t][i] = f64_to_f32_rn(v[t]);
   }
-}
-
-// The interface DOFs with several multiplier rows: x = sqrt(D) sum of the
-// signed rows, one DOF per thread (list bm), TC_GJ directions per thread.
-template <int FMT, int PASSES>
-__global__ void k_gather_multi(int nbm, int m, const int* __restrict__ bm, const int* __restrict__ bpos,
-                               const int* __restrict__ b2l_off, const int* __restrict__ b2l_lam,
-                               const signed char* __restrict__ b2l_sign, const double* __restrict__ sqrtD,
-                               const double* __restrict__ X, int64_t ldx, typename TcFmt<FMT>::T* __restrict__ xb_hi,
-                               typename TcFmt<FMT>::T* __restrict__ xb_lo, int64_t nbp) {
-  using F = TcFmt<FMT>;
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= nbm) return;
-  const int b = bm[i], p = bpos[i];
-  const int j0 = blockIdx.y * TC_GJ;
-  const int jn = min(TC_GJ, m - j0);
-  const float sd = f64_to_f32_rn(sqrtD[b]);
-  float acc[TC_GJ];
+  __syncthreads();
+  const int q0 = slot_off[r], nq = slot_off[r + 1] - q0;
+  const int g = threadIdx.x / SP_QL;
+  constexpr int PER = SP_J / NG;
+  const int64_t cstride = (int64_t)NG * nbp;
+  for (int qq = threadIdx.x % SP_QL; qq < nq; qq += SP_QL) {
+    const int q = q0 + qq;
+    const int e0 = ent_off[q], ne = ent_off[q + 1] - e0;
+    const float w = sd[q];
+    const int64_t o0 = (int64_t)(j0 + g) * nbp + pos[q];
+    const float* xg = &xs[g][0];
+    if (ne == 1) {                       // one row: a signed copy
+      const int u = ent[e0];
+      const float* xr = xg + (u >= 0 ? u : ~u);
+      const float ws = u >= 0 ? w : -w;
 #pragma unroll
-  for (int u = 0; u < TC_GJ; ++u) acc[u] = 0.0f;
-  for (int q = b2l_off[b]; q < b2l_off[b + 1]; ++q) {
-    const double* x = X + b2l_lam[q] + (int64_t)j0 * ldx;
-    const bool pos = b2l_sign[q] > 0;
-#pragma unroll
-    for (int u = 0; u < TC_GJ; ++u)
-      if (u < jn) {
-        const float xv = f64_to_f32_rn(x[(int64_t)u * ldx]);
-        acc[u] += pos ? xv : -xv;
+      for (int t = 0; t < PER; ++t) {
+        if (g + NG * t >= jn) break;
+        const float y = xr[t * NG * (kSpreadRows + 1)] * ws;
+        const typename F::T h = F::round(y);
+        xb_hi[o0 + t * cstride] = h;
+        if (PASSES == 3) xb_lo[o0 + t * cstride] = F::round(y - F::value(h));
       }
-  }
+    } else {                             // several rows, summed in list order
+      int ev[SP_ME];
 #pragma unroll
-  for (int u = 0; u < TC_GJ; ++u) {
-    if (u >= jn) break;
-    const float y = acc[u] * sd;
-    const int64_t o = (int64_t)(j0 + u) * nbp + p;
-    const typename F::T h = F::round(y);
-    xb_hi[o] = h;
-    if (PASSES == 3) xb_lo[o] = F::round(y - F::value(h));
+      for (int k = 0; k < SP_ME; ++k) ev[k] = k < ne ? ent[e0 + k] : 0;
+#pragma unroll
+      for (int t = 0; t < PER; ++t) {
+        if (g + NG * t >= jn) break;
+        const float* xc = xg + t * NG * (kSpreadRows + 1);
+        float acc = 0.0f;
+#pragma unroll
+        for (int k = 0; k < SP_ME; ++k)
+          if (k < ne) acc += ev[k] >= 0 ? xc[ev[k]] : -xc[~ev[k]];
+        for (int k = SP_ME; k < ne; ++k) {
+          const int u = ent[e0 + k];
+          acc += u >= 0 ? xc[u] : -xc[~u];
+        }
+        const float y = acc * w;
+        const typename F::T h = F::round(y);
+        xb_hi[o0 + t * cstride] = h;
+        if (PASSES == 3) xb_lo[o0 + t * cstride] = F::round(y - F::value(h));
+      }
+    }
   }
 }
 
-// w0(l), w1(l) = sign * sqrt(D) of the entries of multiplier row l, in FP32
-// (refreshed at every factorization with the new diagonal).
-__global__ void k_spread_weights(int64_t nl, const int* __restrict__ b0, const signed char* __restrict__ s0,
-                                 const int* __restrict__ b1, const signed char* __restrict__ s1,
-                                 const double* __restrict__ sqrtD, float* __restrict__ w0, float* __restrict__ w1) {
-  const int64_t l = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (l >= nl) return;
-  const float d0 = f64_to_f32_rn(sqrtD[b0[l]]);
-  w0[l] = s0[l] < 0 ? -d0 : d0;
-  const int q = b1[l];
-  float d1 = 0.0f;
-  if (q >= 0) {
-    d1 = f64_to_f32_rn(sqrtD[q]);
-    if (s1[l] < 0) d1 = -d1;
-  }
-  w1[l] = d1;
+// sqrt(D) of every operand slot's interface DOF in FP32 (refreshed at every
+// factorization with the new diagonal).
+__global__ void k_spread_weights(int n, const int* __restrict__ b, const double* __restrict__ sqrtD,
+                                 float* __restrict__ sd) {
+  const int q = blockIdx.x * blockDim.x + threadIdx.x;
+  if (q < n) sd[q] = f64_to_f32_rn(sqrtD[b[q]]);
 }
 
 // A operand: arena rows of Fhat_s = D^{-1/2} F_s D^{-1/2} in the operand
@@ -845,7 +842,9 @@ __global__ void __launch_bounds__(256) k_frct_lowp(const DevType* __restrict__ t
 
 // The K-extension of the operand: V_s (the coarse correction at the
 // subdomain's corners) in the chunks after its b range, zero past n_c.
-// blockDim.x covers the widest extension; each subdomain writes its own.
+// blockDim.x covers the widest extension; each subdomain (blockIdx.y) writes
+// its own, PV_J directions per block.
+constexpr int PV_J = 64;
 template <int FMT, int PASSES>
 __global__ void k_put_v(const DevType* __restrict__ types, const DevSub* __restrict__ subs,
                         const int64_t* __restrict__ bpad, const int* __restrict__ cg, const double* __restrict__ V,
@@ -854,13 +853,18 @@ __global__ void k_put_v(const DevType* __restrict__ types, const DevSub* __restr
   using F = TcFmt<FMT>;
   const DevSub S = subs[blockIdx.y];
   const DevType T = types[S.type];
-  const int c = threadIdx.x, j = blockIdx.x * blockDim.y + threadIdx.y;
-  if (j >= m || T.n_c == 0 || c >= (T.n_c + F::KC - 1) / F::KC * F::KC) return;
-  const float v = c < T.n_c ? static_cast<float>(V[cg[S.c_off + c] + (int64_t)j * np]) : 0.0f;
-  const int64_t o = (int64_t)j * nbp + bpad[blockIdx.y] + k_extent(T.n_b, 0, 0, F::KC) + c;
-  const typename F::T hi = F::round(v);
-  xb_hi[o] = hi;
-  if (PASSES == 3) xb_lo[o] = F::round(v - F::value(hi));
+  const int c = threadIdx.x;
+  if (T.n_c == 0 || c >= (T.n_c + F::KC - 1) / F::KC * F::KC) return;
+  const int cgl = c < T.n_c ? cg[S.c_off + c] : 0;
+  const int64_t o0 = bpad[blockIdx.y] + k_extent(T.n_b, 0, 0, F::KC) + c;
+  const int j1 = min(m, (int)(blockIdx.x + 1) * PV_J);
+  for (int j = blockIdx.x * PV_J + threadIdx.y; j < j1; j += blockDim.y) {
+    const float v = c < T.n_c ? f64_to_f32_rn(V[cgl + (int64_t)j * np]) : 0.0f;
+    const int64_t o = (int64_t)j * nbp + o0;
+    const typename F::T hi = F::round(v);
+    xb_hi[o] = hi;
+    if (PASSES == 3) xb_lo[o] = F::round(v - F::value(hi));
+  }
 }
 
 // FP32 copy of the coarse inverse (precision form).
@@ -871,66 +875,103 @@ __global__ void k_to_f32(int64_t n, const double* __restrict__ x, float* __restr
 
 // V = Kbar^{-1} Vraw in FP32 arithmetic (the precision form's coarse
 // correction).  A = Kbar^{-1} in FP32 (n x n, symmetric: read as row k gives
-// column k), B = Vraw FP64 column-major (n x m, ld n).  64 x 64 output tiles,
-// 256 threads with 4 x 4 outputs each, K staged 16 at a time and split in
-// CG_SPLIT ranges (blockIdx.z) whose FP32 partial products go to P
-// [CG_SPLIT x n x m]; k_coarse_sum adds them in a fixed order into V (FP64).
-constexpr int CG_T = 64, CG_K = 16, CG_SPLIT = 8;
-__global__ void __launch_bounds__(256) k_sgemm_coarse(int n, int m, const float* __restrict__ A,
-                                                      const double* __restrict__ B, float* __restrict__ P) {
-  __shared__ __align__(16) float As[CG_K][CG_T];
-  __shared__ __align__(16) float Bs[CG_K][CG_T];
+// column k), B = Vraw in FP32 (n x m, column-major, ld n).  128 x 128 output
+// tiles, 256 threads with 8 x 8 outputs each (rows tx*4.. and 64+tx*4.., so
+// that every thread stores four consecutive rows of a column at once), K
+// staged CG_K at a time (the next stage loaded into registers while the
+// current one is multiplied), split in CG_SPLIT ranges (blockIdx.z) whose FP32
+// partial products go to P [CG_SPLIT x m x ldp], ldp = n rounded up to 4;
+// k_coarse_sum adds them in a fixed order into V (FP64).
+constexpr int CG_T = 128, CG_K = 8, CG_SPLIT = 4;
+__global__ void __launch_bounds__(256, 2) k_sgemm_coarse(int n, int m, int ldp, const float* __restrict__ A,
+                                                         const float* __restrict__ B, float* __restrict__ P) {
+  __shared__ __align__(16) float As[2][CG_K][CG_T];
+  __shared__ __align__(16) float Bs[2][CG_K][CG_T];
   const int i0 = blockIdx.x * CG_T, j0 = blockIdx.y * CG_T;
   const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
-  float acc[4][4];
+  float acc[8][8];
 #pragma unroll
-  for (int r = 0; r < 4; ++r)
+  for (int r = 0; r < 8; ++r)
 #pragma unroll
-    for (int q = 0; q < 4; ++q) acc[r][q] = 0.0f;
+    for (int q = 0; q < 8; ++q) acc[r][q] = 0.0f;
   const int kper = ((n + CG_SPLIT * CG_K - 1) / (CG_SPLIT * CG_K)) * CG_K;
   const int kbeg = blockIdx.z * kper, kend = min(n, kbeg + kper);
+  float ra[4], rb[4];
+  auto load = [&](int k0) {
+#pragma unroll
+    for (int t = 0; t < 4; ++t) {
+      const int e = tid + 256 * t, ii = e & (CG_T - 1), kk = e >> 7, i = i0 + ii, k = k0 + kk;
+      ra[t] = (i < n && k < kend) ? A[(int64_t)k * n + i] : 0.0f;
+    }
+#pragma unroll
+    for (int t = 0; t < 4; ++t) {
+      const int e = tid + 256 * t, kk = e & (CG_K - 1), jj = e >> 3, k = k0 + kk, j = j0 + jj;
+      rb[t] = (k < kend && j < m) ? B[(int64_t)j * n + k] : 0.0f;
+    }
+  };
+  auto store = [&](int buf) {
+#pragma unroll
+    for (int t = 0; t < 4; ++t) {
+      const int e = tid + 256 * t;
+      As[buf][e >> 7][e & (CG_T - 1)] = ra[t];
+      Bs[buf][e & (CG_K - 1)][e >> 3] = rb[t];
+    }
+  };
+  if (kbeg < kend) {
+    load(kbeg);
+    store(0);
+  }
+  __syncthreads();
+  int buf = 0;
   for (int k0 = kbeg; k0 < kend; k0 += CG_K) {
-    for (int e = tid; e < CG_K * CG_T; e += 256) {
-      const int kk = e / CG_T, ii = e % CG_T, i = i0 + ii, k = k0 + kk;
-      As[kk][ii] = (i < n && k < kend) ? A[(int64_t)k * n + i] : 0.0f;
-    }
-    for (int e = tid; e < CG_K * CG_T; e += 256) {
-      const int kk = e % CG_K, jj = e / CG_K, k = k0 + kk, j = j0 + jj;
-      Bs[kk][jj] = (k < kend && j < m) ? f64_to_f32_rn(B[(int64_t)j * n + k]) : 0.0f;
-    }
-    __syncthreads();
+    const bool more = k0 + CG_K < kend;
+    if (more) load(k0 + CG_K);
 #pragma unroll
     for (int kk = 0; kk < CG_K; ++kk) {
-      const float4 a = *reinterpret_cast<const float4*>(&As[kk][ty * 4]);
-      const float4 b = *reinterpret_cast<const float4*>(&Bs[kk][tx * 4]);
-      const float av[4] = {a.x, a.y, a.z, a.w}, bv[4] = {b.x, b.y, b.z, b.w};
+      const float4 a0 = *reinterpret_cast<const float4*>(&As[buf][kk][tx * 4]);
+      const float4 a1 = *reinterpret_cast<const float4*>(&As[buf][kk][64 + tx * 4]);
+      const float4 b0 = *reinterpret_cast<const float4*>(&Bs[buf][kk][ty * 4]);
+      const float4 b1 = *reinterpret_cast<const float4*>(&Bs[buf][kk][64 + ty * 4]);
+      const float av[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
+      const float bv[8] = {b0.x, b0.y, b0.z, b0.w, b1.x, b1.y, b1.z, b1.w};
 #pragma unroll
-      for (int r = 0; r < 4; ++r)
+      for (int r = 0; r < 8; ++r)
 #pragma unroll
-        for (int q = 0; q < 4; ++q) acc[r][q] = fmaf(av[r], bv[q], acc[r][q]);
+        for (int q = 0; q < 8; ++q) acc[r][q] = fmaf(av[r], bv[q], acc[r][q]);
     }
+    if (more) store(buf ^ 1);
     __syncthreads();
+    buf ^= 1;
   }
-  float* Pz = P + (int64_t)blockIdx.z * n * m;
+  float* Pz = P + (int64_t)blockIdx.z * ldp * m;
 #pragma unroll
-  for (int r = 0; r < 4; ++r) {
-    const int i = i0 + ty * 4 + r;
-    if (i >= n) continue;
+  for (int q = 0; q < 8; ++q) {
+    const int j = j0 + (q < 4 ? ty * 4 + q : 64 + ty * 4 + q - 4);
+    if (j >= m) continue;
 #pragma unroll
-    for (int q = 0; q < 4; ++q) {
-      const int j = j0 + tx * 4 + q;
-      if (j < m) Pz[(int64_t)j * n + i] = acc[r][q];
+    for (int h = 0; h < 2; ++h) {
+      const int i = i0 + h * 64 + tx * 4;          // i, ldp multiples of 4: i < ldp covers i + 3
+      if (i < ldp)
+        *reinterpret_cast<float4*>(Pz + (int64_t)j * ldp + i) =
+            make_float4(acc[4 * h][q], acc[4 * h + 1][q], acc[4 * h + 2][q], acc[4 * h + 3][q]);
     }
   }
 }
 
-__global__ void k_coarse_sum(int64_t nm, const float* __restrict__ P, double* __restrict__ V) {
-  const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (e >= nm) return;
+// V(i, j) = sum over the K ranges z, in order, of P_z(i, j); widened exactly.
+__global__ void k_coarse_sum(int n, int m, int ldp, const float* __restrict__ P, double* __restrict__ V) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x, j = blockIdx.y;
+  if (i >= n) return;
   float v = 0.0f;
 #pragma unroll
-  for (int z = 0; z < CG_SPLIT; ++z) v += P[z * nm + e];
-  V[e] = f32_to_f64(v);
+  for (int z = 0; z < CG_SPLIT; ++z) v += P[((int64_t)z * m + j) * ldp + i];
+  V[(int64_t)j * n + i] = f32_to_f64(v);
+}
+
+// y = x in FP32 on the integer pipe (the coarse product's right-hand sides).
+__global__ void k_f32_of(int64_t n, const double* __restrict__ x, float* __restrict__ y) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i < n) y[i] = f64_to_f32_rn(x[i]);
 }
 
 // Shat = D_S^{-1/2} S_bb D_S^{-1/2} (FP32) per module, for the preconditioner
@@ -974,11 +1015,19 @@ __global__ void k_sqrt_diag(const DevType* __restrict__ types, const DevModule* 
   sqrtDS[S.b_off + k] = sqrt(mem[M.S + (int64_t)k * nbc + k]);
 }
 
-// y_b(s) = D_S^{1/2} Shat_s D_S^{1/2} x_b(s) in FP32 arithmetic (preconditioner
-// block of the precision form), one warp per row.
+// xh = D_S^{1/2} x_b in FP32 (the scaled right-hand side of the
+// preconditioner block, converted once per entry on the integer pipe).
+__global__ void k_scale_x32(int64_t nbt, const double* __restrict__ sqrtDS, const double* __restrict__ x,
+                            float* __restrict__ xh) {
+  const int64_t b = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (b < nbt) xh[b] = f64_to_f32_rn(sqrtDS[b] * x[b]);
+}
+
+// y_b(s) = D_S^{1/2} Shat_s xh(s) in FP32 arithmetic (preconditioner block of
+// the precision form), one warp per row.
 __global__ void k_sub_gemv_lowp(const DevType* __restrict__ types, const DevModule* __restrict__ mods,
                                 const DevSub* __restrict__ subs, const float* __restrict__ fmem,
-                                const double* __restrict__ sqrtDS, const double* __restrict__ x,
+                                const double* __restrict__ sqrtDS, const float* __restrict__ xh,
                                 double* __restrict__ y) {
   const DevSub S = subs[blockIdx.y];
   const DevType T = types[S.type];
@@ -987,12 +1036,11 @@ __global__ void k_sub_gemv_lowp(const DevType* __restrict__ types, const DevModu
   const int n = T.n_b;
   if (row >= n) return;
   const float* a = fmem + mods[S.module].W + (int64_t)row * n;
-  const double* xs = x + S.b_off;
-  const double* ds = sqrtDS + S.b_off;
+  const float* xs = xh + S.b_off;
   float acc = 0.0f;
-  for (int k = lane; k < n; k += 32) acc = fmaf(a[k], static_cast<float>(ds[k] * xs[k]), acc);
+  for (int k = lane; k < n; k += 32) acc = fmaf(a[k], xs[k], acc);
   for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-  if (lane == 0) y[S.b_off + row] = ds[row] * (double)acc;
+  if (lane == 0) y[S.b_off + row] = sqrtDS[S.b_off + row] * f32_to_f64(acc);
 }
 
 }  // namespace
@@ -1050,9 +1098,8 @@ cudaError_t tc_prepare(const Ctx& c, cudaStream_t st) {
   k_sqrt_diag<<<dim3((c.max_nb + 127) / 128, c.hp.n_sub), 128, 0, st>>>(c.d_types, c.d_mods, c.d_subs, c.d_modmem,
                                                                         c.d_sqrtDF, c.d_sqrtDS);
   note_launches(1);
-  const int64_t nl = c.hp.n_lam;
-  k_spread_weights<<<(unsigned)((nl + 255) / 256), 256, 0, st>>>(nl, c.d_lam_b0, c.d_lam_s0, c.d_lam_b1, c.d_lam_s1,
-                                                                 c.d_sqrtDF, c.d_lam_w0f, c.d_lam_w1f);
+  const int nsl = std::max(c.n_spread_slots, 1);
+  k_spread_weights<<<(unsigned)((nsl + 255) / 256), 256, 0, st>>>(c.n_spread_slots, c.d_sp_b, c.d_sqrtDF, c.d_sp_sd);
   note_launches(1);
   return cudaGetLastError();
 }
@@ -1148,18 +1195,11 @@ cudaError_t launch_tc_p(const Ctx& c, int m, float* Yb, cudaStream_t st, bool co
 template <int FMT, int PASSES>
 void launch_gather(const Ctx& c, const double* X, int64_t ldx, int m, cudaStream_t st) {
   using T = typename TcFmt<FMT>::T;
-  const int64_t nl = c.hp.n_lam;
-  dim3 g((unsigned)((nl + 255) / 256), (m + TC_GJ - 1) / TC_GJ);
-  k_spread_tc<FMT, PASSES><<<g, 256, 0, st>>>(nl, m, c.d_lam_xp0, c.d_lam_xp1, c.d_lam_w0f, c.d_lam_w1f, X, ldx,
-                                              static_cast<T*>(c.d_xb_hi),
-                                              PASSES == 3 ? static_cast<T*>(c.d_xb_lo) : nullptr, c.nbp_total);
-  if (c.n_bmulti > 0) {
-    dim3 gm((unsigned)((c.n_bmulti + 127) / 128), (m + TC_GJ - 1) / TC_GJ);
-    k_gather_multi<FMT, PASSES><<<gm, 128, 0, st>>>(c.n_bmulti, m, c.d_bmulti, c.d_bmulti_pos, c.d_b2l_off,
-                                                    c.d_b2l_lam, c.d_b2l_sign, c.d_sqrtDF, X, ldx,
-                                                    static_cast<T*>(c.d_xb_hi),
-                                                    PASSES == 3 ? static_cast<T*>(c.d_xb_lo) : nullptr, c.nbp_total);
-  }
+  dim3 g((unsigned)c.n_spread_ranges, (m + SP_J - 1) / SP_J);
+  k_spread_tc<FMT, PASSES><<<g, SP_THREADS, 0, st>>>(m, c.d_sp_row0, c.d_sp_slot_off, c.d_sp_pos, c.d_sp_sd,
+                                                     c.d_sp_ent_off, c.d_sp_ent, X, ldx, static_cast<T*>(c.d_xb_hi),
+                                                     PASSES == 3 ? static_cast<T*>(c.d_xb_lo) : nullptr,
+                                                     c.nbp_total);
 }
 
 template <int FMT, int PASSES>
@@ -1167,7 +1207,7 @@ void launch_put_v(const Ctx& c, const double* V, int m, cudaStream_t st) {
   using T = typename TcFmt<FMT>::T;
   constexpr int KC = TcFmt<FMT>::KC;
   const int ext = (c.max_nc + KC - 1) / KC * KC;      // widest corner extension (<= 64)
-  dim3 g((m + 7) / 8, c.hp.n_sub);
+  dim3 g((m + PV_J - 1) / PV_J, c.hp.n_sub);
   k_put_v<FMT, PASSES><<<g, dim3(ext, 8), 0, st>>>(
       c.d_types, c.d_subs, c.d_bpad, c.d_c_glob, V, c.hp.n_primal, m, static_cast<T*>(c.d_xb_hi),
       PASSES == 3 ? static_cast<T*>(c.d_xb_lo) : nullptr, c.nbp_total);
@@ -1230,7 +1270,7 @@ cudaError_t tc_gather(const Ctx& c, const double* X, int64_t ldx, int m, cudaStr
   const bool split = tc_split(c);
   if (f == 0) split ? launch_gather<0, 3>(c, X, ldx, m, st) : launch_gather<0, 1>(c, X, ldx, m, st);
   else split ? launch_gather<1, 3>(c, X, ldx, m, st) : launch_gather<1, 1>(c, X, ldx, m, st);
-  note_launches(c.n_bmulti > 0 ? 2 : 1);
+  note_launches(1);
   return cudaGetLastError();
 }
 
@@ -1281,7 +1321,9 @@ cudaError_t tc_put_v(const Ctx& c, const double* V, int m, cudaStream_t st) {
   return cudaGetLastError();
 }
 
-int tc_coarse_split() { return CG_SPLIT; }
+// FP32 scratch of the coarse product for n primal DOFs and cap directions:
+// the split-K partials, then the right-hand sides in FP32.
+int64_t tc_coarse_scratch(int n, int cap) { return ((int64_t)CG_SPLIT * ((n + 3) / 4 * 4) + n) * cap; }
 
 cudaError_t tc_coarse_prepare(const Ctx& c, cudaStream_t st) {
   const int64_t n = (int64_t)c.hp.n_primal * c.hp.n_primal;
@@ -1294,11 +1336,15 @@ cudaError_t tc_coarse_apply(const Ctx& c, const double* Vraw, double* V, int m, 
   const int n = c.hp.n_primal;
   if (!c.d_Kbar_inv32 || n <= 0 || m <= 0) return cudaErrorInvalidValue;
   if (!c.d_coarse_part || m > c.blk_cap) return cudaErrorInvalidValue;
-  dim3 g((n + CG_T - 1) / CG_T, (m + CG_T - 1) / CG_T, CG_SPLIT);
-  k_sgemm_coarse<<<g, 256, 0, st>>>(n, m, c.d_Kbar_inv32, Vraw, c.d_coarse_part);
+  const int ldp = (n + 3) / 4 * 4;
+  float* P = c.d_coarse_part;
+  float* B32 = c.d_coarse_part + (int64_t)CG_SPLIT * ldp * c.blk_cap;
   const int64_t nm = (int64_t)n * m;
-  k_coarse_sum<<<(unsigned)((nm + 255) / 256), 256, 0, st>>>(nm, c.d_coarse_part, V);
-  note_launches(2);
+  k_f32_of<<<(unsigned)((nm + 255) / 256), 256, 0, st>>>(nm, Vraw, B32);
+  dim3 g((n + CG_T - 1) / CG_T, (m + CG_T - 1) / CG_T, CG_SPLIT);
+  k_sgemm_coarse<<<g, 256, 0, st>>>(n, m, ldp, c.d_Kbar_inv32, B32, P);
+  k_coarse_sum<<<dim3((n + 255) / 256, m), 256, 0, st>>>(n, m, ldp, P, V);
+  note_launches(3);
   return cudaGetLastError();
 }
 
@@ -1322,10 +1368,12 @@ cudaError_t tc_product(const Ctx& c, int m, float* Yb, cudaStream_t st) {
   return e;
 }
 
-cudaError_t lowp_gemv_S(const Ctx& c, const double* xb, double* yb, cudaStream_t st) {
+cudaError_t lowp_gemv_S(const Ctx& c, const double* xb, float* xh, double* yb, cudaStream_t st) {
+  const int64_t nbt = c.hp.n_b_total;
+  k_scale_x32<<<(unsigned)((nbt + 255) / 256), 256, 0, st>>>(nbt, c.d_sqrtDS, xb, xh);
   k_sub_gemv_lowp<<<dim3((c.max_nb + 7) / 8, c.hp.n_sub), 256, 0, st>>>(c.d_types, c.d_mods, c.d_subs, c.d_fmem,
-                                                                         c.d_sqrtDS, xb, yb);
-  note_launches(1);
+                                                                         c.d_sqrtDS, xh, yb);
+  note_launches(2);
   return cudaGetLastError();
 }
 

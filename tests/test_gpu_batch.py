@@ -118,3 +118,36 @@ def test_batch_simultaneous_uneven_workload_small():
     # the simultaneous variant needs fewer iterations than PCG on the same batch
     _, st_pcg, res_pcg = _solve_batch(probs, 1e-10)
     assert sum(r[3].iterations for r in res) < sum(r[3].iterations for r in res_pcg)
+
+
+def test_batch_row_tile_autotuned_without_changing_the_result():
+    """The batched Algorithm 1 times its block updates with several row tiles on
+    the first solve and keeps the fastest; the tile only splits the rows into
+    work items, so a second solve (tile already chosen) gives the same
+    multipliers bit for bit."""
+    torch = torch_cuda()
+    probs = _batch(n=4, seed=21)
+    o = fg.feti_options_default()
+    o.method, o.scaling, o.krylov, o.tol, o.max_iter = (fg.FETI_FETIDP, fg.FETI_SCALING_K, fg.FETI_RRS,
+                                                        1e-10, 2000)
+    ctx = fg.feti_create(o, torch.cuda.current_stream().cuda_stream)
+    keep, structs = [], []
+    for p in probs:
+        rho = torch.from_numpy(p.rho).cuda()
+        f = torch.from_numpy(p.f).cuda()
+        d = np.ascontiguousarray(p.dirichlet, np.uint8)
+        keep += [rho, f, d]
+        structs.append(fg.make_problem(p.dim, p.tiles, p.elems, p.E0, p.Emin, p.nu, p.p, rho, d, f, True))
+    fg.feti_setup_batch(ctx, structs)
+    fg.feti_factorize(ctx)
+    assert fg.feti_query(ctx, fg.FETI_Q_BATCH_ROW_TILE) == 0
+    nl = fg.feti_query(ctx, fg.FETI_Q_N_LAMBDA)
+    lam = []
+    for _ in range(2):
+        x = torch.zeros(nl, dtype=torch.float64, device="cuda")
+        status, st = fg.feti_solve_dual(ctx, lambda_inout=x)
+        assert st.converged
+        lam.append(x.cpu().numpy())
+        assert fg.feti_query(ctx, fg.FETI_Q_BATCH_ROW_TILE) in (1024, 2048, 4096, 8192, 16384)
+    assert np.array_equal(lam[0], lam[1])
+    fg.feti_destroy(ctx)
