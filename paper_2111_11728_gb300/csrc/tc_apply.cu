@@ -567,46 +567,22 @@ constexpr int SP_LD = SP_J * kSpreadRows / SP_THREADS;   // loads per thread
 constexpr int SP_QL = 64;              // slots handled side by side
 constexpr int SP_ME = 4;               // rows of a cross-point slot held in registers
 
-// It is built from the multiplier side, one range of consecutive multiplier
-// rows (at most kSpreadRows, every interface DOF's rows inside one range) and
-// SP_J directions per block: the block reads X(l, j) of its rows once
-// (consecutive threads, consecutive rows: coalesced; all SP_LD loads of a
-// thread in flight together; FP64 -> FP32) into shared memory, then writes
-// every operand slot of the range, x = sqrt(D) * (sum of its signed rows):
-// SP_QL consecutive slots side by side (those with one row first, each class
-// in position order), each group of SP_QL threads a share of the directions.
-// A DOF with one row takes that row, a cross-point DOF the sum of its rows,
-// summed in the order of its row list.
+// The operand slots of range r, directions j0 .. j0 + jn - 1, from the range's
+// rows in shared memory (xs[c][i] = X(row0[r] + i, j0 + c) in FP32): SP_QL
+// consecutive slots side by side (those with one row first, each class in
+// position order), each group of SP_QL threads a share of the directions.
+// x = sqrt(D) * (sum of the slot's signed rows): a DOF with one row takes that
+// row, a cross-point DOF the sum of its rows, in the order of its row list.
 template <int FMT, int PASSES>
-__global__ void __launch_bounds__(SP_THREADS) k_spread_tc(int m, const int* __restrict__ row0,
-                                                          const int* __restrict__ slot_off,
-                                                          const int* __restrict__ pos, const float* __restrict__ sd,
-                                                          const int* __restrict__ ent_off,
-                                                          const short* __restrict__ ent,
-                                                          const double* __restrict__ X, int64_t ldx,
-                                                          typename TcFmt<FMT>::T* __restrict__ xb_hi,
-                                                          typename TcFmt<FMT>::T* __restrict__ xb_lo, int64_t nbp) {
+__device__ __forceinline__ void spread_slots(const float (*xs)[kSpreadRows + 1], int r, int j0, int jn,
+                                             const int* __restrict__ slot_off, const int* __restrict__ pos,
+                                             const float* __restrict__ sd, const int* __restrict__ ent_off,
+                                             const short* __restrict__ ent, typename TcFmt<FMT>::T* __restrict__ xb_hi,
+                                             typename TcFmt<FMT>::T* __restrict__ xb_lo, int64_t nbp) {
   using F = TcFmt<FMT>;
-  static_assert(SP_THREADS % kSpreadRows == 0 && SP_THREADS % SP_QL == 0, "block shape");
-  constexpr int CSTEP = SP_THREADS / kSpreadRows, NG = SP_THREADS / SP_QL;
-  __shared__ float xs[SP_J][kSpreadRows + 1];
-  const int r = blockIdx.x;
-  const int l0 = row0[r], nr = row0[r + 1] - l0;
-  const int j0 = blockIdx.y * SP_J, jn = min(SP_J, m - j0);
-  {
-    const int i = threadIdx.x % kSpreadRows, cb = threadIdx.x / kSpreadRows;
-    double v[SP_LD];
-    const double* x = X + (int64_t)(l0 + i) + (int64_t)(j0 + cb) * ldx;
-#pragma unroll
-    for (int t = 0; t < SP_LD; ++t)
-      v[t] = (i < nr && cb + CSTEP * t < jn) ? __ldcs(x + (int64_t)(CSTEP * t) * ldx) : 0.0;
-#pragma unroll
-    for (int t = 0; t < SP_LD; ++t) xs[cb + CSTEP * t][i] = f64_to_f32_rn(v[t]);
-  }
-  __syncthreads();
+  constexpr int NG = SP_THREADS / SP_QL, PER = SP_J / NG;
   const int q0 = slot_off[r], nq = slot_off[r + 1] - q0;
   const int g = threadIdx.x / SP_QL;
-  constexpr int PER = SP_J / NG;
   const int64_t cstride = (int64_t)NG * nbp;
   for (int qq = threadIdx.x % SP_QL; qq < nq; qq += SP_QL) {
     const int q = q0 + qq;
@@ -649,6 +625,41 @@ __global__ void __launch_bounds__(SP_THREADS) k_spread_tc(int m, const int* __re
       }
     }
   }
+}
+
+// It is built from the multiplier side, one range of consecutive multiplier
+// rows (at most kSpreadRows, every interface DOF's rows inside one range) and
+// SP_J directions per block: the block reads X(l, j) of its rows once
+// (consecutive threads, consecutive rows: coalesced; all SP_LD loads of a
+// thread in flight together; FP64 -> FP32) into shared memory, then writes
+// every operand slot of the range (spread_slots).
+template <int FMT, int PASSES>
+__global__ void __launch_bounds__(SP_THREADS) k_spread_tc(int m, const int* __restrict__ row0,
+                                                          const int* __restrict__ slot_off,
+                                                          const int* __restrict__ pos, const float* __restrict__ sd,
+                                                          const int* __restrict__ ent_off,
+                                                          const short* __restrict__ ent,
+                                                          const double* __restrict__ X, int64_t ldx,
+                                                          typename TcFmt<FMT>::T* __restrict__ xb_hi,
+                                                          typename TcFmt<FMT>::T* __restrict__ xb_lo, int64_t nbp) {
+  static_assert(SP_THREADS % kSpreadRows == 0 && SP_THREADS % SP_QL == 0, "block shape");
+  constexpr int CSTEP = SP_THREADS / kSpreadRows;
+  __shared__ float xs[SP_J][kSpreadRows + 1];
+  const int r = blockIdx.x;
+  const int l0 = row0[r], nr = row0[r + 1] - l0;
+  const int j0 = blockIdx.y * SP_J, jn = min(SP_J, m - j0);
+  {
+    const int i = threadIdx.x % kSpreadRows, cb = threadIdx.x / kSpreadRows;
+    double v[SP_LD];
+    const double* x = X + (int64_t)(l0 + i) + (int64_t)(j0 + cb) * ldx;
+#pragma unroll
+    for (int t = 0; t < SP_LD; ++t)
+      v[t] = (i < nr && cb + CSTEP * t < jn) ? __ldcs(x + (int64_t)(CSTEP * t) * ldx) : 0.0;
+#pragma unroll
+    for (int t = 0; t < SP_LD; ++t) xs[cb + CSTEP * t][i] = f64_to_f32_rn(v[t]);
+  }
+  __syncthreads();
+  spread_slots<FMT, PASSES>(xs, r, j0, jn, slot_off, pos, sd, ent_off, ent, xb_hi, xb_lo, nbp);
 }
 
 // sqrt(D) of every operand slot's interface DOF in FP32 (refreshed at every
@@ -1193,13 +1204,14 @@ cudaError_t launch_tc_p(const Ctx& c, int m, float* Yb, cudaStream_t st, bool co
 }
 
 template <int FMT, int PASSES>
-void launch_gather(const Ctx& c, const double* X, int64_t ldx, int m, cudaStream_t st) {
+cudaError_t launch_gather(const Ctx& c, const double* X, int64_t ldx, int m, cudaStream_t st) {
   using T = typename TcFmt<FMT>::T;
   dim3 g((unsigned)c.n_spread_ranges, (m + SP_J - 1) / SP_J);
   k_spread_tc<FMT, PASSES><<<g, SP_THREADS, 0, st>>>(m, c.d_sp_row0, c.d_sp_slot_off, c.d_sp_pos, c.d_sp_sd,
                                                      c.d_sp_ent_off, c.d_sp_ent, X, ldx, static_cast<T*>(c.d_xb_hi),
                                                      PASSES == 3 ? static_cast<T*>(c.d_xb_lo) : nullptr,
                                                      c.nbp_total);
+  return cudaGetLastError();
 }
 
 template <int FMT, int PASSES>
@@ -1268,10 +1280,11 @@ cudaError_t tc_gather(const Ctx& c, const double* X, int64_t ldx, int m, cudaStr
   if (m > c.xb_cap) return cudaErrorInvalidValue;
   const int f = tc_format(c);
   const bool split = tc_split(c);
-  if (f == 0) split ? launch_gather<0, 3>(c, X, ldx, m, st) : launch_gather<0, 1>(c, X, ldx, m, st);
-  else split ? launch_gather<1, 3>(c, X, ldx, m, st) : launch_gather<1, 1>(c, X, ldx, m, st);
+  cudaError_t e;
+  if (f == 0) e = split ? launch_gather<0, 3>(c, X, ldx, m, st) : launch_gather<0, 1>(c, X, ldx, m, st);
+  else e = split ? launch_gather<1, 3>(c, X, ldx, m, st) : launch_gather<1, 1>(c, X, ldx, m, st);
   note_launches(1);
-  return cudaGetLastError();
+  return e;
 }
 
 // Cb = F_rc^T X_b per subdomain (FP32) from the gathered operand, then the
