@@ -1102,7 +1102,7 @@ static feti_status ensure_krylov(Ctx& c, int mmax) {
   TRY(dalloc(c, c.d_Delta, (size_t)mmax * mmax));
   TRY(dalloc(c, c.d_T, (size_t)mmax * mmax));
   TRY(dalloc(c, c.d_gamma, mmax));
-  TRY(dalloc(c, c.d_rrwork, (size_t)2 * mmax * mmax + mmax));
+  TRY(dalloc(c, c.d_rrwork, (size_t)rr_work_doubles(mmax)));
   c.kr_cap = mmax;
   return FETI_OK;
 }
@@ -1312,7 +1312,7 @@ static feti_status batch_rrs(Ctx& c, double tol, int max_iter, feti_stats& S) {
     woff[p] = sw;
     moff[p] = sm;
     sm2 += (int64_t)mp[p] * mp[p];
-    sw += 2 * (int64_t)mp[p] * mp[p] + mp[p];
+    sw += rr_work_doubles(mp[p]);
     sm += mp[p];
   }
   if (M > 1024) { c.err = "more than 1024 subdomains in one problem of the batch"; return FETI_ENOTSUP; }

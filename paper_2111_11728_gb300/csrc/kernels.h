@@ -147,11 +147,11 @@ cudaError_t autotune_gemv(Ctx& c, cudaStream_t st);
 // Rank-revealing pivoted Cholesky of Delta (m x m, column-major ld; only its
 // lower triangle is read): writes U = L~^{-T} (k x k upper triangular,
 // column-major ld m) into T, the pivot order into d_perm[0..m) and k into
-// *d_k, so that W N^T [L~^{-T}; 0] = W[:, perm[0..k)] U.
+// *d_k, so that W N^T [L~^{-T}; 0] = W[:, perm[0..k)] U.  work: rr_work_doubles(m).
 cudaError_t rr_cholesky(const double* Delta, int m, int ld, double rr_tol, double* work, double* T,
                         int* d_k, int* d_perm, cudaStream_t st);
 // The same for n independent matrices (m <= 1024 each), one descriptor per
-// matrix in device memory; work holds 2 m^2 + m doubles per matrix.
+// matrix in device memory; work holds rr_work_doubles(m) doubles per matrix.
 struct RrDesc {
   const double* Delta;
   int m, ld;
@@ -161,6 +161,7 @@ struct RrDesc {
   int* perm;
 };
 cudaError_t rr_cholesky_batched(const RrDesc* d_desc, int n, int max_m, double rr_tol, cudaStream_t st);
+int64_t rr_work_doubles(int m);   // work buffer of the rank-revealing factorization per matrix
 // lam_t += W g ; then r -= Q g, or qout = Q g when qout is not null
 // (W, Q column-major n x k with leading dimension ld)
 cudaError_t step_update(const double* W, const double* Q, int64_t ld, int64_t n, int k, const double* g,

@@ -12,186 +12,261 @@ namespace {
 
 constexpr double EPS2 = 4.930380657631324e-32;   // (2^-52)^2
 
-// Single CTA of 1024 threads; work holds 2*m*m + m doubles.  Pivot rule: the
-// largest ratio of the remaining Schur-complement diagonal to the column's
-// initial diagonal, exact ties to the lowest original column; stop when it is
-// <= rr_tol.
+// Pivot rule: the largest ratio of the remaining Schur-complement diagonal to
+// the column's initial diagonal, exact ties to the lowest original column; stop
+// when it is <= rr_tol.
 //
-// Blocked left-looking form.  Everything is indexed by the original column
-// (no physical swaps): A holds the lower triangle of Delta by original index,
-// updated once per panel of RR_PB pivots (a rank-RR_PB update of the rows and
-// columns still unchosen); within a panel the columns of L are kept in shared
-// memory and each new column subtracts only the panel's earlier columns; the
-// remaining diagonal d is updated after every column and drives the pivot
-// choice.  Every entry receives the same fused multiply-adds in the same
-// order as the unblocked right-looking elimination.
+// Blocked form.  Everything is indexed by the original column (no physical
+// swaps): A holds the lower triangle of Delta by original index, updated once
+// per panel of RR_PB pivots (a rank-RR_PB update of the rows and columns still
+// unchosen); within a panel each new column of L subtracts only the panel's
+// earlier columns; the remaining diagonal d is updated after every column and
+// drives the pivot choice.  Every entry receives the same fused multiply-adds
+// in the same order as the unblocked right-looking elimination.
+//
+// One launch sequence per call: k_rr_setup, then per panel k_rr_panel (one CTA
+// per matrix: the RR_PB pivot steps, which are sequential) and k_rr_update (the
+// panel's rank-RR_PB trailing update, RR_UB CTAs per matrix: the FP64 work,
+// spread over as many SMs), then k_rr_finish.  The state between launches
+// lives in the work buffer (rr_work_doubles(m) doubles per matrix):
+//   A [m*m] | Lg [m*m] | rdiag [m] | d [m] | d0 [m] | Lp [RR_PB*m] |
+//   perm, alive, chosen [m ints each] | k, stop, jn (ints)
 // Output T (column-major, ld m, k columns) = N^T [L~^{-T}; 0] and *d_k = k.
 constexpr int RR_THREADS = 1024;
 constexpr int RR_PB = 16;                       // panel width (pivots per trailing update)
+constexpr int RR_UB = 16;                       // CTAs per matrix in the trailing update
+constexpr int RR_UT = 256;                      // threads per trailing-update CTA
 
-// One CTA per matrix: descs[blockIdx.x] when descs is given (a batch), else `one`.
-__global__ void __launch_bounds__(RR_THREADS) k_rr_chol(const RrDesc* __restrict__ descs, RrDesc one,
-                                                        double rr_tol) {
+struct RrState {
+  double *A, *Lg, *rdiag, *d, *d0, *Lp;
+  int *perm, *alive, *chosen, *k, *stop, *jn;
+};
+
+__device__ __forceinline__ RrState rr_state(double* work, int m) {
+  RrState S;
+  S.A = work;
+  S.Lg = S.A + (int64_t)m * m;
+  S.rdiag = S.Lg + (int64_t)m * m;
+  S.d = S.rdiag + m;
+  S.d0 = S.d + m;
+  S.Lp = S.d0 + m;
+  S.perm = reinterpret_cast<int*>(S.Lp + (int64_t)RR_PB * m);
+  S.alive = S.perm + m;
+  S.chosen = S.alive + m;
+  S.k = S.chosen + m;
+  S.stop = S.k + 1;
+  S.jn = S.k + 2;
+  return S;
+}
+
+// A = lower triangle of Delta, d = d0 = its diagonal, the live columns (initial
+// diagonal above EPS2 times the largest), nothing chosen.
+__global__ void __launch_bounds__(RR_THREADS) k_rr_setup(const RrDesc* __restrict__ descs, RrDesc one) {
   const RrDesc D = descs ? descs[blockIdx.x] : one;
-  const double* __restrict__ Delta = D.Delta;
   const int m = D.m, ld = D.ld;
-  double* __restrict__ work = D.work;
-  int* __restrict__ d_k = D.k;
-  int* __restrict__ perm_out = D.perm;
-  double* A = work;                             // [m x m] by original index, lower triangle a >= b
-  double* Lg = work + (int64_t)m * m;           // [m x m] Lg[id*m + q] = L(position of id, q)
+  const RrState S = rr_state(D.work, m);
+  __shared__ double rv[32];
+  const int tid = threadIdx.x, nt = blockDim.x, lane = tid & 31, wid = tid >> 5, nw = nt >> 5;
+  for (int64_t e = tid; e < (int64_t)m * m; e += nt) {
+    const int a = (int)(e / m), b = (int)(e % m);
+    if (b <= a) S.A[e] = D.Delta[a + (int64_t)b * ld];
+  }
+  double mx = 0.0;
+  for (int t = tid; t < m; t += nt) {
+    const double v = D.Delta[t + (int64_t)t * ld];
+    S.d[t] = S.d0[t] = v;
+    S.chosen[t] = 0;
+    mx = fmax(mx, v);
+  }
+  for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+  if (lane == 0) rv[wid] = mx;
+  __syncthreads();
+  double dmax = 0.0;
+  for (int w = 0; w < nw; ++w) dmax = fmax(dmax, rv[w]);
+  for (int t = tid; t < m; t += nt) {
+    const double v = D.Delta[t + (int64_t)t * ld];
+    S.alive[t] = (dmax > 0.0 && v > EPS2 * dmax) ? 1 : 0;
+  }
+  if (tid == 0) {
+    *S.k = 0;
+    *S.stop = 0;
+    *S.jn = 0;
+  }
+}
+
+// The pivot steps of the panel starting at position p0; the panel's columns of
+// L go to Lg and Lp.  Sets *stop when no column qualifies.
+__global__ void __launch_bounds__(RR_THREADS) k_rr_panel(const RrDesc* __restrict__ descs, RrDesc one, int p0,
+                                                         double rr_tol) {
+  const RrDesc D = descs ? descs[blockIdx.x] : one;
+  const int m = D.m;
+  const RrState S = rr_state(D.work, m);
+  if (p0 >= m || *S.stop) return;
   extern __shared__ double rr_sh[];             // Lp[q][id], q < RR_PB
   double* Lp = rr_sh;
   __shared__ double d[1024], d0[1024];
-  __shared__ int perm[1024];
   __shared__ unsigned char alive[1024], chosen[1024];
   __shared__ double rv[32];
   __shared__ int rp[32];
   __shared__ int s_bp, s_k;
   __shared__ double s_best, s_piv, s_rpiv;
   const int tid = threadIdx.x, nt = blockDim.x;
-  const int lane = tid & 31, wid = tid >> 5, nw = nt >> 5;
+  const int lane = tid & 31, wid = tid >> 5;
   // warps that own at least one column (m <= blockDim.x): only they take part
   // in the pivot reduction -- FP64 work is scarce on this part, so nothing is
   // computed redundantly by idle threads
   const int aw = (m + 31) / 32;
-
-  for (int64_t e = tid; e < (int64_t)m * m; e += nt) {
-    const int a = (int)(e / m), b = (int)(e % m);
-    if (b <= a) A[e] = Delta[a + (int64_t)b * ld];
-  }
-  __syncthreads();
-  double mx = 0.0;
+  const double* A = S.A;
   for (int t = tid; t < m; t += nt) {
-    d[t] = d0[t] = A[(int64_t)t * m + t];
-    chosen[t] = 0;
-    mx = fmax(mx, d0[t]);
+    d[t] = S.d[t];
+    d0[t] = S.d0[t];
+    alive[t] = (unsigned char)S.alive[t];
+    chosen[t] = (unsigned char)S.chosen[t];
   }
-  for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
-  if (lane == 0) rv[wid] = mx;
+  if (tid == 0) s_k = *S.k;
   __syncthreads();
-  if (tid == 0) {
-    double v = 0.0;
-    for (int w = 0; w < nw; ++w) v = fmax(v, rv[w]);
-    s_best = v;
-    s_k = 0;
-  }
-  __syncthreads();
-  const double dmax = s_best;
-  for (int t = tid; t < m; t += nt) alive[t] = (dmax > 0.0 && d0[t] > EPS2 * dmax) ? 1 : 0;
-  __syncthreads();
-
+  const int pend = min(p0 + RR_PB, m);
+  int jn = 0;
   bool stop = false;
-  for (int p0 = 0; p0 < m && !stop; p0 += RR_PB) {
-    const int pend = min(p0 + RR_PB, m);
-    int jn = 0;
-    for (int j = p0; j < pend; ++j) {
-      // --- pivot: max d/d0 over the unchosen live columns, ties to the lowest
-      // id.  Ratios <= 0 never qualify (the stop test needs > rr_tol >= 0), so
-      // they enter as 0 and the comparison runs on the bit patterns of the
-      // non-negative doubles (integer pipe; same order as the values).
-      if (wid < aw) {
-        long long bv = -1;
-        int bp = 0x7fffffff;
-        for (int t = tid; t < m; t += aw * 32) {
-          if (!alive[t] || chosen[t]) continue;
-          const double ratio = d[t] / d0[t];
-          const long long key = ratio > 0.0 ? __double_as_longlong(ratio) : 0ll;
-          if (key > bv || (key == bv && t < bp)) { bv = key; bp = t; }
-        }
-        for (int o = 16; o > 0; o >>= 1) {
-          const long long ov = __shfl_xor_sync(0xffffffffu, bv, o);
-          const int op = __shfl_xor_sync(0xffffffffu, bp, o);
-          if (ov > bv || (ov == bv && op < bp)) { bv = ov; bp = op; }
-        }
-        if (lane == 0) { rv[wid] = __longlong_as_double(bv < 0 ? 0ll : bv); rp[wid] = bv < 0 ? 0x7fffffff : bp; }
+  for (int j = p0; j < pend; ++j) {
+    // --- pivot: max d/d0 over the unchosen live columns, ties to the lowest
+    // id.  Ratios <= 0 never qualify (the stop test needs > rr_tol >= 0), so
+    // they enter as 0 and the comparison runs on the bit patterns of the
+    // non-negative doubles (integer pipe; same order as the values).
+    if (wid < aw) {
+      long long bv = -1;
+      int bp = 0x7fffffff;
+      for (int t = tid; t < m; t += aw * 32) {
+        if (!alive[t] || chosen[t]) continue;
+        const double ratio = d[t] / d0[t];
+        const long long key = ratio > 0.0 ? __double_as_longlong(ratio) : 0ll;
+        if (key > bv || (key == bv && t < bp)) { bv = key; bp = t; }
       }
-      __syncthreads();
-      if (tid == 0) {
-        long long v = -1;
-        int pp = 0x7fffffff;
-        for (int w = 0; w < aw; ++w) {
-          const long long kw = rp[w] == 0x7fffffff ? -1 : __double_as_longlong(rv[w]);
-          if (kw > v || (kw == v && rp[w] < pp)) { v = kw; pp = rp[w]; }
-        }
-        s_best = v < 0 ? -1.0 : __longlong_as_double(v);
-        s_bp = pp == 0x7fffffff ? -1 : pp;
-        if (s_bp >= 0 && s_best > rr_tol) {
-          s_piv = sqrt(d[s_bp]);
-          s_rpiv = 1.0 / s_piv;
-        }
+      for (int o = 16; o > 0; o >>= 1) {
+        const long long ov = __shfl_xor_sync(0xffffffffu, bv, o);
+        const int op = __shfl_xor_sync(0xffffffffu, bp, o);
+        if (ov > bv || (ov == bv && op < bp)) { bv = ov; bp = op; }
       }
-      __syncthreads();
-      if (s_bp < 0 || !(s_best > rr_tol)) { stop = true; break; }
-      const int pj = s_bp;
-      const int jq = j - p0;
-      const double piv = s_piv;
-      const double rpiv = s_rpiv;
-      // --- column j of L for every unchosen live column r != pj
-      for (int r = tid; r < m; r += nt) {
-        if (r == pj || !alive[r] || chosen[r]) continue;
-        double acc = r > pj ? A[(int64_t)r * m + pj] : A[(int64_t)pj * m + r];
-        for (int q = 0; q < jq; ++q) acc = fma(-Lp[q * m + r], Lp[q * m + pj], acc);
-        const double l = acc * rpiv;
-        Lp[jq * m + r] = l;
-        d[r] = fma(-l, l, d[r]);
-      }
-      if (tid == 0) {
-        Lp[jq * m + pj] = piv;
-        chosen[pj] = 1;
-        perm[j] = pj;
-        s_k = j + 1;
-      }
-      jn = jq + 1;
-      __syncthreads();
+      if (lane == 0) { rv[wid] = __longlong_as_double(bv < 0 ? 0ll : bv); rp[wid] = bv < 0 ? 0x7fffffff : bp; }
     }
-    // --- the panel's columns into Lg (rows of ids chosen earlier in the panel
-    // hold stale values past their own column; those entries are never read)
-    for (int e = tid; e < jn * m; e += nt) {
-      const int q = e / m, id = e % m;
-      Lg[(int64_t)id * m + p0 + q] = Lp[q * m + id];
-    }
-    // --- rank-jn update of the unchosen live rows and columns (lower triangle)
-    if (!stop) {
-      for (int a = wid; a < m; a += nw) {
-        if (!alive[a] || chosen[a]) continue;
-        double* row = A + (int64_t)a * m;
-        for (int b0 = 0; b0 <= a; b0 += 32 * 4) {
-          double v[4];
-          bool on[4];
-#pragma unroll
-          for (int u = 0; u < 4; ++u) {
-            const int b = b0 + u * 32 + lane;
-            on[u] = b <= a && alive[b] && !chosen[b];
-            v[u] = on[u] ? row[b] : 0.0;
-          }
-          for (int q = 0; q < jn; ++q) {
-            const double la = Lp[q * m + a];
-#pragma unroll
-            for (int u = 0; u < 4; ++u)
-              if (on[u]) v[u] = fma(-la, Lp[q * m + b0 + u * 32 + lane], v[u]);
-          }
-#pragma unroll
-          for (int u = 0; u < 4; ++u)
-            if (on[u]) row[b0 + u * 32 + lane] = v[u];
-        }
+    __syncthreads();
+    if (tid == 0) {
+      long long v = -1;
+      int pp = 0x7fffffff;
+      for (int w = 0; w < aw; ++w) {
+        const long long kw = rp[w] == 0x7fffffff ? -1 : __double_as_longlong(rv[w]);
+        if (kw > v || (kw == v && rp[w] < pp)) { v = kw; pp = rp[w]; }
+      }
+      s_best = v < 0 ? -1.0 : __longlong_as_double(v);
+      s_bp = pp == 0x7fffffff ? -1 : pp;
+      if (s_bp >= 0 && s_best > rr_tol) {
+        s_piv = sqrt(d[s_bp]);
+        s_rpiv = 1.0 / s_piv;
       }
     }
     __syncthreads();
+    if (s_bp < 0 || !(s_best > rr_tol)) { stop = true; break; }
+    const int pj = s_bp;
+    const int jq = j - p0;
+    const double piv = s_piv;
+    const double rpiv = s_rpiv;
+    // --- column j of L for every unchosen live column r != pj
+    for (int r = tid; r < m; r += nt) {
+      if (r == pj || !alive[r] || chosen[r]) continue;
+      double acc = r > pj ? A[(int64_t)r * m + pj] : A[(int64_t)pj * m + r];
+      for (int q = 0; q < jq; ++q) acc = fma(-Lp[q * m + r], Lp[q * m + pj], acc);
+      const double l = acc * rpiv;
+      Lp[jq * m + r] = l;
+      d[r] = fma(-l, l, d[r]);
+    }
+    if (tid == 0) {
+      Lp[jq * m + pj] = piv;
+      chosen[pj] = 1;
+      S.perm[j] = pj;
+      s_k = j + 1;
+    }
+    jn = jq + 1;
+    __syncthreads();
   }
-  const int k = s_k;
-  // positions >= k: the remaining columns in increasing order
+  // --- the panel's columns into Lg (rows of ids chosen earlier in the panel
+  // hold stale values past their own column; those entries are never read)
+  // and into Lp for the trailing update; the state back
+  for (int e = tid; e < jn * m; e += nt) {
+    const int q = e / m, id = e % m;
+    const double v = Lp[q * m + id];
+    S.Lg[(int64_t)id * m + p0 + q] = v;
+    S.Lp[q * m + id] = v;
+  }
+  for (int t = tid; t < m; t += nt) {
+    S.d[t] = d[t];
+    S.chosen[t] = chosen[t];
+  }
+  if (tid == 0) {
+    *S.k = s_k;
+    *S.jn = jn;
+    if (stop || s_k >= m) *S.stop = stop ? 1 : 0;
+  }
+}
+
+// The panel's rank-jn update of the unchosen live rows and columns (lower
+// triangle), RR_UB CTAs per matrix, one warp per row; skipped once the
+// factorization has stopped.
+__global__ void __launch_bounds__(RR_UT) k_rr_update(const RrDesc* __restrict__ descs, RrDesc one, int p0) {
+  const RrDesc D = descs ? descs[blockIdx.y] : one;
+  const int m = D.m;
+  const RrState S = rr_state(D.work, m);
+  if (p0 >= m || *S.stop) return;
+  const int jn = *S.jn;
+  extern __shared__ double rr_sh[];
+  double* Lp = rr_sh;                           // [jn][m]
+  unsigned char* live = reinterpret_cast<unsigned char*>(Lp + (int64_t)RR_PB * m);
+  const int tid = threadIdx.x, nt = blockDim.x, lane = tid & 31, wid = tid >> 5, nw = nt >> 5;
+  for (int e = tid; e < jn * m; e += nt) Lp[e] = S.Lp[e];
+  for (int t = tid; t < m; t += nt) live[t] = S.alive[t] && !S.chosen[t];
+  __syncthreads();
+  double* A = S.A;
+  for (int a = blockIdx.x * nw + wid; a < m; a += gridDim.x * nw) {
+    if (!live[a]) continue;
+    double* row = A + (int64_t)a * m;
+    for (int b0 = 0; b0 <= a; b0 += 32 * 4) {
+      double v[4];
+      bool on[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const int b = b0 + u * 32 + lane;
+        on[u] = b <= a && live[b];
+        v[u] = on[u] ? row[b] : 0.0;
+      }
+      for (int q = 0; q < jn; ++q) {
+        const double la = Lp[q * m + a];
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+          if (on[u]) v[u] = fma(-la, Lp[q * m + b0 + u * 32 + lane], v[u]);
+      }
+#pragma unroll
+      for (int u = 0; u < 4; ++u)
+        if (on[u]) row[b0 + u * 32 + lane] = v[u];
+    }
+  }
+}
+
+// Positions >= k: the remaining columns in increasing order; the reciprocals
+// of the pivots (diagonal of L~) for the inverse kernel; perm and k out.
+__global__ void __launch_bounds__(RR_THREADS) k_rr_finish(const RrDesc* __restrict__ descs, RrDesc one) {
+  const RrDesc D = descs ? descs[blockIdx.x] : one;
+  const int m = D.m;
+  const RrState S = rr_state(D.work, m);
+  const int tid = threadIdx.x, nt = blockDim.x;
+  const int k = *S.k;
   if (tid == 0) {
     int pos = k;
     for (int t = 0; t < m; ++t)
-      if (!chosen[t]) perm[pos++] = t;
+      if (!S.chosen[t]) S.perm[pos++] = t;
   }
   __syncthreads();
-  // --- reciprocals of the pivots (diagonal of L~) for the inverse kernel
-  double* rdiag_g = work + 2 * (int64_t)m * m;
-  for (int q = tid; q < k; q += nt) rdiag_g[q] = 1.0 / Lg[(int64_t)perm[q] * m + q];
-  for (int t = tid; t < m; t += nt) perm_out[t] = perm[t];
-  if (tid == 0) *d_k = k;
+  for (int q = tid; q < k; q += nt) S.rdiag[q] = 1.0 / S.Lg[(int64_t)S.perm[q] * m + q];
+  for (int t = tid; t < m; t += nt) D.perm[t] = S.perm[t];
+  if (tid == 0) *D.k = k;
 }
 
 // U = L~^{-T} (upper triangular, column-major, ld m): T[jj + i*m] = X[i][jj]
@@ -355,14 +430,29 @@ cudaError_t rr_launch(const RrDesc* d_desc, const RrDesc& one, int n, int max_m,
   if (max_m > 1024) return cudaErrorInvalidValue;
   if (n <= 0 || max_m <= 0) return cudaSuccess;
   static bool attr_set = false;
-  const size_t smem = (size_t)RR_PB * 1024 * sizeof(double);
+  const size_t psmem = (size_t)RR_PB * max_m * sizeof(double);
+  const size_t usmem = psmem + (size_t)max_m;
   if (!attr_set) {
-    cudaError_t e = cudaFuncSetAttribute(k_rr_chol, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t e = cudaFuncSetAttribute(k_rr_panel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)(RR_PB * 1024 * sizeof(double)));
+    if (e != cudaSuccess) return e;
+    e = cudaFuncSetAttribute(k_rr_update, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)(RR_PB * 1024 * sizeof(double) + 1024));
     if (e != cudaSuccess) return e;
     attr_set = true;
   }
-  k_rr_chol<<<n, RR_THREADS, (size_t)RR_PB * max_m * sizeof(double), st>>>(d_desc, one, rr_tol);
-  note_launches(1);
+  k_rr_setup<<<n, RR_THREADS, 0, st>>>(d_desc, one);
+  // the pivot steps are bound by their block-wide barriers: no more threads
+  // than columns
+  const int pt = std::min(RR_THREADS, std::max(64, (max_m + 31) / 32 * 32));
+  int nl = 1;
+  for (int p0 = 0; p0 < max_m; p0 += RR_PB) {
+    k_rr_panel<<<n, pt, psmem, st>>>(d_desc, one, p0, rr_tol);
+    k_rr_update<<<dim3(RR_UB, n), RR_UT, usmem, st>>>(d_desc, one, p0);
+    nl += 2;
+  }
+  k_rr_finish<<<n, RR_THREADS, 0, st>>>(d_desc, one);
+  note_launches(nl + 1);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   static bool inv_attr = false;
@@ -379,6 +469,8 @@ cudaError_t rr_launch(const RrDesc* d_desc, const RrDesc& one, int n, int max_m,
 }
 
 }  // namespace
+
+int64_t rr_work_doubles(int m) { return 2 * (int64_t)m * m + (int64_t)(4 + RR_PB) * m + (3 * (int64_t)m + 4) / 2 + 1; }
 
 cudaError_t rr_cholesky(const double* Delta, int m, int ld, double rr_tol, double* work, double* T, int* d_k,
                         int* d_perm, cudaStream_t st) {
