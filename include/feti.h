@@ -67,6 +67,7 @@ enum { FETI_PCG = 0, FETI_FO = 1, FETI_RRS = 2 };         /* Sections 3.2, 3.3 *
 enum { FETI_FP64 = 0, FETI_TF32 = 1, FETI_TF32X3 = 2, FETI_BF16 = 3, FETI_BF16X3 = 4 };  /* block products */
 enum { FETI_PRECOND_DIRICHLET = 0, FETI_PRECOND_LUMPED = 1, FETI_PRECOND_SUPERLUMPED = 2 };
 enum { FETI_PRIMAL_CORNERS = 0, FETI_PRIMAL_EDGES = 1, FETI_PRIMAL_ADAPTIVE = 2 };
+enum { FETI_REFINE_DUAL = 0, FETI_REFINE_PRIMAL = 1 };   /* reduced precision: the FP64 outer residual */
                                                /* FETI-DP primal set (Section 2.2; richer and adaptive
                                                   sets: Section 5, future work) */
 
@@ -103,6 +104,17 @@ typedef struct {
                           k-scaling weighs -- differ by a factor >= primal_jump; chosen from the
                           densities given at set-up).  TFETI: must be FETI_PRIMAL_CORNERS */
   double primal_jump;  /* FETI_PRIMAL_ADAPTIVE: the jump ratio that selects an edge (default 10; >= 1) */
+  int refine;          /* reduced precision, one problem: the residual the FP64 outer loop refines on.
+                          FETI_REFINE_DUAL (default): r = P^T (d - F lambda) with the FP64 operator,
+                          each correction a reduced-precision solve of F dl = r (inner_tol, default
+                          1e-2); convergence as in FP64 (sqrt(r^T z) <= tol * initial).
+                          FETI_REFINE_PRIMAL: r = f - K u element by element in FP64, each correction
+                          a reduced-precision FETI solve of K du = r (its own dual problem, inner_tol
+                          default 1e-3); converged when ||r|| <= tol ||f|| over the free DOFs (stats
+                          eps0 = 1, eps = that ratio).  feti_recover_displacements then returns the
+                          sum of the du; lambda_inout is output only and receives the sum of the
+                          corrections' multipliers (each for its own residual load: not the
+                          multipliers of f in general) */
 } feti_options;
 
 typedef struct {
@@ -263,6 +275,14 @@ feti_status feti_apply_precond(feti_ctx* ctx, const double* r, double* Z, int ld
  * for the array are rejected as soon as they are set up (before any device
  * work).  No CUDA or other allocation is made by this call. */
 feti_status feti_apply_precond_noalloc(feti_ctx* ctx, const double* r, double* Z, int ldz, double* z);
+
+/* r = f - K u over the free DOFs (0 on the fixed ones) in FP64, element by
+ * element (Eq. 2 with the element moduli of Eq. 1 from the densities of the
+ * last feti_factorize), for the whole set-up problem or batch.  u: device
+ * [n_dofs] (NULL: u = 0); r: device [n_dofs] or NULL (internal scratch);
+ * rel: host, receives ||r|| / ||f|| over the free DOFs (||r|| if that f is
+ * zero), or NULL.  Errors: FETI_ESTATE before feti_factorize. */
+feti_status feti_primal_residual(feti_ctx* ctx, const double* u, double* r, double* rel);
 
 /* Integer facts about the set-up problem; key is one of FETI_Q_*. */
 enum {

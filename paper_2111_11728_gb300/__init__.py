@@ -24,6 +24,7 @@ FETI_PCG, FETI_FO, FETI_RRS = 0, 1, 2
 FETI_FP64, FETI_TF32, FETI_TF32X3, FETI_BF16, FETI_BF16X3 = 0, 1, 2, 3, 4
 FETI_PRECOND_DIRICHLET, FETI_PRECOND_LUMPED, FETI_PRECOND_SUPERLUMPED = 0, 1, 2
 FETI_PRIMAL_CORNERS, FETI_PRIMAL_EDGES, FETI_PRIMAL_ADAPTIVE = 0, 1, 2
+FETI_REFINE_DUAL, FETI_REFINE_PRIMAL = 0, 1
 (FETI_Q_N_LAMBDA, FETI_Q_N_SUBDOMAINS, FETI_Q_N_PRIMAL, FETI_Q_N_MODULES, FETI_Q_N_B_TOTAL, FETI_Q_N_DOFS,
  FETI_Q_N_ELEMENTS, FETI_Q_MAX_NB, FETI_Q_DEVICE_BYTES, FETI_Q_N_RBM, FETI_Q_LAUNCHES, FETI_Q_N_PROBLEMS,
  FETI_Q_GEMV_CONFIG, FETI_Q_TC_BYTES_F, FETI_Q_TC_BYTES_PER_COL, FETI_Q_APPLY1_BYTES,
@@ -36,7 +37,7 @@ STATUS_NAMES = {0: "FETI_OK", 1: "FETI_EINVAL", 2: "FETI_ENOMEM", 3: "FETI_ESTAT
 EXPORTS = [
     "feti_options_default", "feti_create", "feti_set_allocator", "feti_setup_subdomains", "feti_setup_batch", "feti_problem_result",
     "feti_set_density", "feti_factorize",
-    "feti_solve_dual", "feti_recover_displacements", "feti_compliance_grad", "feti_apply_dual",
+    "feti_solve_dual", "feti_recover_displacements", "feti_compliance_grad", "feti_primal_residual", "feti_apply_dual",
     "feti_apply_precond", "feti_apply_precond_noalloc", "feti_test_skip_copy", "feti_query", "feti_profile_begin", "feti_profile_end", "feti_profile_tensor", "feti_profile_phases", "feti_lambda_layout", "feti_local_blocks", "feti_last_error",
     "feti_destroy",
 ]
@@ -47,7 +48,7 @@ class feti_options(ctypes.Structure):
                 ("precision", ctypes.c_int), ("max_iter", ctypes.c_int), ("dedup_modules", ctypes.c_int),
                 ("tol", ctypes.c_double), ("rr_tol", ctypes.c_double), ("inner_tol", ctypes.c_double),
                 ("max_refine", ctypes.c_int), ("precond", ctypes.c_int),
-                ("primal", ctypes.c_int), ("primal_jump", ctypes.c_double)]
+                ("primal", ctypes.c_int), ("primal_jump", ctypes.c_double), ("refine", ctypes.c_int)]
 
 
 class feti_problem(ctypes.Structure):
@@ -95,6 +96,7 @@ def lib():
             "feti_solve_dual": ([vp, vp, ctypes.POINTER(feti_stats)], i),
             "feti_recover_displacements": ([vp, vp, i, ctypes.POINTER(d)], i),
             "feti_compliance_grad": ([vp, vp, i], i),
+            "feti_primal_residual": ([vp, vp, vp, ctypes.POINTER(d)], i),
             "feti_apply_dual": ([vp, vp, i, i, vp, i], i),
             "feti_apply_precond": ([vp, vp, vp, i, vp], i),
             "feti_apply_precond_noalloc": ([vp, vp, vp, i, vp], i),
@@ -262,6 +264,14 @@ def feti_recover_displacements(ctx, u_out, on_device):
     return c.value
 
 
+def feti_primal_residual(ctx, u=None, r=None):
+    """r = f - K u over the free DOFs (device tensors; u None: u = 0); returns
+    ||r|| / ||f|| over the free DOFs."""
+    rel = ctypes.c_double(0.0)
+    _check(ctx, lib().feti_primal_residual(ctx, _ptr(u), _ptr(r), ctypes.byref(rel)))
+    return rel.value
+
+
 def feti_compliance_grad(ctx, out, on_device):
     return _check(ctx, lib().feti_compliance_grad(ctx, _ptr(out), int(on_device)))
 
@@ -352,11 +362,15 @@ class Solver:
 
     def __init__(self, method=FETI_FETIDP, scaling=FETI_SCALING_K, krylov=FETI_RRS, tol=1e-6, max_iter=500,
                  rr_tol=1e-10, dedup=True, stream=None, precision=FETI_FP64, inner_tol=None,
-                 precond=FETI_PRECOND_DIRICHLET, primal=FETI_PRIMAL_CORNERS, allocator=None, primal_jump=None):
+                 precond=FETI_PRECOND_DIRICHLET, primal=FETI_PRIMAL_CORNERS, allocator=None, primal_jump=None,
+                 refine=FETI_REFINE_DUAL, max_refine=None):
         o = feti_options_default()
         o.method, o.scaling, o.krylov, o.precision = method, scaling, krylov, precision
         o.precond = precond
         o.primal = primal
+        o.refine = refine
+        if max_refine is not None:
+            o.max_refine = max_refine
         if primal_jump is not None:
             o.primal_jump = primal_jump
         if inner_tol is not None:

@@ -426,6 +426,7 @@ feti_status feti_options_default(feti_options* opt) {
   opt->precond = FETI_PRECOND_DIRICHLET;
   opt->primal = FETI_PRIMAL_CORNERS;
   opt->primal_jump = 10.0;
+  opt->refine = FETI_REFINE_DUAL;
   return FETI_OK;
 }
 
@@ -447,6 +448,7 @@ feti_status feti_create(feti_ctx** out, const feti_options* opt, void* stream) {
   if (o.primal != FETI_PRIMAL_CORNERS && o.method != FETI_FETIDP) return FETI_EINVAL;
   if (o.primal != FETI_PRIMAL_CORNERS && o.precond != FETI_PRECOND_DIRICHLET) return FETI_ENOTSUP;
   if (o.primal == FETI_PRIMAL_ADAPTIVE && !(o.primal_jump >= 1.0)) return FETI_EINVAL;
+  if (o.refine != FETI_REFINE_DUAL && o.refine != FETI_REFINE_PRIMAL) return FETI_EINVAL;
   feti_ctx* ctx = new (std::nothrow) feti_ctx;
   if (!ctx) return FETI_ENOMEM;
   Ctx& c = ctx->c;
@@ -995,6 +997,50 @@ feti_status feti_set_density(feti_ctx* ctx, const double* rho, int on_device) {
   return FETI_OK;
 }
 
+}  // extern "C"
+
+// The load-dependent part of Eqs. 7 / 12 for the current global load c.d_fglob
+// (the matrix parts are factorized): f^s, h = L^{-1} f_i, f~ = f_bc - Y^T h;
+// d = B K^# f (FETI-DP: d_r - F_rc Kbar_cc^{-1} fbar with fbar_c = sum_s B_c^sT
+// (f~_c - F_rc,s^T f~_b)); TFETI: e = -R^T f and lambda_0 = G^T (G G^T)^{-1} e.
+static feti_status load_rhs(Ctx& c) {
+  const HostProblem& hp = c.hp;
+  cudaStream_t st = c.stream;
+  const bool dp = hp.method == FETI_FETIDP;
+  CU(launch_load_gather(c, st));
+  CU(launch_band_fwd_single(c, st));
+  CU(launch_condense_load(c, st));
+  if (c.max_avg > 0) CU(launch_edge_load(c, c.max_avg, st));      // f~ <- T^T f~
+  const int64_t nl = hp.n_lam, nbt = hp.n_b_total;
+  // d_r (FETI-DP) or d = B K^# f (TFETI, c = 0): x_b = F f~_b, scattered
+  CU(batched_gemv(c, 0, c.d_ft, c.d_pb0, 0.0, st));
+  CU(scatter_b_to_lam(c, c.d_pb0, 1, c.d_d, nl, st));
+  CU(cudaMemsetAsync(c.d_lam0, 0, nl * sizeof(double), st));
+  if (dp) {
+    const int np = hp.n_primal;
+    CU(cudaMemcpyAsync(c.d_Xb, c.d_ft, nbt * sizeof(double), cudaMemcpyDeviceToDevice, st));
+    CU(corner_reduce(c, c.d_Xb, 1, c.d_Cb, c.d_Vraw, st));
+    CU(corner_gather_vec(c, c.d_ft + nbt, c.d_fbar, st));
+    CU(axpby(np, -1.0, c.d_Vraw, 1.0, c.d_fbar, st));
+    // d = d_r - F_rc Kbar^{-1} fbar
+    CU(coarse_matvec(c, c.d_fbar, c.d_V, st));
+    CU(cudaMemsetAsync(c.d_Yb, 0, nbt * sizeof(double), st));
+    CU(corner_expand(c, c.d_V, 1, c.d_Vc, c.d_Yb, st));
+    CU(scatter_b_to_lam(c, c.d_Yb, 1, c.d_lam, nl, st));
+    CU(axpby(nl, -1.0, c.d_lam, 1.0, c.d_d, st));
+  } else {
+    const int nco = c.n_coarse;
+    CU(tfeti_build_e(c, c.d_e, st));
+    CU(gemv_dense(c.d_Kbar_inv, nco, nco, c.d_e, c.d_alpha, 0.0, st));
+    // lambda_0 = G^T alpha: the G^T kernel subtracts, so from 0 it leaves -G^T alpha
+    CU(tfeti_Gt_sub(c, c.d_alpha, 1, c.d_lam0, nl, st));
+    CU(axpby(nl, -1.0, c.d_lam0, 0.0, c.d_lam0, st));
+  }
+  return FETI_OK;
+}
+
+extern "C" {
+
 feti_status feti_factorize(feti_ctx* ctx) {
   if (!ctx) return FETI_EINVAL;
   Ctx& c = ctx->c;
@@ -1041,46 +1087,18 @@ feti_status feti_factorize(feti_ctx* ctx) {
   }
   if (c.opt.precision != FETI_FP64) CU(tc_prepare(c, st));
   if (hp.n_prob > 1 && c.gemv_cfg == 0) CU(autotune_gemv(c, st));   // batches: tune the matrix-vector shape
-  // loads: f^s, h = L^{-1} f_i, f~ = f_bc - Y^T h
-  CU(launch_load_gather(c, st));
-  CU(launch_band_fwd_single(c, st));
-  CU(launch_condense_load(c, st));
-  if (c.max_avg > 0) CU(launch_edge_load(c, c.max_avg, st));      // f~ <- T^T f~
-  const int64_t nl = hp.n_lam, nbt = hp.n_b_total;
-  // d_r (FETI-DP) or d = B K^# f (TFETI, c = 0): x_b = F f~_b, scattered
-  CU(batched_gemv(c, 0, c.d_ft, c.d_pb0, 0.0, st));
-  CU(scatter_b_to_lam(c, c.d_pb0, 1, c.d_d, nl, st));
-  CU(cudaMemsetAsync(c.d_lam0, 0, nl * sizeof(double), st));
   if (dp) {
-    const int np = hp.n_primal;
     // coarse matrix Kbar_cc (Eq. 12) and its inverse
     CU(coarse_assemble_batch(c, st));
     CU(coarse_inverse(c));
     if (c.d_Kbar_inv32) CU(tc_coarse_prepare(c, st));
-    // fbar_c = sum_s B_c^sT (f~_c - F_rc,s^T f~_b)
-    CU(cudaMemcpyAsync(c.d_Xb, c.d_ft, nbt * sizeof(double), cudaMemcpyDeviceToDevice, st));
-    CU(corner_reduce(c, c.d_Xb, 1, c.d_Cb, c.d_Vraw, st));
-    CU(corner_gather_vec(c, c.d_ft + nbt, c.d_fbar, st));
-    CU(axpby(np, -1.0, c.d_Vraw, 1.0, c.d_fbar, st));
-    // d = d_r - F_rc Kbar^{-1} fbar
-    CU(coarse_matvec(c, c.d_fbar, c.d_V, st));
-    CU(cudaMemsetAsync(c.d_Yb, 0, nbt * sizeof(double), st));
-    CU(corner_expand(c, c.d_V, 1, c.d_Vc, c.d_Yb, st));
-    CU(scatter_b_to_lam(c, c.d_Yb, 1, c.d_lam, nl, st));
-    CU(axpby(nl, -1.0, c.d_lam, 1.0, c.d_d, st));
   } else {
-    // TFETI coarse space: G = -R^T B^T (applied, never stored), G G^T, e = -R^T f,
-    // lambda_0 = G^T (G G^T)^{-1} e
-    const int nco = c.n_coarse;
+    // TFETI coarse space: G = -R^T B^T (applied, never stored) and G G^T
     TRY(ensure_blocks(c, kGgtCols));
     CU(tfeti_ggt(c, c.d_gwork, kGgtCols, c.d_ct1, c.d_ct2, c.d_Xb, c.d_Kbar, st));
     CU(coarse_inverse(c));
-    CU(tfeti_build_e(c, c.d_e, st));
-    CU(gemv_dense(c.d_Kbar_inv, nco, nco, c.d_e, c.d_alpha, 0.0, st));
-    // lambda_0 = G^T alpha: the G^T kernel subtracts, so from 0 it leaves -G^T alpha
-    CU(tfeti_Gt_sub(c, c.d_alpha, 1, c.d_lam0, nl, st));
-    CU(axpby(nl, -1.0, c.d_lam0, 0.0, c.d_lam0, st));
   }
+  TRY(load_rhs(c));
   TRY(sync_check(c));
   TRY(check_status(c, "coarse factorization"));
   c.state = 2;
@@ -1617,6 +1635,90 @@ static feti_status cold_reference(Ctx& c, double* eps_ref) {
   return FETI_OK;
 }
 
+static feti_status recover_u(Ctx& c, const double* lam);
+
+// FP64 refinement on the primal residual (the FETI_REFINE_PRIMAL reading of
+// the precision form): r = f - K u element by element in FP64; each step
+// solves K du = r with FETI and the reduced-precision operator (the dual
+// problem of the load r, Algorithm 1 to inner_tol, default 1e-3), recovers du
+// and adds it, u = sum of the du, lambda = sum of the multipliers; stops when
+// ||r|| <= tol ||f|| (free DOFs), or at max_refine / max_iter.  The load is
+// restored at the end; the recovery then returns the summed u.
+static feti_status refine_primal(Ctx& c, feti_stats& S, feti_status& result) {
+  const HostProblem& hp = c.hp;
+  const int64_t nl = hp.n_lam, nd = hp.n_dofs;
+  cudaStream_t st = c.stream;
+  if (!c.d_f0) {
+    TRY(dalloc(c, c.d_f0, nd));
+    TRY(dalloc(c, c.d_uacc, nd));
+    TRY(dalloc(c, c.d_lamacc, nl));
+  }
+  CU(cudaMemcpyAsync(c.d_f0, c.d_fglob, nd * sizeof(double), cudaMemcpyDeviceToDevice, st));
+  CU(cudaMemsetAsync(c.d_uacc, 0, nd * sizeof(double), st));
+  CU(cudaMemsetAsync(c.d_lamacc, 0, nl * sizeof(double), st));
+  if (!c.d_ubest) TRY(dalloc(c, c.d_ubest, nd));
+  double fn2 = 0.0, rel = 1.0, best = 0.0;
+  int outer = 0;
+  for (;;) {
+    CU(launch_residual(c, c.d_f0, outer == 0 ? nullptr : c.d_uacc, c.d_fglob, st));
+    CU(dot(c.d_fglob, c.d_fglob, nd, c.d_red, c.d_scalar, st));
+    double rn2 = 0.0;
+    TRY(read_scalar(c, c.d_scalar, &rn2));
+    if (outer == 0) fn2 = rn2;
+    rel = fn2 > 0.0 ? std::sqrt(rn2 / fn2) : 0.0;
+    // a correction that blew the residual up (a reduced-precision solve too
+    // inaccurate for the problem) is undone: the best sums so far are kept and
+    // the refinement stops unconverged
+    if (outer > 0 && (!std::isfinite(rn2) || rel > 100.0 * best)) {
+      CU(cudaMemcpyAsync(c.d_uacc, c.d_ubest, nd * sizeof(double), cudaMemcpyDeviceToDevice, st));
+      CU(cudaMemcpyAsync(c.d_lamacc, c.d_dl, nl * sizeof(double), cudaMemcpyDeviceToDevice, st));
+      c.err = std::isfinite(rn2) ? "the primal refinement diverged; the best solution is returned"
+                                 : "NaN or Inf in the primal residual; the best solution is returned";
+      if (!std::isfinite(rn2)) result = FETI_EBREAKDOWN;
+      rel = best;
+      break;
+    }
+    if (outer == 0 || rel < best) {
+      best = rel;
+      CU(cudaMemcpyAsync(c.d_ubest, c.d_uacc, nd * sizeof(double), cudaMemcpyDeviceToDevice, st));
+      CU(cudaMemcpyAsync(c.d_dl, c.d_lamacc, nl * sizeof(double), cudaMemcpyDeviceToDevice, st));
+    }
+    if (rel <= c.opt.tol || outer >= c.opt.max_refine || S.iterations >= c.opt.max_iter) break;
+    // the dual problem of the load r, solved from its own lambda_0
+    TRY(load_rhs(c));
+    CU(cudaMemcpyAsync(c.d_lam, c.d_lam0, nl * sizeof(double), cudaMemcpyDeviceToDevice, st));
+    TRY(apply_dual(c, c.d_lam, nl, 1, c.d_r, nl));
+    CU(axpby(nl, 1.0, c.d_d, -1.0, c.d_r, st));
+    TRY(project(c, c.d_r, nl, 1));
+    feti_stats inner{};
+    const int cap = std::min(c.opt.max_iter - S.iterations, 60);
+    const double itol = c.opt.inner_tol > 0.0 ? c.opt.inner_tol : 1e-3;
+    feti_status s2 = krylov_core(c, itol, cap, true, inner, -1.0);
+    S.iterations += inner.iterations;
+    S.f_applies += inner.f_applies + 1;
+    S.last_rank = inner.last_rank;
+    ++outer;
+    if (s2 == FETI_EBREAKDOWN && inner.iterations > 0) c.err.clear();
+    else if (s2 != FETI_OK && s2 != FETI_ENOTCONV) { result = s2; break; }
+    CU(axpby(nl, 1.0, c.d_lamt, 1.0, c.d_lam, st));
+    TRY(recover_u(c, c.d_lam));
+    CU(axpby(nd, 1.0, c.d_uglob, 1.0, c.d_uacc, st));
+    CU(axpby(nl, 1.0, c.d_lam, 1.0, c.d_lamacc, st));
+  }
+  // the loads of the corrections are the successive residuals, which do not
+  // sum to f: u is the sum of the corrections (kept for the recovery), lambda
+  // the sum of their multipliers
+  CU(cudaMemcpyAsync(c.d_fglob, c.d_f0, nd * sizeof(double), cudaMemcpyDeviceToDevice, st));
+  TRY(load_rhs(c));
+  CU(cudaMemcpyAsync(c.d_lam, c.d_lamacc, nl * sizeof(double), cudaMemcpyDeviceToDevice, st));
+  c.u_refined = 1;
+  S.eps0 = 1.0;
+  S.eps = rel;
+  S.converged = rel <= c.opt.tol;
+  S.refinements = outer;
+  return FETI_OK;
+}
+
 static feti_status solve_impl(Ctx& c, double* lambda_inout, feti_stats* stats) {
   const HostProblem& hp = c.hp;
   const int64_t nl = hp.n_lam;
@@ -1645,6 +1747,7 @@ static feti_status solve_impl(Ctx& c, double* lambda_inout, feti_stats* stats) {
     CU(axpby(nl, 1.0, c.d_lam0, 1.0, c.d_lam, st));
   }
   feti_status result = FETI_OK;
+  c.u_refined = 0;
   double eps_ref = -1.0;
   if (lambda_inout && hp.n_prob == 1) TRY(cold_reference(c, &eps_ref));
   if (hp.n_prob > 1) {
@@ -1676,6 +1779,8 @@ static feti_status solve_impl(Ctx& c, double* lambda_inout, feti_stats* stats) {
     TRY(project(c, c.d_r, nl, 1));
     result = krylov_core(c, c.opt.tol, c.opt.max_iter, false, S, eps_ref);
     CU(axpby(nl, 1.0, c.d_lamt, 1.0, c.d_lam, st));
+  } else if (c.opt.refine == FETI_REFINE_PRIMAL) {
+    TRY(refine_primal(c, S, result));
   } else {
     // FP64 iterative refinement on the dual residual: r = P^T (d - F lambda)
     // with the FP64 operator; each correction solves F dl = r with the
@@ -1768,6 +1873,33 @@ feti_status feti_solve_dual(feti_ctx* ctx, double* lambda_inout, feti_stats* sta
   return s;
 }
 
+}  // extern "C"
+
+// u (c.d_uglob) from the multipliers lam and the current load (Eq. 7 / Eq. 12
+// back-substitution; TFETI: alpha = (G G^T)^{-1} G (d - F lambda) first).
+static feti_status recover_u(Ctx& c, const double* lam) {
+  const HostProblem& hp = c.hp;
+  cudaStream_t st = c.stream;
+  if (hp.method == FETI_FETIDP) {
+    CU(recover_fetidp(c, lam, st));
+  } else {
+    const int64_t nl = hp.n_lam;
+    const int nco = c.n_coarse;
+    TRY(ensure_krylov(c, 1));
+    TRY(apply_dual(c, lam, nl, 1, c.d_r, nl));
+    CU(axpby(nl, 1.0, c.d_d, -1.0, c.d_r, st));
+    TRY(ensure_blocks(c, 1));
+    CU(gather_lam_to_b(c, c.d_r, nl, 1, c.d_Xb, st));
+    CU(tfeti_G_apply(c, c.d_Xb, 1, c.d_ct1, st));
+    CU(gemv_dense(c.d_Kbar_inv, nco, nco, c.d_ct1, c.d_alpha, 0.0, st));
+    CU(recover_tfeti(c, lam, c.d_alpha, st));
+  }
+  CU(launch_gather_u(c, st));
+  return FETI_OK;
+}
+
+extern "C" {
+
 feti_status feti_recover_displacements(feti_ctx* ctx, double* u_out, int on_device, double* compliance_out) {
   if (!ctx) return FETI_EINVAL;
   Ctx& c = ctx->c;
@@ -1776,22 +1908,8 @@ feti_status feti_recover_displacements(feti_ctx* ctx, double* u_out, int on_devi
   const HostProblem& hp = c.hp;
   cudaStream_t st = c.stream;
   std::unique_ptr<PhaseScope> phase(new PhaseScope(st, FETI_PHASE_RECOVER, 0.0));
-  if (hp.method == FETI_FETIDP) {
-    CU(recover_fetidp(c, c.d_lam, st));
-  } else {
-    // alpha = (G G^T)^{-1} G (d - F lambda)
-    const int64_t nl = hp.n_lam;
-    const int nco = c.n_coarse;
-    TRY(ensure_krylov(c, 1));
-    TRY(apply_dual(c, c.d_lam, nl, 1, c.d_r, nl));
-    CU(axpby(nl, 1.0, c.d_d, -1.0, c.d_r, st));
-    TRY(ensure_blocks(c, 1));
-    CU(gather_lam_to_b(c, c.d_r, nl, 1, c.d_Xb, st));
-    CU(tfeti_G_apply(c, c.d_Xb, 1, c.d_ct1, st));
-    CU(gemv_dense(c.d_Kbar_inv, nco, nco, c.d_ct1, c.d_alpha, 0.0, st));
-    CU(recover_tfeti(c, c.d_lam, c.d_alpha, st));
-  }
-  CU(launch_gather_u(c, st));
+  if (c.u_refined) CU(cudaMemcpyAsync(c.d_uglob, c.d_uacc, hp.n_dofs * sizeof(double), cudaMemcpyDeviceToDevice, st));
+  else TRY(recover_u(c, c.d_lam));
   phase.reset();
   if (u_out)
     CU(cudaMemcpyAsync(u_out, c.d_uglob, hp.n_dofs * sizeof(double),
@@ -1813,6 +1931,35 @@ feti_status feti_recover_displacements(feti_ctx* ctx, double* u_out, int on_devi
   }
   TRY(sync_check(c));
   c.state = 4;
+  return FETI_OK;
+}
+
+feti_status feti_primal_residual(feti_ctx* ctx, const double* u, double* r, double* rel) {
+  if (!ctx) return FETI_EINVAL;
+  Ctx& c = ctx->c;
+  c.err.clear();
+  if (c.state < 2) { c.err = "feti_primal_residual before feti_factorize"; return FETI_ESTATE; }
+  const int64_t nd = c.hp.n_dofs;
+  cudaStream_t st = c.stream;
+  double* out = r;
+  if (!out) {
+    if (!c.d_rres) TRY(dalloc(c, c.d_rres, nd));
+    out = c.d_rres;
+  }
+  if (rel) {
+    CU(launch_residual(c, c.d_fglob, nullptr, out, st));
+    CU(dot(out, out, nd, c.d_red, c.d_scalar, st));
+    double fn2 = 0.0;
+    TRY(read_scalar(c, c.d_scalar, &fn2));
+    CU(launch_residual(c, c.d_fglob, u, out, st));
+    CU(dot(out, out, nd, c.d_red, c.d_scalar, st));
+    double rn2 = 0.0;
+    TRY(read_scalar(c, c.d_scalar, &rn2));
+    *rel = fn2 > 0.0 ? std::sqrt(rn2 / fn2) : std::sqrt(rn2);
+  } else {
+    CU(launch_residual(c, c.d_fglob, u, out, st));
+  }
+  TRY(sync_check(c));
   return FETI_OK;
 }
 

@@ -211,6 +211,50 @@ __global__ void k_grad(int dim, int n_prob, const int64_t* __restrict__ el_off, 
   out[ge] = -p * pow(rho[ge], p - 1.0) * (E0 - Emin) * en;
 }
 
+// r = f - K u element by element (Eq. 2 with the SIMP moduli E_e of Eq. 1),
+// one thread per global DOF: the DOF's row of every element around its node,
+// the elements taken in a fixed order (x, then y, then z offset), so that the
+// sum is deterministic; fixed DOFs get r = 0 (u null: u = 0).  Problems of a batch are
+// numbered consecutively (tables dof_off, el_off, nel).
+__global__ void k_residual(int dim, int n_prob, const int64_t* __restrict__ dof_off,
+                           const int64_t* __restrict__ el_off, const int* __restrict__ pnel,
+                           const double* __restrict__ E, const double* __restrict__ k0,
+                           const unsigned char* __restrict__ dirichlet, const double* __restrict__ f,
+                           const double* __restrict__ u, double* __restrict__ r) {
+  const int64_t gq = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (gq >= dof_off[n_prob]) return;
+  int lo = 0, hi = n_prob;                       // problem containing DOF gq
+  while (hi - lo > 1) {
+    const int mid = (lo + hi) / 2;
+    if (dof_off[mid] <= gq) lo = mid; else hi = mid;
+  }
+  if (dirichlet[gq]) { r[gq] = 0.0; return; }
+  if (!u) { r[gq] = f[gq]; return; }            // u = 0: the free part of f
+  const int nel0 = pnel[3 * lo], nel1 = pnel[3 * lo + 1], nel2 = dim == 3 ? pnel[3 * lo + 2] : 1;
+  const int64_t q = gq - dof_off[lo];
+  const int64_t node = q / dim;
+  const int comp = (int)(q % dim);
+  const int64_t nn0 = nel0 + 1, nn1 = nel1 + 1;
+  const int64_t nx = node % nn0, ny = (node / nn0) % nn1, nz = node / (nn0 * nn1);
+  const int nen = 1 << dim, nek = nen * dim;
+  const double* up = u + dof_off[lo];
+  const double* Ep = E + el_off[lo];
+  double acc = f[gq];
+  for (int o = 0; o < nen; ++o) {                // element at (nx, ny, nz) minus offset o
+    const int64_t ex = nx - (o & 1), ey = ny - ((o >> 1) & 1), ez = nz - ((o >> 2) & 1);
+    if (ex < 0 || ey < 0 || ez < 0 || ex >= nel0 || ey >= nel1 || ez >= nel2) continue;
+    const int ln = o;                            // the node's local index in that element
+    const int row = ln * dim + comp;
+    double s = 0.0;
+    for (int a = 0; a < nen; ++a) {
+      const int64_t an = (ex + (a & 1)) + nn0 * ((ey + ((a >> 1) & 1)) + nn1 * (ez + ((a >> 2) & 1)));
+      for (int d = 0; d < dim; ++d) s = fma(k0[row * nek + a * dim + d], up[an * dim + d], s);
+    }
+    acc = fma(-Ep[ex + (int64_t)nel0 * (ey + (int64_t)nel1 * ez)], s, acc);
+  }
+  r[gq] = acc;
+}
+
 }  // namespace
 
 // Reference element stiffness for E = 1 (plane stress in 2D), by 2-point
@@ -334,6 +378,14 @@ cudaError_t launch_gather_u(const Ctx& c, cudaStream_t st) {
   const int64_t n = c.hp.n_dofs;
   k_gather_u<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(n, c.d_dof_copy_off, c.d_dof_copy, c.d_dirichlet,
                                                           c.d_uloc, c.d_uglob);
+  note_launches(1);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_residual(const Ctx& c, const double* f, const double* u, double* r, cudaStream_t st) {
+  const int64_t n = c.hp.n_dofs;
+  k_residual<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(c.hp.dim, c.hp.n_prob, c.d_prob_dof_off, c.d_prob_el_off,
+                                                          c.d_prob_nel, c.d_E, c.d_k0, c.d_dirichlet, f, u, r);
   note_launches(1);
   return cudaGetLastError();
 }

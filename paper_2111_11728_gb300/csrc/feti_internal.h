@@ -277,6 +277,10 @@ struct Ctx {
   double* d_sqrtDF = nullptr;    // [n_b_total] sqrt(diag F_s)
   double* d_sqrtDS = nullptr;    // [n_b_total] sqrt(diag S_s)
   double *d_rout = nullptr, *d_zout = nullptr, *d_dl = nullptr;   // refinement vectors
+  double *d_f0 = nullptr, *d_uacc = nullptr, *d_lamacc = nullptr;  // primal refinement: load, sums
+  double* d_ubest = nullptr;                                       // the best summed u so far
+  double* d_rres = nullptr;                                        // primal residual scratch [n_dofs]
+  int u_refined = 0;             // the last solve refined on the primal residual: u = d_uacc
   // per-problem tables (device)
   int64_t *d_prob_el_off = nullptr, *d_prob_dof_off = nullptr, *d_prob_lam_off = nullptr;
   int *d_prob_nel = nullptr, *d_prob_primal_off = nullptr;

@@ -80,6 +80,9 @@ cudaError_t launch_scaling_weights(const Ctx& c, int kind, cudaStream_t st);
 cudaError_t launch_load_gather(const Ctx& c, cudaStream_t st);
 cudaError_t launch_gather_u(const Ctx& c, cudaStream_t st);
 cudaError_t launch_grad(const Ctx& c, double* out, cudaStream_t st);
+// r = f - K u on the free DOFs (0 on the fixed ones), FP64, element by element
+// (moduli of the last factorization); u null: r = free part of f
+cudaError_t launch_residual(const Ctx& c, const double* f, const double* u, double* r, cudaStream_t st);
 
 // ---- factorization (factor.cu) ------------------------------------------------
 cudaError_t launch_band_chol(const Ctx& c, cudaStream_t st);

@@ -74,6 +74,10 @@ def test_option_combinations_rejected_before_any_device_call():
     d = fg.feti_options_default()
     d.precision = 5
     cases.append((d, fg.FETI_EINVAL))
+    assert o.refine == fg.FETI_REFINE_DUAL
+    e_ = fg.feti_options_default()
+    e_.refine = 2                                       # no such refinement residual
+    cases.append((e_, fg.FETI_EINVAL))
     for opt, status in cases:
         with pytest.raises(fg.FetiError) as e:
             fg.feti_create(opt)
