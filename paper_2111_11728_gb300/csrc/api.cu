@@ -809,76 +809,25 @@ static feti_status setup_impl(Ctx& c, const feti_problem* probs, int n) {
     TRY(upload(c, c.d_frow, frow));
     TRY(upload(c, c.d_bpad, bpad));
     {
-      // Operand slots seen from the multiplier rows.  The rows are cut into
-      // ranges of at most kSpreadRows consecutive rows such that every
-      // interface DOF has all its rows in one range (the rows of a shared DOF
-      // are consecutive: they are emitted together); each range lists the
-      // slots whose rows it holds, in slot order, with their signed rows.
-      auto xpos = [&](int b) { const int s = hp.b_sub[b]; return (int64_t)(bpad[s] + (b - hp.b_off[s])); };
-      const int64_t nbt = hp.n_b_total;
-      std::vector<int> cut_bad(nl + 2, 0);    // > 0: no cut between rows l-1 and l
-      for (int64_t b = 0; b < nbt; ++b) {
-        const int q0 = hp.b2l_off[b], q1 = hp.b2l_off[b + 1];
-        if (q1 - q0 < 2) continue;
-        int lo = hp.b2l_lam[q0], hi = lo;
-        for (int q = q0; q < q1; ++q) { lo = std::min(lo, hp.b2l_lam[q]); hi = std::max(hi, hp.b2l_lam[q]); }
-        cut_bad[lo + 1]++;
-        cut_bad[hi + 1]--;
+      // the precision form's operand built from the multiplier side (ranges of
+      // consecutive rows, the slots whose rows each range holds)
+      std::vector<int64_t> pos_of_b(std::max<int64_t>(hp.n_b_total, 1));
+      for (int64_t b = 0; b < hp.n_b_total; ++b) {
+        const int s = hp.b_sub[b];
+        pos_of_b[b] = bpad[s] + (b - hp.b_off[s]);
       }
-      for (int64_t l = 1; l <= nl; ++l) cut_bad[l] += cut_bad[l - 1];
-      std::vector<int> row0{0};
-      for (int64_t l0 = 0; l0 < nl;) {
-        int64_t l1 = std::min<int64_t>(l0 + kSpreadRows, nl);
-        while (l1 > l0 && l1 < nl && cut_bad[l1] > 0) --l1;
-        if (l1 == l0) {
-          c.err = "precision form: an interface DOF has multiplier rows more than " +
-                  std::to_string(kSpreadRows) + " rows apart";
-          return FETI_ENOTSUP;
-        }
-        row0.push_back((int)l1);
-        l0 = l1;
-      }
-      const int nr = (int)row0.size() - 1;
-      // slots by range (the range of their first row), then those with one row
-      // before those with several, each by position
-      std::vector<std::vector<std::pair<int64_t, int>>> by_range(nr);
-      {
-        std::vector<int> range_of(std::max<int64_t>(nl, 1));
-        for (int r = 0; r < nr; ++r)
-          for (int l = row0[r]; l < row0[r + 1]; ++l) range_of[l] = r;
-        for (int64_t b = 0; b < nbt; ++b) {
-          if (hp.b2l_off[b + 1] == hp.b2l_off[b]) continue;
-          int lo = hp.b2l_lam[hp.b2l_off[b]];
-          for (int q = hp.b2l_off[b]; q < hp.b2l_off[b + 1]; ++q) lo = std::min(lo, hp.b2l_lam[q]);
-          const bool multi = hp.b2l_off[b + 1] - hp.b2l_off[b] > 1;
-          by_range[range_of[lo]].push_back({xpos((int)b) + (multi ? ((int64_t)1 << 40) : 0), (int)b});
-        }
-      }
-      std::vector<int> slot_off{0}, slot_pos, slot_b, ent_off{0};
-      std::vector<short> ent;
-      for (int r = 0; r < nr; ++r) {
-        std::sort(by_range[r].begin(), by_range[r].end());
-        for (const auto& pb : by_range[r]) {
-          const int b = pb.second;
-          slot_pos.push_back((int)(pb.first & (((int64_t)1 << 40) - 1)));
-          slot_b.push_back(b);
-          for (int q = hp.b2l_off[b]; q < hp.b2l_off[b + 1]; ++q) {
-            const int rel = hp.b2l_lam[q] - row0[r];
-            ent.push_back((short)(hp.b2l_sign[q] > 0 ? rel : ~rel));
-          }
-          ent_off.push_back((int)ent.size());
-        }
-        slot_off.push_back((int)slot_pos.size());
-      }
-      c.n_spread_ranges = nr;
-      c.n_spread_slots = (int)slot_pos.size();
-      TRY(upload(c, c.d_sp_row0, row0));
-      TRY(upload(c, c.d_sp_slot_off, slot_off));
-      TRY(upload(c, c.d_sp_pos, slot_pos));
-      TRY(upload(c, c.d_sp_b, slot_b));
-      TRY(upload(c, c.d_sp_ent_off, ent_off));
-      TRY(upload(c, c.d_sp_ent, ent));
-      TRY(dalloc(c, c.d_sp_sd, std::max<size_t>(slot_pos.size(), 1)));
+      SpreadTables sp;
+      const std::string msg = build_spread_tables(hp, pos_of_b, kSpreadRows, sp);
+      if (!msg.empty()) { c.err = "precision form: " + msg; return FETI_ENOTSUP; }
+      c.n_spread_ranges = (int)sp.row0.size() - 1;
+      c.n_spread_slots = (int)sp.slot_pos.size();
+      TRY(upload(c, c.d_sp_row0, sp.row0));
+      TRY(upload(c, c.d_sp_slot_off, sp.slot_off));
+      TRY(upload(c, c.d_sp_pos, sp.slot_pos));
+      TRY(upload(c, c.d_sp_b, sp.slot_b));
+      TRY(upload(c, c.d_sp_ent_off, sp.ent_off));
+      TRY(upload(c, c.d_sp_ent, sp.ent));
+      TRY(dalloc(c, c.d_sp_sd, std::max<size_t>(sp.slot_pos.size(), 1)));
     }
     const size_t fa_bytes = (size_t)(c.fa_rows * c.fa_pitch) * tc_elem_bytes(c.opt.precision);
     TRY(dalloc_bytes(c, c.d_fa_hi, fa_bytes));

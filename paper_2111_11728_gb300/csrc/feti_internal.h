@@ -98,6 +98,22 @@ struct HostProblem {
 // DOFs).  All parts must share dim and method.
 std::string merge_host_problems(std::vector<HostProblem>& parts, HostProblem& out);
 
+// The multiplier rows cut into ranges of at most max_rows consecutive rows,
+// never between two rows of one interface DOF; per range the DOFs ("slots")
+// whose rows it holds -- those with one row first, then those with several,
+// each by position -- with their operand position pos_of_b[b], the DOF b and
+// its rows as offsets in the range (~offset for a row entering with sign -1),
+// in the DOF's row order.  DOFs without rows get no slot.
+struct SpreadTables {
+  std::vector<int> row0;        // [n_ranges + 1] first row of each range
+  std::vector<int> slot_off;    // [n_ranges + 1] slots of range r: [slot_off[r], slot_off[r + 1])
+  std::vector<int> slot_pos, slot_b;
+  std::vector<int> ent_off;     // [n_slots + 1]
+  std::vector<short> ent;
+};
+std::string build_spread_tables(const HostProblem& hp, const std::vector<int64_t>& pos_of_b, int max_rows,
+                                SpreadTables& out);
+
 // Builds the host description; returns an error message or "".  edge_mode:
 // 0 corners only, 1 every shared tile-grid edge averaged, 2 only the edges
 // across which the sharers' diagonal stiffness jumps by >= jump_ratio.

@@ -635,3 +635,66 @@ std::string merge_host_problems(std::vector<HostProblem>& parts, HostProblem& ou
 }
 
 }  // namespace feti
+
+namespace feti {
+
+std::string build_spread_tables(const HostProblem& hp, const std::vector<int64_t>& pos_of_b, int max_rows,
+                                SpreadTables& out) {
+  const int64_t nl = hp.n_lam, nbt = hp.n_b_total;
+  if (max_rows < 1 || max_rows > 32767) return "range length out of range";
+  out = SpreadTables{};
+  // cut_bad[l] > 0: some DOF has rows on both sides of the cut before row l
+  std::vector<int> cut_bad(nl + 2, 0);
+  std::vector<int> first(std::max<int64_t>(nbt, 1), -1);
+  for (int64_t b = 0; b < nbt; ++b) {
+    const int q0 = hp.b2l_off[b], q1 = hp.b2l_off[b + 1];
+    if (q1 == q0) continue;
+    int lo = hp.b2l_lam[q0], hi = lo;
+    for (int q = q0; q < q1; ++q) { lo = std::min(lo, hp.b2l_lam[q]); hi = std::max(hi, hp.b2l_lam[q]); }
+    first[b] = lo;
+    if (hi > lo) {
+      cut_bad[lo + 1]++;
+      cut_bad[hi + 1]--;
+    }
+  }
+  for (int64_t l = 1; l <= nl; ++l) cut_bad[l] += cut_bad[l - 1];
+  out.row0.push_back(0);
+  for (int64_t l0 = 0; l0 < nl;) {
+    int64_t l1 = std::min<int64_t>(l0 + max_rows, nl);
+    while (l1 > l0 && l1 < nl && cut_bad[l1] > 0) --l1;
+    if (l1 == l0) return "an interface DOF has multiplier rows more than " + std::to_string(max_rows) + " rows apart";
+    out.row0.push_back((int)l1);
+    l0 = l1;
+  }
+  const int nr = (int)out.row0.size() - 1;
+  std::vector<int> range_of(std::max<int64_t>(nl, 1), 0);
+  for (int r = 0; r < nr; ++r)
+    for (int l = out.row0[r]; l < out.row0[r + 1]; ++l) range_of[l] = r;
+  // key: (several rows?, position)
+  std::vector<std::vector<std::pair<std::pair<int, int64_t>, int>>> by_range(nr);
+  for (int64_t b = 0; b < nbt; ++b) {
+    if (first[b] < 0) continue;
+    const int multi = hp.b2l_off[b + 1] - hp.b2l_off[b] > 1 ? 1 : 0;
+    by_range[range_of[first[b]]].push_back({{multi, pos_of_b[b]}, (int)b});
+  }
+  out.slot_off.push_back(0);
+  out.ent_off.push_back(0);
+  for (int r = 0; r < nr; ++r) {
+    std::sort(by_range[r].begin(), by_range[r].end());
+    for (const auto& kb : by_range[r]) {
+      const int b = kb.second;
+      if (kb.first.second > (int64_t)0x7fffffff) return "operand position beyond 32 bits";
+      out.slot_pos.push_back((int)kb.first.second);
+      out.slot_b.push_back(b);
+      for (int q = hp.b2l_off[b]; q < hp.b2l_off[b + 1]; ++q) {
+        const int rel = hp.b2l_lam[q] - out.row0[r];
+        out.ent.push_back((short)(hp.b2l_sign[q] > 0 ? rel : ~rel));
+      }
+      out.ent_off.push_back((int)out.ent.size());
+    }
+    out.slot_off.push_back((int)out.slot_pos.size());
+  }
+  return "";
+}
+
+}  // namespace feti

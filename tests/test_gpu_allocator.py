@@ -28,6 +28,14 @@ def _solve(p, allocator):
 def test_torch_allocator_serves_all_internal_memory():
     torch = torch_cuda()
     p = workloads.config2(tiles=4, elems=8)
+    # the driver loads a kernel's code on its first launch (lazy module loading),
+    # in device memory of its own: launch every kernel of the pipeline once, in a
+    # throwaway context, before measuring
+    w = _solve(p, None)
+    fg.feti_solve_dual(w.ctx)
+    fg.feti_recover_displacements(w.ctx, torch.empty(p.n_dofs, dtype=torch.float64, device="cuda"), True)
+    w.close()
+    torch.cuda.synchronize()
     alloc = fg.TorchAllocator()
     s = _solve(p, alloc)
     assert alloc.n_alloc > 0 and alloc.bytes_held == s.query(fg.FETI_Q_DEVICE_BYTES)

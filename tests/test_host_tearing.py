@@ -22,6 +22,7 @@ CUDA_INC = "/usr/local/cuda/include"
 
 HARNESS = r'''
 #include <cstdio>
+#include <cstdlib>
 #include <vector>
 #include "feti_internal.h"
 using namespace feti;
@@ -95,7 +96,28 @@ int main(int argc, char** argv) {
     }
     fprintf(fo, "]");
   }
-  fprintf(fo, "]}\n");
+  fprintf(fo, "], \"lam_b\": [");
+  for (long long l = 0; l < hp.n_lam; ++l)
+    fprintf(fo, "%s[%d, %d, %d, %d]", l ? ", " : "", hp.lam_b0[l], (int)hp.lam_s0[l], hp.lam_b1[l], (int)hp.lam_s1[l]);
+  // the precision form's spread tables, positions = the DOF index
+  std::vector<int64_t> pos(hp.n_b_total);
+  for (long long b = 0; b < hp.n_b_total; ++b) pos[b] = b;
+  SpreadTables sp;
+  const int max_rows = argc > 3 ? atoi(argv[3]) : 128;
+  const std::string smsg = build_spread_tables(hp, pos, max_rows, sp);
+  fprintf(fo, "], \"n_b_total\": %lld, \"spread_error\": \"%s\", \"spread\": {", (long long)hp.n_b_total, smsg.c_str());
+  auto dump = [&](const char* name, const auto& v, bool last) {
+    fprintf(fo, "\"%s\": [", name);
+    for (size_t i = 0; i < v.size(); ++i) fprintf(fo, "%s%d", i ? ", " : "", (int)v[i]);
+    fprintf(fo, "]%s", last ? "" : ", ");
+  };
+  dump("row0", sp.row0, false);
+  dump("slot_off", sp.slot_off, false);
+  dump("slot_pos", sp.slot_pos, false);
+  dump("slot_b", sp.slot_b, false);
+  dump("ent_off", sp.ent_off, false);
+  dump("ent", sp.ent, true);
+  fprintf(fo, "}}\n");
   fclose(fo);
   return 0;
 }
@@ -116,7 +138,7 @@ def harness(tmp_path_factory):
     return exe, d
 
 
-def _run(harness, probs, method, edges):
+def _run(harness, probs, method, edges, max_rows=128):
     exe, d = harness
     inp, out = d / "in.bin", d / "out.json"
     with open(inp, "wb") as f:
@@ -132,7 +154,7 @@ def _run(harness, probs, method, edges):
             f.write(np.ascontiguousarray(p.rho, np.float64).tobytes())
             f.write(np.ascontiguousarray(p.dirichlet, np.uint8).tobytes())
             f.write(np.ascontiguousarray(p.f, np.float64).tobytes())
-    subprocess.run([str(exe), str(inp), str(out)], check=True, capture_output=True)
+    subprocess.run([str(exe), str(inp), str(out), str(max_rows)], check=True, capture_output=True)
     return json.loads(out.read_text())
 
 
@@ -217,3 +239,55 @@ def test_batch_merge_keeps_each_problems_tearing(harness, edges):
     assert got["n_primal"] == n_c and got["n_lam"] == n_lam
     assert _canon(got["rows"]) == _canon(rows)
     assert [sorted(b) for b in got["bsets"]] == bsets
+
+
+@pytest.mark.parametrize("max_rows", [128, 30])
+@pytest.mark.parametrize("method,edges,make", [CASES[1], CASES[3], CASES[4], CASES[5],
+                                               ("fetidp", False, lambda: workloads.config4(tiles=3, elems=2))])
+def test_spread_tables_reproduce_the_signed_rows(harness, method, edges, make, max_rows):
+    """The precision form's multiplier-side operand tables: ranges of at most
+    max_rows consecutive rows covering every row once; every interface DOF with
+    rows is one slot, inside the range that holds all of its rows; the slots'
+    signed entries are exactly the rows' entries (B, entry by entry); within a
+    range the single-row slots come first, each class in position order."""
+    p = make()
+    got = _run(harness, [p], method, edges, max_rows)
+    assert got["spread_error"] == ""
+    sp = got["spread"]
+    row0, soff, spos, sb, eoff, ent = (np.array(sp[k]) for k in ("row0", "slot_off", "slot_pos", "slot_b",
+                                                                   "ent_off", "ent"))
+    n_lam = got["n_lam"]
+    assert row0[0] == 0 and row0[-1] == n_lam
+    assert np.all(np.diff(row0) >= 1) and np.all(np.diff(row0) <= max_rows)
+    # B from the rows: (row, DOF) -> sign
+    want = {}
+    for l, (b0, s0, b1, s1) in enumerate(got["lam_b"]):
+        want[(l, b0)] = s0
+        if b1 >= 0:
+            want[(l, b1)] = s1
+    have = {}
+    for r in range(len(row0) - 1):
+        slots = range(soff[r], soff[r + 1])
+        multi = [eoff[q + 1] - eoff[q] > 1 for q in slots]
+        assert multi == sorted(multi)                        # single-row slots first
+        for cls in (False, True):
+            ps = [spos[q] for q, m in zip(slots, multi) if m == cls]
+            assert ps == sorted(ps)
+        for q in slots:
+            assert spos[q] == sb[q]                          # positions given as the DOF index
+            for t in range(eoff[q], eoff[q + 1]):
+                e = int(ent[t])
+                rel, sign = (e, 1) if e >= 0 else (~e, -1)
+                assert 0 <= rel < row0[r + 1] - row0[r]
+                key = (int(row0[r] + rel), int(sb[q]))
+                assert key not in have
+                have[key] = sign
+    assert have == want
+    assert len(set(sb.tolist())) == len(sb)                  # one slot per DOF
+
+
+def test_spread_tables_refuse_a_dof_wider_than_a_range(harness):
+    """A DOF shared by eight subdomains (TFETI, 3D) has its copies' rows spread
+    over its 28 pair-wise rows: ranges shorter than that cannot hold them."""
+    got = _run(harness, [workloads.config4(tiles=2, elems=2)], "tfeti", False, 9)
+    assert "rows apart" in got["spread_error"]
