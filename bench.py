@@ -247,9 +247,11 @@ def oracle_sample(a, tiles=8):
     t0 = time.perf_counter()
     u, lam, info, op = oracle.solve(p, "fetidp", "k", "rrs", tol=a.tol)
     dt = time.perf_counter() - t0
-    return info.f_applies / dt, dt, (f"oracle FETI-DP+k+RRS full step (build+solve+recover) on a {tiles}x{tiles}-tile "
-                                     f"sample of the same {a.elems}x{a.elems} modules: {info.f_applies} F-applies, "
-                                     f"{info.iterations} iterations, {dt:.1f} s")
+    where = (f"the bench workload itself ({tiles}x{tiles} subdomains of {a.elems}x{a.elems})"
+             if tiles == getattr(a, "tiles", None) else
+             f"a {tiles}x{tiles}-tile sample of the same {a.elems}x{a.elems} modules")
+    return info.f_applies / dt, dt, (f"oracle FETI-DP+k+RRS full step (build+solve+recover) on {where}: "
+                                     f"{info.f_applies} F-applies, {info.iterations} iterations, {dt:.1f} s")
 
 
 def oracle_full_size(a, p):

@@ -223,7 +223,7 @@ feti_status gemm_tn(Ctx& c, const double* A, int64_t lda, const double* B, int64
   d.A = A; d.B = B; d.C = C; d.M = M; d.N = N; d.K = K;
   d.ars = lda; d.acs = 1; d.brs = 1; d.bcs = ldb; d.crs = 1; d.ccs = ldc;
   d.tri = lower ? 1 : 0;
-  const int splits = split_for(M, N, K);
+  const int splits = split_for(M, N, K, lower != 0);
   if (splits > 1) TRY(ensure_split(c, (int64_t)splits * M * N));
   // symmetric products: the algorithmic count is the lower triangle
   const double fl = lower ? (double)M * (M + 1.0) * K : -1.0;

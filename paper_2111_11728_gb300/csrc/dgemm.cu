@@ -260,12 +260,41 @@ cudaError_t dgemm_batched(const GemmDesc* d_desc, int n_batch, int max_m, int ma
   return cudaGetLastError();
 }
 
-int split_for(int M, int N, int K) {
-  int tiles = ((M + BM - 1) / BM) * ((N + BN - 1) / BN);
-  int want = (2 * 152 + tiles - 1) / tiles;           // about two CTAs per SM
-  int maxs = (K + 4 * BK - 1) / (4 * BK);             // keep >= 64 of K per split
-  int s = want < maxs ? want : maxs;
-  return s < 1 ? 1 : (s > 64 ? 64 : s);
+// K splits of an M x N product (lower: only the tiles on or below the
+// diagonal run) chosen to fill whole waves: the split count with the best ratio
+// of working CTAs to the resident slots of the waves they occupy (the device's
+// SMs times dgemm_kernel's occupancy), the smallest such count on ties, at
+// least 64 of K per split.  A grid one CTA past a wave would otherwise run a
+// whole extra wave.
+int split_for(int M, int N, int K, bool lower) {
+  static int slots = 0;
+  if (slots <= 0) {
+    int dev = 0, sms = 0, occ = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, dgemm_kernel, NT, 0);
+    cudaGetLastError();
+    slots = std::max(1, sms) * std::max(1, occ);
+  }
+  const int tm = (M + BM - 1) / BM, tn = (N + BN - 1) / BN;
+  int64_t tiles = (int64_t)tm * tn;
+  if (lower) {
+    tiles = 0;
+    for (int i = 0; i < tm; ++i)
+      for (int j = 0; j < tn; ++j)
+        if (j * BN <= i * BM + BM - 1) ++tiles;
+  }
+  if (tiles <= 0) return 1;
+  const int maxs = std::max(1, std::min(64, (K + 4 * BK - 1) / (4 * BK)));   // keep >= 64 of K per split
+  int best = 1;
+  double best_eff = -1.0;
+  for (int sp = 1; sp <= maxs; ++sp) {
+    const int64_t work = tiles * sp;
+    const int64_t waves = (work + slots - 1) / slots;
+    const double eff = (double)work / (double)(waves * slots);
+    if (eff > best_eff + 1e-12) { best_eff = eff; best = sp; }
+  }
+  return best;
 }
 
 cudaError_t dgemm_split(const GemmDesc& d, int splits, double* work, double alpha, double beta,

@@ -68,7 +68,7 @@ cudaError_t dgemm_split(const GemmDesc& d, int splits, double* work, double alph
                         cudaStream_t st, double alg_flops = -1.0);
 
 // Chooses a split count that fills the GPU for an M x N x K product.
-int split_for(int M, int N, int K);
+int split_for(int M, int N, int K, bool lower);   // K splits of a Gram-type FP64 product (whole waves)
 
 // ---- assembly (fem.cu) --------------------------------------------------------
 void element_stiffness_host(int dim, double nu, double* k0);
