@@ -1146,10 +1146,18 @@ static feti_status krylov_core(Ctx& c, double tol, int max_iter, bool lowp, feti
     double* Qi = c.hist_Q[it];
     c.hist_k.push_back(k);
     const double fl_T = (double)nl * k * (k + 1.0);   // 2 n nnz(U)
+    // Inside a reduced-precision inner solve Q_i = F W_i is one more apply of
+    // the k retained directions (tensor cores, a few ms) instead of the FP64
+    // transform Q T (an n_lambda x k x k triangular product on the FP64 pipe).
+    const bool q_by_apply = lowp && multi;
     {
-      PhaseScope ph(st, FETI_PHASE_GRAM, 2.0 * fl_T);
+      PhaseScope ph(st, FETI_PHASE_GRAM, (q_by_apply ? 1.0 : 2.0) * fl_T);
       TRY(gemm_perm_upper(c, c.d_Wb, nl, c.d_perm, c.d_T, m, Wi, nl, (int)nl, k, fl_T));
-      TRY(gemm_perm_upper(c, c.d_Qb, nl, c.d_perm, c.d_T, m, Qi, nl, (int)nl, k, fl_T));
+      if (!q_by_apply) TRY(gemm_perm_upper(c, c.d_Qb, nl, c.d_perm, c.d_T, m, Qi, nl, (int)nl, k, fl_T));
+    }
+    if (q_by_apply) {
+      TRY(applyF(Wi, k, Qi));
+      S.f_applies += k;
     }
     S.f_applies += m;
     // gamma = W^T r; lambda~ += W gamma; r -= P^T Q gamma
